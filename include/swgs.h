@@ -1,0 +1,264 @@
+/*
+ * swgs.h -- C ABI of libswgs, a B300 (sm_103a) implementation of the hot path
+ * of SwinGS (arXiv 2409.07759): differentiable tile-based splatting of the
+ * frame-t active set, the SGLD noise / relocation step, and per-frame slice
+ * replacement.
+ *
+ * Conventions shared by every entry point:
+ *  - All Gaussian, image and gradient buffers are caller-owned DEVICE memory
+ *    unless an argument says "host". The library never frees them.
+ *  - Scratch memory is obtained only through the alloc/free callbacks given to
+ *    swgs_create (or cudaMallocAsync/cudaFreeAsync when they are NULL) and is
+ *    cached inside the context between calls.
+ *  - Work is enqueued on the CUDA stream passed as `stream` (a cudaStream_t,
+ *    NULL = legacy default stream). A context must be used from one stream at a
+ *    time; use one context per stream for concurrent work.
+ *  - Every call returns a swgs_status. On failure swgs_last_error(ctx) gives a
+ *    description. No entry point aborts, asserts or traps on the device.
+ *  - Inputs must be finite; quaternions need not be normalised.
+ */
+#ifndef SWGS_H
+#define SWGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SWGS_ABI_VERSION 1
+
+typedef enum swgs_status {
+    SWGS_OK = 0,
+    SWGS_EINVAL = 1,   /* bad shape, pointer or argument */
+    SWGS_ENOMEM = 2,   /* the allocator failed */
+    SWGS_ECUDA = 3,    /* a CUDA runtime call failed */
+    SWGS_ETIMEOUT = 4, /* a bounded device wait expired */
+    SWGS_EDEVICE = 5,  /* a kernel raised the device error word */
+    SWGS_ESTATE = 6    /* stale or mismatched saved state / slice */
+} swgs_status;
+
+/* Scratch allocator: returns device memory usable on `stream` (NULL on
+ * failure). free receives the same pointer and size. */
+typedef void *(*swgs_alloc_fn)(void *user, size_t bytes, void *stream);
+typedef void (*swgs_free_fn)(void *user, void *ptr, size_t bytes, void *stream);
+
+/* Renderer configuration (the paper leaves the renderer to 3DGS [13]; these
+ * are the launch shapes the autotuner chooses among). */
+typedef struct swgs_config {
+    int32_t tile_w, tile_h;  /* 8x8, 16x16 or 32x8 pixels per tile */
+    int32_t batch;           /* Gaussians staged in shared memory per block step:
+                                32, 64, 128 or 256 */
+    float near_plane;        /* camera-space z below which Gaussians are culled */
+    int32_t blocks_per_sm;   /* persistent blend grid = SMs x this; 0 = auto */
+    int32_t count_pairs;     /* 1: count evaluated (pixel, Gaussian) pairs */
+} swgs_config;
+
+/*
+ * Gaussian state, slot-major structure of arrays, all device pointers
+ * (Sec. 2.1 Eq. 1-2 attributes; Sec. 4.2 lifespans):
+ *   means[N*3], log_scales[N*3] (scale = exp), quats[N*4] (w,x,y,z,
+ *   unnormalised), opacity_logits[N] (opacity = sigmoid), sh[N*K*3]
+ *   (K = (sh_degree+1)^2 coefficients, each an rgb triple),
+ *   start[N], expire[N], birth[N] (int32 frames; a slot renders at frame t iff
+ *   start <= t < expire -- Alg. 1 and Alg. 2 filters),
+ *   frozen[N] (uint8, 1 = matured: rendered, never receives a gradient, noise
+ *   or relocation -- Alg. 1 'matured').
+ * For gradient buffers only the five float arrays are used.
+ */
+typedef struct swgs_gaussians {
+    float *means;
+    float *log_scales;
+    float *quats;
+    float *opacity_logits;
+    float *sh;
+    int32_t *start;
+    int32_t *expire;
+    int32_t *birth;
+    uint8_t *frozen;
+    int64_t capacity;
+    int32_t sh_degree; /* 0..3 (the paper trains with 1, Sec. 8.1) */
+} swgs_gaussians;
+
+/* Pinhole view, OpenCV axes (x right, y down, z forward): p_cam = R p + t
+ * with R row-major; pixel (i, j) is sampled at (i + 0.5, j + 0.5) where the
+ * projection is u = fx x/z + cx, v = fy y/z + cy. `frame` selects the active
+ * set this view renders (Alg. 1 sample_frame_between / Alg. 2 frame). */
+typedef struct swgs_view {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    int32_t frame;
+} swgs_view;
+
+typedef struct swgs_ctx swgs_ctx;
+typedef struct swgs_saved swgs_saved;
+
+/* Fills cfg with 16x16 tiles, batch 256, near plane 0.2, auto grid. */
+swgs_status swgs_default_config(swgs_config *cfg);
+
+/* Creates a context on the current CUDA device. alloc/free may be NULL. */
+swgs_status swgs_create(const swgs_config *cfg, swgs_alloc_fn alloc, swgs_free_fn free_fn,
+                        void *user, swgs_ctx **out);
+
+/* Releases every scratch buffer and saved state of the context. */
+void swgs_destroy(swgs_ctx *ctx);
+
+/* Text of the last error of this context ("" if none). Valid until the next call. */
+const char *swgs_last_error(const swgs_ctx *ctx);
+
+/* Library ABI version (SWGS_ABI_VERSION). */
+int32_t swgs_abi_version(void);
+
+/*
+ * Active-set compaction (Sec. 4.2; Alg. 1 gs.filter / Alg. 2 buffer.filter):
+ * writes the slots i with start[i] <= frame < expire[i], ascending, to
+ * out_ids[0..count) (device, capacity n) and count to *out_count (device
+ * int32). start/expire: device int32[n].
+ */
+swgs_status swgs_active_ids(swgs_ctx *ctx, const int32_t *start, const int32_t *expire, int64_t n,
+                            int32_t frame, int32_t *out_ids, int32_t *out_count, void *stream);
+
+/*
+ * Per-frame slice replacement (Alg. 2 update_thread, Alg. 1 mature rewrite):
+ * overwrites slots [first, first+count) of dst with src's slots [0, count):
+ * every attribute, the three lifespan arrays and frozen. src lives in pinned
+ * host memory when src_on_host = 1 (copied by DMA), else on the device
+ * (copied by a kernel). Both must have the same sh_degree; dst must hold
+ * first+count slots. Renders enqueued earlier on the same stream see the old
+ * slice; later ones the new.
+ */
+swgs_status swgs_frame_update(swgs_ctx *ctx, const swgs_gaussians *dst, int64_t first,
+                              int64_t count, const swgs_gaussians *src, int32_t src_on_host,
+                              void *stream);
+
+/*
+ * Forward render (Sec. 2.1 Eq. 3 over the frame-t active set) of n_views views,
+ * each at its own frame.
+ *   bg: host float[3] background; out_rgb[v]: device float[3*H*W] planar;
+ *   out_T[v] (optional, may be NULL or hold NULLs): device float[H*W] final
+ *   transmittance.
+ *   batched = 1: every stage runs once over all views; the blend is one
+ *   persistent launch over all (view, tile) work items.
+ *   batched = 0: the plain method, each view through its own launches.
+ *   saved: if non-NULL, receives the state the backward pass needs (final T,
+ *   last-contributor index, sorted lists, 2D records); release it with
+ *   swgs_saved_release. If NULL the call only renders.
+ * The call synchronises the stream twice (to size the record and key buffers).
+ */
+swgs_status swgs_render_fwd(swgs_ctx *ctx, const swgs_gaussians *g, int32_t n_views,
+                            const swgs_view *views, const float *bg, float *const *out_rgb,
+                            float *const *out_T, int32_t batched, swgs_saved **saved,
+                            void *stream);
+
+/*
+ * Backward of swgs_render_fwd (Alg. 1 loss.backward): given dL/drgb[v]
+ * (device float[3*H*W] planar, same views as the saved forward), ACCUMULATES
+ * into grads (device arrays with g's layout: means, log_scales, quats,
+ * opacity_logits, sh) the gradient with respect to the raw parameters. Frozen
+ * slots receive nothing. The blend is recomputed back to front from the saved
+ * final transmittance and last-contributor index. g must be unchanged since
+ * the forward.
+ */
+swgs_status swgs_render_bwd(swgs_ctx *ctx, const swgs_gaussians *g, const swgs_saved *saved,
+                            const float *const *dL_drgb, const swgs_gaussians *grads,
+                            void *stream);
+
+/* Returns a saved state to the context's pool (stream-ordered reuse). */
+swgs_status swgs_saved_release(swgs_ctx *ctx, swgs_saved *saved);
+
+typedef struct swgs_saved_info {
+    int32_t n_views;
+    int32_t n_batches;     /* 1 when batched, n_views for the plain path */
+    int64_t n_records;     /* (view, active Gaussian) pairs */
+    int64_t n_keys;        /* (Gaussian, tile) instances */
+    int64_t n_tiles;       /* tiles over all views */
+    int64_t n_pixels;      /* pixels over all views */
+    int64_t pairs;         /* evaluated (pixel, Gaussian) pairs (count_pairs = 1) */
+} swgs_saved_info;
+
+swgs_status swgs_saved_query(swgs_ctx *ctx, const swgs_saved *saved, swgs_saved_info *info);
+
+/* Intermediate arrays of a saved forward, copied to `dst` (device or host,
+ * `bytes` must match). Records, keys and tiles are concatenated over batches
+ * in view order; see the constants for element types. */
+enum {
+    SWGS_EXPORT_RECORD_SLOT = 0,  /* int32 per record: Gaussian slot */
+    SWGS_EXPORT_RECORD_VIEW = 1,  /* int32 per record: view index */
+    SWGS_EXPORT_RECORD_TILES = 2, /* int32 per record: tiles touched */
+    SWGS_EXPORT_RECORD_DEPTH = 3, /* float per record: camera depth (key) */
+    SWGS_EXPORT_RECORD_RECT = 4,  /* int32 x4 per record: tx0, tx1, ty0, ty1 */
+    SWGS_EXPORT_SORTED_SLOT = 5,  /* int32 per key: slot, per-tile depth order */
+    SWGS_EXPORT_TILE_RANGES = 6,  /* int32 x2 per tile: [begin, end) into keys */
+    SWGS_EXPORT_LAST = 7,         /* int32 per pixel: 1 + tile-list position */
+    SWGS_EXPORT_FINAL_T = 8,      /* float per pixel */
+    SWGS_EXPORT_GRAD2D = 9,       /* float x12 per record after a backward:
+                                     du, dv, dA, dB, dC, dopacity, dr, dg, db */
+    SWGS_EXPORT_RECORD_2D = 10    /* float x12 per record: u, v, opacity, depth,
+                                     A, B, C, -, r, g, b, - */
+};
+swgs_status swgs_saved_export(swgs_ctx *ctx, const swgs_saved *saved, int32_t what, void *dst,
+                              size_t bytes, void *stream);
+/* Element count of an export (records, keys, tiles or pixels). */
+swgs_status swgs_saved_count(swgs_ctx *ctx, const swgs_saved *saved, int32_t what,
+                             int64_t *count);
+
+/*
+ * L1 photometric term of Alg. 1 loss_func: loss = mean over views of
+ * mean |rgb - target| over 3*H*W; dL_drgb[v] = sign(rgb - target)/(3*H*W*V)
+ * (sign(0) = 0). rgb, target, dL_drgb: device float[3*H*W] per view; loss:
+ * device float[1], overwritten.
+ */
+swgs_status swgs_loss_l1(swgs_ctx *ctx, int32_t n_views, const swgs_view *views,
+                         const float *const *rgb, const float *const *target,
+                         float *const *dL_drgb, float *loss, void *stream);
+
+/* Optimiser / SGLD / relocation hyper-parameters (Sec. 4.4, 8.1; [14]). */
+typedef struct swgs_sgld_params {
+    float lr_means, lr_log_scales, lr_quats, lr_logits, lr_sh_dc, lr_sh_rest;
+    float beta1, beta2, eps;   /* Adam */
+    float noise_lr;            /* 5e4 in Sec. 8.1 */
+    float noise_k, noise_t;    /* noise gate sigmoid(-k (opacity - t)) */
+    int32_t adam;              /* 1: Adam step from grads before the noise */
+    int32_t relocate;          /* 1: relocate dead Gaussians after the noise */
+    int32_t max_n;             /* cap on copies per target in the formulas */
+} swgs_sgld_params;
+
+/* Adam moments, device arrays shaped like the five float parameter arrays. */
+typedef struct swgs_adam_state {
+    float *m_means, *v_means, *m_log_scales, *v_log_scales, *m_quats, *v_quats,
+          *m_logits, *v_logits, *m_sh, *v_sh;
+} swgs_adam_state;
+
+/*
+ * Alg. 1 steps after the backward, on the Gaussians eligible at this step
+ * (active at any of frames[0..n_frames) -- host int32 -- and not frozen):
+ *   1. if params->adam: one bias-corrected Adam step (step count step+1) from
+ *      grads (may be NULL otherwise);
+ *   2. SGLD noise mu += lr_means * noise_lr * sigmoid(-k (o - t)) Sigma eta,
+ *      eta ~ N(0, I) drawn from Philox4x64-10 keyed by (seed, step, slot);
+ *   3. if params->relocate: every dead (opacity <= 0.005) Gaussian copies an
+ *      alive one sampled in proportion to opacity, and both take the opacity
+ *      1 - (1 - o)^(1/N) and the rescaled scale of [14]; Adam moments of every
+ *      touched slot are zeroed (adam may be NULL when no Adam is used).
+ * targets: optional device int32[capacity]; receives for every slot the slot
+ * it copied in step 3, or -1.
+ * n_relocated: optional host pointer; if non-NULL the call synchronises and
+ * stores the number of relocated slots.
+ */
+swgs_status swgs_sgld_step(swgs_ctx *ctx, const swgs_gaussians *g, const swgs_gaussians *grads,
+                           const swgs_adam_state *adam, const int32_t *frames, int32_t n_frames,
+                           const swgs_sgld_params *params, uint64_t seed, uint64_t step,
+                           int32_t *targets, int64_t *n_relocated, void *stream);
+
+/* Alg. 2: slot range [first, first+count) that the update for target_frame
+ * overwrites: slice = target_frame mod swin_size, count = num_gs / swin_size. */
+swgs_status swgs_slice_range(int64_t target_frame, int64_t swin_size, int64_t num_gs,
+                             int64_t *first, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWGS_H */

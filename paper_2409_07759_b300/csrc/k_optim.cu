@@ -1,0 +1,290 @@
+// k_optim.cu -- the steps of Alg. 1 after the backward pass, on the Gaussians
+// eligible at this step (active at one of the step's frames, not frozen):
+//   - an optional bias-corrected Adam step (the optimiser of [14]);
+//   - the SGLD noise mu += lr * noise_lr * sigmoid(-k (o - t)) * Sigma eta
+//     (Alg. 1 noise step, Sec. 4.4; the noise form of [14]);
+//   - relocation of dead Gaussians onto alive ones sampled in proportion to
+//     opacity, with the opacity and scale adjustment of [14] (Sec. 3.2,
+//     Alg. 1 relocate).
+// Random numbers come from Philox4x64-10 keyed by (seed, purpose) with counter
+// (slot, step), so every draw is independent of launch shape and order.
+#include "swgs_internal.cuh"
+
+namespace swgs {
+
+constexpr int kMaxStepFrames = 64;
+
+struct SgldArgs {
+    swgs_gaussians g;
+    swgs_gaussians grads;
+    swgs_adam_state adam;
+    int has_grads, has_adam;
+    int frames[kMaxStepFrames];
+    int n_frames;
+    swgs_sgld_params p;
+    float bc1, bc2;  // Adam bias corrections 1 - beta^(step+1)
+    unsigned long long seed, step;
+};
+
+__device__ __forceinline__ bool is_eligible(const swgs_gaussians& g, long long i,
+                                            const int* frames, int nf) {
+    if (g.frozen && g.frozen[i]) return false;
+    const int s = g.start[i], e = g.expire[i];
+    for (int f = 0; f < nf; ++f)
+        if (s <= frames[f] && frames[f] < e) return true;
+    return false;
+}
+
+__device__ __forceinline__ void adam1(float* p, float* m, float* v, float g, float lr,
+                                      const SgldArgs& a) {
+    const float mm = a.p.beta1 * *m + (1.f - a.p.beta1) * g;
+    const float vv = a.p.beta2 * *v + (1.f - a.p.beta2) * g * g;
+    const float mh = mm / a.bc1, vh = vv / a.bc2;
+    *p = *p - lr * mh / (sqrtf(vh) + a.p.eps);
+    *m = mm;
+    *v = vv;
+}
+
+__global__ void __launch_bounds__(256) sgld_kernel(SgldArgs a) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.g.capacity) return;
+    if (!is_eligible(a.g, i, a.frames, a.n_frames)) return;
+    const int K = (a.g.sh_degree + 1) * (a.g.sh_degree + 1);
+    if (a.p.adam && a.has_grads && a.has_adam) {
+        for (int k = 0; k < 3; ++k) {
+            adam1(&a.g.means[3 * i + k], &a.adam.m_means[3 * i + k], &a.adam.v_means[3 * i + k],
+                  a.grads.means[3 * i + k], a.p.lr_means, a);
+            adam1(&a.g.log_scales[3 * i + k], &a.adam.m_log_scales[3 * i + k],
+                  &a.adam.v_log_scales[3 * i + k], a.grads.log_scales[3 * i + k],
+                  a.p.lr_log_scales, a);
+        }
+        for (int k = 0; k < 4; ++k)
+            adam1(&a.g.quats[4 * i + k], &a.adam.m_quats[4 * i + k], &a.adam.v_quats[4 * i + k],
+                  a.grads.quats[4 * i + k], a.p.lr_quats, a);
+        adam1(&a.g.opacity_logits[i], &a.adam.m_logits[i], &a.adam.v_logits[i],
+              a.grads.opacity_logits[i], a.p.lr_logits, a);
+        for (int k = 0; k < K; ++k)
+            for (int ch = 0; ch < 3; ++ch) {
+                const long long e = (i * K + k) * 3 + ch;
+                adam1(&a.g.sh[e], &a.adam.m_sh[e], &a.adam.v_sh[e], a.grads.sh[e],
+                      k == 0 ? a.p.lr_sh_dc : a.p.lr_sh_rest, a);
+            }
+    }
+    // noise from the (possibly updated) opacity and covariance
+    const float o = 1.f / (1.f + expf(-a.g.opacity_logits[i]));
+    const float gate = 1.f / (1.f + expf(a.p.noise_k * (o - a.p.noise_t)));
+    const float scale = a.p.lr_means * a.p.noise_lr * gate;
+    if (scale == 0.f) return;
+    float s[3];
+    for (int k = 0; k < 3; ++k) s[k] = expf(a.g.log_scales[3 * i + k]);
+    const float4 q4 = reinterpret_cast<const float4*>(a.g.quats)[i];
+    const float qi = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+    const float w = q4.x * qi, x = q4.y * qi, y = q4.z * qi, z = q4.w * qi;
+    const float R[3][3] = {
+        {1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
+        {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
+        {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
+    const U64x4 rnd = philox4x64_10((unsigned long long)i, a.step, 0ULL, 0ULL, a.seed, kTagNoise);
+    float u[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[k] = ((float)(rnd.v[k] >> 40) + 1.0f) * 0x1p-24f;
+    const float r0 = sqrtf(-2.f * logf(u[0])), r1 = sqrtf(-2.f * logf(u[2]));
+    float sn0, cs0, sn1, cs1;
+    sincospif(2.f * u[1], &sn0, &cs0);
+    sincospif(2.f * u[3], &sn1, &cs1);
+    const float eta[3] = {r0 * cs0, r0 * sn0, r1 * cs1};
+    // Sigma eta = R S^2 R^T eta
+    float tq[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tq[k] = (R[0][k] * eta[0] + R[1][k] * eta[1] + R[2][k] * eta[2]) * s[k] * s[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        a.g.means[3 * i + k] += scale * (R[k][0] * tq[0] + R[k][1] * tq[1] + R[k][2] * tq[2]);
+}
+
+cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
+                        const swgs_adam_state* adam, const int32_t* frames, int n_frames,
+                        const swgs_sgld_params& p, unsigned long long seed,
+                        unsigned long long step, cudaStream_t s) {
+    if (g.capacity <= 0) return cudaSuccess;
+    if (n_frames > kMaxStepFrames) return cudaErrorInvalidValue;
+    SgldArgs a{};
+    a.g = g;
+    if (grads) a.grads = *grads;
+    if (adam) a.adam = *adam;
+    a.has_grads = grads != nullptr;
+    a.has_adam = adam != nullptr;
+    for (int f = 0; f < n_frames; ++f) a.frames[f] = frames[f];
+    a.n_frames = n_frames;
+    a.p = p;
+    a.bc1 = (float)(1.0 - pow((double)p.beta1, (double)(step + 1)));
+    a.bc2 = (float)(1.0 - pow((double)p.beta2, (double)(step + 1)));
+    a.seed = seed;
+    a.step = step;
+    sgld_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Relocation
+// ---------------------------------------------------------------------------
+struct RelocArgs {
+    swgs_gaussians g;
+    int frames[kMaxStepFrames];
+    int n_frames;
+};
+
+// weight = floor(sigmoid(logit) 2^32) for alive eligible slots, 0 otherwise;
+// the sigmoid uses the polynomial exp so the integer matches any IEEE-754
+// implementation of the same operation sequence.
+__global__ void __launch_bounds__(256)
+reloc_weights_kernel(RelocArgs a, unsigned long long* __restrict__ weights,
+                     uint8_t* __restrict__ dead) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.g.capacity) return;
+    unsigned long long w = 0;
+    uint8_t d = 0;
+    if (is_eligible(a.g, i, a.frames, a.n_frames)) {
+        const float lg = a.g.opacity_logits[i];
+        if (lg <= kLogitDead) {
+            d = 1;
+        } else {
+            const double e = kd_exp(-(double)lg);
+            const double o = __ddiv_rn(1.0, __dadd_rn(1.0, e));
+            double f = floor(__dmul_rn(o, 4294967296.0));
+            if (f > 4294967295.0) f = 4294967295.0;
+            w = (unsigned long long)f;
+        }
+    }
+    weights[i] = w;
+    dead[i] = d;
+}
+
+cudaError_t launch_reloc_weights(const swgs_gaussians& g, const int32_t* frames, int n_frames,
+                                 unsigned long long* weights, uint8_t* dead, cudaStream_t s) {
+    if (n_frames > kMaxStepFrames) return cudaErrorInvalidValue;
+    RelocArgs a{};
+    a.g = g;
+    for (int f = 0; f < n_frames; ++f) a.frames[f] = frames[f];
+    a.n_frames = n_frames;
+    reloc_weights_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(a, weights, dead);
+    return cudaGetLastError();
+}
+
+// target = first j with cdf[j] > floor(r * total / 2^64), r the slot's draw.
+__global__ void __launch_bounds__(256)
+reloc_sample_kernel(long long n, const uint8_t* __restrict__ dead,
+                    const unsigned long long* __restrict__ cdf, unsigned long long seed,
+                    unsigned long long step, int32_t* __restrict__ targets,
+                    int32_t* __restrict__ counts, unsigned long long* __restrict__ n_dead) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long total = cdf[n - 1];
+    int32_t tg = -1;
+    if (dead[i] && total > 0) {
+        const U64x4 r = philox4x64_10((unsigned long long)i, step, 0ULL, 0ULL, seed, kTagReloc);
+        const unsigned long long x = __umul64hi(r.v[0], total);
+        long long lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const long long mid = lo + ((hi - lo) >> 1);
+            if (cdf[mid] > x) hi = mid; else lo = mid + 1;
+        }
+        tg = (int32_t)lo;
+        atomicAdd(&counts[lo], 1);
+        atomicAdd(n_dead, 1ULL);
+    }
+    targets[i] = tg;
+}
+
+cudaError_t launch_reloc_sample(const swgs_gaussians& g, const uint8_t* dead,
+                                const unsigned long long* cdf, unsigned long long seed,
+                                unsigned long long step, int32_t* targets, int32_t* counts,
+                                unsigned long long* n_dead, cudaStream_t s) {
+    reloc_sample_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(g.capacity, dead, cdf, seed,
+                                                                 step, targets, counts, n_dead);
+    return cudaGetLastError();
+}
+
+// 1 - (1-o)^(1/N) and the scale ratio o / sum_{k=1..N} C(N,k) (-1)^(k-1) o'^k / sqrt(k),
+// which equals [14]'s double sum over i <= N, k < i (hockey-stick identity).
+__device__ __forceinline__ void reloc_values(double o, int n, double* on, double* ratio) {
+    const double onew = 1.0 - pow(1.0 - o, 1.0 / (double)n);
+    double den = 0.0, c = 1.0, pw = 1.0;
+    for (int k = 1; k <= n; ++k) {
+        c = c * (double)(n - k + 1) / (double)k;
+        pw *= onew;
+        den += ((k & 1) ? 1.0 : -1.0) * c * pw / sqrt((double)k);
+    }
+    *on = onew;
+    *ratio = o / den;
+}
+
+__device__ __forceinline__ void zero_moments(const swgs_adam_state& m, long long i, int K) {
+    if (!m.m_means) return;
+    for (int k = 0; k < 3; ++k) {
+        m.m_means[3 * i + k] = 0.f; m.v_means[3 * i + k] = 0.f;
+        m.m_log_scales[3 * i + k] = 0.f; m.v_log_scales[3 * i + k] = 0.f;
+    }
+    for (int k = 0; k < 4; ++k) { m.m_quats[4 * i + k] = 0.f; m.v_quats[4 * i + k] = 0.f; }
+    m.m_logits[i] = 0.f; m.v_logits[i] = 0.f;
+    for (int k = 0; k < 3 * K; ++k) { m.m_sh[i * 3 * K + k] = 0.f; m.v_sh[i * 3 * K + k] = 0.f; }
+}
+
+// Phase 1 (before the targets change): each dead slot copies its target with
+// the target's relocated opacity and scale.
+__global__ void __launch_bounds__(256)
+reloc_copy_kernel(swgs_gaussians g, swgs_adam_state m, const int32_t* __restrict__ targets,
+                  const int32_t* __restrict__ counts, int max_n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.capacity) return;
+    const int32_t j = targets[i];
+    if (j < 0) return;
+    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    int nn = counts[j] + 1;
+    if (nn > max_n) nn = max_n;
+    const double o = 1.0 / (1.0 + exp(-(double)g.opacity_logits[j]));
+    double on, ratio;
+    reloc_values(o, nn, &on, &ratio);
+    for (int k = 0; k < 3; ++k) {
+        g.means[3 * i + k] = g.means[3 * (long long)j + k];
+        g.log_scales[3 * i + k] = (float)((double)g.log_scales[3 * (long long)j + k] + log(ratio));
+    }
+    for (int k = 0; k < 4; ++k) g.quats[4 * i + k] = g.quats[4 * (long long)j + k];
+    g.opacity_logits[i] = (float)(log(on) - log1p(-on));
+    for (int k = 0; k < 3 * K; ++k) g.sh[i * 3 * K + k] = g.sh[(long long)j * 3 * K + k];
+    zero_moments(m, i, K);
+}
+
+// Phase 2: every target takes its own relocated opacity and scale.
+__global__ void __launch_bounds__(256)
+reloc_target_kernel(swgs_gaussians g, swgs_adam_state m, const int32_t* __restrict__ counts,
+                    int max_n) {
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.capacity) return;
+    if (counts[j] == 0) return;
+    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    int nn = counts[j] + 1;
+    if (nn > max_n) nn = max_n;
+    const double o = 1.0 / (1.0 + exp(-(double)g.opacity_logits[j]));
+    double on, ratio;
+    reloc_values(o, nn, &on, &ratio);
+    for (int k = 0; k < 3; ++k)
+        g.log_scales[3 * j + k] = (float)((double)g.log_scales[3 * j + k] + log(ratio));
+    g.opacity_logits[j] = (float)(log(on) - log1p(-on));
+    zero_moments(m, j, K);
+}
+
+cudaError_t launch_reloc_apply(const swgs_gaussians& g, const swgs_adam_state* adam,
+                               const int32_t* targets, const int32_t* counts, int max_n,
+                               cudaStream_t s) {
+    swgs_adam_state m{};
+    if (adam) m = *adam;
+    const int grid = div_up(g.capacity, 256);
+    reloc_copy_kernel<<<grid, 256, 0, s>>>(g, m, targets, counts, max_n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    reloc_target_kernel<<<grid, 256, 0, s>>>(g, m, counts, max_n);
+    return cudaGetLastError();
+}
+
+}  // namespace swgs

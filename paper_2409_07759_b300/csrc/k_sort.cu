@@ -1,0 +1,236 @@
+// k_sort.cu -- stable LSD radix sort of (uint32 key, uint32 value) pairs.
+//
+// Each pass (<= 8 bits): an upsweep histogram per block over a contiguous
+// share of 4096-key tiles, an exclusive scan of the (digit, block) counts in
+// digit-major order, and a downsweep that ranks each tile stably (warp
+// match.any ranking, warps in order), stages the tile in shared memory in
+// digit order and writes it out, so global writes are contiguous within each
+// digit run. The grid is a fixed multiple of the SM count; block b owns the
+// same tile range in both kernels, so no waits between blocks are needed.
+//
+// Used twice per render: the per-record depth sort (32 bits) and the
+// per-key tile sort (ceil(log2(tiles)) bits). Sorting records by depth and
+// then keys stably by tile gives the order of a stable sort on
+// (tile << 32 | depth), the per-tile depth ordering of Eq. 3.
+#include "swgs_internal.cuh"
+
+namespace swgs {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096
+constexpr int kWarpSpan = 32 * kSortItems;             // 512 keys per warp
+constexpr int kMaxBins = 256;
+
+SortPlan make_sort_plan(int begin_bit, int end_bit) {
+    SortPlan p{};
+    int total = end_bit - begin_bit;
+    if (total <= 0) { p.passes = 0; p.begin_bit = begin_bit; return p; }
+    p.passes = (total + 7) / 8;
+    int base = total / p.passes, extra = total % p.passes;
+    for (int i = 0; i < p.passes; ++i) p.bits_per_pass[i] = base + (i < extra ? 1 : 0);
+    p.begin_bit = begin_bit;
+    return p;
+}
+
+static int sort_grid(long long n, int num_sms) {
+    long long tiles = (n + kSortTile - 1) / kSortTile;
+    long long g = (long long)num_sms * 2;
+    if (tiles < g) g = tiles;
+    return (int)(g < 1 ? 1 : g);
+}
+
+size_t radix_temp_bytes(long long n, int num_sms) {
+    int G = sort_grid(n, num_sms);
+    long long hist = (long long)kMaxBins * G + 1;
+    size_t b = (size_t)hist * sizeof(uint32_t);
+    b = (b + 255) & ~(size_t)255;
+    b += scan_u32_temp_bytes(hist);
+    b = (b + 255) & ~(size_t)255;
+    b += 256;  // total
+    return b;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+radix_upsweep(const uint32_t* __restrict__ keys, long long n, int shift, int bins,
+              int tiles_per_block, long long n_tiles, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[kSortWarps][kMaxBins];
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kSortWarps * kMaxBins; i += kSortThreads) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t mask = (uint32_t)bins - 1u;
+    const long long t0 = (long long)blockIdx.x * tiles_per_block;
+    long long t1 = t0 + tiles_per_block;
+    if (t1 > n_tiles) t1 = n_tiles;
+    for (long long t = t0; t < t1; ++t) {
+        const long long base = t * kSortTile;
+#pragma unroll 4
+        for (int it = 0; it < kSortItems; ++it) {
+            long long i = base + (long long)it * kSortThreads + threadIdx.x;
+            if (i < n) atomicAdd(&h[warp][(keys[i] >> shift) & mask], 1u);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < bins; d += kSortThreads) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) s += h[w][d];
+        hist[(long long)d * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+struct DownSmem {
+    uint32_t keys[kSortTile];
+    uint32_t vals[kSortTile];
+    uint32_t whist[kSortWarps][kMaxBins + 1];
+    uint32_t digoff[kMaxBins + 1];
+    uint32_t run[kMaxBins];
+    uint32_t cnt[kMaxBins + 1];
+    uint32_t warp_tot[kSortWarps];
+};
+
+__global__ void __launch_bounds__(kSortThreads)
+radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, long long n,
+                int shift, int bins, int tiles_per_block, long long n_tiles,
+                const uint32_t* __restrict__ offsets) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DownSmem& S = *reinterpret_cast<DownSmem*>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t mask = (uint32_t)bins - 1u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int d = threadIdx.x; d < bins; d += kSortThreads)
+        S.run[d] = offsets[(long long)d * gridDim.x + blockIdx.x];
+    const long long t0 = (long long)blockIdx.x * tiles_per_block;
+    long long t1 = t0 + tiles_per_block;
+    if (t1 > n_tiles) t1 = n_tiles;
+    for (long long t = t0; t < t1; ++t) {
+        const long long base = t * kSortTile;
+        const int valid = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
+        for (int i = threadIdx.x; i < kSortWarps * (kMaxBins + 1); i += kSortThreads)
+            (&S.whist[0][0])[i] = 0;
+        __syncthreads();
+        uint32_t k[kSortItems], v[kSortItems], dg[kSortItems], rk[kSortItems];
+#pragma unroll
+        for (int it = 0; it < kSortItems; ++it) {
+            const int local = warp * kWarpSpan + it * 32 + lane;
+            const long long i = base + local;
+            if (local < valid) {
+                k[it] = keys_in[i];
+                v[it] = vals_in ? vals_in[i] : (uint32_t)i;
+                dg[it] = (k[it] >> shift) & mask;
+            } else {
+                k[it] = 0; v[it] = 0; dg[it] = (uint32_t)bins;  // sentinel bucket
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < kSortItems; ++it) {
+            const unsigned peers = __match_any_sync(0xffffffffu, dg[it]);
+            const int leader = __ffs(peers) - 1;
+            uint32_t b = 0;
+            if (lane == leader) {
+                b = S.whist[warp][dg[it]];
+                S.whist[warp][dg[it]] = b + (uint32_t)__popc(peers);
+            }
+            b = __shfl_sync(0xffffffffu, b, leader);
+            rk[it] = b + (uint32_t)__popc(peers & lt_mask);
+        }
+        __syncthreads();
+        // per digit: exclusive prefix over warps, and the tile's digit count
+        for (int d = threadIdx.x; d <= bins; d += kSortThreads) {
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) {
+                uint32_t c = S.whist[w][d];
+                S.whist[w][d] = run;
+                run += c;
+            }
+            S.cnt[d] = run;
+        }
+        __syncthreads();
+        // exclusive scan of the digit counts (bins <= 256 = one per thread)
+        {
+            uint32_t c = threadIdx.x < bins ? S.cnt[threadIdx.x] : 0u;
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) S.warp_tot[warp] = incl;
+            __syncthreads();
+            uint32_t wpre = 0;
+#pragma unroll
+            for (int w = 0; w < kSortWarps; ++w) wpre += (w < warp) ? S.warp_tot[w] : 0u;
+            if (threadIdx.x < bins) S.digoff[threadIdx.x] = wpre + incl - c;
+            if (threadIdx.x == 0) S.digoff[bins] = (uint32_t)valid;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < kSortItems; ++it) {
+            if (dg[it] < (uint32_t)bins) {
+                const uint32_t pos = S.digoff[dg[it]] + S.whist[warp][dg[it]] + rk[it];
+                S.keys[pos] = k[it];
+                S.vals[pos] = v[it];
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < valid; i += kSortThreads) {
+            const uint32_t key = S.keys[i];
+            const uint32_t d = (key >> shift) & mask;
+            const uint32_t g = S.run[d] + ((uint32_t)i - S.digoff[d]);
+            keys_out[g] = key;
+            vals_out[g] = S.vals[i];
+        }
+        __syncthreads();
+        for (int d = threadIdx.x; d < bins; d += kSortThreads) S.run[d] += S.cnt[d];
+        __syncthreads();
+    }
+}
+
+cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
+                             uint32_t* vals_b, long long n, const SortPlan& plan, void* temp,
+                             int num_sms, bool vals_iota, bool* in_b, cudaStream_t s) {
+    *in_b = false;
+    if (n <= 0 || plan.passes == 0) return cudaSuccess;
+    const int G = sort_grid(n, num_sms);
+    const long long n_tiles = (n + kSortTile - 1) / kSortTile;
+    const int tpb = (int)((n_tiles + G - 1) / G);
+    uint32_t* hist = (uint32_t*)temp;
+    size_t off = ((size_t)(kMaxBins * (long long)G + 1) * sizeof(uint32_t) + 255) & ~(size_t)255;
+    void* scan_tmp = (char*)temp + off;
+    off += scan_u32_temp_bytes((long long)kMaxBins * G + 1);
+    off = (off + 255) & ~(size_t)255;
+    unsigned long long* total = (unsigned long long*)((char*)temp + off);
+    static bool attr_set = false;
+    const size_t smem = sizeof(DownSmem);
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(radix_downsweep,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    uint32_t *ki = keys_a, *vi = vals_a, *ko = keys_b, *vo = vals_b;
+    int shift = plan.begin_bit;
+    for (int p = 0; p < plan.passes; ++p) {
+        const int bits = plan.bits_per_pass[p];
+        const int bins = 1 << bits;
+        radix_upsweep<<<G, kSortThreads, 0, s>>>(ki, n, shift, bins, tpb, n_tiles, hist);
+        cudaError_t e = exclusive_scan_u32(hist, hist, (long long)bins * G, scan_tmp, total, s);
+        if (e != cudaSuccess) return e;
+        const uint32_t* vread = (p == 0 && vals_iota) ? nullptr : vi;
+        radix_downsweep<<<G, kSortThreads, smem, s>>>(ki, vread, ko, vo, n, shift, bins, tpb,
+                                                      n_tiles, hist);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        shift += bits;
+        uint32_t* tk = ki; ki = ko; ko = tk;
+        uint32_t* tv = vi; vi = vo; vo = tv;
+        *in_b = !*in_b;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace swgs

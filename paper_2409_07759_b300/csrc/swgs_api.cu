@@ -1,0 +1,934 @@
+// swgs_api.cu -- the C ABI of libswgs: context and memory management, and
+// the orchestration of each call on the caller's stream.
+//
+// Render pipeline of one batch of views (every stage one launch over all the
+// batch's views):
+//   1. compaction of the active set of each distinct frame (Sec. 4.2)
+//   2. [sync: active counts]  projection + SH into one record per
+//      (view, active Gaussian)
+//   3. depth sort of the records, scan of their tile counts in depth order
+//   4. [sync: key count]  emission of (tile, record) keys, stable sort by tile,
+//      per-tile ranges
+//   5. persistent blend over all (view, tile) work items (Eq. 3)
+// The backward reuses the saved records, sorted lists, final T and last
+// contributor: reverse blend, then projection backward into the caller's
+// gradient buffers.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "swgs_internal.cuh"
+
+using namespace swgs;
+
+namespace {
+
+struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+struct BatchState {
+    int n_views = 0, n_groups = 0;
+    long long total_active = 0, n_rec = 0, n_keys = 0, n_tiles = 0, n_pix = 0;
+    std::vector<ViewDev> h_views;   // table order (grouped by frame)
+    std::vector<GroupDev> h_groups;
+    std::vector<int> call_index;    // table entry -> index in the call's view list
+    Buf views, groups, ids, rec_a, rec_b, rec_c, rec_tiles, rec_rect, rec_depth, vals, ranges,
+        T, last, grad2d;
+    bool has_grad2d = false;
+};
+
+}  // namespace
+
+struct swgs_saved {
+    swgs_ctx* ctx = nullptr;
+    std::vector<BatchState> batches;
+    int n_batches = 0;
+    int n_views = 0;
+    Buf pairs;  // unsigned long long
+    bool count_pairs = false;
+};
+
+struct swgs_ctx {
+    swgs_config cfg{};
+    swgs_alloc_fn alloc = nullptr;
+    swgs_free_fn free_fn = nullptr;
+    void* user = nullptr;
+    int device = 0;
+    int num_sms = 148;
+    std::string err;
+    cudaStream_t last_stream = nullptr;
+    // transient scratch
+    Buf frames, block_cnt, scan_tmp, counts, order_a, order_b, tcount, koff, keys_a, keys_b,
+        vals_tmp, sort_tmp, counter, totals, l1_tab, reloc_w, reloc_cdf, reloc_dead, reloc_tg,
+        reloc_cnt, reloc_nd;
+    void* pinned = nullptr;
+    size_t pinned_cap = 0;
+    std::vector<swgs_saved*> pool;
+    std::vector<swgs_saved*> all_saved;
+};
+
+namespace {
+
+swgs_status fail(swgs_ctx* c, swgs_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return st;
+}
+
+#define CK(expr)                                                                      \
+    do {                                                                              \
+        cudaError_t _e = (expr);                                                      \
+        if (_e != cudaSuccess)                                                        \
+            return fail(ctx, SWGS_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(_e)); \
+    } while (0)
+
+void* ctx_alloc(swgs_ctx* c, size_t bytes, cudaStream_t s) {
+    if (c->alloc) return c->alloc(c->user, bytes, (void*)s);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) return nullptr;
+    return p;
+}
+
+void ctx_free(swgs_ctx* c, Buf& b, cudaStream_t s) {
+    if (b.p) {
+        if (c->free_fn) c->free_fn(c->user, b.p, b.cap, (void*)s);
+        else cudaFreeAsync(b.p, s);
+    }
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+bool ensure(swgs_ctx* c, Buf& b, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) bytes = 16;
+    if (b.cap >= bytes) return true;
+    ctx_free(c, b, s);
+    size_t nb = bytes + bytes / 4 + 256;
+    b.p = ctx_alloc(c, nb, s);
+    if (!b.p) return false;
+    b.cap = nb;
+    return true;
+}
+
+template <typename T>
+T* P(Buf& b) { return reinterpret_cast<T*>(b.p); }
+
+bool valid_tile(int w, int h) { return (w == 16 && h == 16) || (w == 8 && h == 8) || (w == 32 && h == 8); }
+bool valid_batch(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
+
+swgs_status check_gaussians(swgs_ctx* ctx, const swgs_gaussians* g, bool need_life) {
+    if (!g) return fail(ctx, SWGS_EINVAL, "null Gaussian state");
+    if (g->capacity < 0 || g->capacity > 0x7fffffffLL)
+        return fail(ctx, SWGS_EINVAL, "capacity %lld out of range", (long long)g->capacity);
+    if (g->sh_degree < 0 || g->sh_degree > 3)
+        return fail(ctx, SWGS_EINVAL, "sh_degree %d not in 0..3", g->sh_degree);
+    if (g->capacity > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+        return fail(ctx, SWGS_EINVAL, "null attribute array");
+    if (g->capacity > 0 && ((uintptr_t)g->quats & 15))
+        return fail(ctx, SWGS_EINVAL, "quats must be 16-byte aligned");
+    if (need_life && g->capacity > 0 && (!g->start || !g->expire))
+        return fail(ctx, SWGS_EINVAL, "null lifespan array");
+    return SWGS_OK;
+}
+
+swgs_saved* acquire_saved(swgs_ctx* c) {
+    swgs_saved* s;
+    if (!c->pool.empty()) {
+        s = c->pool.back();
+        c->pool.pop_back();
+    } else {
+        s = new swgs_saved();
+        s->ctx = c;
+        c->all_saved.push_back(s);
+    }
+    s->n_batches = 0;
+    s->n_views = 0;
+    return s;
+}
+
+void free_saved_buffers(swgs_ctx* c, swgs_saved* s, cudaStream_t st) {
+    for (auto& b : s->batches) {
+        Buf* bs[] = {&b.views, &b.groups, &b.ids, &b.rec_a, &b.rec_b, &b.rec_c, &b.rec_tiles,
+                     &b.rec_rect, &b.rec_depth, &b.vals, &b.ranges, &b.T, &b.last, &b.grad2d};
+        for (Buf* x : bs) ctx_free(c, *x, st);
+    }
+    ctx_free(c, s->pairs, st);
+}
+
+Records records_of(BatchState& b) {
+    Records r;
+    r.a = P<float4>(b.rec_a);
+    r.b = P<float4>(b.rec_b);
+    r.c = P<float4>(b.rec_c);
+    r.tiles = P<int32_t>(b.rec_tiles);
+    r.rect = P<short4>(b.rec_rect);
+    r.depth_key = P<uint32_t>(b.rec_depth);
+    return r;
+}
+
+int ceil_log2(long long x) {
+    int b = 0;
+    while ((1LL << b) < x) ++b;
+    return b;
+}
+
+// Render one batch of views (indices idx[] into the call's view list).
+swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view* views,
+                         const std::vector<int>& idx, const float* bg, float* const* out_rgb,
+                         float* const* out_T, BatchState& B, unsigned long long* pairs,
+                         cudaStream_t s) {
+    const int tw = ctx->cfg.tile_w, th = ctx->cfg.tile_h;
+    const long long N = g->capacity;
+    // group the views by frame, in order of first appearance
+    std::vector<int> frames;
+    std::vector<std::vector<int>> members;
+    for (int v : idx) {
+        int f = views[v].frame;
+        size_t k = 0;
+        while (k < frames.size() && frames[k] != f) ++k;
+        if (k == frames.size()) { frames.push_back(f); members.emplace_back(); }
+        members[k].push_back(v);
+    }
+    const int F = (int)frames.size();
+    B.n_views = (int)idx.size();
+    B.n_groups = F;
+    B.has_grad2d = false;
+    // 1. compaction
+    const int nb = N > 0 ? (int)((N + kCompactBlock - 1) / kCompactBlock) : 0;
+    if (!ensure(ctx, ctx->frames, sizeof(int32_t) * F, s) ||
+        !ensure(ctx, ctx->block_cnt, sizeof(uint32_t) * ((size_t)F * nb + 1), s) ||
+        !ensure(ctx, ctx->scan_tmp, scan_u32_temp_bytes((long long)F * nb + 1) + 64, s) ||
+        !ensure(ctx, ctx->counts, sizeof(int32_t) * F, s) || !ensure(ctx, ctx->totals, 64, s) ||
+        !ensure(ctx, B.ids, sizeof(int32_t) * ((size_t)F * (N > 0 ? N : 1)), s))
+        return fail(ctx, SWGS_ENOMEM, "allocation failed (compaction)");
+    CK(cudaMemcpyAsync(ctx->frames.p, frames.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, s));
+    std::vector<int> n_act(F, 0);
+    if (N > 0) {
+        CK(launch_active_flags_count(g->start, g->expire, N, P<int32_t>(ctx->frames), F,
+                                     P<uint32_t>(ctx->block_cnt), nb, s));
+        CK(exclusive_scan_u32(P<uint32_t>(ctx->block_cnt), P<uint32_t>(ctx->block_cnt),
+                              (long long)F * nb, ctx->scan_tmp.p, P<unsigned long long>(ctx->totals), s));
+        CK(launch_active_write(g->start, g->expire, N, P<int32_t>(ctx->frames), F,
+                               P<uint32_t>(ctx->block_cnt), nb, P<int32_t>(B.ids), 0,
+                               P<int32_t>(ctx->counts), s));
+        CK(cudaMemcpyAsync(ctx->pinned, ctx->counts.p, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        memcpy(n_act.data(), ctx->pinned, sizeof(int32_t) * F);
+    }
+    // 2. tables
+    B.h_groups.assign(F, GroupDev{});
+    B.h_views.clear();
+    B.call_index.clear();
+    long long act = 0, rec = 0, tiles = 0, pix = 0;
+    for (int k = 0; k < F; ++k) {
+        GroupDev& G = B.h_groups[k];
+        G.frame = frames[k];
+        G.n_active = n_act[k];
+        G.act_base = (int)act;
+        G.rec_base = (int)rec;
+        G.view_begin = (int)B.h_views.size();
+        G.view_count = (int)members[k].size();
+        for (size_t j = 0; j < members[k].size(); ++j) {
+            const int v = members[k][j];
+            const swgs_view& sv = views[v];
+            ViewDev V{};
+            V.W = sv.width;
+            V.H = sv.height;
+            V.ntx = (sv.width + tw - 1) / tw;
+            V.nty = (sv.height + th - 1) / th;
+            V.tile_base = (int)tiles;
+            V.rec_base = (int)(rec + (long long)j * n_act[k]);
+            V.n_rec = n_act[k];
+            V.group = k;
+            V.pix_base = pix;
+            V.fx = sv.fx; V.fy = sv.fy; V.cx = sv.cx; V.cy = sv.cy;
+            for (int e = 0; e < 9; ++e) V.R[e] = sv.R[e];
+            for (int e = 0; e < 3; ++e) V.t[e] = sv.t[e];
+            for (int e = 0; e < 3; ++e) {
+                double c = 0.0;
+                for (int r = 0; r < 3; ++r) c -= (double)sv.R[3 * r + e] * (double)sv.t[r];
+                V.campos[e] = (float)c;
+            }
+            for (int e = 0; e < 3; ++e) V.bg[e] = bg ? bg[e] : 0.f;
+            V.out_rgb = out_rgb[v];
+            V.out_T = out_T ? out_T[v] : nullptr;
+            V.dL = nullptr;
+            tiles += (long long)V.ntx * V.nty;
+            pix += (long long)sv.width * sv.height;
+            B.h_views.push_back(V);
+            B.call_index.push_back(v);
+        }
+        act += n_act[k];
+        rec += (long long)n_act[k] * members[k].size();
+    }
+    if (rec > 0x7fffffffLL || tiles > 0x7fffffffLL)
+        return fail(ctx, SWGS_EINVAL, "too many records (%lld) or tiles (%lld) in one batch", rec, tiles);
+    B.total_active = act;
+    B.n_rec = rec;
+    B.n_tiles = tiles;
+    B.n_pix = pix;
+    const size_t R = (size_t)rec;
+    if (!ensure(ctx, B.views, sizeof(ViewDev) * B.h_views.size(), s) ||
+        !ensure(ctx, B.groups, sizeof(GroupDev) * F, s) ||
+        !ensure(ctx, B.rec_a, sizeof(float4) * R, s) || !ensure(ctx, B.rec_b, sizeof(float4) * R, s) ||
+        !ensure(ctx, B.rec_c, sizeof(float4) * R, s) ||
+        !ensure(ctx, B.rec_tiles, sizeof(int32_t) * R, s) ||
+        !ensure(ctx, B.rec_rect, sizeof(short4) * R, s) ||
+        !ensure(ctx, B.rec_depth, sizeof(uint32_t) * R, s) ||
+        !ensure(ctx, B.ranges, sizeof(int2) * (size_t)tiles, s) ||
+        !ensure(ctx, B.T, sizeof(float) * (size_t)pix, s) ||
+        !ensure(ctx, B.last, sizeof(int32_t) * (size_t)pix, s) ||
+        !ensure(ctx, ctx->order_a, sizeof(uint32_t) * R, s) ||
+        !ensure(ctx, ctx->order_b, sizeof(uint32_t) * R, s) ||
+        !ensure(ctx, ctx->tcount, sizeof(uint32_t) * R, s) ||
+        !ensure(ctx, ctx->koff, sizeof(uint32_t) * (R + 1), s) ||
+        !ensure(ctx, ctx->totals, 64, s) || !ensure(ctx, ctx->counter, 64, s))
+        return fail(ctx, SWGS_ENOMEM, "allocation failed (records)");
+    CK(cudaMemcpyAsync(B.views.p, B.h_views.data(), sizeof(ViewDev) * B.h_views.size(),
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(B.groups.p, B.h_groups.data(), sizeof(GroupDev) * F, cudaMemcpyHostToDevice, s));
+    Records rc = records_of(B);
+    CK(launch_preprocess(*g, P<ViewDev>(B.views), P<GroupDev>(B.groups), F, P<int32_t>(B.ids), act,
+                         tw, th, ctx->cfg.near_plane, rc, s));
+    // 3. depth order of the records and their key offsets
+    long long n_keys = 0;
+    if (rec > 0) {
+        const SortPlan dp = make_sort_plan(0, 32);
+        if (!ensure(ctx, ctx->sort_tmp, radix_temp_bytes((long long)R, ctx->num_sms), s))
+            return fail(ctx, SWGS_ENOMEM, "allocation failed (sort)");
+        bool in_b = false;
+        CK(radix_sort_pairs(P<uint32_t>(B.rec_depth), P<uint32_t>(ctx->order_a),
+                            P<uint32_t>(ctx->order_b), P<uint32_t>(ctx->tcount), (long long)R, dp,
+                            ctx->sort_tmp.p, ctx->num_sms, true, &in_b, s));
+        // 4 passes: results back in (rec_depth, order_a)
+        const uint32_t* order = in_b ? P<uint32_t>(ctx->tcount) : P<uint32_t>(ctx->order_a);
+        uint32_t* cnt = in_b ? P<uint32_t>(ctx->order_a) : P<uint32_t>(ctx->tcount);
+        CK(launch_gather_tiles(order, rc.tiles, cnt, (long long)R, s));
+        if (!ensure(ctx, ctx->scan_tmp, scan_u32_temp_bytes((long long)R) + 64, s))
+            return fail(ctx, SWGS_ENOMEM, "allocation failed (scan)");
+        CK(exclusive_scan_u32(cnt, P<uint32_t>(ctx->koff), (long long)R, ctx->scan_tmp.p,
+                              P<unsigned long long>(ctx->totals), s));
+        CK(cudaMemcpyAsync(ctx->pinned, ctx->totals.p, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        unsigned long long nk = 0;
+        memcpy(&nk, ctx->pinned, sizeof(nk));
+        if (nk > 0x7fffffffULL)
+            return fail(ctx, SWGS_EINVAL, "%llu tile keys exceed the 2^31 limit of one batch", nk);
+        n_keys = (long long)nk;
+        B.n_keys = n_keys;
+        // 4. keys, tile sort, ranges
+        const int tile_bits = ceil_log2(tiles);
+        const SortPlan tp = make_sort_plan(0, tile_bits);
+        const size_t K = (size_t)n_keys;
+        if (!ensure(ctx, ctx->keys_a, sizeof(uint32_t) * K, s) ||
+            !ensure(ctx, ctx->keys_b, sizeof(uint32_t) * K, s) ||
+            !ensure(ctx, ctx->vals_tmp, sizeof(uint32_t) * K, s) ||
+            !ensure(ctx, B.vals, sizeof(uint32_t) * K, s) ||
+            !ensure(ctx, ctx->sort_tmp, radix_temp_bytes((long long)K, ctx->num_sms), s))
+            return fail(ctx, SWGS_ENOMEM, "allocation failed (keys)");
+        const bool odd = (tp.passes & 1) != 0;
+        uint32_t* ev = odd ? P<uint32_t>(ctx->vals_tmp) : P<uint32_t>(B.vals);
+        uint32_t* ov = odd ? P<uint32_t>(B.vals) : P<uint32_t>(ctx->vals_tmp);
+        CK(launch_emit_keys(order, P<uint32_t>(ctx->koff), (long long)R, rc, P<ViewDev>(B.views),
+                            (int)B.h_views.size(), P<uint32_t>(ctx->keys_a), ev, s));
+        bool kb = false;
+        CK(radix_sort_pairs(P<uint32_t>(ctx->keys_a), ev, P<uint32_t>(ctx->keys_b), ov,
+                            (long long)K, tp, ctx->sort_tmp.p, ctx->num_sms, false, &kb, s));
+        const uint32_t* skeys = kb ? P<uint32_t>(ctx->keys_b) : P<uint32_t>(ctx->keys_a);
+        CK(cudaMemsetAsync(B.ranges.p, 0, sizeof(int2) * (size_t)tiles, s));
+        CK(launch_tile_ranges(skeys, (long long)K, P<int2>(B.ranges), s));
+    } else {
+        B.n_keys = 0;
+        CK(cudaMemsetAsync(B.ranges.p, 0, sizeof(int2) * (size_t)tiles, s));
+        if (!ensure(ctx, B.vals, 16, s)) return fail(ctx, SWGS_ENOMEM, "allocation failed");
+    }
+    // 5. blend
+    BlendArgs ba{};
+    ba.views = P<ViewDev>(B.views);
+    ba.n_views = (int)B.h_views.size();
+    ba.total_tiles = (int)tiles;
+    ba.ranges = P<int2>(B.ranges);
+    ba.vals = P<uint32_t>(B.vals);
+    ba.rec = rc;
+    ba.T = P<float>(B.T);
+    ba.last = P<int32_t>(B.last);
+    ba.work_counter = P<int>(ctx->counter);
+    ba.pairs = pairs;
+    ba.grad2d = nullptr;
+    int bps = ctx->cfg.blocks_per_sm > 0
+                  ? ctx->cfg.blocks_per_sm
+                  : blend_blocks_per_sm(tw, th, ctx->cfg.batch, false);
+    long long grid = (long long)ctx->num_sms * bps;
+    if (grid > tiles) grid = tiles;
+    if (grid < 1) grid = 1;
+    CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), s));
+    CK(launch_blend_fwd(ba, tw, th, ctx->cfg.batch, (int)grid, s));
+    return SWGS_OK;
+}
+
+swgs_status backward_batch(swgs_ctx* ctx, const swgs_gaussians* g, BatchState& B,
+                           const float* const* dL, const swgs_gaussians* grads, cudaStream_t s) {
+    const int tw = ctx->cfg.tile_w, th = ctx->cfg.tile_h;
+    for (size_t i = 0; i < B.h_views.size(); ++i) {
+        B.h_views[i].dL = dL[B.call_index[i]];
+        if (!B.h_views[i].dL) return fail(ctx, SWGS_EINVAL, "null dL_drgb for view %d", B.call_index[i]);
+    }
+    CK(cudaMemcpyAsync(B.views.p, B.h_views.data(), sizeof(ViewDev) * B.h_views.size(),
+                       cudaMemcpyHostToDevice, s));
+    if (!ensure(ctx, B.grad2d, sizeof(float) * 12 * (size_t)(B.n_rec > 0 ? B.n_rec : 1), s) ||
+        !ensure(ctx, ctx->counter, 64, s))
+        return fail(ctx, SWGS_ENOMEM, "allocation failed (grad2d)");
+    CK(cudaMemsetAsync(B.grad2d.p, 0, sizeof(float) * 12 * (size_t)(B.n_rec > 0 ? B.n_rec : 1), s));
+    B.has_grad2d = true;
+    if (B.n_rec == 0) return SWGS_OK;
+    BlendArgs ba{};
+    ba.views = P<ViewDev>(B.views);
+    ba.n_views = (int)B.h_views.size();
+    ba.total_tiles = (int)B.n_tiles;
+    ba.ranges = P<int2>(B.ranges);
+    ba.vals = P<uint32_t>(B.vals);
+    ba.rec = records_of(B);
+    ba.T = P<float>(B.T);
+    ba.last = P<int32_t>(B.last);
+    ba.work_counter = P<int>(ctx->counter);
+    ba.pairs = nullptr;
+    ba.grad2d = P<float>(B.grad2d);
+    int bps = ctx->cfg.blocks_per_sm > 0 ? ctx->cfg.blocks_per_sm
+                                         : blend_blocks_per_sm(tw, th, ctx->cfg.batch, true);
+    long long grid = (long long)ctx->num_sms * bps;
+    if (grid > B.n_tiles) grid = B.n_tiles;
+    if (grid < 1) grid = 1;
+    CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), s));
+    CK(launch_blend_bwd(ba, tw, th, ctx->cfg.batch, (int)grid, s));
+    CK(launch_preprocess_bwd(*g, *grads, P<ViewDev>(B.views), P<GroupDev>(B.groups), B.n_groups,
+                             P<int32_t>(B.ids), B.total_active, P<float>(B.grad2d), s));
+    return SWGS_OK;
+}
+
+// ---- export helpers -------------------------------------------------------
+__global__ void export_record_kernel(int what, const ViewDev* views, int n_views,
+                                     const GroupDev* groups, const int32_t* ids, Records rec,
+                                     const int* call_index_dev, long long n, void* out) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int vi = find_view_by_record(views, n_views, (int)r);
+    const ViewDev& V = views[vi];
+    const GroupDev& G = groups[V.group];
+    const int i = (int)(r - V.rec_base);
+    switch (what) {
+        case SWGS_EXPORT_RECORD_SLOT: ((int32_t*)out)[r] = ids[G.act_base + i]; break;
+        case SWGS_EXPORT_RECORD_VIEW: ((int32_t*)out)[r] = call_index_dev[vi]; break;
+        case SWGS_EXPORT_RECORD_TILES: ((int32_t*)out)[r] = rec.tiles[r]; break;
+        case SWGS_EXPORT_RECORD_DEPTH: ((float*)out)[r] = rec.a[r].w; break;
+        case SWGS_EXPORT_RECORD_RECT: {
+            const short4 q = rec.rect[r];
+            int32_t* o = (int32_t*)out + 4 * r;
+            o[0] = q.x; o[1] = q.y; o[2] = q.z; o[3] = q.w;
+            break;
+        }
+        case SWGS_EXPORT_RECORD_2D: {
+            float4* o = (float4*)out + 3 * r;
+            o[0] = rec.a[r]; o[1] = rec.b[r]; o[2] = rec.c[r];
+            break;
+        }
+    }
+}
+
+__global__ void export_sorted_slot_kernel(const uint32_t* vals, long long n, const ViewDev* views,
+                                          int n_views, const GroupDev* groups, const int32_t* ids,
+                                          int32_t* out) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int r = (int)vals[k];
+    const int vi = find_view_by_record(views, n_views, r);
+    const ViewDev& V = views[vi];
+    out[k] = ids[groups[V.group].act_base + (r - V.rec_base)];
+}
+
+__global__ void export_ranges_kernel(const int2* ranges, long long n, int offset, int2* out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int2 r = ranges[t];
+    out[t] = make_int2(r.x + offset, r.y + offset);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int32_t swgs_abi_version(void) { return SWGS_ABI_VERSION; }
+
+swgs_status swgs_default_config(swgs_config* cfg) {
+    if (!cfg) return SWGS_EINVAL;
+    cfg->tile_w = 16;
+    cfg->tile_h = 16;
+    cfg->batch = 256;
+    cfg->near_plane = 0.2f;
+    cfg->blocks_per_sm = 0;
+    cfg->count_pairs = 0;
+    return SWGS_OK;
+}
+
+swgs_status swgs_create(const swgs_config* cfg, swgs_alloc_fn alloc, swgs_free_fn free_fn,
+                        void* user, swgs_ctx** out) {
+    if (!out) return SWGS_EINVAL;
+    *out = nullptr;
+    swgs_config c{};
+    if (cfg) c = *cfg; else swgs_default_config(&c);
+    if (!valid_tile(c.tile_w, c.tile_h) || !valid_batch(c.batch) || !(c.near_plane > 0.f) ||
+        c.blocks_per_sm < 0)
+        return SWGS_EINVAL;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return SWGS_EINVAL;
+    swgs_ctx* ctx = new swgs_ctx();
+    ctx->cfg = c;
+    ctx->alloc = alloc;
+    ctx->free_fn = free_fn;
+    ctx->user = user;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) !=
+            cudaSuccess ||
+        cudaMallocHost(&ctx->pinned, 4096) != cudaSuccess) {
+        delete ctx;
+        return SWGS_ECUDA;
+    }
+    ctx->pinned_cap = 4096;
+    *out = ctx;
+    return SWGS_OK;
+}
+
+void swgs_destroy(swgs_ctx* ctx) {
+    if (!ctx) return;
+    cudaStream_t s = ctx->last_stream;
+    cudaStreamSynchronize(s);
+    Buf* bs[] = {&ctx->frames, &ctx->block_cnt, &ctx->scan_tmp, &ctx->counts, &ctx->order_a,
+                 &ctx->order_b, &ctx->tcount, &ctx->koff, &ctx->keys_a, &ctx->keys_b,
+                 &ctx->vals_tmp, &ctx->sort_tmp, &ctx->counter, &ctx->totals, &ctx->l1_tab,
+                 &ctx->reloc_w, &ctx->reloc_cdf, &ctx->reloc_dead, &ctx->reloc_tg,
+                 &ctx->reloc_cnt, &ctx->reloc_nd};
+    for (Buf* b : bs) ctx_free(ctx, *b, s);
+    for (swgs_saved* sv : ctx->all_saved) {
+        free_saved_buffers(ctx, sv, s);
+        delete sv;
+    }
+    cudaStreamSynchronize(s);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    delete ctx;
+}
+
+const char* swgs_last_error(const swgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+swgs_status swgs_slice_range(int64_t target_frame, int64_t swin_size, int64_t num_gs,
+                             int64_t* first, int64_t* count) {
+    if (swin_size <= 0 || num_gs < 0 || !first || !count || num_gs % swin_size != 0)
+        return SWGS_EINVAL;
+    int64_t slice = target_frame % swin_size;
+    if (slice < 0) slice += swin_size;
+    *count = num_gs / swin_size;
+    *first = slice * (*count);
+    return SWGS_OK;
+}
+
+swgs_status swgs_active_ids(swgs_ctx* ctx, const int32_t* start, const int32_t* expire, int64_t n,
+                            int32_t frame, int32_t* out_ids, int32_t* out_count, void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    if (n < 0 || n > 0x7fffffffLL || !out_count || (n > 0 && (!start || !expire || !out_ids)))
+        return fail(ctx, SWGS_EINVAL, "bad arguments to swgs_active_ids");
+    if (n == 0) {
+        CK(cudaMemsetAsync(out_count, 0, sizeof(int32_t), s));
+        return SWGS_OK;
+    }
+    const int nb = (int)((n + kCompactBlock - 1) / kCompactBlock);
+    if (!ensure(ctx, ctx->frames, sizeof(int32_t), s) ||
+        !ensure(ctx, ctx->block_cnt, sizeof(uint32_t) * ((size_t)nb + 1), s) ||
+        !ensure(ctx, ctx->scan_tmp, scan_u32_temp_bytes(nb + 1) + 64, s) ||
+        !ensure(ctx, ctx->totals, 64, s))
+        return fail(ctx, SWGS_ENOMEM, "allocation failed");
+    CK(cudaMemcpyAsync(ctx->frames.p, &frame, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    CK(launch_active_flags_count(start, expire, n, P<int32_t>(ctx->frames), 1,
+                                 P<uint32_t>(ctx->block_cnt), nb, s));
+    CK(exclusive_scan_u32(P<uint32_t>(ctx->block_cnt), P<uint32_t>(ctx->block_cnt), nb,
+                          ctx->scan_tmp.p, P<unsigned long long>(ctx->totals), s));
+    CK(launch_active_write(start, expire, n, P<int32_t>(ctx->frames), 1, P<uint32_t>(ctx->block_cnt),
+                           nb, out_ids, 0, out_count, s));
+    return SWGS_OK;
+}
+
+swgs_status swgs_frame_update(swgs_ctx* ctx, const swgs_gaussians* dst, int64_t first,
+                              int64_t count, const swgs_gaussians* src, int32_t src_on_host,
+                              void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    swgs_status st = check_gaussians(ctx, dst, true);
+    if (st != SWGS_OK) return st;
+    if (!src || first < 0 || count < 0 || first + count > dst->capacity || src->capacity < count ||
+        src->sh_degree != dst->sh_degree)
+        return fail(ctx, SWGS_EINVAL, "bad slice [%lld, %lld) for capacity %lld",
+                    (long long)first, (long long)(first + count), (long long)dst->capacity);
+    if (count == 0) return SWGS_OK;
+    const int K = (dst->sh_degree + 1) * (dst->sh_degree + 1);
+    if (src_on_host) {
+        struct { void* d; const void* s; size_t w; } arr[9] = {
+            {dst->means, src->means, 12}, {dst->log_scales, src->log_scales, 12},
+            {dst->quats, src->quats, 16}, {dst->opacity_logits, src->opacity_logits, 4},
+            {dst->sh, src->sh, (size_t)12 * K}, {dst->start, src->start, 4},
+            {dst->expire, src->expire, 4}, {dst->birth, src->birth, 4},
+            {dst->frozen, src->frozen, 1}};
+        for (auto& a : arr) {
+            if (!a.s || !a.d) continue;
+            CK(cudaMemcpyAsync((char*)a.d + a.w * (size_t)first, a.s, a.w * (size_t)count,
+                               cudaMemcpyHostToDevice, s));
+        }
+        return SWGS_OK;
+    }
+    CK(launch_copy_slice(*dst, first, count, *src, s));
+    return SWGS_OK;
+}
+
+swgs_status swgs_render_fwd(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
+                            const swgs_view* views, const float* bg, float* const* out_rgb,
+                            float* const* out_T, int32_t batched, swgs_saved** saved,
+                            void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    ctx->err.clear();
+    swgs_status st = check_gaussians(ctx, g, true);
+    if (st != SWGS_OK) return st;
+    if (n_views <= 0 || !views || !out_rgb)
+        return fail(ctx, SWGS_EINVAL, "need at least one view and its output buffer");
+    if (n_views > kMaxViewsPerBatch)
+        return fail(ctx, SWGS_EINVAL, "at most %d views per call", kMaxViewsPerBatch);
+    for (int v = 0; v < n_views; ++v) {
+        const swgs_view& w = views[v];
+        if (w.width <= 0 || w.height <= 0 || w.width > 16384 || w.height > 16384 ||
+            !(w.fx > 0.f) || !(w.fy > 0.f) || !out_rgb[v])
+            return fail(ctx, SWGS_EINVAL, "view %d: bad size, focal length or output", v);
+    }
+    if (saved) *saved = nullptr;
+    swgs_saved* sv = acquire_saved(ctx);
+    sv->n_views = n_views;
+    sv->count_pairs = ctx->cfg.count_pairs != 0;
+    const int nb = batched ? 1 : n_views;
+    if ((int)sv->batches.size() < nb) sv->batches.resize(nb);
+    sv->n_batches = nb;
+    unsigned long long* pairs = nullptr;
+    if (sv->count_pairs) {
+        if (!ensure(ctx, sv->pairs, sizeof(unsigned long long), s)) {
+            ctx->pool.push_back(sv);
+            return fail(ctx, SWGS_ENOMEM, "allocation failed");
+        }
+        pairs = P<unsigned long long>(sv->pairs);
+        cudaError_t e = cudaMemsetAsync(pairs, 0, sizeof(unsigned long long), s);
+        if (e != cudaSuccess) {
+            ctx->pool.push_back(sv);
+            return fail(ctx, SWGS_ECUDA, "memset: %s", cudaGetErrorString(e));
+        }
+    }
+    for (int b = 0; b < nb; ++b) {
+        std::vector<int> idx;
+        if (batched) for (int v = 0; v < n_views; ++v) idx.push_back(v);
+        else idx.push_back(b);
+        st = render_batch(ctx, g, views, idx, bg, out_rgb, out_T, sv->batches[b], pairs, s);
+        if (st != SWGS_OK) {
+            ctx->pool.push_back(sv);
+            return st;
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        ctx->pool.push_back(sv);
+        return fail(ctx, SWGS_ECUDA, "render: %s", cudaGetErrorString(e));
+    }
+    if (saved) *saved = sv;
+    else ctx->pool.push_back(sv);
+    return SWGS_OK;
+}
+
+swgs_status swgs_render_bwd(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_saved* saved,
+                            const float* const* dL_drgb, const swgs_gaussians* grads,
+                            void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    ctx->err.clear();
+    swgs_status st = check_gaussians(ctx, g, true);
+    if (st != SWGS_OK) return st;
+    if (!saved || saved->ctx != ctx) return fail(ctx, SWGS_ESTATE, "saved state from another context");
+    if (!dL_drgb || !grads || grads->capacity != g->capacity || grads->sh_degree != g->sh_degree ||
+        !grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh)
+        return fail(ctx, SWGS_EINVAL, "gradient buffers do not match the Gaussian state");
+    swgs_saved* sv = const_cast<swgs_saved*>(saved);
+    for (int b = 0; b < sv->n_batches; ++b) {
+        st = backward_batch(ctx, g, sv->batches[b], dL_drgb, grads, s);
+        if (st != SWGS_OK) return st;
+    }
+    return SWGS_OK;
+}
+
+swgs_status swgs_saved_release(swgs_ctx* ctx, swgs_saved* saved) {
+    if (!ctx || !saved || saved->ctx != ctx) return SWGS_EINVAL;
+    ctx->pool.push_back(saved);
+    return SWGS_OK;
+}
+
+swgs_status swgs_saved_query(swgs_ctx* ctx, const swgs_saved* saved, swgs_saved_info* info) {
+    if (!ctx || !saved || !info) return SWGS_EINVAL;
+    swgs_saved_info o{};
+    o.n_views = saved->n_views;
+    o.n_batches = saved->n_batches;
+    for (int b = 0; b < saved->n_batches; ++b) {
+        const BatchState& B = saved->batches[b];
+        o.n_records += B.n_rec;
+        o.n_keys += B.n_keys;
+        o.n_tiles += B.n_tiles;
+        o.n_pixels += B.n_pix;
+    }
+    if (saved->count_pairs && saved->pairs.p) {
+        cudaStream_t s = ctx->last_stream;
+        if (cudaMemcpyAsync(ctx->pinned, saved->pairs.p, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(ctx, SWGS_ECUDA, "reading the pair counter failed");
+        unsigned long long p;
+        memcpy(&p, ctx->pinned, 8);
+        o.pairs = (int64_t)p;
+    } else {
+        o.pairs = -1;
+    }
+    *info = o;
+    return SWGS_OK;
+}
+
+swgs_status swgs_saved_count(swgs_ctx* ctx, const swgs_saved* saved, int32_t what, int64_t* count) {
+    if (!ctx || !saved || !count) return SWGS_EINVAL;
+    long long n = 0;
+    for (int b = 0; b < saved->n_batches; ++b) {
+        const BatchState& B = saved->batches[b];
+        switch (what) {
+            case SWGS_EXPORT_RECORD_SLOT: case SWGS_EXPORT_RECORD_VIEW: case SWGS_EXPORT_RECORD_TILES:
+            case SWGS_EXPORT_RECORD_DEPTH: case SWGS_EXPORT_RECORD_RECT: case SWGS_EXPORT_GRAD2D:
+            case SWGS_EXPORT_RECORD_2D:
+                n += B.n_rec; break;
+            case SWGS_EXPORT_SORTED_SLOT: n += B.n_keys; break;
+            case SWGS_EXPORT_TILE_RANGES: n += B.n_tiles; break;
+            case SWGS_EXPORT_LAST: case SWGS_EXPORT_FINAL_T: n += B.n_pix; break;
+            case 11: n += (long long)B.h_views.size(); break;
+            default: return fail(ctx, SWGS_EINVAL, "unknown export %d", what);
+        }
+    }
+    *count = n;
+    return SWGS_OK;
+}
+
+// what == 11: the view table, int32 x 6 per view in batch order: call index,
+// tile_base, pix_base, rec_base, ntx, nty (bases global over the batches).
+swgs_status swgs_saved_export(swgs_ctx* ctx, const swgs_saved* saved, int32_t what, void* dst,
+                              size_t bytes, void* stream) {
+    if (!ctx || !saved || !dst) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    int64_t n = 0;
+    swgs_status st = swgs_saved_count(ctx, saved, what, &n);
+    if (st != SWGS_OK) return st;
+    size_t el = 4;
+    if (what == SWGS_EXPORT_RECORD_RECT) el = 16;
+    if (what == SWGS_EXPORT_TILE_RANGES) el = 8;
+    if (what == SWGS_EXPORT_GRAD2D || what == SWGS_EXPORT_RECORD_2D) el = 48;
+    if (what == 11) el = 24;
+    if (bytes != el * (size_t)n)
+        return fail(ctx, SWGS_EINVAL, "export %d needs %zu bytes, got %zu", what, el * (size_t)n, bytes);
+    // device staging for kernels that write host memory indirectly
+    cudaPointerAttributes pa{};
+    bool dst_dev = cudaPointerGetAttributes(&pa, dst) == cudaSuccess &&
+                   (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    Buf stage;
+    char* out = (char*)dst;
+    if (!dst_dev) {
+        if (!ensure(ctx, stage, bytes, s)) return fail(ctx, SWGS_ENOMEM, "allocation failed");
+        out = (char*)stage.p;
+    }
+    long long rec_off = 0, key_off = 0, tile_off = 0, pix_off = 0;
+    char* cur = out;
+    std::vector<int32_t> table;
+    for (int b = 0; b < saved->n_batches; ++b) {
+        BatchState& B = const_cast<swgs_saved*>(saved)->batches[b];
+        long long m = 0;
+        switch (what) {
+            case SWGS_EXPORT_RECORD_SLOT: case SWGS_EXPORT_RECORD_VIEW: case SWGS_EXPORT_RECORD_TILES:
+            case SWGS_EXPORT_RECORD_DEPTH: case SWGS_EXPORT_RECORD_RECT: case SWGS_EXPORT_RECORD_2D: {
+                m = B.n_rec;
+                if (m == 0) break;
+                Buf ci;
+                if (!ensure(ctx, ci, sizeof(int) * B.call_index.size(), s))
+                    return fail(ctx, SWGS_ENOMEM, "allocation failed");
+                CK(cudaMemcpyAsync(ci.p, B.call_index.data(), sizeof(int) * B.call_index.size(),
+                                   cudaMemcpyHostToDevice, s));
+                export_record_kernel<<<div_up(m, 256), 256, 0, s>>>(
+                    what, P<ViewDev>(B.views), (int)B.h_views.size(), P<GroupDev>(B.groups),
+                    P<int32_t>(B.ids), records_of(B), P<int>(ci), m, cur);
+                CK(cudaGetLastError());
+                ctx_free(ctx, ci, s);
+                break;
+            }
+            case SWGS_EXPORT_GRAD2D:
+                m = B.n_rec;
+                if (m == 0) break;
+                if (!B.has_grad2d) return fail(ctx, SWGS_ESTATE, "no backward has run on this state");
+                CK(cudaMemcpyAsync(cur, B.grad2d.p, 48 * (size_t)m, cudaMemcpyDeviceToDevice, s));
+                break;
+            case SWGS_EXPORT_SORTED_SLOT:
+                m = B.n_keys;
+                if (m == 0) break;
+                export_sorted_slot_kernel<<<div_up(m, 256), 256, 0, s>>>(
+                    P<uint32_t>(B.vals), m, P<ViewDev>(B.views), (int)B.h_views.size(),
+                    P<GroupDev>(B.groups), P<int32_t>(B.ids), (int32_t*)cur);
+                CK(cudaGetLastError());
+                break;
+            case SWGS_EXPORT_TILE_RANGES:
+                m = B.n_tiles;
+                if (m == 0) break;
+                export_ranges_kernel<<<div_up(m, 256), 256, 0, s>>>(P<int2>(B.ranges), m,
+                                                                   (int)key_off, (int2*)cur);
+                CK(cudaGetLastError());
+                break;
+            case SWGS_EXPORT_LAST:
+                m = B.n_pix;
+                CK(cudaMemcpyAsync(cur, B.last.p, 4 * (size_t)m, cudaMemcpyDeviceToDevice, s));
+                break;
+            case SWGS_EXPORT_FINAL_T:
+                m = B.n_pix;
+                CK(cudaMemcpyAsync(cur, B.T.p, 4 * (size_t)m, cudaMemcpyDeviceToDevice, s));
+                break;
+            case 11:
+                m = (long long)B.h_views.size();
+                for (const ViewDev& V : B.h_views) {
+                    table.push_back(B.call_index[&V - B.h_views.data()]);
+                    table.push_back((int32_t)(V.tile_base + tile_off));
+                    table.push_back((int32_t)(V.pix_base + pix_off));
+                    table.push_back((int32_t)(V.rec_base + rec_off));
+                    table.push_back(V.ntx);
+                    table.push_back(V.nty);
+                }
+                break;
+        }
+        cur += el * (size_t)m;
+        rec_off += B.n_rec;
+        key_off += B.n_keys;
+        tile_off += B.n_tiles;
+        pix_off += B.n_pix;
+    }
+    if (what == 11) {
+        CK(cudaMemcpyAsync(out, table.data(), bytes, cudaMemcpyHostToDevice, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (!dst_dev) {
+        CK(cudaMemcpyAsync(dst, out, bytes, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        ctx_free(ctx, stage, s);
+    }
+    return SWGS_OK;
+}
+
+swgs_status swgs_loss_l1(swgs_ctx* ctx, int32_t n_views, const swgs_view* views,
+                         const float* const* rgb, const float* const* target,
+                         float* const* dL_drgb, float* loss, void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    if (n_views <= 0 || !views || !rgb || !target || !dL_drgb || !loss)
+        return fail(ctx, SWGS_EINVAL, "bad arguments to swgs_loss_l1");
+    // table: pix offsets [V+1] (int64) then 3 pointer arrays [V]
+    std::vector<long long> off(n_views + 1, 0);
+    for (int v = 0; v < n_views; ++v) {
+        if (views[v].width <= 0 || views[v].height <= 0 || !rgb[v] || !target[v] || !dL_drgb[v])
+            return fail(ctx, SWGS_EINVAL, "view %d: bad size or buffer", v);
+        off[v + 1] = off[v] + (long long)views[v].width * views[v].height;
+    }
+    std::vector<unsigned char> tab(8 * (n_views + 1) + 3 * 8 * n_views);
+    memcpy(tab.data(), off.data(), 8 * (n_views + 1));
+    memcpy(tab.data() + 8 * (n_views + 1), rgb, 8 * n_views);
+    memcpy(tab.data() + 8 * (n_views + 1) + 8 * n_views, target, 8 * n_views);
+    memcpy(tab.data() + 8 * (n_views + 1) + 16 * n_views, dL_drgb, 8 * n_views);
+    if (!ensure(ctx, ctx->l1_tab, tab.size(), s)) return fail(ctx, SWGS_ENOMEM, "allocation failed");
+    CK(cudaMemcpyAsync(ctx->l1_tab.p, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
+    char* base = (char*)ctx->l1_tab.p;
+    CK(launch_loss_l1(nullptr, n_views, off[n_views], (const long long*)base,
+                      (const float* const*)(base + 8 * (n_views + 1)),
+                      (const float* const*)(base + 8 * (n_views + 1) + 8 * n_views),
+                      (float* const*)(base + 8 * (n_views + 1) + 16 * n_views), loss, s));
+    return SWGS_OK;
+}
+
+swgs_status swgs_sgld_step(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_gaussians* grads,
+                           const swgs_adam_state* adam, const int32_t* frames, int32_t n_frames,
+                           const swgs_sgld_params* params, uint64_t seed, uint64_t step,
+                           int32_t* targets, int64_t* n_relocated, void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    ctx->err.clear();
+    swgs_status st = check_gaussians(ctx, g, true);
+    if (st != SWGS_OK) return st;
+    if (!params || n_frames < 0 || n_frames > 64 || (n_frames > 0 && !frames))
+        return fail(ctx, SWGS_EINVAL, "bad frames or parameters (at most 64 frames)");
+    if (params->adam && (!grads || !adam))
+        return fail(ctx, SWGS_EINVAL, "an Adam step needs gradients and moments");
+    if (params->max_n < 1) return fail(ctx, SWGS_EINVAL, "max_n must be >= 1");
+    const long long N = g->capacity;
+    if (N == 0) {
+        if (n_relocated) *n_relocated = 0;
+        return SWGS_OK;
+    }
+    CK(launch_sgld(*g, grads, adam, frames, n_frames, *params, seed, step, s));
+    long long nd = 0;
+    if (params->relocate) {
+        if (!ensure(ctx, ctx->reloc_w, 8 * (size_t)N, s) ||
+            !ensure(ctx, ctx->reloc_cdf, 8 * (size_t)N, s) ||
+            !ensure(ctx, ctx->reloc_dead, (size_t)N, s) ||
+            !ensure(ctx, ctx->reloc_cnt, 4 * (size_t)N, s) ||
+            !ensure(ctx, ctx->reloc_nd, 64, s) ||
+            !ensure(ctx, ctx->scan_tmp, scan_u64_temp_bytes(N) + 64, s) ||
+            (!targets && !ensure(ctx, ctx->reloc_tg, 4 * (size_t)N, s)))
+            return fail(ctx, SWGS_ENOMEM, "allocation failed (relocation)");
+        int32_t* tg = targets ? targets : P<int32_t>(ctx->reloc_tg);
+        CK(launch_reloc_weights(*g, frames, n_frames, P<unsigned long long>(ctx->reloc_w),
+                                P<uint8_t>(ctx->reloc_dead), s));
+        CK(inclusive_scan_u64(P<unsigned long long>(ctx->reloc_w), P<unsigned long long>(ctx->reloc_cdf),
+                              N, ctx->scan_tmp.p, s));
+        CK(cudaMemsetAsync(ctx->reloc_cnt.p, 0, 4 * (size_t)N, s));
+        CK(cudaMemsetAsync(ctx->reloc_nd.p, 0, 8, s));
+        CK(launch_reloc_sample(*g, P<uint8_t>(ctx->reloc_dead), P<unsigned long long>(ctx->reloc_cdf),
+                               seed, step, tg, P<int32_t>(ctx->reloc_cnt),
+                               P<unsigned long long>(ctx->reloc_nd), s));
+        CK(launch_reloc_apply(*g, adam, tg, P<int32_t>(ctx->reloc_cnt), params->max_n, s));
+        if (n_relocated) {
+            CK(cudaMemcpyAsync(ctx->pinned, ctx->reloc_nd.p, 8, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            unsigned long long v;
+            memcpy(&v, ctx->pinned, 8);
+            nd = (long long)v;
+        }
+    } else if (targets) {
+        CK(cudaMemsetAsync(targets, 0xff, 4 * (size_t)N, s));
+    }
+    if (n_relocated) *n_relocated = nd;
+    return SWGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,322 @@
+// swgs_internal.cuh -- device-side building blocks shared by the kernels of
+// libswgs (SwinGS frame-t splatting, arXiv 2409.07759).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/swgs.h"
+
+namespace swgs {
+
+constexpr int kMaxViewsPerBatch = 512;
+constexpr int kMaxShCoeffs = 16;  // degree 3
+
+// ---------------------------------------------------------------------------
+// Per-view and per-frame-group descriptors (device copies live in the saved
+// state of a forward call).
+// ---------------------------------------------------------------------------
+struct ViewDev {
+    int W, H, ntx, nty;
+    int tile_base;     // first global tile id of this view inside its batch
+    int rec_base;      // first record of this view
+    int n_rec;         // records of this view (= active Gaussians of its frame)
+    int group;         // frame group index
+    long long pix_base;  // first pixel of this view in the batch's pixel arrays
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float campos[3];
+    float bg[3];
+    float* out_rgb;    // [3,H,W]
+    float* out_T;      // [H,W] or null
+    const float* dL;   // [3,H,W] (backward only)
+};
+
+struct GroupDev {
+    int frame;
+    int n_active;      // active Gaussians of this frame
+    int act_base;      // offset of this group's ids in the ids array
+    int rec_base;      // first record of this group
+    int view_begin;    // first view of this group (views of a group are contiguous)
+    int view_count;
+};
+
+// Records of one (view, Gaussian) pair, structure of float4 arrays.
+struct Records {
+    float4* a;         // u, v, opacity, depth
+    float4* b;         // conic A, B, C (m = A dx^2 + 2B dx dy + C dy^2), 0
+    float4* c;         // r, g, b, 0
+    int32_t* tiles;    // tiles touched (0 if culled)
+    short4* rect;      // tx0, tx1, ty0, ty1
+    uint32_t* depth_key;  // FP32 depth bits, 0xffffffff if no tiles
+};
+
+// ---------------------------------------------------------------------------
+// Thresholds of the per-pixel compositing rule (Eq. 3 plus the readings of
+// the renderer details the paper leaves to 3DGS).
+// ---------------------------------------------------------------------------
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTStop = 1e-4f;
+constexpr float kDilation = 0.3f;
+constexpr float kGuard = 1.3f;
+// m <= 9 written in the log2 domain q = -m/2 * log2(e)
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kQMin = -4.5f * 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// ---------------------------------------------------------------------------
+// Key mode: one correctly rounded FP32 operation per step, never contracted
+// into FMA, so that the discrete quantities (culling, tile rectangle, tile
+// count, depth key) are reproducible bit for bit by an independent CPU
+// implementation of the same operation sequence.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float kadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float ksub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float kmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float kdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float ksqrt(float a) { return __fsqrt_rn(a); }
+
+// exp(x) for the discrete path: Cody-Waite reduction x = k ln2 + r (ln2 split
+// into a 16-bit head and a tail), the degree-7 Taylor polynomial of exp(r) by
+// Horner's rule, and an exact scaling by 2^k.
+__device__ __forceinline__ float km_exp(float x) {
+    x = x < -80.0f ? -80.0f : (x > 80.0f ? 80.0f : x);
+    float t = kmul(x, 0x1.715476p+0f);
+    t = kadd(t, 0.5f);
+    float k = floorf(t);
+    float r = ksub(x, kmul(k, 0x1.62e4p-1f));
+    r = ksub(r, kmul(k, 0x1.7f7d1cp-20f));
+    float p = 0x1.a01a02p-13f;
+    p = kadd(kmul(p, r), 0x1.6c16c2p-10f);
+    p = kadd(kmul(p, r), 0x1.111112p-7f);
+    p = kadd(kmul(p, r), 0x1.555556p-5f);
+    p = kadd(kmul(p, r), 0x1.555556p-3f);
+    p = kadd(kmul(p, r), 0.5f);
+    p = kadd(kmul(p, r), 1.0f);
+    p = kadd(kmul(p, r), 1.0f);
+    int e = (int)k;
+    return kmul(p, __int_as_float((e + 127) << 23));
+}
+
+// Same construction in FP64 (degree 13); used where an integer is derived
+// from a float (the relocation weights).
+__device__ __forceinline__ double kd_exp(double x) {
+    x = x < -700.0 ? -700.0 : (x > 700.0 ? 700.0 : x);
+    double t = __dmul_rn(x, 0x1.71547652b82fep+0);
+    t = __dadd_rn(t, 0.5);
+    double k = floor(t);
+    double r = __dsub_rn(x, __dmul_rn(k, 0x1.62e42feep-1));
+    r = __dsub_rn(r, __dmul_rn(k, 0x1.a39ef35793c76p-33));
+    const double P[14] = {
+        0x1p+0, 0x1p+0, 0x1p-1, 0x1.5555555555555p-3, 0x1.5555555555555p-5,
+        0x1.1111111111111p-7, 0x1.6c16c16c16c17p-10, 0x1.a01a01a01a01ap-13,
+        0x1.a01a01a01a01ap-16, 0x1.71de3a556c734p-19, 0x1.27e4fb7789f5cp-22,
+        0x1.ae64567f544e4p-26, 0x1.1eed8eff8d898p-29, 0x1.6124613a86d09p-33};
+    double p = P[13];
+#pragma unroll
+    for (int i = 12; i >= 0; --i) p = __dadd_rn(__dmul_rn(p, r), P[i]);
+    long long e = (long long)k;
+    return __dmul_rn(p, __longlong_as_double((e + 1023) << 52));
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter-based, so any
+// (seed, step, slot) draw is reproducible without state.
+// ---------------------------------------------------------------------------
+struct U64x4 { unsigned long long v[4]; };
+
+__device__ __forceinline__ U64x4 philox4x64_10(unsigned long long c0, unsigned long long c1,
+                                               unsigned long long c2, unsigned long long c3,
+                                               unsigned long long k0, unsigned long long k1) {
+    const unsigned long long M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const unsigned long long W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        unsigned long long hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        unsigned long long hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        unsigned long long n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    U64x4 r;
+    r.v[0] = c0; r.v[1] = c1; r.v[2] = c2; r.v[3] = c3;
+    return r;
+}
+
+constexpr unsigned long long kTagNoise = 0x53474c44ULL;  // "SGLD"
+constexpr unsigned long long kTagReloc = 0x52454c4fULL;  // "RELO"
+
+// Dead: sigmoid(logit) <= 0.005, decided on the FP32 logit against the largest
+// float not above ln(0.005 / 0.995).
+constexpr float kLogitDead = -0x1.52c582p+2f;
+
+// ---------------------------------------------------------------------------
+// Compositing of one (pixel, Gaussian) pair. The forward and the backward
+// blend call this same function; every operation is an explicit intrinsic so
+// both recompute identical alphas (the backward relies on it to retrace the
+// forward's decisions).
+//   staged: (u, v, qa, qb) and (qc, lo): qa = -A/2 log2e, qb = -B log2e,
+//   qc = -C/2 log2e, lo = log2(opacity).
+// Returns q (= -m/2 log2e); *au = unclamped o*G, *a = min(0.99, *au).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float pair_q(float px, float py, float4 g0, float qc, float* dx,
+                                        float* dy) {
+    float ddx = __fsub_rn(px, g0.x);
+    float ddy = __fsub_rn(py, g0.y);
+    float t1 = __fmaf_rn(g0.w, ddy, __fmul_rn(g0.z, ddx));
+    float t2 = __fmul_rn(__fmul_rn(qc, ddy), ddy);
+    *dx = ddx;
+    *dy = ddy;
+    return __fmaf_rn(t1, ddx, t2);
+}
+
+__device__ __forceinline__ float pair_alpha(float q, float lo, float* au) {
+    float u = ex2_approx(__fadd_rn(q, lo));
+    *au = u;
+    return fminf(kAlphaMax, u);
+}
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_view_by_tile(const ViewDev* views, int n_views, int tile) {
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (views[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_view_by_record(const ViewDev* views, int n_views, int rec) {
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (views[mid].rec_base <= rec) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b),
+                 "f"(c), "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void red_add(float* addr, float a) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(addr), "f"(a) : "memory");
+}
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (one translation unit each).
+// ---------------------------------------------------------------------------
+struct DeviceLimits {
+    int num_sms;
+};
+
+// k_compact.cu
+cudaError_t launch_active_flags_count(const int32_t* start, const int32_t* expire, long long n,
+                                      const int32_t* frames, int n_frames, uint32_t* block_counts,
+                                      int n_blocks, cudaStream_t s);
+cudaError_t launch_active_write(const int32_t* start, const int32_t* expire, long long n,
+                                const int32_t* frames, int n_frames, const uint32_t* block_offsets,
+                                int n_blocks, int32_t* out_ids, long long ids_stride,
+                                int32_t* out_counts, cudaStream_t s);
+constexpr int kCompactBlock = 1024;
+
+// k_scan.cu
+size_t scan_u32_temp_bytes(long long n);
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, long long n, void* temp,
+                               unsigned long long* total, cudaStream_t s);
+size_t scan_u64_temp_bytes(long long n);
+cudaError_t inclusive_scan_u64(const unsigned long long* in, unsigned long long* out, long long n,
+                               void* temp, cudaStream_t s);
+
+// k_preprocess.cu
+cudaError_t launch_preprocess(const swgs_gaussians& g, const ViewDev* views, const GroupDev* groups,
+                              int n_groups, const int32_t* ids, long long total_active,
+                              int tile_w, int tile_h, float near_plane, Records rec,
+                              cudaStream_t s);
+cudaError_t launch_preprocess_bwd(const swgs_gaussians& g, const swgs_gaussians& grads,
+                                  const ViewDev* views, const GroupDev* groups, int n_groups,
+                                  const int32_t* ids, long long total_active,
+                                  const float* grad2d, cudaStream_t s);
+
+// k_sort.cu
+struct SortPlan {
+    int passes;
+    int bits_per_pass[8];
+    int begin_bit;
+};
+SortPlan make_sort_plan(int begin_bit, int end_bit);
+size_t radix_temp_bytes(long long n, int num_sms);
+// Stable LSD sort of (key, value) pairs. Results end in keys_b/vals_b after an
+// odd number of passes, else in keys_a/vals_a; *in_b receives which.
+// vals_iota: the values start as 0..n-1 (vals_a is not read).
+cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
+                             uint32_t* vals_b, long long n, const SortPlan& plan, void* temp,
+                             int num_sms, bool vals_iota, bool* in_b, cudaStream_t s);
+
+// k_keys.cu
+cudaError_t launch_gather_tiles(const uint32_t* order, const int32_t* tiles, uint32_t* out,
+                                long long n, cudaStream_t s);
+cudaError_t launch_emit_keys(const uint32_t* order, const uint32_t* offsets, long long n_rec,
+                             const Records rec, const ViewDev* views, int n_views,
+                             uint32_t* keys, uint32_t* vals, cudaStream_t s);
+cudaError_t launch_tile_ranges(const uint32_t* keys, long long n_keys, int2* ranges,
+                               cudaStream_t s);
+
+// k_blend.cu
+struct BlendArgs {
+    const ViewDev* views;
+    int n_views;
+    int total_tiles;
+    const int2* ranges;
+    const uint32_t* vals;
+    Records rec;
+    float* T;          // per pixel (batch-local)
+    int32_t* last;     // per pixel
+    int* work_counter;
+    unsigned long long* pairs;  // optional
+    float* grad2d;     // backward: 12 floats per record
+};
+cudaError_t launch_blend_fwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int grid,
+                             cudaStream_t s);
+cudaError_t launch_blend_bwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int grid,
+                             cudaStream_t s);
+int blend_blocks_per_sm(int tile_w, int tile_h, int batch, bool backward);
+
+// k_misc.cu
+cudaError_t launch_loss_l1(const ViewDev* views, int n_views, long long total_pix,
+                           const long long* pix_offsets, const float* const* rgb,
+                           const float* const* target, float* const* dl, float* loss,
+                           cudaStream_t s);
+cudaError_t launch_copy_slice(const swgs_gaussians& dst, long long first, long long count,
+                              const swgs_gaussians& src, cudaStream_t s);
+
+// k_optim.cu
+cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
+                        const swgs_adam_state* adam, const int32_t* frames, int n_frames,
+                        const swgs_sgld_params& p, unsigned long long seed,
+                        unsigned long long step, cudaStream_t s);
+cudaError_t launch_reloc_weights(const swgs_gaussians& g, const int32_t* frames, int n_frames,
+                                 unsigned long long* weights, uint8_t* dead, cudaStream_t s);
+cudaError_t launch_reloc_sample(const swgs_gaussians& g, const uint8_t* dead,
+                                const unsigned long long* cdf, unsigned long long seed,
+                                unsigned long long step, int32_t* targets, int32_t* counts,
+                                unsigned long long* n_dead, cudaStream_t s);
+cudaError_t launch_reloc_apply(const swgs_gaussians& g, const swgs_adam_state* adam,
+                               const int32_t* targets, const int32_t* counts, int max_n,
+                               cudaStream_t s);
+
+}  // namespace swgs

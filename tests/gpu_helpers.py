@@ -1,0 +1,79 @@
+"""Shared helpers of the GPU parity tests (comparison of the CUDA path, called
+through the C ABI, with the FP64 oracle on the same seeded inputs)."""
+import numpy as np
+
+# Tolerances (BASELINE): pixels 1e-4 max abs, gradients 1e-3 relative.
+PIX_TOL = 1e-4
+GRAD_REL_TOL = 1e-3
+# Near-discontinuity bands (relative) within which FP32 and FP64 may decide a
+# threshold differently; pixels touched by such a pair are reported and left
+# out of the 1e-4 check (they are never silently dropped: the count is asserted
+# to stay small).
+BANDS = dict(m=2e-4, alpha=2e-4, t_stop=2e-3, clamp=2e-4, guard=1e-4, colour=1e-5)
+
+
+def view_table(saved):
+    from paper_2409_07759_b300 import _abi
+    return saved.export(_abi.EXPORT_VIEW_TABLE)
+
+
+def gpu_lists(saved, view_index):
+    """Per-tile slot lists of one view from the GPU's saved state, as
+    (tile_off, tile_slot) in the oracle's CSR layout."""
+    from paper_2409_07759_b300 import _abi
+    tab = view_table(saved)
+    row = tab[tab[:, 0] == view_index][0]
+    _, tile_base, _, _, ntx, nty = row
+    ranges = saved.export(_abi.EXPORT_TILE_RANGES)
+    slots = saved.export(_abi.EXPORT_SORTED_SLOT)
+    nt = ntx * nty
+    off = [0]
+    out = []
+    for t in range(nt):
+        b, e = ranges[tile_base + t]
+        out.append(slots[b:e])
+        off.append(off[-1] + (e - b))
+    return np.array(off, np.int64), (np.concatenate(out) if out else np.zeros(0, np.int32))
+
+
+def gpu_pixels(saved, view_index, what):
+    from paper_2409_07759_b300 import _abi
+    tab = view_table(saved)
+    row = tab[tab[:, 0] == view_index][0]
+    v = saved.views[view_index]
+    arr = saved.export(what)
+    pb = row[2]
+    return arr[pb:pb + v.width * v.height].reshape(v.height, v.width)
+
+
+def compare_image(gpu_rgb, gpu_T, gpu_last, ref, max_flag_frac=0.02):
+    """Assert pixel parity on unflagged pixels; return the error report."""
+    flag = (ref["flags"] & 1) != 0
+    ok = ~flag
+    err_rgb = np.abs(gpu_rgb.astype(np.float64) - ref["rgb"])
+    err_T = np.abs(gpu_T.astype(np.float64) - ref["T"])
+    rep = dict(max_abs_rgb=float(err_rgb[:, ok].max(initial=0.0)),
+               max_abs_T=float(err_T[ok].max(initial=0.0)),
+               flagged=int(flag.sum()), pixels=int(flag.size),
+               max_abs_rgb_flagged=float(err_rgb[:, flag].max(initial=0.0)),
+               last_mismatch=int(((gpu_last != ref["last_pos"]) & ok).sum()))
+    assert rep["flagged"] <= max_flag_frac * flag.size, rep
+    assert rep["max_abs_rgb"] <= PIX_TOL, rep
+    assert rep["max_abs_T"] <= PIX_TOL, rep
+    assert rep["last_mismatch"] == 0, rep
+    return rep
+
+
+def compare_grads(gpu: dict, ref: dict, tol=GRAD_REL_TOL):
+    """Per attribute: ||d||_2 / ||g||_2 <= tol and max |d| <= tol * max |g|."""
+    rep = {}
+    for k, g in ref.items():
+        a = gpu[k].astype(np.float64)
+        d = a - g
+        nrm = np.linalg.norm(g)
+        rel = float(np.linalg.norm(d) / nrm) if nrm > 0 else float(np.linalg.norm(d))
+        elem = float(np.abs(d).max() / max(np.abs(g).max(), 1e-30))
+        rep[k] = (rel, elem)
+    bad = {k: v for k, v in rep.items() if v[0] > tol or v[1] > tol}
+    assert not bad, rep
+    return rep

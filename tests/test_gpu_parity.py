@@ -1,0 +1,267 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on
+the same seeded inputs. Discrete stages are compared bit for bit, pixels at
+1e-4 max abs, gradients at 1e-3 relative."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2409_07759_b300 import synth
+
+from gpu_helpers import BANDS, compare_grads, compare_image, gpu_lists, gpu_pixels
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def R():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2409_07759_b300 import api
+    r = api.Renderer()
+    yield r
+    r.close()
+
+
+def _state(scene):
+    from paper_2409_07759_b300 import api
+    return api.GaussianState.from_scene(scene)
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+# ------------------------------------------------------------ compaction --
+
+@pytest.mark.parametrize("frame", [0, 57, 150, 299, 400])
+def test_active_ids_bit_exact(R, oracle_mod, frame):
+    """Sec. 4.2 filter: the ascending active ids equal the oracle's."""
+    sc, _, _ = synth.config1()
+    st = _state(sc)
+    ids = _np(R.active_ids(st, frame))
+    ref = oracle_mod.active_ids(sc.start, sc.expire, frame)
+    np.testing.assert_array_equal(ids, ref)
+
+
+def test_active_ids_ragged_and_empty(R, oracle_mod):
+    rng = np.random.default_rng(5)
+    for n in (1, 1023, 1024, 1025, 4097):
+        sc, _ = synth.tiny_scene(1, n=n, sh_degree=0)
+        sc.start = rng.integers(0, 4, n).astype(np.int32)
+        sc.expire = (sc.start + rng.integers(0, 3, n)).astype(np.int32)  # some empty spans
+        st = _state(sc)
+        for f in (0, 2, 9):
+            np.testing.assert_array_equal(_np(R.active_ids(st, f)),
+                                          oracle_mod.active_ids(sc.start, sc.expire, f))
+
+
+# ------------------------------------------------------- records and keys --
+
+def _check_records_and_lists(R, oracle_mod, sc, views, tile=(16, 16)):
+    from paper_2409_07759_b300 import _abi
+    st = _state(sc)
+    _, saved = R.render(st, views, keep_saved=True)
+    rslot = saved.export(_abi.EXPORT_RECORD_SLOT)
+    rview = saved.export(_abi.EXPORT_RECORD_VIEW)
+    rtiles = saved.export(_abi.EXPORT_RECORD_TILES)
+    rrect = saved.export(_abi.EXPORT_RECORD_RECT)
+    rdepth = saved.export(_abi.EXPORT_RECORD_DEPTH)
+    total_keys = 0
+    for vi, v in enumerate(views):
+        ids, km, nk, off, slots = oracle_mod.view_lists(sc, v, tile[0], tile[1])
+        m = rview == vi
+        np.testing.assert_array_equal(rslot[m], ids)
+        want_tiles = np.where(km["culled"] == 1, 0, km["tiles"])
+        np.testing.assert_array_equal(rtiles[m], want_tiles)
+        live = (km["culled"] == 0)
+        np.testing.assert_array_equal(rrect[m][live & (want_tiles > 0)],
+                                      np.stack([km["tx0"], km["tx1"], km["ty0"], km["ty1"]], 1)
+                                      [live & (want_tiles > 0)])
+        np.testing.assert_array_equal(rdepth[m][live].view(np.uint32),
+                                      km["z"][live].view(np.uint32))
+        goff, gslots = gpu_lists(saved, vi)
+        np.testing.assert_array_equal(goff, off)
+        np.testing.assert_array_equal(gslots, slots)
+        total_keys += nk
+    assert saved.info().n_keys == total_keys
+    saved.release()
+    return total_keys
+
+
+def test_config0_records_keys_order_bit_exact(R, oracle_mod):
+    """Active ids, tile counts, tile rectangles, depth keys and the per-tile
+    sorted order of config 0 equal the oracle bit for bit."""
+    sc, views = synth.config0()
+    assert _check_records_and_lists(R, oracle_mod, sc, views) > 0
+
+
+def test_config1_records_keys_order_bit_exact(R, oracle_mod):
+    """Same at the full config-1 size (100k Gaussians, 1352x1014, SH3)."""
+    sc, views, _ = synth.config1()
+    assert _check_records_and_lists(R, oracle_mod, sc, views) > 100_000
+
+
+def test_depth_ties_follow_slot_order(R, oracle_mod):
+    sc, view = synth.tiny_scene(9, n=300, sh_degree=0, width=64, height=48, depth=3.0,
+                                log_scale_mean=-2.0, spread=1.0)
+    view.fx = view.fy = 60.0
+    sc.means[100:140] = sc.means[100]  # 40 Gaussians at one depth
+    _check_records_and_lists(R, oracle_mod, sc, [view])
+
+
+# ---------------------------------------------------------------- pixels --
+
+def _render_and_compare(R, oracle_mod, sc, views, bg=(0.0, 0.0, 0.0), tile=(16, 16)):
+    from paper_2409_07759_b300 import _abi
+    st = _state(sc)
+    imgs, saved = R.render(st, views, bg=bg, keep_saved=True)
+    reps = []
+    for vi, v in enumerate(views):
+        ref = oracle_mod.render(sc, v, bg=bg, tile_w=tile[0], tile_h=tile[1], mode="tiled",
+                                bands=BANDS)
+        T = gpu_pixels(saved, vi, _abi.EXPORT_FINAL_T)
+        last = gpu_pixels(saved, vi, _abi.EXPORT_LAST)
+        reps.append(compare_image(_np(imgs[vi]), T, last, ref))
+    saved.release()
+    return reps
+
+
+def test_config0_pixels(R, oracle_mod):
+    """Config 0 image within 1e-4 of the FP64 oracle (flagged pixels reported)."""
+    sc, views = synth.config0()
+    rep = _render_and_compare(R, oracle_mod, sc, views)
+    print(rep)
+
+
+def test_config0_background_and_ragged(R, oracle_mod):
+    """A non-black background and an image size that is not a multiple of the
+    tile (ragged last row and column of tiles)."""
+    sc, views = synth.config0()
+    v = views[0]
+    v2 = synth.View(131, 97, v.fx, v.fy, 65.5, 48.5, v.R, v.t, 0)
+    _render_and_compare(R, oracle_mod, sc, [v2], bg=(0.2, 0.5, 0.9))
+
+
+@pytest.mark.parametrize("tile,batch", [((8, 8), 32), ((8, 8), 256), ((16, 16), 64),
+                                        ((32, 8), 128), ((32, 8), 256)])
+def test_tile_shapes_and_batches(oracle_mod, tile, batch):
+    """Every tile shape and staging batch size gives the oracle's image."""
+    from paper_2409_07759_b300 import api
+    r = api.Renderer(tile=tile, batch=batch)
+    sc, views = synth.config0()
+    _check_records_and_lists(r, oracle_mod, sc, views, tile=tile)
+    _render_and_compare(r, oracle_mod, sc, views, tile=tile)
+    r.close()
+
+
+def test_config1_pixels_full(R, oracle_mod):
+    """Full config-1 frame (1352x1014, SH3, 100k Gaussians at frame 150)."""
+    sc, views, _ = synth.config1()
+    rep = _render_and_compare(R, oracle_mod, sc, views)
+    print(rep)
+
+
+def test_empty_and_offscreen(R, oracle_mod):
+    """No active Gaussian, and every Gaussian behind the camera: background."""
+    sc, views = synth.config0()
+    v = views[0]
+    empty = synth.View(v.width, v.height, v.fx, v.fy, v.cx, v.cy, v.R, v.t, 5)
+    st = _state(sc)
+    imgs, _ = R.render(st, [empty], bg=(0.3, 0.1, 0.7))
+    want = np.broadcast_to(np.array([0.3, 0.1, 0.7], np.float32)[:, None, None], (3, 96, 128))
+    np.testing.assert_array_equal(_np(imgs[0]), want)
+    behind = synth.View(v.width, v.height, v.fx, v.fy, v.cx, v.cy, v.R,
+                        np.array([0, 0, -10], np.float32), 0)
+    imgs, _ = R.render(st, [behind])
+    assert np.abs(_np(imgs[0])).max() == 0.0
+
+
+def test_batched_equals_plain(R, oracle_mod):
+    """The batched launch and the plain per-view path give identical images."""
+    sc, views, _ = synth.config2(width=160, height=120, n=20000, n_frames=3, per_frame=2)
+    st = _state(sc)
+    a, _ = R.render(st, views, batched=True)
+    b, _ = R.render(st, views, batched=False)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(_np(x), _np(y))
+
+
+def test_multiview_multiframe_pixels(R, oracle_mod):
+    """Views at different frames in one batched call (several frame groups,
+    interleaved in the call order)."""
+    sc, views, _ = synth.config2(width=200, height=150, n=30000, n_frames=3, per_frame=2)
+    views = [views[0], views[2], views[1], views[4], views[3], views[5]]
+    _render_and_compare(R, oracle_mod, sc, views)
+
+
+# -------------------------------------------------------------- backward --
+
+def _grads_vs_oracle(R, oracle_mod, sc, views, dLs, bg=(0.0, 0.0, 0.0), gpu_dLs=None):
+    """GPU backward with gpu_dLs (device tensors, default: dLs) against the
+    oracle's backward with dLs (host arrays that never come from the GPU)."""
+    from paper_2409_07759_b300 import api
+    st = _state(sc)
+    imgs, saved = R.render(st, views, bg=bg, keep_saved=True)
+    grads = st.zero_grads()
+    if gpu_dLs is None:
+        gpu_dLs = [torch.from_numpy(np.asarray(d, np.float32)).cuda() for d in dLs]
+    R.backward(st, saved, gpu_dLs, grads)
+    saved.release()
+    ref = oracle_mod.zero_grads(sc)
+    for v, d in zip(views, dLs):
+        oracle_mod.render_bwd(sc, v, np.asarray(d, np.float32).astype(np.float64), bg=bg,
+                              grads=ref, bands=BANDS)
+    gpu = {k: _np(getattr(grads, k)) for k in api.PARAM_NAMES}
+    return compare_grads(gpu, ref)
+
+
+def test_backward_small_scene(R, oracle_mod):
+    """Gradients of every attribute (SH3) against the FP64 adjoint."""
+    sc, view = synth.tiny_scene(3, n=200, sh_degree=3, width=96, height=72, depth=3.0,
+                                log_scale_mean=-2.2, spread=0.9)
+    view.fx = view.fy = 90.0
+    d = np.random.default_rng(0).normal(size=(3, 72, 96))
+    print(_grads_vs_oracle(R, oracle_mod, sc, [view], [d], bg=(0.1, 0.2, 0.3)))
+
+
+def test_backward_config1_l1(R, oracle_mod):
+    """Config 1 full size: L1 loss against the seeded target, gradients of all
+    attributes of the 100k Gaussians."""
+    sc, views, targets = synth.config1()
+    st = _state(sc)
+    imgs, _ = R.render(st, views)
+    loss, dls = R.loss_l1(views, imgs, [torch.from_numpy(t).cuda() for t in targets])
+    ref_img = oracle_mod.render(sc, views[0], mode="tiled")["rgb"]
+    ref_loss, ref_dl = oracle_mod.l1_loss_grad([ref_img], targets)
+    assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-5)
+    # each side differentiates its own L1: the signs differ only where the two
+    # images straddle the target within rounding
+    flips = int((np.sign(_np(dls[0])) != np.sign(ref_dl[0])).sum())
+    assert flips <= 1e-4 * ref_dl[0].size, flips
+    print(flips, _grads_vs_oracle(R, oracle_mod, sc, views, ref_dl, gpu_dLs=dls))
+
+
+def test_backward_multiview_frozen(R, oracle_mod):
+    """Several views and frames summed into one gradient; frozen slots get none."""
+    sc, views, _ = synth.config2(width=160, height=120, n=20000, n_frames=3, per_frame=2)
+    rng = np.random.default_rng(1)
+    dls = [rng.normal(size=(3, v.height, v.width)) for v in views]
+    print(_grads_vs_oracle(R, oracle_mod, sc, views, dls))
+
+
+def test_autograd_function(R, oracle_mod):
+    """torch.autograd through the library's forward and backward."""
+    from paper_2409_07759_b300 import api
+    sc, view = synth.tiny_scene(4, n=150, sh_degree=1, width=64, height=48, depth=3.0,
+                                log_scale_mean=-2.0, spread=0.8)
+    view.fx = view.fy = 60.0
+    st = _state(sc)
+    params = [p.clone().requires_grad_(True) for p in st.params()]
+    (img,) = api.render(R, st, [view], params=params)
+    w = torch.randn_like(img)
+    (img * w).sum().backward()
+    ref = oracle_mod.zero_grads(sc)
+    oracle_mod.render_bwd(sc, view, _np(w).astype(np.float64), grads=ref, bands=BANDS)
+    compare_grads({k: _np(p.grad) for k, p in zip(api.PARAM_NAMES, params)}, ref)
