@@ -60,13 +60,15 @@ class OrKm(C.Structure):
                 ("b", C.c_float), ("c", C.c_float), ("det", C.c_float),
                 ("lambda1", C.c_float), ("radius", C.c_float), ("culled", C.c_int32),
                 ("tx0", C.c_int32), ("tx1", C.c_int32), ("ty0", C.c_int32),
-                ("ty1", C.c_int32), ("tiles", C.c_int32)]
+                ("ty1", C.c_int32), ("tiles", C.c_int32), ("A", C.c_float), ("B", C.c_float),
+                ("C", C.c_float)]
 
 
 KM_DTYPE = np.dtype([("u", "<f4"), ("v", "<f4"), ("z", "<f4"), ("a", "<f4"), ("b", "<f4"),
                      ("c", "<f4"), ("det", "<f4"), ("lambda1", "<f4"), ("radius", "<f4"),
                      ("culled", "<i4"), ("tx0", "<i4"), ("tx1", "<i4"), ("ty0", "<i4"),
-                     ("ty1", "<i4"), ("tiles", "<i4")])
+                     ("ty1", "<i4"), ("tiles", "<i4"), ("A", "<f4"), ("B", "<f4"),
+                     ("C", "<f4")])
 assert KM_DTYPE.itemsize == C.sizeof(OrKm)
 
 
@@ -151,6 +153,9 @@ def lib():
         _lib.or_sgld_step.argtypes = [P(OrState), P(OrFGrads), P(OrAdam), C.c_void_p, C.c_int32,
                                       P(OrSgldParams), C.c_uint64, C.c_uint64, C.c_void_p]
         _lib.or_num_threads.restype = C.c_int
+        _lib.or_record_tiles.restype = C.c_int32
+        _lib.or_record_tiles.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                         C.c_void_p]
     return _lib
 
 
@@ -226,6 +231,15 @@ def keymode(scene, view, slots, tile_w=16, tile_h=16, near=0.2) -> np.ndarray:
         L.or_keymode(C.byref(ref.s), C.byref(vw), int(s), tile_w, tile_h, near, C.byref(rec))
         out[i] = tuple(getattr(rec, f[0]) for f in OrKm._fields_)
     return out
+
+
+def record_tiles(km_row, view, tile_w=16, tile_h=16) -> np.ndarray:
+    """Tile ids (row-major in the view) that one key-mode record covers."""
+    rec = np.array([km_row], KM_DTYPE)
+    ntx = (view.width + tile_w - 1) // tile_w
+    out = np.zeros(max(1, int(km_row["tiles"])), np.int32)
+    n = lib().or_record_tiles(_p(rec), ntx, tile_w, tile_h, _p(out))
+    return out[:n].copy()
 
 
 def view_lists(scene, view, tile_w=16, tile_h=16, near=0.2, with_lists=True):

@@ -77,9 +77,54 @@ typedef struct {
     float a, b, c;             /* dilated 2D covariance */
     float det, lambda1, radius;
     int32_t culled;            /* 1: behind near plane or det <= 0 */
-    int32_t tx0, tx1, ty0, ty1;/* inclusive tile rectangle (empty if tx1<tx0) */
-    int32_t tiles;             /* tiles touched */
+    int32_t tx0, tx1, ty0, ty1;/* inclusive bounding tile rectangle (empty if tx1<tx0) */
+    int32_t tiles;             /* tiles of the rectangle the 3-sigma ellipse covers */
+    float A, B, C;             /* conic: m = A dx^2 + 2 B dx dy + C dy^2 */
 } or_km;
+
+/* A tile is kept when the minimum of the Mahalanobis form over the rectangle
+ * spanned by its pixel centres is at most this (9 = the 3-sigma support, plus
+ * 0.1% so that FP32 rounding can never drop a tile holding a pixel with
+ * m <= 9). */
+#define OR_TILE_MAHAL 9.009f
+
+/* min over t in [lo, hi] of P s^2 + 2 Q s t + R t^2 for fixed s (key mode). */
+static float km_edge_min(float P, float Q, float R, float s, float lo, float hi)
+{
+    float t = Q * s;
+    t = t / R;
+    t = -t;
+    t = t < lo ? lo : (t > hi ? hi : t);
+    float p1 = P * s;
+    p1 = p1 * s;
+    float p2 = Q * s;
+    p2 = p2 * t;
+    p2 = 2.0f * p2;
+    float p3 = R * t;
+    p3 = p3 * t;
+    float e = p1 + p2;
+    return e + p3;
+}
+
+/* Does the 3-sigma ellipse of (u, v, A, B, C) reach tile (tx, ty)? */
+static int km_tile_covered(float u, float v, float A, float B, float C, int tx, int ty,
+                           int tile_w, int tile_h)
+{
+    float x0 = (float)(tx * tile_w) + 0.5f;
+    float x1 = (float)(tx * tile_w) + ((float)tile_w - 0.5f);
+    float y0 = (float)(ty * tile_h) + 0.5f;
+    float y1 = (float)(ty * tile_h) + ((float)tile_h - 0.5f);
+    float xa = x0 - u, xb = x1 - u, ya = y0 - v, yb = y1 - v;
+    if (xa <= 0.0f && xb >= 0.0f && ya <= 0.0f && yb >= 0.0f) return 1;
+    float best = km_edge_min(A, B, C, xa, ya, yb);
+    float e = km_edge_min(A, B, C, xb, ya, yb);
+    if (e < best) best = e;
+    e = km_edge_min(C, B, A, ya, xa, xb);
+    if (e < best) best = e;
+    e = km_edge_min(C, B, A, yb, xa, xb);
+    if (e < best) best = e;
+    return best <= OR_TILE_MAHAL;
+}
 
 /* Blend thresholds (readings of the unspecified renderer details). */
 #define OR_ALPHA_MIN   (1.0 / 255.0)
@@ -281,9 +326,30 @@ void or_keymode(const or_scene *sc, const or_view *vw, int64_t slot,
     int y0 = fylo < 0.0f ? 0 : (fylo > (float)nty ? nty : (int)fylo);
     int y1 = fyhi > (float)(nty - 1) ? nty - 1 : (fyhi < -1.0f ? -1 : (int)fyhi);
     o->tx0 = x0; o->tx1 = x1; o->ty0 = y0; o->ty1 = y1;
-    int cx = x1 >= x0 ? x1 - x0 + 1 : 0;
-    int cy = y1 >= y0 ? y1 - y0 + 1 : 0;
-    o->tiles = cx * cy;
+    float A = c / det;
+    float B = -(b / det);
+    float C = a / det;
+    o->A = A; o->B = B; o->C = C;
+    int covered = 0;
+    for (int ty = y0; ty <= y1; ++ty)
+        for (int tx = x0; tx <= x1; ++tx)
+            covered += km_tile_covered(u, v, A, B, C, tx, ty, tile_w, tile_h);
+    o->tiles = covered;
+}
+
+/* Tiles covered by one key-mode record, row-major within its rectangle;
+ * returns their number (out: global-in-view tile ids, may be NULL). */
+int32_t or_record_tiles(const or_km *k, int32_t ntx, int32_t tile_w, int32_t tile_h, int32_t *out)
+{
+    int32_t n = 0;
+    if (k->culled) return 0;
+    for (int ty = k->ty0; ty <= k->ty1; ++ty)
+        for (int tx = k->tx0; tx <= k->tx1; ++tx)
+            if (km_tile_covered(k->u, k->v, k->A, k->B, k->C, tx, ty, tile_w, tile_h)) {
+                if (out) out[n] = ty * ntx + tx;
+                ++n;
+            }
+    return n;
 }
 
 /* Depth key: the bits of a positive FP32 depth order like the depth. */
@@ -552,6 +618,8 @@ static int vset_build(const or_scene *sc, const or_view *vw, int32_t tile_w, int
         if (k->culled || k->tiles == 0) continue;
         for (int ty = k->ty0; ty <= k->ty1; ++ty)
             for (int tx = k->tx0; tx <= k->tx1; ++tx) {
+                if (!km_tile_covered(k->u, k->v, k->A, k->B, k->C, tx, ty, tile_w, tile_h))
+                    continue;
                 uint64_t tile = (uint64_t)(ty * S->ntx + tx);
                 keys[e].key = (tile << 32) | depth_bits(k->z);
                 keys[e].idx = i;  /* record order == ascending slot */

@@ -96,7 +96,7 @@ def test_transmittance_stop(oracle_mod):
 @pytest.mark.parametrize("tile", [(8, 8), (16, 16), (32, 8)])
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_tiling_independence(oracle_mod, tile, seed):
-    """The support rule (Mahalanobis^2 <= 9) and the 3-sigma tile rectangle make
+    """The support rule (Mahalanobis^2 <= 9) and the tiles its 3-sigma ellipse covers make
     the per-tile render identical to the brute-force per-pixel walk over the
     whole depth-ordered active set, for every tile shape."""
     sc, view = synth.tiny_scene(seed, n=64, sh_degree=1, width=48, height=40, depth=3.0,
@@ -206,7 +206,7 @@ def test_keymode_quaternion_invariance(oracle_mod):
 
 def test_keymode_matches_fp64_and_covers_support(oracle_mod):
     """The FP32 key mode agrees with the FP64 projection, and every pixel whose
-    FP64 Mahalanobis^2 is <= 9 lies in a tile of the key-mode rectangle."""
+    FP64 Mahalanobis^2 is <= 9 lies in a tile the key mode keeps."""
     sc, view = synth.tiny_scene(5, n=60, sh_degree=0, width=80, height=64, depth=3.0,
                                 log_scale_mean=-2.0, spread=1.0)
     view.fx = view.fy = 70.0
@@ -225,13 +225,49 @@ def test_keymode_matches_fp64_and_covers_support(oracle_mod):
         m = A * dx * dx + 2 * B * dx * dy + Cc * dy * dy
         inside = m <= 9.0
         tx, ty = xs // 16, ys // 16
-        in_rect = (tx >= km[i]["tx0"]) & (tx <= km[i]["tx1"]) & (ty >= km[i]["ty0"]) & \
-                  (ty <= km[i]["ty1"])
-        assert not np.any(inside & ~in_rect)
         ntx, nty = 5, 4
-        assert km[i]["tiles"] == max(0, km[i]["tx1"] - km[i]["tx0"] + 1) * \
+        kept = np.zeros(ntx * nty, bool)
+        kept[oracle_mod.record_tiles(km[i], view, 16, 16)] = True
+        assert not np.any(inside & ~kept[ty * ntx + tx])
+        assert km[i]["tiles"] == kept.sum() <= max(0, km[i]["tx1"] - km[i]["tx0"] + 1) * \
             max(0, km[i]["ty1"] - km[i]["ty0"] + 1)
         assert 0 <= km[i]["tx0"] and km[i]["tx1"] < ntx and km[i]["ty1"] < nty
+
+
+def test_tile_coverage_is_the_support_minimum(oracle_mod):
+    """A tile of the bounding rectangle is kept iff the minimum of the
+    Mahalanobis form over the rectangle spanned by the tile's pixel centres is
+    <= 9.009 (checked against scipy's box-constrained minimiser; the FP32 test
+    may differ only within 1e-4 of the threshold)."""
+    import scipy.optimize
+    sc, view = synth.tiny_scene(6, n=40, sh_degree=0, width=96, height=80, depth=3.0,
+                                log_scale_mean=-2.0, spread=1.0)
+    view.fx = view.fy = 80.0
+    km = oracle_mod.keymode(sc, view, np.arange(sc.n), tile_w=16, tile_h=16)
+    ntx = 6
+    checked = dropped = 0
+    for i in range(sc.n):
+        k = km[i]
+        if k["culled"]:
+            continue
+        kept = set(oracle_mod.record_tiles(k, view, 16, 16).tolist())
+        u, v, A, B, Cc = (float(k[f]) for f in ("u", "v", "A", "B", "C"))
+        for ty in range(k["ty0"], k["ty1"] + 1):
+            for tx in range(k["tx0"], k["tx1"] + 1):
+                lo = np.array([tx * 16 + 0.5 - u, ty * 16 + 0.5 - v])
+                hi = lo + 15.0
+                f = lambda d: A * d[0] ** 2 + 2 * B * d[0] * d[1] + Cc * d[1] ** 2
+                g = lambda d: np.array([2 * A * d[0] + 2 * B * d[1], 2 * B * d[0] + 2 * Cc * d[1]])
+                x0 = np.clip(np.zeros(2), lo, hi)
+                res = scipy.optimize.minimize(f, x0, jac=g, bounds=list(zip(lo, hi)),
+                                              method="L-BFGS-B", options=dict(ftol=1e-15, gtol=1e-12))
+                mmin = float(res.fun)
+                if abs(mmin - 9.009) <= 9.009e-4:
+                    continue
+                assert ((ty * ntx + tx) in kept) == (mmin <= 9.009), (i, tx, ty, mmin)
+                checked += 1
+                dropped += (ty * ntx + tx) not in kept
+    assert checked > 100 and dropped > 10
 
 
 def test_near_plane_culls(oracle_mod):
@@ -251,12 +287,10 @@ def test_sorted_lists_are_depth_then_slot(oracle_mod):
     sc.means[10] = sc.means[11]  # an exact depth tie between slots 10 and 11
     ids, km, nk, off, slots = oracle_mod.view_lists(sc, view, 16, 16)
     assert nk == int(km["tiles"][km["culled"] == 0].sum())
-    ntx = 4
+    covers = [set(oracle_mod.record_tiles(km[i], view, 16, 16).tolist()) for i in range(len(ids))]
     for t in range(len(off) - 1):
         lst = slots[off[t]:off[t + 1]]
-        tx, ty = t % ntx, t // ntx
-        want = [int(ids[i]) for i in range(len(ids)) if not km[i]["culled"] and
-                km[i]["tx0"] <= tx <= km[i]["tx1"] and km[i]["ty0"] <= ty <= km[i]["ty1"]]
+        want = [int(ids[i]) for i in range(len(ids)) if not km[i]["culled"] and t in covers[i]]
         assert sorted(lst.tolist()) == sorted(want)
         z = km["z"][np.searchsorted(ids, lst)]
         keys = list(zip(z.view(np.uint32).tolist(), lst.tolist()))
