@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the SwinGS frame-t splatting hot path on B300.
+
+Workload (one "step"): the sliding-window training step on 300k Gaussians
+(SH degree 3, 300-frame lifespans, frames 145..154, 4 of 20 ring cameras per
+frame = 40 views of 1352x1014): a 6,000-Gaussian slice streamed in from pinned
+host memory (Alg. 2 update), the batched forward of all 40 views, the L1 loss,
+the reverse blend and projection backward, and the Adam + SGLD noise +
+relocation step (Alg. 1). Metric: Mpix/s of the fwd+bwd step (batched); the
+plain per-view path, forward-only rates and the serving latency are reported
+beside it.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank trains a replica on its own
+window of views; gradients are summed across ranks with NCCL before the SGLD
+step (data parallel), so per-GPU work is fixed as N grows (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+FP32_LANES_PER_SM = 128          # FP32 lanes per SM (4 partitions x 32)
+# Algorithmic FP32 operations per evaluated (pixel, Gaussian) pair, FMA = 2.
+FLOP_PER_PAIR_FWD = 21
+FLOP_PER_PAIR_BWD = 62
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="swgs", choices=["swgs", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--views", type=int, default=4, help="cameras per frame")
+    ap.add_argument("--frames", type=int, default=10)
+    ap.add_argument("--tile", default="16x16", help="blend tile, WxH")
+    ap.add_argument("--batch", type=int, default=256, help="Gaussians staged per block step")
+    ap.add_argument("--ppt", type=int, default=2, help="blend pixels per thread")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in loaded for n, v in zip(names, r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+# ------------------------------------------------------------- CPU oracle --
+
+def cpu_oracle_sample(scene, views, targets, budget_s=15.0, max_views=None):
+    """Time the FP64 oracle (tiled fwd + bwd of whole views) on the host cores
+    until about budget_s of work; returns (mpix_per_s, cores, sample text)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    cores = oracle.num_threads()
+    t0 = time.perf_counter()
+    pix = 0
+    n = 0
+    for v, tgt in zip(views, targets):
+        ref = oracle.render(scene, v, mode="tiled", bands=None)
+        _, dl = oracle.l1_loss_grad([ref["rgb"]], [tgt])
+        oracle.render_bwd(scene, v, dl[0])
+        pix += v.width * v.height
+        n += 1
+        if time.perf_counter() - t0 > budget_s or (max_views and n >= max_views):
+            break
+    dt = time.perf_counter() - t0
+    return pix / dt / 1e6, cores, f"{n} of {len(views)} views, fwd+bwd (tiled FP64 oracle), {dt:.1f} s"
+
+
+# -------------------------------------------------------------- workload --
+
+def build_workload(args):
+    from paper_2409_07759_b300 import synth
+    scene, views, targets = synth.config2(n_frames=args.frames, per_frame=args.views,
+                                          forced_dead_fraction=0.01)
+    return scene, views, targets
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    scene, views, targets = build_workload(args)
+    rates = []
+    t_all = 0.0
+    sample = ""
+    cores = 1
+    for k in range(args.warmup + args.steps):
+        v = [views[k % len(views)]]
+        tg = [targets[k % len(views)]]
+        t0 = time.perf_counter()
+        rate, cores, sample = cpu_oracle_sample(scene, v, tg, budget_s=1e9, max_views=1)
+        if k >= args.warmup:
+            rates.append(rate)
+            t_all += time.perf_counter() - t0
+    value = statistics.mean(rates)
+    line = {"metric": "Mpix/s fwd+bwd (sliding-window training step)", "value": value,
+            "unit": "Mpix/s", "impl": "reference", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "sliding-window step, 300k Gaussians SH3, 40 x 1352x1014 "
+                                   "views (one view per reference step)",
+                       "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+                             "sample": "one view per step: " + sample},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+
+    from paper_2409_07759_b300 import api, build, synth
+    from paper_2409_07759_b300.window import WindowTrainer
+    build.build()
+
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) \
+        if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    scene, views, targets = build_workload(args)
+    # ranks train replicas on their own windows (views rotated by rank)
+    if world > 1:
+        views = views[rank:] + views[:rank]
+    mpix = sum(v.width * v.height for v in views) / 1e6
+    state = api.GaussianState.from_scene(scene)
+    tgt_host = [torch.from_numpy(t).pin_memory() for t in targets]
+    tgt_dev = [t.cuda() for t in tgt_host]
+    tw, th = (int(x) for x in args.tile.split("x"))
+    r = api.Renderer(tile=(tw, th), batch=args.batch, pixels_per_thread=args.ppt,
+                     count_pairs=True)
+    tr = WindowTrainer(r, state, views, tgt_dev, seed=1234 + rank)
+    # the streamed slices: 6,000-slot slices of the initial state, from pinned host
+    S = 6000
+    n_slices = scene.n // S
+    host_slices = []
+    for s in range(n_slices):
+        sub = api.GaussianState(*[getattr(state, k)[s * S:(s + 1) * S].clone() for k in
+                                  ("means", "log_scales", "quats", "opacity_logits", "sh",
+                                   "start", "expire", "birth", "frozen")], sh_degree=3)
+        host_slices.append(sub.pin_host())
+    slice_bytes = sum(t.numel() * t.element_size() for t in host_slices[0].values())
+
+    def upd(k):
+        s = k % n_slices
+        return (s * S, host_slices[s])
+
+    def allreduce():
+        if world > 1:
+            dist.all_reduce(tr._gflat)
+
+    if world > 1:
+        # data-parallel step: sum gradients across ranks before the SGLD step
+        orig_backward = r.backward
+
+        def backward_and_reduce(*a, **kw):
+            out = orig_backward(*a, **kw)
+            allreduce()
+            return out
+        r.backward = backward_and_reduce
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    for k in range(args.warmup):
+        tr.step(k, update=upd(k))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    # ---- timed region: the batched fwd+bwd window step ----
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    r.profile(True)
+    r.profile_read(reset=True)
+    launches0 = api.Renderer.kernel_launches()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record()
+        tr.step(args.warmup + k, update=upd(args.warmup + k))
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    launches = api.Renderer.kernel_launches() - launches0
+    prof = r.profile_read(reset=True)
+    r.profile(False)
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * args.steps * mpix / (ms / 1e3)
+
+    # pair counts of this workload (one untimed forward)
+    _, saved = r.render(state, views, keep_saved=True)
+    info = saved.info()
+    from paper_2409_07759_b300 import _abi
+    pairs_fwd = int(info.pairs)
+    pairs_bwd = int(saved.export(_abi.EXPORT_LAST).astype(np.int64).sum())
+    n_keys, n_rec = int(info.n_keys), int(info.n_records)
+    saved.release()
+
+    extra = {}
+    # ---- forward only, batched ----
+    torch.cuda.synchronize()
+    fe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        fe[k][0].record()
+        tr.step(0, render_only=True)
+        fe[k][1].record()
+    torch.cuda.synchronize()
+    fwd_ms = sum(a.elapsed_time(b) for a, b in fe) / args.steps
+    extra["fwd_batched_mpix_s"] = mpix / (fwd_ms / 1e3)
+    extra["step_batched_ms"] = ms / args.steps
+
+    # ---- plain per-view path (one view per launch sequence) ----
+    if not args.no_plain and args.plain_steps > 0:
+        tr.batched = False
+        tr.step(0)
+        torch.cuda.synchronize()
+        pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.plain_steps)]
+        for k in range(args.plain_steps):
+            flush.fill_(float(k))
+            pe[k][0].record()
+            tr.step(10_000 + k, update=upd(k))
+            pe[k][1].record()
+        torch.cuda.synchronize()
+        pms = sum(a.elapsed_time(b) for a, b in pe) / args.plain_steps
+        for k in range(args.plain_steps):
+            flush.fill_(float(k))
+            pe[k][0].record()
+            tr.step(0, render_only=True)
+            pe[k][1].record()
+        torch.cuda.synchronize()
+        pfms = sum(a.elapsed_time(b) for a, b in pe) / args.plain_steps
+        tr.batched = True
+        extra["plain_mpix_s"] = mpix / (pms / 1e3)
+        extra["fwd_plain_mpix_s"] = mpix / (pfms / 1e3)
+        extra["batched_over_plain"] = (ms / args.steps) and (pms / (ms / args.steps))
+
+    # ---- end to end through the public API with host buffers ----
+    h2d = sum(t.numel() * 4 for t in tgt_host) + slice_bytes
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        for d, h in zip(tgt_dev, tgt_host):
+            d.copy_(h, non_blocking=True)
+        loss = tr.step(20_000 + k, update=upd(k))
+        float(loss.item())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * args.steps * mpix / e2e_s, "unit": "Mpix/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4}
+
+    # ---- roofline of the dominant kernel ----
+    steps = args.steps
+    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
+    clk = (clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0))
+    alu_peak = sm_count * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    tile_passes = math.ceil(math.ceil(math.log2(max(2, sum(
+        ((v.width + tw - 1) // tw) * ((v.height + th - 1) // th) for v in views)))) / 8)
+    stage_cost = {
+        "blend_fwd": ("alu", FLOP_PER_PAIR_FWD * pairs_fwd / 1e12, "TFLOP/s"),
+        "blend_bwd": ("alu", FLOP_PER_PAIR_BWD * pairs_bwd / 1e12, "TFLOP/s"),
+        "tile_sort": ("hbm", 16.0 * tile_passes * n_keys / 1e9, "GB/s"),
+        "depth_sort": ("hbm", 16.0 * 4 * n_rec / 1e9, "GB/s"),
+        "emit": ("hbm", (8.0 * n_keys + 16.0 * n_rec) / 1e9, "GB/s"),
+        "preprocess": ("hbm", (236.0 * n_rec / args.views + 64.0 * n_rec) / 1e9, "GB/s"),
+        "preprocess_bwd": ("hbm", (236.0 * 2 * n_rec / args.views + 48.0 * n_rec) / 1e9, "GB/s"),
+    }
+    stages = {}
+    for name, (tot_ms, calls) in prof.items():
+        if calls == 0:
+            continue
+        per = tot_ms / steps
+        s = {"ms_per_step": per, "share": tot_ms / ms if ms else None}
+        if name in stage_cost:
+            bound, amount, unit = stage_cost[name]
+            ach = amount / (per / 1e3)
+            peak = alu_peak if bound == "alu" else hbm_peak
+            s.update(bound=bound, achieved=ach, unit=unit, frac=ach / peak)
+        stages[name] = s
+    dom = max(stages, key=lambda n: stages[n]["ms_per_step"])
+    d = stages[dom]
+    if "bound" in d:
+        roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"],
+                "peak": alu_peak if d["bound"] == "alu" else hbm_peak, "unit": d["unit"],
+                "frac": d["frac"], "traffic": None,
+                "peak_source": ("FP32 lanes x 2 x max SM clock" if d["bound"] == "alu"
+                                else f"{hbm_src} copy bandwidth")}
+    else:
+        roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, cores, sample = cpu_oracle_sample(scene, views, targets, budget_s=15.0)
+        cpu = {"value": rate, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+               "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": "Mpix/s fwd+bwd (sliding-window training step)",
+            "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded scene shaped like DyNeRF multi-view clips)",
+            "config": {"workload": "sliding-window step: 300k Gaussians SH3, frames 145-154 x "
+                                   f"{args.views} of 20 ring cameras = {len(views)} views of "
+                                   "1352x1014, fwd+bwd + Adam/SGLD + relocation + 6k-slot "
+                                   "slice update",
+                       "mpix_per_step": mpix, "tile": args.tile, "batch": args.batch,
+                       "pixels_per_thread": args.ppt,
+                       "parallelism": f"dp{world}", "l2": "flushed (256 MB write) before each step"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "pairs_fwd": pairs_fwd, "pairs_bwd": pairs_bwd, "keys": n_keys, "records": n_rec,
+            "stages": stages,
+            **extra,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    r.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -53,6 +53,7 @@ typedef struct swgs_config {
     float near_plane;        /* camera-space z below which Gaussians are culled */
     int32_t blocks_per_sm;   /* persistent blend grid = SMs x this; 0 = auto */
     int32_t count_pairs;     /* 1: count evaluated (pixel, Gaussian) pairs */
+    int32_t pixels_per_thread; /* blend pixels per thread: 1, 2 or 4 (4 not with 8x8) */
 } swgs_config;
 
 /*
@@ -96,7 +97,8 @@ typedef struct swgs_view {
 typedef struct swgs_ctx swgs_ctx;
 typedef struct swgs_saved swgs_saved;
 
-/* Fills cfg with 16x16 tiles, batch 256, near plane 0.2, auto grid. */
+/* Fills cfg with 16x16 tiles, batch 256, 2 pixels per thread, near plane 0.2,
+ * auto grid. */
 swgs_status swgs_default_config(swgs_config *cfg);
 
 /* Creates a context on the current CUDA device. alloc/free may be NULL. */
@@ -257,6 +259,37 @@ swgs_status swgs_sgld_step(swgs_ctx *ctx, const swgs_gaussians *g, const swgs_ga
  * overwrites: slice = target_frame mod swin_size, count = num_gs / swin_size. */
 swgs_status swgs_slice_range(int64_t target_frame, int64_t swin_size, int64_t num_gs,
                              int64_t *first, int64_t *count);
+
+/* ---- measurement (not part of the method) -------------------------------
+ * With profiling on, every stage of every call records a pair of CUDA events
+ * on the caller's stream; swgs_profile_read synchronises those events and
+ * returns the summed device time per stage. */
+enum {
+    SWGS_STAGE_COMPACT = 0,      /* active-set compaction */
+    SWGS_STAGE_PREPROCESS = 1,   /* projection + SH */
+    SWGS_STAGE_DEPTH_SORT = 2,   /* record depth sort */
+    SWGS_STAGE_KEY_SCAN = 3,     /* tiles touched in depth order + scan */
+    SWGS_STAGE_EMIT = 4,         /* key emission */
+    SWGS_STAGE_TILE_SORT = 5,    /* stable sort of keys by tile */
+    SWGS_STAGE_RANGES = 6,       /* per-tile ranges */
+    SWGS_STAGE_BLEND_FWD = 7,    /* forward blend (one kernel) */
+    SWGS_STAGE_BLEND_BWD = 8,    /* reverse blend (one kernel) */
+    SWGS_STAGE_PREPROCESS_BWD = 9,
+    SWGS_STAGE_LOSS = 10,
+    SWGS_STAGE_SGLD = 11,        /* Adam + noise (one kernel) */
+    SWGS_STAGE_RELOCATE = 12,
+    SWGS_STAGE_UPDATE = 13,      /* slice replacement */
+    SWGS_NUM_STAGES = 14
+};
+typedef struct swgs_profile {
+    double ms[SWGS_NUM_STAGES];      /* summed device milliseconds */
+    int64_t calls[SWGS_NUM_STAGES];  /* stage executions */
+} swgs_profile;
+swgs_status swgs_profile_enable(swgs_ctx *ctx, int32_t on);
+/* Synchronises the recorded events; reset = 1 clears the sums afterwards. */
+swgs_status swgs_profile_read(swgs_ctx *ctx, swgs_profile *out, int32_t reset);
+/* Kernels launched by this library in this process so far (all contexts). */
+int64_t swgs_kernel_launches(void);
 
 #ifdef __cplusplus
 }

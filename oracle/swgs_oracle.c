@@ -82,48 +82,100 @@ typedef struct {
     float A, B, C;             /* conic: m = A dx^2 + 2 B dx dy + C dy^2 */
 } or_km;
 
-/* A tile is kept when the minimum of the Mahalanobis form over the rectangle
- * spanned by its pixel centres is at most this (9 = the 3-sigma support, plus
- * 0.1% so that FP32 rounding can never drop a tile holding a pixel with
- * m <= 9). */
+/* A tile is kept when the ellipse {m <= OR_TILE_MAHAL} reaches the rectangle
+ * spanned by its pixel centres (9 = the 3-sigma support, plus 0.1% so that
+ * FP32 rounding can never drop a tile holding a pixel with m <= 9). */
 #define OR_TILE_MAHAL 9.009f
 
-/* min over t in [lo, hi] of P s^2 + 2 Q s t + R t^2 for fixed s (key mode). */
-static float km_edge_min(float P, float Q, float R, float s, float lo, float hi)
+/* Row rule (key mode). The ellipse E = {m <= OR_TILE_MAHAL} meets the band of
+ * pixel-centre rows dy in [ya, yb] in a convex set, so the tiles of a tile row
+ * that E reaches form one run; its x-extent [left, right] over the band comes
+ * from the chord ends c(y) -+ w(y) at the band ends (c = -(B/A) y,
+ * w = sqrt(A T - det_c y^2) / A) and from E's extreme points
+ * (+-xm, -+(B/C) xm), xm = sqrt(C T / det_c), where the x-extent is attained.
+ * km_row_extent returns 0 when the band misses E. */
+typedef struct { float AT, detc, rBA, iA, rBC, xm, ym; } km_ell;
+
+static km_ell km_ellipse(float A, float B, float C)
 {
-    float t = Q * s;
-    t = t / R;
-    t = -t;
-    t = t < lo ? lo : (t > hi ? hi : t);
-    float p1 = P * s;
-    p1 = p1 * s;
-    float p2 = Q * s;
-    p2 = p2 * t;
-    p2 = 2.0f * p2;
-    float p3 = R * t;
-    p3 = p3 * t;
-    float e = p1 + p2;
-    return e + p3;
+    km_ell e;
+    e.AT = A * OR_TILE_MAHAL;
+    float t1 = A * C;
+    float t2 = B * B;
+    e.detc = t1 - t2;
+    e.rBA = B / A;
+    e.iA = 1.0f / A;
+    e.rBC = B / C;
+    float q = C * OR_TILE_MAHAL;
+    q = q / e.detc;
+    e.xm = sqrtf(q);
+    q = e.AT / e.detc;
+    e.ym = sqrtf(q);
+    return e;
 }
 
-/* Does the 3-sigma ellipse of (u, v, A, B, C) reach tile (tx, ty)? */
-static int km_tile_covered(float u, float v, float A, float B, float C, int tx, int ty,
-                           int tile_w, int tile_h)
+/* The two ends c(y) -+ w(y) of the ellipse's chord at row offset y. */
+static void km_chord(const km_ell *e, float y, float *l, float *r)
 {
-    float x0 = (float)(tx * tile_w) + 0.5f;
-    float x1 = (float)(tx * tile_w) + ((float)tile_w - 0.5f);
-    float y0 = (float)(ty * tile_h) + 0.5f;
-    float y1 = (float)(ty * tile_h) + ((float)tile_h - 0.5f);
-    float xa = x0 - u, xb = x1 - u, ya = y0 - v, yb = y1 - v;
-    if (xa <= 0.0f && xb >= 0.0f && ya <= 0.0f && yb >= 0.0f) return 1;
-    float best = km_edge_min(A, B, C, xa, ya, yb);
-    float e = km_edge_min(A, B, C, xb, ya, yb);
-    if (e < best) best = e;
-    e = km_edge_min(C, B, A, ya, xa, xb);
-    if (e < best) best = e;
-    e = km_edge_min(C, B, A, yb, xa, xb);
-    if (e < best) best = e;
-    return best <= OR_TILE_MAHAL;
+    float c = e->rBA * y;
+    c = -c;
+    float q = e->detc * y;
+    q = q * y;
+    q = e->AT - q;
+    if (q < 0.0f) q = 0.0f;
+    q = sqrtf(q);
+    float w = q * e->iA;
+    *l = c - w;
+    *r = c + w;
+}
+
+static int km_row_extent(const km_ell *e, float ya, float yb, float *left, float *right)
+{
+    float lo = ya > -e->ym ? ya : -e->ym;
+    float hi = yb < e->ym ? yb : e->ym;
+    if (!(lo <= hi)) return 0;
+    float t = e->rBC * e->xm;
+    float dyr = -t;      /* row of the rightmost point */
+    float dyl = t;       /* row of the leftmost point */
+    float l0, r0, l1, r1;
+    km_chord(e, lo, &l0, &r0);
+    km_chord(e, hi, &l1, &r1);
+    if (lo <= dyr && dyr <= hi) *right = e->xm;
+    else *right = r0 > r1 ? r0 : r1;
+    if (lo <= dyl && dyl <= hi) *left = -e->xm;
+    else *left = l0 < l1 ? l0 : l1;
+    return 1;
+}
+
+/* The run [*first, *last] of kept tiles of row ty inside [tx0, tx1]
+ * (returns its length, 0 if none). A tile is kept when its pixel-centre
+ * x-span [xa, xb] meets [left, right]. If det_c <= 0 (degenerate conic) the
+ * whole row of the rectangle is kept. */
+static int km_row_run(const km_ell *e, float u, float v, int tx0, int tx1, int ty, int tile_w,
+                      int tile_h, int *first, int *last)
+{
+    if (!(e->detc > 0.0f)) { *first = tx0; *last = tx1; return tx1 - tx0 + 1; }
+    float by = (float)(ty * tile_h);
+    float ya = (by + 0.5f) - v;
+    float yb = (by + ((float)tile_h - 0.5f)) - v;
+    float left, right;
+    if (!km_row_extent(e, ya, yb, &left, &right)) return 0;
+    int a = tx0;
+    while (a <= tx1) {
+        float xb = ((float)(a * tile_w) + ((float)tile_w - 0.5f)) - u;
+        if (xb >= left) break;
+        ++a;
+    }
+    if (a > tx1) return 0;
+    int b = tx1;
+    while (b > a) {
+        float xa = ((float)(b * tile_w) + 0.5f) - u;
+        if (xa <= right) break;
+        --b;
+    }
+    *first = a;
+    *last = b;
+    return b - a + 1;
 }
 
 /* Blend thresholds (readings of the unspecified renderer details). */
@@ -330,10 +382,13 @@ void or_keymode(const or_scene *sc, const or_view *vw, int64_t slot,
     float B = -(b / det);
     float C = a / det;
     o->A = A; o->B = B; o->C = C;
+    km_ell e = km_ellipse(A, B, C);
     int covered = 0;
-    for (int ty = y0; ty <= y1; ++ty)
-        for (int tx = x0; tx <= x1; ++tx)
-            covered += km_tile_covered(u, v, A, B, C, tx, ty, tile_w, tile_h);
+    if (x1 >= x0)
+        for (int ty = y0; ty <= y1; ++ty) {
+            int f, l;
+            covered += km_row_run(&e, u, v, x0, x1, ty, tile_w, tile_h, &f, &l);
+        }
     o->tiles = covered;
 }
 
@@ -342,13 +397,16 @@ void or_keymode(const or_scene *sc, const or_view *vw, int64_t slot,
 int32_t or_record_tiles(const or_km *k, int32_t ntx, int32_t tile_w, int32_t tile_h, int32_t *out)
 {
     int32_t n = 0;
-    if (k->culled) return 0;
-    for (int ty = k->ty0; ty <= k->ty1; ++ty)
-        for (int tx = k->tx0; tx <= k->tx1; ++tx)
-            if (km_tile_covered(k->u, k->v, k->A, k->B, k->C, tx, ty, tile_w, tile_h)) {
-                if (out) out[n] = ty * ntx + tx;
-                ++n;
-            }
+    if (k->culled || k->tx1 < k->tx0) return 0;
+    km_ell e = km_ellipse(k->A, k->B, k->C);
+    for (int ty = k->ty0; ty <= k->ty1; ++ty) {
+        int f, l;
+        if (!km_row_run(&e, k->u, k->v, k->tx0, k->tx1, ty, tile_w, tile_h, &f, &l)) continue;
+        for (int tx = f; tx <= l; ++tx) {
+            if (out) out[n] = ty * ntx + tx;
+            ++n;
+        }
+    }
     return n;
 }
 
@@ -616,15 +674,18 @@ static int vset_build(const or_scene *sc, const or_view *vw, int32_t tile_w, int
     for (int64_t i = 0; i < S->n; ++i) {
         const or_km *k = &S->km[i];
         if (k->culled || k->tiles == 0) continue;
-        for (int ty = k->ty0; ty <= k->ty1; ++ty)
-            for (int tx = k->tx0; tx <= k->tx1; ++tx) {
-                if (!km_tile_covered(k->u, k->v, k->A, k->B, k->C, tx, ty, tile_w, tile_h))
-                    continue;
+        km_ell el = km_ellipse(k->A, k->B, k->C);
+        for (int ty = k->ty0; ty <= k->ty1; ++ty) {
+            int f, l;
+            if (!km_row_run(&el, k->u, k->v, k->tx0, k->tx1, ty, tile_w, tile_h, &f, &l))
+                continue;
+            for (int tx = f; tx <= l; ++tx) {
                 uint64_t tile = (uint64_t)(ty * S->ntx + tx);
                 keys[e].key = (tile << 32) | depth_bits(k->z);
                 keys[e].idx = i;  /* record order == ascending slot */
                 ++e;
             }
+        }
     }
     {
         /* ties on the full key keep emission (record) order: sort on

@@ -32,7 +32,7 @@ EXPORT_VIEW_TABLE = 11
 class SwgsConfig(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("batch", C.c_int32),
                 ("near_plane", C.c_float), ("blocks_per_sm", C.c_int32),
-                ("count_pairs", C.c_int32)]
+                ("count_pairs", C.c_int32), ("pixels_per_thread", C.c_int32)]
 
 
 class SwgsGaussians(C.Structure):
@@ -66,6 +66,15 @@ class SwgsAdamState(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in
                 ("m_means", "v_means", "m_log_scales", "v_log_scales", "m_quats", "v_quats",
                  "m_logits", "v_logits", "m_sh", "v_sh")]
+
+
+NUM_STAGES = 14
+STAGE_NAMES = ["compact", "preprocess", "depth_sort", "key_scan", "emit", "tile_sort", "ranges",
+               "blend_fwd", "blend_bwd", "preprocess_bwd", "loss", "sgld", "relocate", "update"]
+
+
+class SwgsProfile(C.Structure):
+    _fields_ = [("ms", C.c_double * NUM_STAGES), ("calls", C.c_int64 * NUM_STAGES)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -103,6 +112,9 @@ PROTOTYPES = [
                                  C.POINTER(C.c_int64), C.c_void_p]),
     ("swgs_slice_range", C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_int64),
                                    C.POINTER(C.c_int64)]),
+    ("swgs_profile_enable", C.c_int, [C.c_void_p, C.c_int32]),
+    ("swgs_profile_read", C.c_int, [C.c_void_p, C.POINTER(SwgsProfile), C.c_int32]),
+    ("swgs_kernel_launches", C.c_int64, []),
 ]
 
 _lib = None

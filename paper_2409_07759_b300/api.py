@@ -193,7 +193,7 @@ class Renderer:
     comes from torch's caching allocator through the library's callbacks."""
 
     def __init__(self, tile=(16, 16), batch=256, near_plane=0.2, blocks_per_sm=0,
-                 count_pairs=False, use_torch_allocator=True):
+                 count_pairs=False, pixels_per_thread=2, use_torch_allocator=True):
         L = _abi.load()
         cfg = _abi.SwgsConfig()
         L.swgs_default_config(C.byref(cfg))
@@ -202,6 +202,7 @@ class Renderer:
         cfg.near_plane = float(near_plane)
         cfg.blocks_per_sm = int(blocks_per_sm)
         cfg.count_pairs = int(bool(count_pairs))
+        cfg.pixels_per_thread = int(pixels_per_thread)
         self.cfg = cfg
         self.device = torch.cuda.current_device()
         if use_torch_allocator:
@@ -248,6 +249,20 @@ class Renderer:
     def _stream(stream=None):
         s = stream if stream is not None else torch.cuda.current_stream()
         return C.c_void_p(s.cuda_stream)
+
+    # -- measurement -----------------------------------------------------------
+    def profile(self, on: bool = True):
+        self._check(_abi.load().swgs_profile_enable(self.ctx, int(bool(on))))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """Summed device milliseconds per stage since the last reset."""
+        p = _abi.SwgsProfile()
+        self._check(_abi.load().swgs_profile_read(self.ctx, C.byref(p), int(bool(reset))))
+        return {n: (p.ms[i], int(p.calls[i])) for i, n in enumerate(_abi.STAGE_NAMES)}
+
+    @staticmethod
+    def kernel_launches() -> int:
+        return int(_abi.load().swgs_kernel_launches())
 
     # -- Sec. 4.2 / Alg. 2 filter ------------------------------------------------
     def active_ids(self, state: GaussianState, frame: int, stream=None) -> torch.Tensor:

@@ -2,18 +2,23 @@
 // its reverse-order backward (Alg. 1 loss.backward).
 //
 // Persistent launch: a grid of (SMs x resident blocks) pulls (view, tile) work
-// items from one atomic counter, over every view of the batch at once. One
-// thread per pixel; Gaussians of the tile's depth-sorted list are staged in
-// shared memory BATCH at a time (converted once per block to the log2-domain
-// form the inner loop needs). A thread leaves the inner loop as soon as its
-// pixel saturates, so a warp stops when all 32 of its pixels are done and the
-// block stops staging when all its pixels are.
+// items from one atomic counter, over every view of the batch at once. Each
+// thread owns PPT vertically adjacent pixels of the tile; the Gaussians of the
+// tile's depth-sorted list are staged in shared memory BATCH at a time
+// (converted once per block to the log2-domain form the inner loop needs).
+// The inner loops are branch-free: every lane of a warp walks the list in
+// lockstep with predicated updates, so no lane diverges at the per-pair
+// tests, and the warp leaves as soon as a vote says all its pixels saturated;
+// the block stops staging when all its pixels have.
 //
 // The backward walks the list from the block's largest last-contributor index
 // down to the front, recovering each T from the saved final transmittance by
-// division, and reduces the nine 2D gradients of each Gaussian across the warp
-// (a transposing butterfly, 14 shuffles for 9 values), then across the block
-// in shared memory, before one vector atomic per Gaussian per tile.
+// division. Per Gaussian it accumulates nine moments -- sum of gm, gm dx,
+// gm dy, gm dx^2, gm dx dy, gm dy^2 (gm = dL/dm) and of the colour weights --
+// over the thread's pixels, sums them across the warp (a transposing butterfly,
+// 14 shuffles for 9 values) and across the block in shared memory, and turns
+// them into the nine 2D gradients (centre, conic, opacity, colour) once per
+// Gaussian per tile before one vector atomic.
 #include "swgs_internal.cuh"
 
 namespace swgs {
@@ -24,17 +29,25 @@ __device__ __forceinline__ void stage_gaussian(const Records& rec, uint32_t r, f
     const float4 B = rec.b[r];
     const float4 Cc = rec.c[r];
     *s0 = make_float4(A.x, A.y, __fmul_rn(B.x, -0.5f * kLog2e), __fmul_rn(B.y, -kLog2e));
-    *s1 = make_float4(__fmul_rn(B.z, -0.5f * kLog2e), __log2f(A.z), A.z, 0.f);
+    *s1 = make_float4(__fmul_rn(B.z, -0.5f * kLog2e), __log2f(A.z), 0.f, 0.f);
     *s2 = Cc;
 }
 
-template <int TW, int TH, int BATCH>
-__global__ void __launch_bounds__(TW * TH) blend_fwd_kernel(BlendArgs a) {
-    constexpr int NT = TW * TH;
+template <int TW, int TH, int PPT>
+struct TileGeom {
+    static constexpr int NT = TW * TH / PPT;
+    static_assert(NT % 32 == 0, "a tile block must be whole warps");
+    static_assert(TH % PPT == 0, "pixels per thread must divide the tile height");
+};
+
+template <int TW, int TH, int BATCH, int PPT>
+__global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
+    constexpr int NT = TileGeom<TW, TH, PPT>::NT;
     __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
     __shared__ int s_item;
+    const unsigned F = 0xffffffffu;
     const int tid = threadIdx.x;
-    const int lx = tid % TW, ly = tid / TW;
+    const int lx = tid % TW, ly = (tid / TW) * PPT;
     unsigned long long pairs = 0;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.work_counter, 1);
@@ -45,62 +58,77 @@ __global__ void __launch_bounds__(TW * TH) blend_fwd_kernel(BlendArgs a) {
         const ViewDev& V = a.views[vi];
         const int W = V.W, H = V.H;
         const int lt = item - V.tile_base;
-        const int x = (lt % V.ntx) * TW + lx, y = (lt / V.ntx) * TH + ly;
-        const bool inside = x < W && y < H;
-        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+        const int x = (lt % V.ntx) * TW + lx, y0 = (lt / V.ntx) * TH + ly;
+        const float px = (float)x + 0.5f;
         const int2 rg = a.ranges[item];
-        float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-        int last = 0;
-        bool done = !inside;
-        int stop = rg.y;
+        float T[PPT], C0[PPT], C1[PPT], C2[PPT], py[PPT];
+        int last[PPT], stop[PPT];
+        bool done[PPT];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            T[p] = 1.f; C0[p] = C1[p] = C2[p] = 0.f; last[p] = 0; stop[p] = rg.y;
+            py[p] = (float)(y0 + p) + 0.5f;
+            done[p] = !(x < W && y0 + p < H);
+        }
         for (int b0 = rg.x; b0 < rg.y; b0 += BATCH) {
-            if (__syncthreads_count(done) == NT) break;
+            bool tdone = true;
+#pragma unroll
+            for (int p = 0; p < PPT; ++p) tdone &= done[p];
+            if (__syncthreads_count(tdone) == NT) break;
             for (int k = tid; k < BATCH; k += NT) {
                 const int idx = b0 + k;
                 if (idx < rg.y) stage_gaussian(a.rec, a.vals[idx], &s0[k], &s1[k], &s2[k]);
             }
             __syncthreads();
             const int cnt = min(BATCH, rg.y - b0);
-            if (!done) {
-                for (int j = 0; j < cnt; ++j) {
-                    const float4 g0 = s0[j];
-                    const float2 g1 = make_float2(s1[j].x, s1[j].y);
+            for (int j = 0; j < cnt; ++j) {
+                if (__all_sync(F, tdone)) break;
+                const float4 g0 = s0[j];
+                const float2 g1 = *reinterpret_cast<const float2*>(&s1[j]);
+                const float4 c = s2[j];
+                const int pos = b0 + j;
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
                     float dx, dy, au;
-                    const float q = pair_q(px, py, g0, g1.x, &dx, &dy);
-                    if (q < kQMin) continue;
+                    const float q = pair_q(px, py[p], g0, g1.x, &dx, &dy);
                     const float al = pair_alpha(q, g1.y, &au);
-                    if (al < kAlphaMin) continue;
-                    const float tT = __fmul_rn(T, __fsub_rn(1.f, al));
-                    if (tT < kTStop) {
-                        done = true;
-                        stop = b0 + j;
-                        break;
-                    }
-                    const float w = __fmul_rn(al, T);
-                    const float4 c = s2[j];
-                    C0 = __fmaf_rn(c.x, w, C0);
-                    C1 = __fmaf_rn(c.y, w, C1);
-                    C2 = __fmaf_rn(c.z, w, C2);
-                    T = tT;
-                    last = b0 + j - rg.x + 1;
+                    const bool ok = !done[p] && q >= kQMin && al >= kAlphaMin;
+                    const float tT = __fmul_rn(T[p], __fsub_rn(1.f, al));
+                    const bool stp = ok && tT < kTStop;
+                    const bool inc = ok && !stp;
+                    stop[p] = stp ? pos : stop[p];
+                    done[p] = done[p] || stp;
+                    const float w = inc ? __fmul_rn(al, T[p]) : 0.f;
+                    C0[p] = __fmaf_rn(c.x, w, C0[p]);
+                    C1[p] = __fmaf_rn(c.y, w, C1[p]);
+                    C2[p] = __fmaf_rn(c.z, w, C2[p]);
+                    T[p] = inc ? tT : T[p];
+                    last[p] = inc ? pos - rg.x + 1 : last[p];
                 }
+                tdone = true;
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) tdone &= done[p];
             }
         }
-        if (inside) {
-            const long long hw = (long long)W * H, p = (long long)y * W + x;
-            V.out_rgb[p] = C0 + T * V.bg[0];
-            V.out_rgb[hw + p] = C1 + T * V.bg[1];
-            V.out_rgb[2 * hw + p] = C2 + T * V.bg[2];
-            if (V.out_T) V.out_T[p] = T;
-            if (a.T) a.T[V.pix_base + p] = T;
-            if (a.last) a.last[V.pix_base + p] = last;
-            pairs += (unsigned long long)((stop < rg.y ? stop + 1 : rg.y) - rg.x);
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int y = y0 + p;
+            if (x < W && y < H) {
+                const long long hw = (long long)W * H, q = (long long)y * W + x;
+                V.out_rgb[q] = C0[p] + T[p] * V.bg[0];
+                V.out_rgb[hw + q] = C1[p] + T[p] * V.bg[1];
+                V.out_rgb[2 * hw + q] = C2[p] + T[p] * V.bg[2];
+                if (V.out_T) V.out_T[q] = T[p];
+                if (a.T) a.T[V.pix_base + q] = T[p];
+                if (a.last) a.last[V.pix_base + q] = last[p];
+                pairs += (unsigned long long)((stop[p] < rg.y ? stop[p] + 1 : rg.y) - rg.x);
+            }
         }
         __syncthreads();
     }
     if (a.pairs) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(F, pairs, o);
         if ((tid & 31) == 0 && pairs) atomicAdd(a.pairs, pairs);
     }
 }
@@ -137,15 +165,16 @@ __device__ __forceinline__ void warp_sum9_to_smem(const float* v, float* acc) {
     if (lane == 0 && v8 != 0.f) atomicAdd(&acc[8], v8);
 }
 
-template <int TW, int TH, int BATCH>
-__global__ void __launch_bounds__(TW * TH) blend_bwd_kernel(BlendArgs a) {
-    constexpr int NT = TW * TH;
-    __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH], s3[BATCH];
+template <int TW, int TH, int BATCH, int PPT>
+__global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
+    constexpr int NT = TileGeom<TW, TH, PPT>::NT;
+    __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
     __shared__ uint32_t s_rec[BATCH];
     __shared__ float s_acc[BATCH * 9];
     __shared__ int s_item, s_maxlast;
+    const unsigned F = 0xffffffffu;
     const int tid = threadIdx.x;
-    const int lx = tid % TW, ly = tid / TW;
+    const int lx = tid % TW, ly = (tid / TW) * PPT;
     for (int k = tid; k < BATCH * 9; k += NT) s_acc[k] = 0.f;
     for (;;) {
         if (tid == 0) { s_item = atomicAdd(a.work_counter, 1); s_maxlast = 0; }
@@ -156,22 +185,29 @@ __global__ void __launch_bounds__(TW * TH) blend_bwd_kernel(BlendArgs a) {
         const ViewDev& V = a.views[vi];
         const int W = V.W, H = V.H;
         const int lt = item - V.tile_base;
-        const int x = (lt % V.ntx) * TW + lx, y = (lt / V.ntx) * TH + ly;
-        const bool inside = x < W && y < H;
-        const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+        const int x = (lt % V.ntx) * TW + lx, y0 = (lt / V.ntx) * TH + ly;
+        const float px = (float)x + 0.5f;
         const int2 rg = a.ranges[item];
-        float T = 1.f, dL0 = 0.f, dL1 = 0.f, dL2 = 0.f;
-        int last = 0;
-        if (inside) {
-            const long long hw = (long long)W * H, p = (long long)y * W + x;
-            T = a.T[V.pix_base + p];
-            last = a.last[V.pix_base + p];
-            dL0 = V.dL[p];
-            dL1 = V.dL[hw + p];
-            dL2 = V.dL[2 * hw + p];
+        float T[PPT], dL0[PPT], dL1[PPT], dL2[PPT], B0[PPT], B1[PPT], B2[PPT], py[PPT];
+        int last[PPT];
+        int mylast = 0;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int y = y0 + p;
+            py[p] = (float)y + 0.5f;
+            T[p] = 1.f; dL0[p] = dL1[p] = dL2[p] = 0.f; last[p] = 0;
+            B0[p] = V.bg[0]; B1[p] = V.bg[1]; B2[p] = V.bg[2];
+            if (x < W && y < H) {
+                const long long hw = (long long)W * H, q = (long long)y * W + x;
+                T[p] = a.T[V.pix_base + q];
+                last[p] = a.last[V.pix_base + q];
+                dL0[p] = V.dL[q];
+                dL1[p] = V.dL[hw + q];
+                dL2[p] = V.dL[2 * hw + q];
+            }
+            mylast = max(mylast, last[p]);
         }
-        float B0 = V.bg[0], B1 = V.bg[1], B2 = V.bg[2];
-        if (last > 0) atomicMax(&s_maxlast, last);
+        if (mylast > 0) atomicMax(&s_maxlast, mylast);
         __syncthreads();
         const int end = rg.x + s_maxlast;
         for (int b1 = end; b1 > rg.x; b1 -= BATCH) {
@@ -182,129 +218,149 @@ __global__ void __launch_bounds__(TW * TH) blend_bwd_kernel(BlendArgs a) {
                 const uint32_t r = a.vals[b0 + k];
                 s_rec[k] = r;
                 stage_gaussian(a.rec, r, &s0[k], &s1[k], &s2[k]);
-                s3[k] = a.rec.b[r];
             }
             __syncthreads();
             for (int j = cnt - 1; j >= 0; --j) {
                 const int pos = b0 + j - rg.x;
-                float g[9];
+                if (__all_sync(F, pos >= mylast)) continue;
+                const float4 g0 = s0[j];
+                const float2 g1 = *reinterpret_cast<const float2*>(&s1[j]);
+                const float4 c = s2[j];
+                float m[9];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) g[k] = 0.f;
-                bool contrib = false;
-                if (pos < last) {
-                    const float4 g0 = s0[j];
-                    const float4 g1 = s1[j];
+                for (int k = 0; k < 9; ++k) m[k] = 0.f;
+                bool any = false;
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
                     float dx, dy, au;
-                    const float q = pair_q(px, py, g0, g1.x, &dx, &dy);
-                    if (q >= kQMin) {
-                        const float al = pair_alpha(q, g1.y, &au);
-                        if (al >= kAlphaMin) {
-                            contrib = true;
-                            const float om = __fsub_rn(1.f, al);
-                            T = __fdividef(T, om);
-                            const float w = al * T;
-                            const float4 c = s2[j];
-                            g[6] = w * dL0;
-                            g[7] = w * dL1;
-                            g[8] = w * dL2;
-                            const float ga = T * (dL0 * (c.x - B0) + dL1 * (c.y - B1) + dL2 * (c.z - B2));
-                            B0 = al * c.x + om * B0;
-                            B1 = al * c.y + om * B1;
-                            B2 = al * c.z + om * B2;
-                            if (au <= kAlphaMax) {
-                                const float4 cn = s3[j];
-                                g[5] = ga * au / g1.z;
-                                const float gm = -0.5f * au * ga;
-                                g[2] = gm * dx * dx;
-                                g[3] = 2.f * gm * dx * dy;
-                                g[4] = gm * dy * dy;
-                                g[0] = -2.f * gm * (cn.x * dx + cn.y * dy);
-                                g[1] = -2.f * gm * (cn.y * dx + cn.z * dy);
-                            }
-                        }
-                    }
+                    const float q = pair_q(px, py[p], g0, g1.x, &dx, &dy);
+                    const float al = pair_alpha(q, g1.y, &au);
+                    const bool ok = pos < last[p] && q >= kQMin && al >= kAlphaMin;
+                    any |= ok;
+                    const float om = __fsub_rn(1.f, al);
+                    T[p] = ok ? __fdividef(T[p], om) : T[p];
+                    const float w = ok ? al * T[p] : 0.f;
+                    m[6] = fmaf(w, dL0[p], m[6]);
+                    m[7] = fmaf(w, dL1[p], m[7]);
+                    m[8] = fmaf(w, dL2[p], m[8]);
+                    const float ga = T[p] * (dL0[p] * (c.x - B0[p]) + dL1[p] * (c.y - B1[p]) +
+                                             dL2[p] * (c.z - B2[p]));
+                    B0[p] = ok ? fmaf(al, c.x, om * B0[p]) : B0[p];
+                    B1[p] = ok ? fmaf(al, c.y, om * B1[p]) : B1[p];
+                    B2[p] = ok ? fmaf(al, c.z, om * B2[p]) : B2[p];
+                    const float gm = (ok && au <= kAlphaMax) ? -0.5f * au * ga : 0.f;
+                    const float gx = gm * dx, gy = gm * dy;
+                    m[0] += gm;
+                    m[1] += gx;
+                    m[2] += gy;
+                    m[3] = fmaf(gx, dx, m[3]);
+                    m[4] = fmaf(gx, dy, m[4]);
+                    m[5] = fmaf(gy, dy, m[5]);
                 }
-                if (__any_sync(0xffffffffu, contrib)) warp_sum9_to_smem(g, &s_acc[j * 9]);
+                if (__any_sync(F, any)) warp_sum9_to_smem(m, &s_acc[j * 9]);
             }
             __syncthreads();
             for (int k = tid; k < cnt; k += NT) {
                 float* acc = &s_acc[k * 9];
-                float* dst = a.grad2d + 12ll * s_rec[k];
                 bool nz = false;
 #pragma unroll
                 for (int e = 0; e < 9; ++e) nz |= acc[e] != 0.f;
-                if (nz) {
-                    red_add_v4(dst, acc[0], acc[1], acc[2], acc[3]);
-                    red_add_v4(dst + 4, acc[4], acc[5], acc[6], acc[7]);
-                    red_add(dst + 8, acc[8]);
+                if (!nz) continue;
+                const uint32_t r = s_rec[k];
+                const float4 ra = a.rec.a[r];   // u, v, opacity, depth
+                const float4 rb = a.rec.b[r];   // A, B, C
+                // m = A dx^2 + 2B dx dy + C dy^2, dx = px - u: dm/du = -2(A dx + B dy)
+                const float du = -2.f * (rb.x * acc[1] + rb.y * acc[2]);
+                const float dv = -2.f * (rb.y * acc[1] + rb.z * acc[2]);
+                // alpha = o G, dalpha/do = G = alpha/o and gm = -alpha/2 dL/dalpha
+                const float dop = -2.f * acc[0] / ra.z;
+                float* dst = a.grad2d + 12ll * r;
+                red_add_v4(dst, du, dv, acc[3], 2.f * acc[4]);
+                red_add_v4(dst + 4, acc[5], dop, acc[6], acc[7]);
+                red_add(dst + 8, acc[8]);
 #pragma unroll
-                    for (int e = 0; e < 9; ++e) acc[e] = 0.f;
-                }
+                for (int e = 0; e < 9; ++e) acc[e] = 0.f;
             }
         }
         __syncthreads();
     }
 }
 
-template <int TW, int TH, int BATCH>
+template <int TW, int TH, int BATCH, int PPT>
 static cudaError_t run_fwd(const BlendArgs& a, int grid, cudaStream_t s) {
-    blend_fwd_kernel<TW, TH, BATCH><<<grid, TW * TH, 0, s>>>(a);
+    note_launch();
+    blend_fwd_kernel<TW, TH, BATCH, PPT><<<grid, TW * TH / PPT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int TW, int TH, int BATCH>
+template <int TW, int TH, int BATCH, int PPT>
 static cudaError_t run_bwd(const BlendArgs& a, int grid, cudaStream_t s) {
-    blend_bwd_kernel<TW, TH, BATCH><<<grid, TW * TH, 0, s>>>(a);
+    note_launch();
+    blend_bwd_kernel<TW, TH, BATCH, PPT><<<grid, TW * TH / PPT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int TW, int TH, int BATCH>
+template <int TW, int TH, int BATCH, int PPT>
 static int occ(bool bwd) {
     int n = 0;
     if (bwd)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_bwd_kernel<TW, TH, BATCH>, TW * TH, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_bwd_kernel<TW, TH, BATCH, PPT>,
+                                                      TW * TH / PPT, 0);
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_fwd_kernel<TW, TH, BATCH>, TW * TH, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_fwd_kernel<TW, TH, BATCH, PPT>,
+                                                      TW * TH / PPT, 0);
     return n < 1 ? 1 : n;
 }
 
-#define SWGS_TILE_DISPATCH(FN, ...)                                                  \
-    do {                                                                             \
-        if (tile_w == 16 && tile_h == 16) {                                          \
-            if (batch == 32) return FN<16, 16, 32>(__VA_ARGS__);                     \
-            if (batch == 64) return FN<16, 16, 64>(__VA_ARGS__);                     \
-            if (batch == 128) return FN<16, 16, 128>(__VA_ARGS__);                   \
-            if (batch == 256) return FN<16, 16, 256>(__VA_ARGS__);                   \
-        } else if (tile_w == 8 && tile_h == 8) {                                     \
-            if (batch == 32) return FN<8, 8, 32>(__VA_ARGS__);                       \
-            if (batch == 64) return FN<8, 8, 64>(__VA_ARGS__);                       \
-            if (batch == 128) return FN<8, 8, 128>(__VA_ARGS__);                     \
-            if (batch == 256) return FN<8, 8, 256>(__VA_ARGS__);                     \
-        } else if (tile_w == 32 && tile_h == 8) {                                    \
-            if (batch == 32) return FN<32, 8, 32>(__VA_ARGS__);                      \
-            if (batch == 64) return FN<32, 8, 64>(__VA_ARGS__);                      \
-            if (batch == 128) return FN<32, 8, 128>(__VA_ARGS__);                    \
-            if (batch == 256) return FN<32, 8, 256>(__VA_ARGS__);                    \
-        }                                                                            \
+#define SWGS_BATCH_DISPATCH(FN, TW, TH, PPT, ...)                  \
+    do {                                                           \
+        if (batch == 32) return FN<TW, TH, 32, PPT>(__VA_ARGS__);  \
+        if (batch == 64) return FN<TW, TH, 64, PPT>(__VA_ARGS__);  \
+        if (batch == 128) return FN<TW, TH, 128, PPT>(__VA_ARGS__); \
+        if (batch == 256) return FN<TW, TH, 256, PPT>(__VA_ARGS__); \
     } while (0)
 
-cudaError_t launch_blend_fwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int grid,
-                             cudaStream_t s) {
+#define SWGS_TILE_DISPATCH(FN, ...)                                              \
+    do {                                                                         \
+        if (tile_w == 16 && tile_h == 16) {                                      \
+            if (ppt == 1) SWGS_BATCH_DISPATCH(FN, 16, 16, 1, __VA_ARGS__);       \
+            if (ppt == 2) SWGS_BATCH_DISPATCH(FN, 16, 16, 2, __VA_ARGS__);       \
+            if (ppt == 4) SWGS_BATCH_DISPATCH(FN, 16, 16, 4, __VA_ARGS__);       \
+        } else if (tile_w == 8 && tile_h == 8) {                                 \
+            if (ppt == 1) SWGS_BATCH_DISPATCH(FN, 8, 8, 1, __VA_ARGS__);         \
+            if (ppt == 2) SWGS_BATCH_DISPATCH(FN, 8, 8, 2, __VA_ARGS__);         \
+        } else if (tile_w == 32 && tile_h == 8) {                                \
+            if (ppt == 1) SWGS_BATCH_DISPATCH(FN, 32, 8, 1, __VA_ARGS__);        \
+            if (ppt == 2) SWGS_BATCH_DISPATCH(FN, 32, 8, 2, __VA_ARGS__);        \
+            if (ppt == 4) SWGS_BATCH_DISPATCH(FN, 32, 8, 4, __VA_ARGS__);        \
+        }                                                                        \
+    } while (0)
+
+cudaError_t launch_blend_fwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int ppt,
+                             int grid, cudaStream_t s) {
     if (a.total_tiles <= 0) return cudaSuccess;
     SWGS_TILE_DISPATCH(run_fwd, a, grid, s);
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_blend_bwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int grid,
-                             cudaStream_t s) {
+cudaError_t launch_blend_bwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int ppt,
+                             int grid, cudaStream_t s) {
     if (a.total_tiles <= 0) return cudaSuccess;
     SWGS_TILE_DISPATCH(run_bwd, a, grid, s);
     return cudaErrorInvalidValue;
 }
 
-int blend_blocks_per_sm(int tile_w, int tile_h, int batch, bool backward) {
+int blend_blocks_per_sm(int tile_w, int tile_h, int batch, int ppt, bool backward) {
     SWGS_TILE_DISPATCH(occ, backward);
     return 1;
+}
+
+bool blend_config_valid(int tile_w, int tile_h, int batch, int ppt) {
+    if (!(batch == 32 || batch == 64 || batch == 128 || batch == 256)) return false;
+    if (tile_w == 16 && tile_h == 16) return ppt == 1 || ppt == 2 || ppt == 4;
+    if (tile_w == 8 && tile_h == 8) return ppt == 1 || ppt == 2;
+    if (tile_w == 32 && tile_h == 8) return ppt == 1 || ppt == 2 || ppt == 4;
+    return false;
 }
 
 }  // namespace swgs

@@ -67,6 +67,7 @@ cudaError_t launch_active_flags_count(const int32_t* start, const int32_t* expir
                                       const int32_t* frames, int n_frames, uint32_t* block_counts,
                                       int n_blocks, cudaStream_t s) {
     dim3 grid(n_blocks, n_frames);
+    note_launch();
     active_count_kernel<<<grid, kCompactBlock, 0, s>>>(start, expire, n, frames, block_counts,
                                                        n_blocks);
     return cudaGetLastError();
@@ -77,6 +78,7 @@ cudaError_t launch_active_write(const int32_t* start, const int32_t* expire, lon
                                 int n_blocks, int32_t* out_ids, long long /*ids_stride*/,
                                 int32_t* out_counts, cudaStream_t s) {
     dim3 grid(n_blocks, n_frames);
+    note_launch();
     active_write_kernel<<<grid, kCompactBlock, 0, s>>>(start, expire, n, frames, block_offsets,
                                                        n_blocks, out_ids, out_counts);
     return cudaGetLastError();

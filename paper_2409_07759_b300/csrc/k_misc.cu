@@ -55,6 +55,7 @@ cudaError_t launch_loss_l1(const ViewDev*, int n_views, long long total_pix,
     cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), s);
     if (e != cudaSuccess || total_pix <= 0) return e;
     L1Args a{pix_offsets, rgb, target, dl, n_views, total_pix, loss};
+    note_launch();
     loss_l1_kernel<<<div_up(total_pix, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -107,6 +108,7 @@ cudaError_t launch_copy_slice(const swgs_gaussians& dst, long long first, long l
     long long mx = count * 3LL * K;
     int gx = div_up(mx, 256);
     if (gx > 1184) gx = 1184;
+    note_launch();
     copy_slice_kernel<<<dim3(gx, 9), 256, 0, s>>>(a);
     return cudaGetLastError();
 }

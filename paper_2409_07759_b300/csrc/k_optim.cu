@@ -121,6 +121,7 @@ cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
     a.bc2 = (float)(1.0 - pow((double)p.beta2, (double)(step + 1)));
     a.seed = seed;
     a.step = step;
+    note_launch();
     sgld_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -167,6 +168,7 @@ cudaError_t launch_reloc_weights(const swgs_gaussians& g, const int32_t* frames,
     a.g = g;
     for (int f = 0; f < n_frames; ++f) a.frames[f] = frames[f];
     a.n_frames = n_frames;
+    note_launch();
     reloc_weights_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(a, weights, dead);
     return cudaGetLastError();
 }
@@ -200,6 +202,7 @@ cudaError_t launch_reloc_sample(const swgs_gaussians& g, const uint8_t* dead,
                                 const unsigned long long* cdf, unsigned long long seed,
                                 unsigned long long step, int32_t* targets, int32_t* counts,
                                 unsigned long long* n_dead, cudaStream_t s) {
+    note_launch();
     reloc_sample_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(g.capacity, dead, cdf, seed,
                                                                  step, targets, counts, n_dead);
     return cudaGetLastError();
@@ -280,9 +283,11 @@ cudaError_t launch_reloc_apply(const swgs_gaussians& g, const swgs_adam_state* a
     swgs_adam_state m{};
     if (adam) m = *adam;
     const int grid = div_up(g.capacity, 256);
+    note_launch();
     reloc_copy_kernel<<<grid, 256, 0, s>>>(g, m, targets, counts, max_n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    note_launch();
     reloc_target_kernel<<<grid, 256, 0, s>>>(g, m, counts, max_n);
     return cudaGetLastError();
 }

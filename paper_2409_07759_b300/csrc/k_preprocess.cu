@@ -264,9 +264,14 @@ __global__ void __launch_bounds__(128) preprocess_kernel(PreArgs a) {
                 const int x1 = fxhi > (float)(ntx - 1) ? ntx - 1 : (fxhi < -1.0f ? -1 : (int)fxhi);
                 const int y0 = fylo < 0.0f ? 0 : (fylo > (float)nty ? nty : (int)fylo);
                 const int y1 = fyhi > (float)(nty - 1) ? nty - 1 : (fyhi < -1.0f ? -1 : (int)fyhi);
-                const int cx = x1 >= x0 ? x1 - x0 + 1 : 0;
-                const int cy = y1 >= y0 ? y1 - y0 + 1 : 0;
-                tiles = cx * cy;
+                // tiles of the bounding rectangle the 3-sigma ellipse reaches
+                if (x1 >= x0) {
+                    const KmEllipse el = km_ellipse(A, B, C);
+                    for (int ty = y0; ty <= y1; ++ty) {
+                        int f, l;
+                        tiles += km_row_run(el, u, v, x0, x1, ty, a.tile_w, a.tile_h, &f, &l);
+                    }
+                }
                 rect = make_short4((short)x0, (short)x1, (short)y0, (short)y1);
             }
         }
@@ -300,6 +305,7 @@ cudaError_t launch_preprocess(const swgs_gaussians& g, const ViewDev* views, con
                               cudaStream_t s) {
     if (total_active <= 0) return cudaSuccess;
     PreArgs a{g, views, groups, n_groups, ids, total_active, tile_w, tile_h, near_plane, rec};
+    note_launch();
     preprocess_kernel<<<div_up(total_active, 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -524,6 +530,7 @@ cudaError_t launch_preprocess_bwd(const swgs_gaussians& g, const swgs_gaussians&
                                   const float* grad2d, cudaStream_t s) {
     if (total_active <= 0) return cudaSuccess;
     PreBwdArgs a{g, grads, views, groups, n_groups, ids, total_active, grad2d};
+    note_launch();
     preprocess_bwd_kernel<<<div_up(total_active, 128), 128, 0, s>>>(a);
     return cudaGetLastError();
 }

@@ -120,8 +120,11 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, long long n, v
     }
     long long nb = (n + kScanTile - 1) / kScanTile;
     unsigned long long* part = (unsigned long long*)temp;
+    note_launch();
     scan_reduce_kernel<uint32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part);
+    note_launch();
     scan_partials_kernel<<<1, kScanThreads, 0, s>>>(part, nb, total);
+    note_launch();
     scan_final_kernel<uint32_t, false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, part);
     return cudaGetLastError();
 }
@@ -133,8 +136,11 @@ cudaError_t inclusive_scan_u64(const unsigned long long* in, unsigned long long*
     if (n <= 0) return cudaSuccess;
     long long nb = (n + kScanTile - 1) / kScanTile;
     unsigned long long* part = (unsigned long long*)temp;
+    note_launch();
     scan_reduce_kernel<unsigned long long><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part);
+    note_launch();
     scan_partials_kernel<<<1, kScanThreads, 0, s>>>(part, nb, nullptr);
+    note_launch();
     scan_final_kernel<unsigned long long, true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n,
                                                                                        part);
     return cudaGetLastError();

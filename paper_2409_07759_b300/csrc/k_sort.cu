@@ -217,10 +217,12 @@ cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_
     for (int p = 0; p < plan.passes; ++p) {
         const int bits = plan.bits_per_pass[p];
         const int bins = 1 << bits;
+        note_launch();
         radix_upsweep<<<G, kSortThreads, 0, s>>>(ki, n, shift, bins, tpb, n_tiles, hist);
         cudaError_t e = exclusive_scan_u32(hist, hist, (long long)bins * G, scan_tmp, total, s);
         if (e != cudaSuccess) return e;
         const uint32_t* vread = (p == 0 && vals_iota) ? nullptr : vi;
+        note_launch();
         radix_downsweep<<<G, kSortThreads, smem, s>>>(ki, vread, ko, vo, n, shift, bins, tpb,
                                                       n_tiles, hist);
         e = cudaGetLastError();

@@ -25,7 +25,16 @@
 
 using namespace swgs;
 
+namespace swgs {
+std::atomic<long long> g_kernel_launches{0};
+}
+
 namespace {
+
+struct ProfEvent {
+    int stage;
+    cudaEvent_t a, b;
+};
 
 struct Buf {
     void* p = nullptr;
@@ -71,6 +80,12 @@ struct swgs_ctx {
     size_t pinned_cap = 0;
     std::vector<swgs_saved*> pool;
     std::vector<swgs_saved*> all_saved;
+    // stage profiling
+    bool prof = false;
+    std::vector<ProfEvent> prof_pending;
+    std::vector<cudaEvent_t> prof_free;
+    double prof_ms[SWGS_NUM_STAGES] = {};
+    long long prof_calls[SWGS_NUM_STAGES] = {};
 };
 
 namespace {
@@ -91,6 +106,38 @@ swgs_status fail(swgs_ctx* c, swgs_status st, const char* fmt, ...) {
         if (_e != cudaSuccess)                                                        \
             return fail(ctx, SWGS_ECUDA, "%s failed: %s", #expr, cudaGetErrorString(_e)); \
     } while (0)
+
+cudaEvent_t prof_event(swgs_ctx* c) {
+    if (!c->prof_free.empty()) {
+        cudaEvent_t e = c->prof_free.back();
+        c->prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Records a pair of events around one stage on the caller's stream.
+struct StageScope {
+    swgs_ctx* c;
+    int stage;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    StageScope(swgs_ctx* c_, int st, cudaStream_t s_) : c(c_), stage(st), s(s_) {
+        if (c->prof) {
+            a = prof_event(c);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~StageScope() {
+        if (c->prof && a) {
+            cudaEvent_t b = prof_event(c);
+            cudaEventRecord(b, s);
+            c->prof_pending.push_back({stage, a, b});
+        }
+    }
+};
 
 void* ctx_alloc(swgs_ctx* c, size_t bytes, cudaStream_t s) {
     if (c->alloc) return c->alloc(c->user, bytes, (void*)s);
@@ -213,6 +260,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
     CK(cudaMemcpyAsync(ctx->frames.p, frames.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, s));
     std::vector<int> n_act(F, 0);
     if (N > 0) {
+        StageScope sc_(ctx, SWGS_STAGE_COMPACT, s);
         CK(launch_active_flags_count(g->start, g->expire, N, P<int32_t>(ctx->frames), F,
                                      P<uint32_t>(ctx->block_cnt), nb, s));
         CK(exclusive_scan_u32(P<uint32_t>(ctx->block_cnt), P<uint32_t>(ctx->block_cnt),
@@ -220,6 +268,8 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
         CK(launch_active_write(g->start, g->expire, N, P<int32_t>(ctx->frames), F,
                                P<uint32_t>(ctx->block_cnt), nb, P<int32_t>(B.ids), 0,
                                P<int32_t>(ctx->counts), s));
+    }
+    if (N > 0) {
         CK(cudaMemcpyAsync(ctx->pinned, ctx->counts.p, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         memcpy(n_act.data(), ctx->pinned, sizeof(int32_t) * F);
@@ -297,8 +347,11 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
                        cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.groups.p, B.h_groups.data(), sizeof(GroupDev) * F, cudaMemcpyHostToDevice, s));
     Records rc = records_of(B);
-    CK(launch_preprocess(*g, P<ViewDev>(B.views), P<GroupDev>(B.groups), F, P<int32_t>(B.ids), act,
-                         tw, th, ctx->cfg.near_plane, rc, s));
+    {
+        StageScope sc_(ctx, SWGS_STAGE_PREPROCESS, s);
+        CK(launch_preprocess(*g, P<ViewDev>(B.views), P<GroupDev>(B.groups), F, P<int32_t>(B.ids),
+                             act, tw, th, ctx->cfg.near_plane, rc, s));
+    }
     // 3. depth order of the records and their key offsets
     long long n_keys = 0;
     if (rec > 0) {
@@ -306,17 +359,23 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
         if (!ensure(ctx, ctx->sort_tmp, radix_temp_bytes((long long)R, ctx->num_sms), s))
             return fail(ctx, SWGS_ENOMEM, "allocation failed (sort)");
         bool in_b = false;
-        CK(radix_sort_pairs(P<uint32_t>(B.rec_depth), P<uint32_t>(ctx->order_a),
-                            P<uint32_t>(ctx->order_b), P<uint32_t>(ctx->tcount), (long long)R, dp,
-                            ctx->sort_tmp.p, ctx->num_sms, true, &in_b, s));
+        {
+            StageScope sc_(ctx, SWGS_STAGE_DEPTH_SORT, s);
+            CK(radix_sort_pairs(P<uint32_t>(B.rec_depth), P<uint32_t>(ctx->order_a),
+                                P<uint32_t>(ctx->order_b), P<uint32_t>(ctx->tcount), (long long)R,
+                                dp, ctx->sort_tmp.p, ctx->num_sms, true, &in_b, s));
+        }
         // 4 passes: results back in (rec_depth, order_a)
         const uint32_t* order = in_b ? P<uint32_t>(ctx->tcount) : P<uint32_t>(ctx->order_a);
         uint32_t* cnt = in_b ? P<uint32_t>(ctx->order_a) : P<uint32_t>(ctx->tcount);
-        CK(launch_gather_tiles(order, rc.tiles, cnt, (long long)R, s));
         if (!ensure(ctx, ctx->scan_tmp, scan_u32_temp_bytes((long long)R) + 64, s))
             return fail(ctx, SWGS_ENOMEM, "allocation failed (scan)");
-        CK(exclusive_scan_u32(cnt, P<uint32_t>(ctx->koff), (long long)R, ctx->scan_tmp.p,
-                              P<unsigned long long>(ctx->totals), s));
+        {
+            StageScope sc_(ctx, SWGS_STAGE_KEY_SCAN, s);
+            CK(launch_gather_tiles(order, rc.tiles, cnt, (long long)R, s));
+            CK(exclusive_scan_u32(cnt, P<uint32_t>(ctx->koff), (long long)R, ctx->scan_tmp.p,
+                                  P<unsigned long long>(ctx->totals), s));
+        }
         CK(cudaMemcpyAsync(ctx->pinned, ctx->totals.p, sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -339,14 +398,24 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
         const bool odd = (tp.passes & 1) != 0;
         uint32_t* ev = odd ? P<uint32_t>(ctx->vals_tmp) : P<uint32_t>(B.vals);
         uint32_t* ov = odd ? P<uint32_t>(B.vals) : P<uint32_t>(ctx->vals_tmp);
-        CK(launch_emit_keys(order, P<uint32_t>(ctx->koff), (long long)R, rc, P<ViewDev>(B.views),
-                            (int)B.h_views.size(), P<uint32_t>(ctx->keys_a), ev, s));
+        {
+            StageScope sc_(ctx, SWGS_STAGE_EMIT, s);
+            CK(launch_emit_keys(order, P<uint32_t>(ctx->koff), (long long)R, rc,
+                                P<ViewDev>(B.views), (int)B.h_views.size(), tw, th,
+                                ctx->num_sms, P<uint32_t>(ctx->keys_a), ev, s));
+        }
         bool kb = false;
-        CK(radix_sort_pairs(P<uint32_t>(ctx->keys_a), ev, P<uint32_t>(ctx->keys_b), ov,
-                            (long long)K, tp, ctx->sort_tmp.p, ctx->num_sms, false, &kb, s));
+        {
+            StageScope sc_(ctx, SWGS_STAGE_TILE_SORT, s);
+            CK(radix_sort_pairs(P<uint32_t>(ctx->keys_a), ev, P<uint32_t>(ctx->keys_b), ov,
+                                (long long)K, tp, ctx->sort_tmp.p, ctx->num_sms, false, &kb, s));
+        }
         const uint32_t* skeys = kb ? P<uint32_t>(ctx->keys_b) : P<uint32_t>(ctx->keys_a);
-        CK(cudaMemsetAsync(B.ranges.p, 0, sizeof(int2) * (size_t)tiles, s));
-        CK(launch_tile_ranges(skeys, (long long)K, P<int2>(B.ranges), s));
+        {
+            StageScope sc_(ctx, SWGS_STAGE_RANGES, s);
+            CK(cudaMemsetAsync(B.ranges.p, 0, sizeof(int2) * (size_t)tiles, s));
+            CK(launch_tile_ranges(skeys, (long long)K, P<int2>(B.ranges), s));
+        }
     } else {
         B.n_keys = 0;
         CK(cudaMemsetAsync(B.ranges.p, 0, sizeof(int2) * (size_t)tiles, s));
@@ -365,14 +434,18 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
     ba.work_counter = P<int>(ctx->counter);
     ba.pairs = pairs;
     ba.grad2d = nullptr;
+    const int ppt = ctx->cfg.pixels_per_thread;
     int bps = ctx->cfg.blocks_per_sm > 0
                   ? ctx->cfg.blocks_per_sm
-                  : blend_blocks_per_sm(tw, th, ctx->cfg.batch, false);
+                  : blend_blocks_per_sm(tw, th, ctx->cfg.batch, ppt, false);
     long long grid = (long long)ctx->num_sms * bps;
     if (grid > tiles) grid = tiles;
     if (grid < 1) grid = 1;
     CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), s));
-    CK(launch_blend_fwd(ba, tw, th, ctx->cfg.batch, (int)grid, s));
+    {
+        StageScope sc_(ctx, SWGS_STAGE_BLEND_FWD, s);
+        CK(launch_blend_fwd(ba, tw, th, ctx->cfg.batch, ppt, (int)grid, s));
+    }
     return SWGS_OK;
 }
 
@@ -403,15 +476,24 @@ swgs_status backward_batch(swgs_ctx* ctx, const swgs_gaussians* g, BatchState& B
     ba.work_counter = P<int>(ctx->counter);
     ba.pairs = nullptr;
     ba.grad2d = P<float>(B.grad2d);
-    int bps = ctx->cfg.blocks_per_sm > 0 ? ctx->cfg.blocks_per_sm
-                                         : blend_blocks_per_sm(tw, th, ctx->cfg.batch, true);
+    const int ppt = ctx->cfg.pixels_per_thread;
+    int bps = ctx->cfg.blocks_per_sm > 0
+                  ? ctx->cfg.blocks_per_sm
+                  : blend_blocks_per_sm(tw, th, ctx->cfg.batch, ppt, true);
     long long grid = (long long)ctx->num_sms * bps;
     if (grid > B.n_tiles) grid = B.n_tiles;
     if (grid < 1) grid = 1;
     CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), s));
-    CK(launch_blend_bwd(ba, tw, th, ctx->cfg.batch, (int)grid, s));
-    CK(launch_preprocess_bwd(*g, *grads, P<ViewDev>(B.views), P<GroupDev>(B.groups), B.n_groups,
-                             P<int32_t>(B.ids), B.total_active, P<float>(B.grad2d), s));
+    {
+        StageScope sc_(ctx, SWGS_STAGE_BLEND_BWD, s);
+        CK(launch_blend_bwd(ba, tw, th, ctx->cfg.batch, ppt, (int)grid, s));
+    }
+    {
+        StageScope sc_(ctx, SWGS_STAGE_PREPROCESS_BWD, s);
+        CK(launch_preprocess_bwd(*g, *grads, P<ViewDev>(B.views), P<GroupDev>(B.groups),
+                                 B.n_groups, P<int32_t>(B.ids), B.total_active,
+                                 P<float>(B.grad2d), s));
+    }
     return SWGS_OK;
 }
 
@@ -479,6 +561,7 @@ swgs_status swgs_default_config(swgs_config* cfg) {
     cfg->near_plane = 0.2f;
     cfg->blocks_per_sm = 0;
     cfg->count_pairs = 0;
+    cfg->pixels_per_thread = 2;
     return SWGS_OK;
 }
 
@@ -489,7 +572,7 @@ swgs_status swgs_create(const swgs_config* cfg, swgs_alloc_fn alloc, swgs_free_f
     swgs_config c{};
     if (cfg) c = *cfg; else swgs_default_config(&c);
     if (!valid_tile(c.tile_w, c.tile_h) || !valid_batch(c.batch) || !(c.near_plane > 0.f) ||
-        c.blocks_per_sm < 0)
+        c.blocks_per_sm < 0 || !blend_config_valid(c.tile_w, c.tile_h, c.batch, c.pixels_per_thread))
         return SWGS_EINVAL;
     if ((alloc == nullptr) != (free_fn == nullptr)) return SWGS_EINVAL;
     swgs_ctx* ctx = new swgs_ctx();
@@ -524,6 +607,8 @@ void swgs_destroy(swgs_ctx* ctx) {
         delete sv;
     }
     cudaStreamSynchronize(s);
+    for (const ProfEvent& e : ctx->prof_pending) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    for (cudaEvent_t e : ctx->prof_free) cudaEventDestroy(e);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     delete ctx;
 }
@@ -582,6 +667,7 @@ swgs_status swgs_frame_update(swgs_ctx* ctx, const swgs_gaussians* dst, int64_t 
                     (long long)first, (long long)(first + count), (long long)dst->capacity);
     if (count == 0) return SWGS_OK;
     const int K = (dst->sh_degree + 1) * (dst->sh_degree + 1);
+    StageScope sc_(ctx, SWGS_STAGE_UPDATE, s);
     if (src_on_host) {
         struct { void* d; const void* s; size_t w; } arr[9] = {
             {dst->means, src->means, 12}, {dst->log_scales, src->log_scales, 12},
@@ -779,6 +865,7 @@ swgs_status swgs_saved_export(swgs_ctx* ctx, const swgs_saved* saved, int32_t wh
                     return fail(ctx, SWGS_ENOMEM, "allocation failed");
                 CK(cudaMemcpyAsync(ci.p, B.call_index.data(), sizeof(int) * B.call_index.size(),
                                    cudaMemcpyHostToDevice, s));
+                note_launch();
                 export_record_kernel<<<div_up(m, 256), 256, 0, s>>>(
                     what, P<ViewDev>(B.views), (int)B.h_views.size(), P<GroupDev>(B.groups),
                     P<int32_t>(B.ids), records_of(B), P<int>(ci), m, cur);
@@ -795,6 +882,7 @@ swgs_status swgs_saved_export(swgs_ctx* ctx, const swgs_saved* saved, int32_t wh
             case SWGS_EXPORT_SORTED_SLOT:
                 m = B.n_keys;
                 if (m == 0) break;
+                note_launch();
                 export_sorted_slot_kernel<<<div_up(m, 256), 256, 0, s>>>(
                     P<uint32_t>(B.vals), m, P<ViewDev>(B.views), (int)B.h_views.size(),
                     P<GroupDev>(B.groups), P<int32_t>(B.ids), (int32_t*)cur);
@@ -803,6 +891,7 @@ swgs_status swgs_saved_export(swgs_ctx* ctx, const swgs_saved* saved, int32_t wh
             case SWGS_EXPORT_TILE_RANGES:
                 m = B.n_tiles;
                 if (m == 0) break;
+                note_launch();
                 export_ranges_kernel<<<div_up(m, 256), 256, 0, s>>>(P<int2>(B.ranges), m,
                                                                    (int)key_off, (int2*)cur);
                 CK(cudaGetLastError());
@@ -868,6 +957,7 @@ swgs_status swgs_loss_l1(swgs_ctx* ctx, int32_t n_views, const swgs_view* views,
     if (!ensure(ctx, ctx->l1_tab, tab.size(), s)) return fail(ctx, SWGS_ENOMEM, "allocation failed");
     CK(cudaMemcpyAsync(ctx->l1_tab.p, tab.data(), tab.size(), cudaMemcpyHostToDevice, s));
     char* base = (char*)ctx->l1_tab.p;
+    StageScope sc_(ctx, SWGS_STAGE_LOSS, s);
     CK(launch_loss_l1(nullptr, n_views, off[n_views], (const long long*)base,
                       (const float* const*)(base + 8 * (n_views + 1)),
                       (const float* const*)(base + 8 * (n_views + 1) + 8 * n_views),
@@ -895,9 +985,13 @@ swgs_status swgs_sgld_step(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_ga
         if (n_relocated) *n_relocated = 0;
         return SWGS_OK;
     }
-    CK(launch_sgld(*g, grads, adam, frames, n_frames, *params, seed, step, s));
+    {
+        StageScope sc_(ctx, SWGS_STAGE_SGLD, s);
+        CK(launch_sgld(*g, grads, adam, frames, n_frames, *params, seed, step, s));
+    }
     long long nd = 0;
     if (params->relocate) {
+        StageScope sc_(ctx, SWGS_STAGE_RELOCATE, s);
         if (!ensure(ctx, ctx->reloc_w, 8 * (size_t)N, s) ||
             !ensure(ctx, ctx->reloc_cdf, 8 * (size_t)N, s) ||
             !ensure(ctx, ctx->reloc_dead, (size_t)N, s) ||
@@ -930,5 +1024,35 @@ swgs_status swgs_sgld_step(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_ga
     if (n_relocated) *n_relocated = nd;
     return SWGS_OK;
 }
+
+swgs_status swgs_profile_enable(swgs_ctx* ctx, int32_t on) {
+    if (!ctx) return SWGS_EINVAL;
+    ctx->prof = on != 0;
+    return SWGS_OK;
+}
+
+swgs_status swgs_profile_read(swgs_ctx* ctx, swgs_profile* out, int32_t reset) {
+    if (!ctx || !out) return SWGS_EINVAL;
+    for (const ProfEvent& e : ctx->prof_pending) {
+        CK(cudaEventSynchronize(e.b));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e.a, e.b));
+        ctx->prof_ms[e.stage] += ms;
+        ctx->prof_calls[e.stage] += 1;
+        ctx->prof_free.push_back(e.a);
+        ctx->prof_free.push_back(e.b);
+    }
+    ctx->prof_pending.clear();
+    for (int i = 0; i < SWGS_NUM_STAGES; ++i) {
+        out->ms[i] = ctx->prof_ms[i];
+        out->calls[i] = ctx->prof_calls[i];
+    }
+    if (reset) {
+        for (int i = 0; i < SWGS_NUM_STAGES; ++i) { ctx->prof_ms[i] = 0.0; ctx->prof_calls[i] = 0; }
+    }
+    return SWGS_OK;
+}
+
+int64_t swgs_kernel_launches(void) { return (int64_t)g_kernel_launches.load(); }
 
 }  // extern "C"

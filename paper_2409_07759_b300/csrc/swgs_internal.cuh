@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/swgs.h"
 
 namespace swgs {
@@ -121,6 +123,84 @@ __device__ __forceinline__ double kd_exp(double x) {
     return __dmul_rn(p, __longlong_as_double((e + 1023) << 52));
 }
 
+// A tile is kept when the ellipse {m <= 9.009} reaches the rectangle spanned
+// by its pixel centres: the 3-sigma support plus 0.1%, so FP32 rounding never
+// drops a tile holding a pixel with m <= 9.
+constexpr float kTileMahal = 9.009f;
+
+// Row rule (key mode): the ellipse meets a band of pixel-centre rows in a
+// convex set, so the kept tiles of a tile row form one run; its x-extent
+// [left, right] over the band comes from the chord ends c(y) -+ w(y) at the
+// band ends (c = -(B/A) y, w = sqrt(A T - det_c y^2) / A) and from the
+// ellipse's extreme points (+-xm, -+(B/C) xm), xm = sqrt(C T / det_c).
+struct KmEllipse {
+    float AT, detc, rBA, iA, rBC, xm, ym;
+};
+
+__device__ __forceinline__ KmEllipse km_ellipse(float A, float B, float C) {
+    KmEllipse e;
+    e.AT = kmul(A, kTileMahal);
+    e.detc = ksub(kmul(A, C), kmul(B, B));
+    e.rBA = kdiv(B, A);
+    e.iA = kdiv(1.0f, A);
+    e.rBC = kdiv(B, C);
+    e.xm = ksqrt(kdiv(kmul(C, kTileMahal), e.detc));
+    e.ym = ksqrt(kdiv(e.AT, e.detc));
+    return e;
+}
+
+// The two ends c(y) -+ w(y) of the ellipse's chord at row offset y.
+__device__ __forceinline__ void km_chord(const KmEllipse& e, float y, float* l, float* r) {
+    const float c = -kmul(e.rBA, y);
+    float q = ksub(e.AT, kmul(kmul(e.detc, y), y));
+    q = q < 0.0f ? 0.0f : q;
+    const float w = kmul(ksqrt(q), e.iA);
+    *l = ksub(c, w);
+    *r = kadd(c, w);
+}
+
+__device__ __forceinline__ bool km_row_extent(const KmEllipse& e, float ya, float yb,
+                                              float* left, float* right) {
+    const float lo = ya > -e.ym ? ya : -e.ym;
+    const float hi = yb < e.ym ? yb : e.ym;
+    if (!(lo <= hi)) return false;
+    const float t = kmul(e.rBC, e.xm);
+    const float dyr = -t, dyl = t;
+    float l0, r0, l1, r1;
+    km_chord(e, lo, &l0, &r0);
+    km_chord(e, hi, &l1, &r1);
+    *right = (lo <= dyr && dyr <= hi) ? e.xm : (r0 > r1 ? r0 : r1);
+    *left = (lo <= dyl && dyl <= hi) ? -e.xm : (l0 < l1 ? l0 : l1);
+    return true;
+}
+
+// Kept run [first, last] of tile row ty within [tx0, tx1]; returns its length.
+__device__ __forceinline__ int km_row_run(const KmEllipse& e, float u, float v, int tx0, int tx1,
+                                          int ty, int tile_w, int tile_h, int* first, int* last) {
+    if (!(e.detc > 0.0f)) { *first = tx0; *last = tx1; return tx1 - tx0 + 1; }
+    const float by = (float)(ty * tile_h);
+    const float ya = ksub(kadd(by, 0.5f), v);
+    const float yb = ksub(kadd(by, (float)tile_h - 0.5f), v);
+    float left, right;
+    if (!km_row_extent(e, ya, yb, &left, &right)) return 0;
+    int a = tx0;
+    while (a <= tx1) {
+        const float xb = ksub(kadd((float)(a * tile_w), (float)tile_w - 0.5f), u);
+        if (xb >= left) break;
+        ++a;
+    }
+    if (a > tx1) return 0;
+    int b = tx1;
+    while (b > a) {
+        const float xa = ksub(kadd((float)(b * tile_w), 0.5f), u);
+        if (xa <= right) break;
+        --b;
+    }
+    *first = a;
+    *last = b;
+    return b - a + 1;
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): counter-based, so any
 // (seed, step, slot) draw is reproducible without state.
@@ -217,6 +297,10 @@ __device__ __forceinline__ void red_add(float* addr, float a) {
 
 inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// Kernel launches issued by the library (reported by the benchmark).
+extern std::atomic<long long> g_kernel_launches;
+inline void note_launch(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
 // ---------------------------------------------------------------------------
 // Host-side launchers (one translation unit each).
 // ---------------------------------------------------------------------------
@@ -271,8 +355,9 @@ cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_
 cudaError_t launch_gather_tiles(const uint32_t* order, const int32_t* tiles, uint32_t* out,
                                 long long n, cudaStream_t s);
 cudaError_t launch_emit_keys(const uint32_t* order, const uint32_t* offsets, long long n_rec,
-                             const Records rec, const ViewDev* views, int n_views,
-                             uint32_t* keys, uint32_t* vals, cudaStream_t s);
+                             const Records rec, const ViewDev* views, int n_views, int tile_w,
+                             int tile_h, int num_sms, uint32_t* keys, uint32_t* vals,
+                             cudaStream_t s);
 cudaError_t launch_tile_ranges(const uint32_t* keys, long long n_keys, int2* ranges,
                                cudaStream_t s);
 
@@ -290,11 +375,12 @@ struct BlendArgs {
     unsigned long long* pairs;  // optional
     float* grad2d;     // backward: 12 floats per record
 };
-cudaError_t launch_blend_fwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int grid,
-                             cudaStream_t s);
-cudaError_t launch_blend_bwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int grid,
-                             cudaStream_t s);
-int blend_blocks_per_sm(int tile_w, int tile_h, int batch, bool backward);
+cudaError_t launch_blend_fwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int ppt,
+                             int grid, cudaStream_t s);
+cudaError_t launch_blend_bwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int ppt,
+                             int grid, cudaStream_t s);
+int blend_blocks_per_sm(int tile_w, int tile_h, int batch, int ppt, bool backward);
+bool blend_config_valid(int tile_w, int tile_h, int batch, int ppt);
 
 // k_misc.cu
 cudaError_t launch_loss_l1(const ViewDev* views, int n_views, long long total_pix,

@@ -1,0 +1,84 @@
+"""The inner step of Alg. 1 (train_swin) over a whole sliding window at once:
+every (frame, camera) view of the window is rendered forward and backward in
+one batched pass, then the optimiser / SGLD noise / relocation step runs on
+the Gaussians active in the window's frames. A per-frame slice replacement
+(Alg. 2 update_thread) can be streamed in from pinned host memory first.
+
+Every stage is one call into libswgs on the current torch stream.
+"""
+from __future__ import annotations
+
+from typing import Optional, Sequence
+
+import torch
+
+from . import api
+
+DEFAULT_SGLD = dict(lr_means=1.6e-4, lr_log_scales=5e-3, lr_quats=1e-3, lr_logits=5e-2,
+                    lr_sh_dc=2.5e-3, lr_sh_rest=2.5e-3 / 20.0, beta1=0.9, beta2=0.999, eps=1e-15,
+                    noise_lr=5e4, noise_k=100.0, noise_t=0.005, adam=1, relocate=1, max_n=51)
+
+
+def _flat_views(n: int, K: int, device="cuda"):
+    """One flat zero-filled buffer viewed as the five parameter-shaped arrays
+    (one memset clears all of them)."""
+    sizes = [n * 3, n * 3, n * 4, n, n * K * 3]
+    flat = torch.zeros(sum(sizes), dtype=torch.float32, device=device)
+    parts = torch.split(flat, sizes)
+    shapes = [(n, 3), (n, 3), (n, 4), (n,), (n, K, 3)]
+    return flat, [p.view(s) for p, s in zip(parts, shapes)]
+
+
+class WindowTrainer:
+    """Holds the state, gradients, Adam moments and per-view buffers of one
+    window and runs training steps on it."""
+
+    def __init__(self, renderer: api.Renderer, state: api.GaussianState, views: Sequence,
+                 targets: Sequence[torch.Tensor], params: Optional[dict] = None, seed: int = 0,
+                 batched: bool = True, bg=(0.0, 0.0, 0.0)):
+        self.r = renderer
+        self.state = state
+        self.views = list(views)
+        self.targets = list(targets)
+        self.frames = sorted({int(v.frame) for v in self.views})
+        self.params = dict(DEFAULT_SGLD)
+        if params:
+            self.params.update(params)
+        self.seed = seed
+        self.batched = batched
+        self.bg = bg
+        K = (state.sh_degree + 1) ** 2
+        self._gflat, g = _flat_views(state.n, K)
+        self.grads = api.GaussianGrads(*g, state.sh_degree)
+        self._mflat, m = _flat_views(state.n, K)
+        self._vflat, v = _flat_views(state.n, K)
+        names = ("means", "log_scales", "quats", "opacity_logits", "sh")
+        self.adam = {}
+        for k, a, b in zip(names, m, v):
+            self.adam["m_" + k] = a
+            self.adam["v_" + k] = b
+        self.images = [torch.empty((3, vw.height, vw.width), dtype=torch.float32, device="cuda")
+                       for vw in self.views]
+        self.dl = [torch.empty_like(i) for i in self.images]
+        self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+
+    def step(self, step: int, update: Optional[tuple] = None, render_only: bool = False):
+        """One training step. update = (first_slot, pinned host dict) streams a
+        slice in before rendering. Returns the (device) loss tensor."""
+        if update is not None:
+            first, host = update
+            self.r.frame_update(self.state, first, host, src_on_host=True)
+        if render_only:
+            self.r.render(self.state, self.views, bg=self.bg, batched=self.batched,
+                          out=self.images)
+            return None
+        _, saved = self.r.render(self.state, self.views, bg=self.bg, batched=self.batched,
+                                 keep_saved=True, out=self.images)
+        self.r.loss_l1(self.views, self.images, self.targets, dL_out=self.dl,
+                       loss_out=self.loss)
+        self._gflat.zero_()
+        self.r.backward(self.state, saved, self.dl, self.grads)
+        saved.release()
+        self.r.sgld_step(self.state, self.frames, self.params, self.seed, step,
+                         grads=self.grads, adam=self.adam)
+        return self.loss

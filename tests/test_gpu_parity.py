@@ -144,12 +144,14 @@ def test_config0_background_and_ragged(R, oracle_mod):
     _render_and_compare(R, oracle_mod, sc, [v2], bg=(0.2, 0.5, 0.9))
 
 
-@pytest.mark.parametrize("tile,batch", [((8, 8), 32), ((8, 8), 256), ((16, 16), 64),
-                                        ((32, 8), 128), ((32, 8), 256)])
-def test_tile_shapes_and_batches(oracle_mod, tile, batch):
-    """Every tile shape and staging batch size gives the oracle's image."""
+@pytest.mark.parametrize("tile,batch,ppt", [((8, 8), 32, 1), ((8, 8), 256, 2),
+                                            ((16, 16), 64, 1), ((16, 16), 128, 4),
+                                            ((32, 8), 128, 2), ((32, 8), 256, 4)])
+def test_tile_shapes_and_batches(oracle_mod, tile, batch, ppt):
+    """Every tile shape, staging batch size and pixels-per-thread choice gives
+    the oracle's image."""
     from paper_2409_07759_b300 import api
-    r = api.Renderer(tile=tile, batch=batch)
+    r = api.Renderer(tile=tile, batch=batch, pixels_per_thread=ppt)
     sc, views = synth.config0()
     _check_records_and_lists(r, oracle_mod, sc, views, tile=tile)
     _render_and_compare(r, oracle_mod, sc, views, tile=tile)
@@ -217,13 +219,18 @@ def _grads_vs_oracle(R, oracle_mod, sc, views, dLs, bg=(0.0, 0.0, 0.0), gpu_dLs=
     return compare_grads(gpu, ref)
 
 
-def test_backward_small_scene(R, oracle_mod):
-    """Gradients of every attribute (SH3) against the FP64 adjoint."""
+@pytest.mark.parametrize("ppt", [1, 2, 4])
+def test_backward_small_scene(oracle_mod, ppt):
+    """Gradients of every attribute (SH3) against the FP64 adjoint, for each
+    pixels-per-thread variant of the reverse blend."""
+    from paper_2409_07759_b300 import api
+    r = api.Renderer(pixels_per_thread=ppt)
     sc, view = synth.tiny_scene(3, n=200, sh_degree=3, width=96, height=72, depth=3.0,
                                 log_scale_mean=-2.2, spread=0.9)
     view.fx = view.fy = 90.0
     d = np.random.default_rng(0).normal(size=(3, 72, 96))
-    print(_grads_vs_oracle(R, oracle_mod, sc, [view], [d], bg=(0.1, 0.2, 0.3)))
+    print(_grads_vs_oracle(r, oracle_mod, sc, [view], [d], bg=(0.1, 0.2, 0.3)))
+    r.close()
 
 
 def test_backward_config1_l1(R, oracle_mod):
