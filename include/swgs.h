@@ -124,6 +124,32 @@ swgs_status swgs_active_ids(swgs_ctx *ctx, const int32_t *start, const int32_t *
                             int32_t frame, int32_t *out_ids, int32_t *out_count, void *stream);
 
 /*
+ * Allocation-free variant of swgs_active_ids, for callers that cannot let a
+ * library allocate device memory: processes whose device memory belongs to one
+ * allocator or budget (an engine's pool, a memory-capped server), where an
+ * extra cudaMalloc would break the accounting, and latency-critical threads
+ * that cannot afford cudaMalloc's device-wide synchronisation. The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * Same arguments and result as swgs_active_ids, but no context: its scratch
+ * (about 66 KB) is a fixed array compiled into the library, which every GPU
+ * that loads the library holds until the process exits. The first call on
+ * each device looks up that array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   - n must be at most SWGS_NOALLOC_MAX_SLOTS; larger n returns SWGS_EINVAL
+ *     and enqueues nothing.
+ *   - All calls on a device share the one array: calls whose work overlaps on
+ *     the GPU (different streams, not ordered by events) race and give wrong
+ *     results. Calls ordered on one stream are safe; nothing left in the
+ *     array by a previous call is read.
+ */
+#define SWGS_NOALLOC_MAX_SLOTS (1 << 24)
+swgs_status swgs_active_ids_noalloc(const int32_t *start, const int32_t *expire, int64_t n,
+                                    int32_t frame, int32_t *out_ids, int32_t *out_count,
+                                    void *stream);
+
+/*
  * Per-frame slice replacement (Alg. 2 update_thread, Alg. 1 mature rewrite):
  * overwrites slots [first, first+count) of dst with src's slots [0, count):
  * every attribute, the three lifespan arrays and frozen. src lives in pinned

@@ -28,6 +28,8 @@ EXPORT_GRAD2D = 9
 EXPORT_RECORD_2D = 10
 EXPORT_VIEW_TABLE = 11
 
+NOALLOC_MAX_SLOTS = 1 << 24   # SWGS_NOALLOC_MAX_SLOTS
+
 
 class SwgsConfig(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("batch", C.c_int32),
@@ -90,6 +92,8 @@ PROTOTYPES = [
     ("swgs_last_error", C.c_char_p, [C.c_void_p]),
     ("swgs_active_ids", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
                                   C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("swgs_active_ids_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]),
     ("swgs_frame_update", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_int64, C.c_int64,
                                     C.POINTER(SwgsGaussians), C.c_int32, C.c_void_p]),
     ("swgs_render_fwd", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_int32,
