@@ -41,7 +41,7 @@ FLOP_PER_PAIR_BWD = 62
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="swgs", choices=["swgs", "reference"])
     ap.add_argument("--plain-steps", type=int, default=3)
@@ -53,7 +53,49 @@ def parse():
     ap.add_argument("--tile", default="16x16", help="blend tile, WxH")
     ap.add_argument("--batch", type=int, default=256, help="Gaussians staged per block step")
     ap.add_argument("--ppt", type=int, default=2, help="blend pixels per thread")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--viewers", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=30.0, help="requests/s per viewer")
+    ap.add_argument("--serve-streams", type=int, default=3)
+    ap.add_argument("--hbm-budget-gb", type=float, default=24.0)
     return ap.parse_args()
+
+
+def serving_leg(args):
+    """Config 4: 300k Gaussians in 50 slices of 6,000 (swin_size 50), one
+    slice swapped per frame at 30 fps, Poisson viewers on orbits requesting the
+    current frame at 640x480 / 1280x720 / 1920x1080 (1:2:1)."""
+    import torch
+    from paper_2409_07759_b300 import api, serving, synth
+    swin, S = synth.SWIN_SIZE_SERVING, synth.SLICE_SIZE_SERVING
+    scene = synth.config4_initial(S, swin, 3)
+    st = api.GaussianState.from_scene(scene)
+    pool = [api.GaussianState.from_scene(synth.config4_slice(f, S, swin, 3)).pin_host()
+            for f in range(1, 9)]
+
+    def provider(frame):
+        h = pool[frame % len(pool)]
+        h["start"].fill_(frame)
+        h["expire"].fill_(frame + swin)
+        h["birth"].fill_(frame)
+        return h
+
+    loop = serving.ServingLoop(st, swin, fps=30.0, n_streams=args.serve_streams, max_batch=16,
+                               hbm_budget_bytes=args.hbm_budget_gb * 1e9,
+                               slice_provider=provider)
+    warm = serving.make_requests(args.viewers, args.rate, 1.0, seed=40)
+    loop.run(warm, 1.0)
+    reqs = serving.make_requests(args.viewers, args.rate, args.serve_seconds, seed=41)
+    stats = loop.run(reqs, args.serve_seconds)
+    ser = serving.serial_rates(st, reqs, loop.frame, renderer=loop.renderers[0], n=40)
+    loop.close()
+    out = stats.as_dict()
+    out.update(viewers=args.viewers, rate_hz_per_viewer=args.rate,
+               resolutions="640x480:1280x720:1920x1080 = 1:2:1", gaussians=scene.n,
+               swin_size=swin, slice_size=S, streams=args.serve_streams,
+               hbm_budget_gb=args.hbm_budget_gb, serial=ser,
+               offered_mpix_s=sum(r.width * r.height for r in reqs) / 1e6 / args.serve_seconds)
+    return out
 
 
 # ----------------------------------------------------------------- clocks --
@@ -73,7 +115,7 @@ class ClockSampler:
         try:
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -381,6 +423,10 @@ def main():
     else:
         roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None}
+
+    if not args.no_serving:
+        torch.cuda.synchronize()
+        extra["serving"] = serving_leg(args)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
