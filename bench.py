@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=10)
     ap.add_argument("--tile", default="16x16", help="blend tile, WxH")
     ap.add_argument("--batch", type=int, default=256, help="Gaussians staged per block step")
-    ap.add_argument("--ppt", type=int, default=2, help="blend pixels per thread")
+    ap.add_argument("--ppt", type=int, default=2, help="forward blend pixels per thread")
+    ap.add_argument("--bwd-ppt", type=int, default=4, help="reverse blend pixels per thread")
+    ap.add_argument("--bwd-batch", type=int, default=128, help="reverse blend staging batch")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--viewers", type=int, default=64)
     ap.add_argument("--rate", type=float, default=30.0, help="requests/s per viewer")
@@ -252,6 +254,7 @@ def main():
     tgt_dev = [t.cuda() for t in tgt_host]
     tw, th = (int(x) for x in args.tile.split("x"))
     r = api.Renderer(tile=(tw, th), batch=args.batch, pixels_per_thread=args.ppt,
+                     bwd_pixels_per_thread=args.bwd_ppt, bwd_batch=args.bwd_batch,
                      count_pairs=True)
     tr = WindowTrainer(r, state, views, tgt_dev, seed=1234 + rank)
     # the streamed slices: 6,000-slot slices of the initial state, from pinned host
@@ -447,6 +450,7 @@ def main():
                                    "slice update",
                        "mpix_per_step": mpix, "tile": args.tile, "batch": args.batch,
                        "pixels_per_thread": args.ppt,
+                       "bwd_pixels_per_thread": args.bwd_ppt, "bwd_batch": args.bwd_batch,
                        "parallelism": f"dp{world}", "l2": "flushed (256 MB write) before each step"},
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -53,7 +53,10 @@ typedef struct swgs_config {
     float near_plane;        /* camera-space z below which Gaussians are culled */
     int32_t blocks_per_sm;   /* persistent blend grid = SMs x this; 0 = auto */
     int32_t count_pairs;     /* 1: count evaluated (pixel, Gaussian) pairs */
-    int32_t pixels_per_thread; /* blend pixels per thread: 1, 2 or 4 (4 not with 8x8) */
+    int32_t pixels_per_thread; /* forward blend pixels per thread: 1, 2 or 4 (not 4 with 8x8) */
+    int32_t bwd_pixels_per_thread; /* reverse blend: 1, 2, 4 or 8 (16x16, 32x8: up to 8;
+                                      8x8: up to 2); 0 = pixels_per_thread */
+    int32_t bwd_batch;       /* reverse blend staging batch; 0 = batch */
 } swgs_config;
 
 /*
@@ -97,8 +100,8 @@ typedef struct swgs_view {
 typedef struct swgs_ctx swgs_ctx;
 typedef struct swgs_saved swgs_saved;
 
-/* Fills cfg with 16x16 tiles, batch 256, 2 pixels per thread, near plane 0.2,
- * auto grid. */
+/* Fills cfg with 16x16 tiles; forward batch 256 with 2 pixels per thread;
+ * reverse blend batch 128 with 4 pixels per thread; near plane 0.2; auto grid. */
 swgs_status swgs_default_config(swgs_config *cfg);
 
 /* Creates a context on the current CUDA device. alloc/free may be NULL. */

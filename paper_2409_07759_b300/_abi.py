@@ -34,7 +34,8 @@ NOALLOC_MAX_SLOTS = 1 << 24   # SWGS_NOALLOC_MAX_SLOTS
 class SwgsConfig(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("batch", C.c_int32),
                 ("near_plane", C.c_float), ("blocks_per_sm", C.c_int32),
-                ("count_pairs", C.c_int32), ("pixels_per_thread", C.c_int32)]
+                ("count_pairs", C.c_int32), ("pixels_per_thread", C.c_int32),
+                ("bwd_pixels_per_thread", C.c_int32), ("bwd_batch", C.c_int32)]
 
 
 class SwgsGaussians(C.Structure):

@@ -193,7 +193,8 @@ class Renderer:
     comes from torch's caching allocator through the library's callbacks."""
 
     def __init__(self, tile=(16, 16), batch=256, near_plane=0.2, blocks_per_sm=0,
-                 count_pairs=False, pixels_per_thread=2, use_torch_allocator=True):
+                 count_pairs=False, pixels_per_thread=2, bwd_pixels_per_thread=4,
+                 bwd_batch=128, use_torch_allocator=True):
         L = _abi.load()
         cfg = _abi.SwgsConfig()
         L.swgs_default_config(C.byref(cfg))
@@ -203,6 +204,8 @@ class Renderer:
         cfg.blocks_per_sm = int(blocks_per_sm)
         cfg.count_pairs = int(bool(count_pairs))
         cfg.pixels_per_thread = int(pixels_per_thread)
+        cfg.bwd_pixels_per_thread = int(bwd_pixels_per_thread)
+        cfg.bwd_batch = int(bwd_batch)
         self.cfg = cfg
         self.device = torch.cuda.current_device()
         if use_torch_allocator:

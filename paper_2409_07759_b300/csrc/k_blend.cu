@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
                 const float4 g0 = s0[j];
                 const float2 g1 = *reinterpret_cast<const float2*>(&s1[j]);
                 const float4 c = s2[j];
-                const int pos = b0 + j;
+                const int pos = b0 + j, pos1 = pos - rg.x + 1;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     float dx, dy, au;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
                     C1[p] = __fmaf_rn(c.y, w, C1[p]);
                     C2[p] = __fmaf_rn(c.z, w, C2[p]);
                     T[p] = inc ? tT : T[p];
-                    last[p] = inc ? pos - rg.x + 1 : last[p];
+                    last[p] = inc ? pos1 : last[p];
                 }
                 tdone = true;
 #pragma unroll
@@ -237,17 +237,20 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                     const float al = pair_alpha(q, g1.y, &au);
                     const bool ok = pos < last[p] && q >= kQMin && al >= kAlphaMin;
                     any |= ok;
-                    const float om = __fsub_rn(1.f, al);
-                    T[p] = ok ? __fdividef(T[p], om) : T[p];
-                    const float w = ok ? al * T[p] : 0.f;
+                    // T before this Gaussian, recovered from the T after it
+                    T[p] = ok ? __fdividef(T[p], __fsub_rn(1.f, al)) : T[p];
+                    const float a1 = ok ? al : 0.f;
+                    const float w = a1 * T[p];
                     m[6] = fmaf(w, dL0[p], m[6]);
                     m[7] = fmaf(w, dL1[p], m[7]);
                     m[8] = fmaf(w, dL2[p], m[8]);
-                    const float ga = T[p] * (dL0[p] * (c.x - B0[p]) + dL1[p] * (c.y - B1[p]) +
-                                             dL2[p] * (c.z - B2[p]));
-                    B0[p] = ok ? fmaf(al, c.x, om * B0[p]) : B0[p];
-                    B1[p] = ok ? fmaf(al, c.y, om * B1[p]) : B1[p];
-                    B2[p] = ok ? fmaf(al, c.z, om * B2[p]) : B2[p];
+                    // colour behind: B' = a c + (1 - a) B = B + a (c - B);
+                    // dL/dalpha = T sum_ch dL_ch (c_ch - B_ch)
+                    const float d0 = c.x - B0[p], d1 = c.y - B1[p], d2 = c.z - B2[p];
+                    const float ga = T[p] * fmaf(dL0[p], d0, fmaf(dL1[p], d1, dL2[p] * d2));
+                    B0[p] = fmaf(a1, d0, B0[p]);
+                    B1[p] = fmaf(a1, d1, B1[p]);
+                    B2[p] = fmaf(a1, d2, B2[p]);
                     const float gm = (ok && au <= kAlphaMax) ? -0.5f * au * ga : 0.f;
                     const float gx = gm * dx, gy = gm * dy;
                     m[0] += gm;
@@ -301,14 +304,18 @@ static cudaError_t run_bwd(const BlendArgs& a, int grid, cudaStream_t s) {
 }
 
 template <int TW, int TH, int BATCH, int PPT>
-static int occ(bool bwd) {
+static int occ_fwd() {
     int n = 0;
-    if (bwd)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_bwd_kernel<TW, TH, BATCH, PPT>,
-                                                      TW * TH / PPT, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_fwd_kernel<TW, TH, BATCH, PPT>,
-                                                      TW * TH / PPT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_fwd_kernel<TW, TH, BATCH, PPT>,
+                                                  TW * TH / PPT, 0);
+    return n < 1 ? 1 : n;
+}
+
+template <int TW, int TH, int BATCH, int PPT>
+static int occ_bwd() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_bwd_kernel<TW, TH, BATCH, PPT>,
+                                                  TW * TH / PPT, 0);
     return n < 1 ? 1 : n;
 }
 
@@ -336,6 +343,16 @@ static int occ(bool bwd) {
         }                                                                        \
     } while (0)
 
+// the reverse blend also has 8 pixels per thread (one warp per 16x16 or 32x8 tile)
+#define SWGS_TILE_DISPATCH_BWD(FN, ...)                                          \
+    do {                                                                         \
+        if (ppt == 8 && tile_w == 16 && tile_h == 16)                            \
+            SWGS_BATCH_DISPATCH(FN, 16, 16, 8, __VA_ARGS__);                     \
+        if (ppt == 8 && tile_w == 32 && tile_h == 8)                             \
+            SWGS_BATCH_DISPATCH(FN, 32, 8, 8, __VA_ARGS__);                      \
+        SWGS_TILE_DISPATCH(FN, __VA_ARGS__);                                     \
+    } while (0)
+
 cudaError_t launch_blend_fwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int ppt,
                              int grid, cudaStream_t s) {
     if (a.total_tiles <= 0) return cudaSuccess;
@@ -346,20 +363,23 @@ cudaError_t launch_blend_fwd(const BlendArgs& a, int tile_w, int tile_h, int bat
 cudaError_t launch_blend_bwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int ppt,
                              int grid, cudaStream_t s) {
     if (a.total_tiles <= 0) return cudaSuccess;
-    SWGS_TILE_DISPATCH(run_bwd, a, grid, s);
+    SWGS_TILE_DISPATCH_BWD(run_bwd, a, grid, s);
     return cudaErrorInvalidValue;
 }
 
 int blend_blocks_per_sm(int tile_w, int tile_h, int batch, int ppt, bool backward) {
-    SWGS_TILE_DISPATCH(occ, backward);
+    if (backward) SWGS_TILE_DISPATCH_BWD(occ_bwd);
+    else SWGS_TILE_DISPATCH(occ_fwd);
     return 1;
 }
 
-bool blend_config_valid(int tile_w, int tile_h, int batch, int ppt) {
+bool blend_config_valid(int tile_w, int tile_h, int batch, int ppt, bool backward) {
     if (!(batch == 32 || batch == 64 || batch == 128 || batch == 256)) return false;
-    if (tile_w == 16 && tile_h == 16) return ppt == 1 || ppt == 2 || ppt == 4;
+    if (tile_w == 16 && tile_h == 16)
+        return ppt == 1 || ppt == 2 || ppt == 4 || (backward && ppt == 8);
     if (tile_w == 8 && tile_h == 8) return ppt == 1 || ppt == 2;
-    if (tile_w == 32 && tile_h == 8) return ppt == 1 || ppt == 2 || ppt == 4;
+    if (tile_w == 32 && tile_h == 8)
+        return ppt == 1 || ppt == 2 || ppt == 4 || (backward && ppt == 8);
     return false;
 }
 

@@ -172,141 +172,150 @@ struct PreArgs {
     Records rec;
 };
 
-__global__ void __launch_bounds__(128) preprocess_kernel(PreArgs a) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.total_active) return;
-    const int gi = find_group(a.groups, a.n_groups, t);
+__device__ __forceinline__ int find_group_by_record(const GroupDev* groups, int n_groups,
+                                                    long long r) {
+    int lo = 0, hi = n_groups - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (groups[mid].rec_base <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One thread per record r = rec_base(group) + j * n_active + i (view j of the
+// group, active Gaussian i): consecutive threads write consecutive records and
+// read consecutive active ids; a Gaussian's parameters are re-read by each view
+// of its frame from L2.
+__global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_rec) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rec) return;
+    const int gi = find_group_by_record(a.groups, a.n_groups, r);
     const GroupDev G = a.groups[gi];
-    const int i = (int)(t - G.act_base);
-    const long long slot = a.ids[t];
+    const long long off = r - G.rec_base;
+    const int j = (int)(off / G.n_active), i = (int)(off - (long long)j * G.n_active);
+    const ViewDev& V = a.views[G.view_begin + j];
+    const long long slot = a.ids[G.act_base + i];
     const int K = (a.g.sh_degree + 1) * (a.g.sh_degree + 1);
 
     const float mu[3] = {a.g.means[3 * slot], a.g.means[3 * slot + 1], a.g.means[3 * slot + 2]};
-    const float ls[3] = {a.g.log_scales[3 * slot], a.g.log_scales[3 * slot + 1],
-                         a.g.log_scales[3 * slot + 2]};
-    const float4 q4 = reinterpret_cast<const float4*>(a.g.quats)[slot];
-    const float q[4] = {q4.x, q4.y, q4.z, q4.w};
-    float Sg[6];
-    km_sigma(ls, q, Sg);
-    const float opacity = 1.0f / (1.0f + __expf(-a.g.opacity_logits[slot]));
-    float sh[kMaxShCoeffs * 3];
-    const float* shp = a.g.sh + slot * (long long)(K * 3);
+    // camera transform
+    float p[3];
 #pragma unroll
-    for (int k = 0; k < kMaxShCoeffs * 3; ++k) sh[k] = k < K * 3 ? shp[k] : 0.f;
-
-    for (int j = 0; j < G.view_count; ++j) {
-        const ViewDev& V = a.views[G.view_begin + j];
-        const long long r = (long long)G.rec_base + (long long)j * G.n_active + i;
-        // camera transform
-        float p[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            float s0 = kmul(V.R[3 * k + 0], mu[0]);
-            float s1 = kmul(V.R[3 * k + 1], mu[1]);
-            float s2 = kmul(V.R[3 * k + 2], mu[2]);
-            p[k] = kadd(kadd(kadd(s0, s1), s2), V.t[k]);
-        }
-        const float z = p[2];
-        int tiles = 0;
-        short4 rect = make_short4(0, -1, 0, -1);
-        float u = 0.f, v = 0.f, A = 0.f, B = 0.f, C = 0.f;
-        bool culled = !(z > a.near_plane);
-        if (!culled) {
-            const float tanx = kdiv(kmul(0.5f, (float)V.W), V.fx);
-            const float tany = kdiv(kmul(0.5f, (float)V.H), V.fy);
-            const float limx = kmul(kGuard, tanx), limy = kmul(kGuard, tany);
-            const float xz = kdiv(p[0], z), yz = kdiv(p[1], z);
-            const float xzc = xz < -limx ? -limx : (xz > limx ? limx : xz);
-            const float yzc = yz < -limy ? -limy : (yz > limy ? limy : yz);
-            const float tx = kmul(xzc, z), ty = kmul(yzc, z);
-            const float zz = kmul(z, z);
-            const float J00 = kdiv(V.fx, z), J11 = kdiv(V.fy, z);
-            const float J02 = -kdiv(kmul(V.fx, tx), zz);
-            const float J12 = -kdiv(kmul(V.fy, ty), zz);
-            float T0[3], T1[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                T0[c] = kadd(kmul(J00, V.R[c]), kmul(J02, V.R[6 + c]));
-                T1[c] = kadd(kmul(J11, V.R[3 + c]), kmul(J12, V.R[6 + c]));
-            }
-            float U0[3], U1[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                U0[c] = kadd(kadd(kmul(T0[0], sg_at(Sg, 0, c)), kmul(T0[1], sg_at(Sg, 1, c))),
-                             kmul(T0[2], sg_at(Sg, 2, c)));
-                U1[c] = kadd(kadd(kmul(T1[0], sg_at(Sg, 0, c)), kmul(T1[1], sg_at(Sg, 1, c))),
-                             kmul(T1[2], sg_at(Sg, 2, c)));
-            }
-            const float c00 = kadd(kadd(kmul(U0[0], T0[0]), kmul(U0[1], T0[1])), kmul(U0[2], T0[2]));
-            const float c01 = kadd(kadd(kmul(U0[0], T1[0]), kmul(U0[1], T1[1])), kmul(U0[2], T1[2]));
-            const float c11 = kadd(kadd(kmul(U1[0], T1[0]), kmul(U1[1], T1[1])), kmul(U1[2], T1[2]));
-            const float ca = kadd(c00, kDilation), cb = c01, cc = kadd(c11, kDilation);
-            const float det = ksub(kmul(ca, cc), kmul(cb, cb));
-            if (!(det > 0.0f)) {
-                culled = true;
-            } else {
-                const float mid = kmul(0.5f, kadd(ca, cc));
-                float disc = ksub(kmul(mid, mid), det);
-                disc = disc < 0.1f ? 0.1f : disc;
-                const float l1 = kadd(mid, ksqrt(disc));
-                const float rad = ceilf(kmul(3.0f, ksqrt(l1)));
-                u = kadd(kmul(V.fx, xz), V.cx);
-                v = kadd(kmul(V.fy, yz), V.cy);
-                A = kdiv(cc, det);
-                B = -kdiv(cb, det);
-                C = kdiv(ca, det);
-                const float fxlo = floorf(kdiv(ksub(u, rad), (float)a.tile_w));
-                const float fxhi = floorf(kdiv(kadd(u, rad), (float)a.tile_w));
-                const float fylo = floorf(kdiv(ksub(v, rad), (float)a.tile_h));
-                const float fyhi = floorf(kdiv(kadd(v, rad), (float)a.tile_h));
-                const int ntx = V.ntx, nty = V.nty;
-                const int x0 = fxlo < 0.0f ? 0 : (fxlo > (float)ntx ? ntx : (int)fxlo);
-                const int x1 = fxhi > (float)(ntx - 1) ? ntx - 1 : (fxhi < -1.0f ? -1 : (int)fxhi);
-                const int y0 = fylo < 0.0f ? 0 : (fylo > (float)nty ? nty : (int)fylo);
-                const int y1 = fyhi > (float)(nty - 1) ? nty - 1 : (fyhi < -1.0f ? -1 : (int)fyhi);
-                // tiles of the bounding rectangle the 3-sigma ellipse reaches
-                if (x1 >= x0) {
-                    const KmEllipse el = km_ellipse(A, B, C);
-                    for (int ty = y0; ty <= y1; ++ty) {
-                        int f, l;
-                        tiles += km_row_run(el, u, v, x0, x1, ty, a.tile_w, a.tile_h, &f, &l);
-                    }
-                }
-                rect = make_short4((short)x0, (short)x1, (short)y0, (short)y1);
-            }
-        }
-        // view-dependent colour (Sec. 8.1)
-        float dx = mu[0] - V.campos[0], dy = mu[1] - V.campos[1], dz = mu[2] - V.campos[2];
-        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-        dx *= inv; dy *= inv; dz *= inv;
-        float Y[kMaxShCoeffs];
-        sh_basis(K, dx, dy, dz, Y);
-        float col[3];
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < kMaxShCoeffs; ++k)
-                if (k < K) acc = fmaf(Y[k], sh[3 * k + ch], acc);
-            col[ch] = fmaxf(acc + 0.5f, 0.0f);
-        }
-        a.rec.a[r] = make_float4(u, v, opacity, z);
-        a.rec.b[r] = make_float4(A, B, C, 0.f);
-        a.rec.c[r] = make_float4(col[0], col[1], col[2], 0.f);
-        a.rec.tiles[r] = culled ? 0 : tiles;
-        a.rec.rect[r] = rect;
-        a.rec.depth_key[r] = (culled || tiles == 0) ? 0xffffffffu : __float_as_uint(z);
+    for (int k = 0; k < 3; ++k) {
+        float s0 = kmul(V.R[3 * k + 0], mu[0]);
+        float s1 = kmul(V.R[3 * k + 1], mu[1]);
+        float s2 = kmul(V.R[3 * k + 2], mu[2]);
+        p[k] = kadd(kadd(kadd(s0, s1), s2), V.t[k]);
     }
+    const float z = p[2];
+    int tiles = 0;
+    short4 rect = make_short4(0, -1, 0, -1);
+    float u = 0.f, v = 0.f, A = 0.f, B = 0.f, C = 0.f;
+    bool culled = !(z > a.near_plane);
+    if (!culled) {
+        const float ls[3] = {a.g.log_scales[3 * slot], a.g.log_scales[3 * slot + 1],
+                             a.g.log_scales[3 * slot + 2]};
+        const float4 q4 = reinterpret_cast<const float4*>(a.g.quats)[slot];
+        const float q[4] = {q4.x, q4.y, q4.z, q4.w};
+        float Sg[6];
+        km_sigma(ls, q, Sg);
+        const float tanx = kdiv(kmul(0.5f, (float)V.W), V.fx);
+        const float tany = kdiv(kmul(0.5f, (float)V.H), V.fy);
+        const float limx = kmul(kGuard, tanx), limy = kmul(kGuard, tany);
+        const float xz = kdiv(p[0], z), yz = kdiv(p[1], z);
+        const float xzc = xz < -limx ? -limx : (xz > limx ? limx : xz);
+        const float yzc = yz < -limy ? -limy : (yz > limy ? limy : yz);
+        const float tx = kmul(xzc, z), ty = kmul(yzc, z);
+        const float zz = kmul(z, z);
+        const float J00 = kdiv(V.fx, z), J11 = kdiv(V.fy, z);
+        const float J02 = -kdiv(kmul(V.fx, tx), zz);
+        const float J12 = -kdiv(kmul(V.fy, ty), zz);
+        float T0[3], T1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T0[c] = kadd(kmul(J00, V.R[c]), kmul(J02, V.R[6 + c]));
+            T1[c] = kadd(kmul(J11, V.R[3 + c]), kmul(J12, V.R[6 + c]));
+        }
+        float U0[3], U1[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            U0[c] = kadd(kadd(kmul(T0[0], sg_at(Sg, 0, c)), kmul(T0[1], sg_at(Sg, 1, c))),
+                         kmul(T0[2], sg_at(Sg, 2, c)));
+            U1[c] = kadd(kadd(kmul(T1[0], sg_at(Sg, 0, c)), kmul(T1[1], sg_at(Sg, 1, c))),
+                         kmul(T1[2], sg_at(Sg, 2, c)));
+        }
+        const float c00 = kadd(kadd(kmul(U0[0], T0[0]), kmul(U0[1], T0[1])), kmul(U0[2], T0[2]));
+        const float c01 = kadd(kadd(kmul(U0[0], T1[0]), kmul(U0[1], T1[1])), kmul(U0[2], T1[2]));
+        const float c11 = kadd(kadd(kmul(U1[0], T1[0]), kmul(U1[1], T1[1])), kmul(U1[2], T1[2]));
+        const float ca = kadd(c00, kDilation), cb = c01, cc = kadd(c11, kDilation);
+        const float det = ksub(kmul(ca, cc), kmul(cb, cb));
+        if (!(det > 0.0f)) {
+            culled = true;
+        } else {
+            const float mid = kmul(0.5f, kadd(ca, cc));
+            float disc = ksub(kmul(mid, mid), det);
+            disc = disc < 0.1f ? 0.1f : disc;
+            const float l1 = kadd(mid, ksqrt(disc));
+            const float rad = ceilf(kmul(3.0f, ksqrt(l1)));
+            u = kadd(kmul(V.fx, xz), V.cx);
+            v = kadd(kmul(V.fy, yz), V.cy);
+            A = kdiv(cc, det);
+            B = -kdiv(cb, det);
+            C = kdiv(ca, det);
+            const float fxlo = floorf(kdiv(ksub(u, rad), (float)a.tile_w));
+            const float fxhi = floorf(kdiv(kadd(u, rad), (float)a.tile_w));
+            const float fylo = floorf(kdiv(ksub(v, rad), (float)a.tile_h));
+            const float fyhi = floorf(kdiv(kadd(v, rad), (float)a.tile_h));
+            const int ntx = V.ntx, nty = V.nty;
+            const int x0 = fxlo < 0.0f ? 0 : (fxlo > (float)ntx ? ntx : (int)fxlo);
+            const int x1 = fxhi > (float)(ntx - 1) ? ntx - 1 : (fxhi < -1.0f ? -1 : (int)fxhi);
+            const int y0 = fylo < 0.0f ? 0 : (fylo > (float)nty ? nty : (int)fylo);
+            const int y1 = fyhi > (float)(nty - 1) ? nty - 1 : (fyhi < -1.0f ? -1 : (int)fyhi);
+            // tiles of the bounding rectangle the 3-sigma ellipse reaches
+            if (x1 >= x0) {
+                const KmEllipse el = km_ellipse(A, B, C);
+                for (int ty = y0; ty <= y1; ++ty) {
+                    int f, l;
+                    tiles += km_row_run(el, u, v, x0, x1, ty, a.tile_w, a.tile_h, &f, &l);
+                }
+            }
+            rect = make_short4((short)x0, (short)x1, (short)y0, (short)y1);
+        }
+    }
+    const float opacity = 1.0f / (1.0f + __expf(-a.g.opacity_logits[slot]));
+    // view-dependent colour (Sec. 8.1)
+    float dx = mu[0] - V.campos[0], dy = mu[1] - V.campos[1], dz = mu[2] - V.campos[2];
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    dx *= inv; dy *= inv; dz *= inv;
+    float Y[kMaxShCoeffs];
+    sh_basis(K, dx, dy, dz, Y);
+    const float* shp = a.g.sh + slot * (long long)(K * 3);
+    float col0 = 0.f, col1 = 0.f, col2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxShCoeffs; ++k) {
+        if (k < K) {
+            col0 = fmaf(Y[k], shp[3 * k + 0], col0);
+            col1 = fmaf(Y[k], shp[3 * k + 1], col1);
+            col2 = fmaf(Y[k], shp[3 * k + 2], col2);
+        }
+    }
+    a.rec.a[r] = make_float4(u, v, opacity, z);
+    a.rec.b[r] = make_float4(A, B, C, 0.f);
+    a.rec.c[r] = make_float4(fmaxf(col0 + 0.5f, 0.f), fmaxf(col1 + 0.5f, 0.f),
+                             fmaxf(col2 + 0.5f, 0.f), 0.f);
+    a.rec.tiles[r] = culled ? 0 : tiles;
+    a.rec.rect[r] = rect;
+    a.rec.depth_key[r] = (culled || tiles == 0) ? 0xffffffffu : __float_as_uint(z);
 }
 
 cudaError_t launch_preprocess(const swgs_gaussians& g, const ViewDev* views, const GroupDev* groups,
                               int n_groups, const int32_t* ids, long long total_active,
-                              int tile_w, int tile_h, float near_plane, Records rec,
-                              cudaStream_t s) {
-    if (total_active <= 0) return cudaSuccess;
+                              long long n_rec, int tile_w, int tile_h, float near_plane,
+                              Records rec, cudaStream_t s) {
+    if (n_rec <= 0) return cudaSuccess;
     PreArgs a{g, views, groups, n_groups, ids, total_active, tile_w, tile_h, near_plane, rec};
     note_launch();
-    preprocess_kernel<<<div_up(total_active, 128), 128, 0, s>>>(a);
+    preprocess_kernel<<<div_up(n_rec, 256), 256, 0, s>>>(a, n_rec);
     return cudaGetLastError();
 }
 

@@ -1,17 +1,19 @@
 // k_sort.cu -- stable LSD radix sort of (uint32 key, uint32 value) pairs.
 //
-// Each pass (<= 8 bits): an upsweep histogram per block over a contiguous
-// share of 4096-key tiles, an exclusive scan of the (digit, block) counts in
-// digit-major order, and a downsweep that ranks each tile stably (warp
-// match.any ranking, warps in order), stages the tile in shared memory in
-// digit order and writes it out, so global writes are contiguous within each
-// digit run. The grid is a fixed multiple of the SM count; block b owns the
-// same tile range in both kernels, so no waits between blocks are needed.
+// Each pass (<= 9 bits, up to 512 buckets): an upsweep histogram per block
+// over a contiguous share of 4096-key tiles, an exclusive scan of the
+// (digit, block) counts in digit-major order, and a downsweep that ranks each
+// tile stably (warp match.any ranking, warps in order), stages it in shared
+// memory in digit order and writes it out, so global writes are contiguous
+// within each digit run. Keys and ranks are the only per-item registers; the
+// values are loaded after the keys have been placed. The grid is a fixed
+// multiple of the SM count and block b owns the same tile range in both
+// kernels, so no block ever waits for another.
 //
-// Used twice per render: the per-record depth sort (32 bits) and the
-// per-key tile sort (ceil(log2(tiles)) bits). Sorting records by depth and
-// then keys stably by tile gives the order of a stable sort on
-// (tile << 32 | depth), the per-tile depth ordering of Eq. 3.
+// Used twice per render: the per-record depth sort (32 bits, 4 passes) and the
+// per-key tile sort (ceil(log2(tiles)) bits, 2 passes up to 18 bits). Sorting
+// records by depth and then keys stably by tile gives the order of a stable
+// sort on (tile << 32 | depth), the per-tile depth ordering of Eq. 3.
 #include "swgs_internal.cuh"
 
 namespace swgs {
@@ -21,13 +23,15 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096
 constexpr int kWarpSpan = 32 * kSortItems;             // 512 keys per warp
-constexpr int kMaxBins = 256;
+constexpr int kMaxDigitBits = 9;
+constexpr int kMaxBins = 1 << kMaxDigitBits;           // 512
+constexpr int kBinsPerThread = kMaxBins / kSortThreads;  // 2
 
 SortPlan make_sort_plan(int begin_bit, int end_bit) {
     SortPlan p{};
     int total = end_bit - begin_bit;
     if (total <= 0) { p.passes = 0; p.begin_bit = begin_bit; return p; }
-    p.passes = (total + 7) / 8;
+    p.passes = (total + kMaxDigitBits - 1) / kMaxDigitBits;
     int base = total / p.passes, extra = total % p.passes;
     for (int i = 0; i < p.passes; ++i) p.bits_per_pass[i] = base + (i < extra ? 1 : 0);
     p.begin_bit = begin_bit;
@@ -36,7 +40,7 @@ SortPlan make_sort_plan(int begin_bit, int end_bit) {
 
 static int sort_grid(long long n, int num_sms) {
     long long tiles = (n + kSortTile - 1) / kSortTile;
-    long long g = (long long)num_sms * 2;
+    long long g = (long long)num_sms * 4;
     if (tiles < g) g = tiles;
     return (int)(g < 1 ? 1 : g);
 }
@@ -65,10 +69,21 @@ radix_upsweep(const uint32_t* __restrict__ keys, long long n, int shift, int bin
     if (t1 > n_tiles) t1 = n_tiles;
     for (long long t = t0; t < t1; ++t) {
         const long long base = t * kSortTile;
-#pragma unroll 4
-        for (int it = 0; it < kSortItems; ++it) {
-            long long i = base + (long long)it * kSortThreads + threadIdx.x;
-            if (i < n) atomicAdd(&h[warp][(keys[i] >> shift) & mask], 1u);
+        if (base + kSortTile <= n) {
+            const uint4* k4 = reinterpret_cast<const uint4*>(keys + base);
+#pragma unroll
+            for (int it = 0; it < kSortItems / 4; ++it) {
+                const uint4 q = k4[it * kSortThreads + threadIdx.x];
+                atomicAdd(&h[warp][(q.x >> shift) & mask], 1u);
+                atomicAdd(&h[warp][(q.y >> shift) & mask], 1u);
+                atomicAdd(&h[warp][(q.z >> shift) & mask], 1u);
+                atomicAdd(&h[warp][(q.w >> shift) & mask], 1u);
+            }
+        } else {
+            for (int it = 0; it < kSortItems; ++it) {
+                long long i = base + (long long)it * kSortThreads + threadIdx.x;
+                if (i < n) atomicAdd(&h[warp][(keys[i] >> shift) & mask], 1u);
+            }
         }
     }
     __syncthreads();
@@ -90,7 +105,7 @@ struct DownSmem {
     uint32_t warp_tot[kSortWarps];
 };
 
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 4)
 radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, long long n,
                 int shift, int bins, int tiles_per_block, long long n_tiles,
@@ -111,27 +126,23 @@ radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
         for (int i = threadIdx.x; i < kSortWarps * (kMaxBins + 1); i += kSortThreads)
             (&S.whist[0][0])[i] = 0;
         __syncthreads();
-        uint32_t k[kSortItems], v[kSortItems], dg[kSortItems], rk[kSortItems];
+        uint32_t k[kSortItems], rk[kSortItems];
 #pragma unroll
         for (int it = 0; it < kSortItems; ++it) {
             const int local = warp * kWarpSpan + it * 32 + lane;
-            const long long i = base + local;
-            if (local < valid) {
-                k[it] = keys_in[i];
-                v[it] = vals_in ? vals_in[i] : (uint32_t)i;
-                dg[it] = (k[it] >> shift) & mask;
-            } else {
-                k[it] = 0; v[it] = 0; dg[it] = (uint32_t)bins;  // sentinel bucket
-            }
+            k[it] = local < valid ? keys_in[base + local] : 0xffffffffu;
         }
+        // rank each item among equal digits of its warp, in (item, lane) order
 #pragma unroll
         for (int it = 0; it < kSortItems; ++it) {
-            const unsigned peers = __match_any_sync(0xffffffffu, dg[it]);
+            const int local = warp * kWarpSpan + it * 32 + lane;
+            const uint32_t d = local < valid ? (k[it] >> shift) & mask : (uint32_t)bins;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
             const int leader = __ffs(peers) - 1;
             uint32_t b = 0;
             if (lane == leader) {
-                b = S.whist[warp][dg[it]];
-                S.whist[warp][dg[it]] = b + (uint32_t)__popc(peers);
+                b = S.whist[warp][d];
+                S.whist[warp][d] = b + (uint32_t)__popc(peers);
             }
             b = __shfl_sync(0xffffffffu, b, leader);
             rk[it] = b + (uint32_t)__popc(peers & lt_mask);
@@ -142,38 +153,57 @@ radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
             uint32_t run = 0;
 #pragma unroll
             for (int w = 0; w < kSortWarps; ++w) {
-                uint32_t c = S.whist[w][d];
+                const uint32_t c = S.whist[w][d];
                 S.whist[w][d] = run;
                 run += c;
             }
             S.cnt[d] = run;
         }
         __syncthreads();
-        // exclusive scan of the digit counts (bins <= 256 = one per thread)
+        // exclusive scan of the digit counts: two consecutive digits per thread
         {
-            uint32_t c = threadIdx.x < bins ? S.cnt[threadIdx.x] : 0u;
-            uint32_t incl = c;
+            const int d0 = threadIdx.x * kBinsPerThread;
+            uint32_t c[kBinsPerThread], sum = 0;
+#pragma unroll
+            for (int e = 0; e < kBinsPerThread; ++e) {
+                c[e] = d0 + e < bins ? S.cnt[d0 + e] : 0u;
+                sum += c[e];
+            }
+            uint32_t incl = sum;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
             if (lane == 31) S.warp_tot[warp] = incl;
             __syncthreads();
-            uint32_t wpre = 0;
+            uint32_t run = incl - sum;
 #pragma unroll
-            for (int w = 0; w < kSortWarps; ++w) wpre += (w < warp) ? S.warp_tot[w] : 0u;
-            if (threadIdx.x < bins) S.digoff[threadIdx.x] = wpre + incl - c;
+            for (int w = 0; w < kSortWarps; ++w) run += (w < warp) ? S.warp_tot[w] : 0u;
+#pragma unroll
+            for (int e = 0; e < kBinsPerThread; ++e) {
+                if (d0 + e < bins) S.digoff[d0 + e] = run;
+                run += c[e];
+            }
             if (threadIdx.x == 0) S.digoff[bins] = (uint32_t)valid;
         }
         __syncthreads();
+        // place the keys; rk becomes the tile-local position
 #pragma unroll
         for (int it = 0; it < kSortItems; ++it) {
-            if (dg[it] < (uint32_t)bins) {
-                const uint32_t pos = S.digoff[dg[it]] + S.whist[warp][dg[it]] + rk[it];
-                S.keys[pos] = k[it];
-                S.vals[pos] = v[it];
+            const int local = warp * kWarpSpan + it * 32 + lane;
+            if (local < valid) {
+                const uint32_t d = (k[it] >> shift) & mask;
+                rk[it] += S.digoff[d] + S.whist[warp][d];
+                S.keys[rk[it]] = k[it];
             }
+        }
+        // then the values, read with the same coalesced pattern
+#pragma unroll
+        for (int it = 0; it < kSortItems; ++it) {
+            const int local = warp * kWarpSpan + it * 32 + lane;
+            if (local < valid)
+                S.vals[rk[it]] = vals_in ? vals_in[base + local] : (uint32_t)(base + local);
         }
         __syncthreads();
         for (int i = threadIdx.x; i < valid; i += kSortThreads) {

@@ -350,7 +350,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
     {
         StageScope sc_(ctx, SWGS_STAGE_PREPROCESS, s);
         CK(launch_preprocess(*g, P<ViewDev>(B.views), P<GroupDev>(B.groups), F, P<int32_t>(B.ids),
-                             act, tw, th, ctx->cfg.near_plane, rc, s));
+                             act, rec, tw, th, ctx->cfg.near_plane, rc, s));
     }
     // 3. depth order of the records and their key offsets
     long long n_keys = 0;
@@ -476,17 +476,18 @@ swgs_status backward_batch(swgs_ctx* ctx, const swgs_gaussians* g, BatchState& B
     ba.work_counter = P<int>(ctx->counter);
     ba.pairs = nullptr;
     ba.grad2d = P<float>(B.grad2d);
-    const int ppt = ctx->cfg.pixels_per_thread;
+    const int ppt = ctx->cfg.bwd_pixels_per_thread;
+    const int bbatch = ctx->cfg.bwd_batch;
     int bps = ctx->cfg.blocks_per_sm > 0
                   ? ctx->cfg.blocks_per_sm
-                  : blend_blocks_per_sm(tw, th, ctx->cfg.batch, ppt, true);
+                  : blend_blocks_per_sm(tw, th, bbatch, ppt, true);
     long long grid = (long long)ctx->num_sms * bps;
     if (grid > B.n_tiles) grid = B.n_tiles;
     if (grid < 1) grid = 1;
     CK(cudaMemsetAsync(ctx->counter.p, 0, sizeof(int), s));
     {
         StageScope sc_(ctx, SWGS_STAGE_BLEND_BWD, s);
-        CK(launch_blend_bwd(ba, tw, th, ctx->cfg.batch, ppt, (int)grid, s));
+        CK(launch_blend_bwd(ba, tw, th, bbatch, ppt, (int)grid, s));
     }
     {
         StageScope sc_(ctx, SWGS_STAGE_PREPROCESS_BWD, s);
@@ -562,6 +563,8 @@ swgs_status swgs_default_config(swgs_config* cfg) {
     cfg->blocks_per_sm = 0;
     cfg->count_pairs = 0;
     cfg->pixels_per_thread = 2;
+    cfg->bwd_pixels_per_thread = 4;
+    cfg->bwd_batch = 128;
     return SWGS_OK;
 }
 
@@ -571,8 +574,12 @@ swgs_status swgs_create(const swgs_config* cfg, swgs_alloc_fn alloc, swgs_free_f
     *out = nullptr;
     swgs_config c{};
     if (cfg) c = *cfg; else swgs_default_config(&c);
+    if (c.bwd_pixels_per_thread == 0) c.bwd_pixels_per_thread = c.pixels_per_thread;
+    if (c.bwd_batch == 0) c.bwd_batch = c.batch;
     if (!valid_tile(c.tile_w, c.tile_h) || !valid_batch(c.batch) || !(c.near_plane > 0.f) ||
-        c.blocks_per_sm < 0 || !blend_config_valid(c.tile_w, c.tile_h, c.batch, c.pixels_per_thread))
+        c.blocks_per_sm < 0 ||
+        !blend_config_valid(c.tile_w, c.tile_h, c.batch, c.pixels_per_thread, false) ||
+        !blend_config_valid(c.tile_w, c.tile_h, c.bwd_batch, c.bwd_pixels_per_thread, true))
         return SWGS_EINVAL;
     if ((alloc == nullptr) != (free_fn == nullptr)) return SWGS_EINVAL;
     swgs_ctx* ctx = new swgs_ctx();

@@ -329,8 +329,8 @@ cudaError_t inclusive_scan_u64(const unsigned long long* in, unsigned long long*
 // k_preprocess.cu
 cudaError_t launch_preprocess(const swgs_gaussians& g, const ViewDev* views, const GroupDev* groups,
                               int n_groups, const int32_t* ids, long long total_active,
-                              int tile_w, int tile_h, float near_plane, Records rec,
-                              cudaStream_t s);
+                              long long n_rec, int tile_w, int tile_h, float near_plane,
+                              Records rec, cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const swgs_gaussians& g, const swgs_gaussians& grads,
                                   const ViewDev* views, const GroupDev* groups, int n_groups,
                                   const int32_t* ids, long long total_active,
@@ -380,7 +380,7 @@ cudaError_t launch_blend_fwd(const BlendArgs& a, int tile_w, int tile_h, int bat
 cudaError_t launch_blend_bwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int ppt,
                              int grid, cudaStream_t s);
 int blend_blocks_per_sm(int tile_w, int tile_h, int batch, int ppt, bool backward);
-bool blend_config_valid(int tile_w, int tile_h, int batch, int ppt);
+bool blend_config_valid(int tile_w, int tile_h, int batch, int ppt, bool backward);
 
 // k_misc.cu
 cudaError_t launch_loss_l1(const ViewDev* views, int n_views, long long total_pix,

@@ -151,7 +151,8 @@ def test_tile_shapes_and_batches(oracle_mod, tile, batch, ppt):
     """Every tile shape, staging batch size and pixels-per-thread choice gives
     the oracle's image."""
     from paper_2409_07759_b300 import api
-    r = api.Renderer(tile=tile, batch=batch, pixels_per_thread=ppt)
+    r = api.Renderer(tile=tile, batch=batch, pixels_per_thread=ppt,
+                     bwd_pixels_per_thread=ppt, bwd_batch=batch)
     sc, views = synth.config0()
     _check_records_and_lists(r, oracle_mod, sc, views, tile=tile)
     _render_and_compare(r, oracle_mod, sc, views, tile=tile)
@@ -219,12 +220,13 @@ def _grads_vs_oracle(R, oracle_mod, sc, views, dLs, bg=(0.0, 0.0, 0.0), gpu_dLs=
     return compare_grads(gpu, ref)
 
 
-@pytest.mark.parametrize("ppt", [1, 2, 4])
-def test_backward_small_scene(oracle_mod, ppt):
+@pytest.mark.parametrize("ppt,tile", [(1, (16, 16)), (2, (16, 16)), (4, (16, 16)),
+                                      (8, (16, 16)), (8, (32, 8)), (2, (8, 8))])
+def test_backward_small_scene(oracle_mod, ppt, tile):
     """Gradients of every attribute (SH3) against the FP64 adjoint, for each
     pixels-per-thread variant of the reverse blend."""
     from paper_2409_07759_b300 import api
-    r = api.Renderer(pixels_per_thread=ppt)
+    r = api.Renderer(tile=tile, bwd_pixels_per_thread=ppt, pixels_per_thread=min(ppt, 2))
     sc, view = synth.tiny_scene(3, n=200, sh_degree=3, width=96, height=72, depth=3.0,
                                 log_scale_mean=-2.2, spread=0.9)
     view.fx = view.fy = 90.0
