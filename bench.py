@@ -33,9 +33,10 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 FP32_LANES_PER_SM = 128          # FP32 lanes per SM (4 partitions x 32)
-# Algorithmic FP32 operations per evaluated (pixel, Gaussian) pair, FMA = 2.
-FLOP_PER_PAIR_FWD = 21
-FLOP_PER_PAIR_BWD = 62
+# Algorithmic FP32 operations per evaluated (pixel, Gaussian) pair, FMA = 2
+# (the per-pair operation counts are itemised in the design notes).
+FLOP_PER_PAIR_FWD = 23
+FLOP_PER_PAIR_BWD = 64
 
 
 def parse():
@@ -393,7 +394,7 @@ def main():
     clk = (clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0))
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     tile_passes = math.ceil(math.ceil(math.log2(max(2, sum(
-        ((v.width + tw - 1) // tw) * ((v.height + th - 1) // th) for v in views)))) / 8)
+        ((v.width + tw - 1) // tw) * ((v.height + th - 1) // th) for v in views)))) / 9)
     stage_cost = {
         "blend_fwd": ("alu", FLOP_PER_PAIR_FWD * pairs_fwd / 1e12, "TFLOP/s"),
         "blend_bwd": ("alu", FLOP_PER_PAIR_BWD * pairs_bwd / 1e12, "TFLOP/s"),
