@@ -33,8 +33,11 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 FP32_LANES_PER_SM = 128          # FP32 lanes per SM (4 partitions x 32)
-# Algorithmic FP32 operations per evaluated (pixel, Gaussian) pair, FMA = 2
-# (the per-pair operation counts are itemised in the design notes).
+# Algorithmic FP32 operations per evaluated (pixel, Gaussian) pair, FMA = 2.
+# Forward (Eq. 3): offset d 2, Mahalanobis form m 9, G = exp(-m/2) 2, o*G 1,
+# T(1 - alpha) 2, colour accumulation c*alpha*T 7.
+# Backward: the forward's alpha 14, T recovery 2, colour weights 4, dL/dalpha 9,
+# colour-behind update 9, dalpha/dm 2, conic/centre/opacity terms 15, sums 9.
 FLOP_PER_PAIR_FWD = 23
 FLOP_PER_PAIR_BWD = 64
 
