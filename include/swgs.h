@@ -185,6 +185,19 @@ swgs_status swgs_render_fwd(swgs_ctx *ctx, const swgs_gaussians *g, int32_t n_vi
                             void *stream);
 
 /*
+ * swgs_render_fwd fused with the L1 term of Alg. 1 loss_func (same as
+ * swgs_loss_l1 on the rendered images, without a separate pass over them):
+ * besides out_rgb it reads target[v] (device float[3*H*W]), writes
+ * dL_drgb[v] = sign(rgb - target)/(3*H*W*V) and overwrites *loss (device
+ * float) with the mean over views of mean |rgb - target|.
+ */
+swgs_status swgs_render_fwd_l1(swgs_ctx *ctx, const swgs_gaussians *g, int32_t n_views,
+                               const swgs_view *views, const float *bg, float *const *out_rgb,
+                               float *const *out_T, const float *const *target,
+                               float *const *dL_drgb, float *loss, int32_t batched,
+                               swgs_saved **saved, void *stream);
+
+/*
  * Backward of swgs_render_fwd (Alg. 1 loss.backward): given dL/drgb[v]
  * (device float[3*H*W] planar, same views as the saved forward), ACCUMULATES
  * into grads (device arrays with g's layout: means, log_scales, quats,

@@ -295,6 +295,29 @@ class Renderer:
         saved = SavedState(self, handle, cviews) if keep_saved else None
         return out, saved
 
+    def render_l1(self, state: GaussianState, views: Sequence, targets, bg=(0.0, 0.0, 0.0),
+                  batched=True, keep_saved=True, out=None, dL_out=None, loss_out=None,
+                  stream=None):
+        """Forward render fused with the L1 term: returns (images, dL/drgb, loss,
+        saved)."""
+        cviews = _views_array(views)
+        if out is None:
+            out = [torch.empty((3, v.height, v.width), dtype=torch.float32, device="cuda")
+                   for v in cviews]
+        if dL_out is None:
+            dL_out = [torch.empty_like(o) for o in out]
+        if loss_out is None:
+            loss_out = torch.zeros(1, dtype=torch.float32, device="cuda")
+        bgv = (C.c_float * 3)(*[float(x) for x in bg])
+        handle = C.c_void_p()
+        g = state.c_struct()
+        self._check(_abi.load().swgs_render_fwd_l1(
+            self.ctx, C.byref(g), len(cviews), cviews, bgv, _ptr_array(out), None,
+            _ptr_array(targets), _ptr_array(dL_out), _ptr(loss_out), int(bool(batched)),
+            C.byref(handle) if keep_saved else None, self._stream(stream)))
+        saved = SavedState(self, handle, cviews) if keep_saved else None
+        return out, dL_out, loss_out, saved
+
     def backward(self, state: GaussianState, saved: SavedState, dL_drgb, grads: GaussianGrads,
                  stream=None):
         for t in dL_drgb:

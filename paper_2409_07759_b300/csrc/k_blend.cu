@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
     const int tid = threadIdx.x;
     const int lx = tid % TW, ly = (tid / TW) * PPT;
     unsigned long long pairs = 0;
+    float l1 = 0.f;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(a.work_counter, 1);
         __syncthreads();
@@ -115,16 +116,34 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
             const int y = y0 + p;
             if (x < W && y < H) {
                 const long long hw = (long long)W * H, q = (long long)y * W + x;
-                V.out_rgb[q] = C0[p] + T[p] * V.bg[0];
-                V.out_rgb[hw + q] = C1[p] + T[p] * V.bg[1];
-                V.out_rgb[2 * hw + q] = C2[p] + T[p] * V.bg[2];
+                const float r0 = C0[p] + T[p] * V.bg[0];
+                const float r1 = C1[p] + T[p] * V.bg[1];
+                const float r2 = C2[p] + T[p] * V.bg[2];
+                V.out_rgb[q] = r0;
+                V.out_rgb[hw + q] = r1;
+                V.out_rgb[2 * hw + q] = r2;
                 if (V.out_T) V.out_T[q] = T[p];
                 if (a.T) a.T[V.pix_base + q] = T[p];
                 if (a.last) a.last[V.pix_base + q] = last[p];
                 pairs += (unsigned long long)((stop[p] < rg.y ? stop[p] + 1 : rg.y) - rg.x);
+                if (V.target) {
+                    // L1 term of the loss and its gradient, sign(0) = 0
+                    const float e0 = r0 - V.target[q], e1 = r1 - V.target[hw + q],
+                                e2 = r2 - V.target[2 * hw + q];
+                    const float s = V.l1_scale;
+                    V.dL_out[q] = e0 > 0.f ? s : (e0 < 0.f ? -s : 0.f);
+                    V.dL_out[hw + q] = e1 > 0.f ? s : (e1 < 0.f ? -s : 0.f);
+                    V.dL_out[2 * hw + q] = e2 > 0.f ? s : (e2 < 0.f ? -s : 0.f);
+                    l1 += (fabsf(e0) + fabsf(e1) + fabsf(e2)) * s;
+                }
             }
         }
         __syncthreads();
+    }
+    if (a.loss) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(F, l1, o);
+        if ((tid & 31) == 0 && l1 != 0.f) atomicAdd(a.loss, l1);
     }
     if (a.pairs) {
 #pragma unroll

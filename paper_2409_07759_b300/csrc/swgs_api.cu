@@ -231,8 +231,9 @@ int ceil_log2(long long x) {
 // Render one batch of views (indices idx[] into the call's view list).
 swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view* views,
                          const std::vector<int>& idx, const float* bg, float* const* out_rgb,
-                         float* const* out_T, BatchState& B, unsigned long long* pairs,
-                         cudaStream_t s) {
+                         float* const* out_T, const float* const* targets, float* const* dls,
+                         float* loss, int n_views_total, BatchState& B,
+                         unsigned long long* pairs, cudaStream_t s) {
     const int tw = ctx->cfg.tile_w, th = ctx->cfg.tile_h;
     const long long N = g->capacity;
     // group the views by frame, in order of first appearance
@@ -312,6 +313,9 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             V.out_rgb = out_rgb[v];
             V.out_T = out_T ? out_T[v] : nullptr;
             V.dL = nullptr;
+            V.target = targets ? targets[v] : nullptr;
+            V.dL_out = dls ? dls[v] : nullptr;
+            V.l1_scale = 1.0f / (3.0f * (float)sv.width * (float)sv.height * (float)n_views_total);
             tiles += (long long)V.ntx * V.nty;
             pix += (long long)sv.width * sv.height;
             B.h_views.push_back(V);
@@ -434,6 +438,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
     ba.work_counter = P<int>(ctx->counter);
     ba.pairs = pairs;
     ba.grad2d = nullptr;
+    ba.loss = targets ? loss : nullptr;
     const int ppt = ctx->cfg.pixels_per_thread;
     int bps = ctx->cfg.blocks_per_sm > 0
                   ? ctx->cfg.blocks_per_sm
@@ -476,6 +481,7 @@ swgs_status backward_batch(swgs_ctx* ctx, const swgs_gaussians* g, BatchState& B
     ba.work_counter = P<int>(ctx->counter);
     ba.pairs = nullptr;
     ba.grad2d = P<float>(B.grad2d);
+    ba.loss = nullptr;
     const int ppt = ctx->cfg.bwd_pixels_per_thread;
     const int bbatch = ctx->cfg.bwd_batch;
     int bps = ctx->cfg.blocks_per_sm > 0
@@ -693,10 +699,40 @@ swgs_status swgs_frame_update(swgs_ctx* ctx, const swgs_gaussians* dst, int64_t 
     return SWGS_OK;
 }
 
+static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
+                                   const swgs_view* views, const float* bg,
+                                   float* const* out_rgb, float* const* out_T,
+                                   const float* const* targets, float* const* dls, float* loss,
+                                   int32_t batched, swgs_saved** saved, void* stream);
+
 swgs_status swgs_render_fwd(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
                             const swgs_view* views, const float* bg, float* const* out_rgb,
                             float* const* out_T, int32_t batched, swgs_saved** saved,
                             void* stream) {
+    return render_fwd_impl(ctx, g, n_views, views, bg, out_rgb, out_T, nullptr, nullptr, nullptr,
+                           batched, saved, stream);
+}
+
+swgs_status swgs_render_fwd_l1(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
+                               const swgs_view* views, const float* bg, float* const* out_rgb,
+                               float* const* out_T, const float* const* target,
+                               float* const* dL_drgb, float* loss, int32_t batched,
+                               swgs_saved** saved, void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    if (!target || !dL_drgb || !loss) return fail(ctx, SWGS_EINVAL, "null target, dL or loss");
+    for (int v = 0; v < n_views; ++v)
+        if (!target[v] || !dL_drgb[v]) return fail(ctx, SWGS_EINVAL, "view %d: null target or dL", v);
+    if (cudaMemsetAsync(loss, 0, sizeof(float), (cudaStream_t)stream) != cudaSuccess)
+        return fail(ctx, SWGS_ECUDA, "clearing the loss failed");
+    return render_fwd_impl(ctx, g, n_views, views, bg, out_rgb, out_T, target, dL_drgb, loss,
+                           batched, saved, stream);
+}
+
+static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
+                                   const swgs_view* views, const float* bg,
+                                   float* const* out_rgb, float* const* out_T,
+                                   const float* const* targets, float* const* dls, float* loss,
+                                   int32_t batched, swgs_saved** saved, void* stream) {
     if (!ctx) return SWGS_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     ctx->last_stream = s;
@@ -737,7 +773,8 @@ swgs_status swgs_render_fwd(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_vi
         std::vector<int> idx;
         if (batched) for (int v = 0; v < n_views; ++v) idx.push_back(v);
         else idx.push_back(b);
-        st = render_batch(ctx, g, views, idx, bg, out_rgb, out_T, sv->batches[b], pairs, s);
+        st = render_batch(ctx, g, views, idx, bg, out_rgb, out_T, targets, dls, loss, n_views,
+                          sv->batches[b], pairs, s);
         if (st != SWGS_OK) {
             ctx->pool.push_back(sv);
             return st;

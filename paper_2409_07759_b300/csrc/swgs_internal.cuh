@@ -33,6 +33,9 @@ struct ViewDev {
     float* out_rgb;    // [3,H,W]
     float* out_T;      // [H,W] or null
     const float* dL;   // [3,H,W] (backward only)
+    const float* target;  // [3,H,W] (forward fused with the L1 term) or null
+    float* dL_out;        // [3,H,W] written with the L1 gradient (fused forward)
+    float l1_scale;       // 1 / (3 H W V)
 };
 
 struct GroupDev {
@@ -374,6 +377,7 @@ struct BlendArgs {
     int* work_counter;
     unsigned long long* pairs;  // optional
     float* grad2d;     // backward: 12 floats per record
+    float* loss;       // fused L1 forward: accumulated loss (device float)
 };
 cudaError_t launch_blend_fwd(const BlendArgs& a, int tile_w, int tile_h, int batch, int ppt,
                              int grid, cudaStream_t s);

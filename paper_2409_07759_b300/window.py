@@ -72,10 +72,10 @@ class WindowTrainer:
             self.r.render(self.state, self.views, bg=self.bg, batched=self.batched,
                           out=self.images)
             return None
-        _, saved = self.r.render(self.state, self.views, bg=self.bg, batched=self.batched,
-                                 keep_saved=True, out=self.images)
-        self.r.loss_l1(self.views, self.images, self.targets, dL_out=self.dl,
-                       loss_out=self.loss)
+        # forward with the L1 term fused into the blend's epilogue
+        _, _, _, saved = self.r.render_l1(self.state, self.views, self.targets, bg=self.bg,
+                                          batched=self.batched, out=self.images,
+                                          dL_out=self.dl, loss_out=self.loss)
         self._gflat.zero_()
         self.r.backward(self.state, saved, self.dl, self.grads)
         saved.release()

@@ -274,3 +274,20 @@ def test_autograd_function(R, oracle_mod):
     ref = oracle_mod.zero_grads(sc)
     oracle_mod.render_bwd(sc, view, _np(w).astype(np.float64), grads=ref, bands=BANDS)
     compare_grads({k: _np(p.grad) for k, p in zip(api.PARAM_NAMES, params)}, ref)
+
+
+def test_fused_forward_l1(R, oracle_mod):
+    """The forward with the L1 term fused into the blend gives the same image
+    and gradient as the separate loss pass, and the oracle's loss."""
+    sc, views, targets = synth.config1()
+    st = _state(sc)
+    tg = [torch.from_numpy(t).cuda() for t in targets]
+    imgs, dl, loss, saved = R.render_l1(st, views, tg)
+    saved.release()
+    imgs2, _ = R.render(st, views)
+    loss2, dl2 = R.loss_l1(views, imgs2, tg)
+    assert torch.equal(imgs[0], imgs2[0]) and torch.equal(dl[0], dl2[0])
+    assert float(loss.item()) == pytest.approx(float(loss2.item()), rel=1e-6)
+    ref_img = oracle_mod.render(sc, views[0], mode="tiled")["rgb"]
+    ref_loss, _ = oracle_mod.l1_loss_grad([ref_img], targets)
+    assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-5)
