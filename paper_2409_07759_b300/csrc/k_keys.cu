@@ -43,17 +43,26 @@ emit_keys_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict_
         const int vi = find_view_by_record(views, n_views, (int)r);
         const int base_tile = views[vi].tile_base, ntx = views[vi].ntx;
         const short4 rc = rec.rect[r];
-        const float4 ga = rec.a[r];
-        const float4 gb = rec.b[r];
-        const KmEllipse el = km_ellipse(gb.x, gb.y, gb.z);
         const int h = rc.w - rc.z + 1;
         uint32_t o = offsets[k];
         const uint32_t o_end = o + (uint32_t)n;  // never past this record's range
         for (int r0 = 0; r0 < h; r0 += 32) {
             int f = 0, l = 0, cnt = 0;
-            if (r0 + lane < h)
-                cnt = km_row_run(el, ga.x, ga.y, rc.x, rc.y, rc.z + r0 + lane, tile_w, tile_h,
-                                 &f, &l);
+            const int row = r0 + lane;
+            const bool wide = rc.y - rc.x >= 255;  // runs do not fit one byte: recompute
+            if (row < h) {
+                if (row < kRunRows && !wide) {
+                    const uint16_t run = rec.runs[(long long)r * kRunRows + row];
+                    cnt = run >> 8;
+                    f = rc.x + (run & 0xff);
+                } else {  // taller than the stored rows: recompute
+                    const float4 ga = rec.a[r];
+                    const float4 gb = rec.b[r];
+                    const KmEllipse el = km_ellipse(gb.x, gb.y, gb.z);
+                    cnt = km_row_run_fast(el, ga.x, ga.y, rc.x, rc.y, rc.z + row, tile_w,
+                                          tile_h, &f, &l);
+                }
+            }
             int incl = cnt;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {

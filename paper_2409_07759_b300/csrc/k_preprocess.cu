@@ -271,12 +271,20 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_
             const int x1 = fxhi > (float)(ntx - 1) ? ntx - 1 : (fxhi < -1.0f ? -1 : (int)fxhi);
             const int y0 = fylo < 0.0f ? 0 : (fylo > (float)nty ? nty : (int)fylo);
             const int y1 = fyhi > (float)(nty - 1) ? nty - 1 : (fyhi < -1.0f ? -1 : (int)fyhi);
-            // tiles of the bounding rectangle the 3-sigma ellipse reaches
+            // tiles of the bounding rectangle the 3-sigma ellipse reaches: one run
+            // per tile row; the runs of the first kRunRows rows are kept for the
+            // key emission (one byte each for offset and length)
             if (x1 >= x0) {
                 const KmEllipse el = km_ellipse(A, B, C);
+                const bool narrow = x1 - x0 < 255;
+                uint16_t* runs = a.rec.runs + r * kRunRows;
                 for (int ty = y0; ty <= y1; ++ty) {
-                    int f, l;
-                    tiles += km_row_run(el, u, v, x0, x1, ty, a.tile_w, a.tile_h, &f, &l);
+                    int f = 0, l = 0;
+                    const int cnt = km_row_run_fast(el, u, v, x0, x1, ty, a.tile_w, a.tile_h,
+                                                    &f, &l);
+                    if (ty - y0 < kRunRows && narrow)
+                        runs[ty - y0] = (uint16_t)((cnt ? (f - x0) : 0) | (cnt << 8));
+                    tiles += cnt;
                 }
             }
             rect = make_short4((short)x0, (short)x1, (short)y0, (short)y1);
@@ -304,7 +312,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_
     a.rec.c[r] = make_float4(fmaxf(col0 + 0.5f, 0.f), fmaxf(col1 + 0.5f, 0.f),
                              fmaxf(col2 + 0.5f, 0.f), 0.f);
     a.rec.tiles[r] = culled ? 0 : tiles;
-    a.rec.rect[r] = rect;
+    a.rec.rect[r] = culled ? make_short4(0, -1, 0, -1) : rect;
     a.rec.depth_key[r] = (culled || tiles == 0) ? 0xffffffffu : __float_as_uint(z);
 }
 

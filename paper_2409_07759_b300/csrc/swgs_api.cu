@@ -47,8 +47,8 @@ struct BatchState {
     std::vector<ViewDev> h_views;   // table order (grouped by frame)
     std::vector<GroupDev> h_groups;
     std::vector<int> call_index;    // table entry -> index in the call's view list
-    Buf views, groups, ids, rec_a, rec_b, rec_c, rec_tiles, rec_rect, rec_depth, vals, ranges,
-        T, last, grad2d;
+    Buf views, groups, ids, rec_a, rec_b, rec_c, rec_tiles, rec_rect, rec_depth, rec_runs, vals,
+        ranges, T, last, grad2d;
     bool has_grad2d = false;
 };
 
@@ -205,7 +205,8 @@ swgs_saved* acquire_saved(swgs_ctx* c) {
 void free_saved_buffers(swgs_ctx* c, swgs_saved* s, cudaStream_t st) {
     for (auto& b : s->batches) {
         Buf* bs[] = {&b.views, &b.groups, &b.ids, &b.rec_a, &b.rec_b, &b.rec_c, &b.rec_tiles,
-                     &b.rec_rect, &b.rec_depth, &b.vals, &b.ranges, &b.T, &b.last, &b.grad2d};
+                     &b.rec_rect, &b.rec_depth, &b.rec_runs, &b.vals, &b.ranges, &b.T, &b.last,
+                     &b.grad2d};
         for (Buf* x : bs) ctx_free(c, *x, st);
     }
     ctx_free(c, s->pairs, st);
@@ -219,6 +220,7 @@ Records records_of(BatchState& b) {
     r.tiles = P<int32_t>(b.rec_tiles);
     r.rect = P<short4>(b.rec_rect);
     r.depth_key = P<uint32_t>(b.rec_depth);
+    r.runs = P<uint16_t>(b.rec_runs);
     return r;
 }
 
@@ -338,6 +340,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
         !ensure(ctx, B.rec_tiles, sizeof(int32_t) * R, s) ||
         !ensure(ctx, B.rec_rect, sizeof(short4) * R, s) ||
         !ensure(ctx, B.rec_depth, sizeof(uint32_t) * R, s) ||
+        !ensure(ctx, B.rec_runs, sizeof(uint16_t) * kRunRows * R, s) ||
         !ensure(ctx, B.ranges, sizeof(int2) * (size_t)tiles, s) ||
         !ensure(ctx, B.T, sizeof(float) * (size_t)pix, s) ||
         !ensure(ctx, B.last, sizeof(int32_t) * (size_t)pix, s) ||

@@ -55,7 +55,11 @@ struct Records {
     int32_t* tiles;    // tiles touched (0 if culled)
     short4* rect;      // tx0, tx1, ty0, ty1
     uint32_t* depth_key;  // FP32 depth bits, 0xffffffff if no tiles
+    uint16_t* runs;    // kRunRows per record: first - tx0 (low byte), length (high byte)
 };
+
+// Rows of a record whose tile runs are stored; taller rectangles recompute the rest.
+constexpr int kRunRows = 32;
 
 // ---------------------------------------------------------------------------
 // Thresholds of the per-pixel compositing rule (Eq. 3 plus the readings of
@@ -175,6 +179,39 @@ __device__ __forceinline__ bool km_row_extent(const KmEllipse& e, float ya, floa
     *right = (lo <= dyr && dyr <= hi) ? e.xm : (r0 > r1 ? r0 : r1);
     *left = (lo <= dyl && dyl <= hi) ? -e.xm : (l0 < l1 ? l0 : l1);
     return true;
+}
+
+// Same result as km_row_run, with the two end searches started from a guess
+// and adjusted: both predicates (pixel-centre span end >= left, start <=
+// right) are monotone in the tile index, so the smallest / largest index
+// satisfying them is unique whatever the starting point.
+__device__ __forceinline__ int km_row_run_fast(const KmEllipse& e, float u, float v, int tx0,
+                                               int tx1, int ty, int tile_w, int tile_h,
+                                               int* first, int* last) {
+    if (!(e.detc > 0.0f)) { *first = tx0; *last = tx1; return tx1 - tx0 + 1; }
+    const float by = (float)(ty * tile_h);
+    const float ya = ksub(kadd(by, 0.5f), v);
+    const float yb = ksub(kadd(by, (float)tile_h - 0.5f), v);
+    float left, right;
+    if (!km_row_extent(e, ya, yb, &left, &right)) return 0;
+    const float itw = 1.0f / (float)tile_w;
+    const float hi_off = (float)tile_w - 0.5f;
+    auto xb_of = [&](int t) { return ksub(kadd((float)(t * tile_w), hi_off), u); };
+    auto xa_of = [&](int t) { return ksub(kadd((float)(t * tile_w), 0.5f), u); };
+    float ga = floorf((left + u) * itw);
+    ga = fminf(fmaxf(ga, (float)tx0), (float)(tx1 + 1));
+    int a = (int)ga;
+    while (a > tx0 && xb_of(a - 1) >= left) --a;
+    while (a <= tx1 && !(xb_of(a) >= left)) ++a;
+    if (a > tx1) return 0;
+    float gb = floorf((right + u) * itw);
+    gb = fminf(fmaxf(gb, (float)a), (float)tx1);
+    int b = (int)gb;
+    while (b < tx1 && xa_of(b + 1) <= right) ++b;
+    while (b > a && !(xa_of(b) <= right)) --b;
+    *first = a;
+    *last = b;
+    return b - a + 1;
 }
 
 // Kept run [first, last] of tile row ty within [tx0, tx1]; returns its length.
