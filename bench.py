@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-config3", action="store_true")
     ap.add_argument("--views", type=int, default=4, help="cameras per frame")
     ap.add_argument("--frames", type=int, default=10)
     ap.add_argument("--tile", default="16x16", help="blend tile, WxH")
@@ -65,6 +66,37 @@ def parse():
     ap.add_argument("--serve-streams", type=int, default=3)
     ap.add_argument("--hbm-budget-gb", type=float, default=24.0)
     return ap.parse_args()
+
+
+def config3_leg(args):
+    """Config 3: batched multi-view forward of 1M Gaussians (~20% active) to 32
+    Fibonacci-sphere cameras (8 x 640x480, 16 x 1280x720, 8 x 1920x1080) in one
+    batched call with the autotuned launch shape, against the plain per-view path."""
+    import torch
+    from paper_2409_07759_b300 import api, autotune, synth
+    sc, views = synth.config3()
+    st = api.GaussianState.from_scene(sc)
+    best = autotune.autotune(st, views, mode="fwd", reps=2, cache=None)
+    r = api.Renderer(**best)
+    mpix = sum(v.width * v.height for v in views) / 1e6
+
+    def timed(batched, reps):
+        r.render(st, views, batched=batched)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            r.render(st, views, batched=batched)
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    bms, pms = timed(True, 5), timed(False, 3)
+    r.close()
+    return {"mpix": mpix, "views": len(views), "gaussians": sc.n,
+            "batched_ms": bms, "batched_mpix_s": mpix / (bms / 1e3),
+            "plain_ms": pms, "plain_mpix_s": mpix / (pms / 1e3), "batched_over_plain": pms / bms,
+            "autotuned": dict(best, tile="%dx%d" % tuple(best["tile"]))}
 
 
 def serving_leg(args):
@@ -434,6 +466,9 @@ def main():
     if not args.no_serving:
         torch.cuda.synchronize()
         extra["serving"] = serving_leg(args)
+    if not args.no_config3:
+        torch.cuda.synchronize()
+        extra["config3_batched_fwd"] = config3_leg(args)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
