@@ -236,10 +236,10 @@ def cpu_oracle_sample(scene, views, targets, budget_s=15.0, max_views=None):
 
 # -------------------------------------------------------------- workload --
 
-def build_workload(args):
+def build_workload(args, rank=0):
     from paper_2409_07759_b300 import synth
     scene, views, targets = synth.config2(n_frames=args.frames, per_frame=args.views,
-                                          forced_dead_fraction=0.01)
+                                          forced_dead_fraction=0.01, rank=rank)
     return scene, views, targets
 
 
@@ -303,10 +303,9 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
-    scene, views, targets = build_workload(args)
-    # ranks train replicas on their own windows (views rotated by rank)
-    if world > 1:
-        views = views[rank:] + views[:rank]
+    # weak scaling: every rank holds a replica of the scene and renders its own
+    # 4 cameras per frame of the window (rank 0: the single-GPU workload)
+    scene, views, targets = build_workload(args, rank=rank)
     mpix = sum(v.width * v.height for v in views) / 1e6
     state = api.GaussianState.from_scene(scene)
     tgt_host = [torch.from_numpy(t).pin_memory() for t in targets]
@@ -315,7 +314,13 @@ def main():
     r = api.Renderer(tile=(tw, th), batch=args.batch, pixels_per_thread=args.ppt,
                      bwd_pixels_per_thread=args.bwd_ppt, bwd_batch=args.bwd_batch,
                      count_pairs=True)
-    tr = WindowTrainer(r, state, views, tgt_dev, seed=1234 + rank)
+    reducer = None
+    if world > 1:
+        # one all-reduce of the flat gradient buffer (weighted by view share)
+        # before the optimiser/SGLD step; same seed on every replica
+        from paper_2409_07759_b300 import dp
+        reducer = dp.GradientReducer(len(views), dp.total_views(len(views), device="cuda"))
+    tr = WindowTrainer(r, state, views, tgt_dev, seed=1234, reduce=reducer)
     # the streamed slices: 6,000-slot slices of the initial state, from pinned host
     S = 6000
     n_slices = scene.n // S
@@ -330,20 +335,6 @@ def main():
     def upd(k):
         s = k % n_slices
         return (s * S, host_slices[s])
-
-    def allreduce():
-        if world > 1:
-            dist.all_reduce(tr._gflat)
-
-    if world > 1:
-        # data-parallel step: sum gradients across ranks before the SGLD step
-        orig_backward = r.backward
-
-        def backward_and_reduce(*a, **kw):
-            out = orig_backward(*a, **kw)
-            allreduce()
-            return out
-        r.backward = backward_and_reduce
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     for k in range(args.warmup):

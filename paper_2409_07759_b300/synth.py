@@ -196,12 +196,14 @@ def config1(width: int = 1352, height: int = 1014):
 
 def config2(width: int = 1352, height: int = 1014, n: int = 300_000,
             first_frame: int = 145, n_frames: int = 10, per_frame: int = 4,
-            forced_dead_fraction: float = 0.0):
+            forced_dead_fraction: float = 0.0, rank: int = 0):
     """Sliding-window training step: 300k Gaussians, SH3, lifespans as config 1;
     20 ring cameras; frames 145..154 with 4 of the 20 cameras per frame drawn
     without replacement (seed 2) -> 40 views; targets U[0,1]; frozen = start <
     first_frame (the maturation rule of Alg. 1). `forced_dead_fraction` sets that
-    fraction of logits to -8 so that relocation has work to do."""
+    fraction of logits to -8 so that relocation has work to do. `rank` > 0 keeps
+    the scene and draws that rank's own cameras and targets (data-parallel
+    weak scaling; rank 0 is the single-GPU workload)."""
     rng = np.random.default_rng(2)
     attrs = make_gaussians(rng, n, 3)
     start, expire = _lifespans(rng, n, 300, 10, 60)
@@ -212,6 +214,8 @@ def config2(width: int = 1352, height: int = 1014, n: int = 300_000,
         attrs["opacity_logits"][idx] = -8.0
     scene = _scene(attrs, 3, start, expire, frozen=frozen)
     ring = ring_cameras(20, 4.0, width, height)
+    if rank > 0:
+        rng = np.random.default_rng([2, rank])
     views, targets = [], []
     for f in range(first_frame, first_frame + n_frames):
         for c in rng.choice(20, size=per_frame, replace=False):

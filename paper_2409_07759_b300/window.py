@@ -35,7 +35,7 @@ class WindowTrainer:
 
     def __init__(self, renderer: api.Renderer, state: api.GaussianState, views: Sequence,
                  targets: Sequence[torch.Tensor], params: Optional[dict] = None, seed: int = 0,
-                 batched: bool = True, bg=(0.0, 0.0, 0.0)):
+                 batched: bool = True, bg=(0.0, 0.0, 0.0), reduce=None):
         self.r = renderer
         self.state = state
         self.views = list(views)
@@ -47,6 +47,9 @@ class WindowTrainer:
         self.seed = seed
         self.batched = batched
         self.bg = bg
+        # data parallel: called as reduce(flat_grads, loss) between the backward
+        # and the optimiser step (see dp.GradientReducer)
+        self.reduce = reduce
         K = (state.sh_degree + 1) ** 2
         self._gflat, g = _flat_views(state.n, K)
         self.grads = api.GaussianGrads(*g, state.sh_degree)
@@ -79,6 +82,8 @@ class WindowTrainer:
         self._gflat.zero_()
         self.r.backward(self.state, saved, self.dl, self.grads)
         saved.release()
+        if self.reduce is not None:
+            self.reduce(self._gflat, self.loss)
         self.r.sgld_step(self.state, self.frames, self.params, self.seed, step,
                          grads=self.grads, adam=self.adam)
         return self.loss
