@@ -196,7 +196,7 @@ class Renderer:
                  count_pairs=False, pixels_per_thread=2, bwd_pixels_per_thread=None,
                  bwd_batch=128, use_torch_allocator=True):
         if bwd_pixels_per_thread is None:  # 8x8 tiles hold at most 2 pixels per thread
-            bwd_pixels_per_thread = 2 if tuple(tile) == (8, 8) else 4
+            bwd_pixels_per_thread = 2 if tuple(tile) == (8, 8) else 8
         L = _abi.load()
         cfg = _abi.SwgsConfig()
         L.swgs_default_config(C.byref(cfg))

@@ -56,7 +56,7 @@ def candidates(mode: str):
             for ppt in FWD_PPT[tile]:
                 if mode == "fwd":
                     yield dict(tile=tile, batch=batch, pixels_per_thread=ppt,
-                               bwd_pixels_per_thread=min(ppt, 2) if tile == (8, 8) else 4,
+                               bwd_pixels_per_thread=min(ppt, 2) if tile == (8, 8) else 8,
                                bwd_batch=128)
                 else:
                     for bppt in BWD_PPT[tile]:

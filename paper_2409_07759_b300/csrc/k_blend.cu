@@ -207,7 +207,11 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
         const int x = (lt % V.ntx) * TW + lx, y0 = (lt / V.ntx) * TH + ly;
         const float px = (float)x + 0.5f;
         const int2 rg = a.ranges[item];
-        float T[PPT], dL0[PPT], dL1[PPT], dL2[PPT], B0[PPT], B1[PPT], B2[PPT], py[PPT];
+        // Per pixel: T (recovered back to front), dL/dC, and D = sum_ch dL_ch B_ch with
+        // B the colour composited behind the current Gaussian (starts at the
+        // background). With E = sum_ch dL_ch c_ch: dL/dalpha = T (E - D) and the
+        // step to the next Gaussian in front is D' = D + alpha (E - D).
+        float T[PPT], dL0[PPT], dL1[PPT], dL2[PPT], D[PPT], py[PPT];
         int last[PPT];
         int mylast = 0;
 #pragma unroll
@@ -215,7 +219,6 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
             const int y = y0 + p;
             py[p] = (float)y + 0.5f;
             T[p] = 1.f; dL0[p] = dL1[p] = dL2[p] = 0.f; last[p] = 0;
-            B0[p] = V.bg[0]; B1[p] = V.bg[1]; B2[p] = V.bg[2];
             if (x < W && y < H) {
                 const long long hw = (long long)W * H, q = (long long)y * W + x;
                 T[p] = a.T[V.pix_base + q];
@@ -224,6 +227,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                 dL1[p] = V.dL[hw + q];
                 dL2[p] = V.dL[2 * hw + q];
             }
+            D[p] = fmaf(dL0[p], V.bg[0], fmaf(dL1[p], V.bg[1], dL2[p] * V.bg[2]));
             mylast = max(mylast, last[p]);
         }
         if (mylast > 0) atomicMax(&s_maxlast, mylast);
@@ -245,13 +249,15 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                 const float4 g0 = s0[j];
                 const float2 g1 = *reinterpret_cast<const float2*>(&s1[j]);
                 const float4 c = s2[j];
-                float m[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) m[k] = 0.f;
+                // The thread's pixels share x, so dx is common to them: only
+                // sum gm, sum gm dy and sum gm dy^2 run per pixel; the dx terms
+                // are applied once below. gm here is alpha dL/dalpha (the
+                // factor -1/2 of dalpha/dm is applied at the flush).
+                float s0m = 0.f, sy = 0.f, syy = 0.f, m6 = 0.f, m7 = 0.f, m8 = 0.f, dx = 0.f;
                 bool any = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
-                    float dx, dy, au;
+                    float dy, au;
                     const float q = pair_q(px, py[p], g0, g1.x, &dx, &dy);
                     const float al = pair_alpha(q, g1.y, &au);
                     const bool ok = pos < last[p] && q >= kQMin && al >= kAlphaMin;
@@ -260,26 +266,32 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                     T[p] = ok ? __fdividef(T[p], __fsub_rn(1.f, al)) : T[p];
                     const float a1 = ok ? al : 0.f;
                     const float w = a1 * T[p];
-                    m[6] = fmaf(w, dL0[p], m[6]);
-                    m[7] = fmaf(w, dL1[p], m[7]);
-                    m[8] = fmaf(w, dL2[p], m[8]);
-                    // colour behind: B' = a c + (1 - a) B = B + a (c - B);
-                    // dL/dalpha = T sum_ch dL_ch (c_ch - B_ch)
-                    const float d0 = c.x - B0[p], d1 = c.y - B1[p], d2 = c.z - B2[p];
-                    const float ga = T[p] * fmaf(dL0[p], d0, fmaf(dL1[p], d1, dL2[p] * d2));
-                    B0[p] = fmaf(a1, d0, B0[p]);
-                    B1[p] = fmaf(a1, d1, B1[p]);
-                    B2[p] = fmaf(a1, d2, B2[p]);
-                    const float gm = (ok && au <= kAlphaMax) ? -0.5f * au * ga : 0.f;
-                    const float gx = gm * dx, gy = gm * dy;
-                    m[0] += gm;
-                    m[1] += gx;
-                    m[2] += gy;
-                    m[3] = fmaf(gx, dx, m[3]);
-                    m[4] = fmaf(gx, dy, m[4]);
-                    m[5] = fmaf(gy, dy, m[5]);
+                    m6 = fmaf(w, dL0[p], m6);
+                    m7 = fmaf(w, dL1[p], m7);
+                    m8 = fmaf(w, dL2[p], m8);
+                    const float e = fmaf(dL0[p], c.x, fmaf(dL1[p], c.y, dL2[p] * c.z));
+                    const float diff = e - D[p];
+                    const float ga = T[p] * diff;
+                    D[p] = fmaf(a1, diff, D[p]);
+                    const float gm = (ok && au <= kAlphaMax) ? au * ga : 0.f;
+                    const float gy = gm * dy;
+                    s0m += gm;
+                    sy += gy;
+                    syy = fmaf(gy, dy, syy);
                 }
-                if (__any_sync(F, any)) warp_sum9_to_smem(m, &s_acc[j * 9]);
+                if (__any_sync(F, any)) {
+                    float m[9];
+                    m[0] = s0m;
+                    m[1] = s0m * dx;
+                    m[2] = sy;
+                    m[3] = m[1] * dx;
+                    m[4] = sy * dx;
+                    m[5] = syy;
+                    m[6] = m6;
+                    m[7] = m7;
+                    m[8] = m8;
+                    warp_sum9_to_smem(m, &s_acc[j * 9]);
+                }
             }
             __syncthreads();
             for (int k = tid; k < cnt; k += NT) {
@@ -291,14 +303,17 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                 const uint32_t r = s_rec[k];
                 const float4 ra = a.rec.a[r];   // u, v, opacity, depth
                 const float4 rb = a.rec.b[r];   // A, B, C
+                // acc[0..5] hold sums of alpha dL/dalpha times (1, dx, dy, dx^2,
+                // dx dy, dy^2); dL/dm = -1/2 of them (G = exp(-m/2)).
                 // m = A dx^2 + 2B dx dy + C dy^2, dx = px - u: dm/du = -2(A dx + B dy)
-                const float du = -2.f * (rb.x * acc[1] + rb.y * acc[2]);
-                const float dv = -2.f * (rb.y * acc[1] + rb.z * acc[2]);
-                // alpha = o G, dalpha/do = G = alpha/o and gm = -alpha/2 dL/dalpha
-                const float dop = -2.f * acc[0] / ra.z;
+                const float m1 = -0.5f * acc[1], m2 = -0.5f * acc[2];
+                const float du = -2.f * (rb.x * m1 + rb.y * m2);
+                const float dv = -2.f * (rb.y * m1 + rb.z * m2);
+                // alpha = o G, dalpha/do = G = alpha/o
+                const float dop = acc[0] / ra.z;
                 float* dst = a.grad2d + 12ll * r;
-                red_add_v4(dst, du, dv, acc[3], 2.f * acc[4]);
-                red_add_v4(dst + 4, acc[5], dop, acc[6], acc[7]);
+                red_add_v4(dst, du, dv, -0.5f * acc[3], -acc[4]);
+                red_add_v4(dst + 4, -0.5f * acc[5], dop, acc[6], acc[7]);
                 red_add(dst + 8, acc[8]);
 #pragma unroll
                 for (int e = 0; e < 9; ++e) acc[e] = 0.f;

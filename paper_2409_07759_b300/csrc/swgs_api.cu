@@ -572,7 +572,7 @@ swgs_status swgs_default_config(swgs_config* cfg) {
     cfg->blocks_per_sm = 0;
     cfg->count_pairs = 0;
     cfg->pixels_per_thread = 2;
-    cfg->bwd_pixels_per_thread = 4;
+    cfg->bwd_pixels_per_thread = 8;
     cfg->bwd_batch = 128;
     return SWGS_OK;
 }

@@ -287,7 +287,9 @@ def test_fused_forward_l1(R, oracle_mod):
     imgs2, _ = R.render(st, views)
     loss2, dl2 = R.loss_l1(views, imgs2, tg)
     assert torch.equal(imgs[0], imgs2[0]) and torch.equal(dl[0], dl2[0])
-    assert float(loss.item()) == pytest.approx(float(loss2.item()), rel=1e-6)
+    # both losses are FP32 sums of ~4e4 warp partials added atomically in no
+    # fixed order: relative spread ~sqrt(n) * 6e-8, so 1e-5 (as against FP64)
+    assert float(loss.item()) == pytest.approx(float(loss2.item()), rel=1e-5)
     ref_img = oracle_mod.render(sc, views[0], mode="tiled")["rgb"]
     ref_loss, _ = oracle_mod.l1_loss_grad([ref_img], targets)
     assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-5)
