@@ -310,10 +310,10 @@ enum {
     SWGS_STAGE_COMPACT = 0,      /* active-set compaction */
     SWGS_STAGE_PREPROCESS = 1,   /* projection + SH */
     SWGS_STAGE_DEPTH_SORT = 2,   /* record depth sort */
-    SWGS_STAGE_KEY_SCAN = 3,     /* tiles touched in depth order + scan */
-    SWGS_STAGE_EMIT = 4,         /* key emission */
-    SWGS_STAGE_TILE_SORT = 5,    /* stable sort of keys by tile */
-    SWGS_STAGE_RANGES = 6,       /* per-tile ranges */
+    SWGS_STAGE_KEY_SCAN = 3,     /* super tiles keyed per record, in depth order + scan */
+    SWGS_STAGE_EMIT = 4,         /* (super tile, record) key emission */
+    SWGS_STAGE_TILE_SORT = 5,    /* stable sort of the keys by super tile */
+    SWGS_STAGE_RANGES = 6,       /* super-tile ranges + expansion into per-tile lists */
     SWGS_STAGE_BLEND_FWD = 7,    /* forward blend (one kernel) */
     SWGS_STAGE_BLEND_BWD = 8,    /* reverse blend (one kernel) */
     SWGS_STAGE_PREPROCESS_BWD = 9,

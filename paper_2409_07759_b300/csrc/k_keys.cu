@@ -1,126 +1,241 @@
-// k_keys.cu -- tile keys of the depth-ordered records and the per-tile ranges
-// of the sorted key list (the per-tile depth order that Eq. 3 composites in).
+// k_keys.cu -- keys of the depth-ordered records, the ranges of a sorted key
+// list, and the per-tile depth-ordered lists that Eq. 3 composites in.
 #include "swgs_internal.cuh"
 
 namespace swgs {
 
-// out[k] = tiles touched by the k-th record in depth order.
-__global__ void gather_tiles_kernel(const uint32_t* __restrict__ order,
-                                    const int32_t* __restrict__ tiles, uint32_t* __restrict__ out,
-                                    long long n) {
-    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) out[k] = (uint32_t)tiles[order[k]];
+// Tile keys are emitted per super tile (a block of SX x SY tiles) rather than
+// per tile: a record keys each super tile its tile rectangle overlaps, the
+// (super tile, record) keys are sorted stably by super tile, and each super
+// tile's depth-ordered candidate list is then expanded into the exact per-tile
+// lists by the coverage rule (the row runs). Filtering preserves order, so each
+// tile's list is the same depth-ordered list a per-tile key sort gives, from a
+// sort over about a fifth as many keys (4x4 super tiles of 16x16-pixel tiles).
+
+__device__ __forceinline__ int super_count(short4 rc, int tiles, int sx, int sy) {
+    if (tiles == 0) return 0;
+    return (rc.y / sx - rc.x / sx + 1) * (rc.w / sy - rc.z / sy + 1);
 }
 
-cudaError_t launch_gather_tiles(const uint32_t* order, const int32_t* tiles, uint32_t* out,
-                                long long n, cudaStream_t s) {
+// out[k] = super tiles keyed by the k-th record in depth order; *exact += the
+// records' exact tile counts (the number of per-tile list entries).
+__global__ void __launch_bounds__(256)
+gather_supers_kernel(const uint32_t* __restrict__ order, Records rec, int sx, int sy,
+                     uint32_t* __restrict__ out, unsigned long long* __restrict__ exact,
+                     long long n) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long t = 0;
+    if (k < n) {
+        const uint32_t r = order[k];
+        const int tiles = rec.tiles[r];
+        out[k] = (uint32_t)super_count(rec.rect[r], tiles, sx, sy);
+        t = (unsigned long long)tiles;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(exact, t);
+}
+
+cudaError_t launch_gather_supers(const uint32_t* order, const Records rec, int sx, int sy,
+                                 uint32_t* out, unsigned long long* exact, long long n,
+                                 cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     note_launch();
-    gather_tiles_kernel<<<div_up(n, 256), 256, 0, s>>>(order, tiles, out, n);
+    gather_supers_kernel<<<div_up(n, 256), 256, 0, s>>>(order, rec, sx, sy, out, exact, n);
     return cudaGetLastError();
 }
 
-// The k-th record in depth order writes one (global tile id, record) pair per
-// tile its 3-sigma ellipse covers, at offsets[k]. One warp per record: lane i
-// computes the kept run of tile row i (row rule) and a warp scan places the
-// runs; then every lane writes consecutive outputs, finding its row by a
-// shuffle binary search over the run offsets (fully coalesced stores).
-// Records with the same depth keep their (slot-ascending) record order, so a
-// stable sort by tile gives each tile's list in (depth, slot) order.
+// Kept tile run [first, first + count) of record r in absolute tile row ty
+// (the row rule: stored for the first kRunRows rows of narrow records,
+// recomputed otherwise).
+__device__ __forceinline__ int record_row_run(const Records& rec, uint32_t r, short4 rc, int ty,
+                                              int tile_w, int tile_h, int* first) {
+    const int row = ty - rc.z;
+    const bool wide = rc.y - rc.x >= 255;
+    if (row < kRunRows && !wide) {
+        const uint16_t run = rec.runs[(long long)r * kRunRows + row];
+        *first = rc.x + (run & 0xff);
+        return run >> 8;
+    }
+    const float4 ga = rec.a[r];
+    const float4 gb = rec.b[r];
+    const KmEllipse el = km_ellipse(gb.x, gb.y, gb.z);
+    int l = 0;
+    return km_row_run_fast(el, ga.x, ga.y, rc.x, rc.y, ty, tile_w, tile_h, first, &l);
+}
+
+// The k-th record in depth order writes, for every super tile of its super
+// rectangle (row-major, at offsets[k]), the key (global super tile id) |
+// (coverage mask << 16) and the value r. Bit ly*SX + lx of the mask is set when
+// the record covers tile (lx, ly) of the super tile by the row rule. The sort
+// reads only the low 16 bits (the super tile id), so the mask rides along.
 __global__ void __launch_bounds__(256)
-emit_keys_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
-                 long long n_rec, Records rec, const ViewDev* __restrict__ views, int n_views,
-                 int tile_w, int tile_h, uint32_t* __restrict__ keys,
-                 uint32_t* __restrict__ vals) {
-    const unsigned F = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long k = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n_rec;
-         k += nw) {
+emit_supers_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
+                   long long n_rec, Records rec, const ViewDev* __restrict__ views, int n_views,
+                   int sx, int sy, int tile_w, int tile_h, uint32_t* __restrict__ keys,
+                   uint32_t* __restrict__ vals) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_rec;
+         k += (long long)gridDim.x * blockDim.x) {
         const uint32_t r = order[k];
-        const int n = rec.tiles[r];
-        if (n == 0) continue;
-        const int vi = find_view_by_record(views, n_views, (int)r);
-        const int base_tile = views[vi].tile_base, ntx = views[vi].ntx;
+        const int tiles = rec.tiles[r];
+        if (tiles == 0) continue;
         const short4 rc = rec.rect[r];
-        const int h = rc.w - rc.z + 1;
+        const ViewDev& V = views[find_view_by_record(views, n_views, (int)r)];
+        const int x0 = rc.x / sx, x1 = rc.y / sx, y0 = rc.z / sy, y1 = rc.w / sy;
         uint32_t o = offsets[k];
-        const uint32_t o_end = o + (uint32_t)n;  // never past this record's range
-        for (int r0 = 0; r0 < h; r0 += 32) {
-            int f = 0, l = 0, cnt = 0;
-            const int row = r0 + lane;
-            const bool wide = rc.y - rc.x >= 255;  // runs do not fit one byte: recompute
-            if (row < h) {
-                if (row < kRunRows && !wide) {
-                    const uint16_t run = rec.runs[(long long)r * kRunRows + row];
-                    cnt = run >> 8;
-                    f = rc.x + (run & 0xff);
-                } else {  // taller than the stored rows: recompute
-                    const float4 ga = rec.a[r];
-                    const float4 gb = rec.b[r];
-                    const KmEllipse el = km_ellipse(gb.x, gb.y, gb.z);
-                    cnt = km_row_run_fast(el, ga.x, ga.y, rc.x, rc.y, rc.z + row, tile_w,
-                                          tile_h, &f, &l);
-                }
-            }
-            int incl = cnt;
+        for (int y = y0; y <= y1; ++y) {
+            int f[8], n[8];
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int y = __shfl_up_sync(F, incl, d);
-                if (lane >= d) incl += y;
+            for (int ly = 0; ly < 8; ++ly) {
+                f[ly] = 0;
+                n[ly] = 0;
+                const int ty = y * sy + ly;
+                if (ly < sy && ty >= rc.z && ty <= rc.w)
+                    n[ly] = record_row_run(rec, r, rc, ty, tile_w, tile_h, &f[ly]);
             }
-            const int tot = __shfl_sync(F, incl, 31);
-            for (int t0 = 0; t0 < tot; t0 += 32) {
-                const int t = t0 + lane;
-                // first row j whose inclusive count exceeds t
-                int j = 0;
+            for (int x = x0; x <= x1; ++x) {
+                const int tx0 = x * sx;
+                unsigned m = 0;
 #pragma unroll
-                for (int step = 16; step > 0; step >>= 1) {
-                    const int cand = j + step - 1;
-                    const int v = __shfl_sync(F, incl, cand);
-                    if (v <= t) j += step;
+                for (int ly = 0; ly < 8; ++ly) {
+                    const int lo = max(f[ly], tx0), hi = min(f[ly] + n[ly], tx0 + sx);
+                    if (ly < sy && lo < hi) m |= ((1u << (hi - lo)) - 1u) << (lo - tx0 + ly * sx);
                 }
-                const int fj = __shfl_sync(F, f, j);
-                const int ej = __shfl_sync(F, incl - cnt, j);
-                const uint32_t pos = o + (uint32_t)t;
-                if (t < tot && pos < o_end) {
-                    keys[pos] = (uint32_t)(base_tile + (rc.z + r0 + j) * ntx + fj + (t - ej));
-                    vals[pos] = r;
-                }
+                keys[o] = (uint32_t)(V.super_base + y * V.nsx + x) | (m << 16);
+                vals[o] = r;
+                ++o;
             }
-            o += (uint32_t)tot;
         }
     }
 }
 
-cudaError_t launch_emit_keys(const uint32_t* order, const uint32_t* offsets, long long n_rec,
-                             const Records rec, const ViewDev* views, int n_views, int tile_w,
-                             int tile_h, int num_sms, uint32_t* keys, uint32_t* vals,
-                             cudaStream_t s) {
+cudaError_t launch_emit_supers(const uint32_t* order, const uint32_t* offsets, long long n_rec,
+                               const Records rec, const ViewDev* views, int n_views, int sx,
+                               int sy, int tile_w, int tile_h, int num_sms, uint32_t* keys,
+                               uint32_t* vals, cudaStream_t s) {
     if (n_rec <= 0) return cudaSuccess;
-    long long blocks = (n_rec + 7) / 8;
-    if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
+    long long blocks = div_up(n_rec, 256);
+    if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
     note_launch();
-    emit_keys_kernel<<<(int)blocks, 256, 0, s>>>(order, offsets, n_rec, rec, views, n_views,
-                                                 tile_w, tile_h, keys, vals);
+    emit_supers_kernel<<<(int)blocks, 256, 0, s>>>(order, offsets, n_rec, rec, views, n_views,
+                                                   sx, sy, tile_w, tile_h, keys, vals);
     return cudaGetLastError();
 }
 
-// ranges[t] = [first, last+1) of tile t in the sorted keys (ranges zeroed before).
-__global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys, long long n,
-                                   int2* __restrict__ ranges) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t t = keys[i];
-    if (i == 0 || keys[i - 1] != t) ranges[t].x = (int)i;
-    if (i == n - 1 || keys[i + 1] != t) ranges[t].y = (int)(i + 1);
+__device__ __forceinline__ int find_view_by_super(const ViewDev* views, int n_views, int sup) {
+    int lo = 0, hi = n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (views[mid].super_base <= sup) lo = mid; else hi = mid - 1;
+    }
+    return lo;
 }
 
-cudaError_t launch_tile_ranges(const uint32_t* keys, long long n_keys, int2* ranges,
-                               cudaStream_t s) {
-    if (n_keys <= 0) return cudaSuccess;
+// One block per super tile, one warp per tile of it (SX*SY = 16 warps). Each
+// chunk of the super tile's depth-ordered (key, record) list is loaded once
+// into shared memory; each warp takes the records whose mask bit is set for
+// its tile, in order. The counting pass writes the tiles' list lengths; after
+// their exclusive scan the writing pass appends the lists at the tiles'
+// offsets (never past cap) and writes the tiles' ranges.
+template <int SX, int SY, bool WRITE>
+__global__ void __launch_bounds__(SX * SY * 32)
+expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict__ skeys,
+                    const uint32_t* __restrict__ svals, const ViewDev* __restrict__ views,
+                    int n_views, uint32_t* __restrict__ tcount, const uint32_t* __restrict__ toff,
+                    uint32_t* __restrict__ vals, long long cap, int2* __restrict__ ranges) {
+    constexpr int NT = SX * SY * 32;
+    __shared__ uint32_t s_r[NT];
+    __shared__ uint16_t s_m[NT];
+    const int sup = blockIdx.x;
+    const ViewDev& V = views[find_view_by_super(views, n_views, sup)];
+    const int ls = sup - V.super_base;
+    const int tx0 = (ls % V.nsx) * SX, ty0 = (ls / V.nsx) * SY;
+    const int2 sr = sranges[sup];
+    const int b = sr.x, L = sr.y - sr.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tx = tx0 + warp % SX, ty = ty0 + warp / SX;
+    const bool valid = tx < V.ntx && ty < V.nty;
+    const int tile = V.tile_base + ty * V.ntx + tx;
+    const long long base = (WRITE && valid) ? (long long)toff[tile] : 0;
+    int count = 0;
+    for (int c0 = 0; c0 < L; c0 += NT) {
+        const int i = c0 + threadIdx.x;
+        if (i < L) {
+            s_m[threadIdx.x] = (uint16_t)(skeys[b + i] >> 16);
+            if (WRITE) s_r[threadIdx.x] = svals[b + i];
+        }
+        __syncthreads();
+        const int n = min(NT, L - c0);
+        if (valid) {
+            for (int j0 = 0; j0 < n; j0 += 32) {
+                const int j = j0 + lane;
+                const bool hit = j < n && ((s_m[j] >> warp) & 1u);
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                if (WRITE && hit) {
+                    const long long o = base + count + __popc(bal & ((1u << lane) - 1u));
+                    if (o < cap) vals[o] = s_r[j];
+                }
+                count += __popc(bal);
+            }
+        }
+        __syncthreads();
+    }
+    if (valid && lane == 0) {
+        if (WRITE) {
+            const long long e = base + count < cap ? base + count : cap;
+            ranges[tile] = make_int2((int)base, (int)e);
+        } else {
+            tcount[tile] = (uint32_t)count;
+        }
+    }
+}
+
+template <bool WRITE>
+static cudaError_t run_expand(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
+                              const ViewDev* views, int n_views, int total_supers, int tile_w,
+                              uint32_t* tcount, const uint32_t* toff, uint32_t* vals,
+                              long long cap, int2* ranges, cudaStream_t s) {
+    if (total_supers <= 0) return cudaSuccess;
     note_launch();
-    tile_ranges_kernel<<<div_up(n_keys, 256), 256, 0, s>>>(keys, n_keys, ranges);
+    if (tile_w == 32)
+        expand_tiles_kernel<2, 8, WRITE><<<total_supers, 512, 0, s>>>(
+            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges);
+    else
+        expand_tiles_kernel<4, 4, WRITE><<<total_supers, 512, 0, s>>>(
+            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
+                                int n_views, int total_supers, int tile_w, uint32_t* tcount,
+                                cudaStream_t s) {
+    return run_expand<false>(sranges, skeys, nullptr, views, n_views, total_supers, tile_w,
+                             tcount, nullptr, nullptr, 0, nullptr, s);
+}
+
+cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
+                                const ViewDev* views, int n_views, int total_supers, int tile_w,
+                                const uint32_t* toff, uint32_t* vals, long long cap, int2* ranges,
+                                cudaStream_t s) {
+    return run_expand<true>(sranges, skeys, svals, views, n_views, total_supers, tile_w,
+                            nullptr, toff, vals, cap, ranges, s);
+}
+
+// sranges[t] = [first, last+1) of super tile t (the low 16 key bits) in the
+// sorted super keys (sranges zeroed before).
+__global__ void super_ranges_kernel(const uint32_t* __restrict__ keys, long long n,
+                                    int2* __restrict__ ranges) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t t = keys[i] & 0xffffu;
+    if (i == 0 || (keys[i - 1] & 0xffffu) != t) ranges[t].x = (int)i;
+    if (i == n - 1 || (keys[i + 1] & 0xffffu) != t) ranges[t].y = (int)(i + 1);
+}
+
+cudaError_t launch_super_ranges(const uint32_t* keys, long long n, int2* ranges, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    note_launch();
+    super_ranges_kernel<<<div_up(n, 256), 256, 0, s>>>(keys, n, ranges);
     return cudaGetLastError();
 }
 

@@ -74,7 +74,7 @@ struct swgs_ctx {
     cudaStream_t last_stream = nullptr;
     // transient scratch
     Buf frames, block_cnt, scan_tmp, counts, order_a, order_b, tcount, koff, keys_a, keys_b,
-        vals_tmp, sort_tmp, counter, totals, l1_tab, reloc_w, reloc_cdf, reloc_dead, reloc_tg,
+        vals_tmp, vals_b, sranges, tile_cnt, tile_off, sort_tmp, counter, totals, l1_tab, reloc_w, reloc_cdf, reloc_dead, reloc_tg,
         reloc_cnt, reloc_nd;
     void* pinned = nullptr;
     size_t pinned_cap = 0;
@@ -281,7 +281,8 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
     B.h_groups.assign(F, GroupDev{});
     B.h_views.clear();
     B.call_index.clear();
-    long long act = 0, rec = 0, tiles = 0, pix = 0;
+    const int SX = super_w(tw), SY = super_h(tw);
+    long long act = 0, rec = 0, tiles = 0, supers = 0, pix = 0;
     for (int k = 0; k < F; ++k) {
         GroupDev& G = B.h_groups[k];
         G.frame = frames[k];
@@ -299,6 +300,9 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             V.ntx = (sv.width + tw - 1) / tw;
             V.nty = (sv.height + th - 1) / th;
             V.tile_base = (int)tiles;
+            V.nsx = (V.ntx + SX - 1) / SX;
+            V.nsy = (V.nty + SY - 1) / SY;
+            V.super_base = (int)supers;
             V.rec_base = (int)(rec + (long long)j * n_act[k]);
             V.n_rec = n_act[k];
             V.group = k;
@@ -319,6 +323,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             V.dL_out = dls ? dls[v] : nullptr;
             V.l1_scale = 1.0f / (3.0f * (float)sv.width * (float)sv.height * (float)n_views_total);
             tiles += (long long)V.ntx * V.nty;
+            supers += (long long)V.nsx * V.nsy;
             pix += (long long)sv.width * sv.height;
             B.h_views.push_back(V);
             B.call_index.push_back(v);
@@ -328,6 +333,9 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
     }
     if (rec > 0x7fffffffLL || tiles > 0x7fffffffLL)
         return fail(ctx, SWGS_EINVAL, "too many records (%lld) or tiles (%lld) in one batch", rec, tiles);
+    if (supers > kMaxSupersPerBatch)
+        return fail(ctx, SWGS_EINVAL, "%lld super tiles in one batch (at most %lld)", supers,
+                    kMaxSupersPerBatch);
     B.total_active = act;
     B.n_rec = rec;
     B.n_tiles = tiles;
@@ -379,49 +387,67 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             return fail(ctx, SWGS_ENOMEM, "allocation failed (scan)");
         {
             StageScope sc_(ctx, SWGS_STAGE_KEY_SCAN, s);
-            CK(launch_gather_tiles(order, rc.tiles, cnt, (long long)R, s));
+            CK(cudaMemsetAsync(ctx->totals.p, 0, 16, s));
+            CK(launch_gather_supers(order, rc, SX, SY, cnt,
+                                    P<unsigned long long>(ctx->totals) + 1, (long long)R, s));
             CK(exclusive_scan_u32(cnt, P<uint32_t>(ctx->koff), (long long)R, ctx->scan_tmp.p,
                                   P<unsigned long long>(ctx->totals), s));
         }
-        CK(cudaMemcpyAsync(ctx->pinned, ctx->totals.p, sizeof(unsigned long long),
+        CK(cudaMemcpyAsync(ctx->pinned, ctx->totals.p, 2 * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
-        unsigned long long nk = 0;
-        memcpy(&nk, ctx->pinned, sizeof(nk));
-        if (nk > 0x7fffffffULL)
-            return fail(ctx, SWGS_EINVAL, "%llu tile keys exceed the 2^31 limit of one batch", nk);
-        n_keys = (long long)nk;
+        unsigned long long tot[2] = {0, 0};
+        memcpy(tot, ctx->pinned, sizeof(tot));
+        if (tot[1] > 0x7fffffffULL || tot[0] > 0x7fffffffULL)
+            return fail(ctx, SWGS_EINVAL,
+                        "%llu tile keys (%llu super-tile keys) exceed the 2^31 limit of one "
+                        "batch; render fewer views per call", tot[1], tot[0]);
+        n_keys = (long long)tot[1];
         B.n_keys = n_keys;
-        // 4. keys, tile sort, ranges
-        const int tile_bits = ceil_log2(tiles);
-        const SortPlan tp = make_sort_plan(0, tile_bits);
-        const size_t K = (size_t)n_keys;
+        const long long n_sk = (long long)tot[0];
+        // 4. super-tile keys, their stable sort by super tile, per-tile lists
+        const SortPlan sp = make_sort_plan(0, ceil_log2(supers));
+        const size_t K = (size_t)n_sk;
         if (!ensure(ctx, ctx->keys_a, sizeof(uint32_t) * K, s) ||
             !ensure(ctx, ctx->keys_b, sizeof(uint32_t) * K, s) ||
             !ensure(ctx, ctx->vals_tmp, sizeof(uint32_t) * K, s) ||
-            !ensure(ctx, B.vals, sizeof(uint32_t) * K, s) ||
+            !ensure(ctx, ctx->vals_b, sizeof(uint32_t) * K, s) ||
+            !ensure(ctx, ctx->sranges, sizeof(int2) * (size_t)supers, s) ||
+            !ensure(ctx, B.vals, sizeof(uint32_t) * (size_t)n_keys, s) ||
+            !ensure(ctx, ctx->tile_cnt, sizeof(uint32_t) * (size_t)tiles, s) ||
+            !ensure(ctx, ctx->tile_off, sizeof(uint32_t) * (size_t)tiles, s) ||
+            !ensure(ctx, ctx->scan_tmp, scan_u32_temp_bytes(tiles) + 64, s) ||
             !ensure(ctx, ctx->sort_tmp, radix_temp_bytes((long long)K, ctx->num_sms), s))
             return fail(ctx, SWGS_ENOMEM, "allocation failed (keys)");
-        const bool odd = (tp.passes & 1) != 0;
-        uint32_t* ev = odd ? P<uint32_t>(ctx->vals_tmp) : P<uint32_t>(B.vals);
-        uint32_t* ov = odd ? P<uint32_t>(B.vals) : P<uint32_t>(ctx->vals_tmp);
         {
             StageScope sc_(ctx, SWGS_STAGE_EMIT, s);
-            CK(launch_emit_keys(order, P<uint32_t>(ctx->koff), (long long)R, rc,
-                                P<ViewDev>(B.views), (int)B.h_views.size(), tw, th,
-                                ctx->num_sms, P<uint32_t>(ctx->keys_a), ev, s));
+            CK(launch_emit_supers(order, P<uint32_t>(ctx->koff), (long long)R, rc,
+                                  P<ViewDev>(B.views), (int)B.h_views.size(), SX, SY, tw, th,
+                                  ctx->num_sms, P<uint32_t>(ctx->keys_a),
+                                  P<uint32_t>(ctx->vals_tmp), s));
         }
         bool kb = false;
         {
             StageScope sc_(ctx, SWGS_STAGE_TILE_SORT, s);
-            CK(radix_sort_pairs(P<uint32_t>(ctx->keys_a), ev, P<uint32_t>(ctx->keys_b), ov,
-                                (long long)K, tp, ctx->sort_tmp.p, ctx->num_sms, false, &kb, s));
+            CK(radix_sort_pairs(P<uint32_t>(ctx->keys_a), P<uint32_t>(ctx->vals_tmp),
+                                P<uint32_t>(ctx->keys_b), P<uint32_t>(ctx->vals_b), (long long)K,
+                                sp, ctx->sort_tmp.p, ctx->num_sms, false, &kb, s));
         }
         const uint32_t* skeys = kb ? P<uint32_t>(ctx->keys_b) : P<uint32_t>(ctx->keys_a);
+        const uint32_t* svals = kb ? P<uint32_t>(ctx->vals_b) : P<uint32_t>(ctx->vals_tmp);
         {
             StageScope sc_(ctx, SWGS_STAGE_RANGES, s);
-            CK(cudaMemsetAsync(B.ranges.p, 0, sizeof(int2) * (size_t)tiles, s));
-            CK(launch_tile_ranges(skeys, (long long)K, P<int2>(B.ranges), s));
+            CK(cudaMemsetAsync(ctx->sranges.p, 0, sizeof(int2) * (size_t)supers, s));
+            CK(launch_super_ranges(skeys, (long long)K, P<int2>(ctx->sranges), s));
+            CK(launch_expand_count(P<int2>(ctx->sranges), skeys, P<ViewDev>(B.views),
+                                   (int)B.h_views.size(), (int)supers, tw,
+                                   P<uint32_t>(ctx->tile_cnt), s));
+            CK(exclusive_scan_u32(P<uint32_t>(ctx->tile_cnt), P<uint32_t>(ctx->tile_off), tiles,
+                                  ctx->scan_tmp.p, P<unsigned long long>(ctx->totals) + 2, s));
+            CK(launch_expand_write(P<int2>(ctx->sranges), skeys, svals, P<ViewDev>(B.views),
+                                   (int)B.h_views.size(), (int)supers, tw,
+                                   P<uint32_t>(ctx->tile_off), P<uint32_t>(B.vals), n_keys,
+                                   P<int2>(B.ranges), s));
         }
     } else {
         B.n_keys = 0;
@@ -536,22 +562,21 @@ __global__ void export_record_kernel(int what, const ViewDev* views, int n_views
     }
 }
 
-__global__ void export_sorted_slot_kernel(const uint32_t* vals, long long n, const ViewDev* views,
-                                          int n_views, const GroupDev* groups, const int32_t* ids,
-                                          int32_t* out) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int r = (int)vals[k];
-    const int vi = find_view_by_record(views, n_views, r);
-    const ViewDev& V = views[vi];
-    out[k] = ids[groups[V.group].act_base + (r - V.rec_base)];
-}
-
-__global__ void export_ranges_kernel(const int2* ranges, long long n, int offset, int2* out) {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int2 r = ranges[t];
-    out[t] = make_int2(r.x + offset, r.y + offset);
+// The per-tile lists, compacted in tile order (CSR at coff), as slots: one
+// warp per tile.
+__global__ void export_lists_kernel(const int2* ranges, const int32_t* coff, long long n_tiles,
+                                    const uint32_t* vals, const ViewDev* views, int n_views,
+                                    const GroupDev* groups, const int32_t* ids, int32_t* out) {
+    const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= n_tiles) return;
+    const int2 rg = ranges[t];
+    const int o = coff[t];
+    for (int i = rg.x + lane; i < rg.y; i += 32) {
+        const int r = (int)vals[i];
+        const ViewDev& V = views[find_view_by_record(views, n_views, r)];
+        out[o + (i - rg.x)] = ids[groups[V.group].act_base + (r - V.rec_base)];
+    }
 }
 
 }  // namespace
@@ -614,7 +639,7 @@ void swgs_destroy(swgs_ctx* ctx) {
     cudaStreamSynchronize(s);
     Buf* bs[] = {&ctx->frames, &ctx->block_cnt, &ctx->scan_tmp, &ctx->counts, &ctx->order_a,
                  &ctx->order_b, &ctx->tcount, &ctx->koff, &ctx->keys_a, &ctx->keys_b,
-                 &ctx->vals_tmp, &ctx->sort_tmp, &ctx->counter, &ctx->totals, &ctx->l1_tab,
+                 &ctx->vals_tmp, &ctx->vals_b, &ctx->sranges, &ctx->tile_cnt, &ctx->tile_off, &ctx->sort_tmp, &ctx->counter, &ctx->totals, &ctx->l1_tab,
                  &ctx->reloc_w, &ctx->reloc_cdf, &ctx->reloc_dead, &ctx->reloc_tg,
                  &ctx->reloc_cnt, &ctx->reloc_nd};
     for (Buf* b : bs) ctx_free(ctx, *b, s);
@@ -756,7 +781,31 @@ static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32
     swgs_saved* sv = acquire_saved(ctx);
     sv->n_views = n_views;
     sv->count_pairs = ctx->cfg.count_pairs != 0;
-    const int nb = batched ? 1 : n_views;
+    // batches: one per view (plain), or consecutive runs of views holding at
+    // most kMaxSupersPerBatch super tiles each (batched)
+    std::vector<std::vector<int>> parts;
+    {
+        const int tw = ctx->cfg.tile_w, th = ctx->cfg.tile_h;
+        const int SX = super_w(tw), SY = super_h(tw);
+        long long acc = 0;
+        for (int v = 0; v < n_views; ++v) {
+            const long long ntx = (views[v].width + tw - 1) / tw, nty = (views[v].height + th - 1) / th;
+            const long long sup = ((ntx + SX - 1) / SX) * ((nty + SY - 1) / SY);
+            if (sup > kMaxSupersPerBatch) {
+                ctx->pool.push_back(sv);
+                return fail(ctx, SWGS_EINVAL,
+                            "view %d has %lld super tiles of %dx%d tiles (at most %lld): "
+                            "use larger tiles", v, sup, SX, SY, kMaxSupersPerBatch);
+            }
+            if (parts.empty() || !batched || acc + sup > kMaxSupersPerBatch) {
+                parts.emplace_back();
+                acc = 0;
+            }
+            parts.back().push_back(v);
+            acc += sup;
+        }
+    }
+    const int nb = (int)parts.size();
     if ((int)sv->batches.size() < nb) sv->batches.resize(nb);
     sv->n_batches = nb;
     unsigned long long* pairs = nullptr;
@@ -773,10 +822,7 @@ static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32
         }
     }
     for (int b = 0; b < nb; ++b) {
-        std::vector<int> idx;
-        if (batched) for (int v = 0; v < n_views; ++v) idx.push_back(v);
-        else idx.push_back(b);
-        st = render_batch(ctx, g, views, idx, bg, out_rgb, out_T, targets, dls, loss, n_views,
+        st = render_batch(ctx, g, views, parts[b], bg, out_rgb, out_T, targets, dls, loss, n_views,
                           sv->batches[b], pairs, s);
         if (st != SWGS_OK) {
             ctx->pool.push_back(sv);
@@ -927,22 +973,41 @@ swgs_status swgs_saved_export(swgs_ctx* ctx, const swgs_saved* saved, int32_t wh
                 CK(cudaMemcpyAsync(cur, B.grad2d.p, 48 * (size_t)m, cudaMemcpyDeviceToDevice, s));
                 break;
             case SWGS_EXPORT_SORTED_SLOT:
-                m = B.n_keys;
-                if (m == 0) break;
+            case SWGS_EXPORT_TILE_RANGES: {
+                // the lists live in per-tile regions of a capacity buffer;
+                // both exports give them compacted in tile order
+                m = what == SWGS_EXPORT_SORTED_SLOT ? B.n_keys : B.n_tiles;
+                if (m == 0 || B.n_tiles == 0) break;
+                std::vector<int2> hr((size_t)B.n_tiles);
+                CK(cudaMemcpyAsync(hr.data(), B.ranges.p, sizeof(int2) * hr.size(),
+                                   cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                std::vector<int32_t> coff(hr.size() + 1, 0);
+                for (size_t t = 0; t < hr.size(); ++t) coff[t + 1] = coff[t] + (hr[t].y - hr[t].x);
+                if (what == SWGS_EXPORT_TILE_RANGES) {
+                    std::vector<int2> cr(hr.size());
+                    for (size_t t = 0; t < hr.size(); ++t)
+                        cr[t] = make_int2((int)(coff[t] + key_off), (int)(coff[t + 1] + key_off));
+                    CK(cudaMemcpyAsync(cur, cr.data(), sizeof(int2) * cr.size(),
+                                       cudaMemcpyHostToDevice, s));
+                    CK(cudaStreamSynchronize(s));
+                    break;
+                }
+                Buf dco;
+                if (!ensure(ctx, dco, sizeof(int32_t) * coff.size(), s))
+                    return fail(ctx, SWGS_ENOMEM, "allocation failed");
+                CK(cudaMemcpyAsync(dco.p, coff.data(), sizeof(int32_t) * coff.size(),
+                                   cudaMemcpyHostToDevice, s));
                 note_launch();
-                export_sorted_slot_kernel<<<div_up(m, 256), 256, 0, s>>>(
-                    P<uint32_t>(B.vals), m, P<ViewDev>(B.views), (int)B.h_views.size(),
-                    P<GroupDev>(B.groups), P<int32_t>(B.ids), (int32_t*)cur);
+                export_lists_kernel<<<div_up(B.n_tiles * 32, 256), 256, 0, s>>>(
+                    P<int2>(B.ranges), P<int32_t>(dco), B.n_tiles, P<uint32_t>(B.vals),
+                    P<ViewDev>(B.views), (int)B.h_views.size(), P<GroupDev>(B.groups),
+                    P<int32_t>(B.ids), (int32_t*)cur);
                 CK(cudaGetLastError());
+                CK(cudaStreamSynchronize(s));
+                ctx_free(ctx, dco, s);
                 break;
-            case SWGS_EXPORT_TILE_RANGES:
-                m = B.n_tiles;
-                if (m == 0) break;
-                note_launch();
-                export_ranges_kernel<<<div_up(m, 256), 256, 0, s>>>(P<int2>(B.ranges), m,
-                                                                   (int)key_off, (int2*)cur);
-                CK(cudaGetLastError());
-                break;
+            }
             case SWGS_EXPORT_LAST:
                 m = B.n_pix;
                 CK(cudaMemcpyAsync(cur, B.last.p, 4 * (size_t)m, cudaMemcpyDeviceToDevice, s));

@@ -21,6 +21,8 @@ constexpr int kMaxShCoeffs = 16;  // degree 3
 struct ViewDev {
     int W, H, ntx, nty;
     int tile_base;     // first global tile id of this view inside its batch
+    int super_base;    // first global super-tile id of this view inside its batch
+    int nsx, nsy;      // super tiles across and down
     int rec_base;      // first record of this view
     int n_rec;         // records of this view (= active Gaussians of its frame)
     int group;         // frame group index
@@ -392,14 +394,26 @@ cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_
                              int num_sms, bool vals_iota, bool* in_b, cudaStream_t s);
 
 // k_keys.cu
-cudaError_t launch_gather_tiles(const uint32_t* order, const int32_t* tiles, uint32_t* out,
-                                long long n, cudaStream_t s);
-cudaError_t launch_emit_keys(const uint32_t* order, const uint32_t* offsets, long long n_rec,
-                             const Records rec, const ViewDev* views, int n_views, int tile_w,
-                             int tile_h, int num_sms, uint32_t* keys, uint32_t* vals,
-                             cudaStream_t s);
-cudaError_t launch_tile_ranges(const uint32_t* keys, long long n_keys, int2* ranges,
-                               cudaStream_t s);
+// Super tiles: SX x SY tiles (4 x 4, or 2 x 8 for 32x8 tiles); at most 2^16 per
+// batch (their ids share a 32-bit key with a 16-bit tile coverage mask).
+constexpr long long kMaxSupersPerBatch = 1 << 16;
+inline int super_w(int tile_w) { return tile_w == 32 ? 2 : 4; }
+inline int super_h(int tile_w) { return tile_w == 32 ? 8 : 4; }
+cudaError_t launch_gather_supers(const uint32_t* order, const Records rec, int sx, int sy,
+                                 uint32_t* out, unsigned long long* exact, long long n,
+                                 cudaStream_t s);
+cudaError_t launch_emit_supers(const uint32_t* order, const uint32_t* offsets, long long n_rec,
+                               const Records rec, const ViewDev* views, int n_views, int sx,
+                               int sy, int tile_w, int tile_h, int num_sms, uint32_t* keys,
+                               uint32_t* vals, cudaStream_t s);
+cudaError_t launch_super_ranges(const uint32_t* keys, long long n, int2* ranges, cudaStream_t s);
+cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
+                                int n_views, int total_supers, int tile_w, uint32_t* tcount,
+                                cudaStream_t s);
+cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
+                                const ViewDev* views, int n_views, int total_supers, int tile_w,
+                                const uint32_t* toff, uint32_t* vals, long long cap, int2* ranges,
+                                cudaStream_t s);
 
 // k_blend.cu
 struct BlendArgs {
