@@ -172,12 +172,17 @@ swgs_status swgs_frame_update(swgs_ctx *ctx, const swgs_gaussians *dst, int64_t 
  *   out_T[v] (optional, may be NULL or hold NULLs): device float[H*W] final
  *   transmittance.
  *   batched = 1: every stage runs once over all views; the blend is one
- *   persistent launch over all (view, tile) work items.
+ *   persistent launch over all (view, tile) work items. Views are taken in
+ *   consecutive batches of at most 2^16 super tiles (a super tile is 4x4 tiles,
+ *   2x8 for 32x8 tiles); one batch holds every view of typical calls.
  *   batched = 0: the plain method, each view through its own launches.
  *   saved: if non-NULL, receives the state the backward pass needs (final T,
  *   last-contributor index, sorted lists, 2D records); release it with
  *   swgs_saved_release. If NULL the call only renders.
- * The call synchronises the stream twice (to size the record and key buffers).
+ * The call synchronises the stream twice per batch (to size the record and key
+ * buffers). SWGS_EINVAL: bad sizes or pointers, more than the view limit, or a
+ * single view with more than 2^16 super tiles (with 8x8 tiles, views beyond
+ * about 8192 x 8192 pixels).
  */
 swgs_status swgs_render_fwd(swgs_ctx *ctx, const swgs_gaussians *g, int32_t n_views,
                             const swgs_view *views, const float *bg, float *const *out_rgb,
