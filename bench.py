@@ -312,8 +312,7 @@ def main():
     tgt_dev = [t.cuda() for t in tgt_host]
     tw, th = (int(x) for x in args.tile.split("x"))
     r = api.Renderer(tile=(tw, th), batch=args.batch, pixels_per_thread=args.ppt,
-                     bwd_pixels_per_thread=args.bwd_ppt, bwd_batch=args.bwd_batch,
-                     count_pairs=True)
+                     bwd_pixels_per_thread=args.bwd_ppt, bwd_batch=args.bwd_batch)
     reducer = None
     if world > 1:
         # one all-reduce of the flat gradient buffer (weighted by view share)
@@ -373,14 +372,18 @@ def main():
         ms = float(t.item())
     value = world * args.steps * mpix / (ms / 1e3)
 
-    # pair counts of this workload (one untimed forward)
-    _, saved = r.render(state, views, keep_saved=True)
+    # pair counts of this workload (one untimed forward with the counting blend)
+    rc = api.Renderer(tile=(tw, th), batch=args.batch, pixels_per_thread=args.ppt,
+                      bwd_pixels_per_thread=args.bwd_ppt, bwd_batch=args.bwd_batch,
+                      count_pairs=True)
+    _, saved = rc.render(state, views, keep_saved=True)
     info = saved.info()
     from paper_2409_07759_b300 import _abi
     pairs_fwd = int(info.pairs)
     pairs_bwd = int(saved.export(_abi.EXPORT_LAST).astype(np.int64).sum())
     n_keys, n_rec = int(info.n_keys), int(info.n_records)
     saved.release()
+    rc.close()
 
     extra = {}
     # ---- forward only, batched ----

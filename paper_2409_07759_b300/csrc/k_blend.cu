@@ -29,7 +29,8 @@ __device__ __forceinline__ void stage_gaussian(const Records& rec, uint32_t r, f
     const float4 B = rec.b[r];
     const float4 Cc = rec.c[r];
     *s0 = make_float4(A.x, A.y, __fmul_rn(B.x, -0.5f * kLog2e), __fmul_rn(B.y, -kLog2e));
-    *s1 = make_float4(__fmul_rn(B.z, -0.5f * kLog2e), __log2f(A.z), 0.f, 0.f);
+    const float lo = __log2f(A.z);
+    *s1 = make_float4(__fmul_rn(B.z, -0.5f * kLog2e), lo, pair_qmin(lo), 0.f);
     *s2 = Cc;
 }
 
@@ -40,7 +41,7 @@ struct TileGeom {
     static_assert(TH % PPT == 0, "pixels per thread must divide the tile height");
 };
 
-template <int TW, int TH, int BATCH, int PPT>
+template <int TW, int TH, int BATCH, int PPT, bool COUNT>
 __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
     constexpr int NT = TileGeom<TW, TH, PPT>::NT;
     __shared__ float4 s0[BATCH], s1[BATCH], s2[BATCH];
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
             for (int j = 0; j < cnt; ++j) {
                 if (__all_sync(F, tdone)) break;
                 const float4 g0 = s0[j];
-                const float2 g1 = *reinterpret_cast<const float2*>(&s1[j]);
+                const float4 g1 = s1[j];
                 const float4 c = s2[j];
                 const int pos = b0 + j, pos1 = pos - rg.x + 1;
 #pragma unroll
@@ -93,17 +94,17 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
                     float dx, dy, au;
                     const float q = pair_q(px, py[p], g0, g1.x, &dx, &dy);
                     const float al = pair_alpha(q, g1.y, &au);
-                    const bool ok = !done[p] && q >= kQMin && al >= kAlphaMin;
-                    const float tT = __fmul_rn(T[p], __fsub_rn(1.f, al));
-                    const bool stp = ok && tT < kTStop;
-                    const bool inc = ok && !stp;
-                    stop[p] = stp ? pos : stop[p];
-                    done[p] = done[p] || stp;
-                    const float w = inc ? __fmul_rn(al, T[p]) : 0.f;
+                    const bool ok = !done[p] && q >= g1.z;
+                    // T (1 - alpha), rounded once: the stopping test
+                    const float tT = __fmaf_rn(-al, T[p], T[p]);
+                    const bool inc = ok && tT >= kTStop;
+                    if (COUNT) stop[p] = (ok && !inc) ? pos : stop[p];
+                    done[p] = done[p] || (ok && !inc);
+                    const float w = __fmul_rn(inc ? al : 0.f, T[p]);
                     C0[p] = __fmaf_rn(c.x, w, C0[p]);
                     C1[p] = __fmaf_rn(c.y, w, C1[p]);
                     C2[p] = __fmaf_rn(c.z, w, C2[p]);
-                    T[p] = inc ? tT : T[p];
+                    T[p] = __fsub_rn(T[p], w);
                     last[p] = inc ? pos1 : last[p];
                 }
                 tdone = true;
@@ -125,7 +126,8 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
                 if (V.out_T) V.out_T[q] = T[p];
                 if (a.T) a.T[V.pix_base + q] = T[p];
                 if (a.last) a.last[V.pix_base + q] = last[p];
-                pairs += (unsigned long long)((stop[p] < rg.y ? stop[p] + 1 : rg.y) - rg.x);
+                if (COUNT)
+                    pairs += (unsigned long long)((stop[p] < rg.y ? stop[p] + 1 : rg.y) - rg.x);
                 if (V.target) {
                     // L1 term of the loss and its gradient, sign(0) = 0
                     const float e0 = r0 - V.target[q], e1 = r1 - V.target[hw + q],
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
         for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(F, l1, o);
         if ((tid & 31) == 0 && l1 != 0.f) atomicAdd(a.loss, l1);
     }
-    if (a.pairs) {
+    if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(F, pairs, o);
         if ((tid & 31) == 0 && pairs) atomicAdd(a.pairs, pairs);
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                 const int pos = b0 + j - rg.x;
                 if (__all_sync(F, pos >= mylast)) continue;
                 const float4 g0 = s0[j];
-                const float2 g1 = *reinterpret_cast<const float2*>(&s1[j]);
+                const float4 g1 = s1[j];
                 const float4 c = s2[j];
                 // The thread's pixels share x, so dx is common to them: only
                 // sum gm, sum gm dy and sum gm dy^2 run per pixel; the dx terms
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                     float dy, au;
                     const float q = pair_q(px, py[p], g0, g1.x, &dx, &dy);
                     const float al = pair_alpha(q, g1.y, &au);
-                    const bool ok = pos < last[p] && q >= kQMin && al >= kAlphaMin;
+                    const bool ok = pos < last[p] && q >= g1.z;
                     any |= ok;
                     // T before this Gaussian, recovered from the T after it
                     T[p] = ok ? __fdividef(T[p], __fsub_rn(1.f, al)) : T[p];
@@ -326,7 +328,10 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
 template <int TW, int TH, int BATCH, int PPT>
 static cudaError_t run_fwd(const BlendArgs& a, int grid, cudaStream_t s) {
     note_launch();
-    blend_fwd_kernel<TW, TH, BATCH, PPT><<<grid, TW * TH / PPT, 0, s>>>(a);
+    if (a.pairs)
+        blend_fwd_kernel<TW, TH, BATCH, PPT, true><<<grid, TW * TH / PPT, 0, s>>>(a);
+    else
+        blend_fwd_kernel<TW, TH, BATCH, PPT, false><<<grid, TW * TH / PPT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -340,7 +345,7 @@ static cudaError_t run_bwd(const BlendArgs& a, int grid, cudaStream_t s) {
 template <int TW, int TH, int BATCH, int PPT>
 static int occ_fwd() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_fwd_kernel<TW, TH, BATCH, PPT>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_fwd_kernel<TW, TH, BATCH, PPT, false>,
                                                   TW * TH / PPT, 0);
     return n < 1 ? 1 : n;
 }

@@ -75,6 +75,8 @@ constexpr float kGuard = 1.3f;
 // m <= 9 written in the log2 domain q = -m/2 * log2(e)
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kQMin = -4.5f * 1.4426950408889634f;
+// alpha >= 1/255 written in the log2 domain: q + log2(o) >= log2(1/255)
+constexpr float kLog2AlphaMin = -7.99435343685885793f;
 constexpr float kLn2 = 0.6931471805599453f;
 
 // ---------------------------------------------------------------------------
@@ -298,6 +300,13 @@ __device__ __forceinline__ float pair_q(float px, float py, float4 g0, float qc,
     *dx = ddx;
     *dy = ddy;
     return __fmaf_rn(t1, ddx, t2);
+}
+
+// Per-Gaussian lower bound on q for a pair to count: m <= 9 and alpha >= 1/255
+// (alpha = min(0.99, 2^(q + lo)) with lo = log2(o)). Both blends test q
+// against it, so their decisions agree exactly.
+__device__ __forceinline__ float pair_qmin(float lo) {
+    return fmaxf(kQMin, __fsub_rn(kLog2AlphaMin, lo));
 }
 
 __device__ __forceinline__ float pair_alpha(float q, float lo, float* au) {
