@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--views", type=int, default=4, help="cameras per frame")
     ap.add_argument("--frames", type=int, default=10)
     ap.add_argument("--tile", default="16x16", help="blend tile, WxH")
-    ap.add_argument("--batch", type=int, default=256, help="Gaussians staged per block step")
+    ap.add_argument("--batch", type=int, default=128, help="Gaussians staged per block step")
     ap.add_argument("--ppt", type=int, default=2, help="forward blend pixels per thread")
     ap.add_argument("--bwd-ppt", type=int, default=8, help="reverse blend pixels per thread")
     ap.add_argument("--bwd-batch", type=int, default=128, help="reverse blend staging batch")

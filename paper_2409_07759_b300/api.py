@@ -192,7 +192,7 @@ class Renderer:
     """One libswgs context (tile shape, batch size, near plane). Scratch memory
     comes from torch's caching allocator through the library's callbacks."""
 
-    def __init__(self, tile=(16, 16), batch=256, near_plane=0.2, blocks_per_sm=0,
+    def __init__(self, tile=(16, 16), batch=128, near_plane=0.2, blocks_per_sm=0,
                  count_pairs=False, pixels_per_thread=2, bwd_pixels_per_thread=None,
                  bwd_batch=128, use_torch_allocator=True):
         if bwd_pixels_per_thread is None:  # 8x8 tiles hold at most 2 pixels per thread

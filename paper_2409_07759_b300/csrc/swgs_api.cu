@@ -592,7 +592,7 @@ swgs_status swgs_default_config(swgs_config* cfg) {
     if (!cfg) return SWGS_EINVAL;
     cfg->tile_w = 16;
     cfg->tile_h = 16;
-    cfg->batch = 256;
+    cfg->batch = 128;
     cfg->near_plane = 0.2f;
     cfg->blocks_per_sm = 0;
     cfg->count_pairs = 0;
