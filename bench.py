@@ -382,6 +382,7 @@ def main():
     pairs_fwd = int(info.pairs)
     pairs_bwd = int(saved.export(_abi.EXPORT_LAST).astype(np.int64).sum())
     n_keys, n_rec = int(info.n_keys), int(info.n_records)
+    n_sort_keys, n_supers = int(info.n_sort_keys), int(info.n_supers)
     saved.release()
     rc.close()
 
@@ -427,13 +428,17 @@ def main():
         extra["batched_over_plain"] = (ms / args.steps) and (pms / (ms / args.steps))
 
     # ---- end to end through the public API with host buffers ----
-    h2d = sum(t.numel() * 4 for t in tgt_host) + slice_bytes
+    # Every step's targets are copied from pinned host memory (on a side stream,
+    # overlapping the previous step's compute), its slice is streamed in from
+    # pinned host memory, and its loss is read back to the host.
+    h2d = sum(t.numel() * t.element_size() for t in tgt_host) + slice_bytes
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    tr.prefetch_targets(tgt_host)
     for k in range(args.steps):
-        for d, h in zip(tgt_dev, tgt_host):
-            d.copy_(h, non_blocking=True)
-        loss = tr.step(20_000 + k, update=upd(k))
+        loss = tr.step(20_000 + k, update=upd(k), prefetched=True)
+        if k + 1 < args.steps:
+            tr.prefetch_targets(tgt_host)
         float(loss.item())
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -445,14 +450,18 @@ def main():
     sm_count = torch.cuda.get_device_properties(0).multi_processor_count
     clk = (clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0))
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-    tile_passes = math.ceil(math.ceil(math.log2(max(2, sum(
-        ((v.width + tw - 1) // tw) * ((v.height + th - 1) // th) for v in views)))) / 9)
+    # the list sort orders (super tile, record) keys: ceil(bits / 9) digit passes
+    sort_passes = math.ceil(math.ceil(math.log2(max(2, n_supers))) / 9)
     stage_cost = {
         "blend_fwd": ("alu", FLOP_PER_PAIR_FWD * pairs_fwd / 1e12, "TFLOP/s"),
         "blend_bwd": ("alu", FLOP_PER_PAIR_BWD * pairs_bwd / 1e12, "TFLOP/s"),
-        "tile_sort": ("hbm", 16.0 * tile_passes * n_keys / 1e9, "GB/s"),
+        "tile_sort": ("hbm", 16.0 * sort_passes * n_sort_keys / 1e9, "GB/s"),
         "depth_sort": ("hbm", 16.0 * 4 * n_rec / 1e9, "GB/s"),
-        "emit": ("hbm", (8.0 * n_keys + 16.0 * n_rec) / 1e9, "GB/s"),
+        # super keys written, record rectangles and row runs read
+        "emit": ("hbm", (8.0 * n_sort_keys + 80.0 * n_rec) / 1e9, "GB/s"),
+        # super ranges (4 B/key), count pass (4 B/key), write pass (8 B/key
+        # read, 4 B per tile-list entry written)
+        "ranges": ("hbm", (16.0 * n_sort_keys + 4.0 * n_keys) / 1e9, "GB/s"),
         "preprocess": ("hbm", (236.0 * n_rec / args.views + 64.0 * n_rec) / 1e9, "GB/s"),
         "preprocess_bwd": ("hbm", (236.0 * 2 * n_rec / args.views + 48.0 * n_rec) / 1e9, "GB/s"),
     }
@@ -519,6 +528,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
             "pairs_fwd": pairs_fwd, "pairs_bwd": pairs_bwd, "keys": n_keys, "records": n_rec,
+            "sort_keys": n_sort_keys, "super_tiles": n_supers,
             "stages": stages,
             **extra,
         }

@@ -27,7 +27,7 @@
 extern "C" {
 #endif
 
-#define SWGS_ABI_VERSION 1
+#define SWGS_ABI_VERSION 2
 
 typedef enum swgs_status {
     SWGS_OK = 0,
@@ -226,6 +226,8 @@ typedef struct swgs_saved_info {
     int64_t n_tiles;       /* tiles over all views */
     int64_t n_pixels;      /* pixels over all views */
     int64_t pairs;         /* evaluated (pixel, Gaussian) pairs (count_pairs = 1) */
+    int64_t n_sort_keys;   /* (super tile, Gaussian) keys sorted to build the tile lists */
+    int64_t n_supers;      /* super tiles over all views */
 } swgs_saved_info;
 
 swgs_status swgs_saved_query(swgs_ctx *ctx, const swgs_saved *saved, swgs_saved_info *info);

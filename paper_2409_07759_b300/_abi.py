@@ -54,7 +54,7 @@ class SwgsView(C.Structure):
 class SwgsSavedInfo(C.Structure):
     _fields_ = [("n_views", C.c_int32), ("n_batches", C.c_int32), ("n_records", C.c_int64),
                 ("n_keys", C.c_int64), ("n_tiles", C.c_int64), ("n_pixels", C.c_int64),
-                ("pairs", C.c_int64)]
+                ("pairs", C.c_int64), ("n_sort_keys", C.c_int64), ("n_supers", C.c_int64)]
 
 
 class SwgsSgldParams(C.Structure):
@@ -130,6 +130,10 @@ PROTOTYPES = [
 _lib = None
 
 
+# The struct layouts above mirror include/swgs.h at this SWGS_ABI_VERSION.
+ABI_VERSION = 2
+
+
 def load():
     """Load libswgs.so (raises if it is missing -- there is no CPU fallback)."""
     global _lib
@@ -142,6 +146,9 @@ def load():
             f = getattr(lib, name)
             f.restype = res
             f.argtypes = args
+        if lib.swgs_abi_version() != ABI_VERSION:
+            raise RuntimeError(f"libswgs.so has ABI version {lib.swgs_abi_version()}, this "
+                               f"binding mirrors version {ABI_VERSION}: rebuild the library")
         _lib = lib
     return _lib
 

@@ -44,6 +44,7 @@ struct Buf {
 struct BatchState {
     int n_views = 0, n_groups = 0;
     long long total_active = 0, n_rec = 0, n_keys = 0, n_tiles = 0, n_pix = 0;
+    long long n_sort_keys = 0, n_supers = 0;
     std::vector<ViewDev> h_views;   // table order (grouped by frame)
     std::vector<GroupDev> h_groups;
     std::vector<int> call_index;    // table entry -> index in the call's view list
@@ -339,6 +340,8 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
     B.total_active = act;
     B.n_rec = rec;
     B.n_tiles = tiles;
+    B.n_supers = supers;
+    B.n_sort_keys = 0;
     B.n_pix = pix;
     const size_t R = (size_t)rec;
     if (!ensure(ctx, B.views, sizeof(ViewDev) * B.h_views.size(), s) ||
@@ -405,6 +408,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
         n_keys = (long long)tot[1];
         B.n_keys = n_keys;
         const long long n_sk = (long long)tot[0];
+        B.n_sort_keys = n_sk;
         // 4. super-tile keys, their stable sort by super tile, per-tile lists
         const SortPlan sp = make_sort_plan(0, ceil_log2(supers));
         const size_t K = (size_t)n_sk;
@@ -877,6 +881,8 @@ swgs_status swgs_saved_query(swgs_ctx* ctx, const swgs_saved* saved, swgs_saved_
         o.n_keys += B.n_keys;
         o.n_tiles += B.n_tiles;
         o.n_pixels += B.n_pix;
+        o.n_sort_keys += B.n_sort_keys;
+        o.n_supers += B.n_supers;
     }
     if (saved->count_pairs && saved->pairs.p) {
         cudaStream_t s = ctx->last_stream;

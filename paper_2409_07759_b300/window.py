@@ -62,12 +62,44 @@ class WindowTrainer:
             self.adam["v_" + k] = b
         self.images = [torch.empty((3, vw.height, vw.width), dtype=torch.float32, device="cuda")
                        for vw in self.views]
+        # host-input pipeline: two target buffers, the back one filled on a side
+        # stream while a step reads the front one
+        self._bufs = None
+        self._front = 0
+        self._copy_stream = None
+        self._copied = None      # event: the back buffer is filled
+        self._released = None    # per buffer: the last step reading it has ended
         self.dl = [torch.empty_like(i) for i in self.images]
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
 
-    def step(self, step: int, update: Optional[tuple] = None, render_only: bool = False):
+    def prefetch_targets(self, host_targets: Sequence[torch.Tensor]):
+        """Start copying the next step's targets from pinned host memory into a
+        back buffer on a side stream, so that the copy overlaps the step in
+        flight; the next step(..., prefetched=True) waits for it and uses it."""
+        if self._bufs is None:
+            self._bufs = [self.targets, [torch.empty_like(t) for t in self.targets]]
+            self._front = 0
+            self._copy_stream = torch.cuda.Stream()
+            self._copied = torch.cuda.Event()
+            self._released = [torch.cuda.Event(), torch.cuda.Event()]
+            for e in self._released:
+                e.record()
+        back = 1 - self._front
+        with torch.cuda.stream(self._copy_stream):
+            self._copy_stream.wait_event(self._released[back])
+            for d, h in zip(self._bufs[back], host_targets):
+                d.copy_(h, non_blocking=True)
+            self._copied.record(self._copy_stream)
+
+    def step(self, step: int, update: Optional[tuple] = None, render_only: bool = False,
+             prefetched: bool = False):
         """One training step. update = (first_slot, pinned host dict) streams a
-        slice in before rendering. Returns the (device) loss tensor."""
+        slice in before rendering; prefetched = True takes the targets from the
+        last prefetch_targets call. Returns the (device) loss tensor."""
+        if prefetched:
+            torch.cuda.current_stream().wait_event(self._copied)
+            self._front = 1 - self._front
+            self.targets = self._bufs[self._front]
         if update is not None:
             first, host = update
             self.r.frame_update(self.state, first, host, src_on_host=True)
@@ -86,4 +118,6 @@ class WindowTrainer:
             self.reduce(self._gflat, self.loss)
         self.r.sgld_step(self.state, self.frames, self.params, self.seed, step,
                          grads=self.grads, adam=self.adam)
+        if self._bufs is not None:
+            self._released[self._front].record()
         return self.loss
