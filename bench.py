@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--ppt", type=int, default=2, help="forward blend pixels per thread")
     ap.add_argument("--bwd-ppt", type=int, default=8, help="reverse blend pixels per thread")
     ap.add_argument("--bwd-batch", type=int, default=128, help="reverse blend staging batch")
+    ap.add_argument("--targets", default="u8", choices=["u8", "f32"],
+                    help="target frames: 8-bit (k/255) or float32")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--viewers", type=int, default=64)
     ap.add_argument("--rate", type=float, default=30.0, help="requests/s per viewer")
@@ -308,6 +310,11 @@ def main():
     scene, views, targets = build_workload(args, rank=rank)
     mpix = sum(v.width * v.height for v in views) / 1e6
     state = api.GaussianState.from_scene(scene)
+    if args.targets == "u8":  # 8-bit frames, the form video targets come in
+        targets = [np.rint(t * 255.0).astype(np.uint8) for t in targets]
+        oracle_targets = [t.astype(np.float32) * np.float32(1.0 / 255.0) for t in targets]
+    else:
+        oracle_targets = targets
     tgt_host = [torch.from_numpy(t).pin_memory() for t in targets]
     tgt_dev = [t.cuda() for t in tgt_host]
     tw, th = (int(x) for x in args.tile.split("x"))
@@ -503,7 +510,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        rate, cores, sample = cpu_oracle_sample(scene, views, targets, budget_s=15.0)
+        rate, cores, sample = cpu_oracle_sample(scene, views, oracle_targets, budget_s=15.0)
         cpu = {"value": rate, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
                "sample": sample}
 
@@ -521,6 +528,8 @@ def main():
                        "mpix_per_step": mpix, "tile": args.tile, "batch": args.batch,
                        "pixels_per_thread": args.ppt,
                        "bwd_pixels_per_thread": args.bwd_ppt, "bwd_batch": args.bwd_batch,
+                       "targets": ("8-bit RGB frames (k/255)" if args.targets == "u8"
+                                   else "float32 RGB"),
                        "parallelism": f"dp{world}", "l2": "flushed (256 MB write) before each step"},
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -203,6 +203,18 @@ swgs_status swgs_render_fwd_l1(swgs_ctx *ctx, const swgs_gaussians *g, int32_t n
                                swgs_saved **saved, void *stream);
 
 /*
+ * swgs_render_fwd_l1 with 8-bit targets (the form video frames arrive in):
+ * target[v] is device uint8_t[3*H*W] planar, read as k * (1/255) in FP32
+ * (within one ulp of k / 255). Same outputs, errors and ownership otherwise.
+ */
+swgs_status swgs_render_fwd_l1_u8(swgs_ctx *ctx, const swgs_gaussians *g, int32_t n_views,
+                                  const swgs_view *views, const float *bg,
+                                  float *const *out_rgb, float *const *out_T,
+                                  const uint8_t *const *target, float *const *dL_drgb,
+                                  float *loss, int32_t batched, swgs_saved **saved,
+                                  void *stream);
+
+/*
  * Backward of swgs_render_fwd (Alg. 1 loss.backward): given dL/drgb[v]
  * (device float[3*H*W] planar, same views as the saved forward), ACCUMULATES
  * into grads (device arrays with g's layout: means, log_scales, quats,

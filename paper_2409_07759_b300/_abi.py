@@ -106,6 +106,12 @@ PROTOTYPES = [
                                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p,
                                      C.c_int32, C.POINTER(C.c_void_p), C.c_void_p]),
+    ("swgs_render_fwd_l1_u8", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_int32,
+                                        C.POINTER(SwgsView), C.POINTER(C.c_float),
+                                        C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                        C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                        C.c_void_p, C.c_int32, C.POINTER(C.c_void_p),
+                                        C.c_void_p]),
     ("swgs_render_bwd", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_void_p,
                                   C.POINTER(C.c_void_p), C.POINTER(SwgsGaussians), C.c_void_p]),
     ("swgs_saved_release", C.c_int, [C.c_void_p, C.c_void_p]),

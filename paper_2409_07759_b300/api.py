@@ -301,8 +301,16 @@ class Renderer:
                   batched=True, keep_saved=True, out=None, dL_out=None, loss_out=None,
                   stream=None):
         """Forward render fused with the L1 term: returns (images, dL/drgb, loss,
-        saved)."""
+        saved). targets: float32 [3,H,W] per view, or uint8 [3,H,W] (8-bit
+        frames, read as k * (1/255) in FP32)."""
         cviews = _views_array(views)
+        dts = {t.dtype for t in targets}
+        if len(dts) != 1 or dts.pop() not in (torch.float32, torch.uint8):
+            raise ValueError("targets must all be float32 or all uint8")
+        u8 = targets[0].dtype == torch.uint8
+        for t, v in zip(targets, cviews):
+            if not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != (3, v.height, v.width):
+                raise ValueError("each target must be a contiguous CUDA [3, H, W] tensor")
         if out is None:
             out = [torch.empty((3, v.height, v.width), dtype=torch.float32, device="cuda")
                    for v in cviews]
@@ -313,7 +321,8 @@ class Renderer:
         bgv = (C.c_float * 3)(*[float(x) for x in bg])
         handle = C.c_void_p()
         g = state.c_struct()
-        self._check(_abi.load().swgs_render_fwd_l1(
+        fn = _abi.load().swgs_render_fwd_l1_u8 if u8 else _abi.load().swgs_render_fwd_l1
+        self._check(fn(
             self.ctx, C.byref(g), len(cviews), cviews, bgv, _ptr_array(out), None,
             _ptr_array(targets), _ptr_array(dL_out), _ptr(loss_out), int(bool(batched)),
             C.byref(handle) if keep_saved else None, self._stream(stream)))

@@ -128,10 +128,20 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
                 if (a.last) a.last[V.pix_base + q] = last[p];
                 if (COUNT)
                     pairs += (unsigned long long)((stop[p] < rg.y ? stop[p] + 1 : rg.y) - rg.x);
-                if (V.target) {
+                if (V.target || V.target_u8) {
                     // L1 term of the loss and its gradient, sign(0) = 0
-                    const float e0 = r0 - V.target[q], e1 = r1 - V.target[hw + q],
-                                e2 = r2 - V.target[2 * hw + q];
+                    float t0, t1, t2;
+                    if (V.target_u8) {  // k x (1/255) in FP32
+                        constexpr float kInv255 = 1.0f / 255.0f;
+                        t0 = __fmul_rn((float)V.target_u8[q], kInv255);
+                        t1 = __fmul_rn((float)V.target_u8[hw + q], kInv255);
+                        t2 = __fmul_rn((float)V.target_u8[2 * hw + q], kInv255);
+                    } else {
+                        t0 = V.target[q];
+                        t1 = V.target[hw + q];
+                        t2 = V.target[2 * hw + q];
+                    }
+                    const float e0 = r0 - t0, e1 = r1 - t1, e2 = r2 - t2;
                     const float s = V.l1_scale;
                     V.dL_out[q] = e0 > 0.f ? s : (e0 < 0.f ? -s : 0.f);
                     V.dL_out[hw + q] = e1 > 0.f ? s : (e1 < 0.f ? -s : 0.f);

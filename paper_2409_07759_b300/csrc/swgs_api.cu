@@ -234,7 +234,8 @@ int ceil_log2(long long x) {
 // Render one batch of views (indices idx[] into the call's view list).
 swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view* views,
                          const std::vector<int>& idx, const float* bg, float* const* out_rgb,
-                         float* const* out_T, const float* const* targets, float* const* dls,
+                         float* const* out_T, const void* const* targets, int target_u8,
+                         float* const* dls,
                          float* loss, int n_views_total, BatchState& B,
                          unsigned long long* pairs, cudaStream_t s) {
     const int tw = ctx->cfg.tile_w, th = ctx->cfg.tile_h;
@@ -320,7 +321,8 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             V.out_rgb = out_rgb[v];
             V.out_T = out_T ? out_T[v] : nullptr;
             V.dL = nullptr;
-            V.target = targets ? targets[v] : nullptr;
+            V.target = (targets && !target_u8) ? (const float*)targets[v] : nullptr;
+            V.target_u8 = (targets && target_u8) ? (const uint8_t*)targets[v] : nullptr;
             V.dL_out = dls ? dls[v] : nullptr;
             V.l1_scale = 1.0f / (3.0f * (float)sv.width * (float)sv.height * (float)n_views_total);
             tiles += (long long)V.ntx * V.nty;
@@ -734,15 +736,33 @@ swgs_status swgs_frame_update(swgs_ctx* ctx, const swgs_gaussians* dst, int64_t 
 static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
                                    const swgs_view* views, const float* bg,
                                    float* const* out_rgb, float* const* out_T,
-                                   const float* const* targets, float* const* dls, float* loss,
+                                   const void* const* targets, int target_u8,
+                                   float* const* dls, float* loss,
                                    int32_t batched, swgs_saved** saved, void* stream);
 
 swgs_status swgs_render_fwd(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
                             const swgs_view* views, const float* bg, float* const* out_rgb,
                             float* const* out_T, int32_t batched, swgs_saved** saved,
                             void* stream) {
-    return render_fwd_impl(ctx, g, n_views, views, bg, out_rgb, out_T, nullptr, nullptr, nullptr,
-                           batched, saved, stream);
+    return render_fwd_impl(ctx, g, n_views, views, bg, out_rgb, out_T, nullptr, 0, nullptr,
+                           nullptr, batched, saved, stream);
+}
+
+static swgs_status render_fwd_l1_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
+                                      const swgs_view* views, const float* bg,
+                                      float* const* out_rgb, float* const* out_T,
+                                      const void* const* target, int target_u8,
+                                      float* const* dL_drgb, float* loss, int32_t batched,
+                                      swgs_saved** saved, void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    if (!target || !dL_drgb || !loss) return fail(ctx, SWGS_EINVAL, "null target, dL or loss");
+    if (n_views > 0 && !views) return fail(ctx, SWGS_EINVAL, "null view list");
+    for (int v = 0; v < n_views; ++v)
+        if (!target[v] || !dL_drgb[v]) return fail(ctx, SWGS_EINVAL, "view %d: null target or dL", v);
+    if (cudaMemsetAsync(loss, 0, sizeof(float), (cudaStream_t)stream) != cudaSuccess)
+        return fail(ctx, SWGS_ECUDA, "clearing the loss failed");
+    return render_fwd_impl(ctx, g, n_views, views, bg, out_rgb, out_T, target, target_u8,
+                           dL_drgb, loss, batched, saved, stream);
 }
 
 swgs_status swgs_render_fwd_l1(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
@@ -750,20 +770,26 @@ swgs_status swgs_render_fwd_l1(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n
                                float* const* out_T, const float* const* target,
                                float* const* dL_drgb, float* loss, int32_t batched,
                                swgs_saved** saved, void* stream) {
-    if (!ctx) return SWGS_EINVAL;
-    if (!target || !dL_drgb || !loss) return fail(ctx, SWGS_EINVAL, "null target, dL or loss");
-    for (int v = 0; v < n_views; ++v)
-        if (!target[v] || !dL_drgb[v]) return fail(ctx, SWGS_EINVAL, "view %d: null target or dL", v);
-    if (cudaMemsetAsync(loss, 0, sizeof(float), (cudaStream_t)stream) != cudaSuccess)
-        return fail(ctx, SWGS_ECUDA, "clearing the loss failed");
-    return render_fwd_impl(ctx, g, n_views, views, bg, out_rgb, out_T, target, dL_drgb, loss,
-                           batched, saved, stream);
+    return render_fwd_l1_impl(ctx, g, n_views, views, bg, out_rgb, out_T,
+                              (const void* const*)target, 0, dL_drgb, loss, batched, saved,
+                              stream);
+}
+
+swgs_status swgs_render_fwd_l1_u8(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
+                                  const swgs_view* views, const float* bg, float* const* out_rgb,
+                                  float* const* out_T, const uint8_t* const* target,
+                                  float* const* dL_drgb, float* loss, int32_t batched,
+                                  swgs_saved** saved, void* stream) {
+    return render_fwd_l1_impl(ctx, g, n_views, views, bg, out_rgb, out_T,
+                              (const void* const*)target, 1, dL_drgb, loss, batched, saved,
+                              stream);
 }
 
 static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
                                    const swgs_view* views, const float* bg,
                                    float* const* out_rgb, float* const* out_T,
-                                   const float* const* targets, float* const* dls, float* loss,
+                                   const void* const* targets, int target_u8,
+                                   float* const* dls, float* loss,
                                    int32_t batched, swgs_saved** saved, void* stream) {
     if (!ctx) return SWGS_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
@@ -826,7 +852,8 @@ static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32
         }
     }
     for (int b = 0; b < nb; ++b) {
-        st = render_batch(ctx, g, views, parts[b], bg, out_rgb, out_T, targets, dls, loss, n_views,
+        st = render_batch(ctx, g, views, parts[b], bg, out_rgb, out_T, targets, target_u8, dls,
+                          loss, n_views,
                           sv->batches[b], pairs, s);
         if (st != SWGS_OK) {
             ctx->pool.push_back(sv);

@@ -36,6 +36,7 @@ struct ViewDev {
     float* out_T;      // [H,W] or null
     const float* dL;   // [3,H,W] (backward only)
     const float* target;  // [3,H,W] (forward fused with the L1 term) or null
+    const uint8_t* target_u8;  // or [3,H,W] 8-bit, value k / 255
     float* dL_out;        // [3,H,W] written with the L1 gradient (fused forward)
     float l1_scale;       // 1 / (3 H W V)
 };

@@ -276,6 +276,27 @@ def test_autograd_function(R, oracle_mod):
     compare_grads({k: _np(p.grad) for k, p in zip(api.PARAM_NAMES, params)}, ref)
 
 
+def test_fused_forward_l1_u8_targets(R):
+    """8-bit targets give the same image, dL/dC and loss as the float
+    targets k * (1/255) (FP32 product, as the kernel reads them)."""
+    sc, views, targets = synth.config1()
+    st = _state(sc)
+    rng = np.random.default_rng(11)
+    t8 = [rng.integers(0, 256, size=t.shape, dtype=np.uint8) for t in targets]
+    tu = [torch.from_numpy(t).cuda() for t in t8]
+    inv = torch.tensor(1.0 / 255.0, dtype=torch.float32, device="cuda")
+    tf = [t.float() * inv for t in tu]
+    ia, da, la, sa = R.render_l1(st, views, tu)
+    ib, db, lb, sb = R.render_l1(st, views, tf)
+    sa.release()
+    sb.release()
+    for x, y in zip(ia + da, ib + db):
+        assert torch.equal(x, y)
+    assert float(la.item()) == pytest.approx(float(lb.item()), rel=1e-5)
+    with pytest.raises(ValueError):
+        R.render_l1(st, views, [tu[0].float().double()])
+
+
 def test_fused_forward_l1(R, oracle_mod):
     """The forward with the L1 term fused into the blend gives the same image
     and gradient as the separate loss pass, and the oracle's loss."""
