@@ -131,21 +131,40 @@ __device__ __forceinline__ int find_view_by_super(const ViewDev* views, int n_vi
     return lo;
 }
 
-// One block per super tile, one warp per tile of it (SX*SY = 16 warps). Each
-// chunk of the super tile's depth-ordered (key, record) list is loaded once
-// into shared memory; each warp takes the records whose mask bit is set for
-// its tile, in order. The counting pass writes the tiles' list lengths; after
-// their exclusive scan the writing pass appends the lists at the tiles'
-// offsets (never past cap) and writes the tiles' ranges.
+// Spread the 16 mask bits of m over the 16 bytes of out[0..3] (bit 4k+e of m
+// becomes byte e of out[k]), so that a warp sum of out counts, per bit, the
+// lanes that have it set (at most 32 per byte).
+__device__ __forceinline__ void spread_mask(unsigned m, unsigned out[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned v = (m >> (4 * k)) & 0xfu;
+        out[k] = (v & 1u) | ((v & 2u) << 7) | ((v & 4u) << 14) | ((v & 8u) << 21);
+    }
+}
+
+// Per-tile lists of one super tile (one block per super tile, kExpandWarps
+// warps). The super tile's depth-ordered keys are taken in chunks of one key
+// per thread; warp w holds keys [32w, 32w + 32) of a chunk. For each chunk:
+//  - every warp counts, per tile bit, its keys with the bit set (the spread
+//    mask summed over the warp: four warp reductions for 16 tiles);
+//  - the counting pass adds the counts up per tile and writes the tiles' list
+//    lengths;
+//  - the writing pass takes, per tile, the count of earlier warps of the chunk
+//    plus the tile's running total as the warp's offset and appends its keys
+//    with the bit set at offset + (rank among the warp's set lanes): every
+//    tile's list keeps the depth order. It then writes the tiles' ranges at
+//    their offsets from the scan of the lengths (never past cap).
+constexpr int kExpandWarps = 8;
+
 template <int SX, int SY, bool WRITE>
-__global__ void __launch_bounds__(SX * SY * 32)
+__global__ void __launch_bounds__(kExpandWarps * 32)
 expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict__ skeys,
                     const uint32_t* __restrict__ svals, const ViewDev* __restrict__ views,
                     int n_views, uint32_t* __restrict__ tcount, const uint32_t* __restrict__ toff,
                     uint32_t* __restrict__ vals, long long cap, int2* __restrict__ ranges) {
-    constexpr int NT = SX * SY * 32;
-    __shared__ uint32_t s_r[NT];
-    __shared__ uint16_t s_m[NT];
+    static_assert(SX * SY == 16, "16 tiles per super tile");
+    constexpr int NT = kExpandWarps * 32;
+    __shared__ __align__(16) uint32_t s_cnt[kExpandWarps][4];
     const int sup = blockIdx.x;
     const ViewDev& V = views[find_view_by_super(views, n_views, sup)];
     const int ls = sup - V.super_base;
@@ -153,39 +172,59 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
     const int2 sr = sranges[sup];
     const int b = sr.x, L = sr.y - sr.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tx = tx0 + warp % SX, ty = ty0 + warp / SX;
-    const bool valid = tx < V.ntx && ty < V.nty;
-    const int tile = V.tile_base + ty * V.ntx + tx;
-    const long long base = (WRITE && valid) ? (long long)toff[tile] : 0;
-    int count = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    // lane t < 16 of every warp tracks tile t of the super tile
+    const int ltx = tx0 + (lane & 15) % SX, lty = ty0 + (lane & 15) / SX;
+    const bool lvalid = lane < 16 && ltx < V.ntx && lty < V.nty;
+    const int ltile = V.tile_base + lty * V.ntx + ltx;
+    long long run = (WRITE && lvalid) ? (long long)toff[ltile] : 0;  // tile's next offset
+    long long total = 0;                                            // counting pass
     for (int c0 = 0; c0 < L; c0 += NT) {
         const int i = c0 + threadIdx.x;
+        unsigned m = 0;
+        uint32_t r = 0;
         if (i < L) {
-            s_m[threadIdx.x] = (uint16_t)(skeys[b + i] >> 16);
-            if (WRITE) s_r[threadIdx.x] = svals[b + i];
+            m = skeys[b + i] >> 16;
+            if (WRITE) r = svals[b + i];
         }
+        unsigned sp[4];
+        spread_mask(m, sp);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sp[k] = __reduce_add_sync(0xffffffffu, sp[k]);
+        if (lane == 0)
+            *reinterpret_cast<uint4*>(s_cnt[warp]) = make_uint4(sp[0], sp[1], sp[2], sp[3]);
         __syncthreads();
-        const int n = min(NT, L - c0);
-        if (valid) {
-            for (int j0 = 0; j0 < n; j0 += 32) {
-                const int j = j0 + lane;
-                const bool hit = j < n && ((s_m[j] >> warp) & 1u);
-                const unsigned bal = __ballot_sync(0xffffffffu, hit);
-                if (WRITE && hit) {
-                    const long long o = base + count + __popc(bal & ((1u << lane) - 1u));
-                    if (o < cap) vals[o] = s_r[j];
-                }
-                count += __popc(bal);
+        // lane t < 16: tile t's count in the warps before this one, and in the chunk
+        long long before = 0, chunk = 0;
+        if (lane < 16) {
+            const int k = lane >> 2, sh = 8 * (lane & 3);
+            for (int w = 0; w < kExpandWarps; ++w) {
+                const long long c = (s_cnt[w][k] >> sh) & 0xffu;
+                before += w < warp ? c : 0;
+                chunk += c;
             }
+        }
+        if (WRITE) {
+            const long long base = run + before;
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+                const bool hit = (m >> t) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, hit);
+                const long long o = __shfl_sync(0xffffffffu, base, t) + __popc(bal & lt);
+                if (hit && o < cap) vals[o] = r;
+            }
+            run += chunk;
+        } else {
+            total += chunk;
         }
         __syncthreads();
     }
-    if (valid && lane == 0) {
+    if (warp == 0 && lvalid) {
         if (WRITE) {
-            const long long e = base + count < cap ? base + count : cap;
-            ranges[tile] = make_int2((int)base, (int)e);
+            const long long s0 = toff[ltile];
+            ranges[ltile] = make_int2((int)(s0 < cap ? s0 : cap), (int)(run < cap ? run : cap));
         } else {
-            tcount[tile] = (uint32_t)count;
+            tcount[ltile] = (uint32_t)total;
         }
     }
 }
@@ -198,10 +237,10 @@ static cudaError_t run_expand(const int2* sranges, const uint32_t* skeys, const 
     if (total_supers <= 0) return cudaSuccess;
     note_launch();
     if (tile_w == 32)
-        expand_tiles_kernel<2, 8, WRITE><<<total_supers, 512, 0, s>>>(
+        expand_tiles_kernel<2, 8, WRITE><<<total_supers, kExpandWarps * 32, 0, s>>>(
             sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges);
     else
-        expand_tiles_kernel<4, 4, WRITE><<<total_supers, 512, 0, s>>>(
+        expand_tiles_kernel<4, 4, WRITE><<<total_supers, kExpandWarps * 32, 0, s>>>(
             sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges);
     return cudaGetLastError();
 }
