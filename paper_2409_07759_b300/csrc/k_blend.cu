@@ -266,17 +266,16 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                 // are applied once below. gm here is alpha dL/dalpha (the
                 // factor -1/2 of dalpha/dm is applied at the flush).
                 float s0m = 0.f, sy = 0.f, syy = 0.f, m6 = 0.f, m7 = 0.f, m8 = 0.f, dx = 0.f;
-                bool any = false;
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     float dy, au;
                     const float q = pair_q(px, py[p], g0, g1.x, &dx, &dy);
                     const float al = pair_alpha(q, g1.y, &au);
                     const bool ok = pos < last[p] && q >= g1.z;
-                    any |= ok;
-                    // T before this Gaussian, recovered from the T after it
-                    T[p] = ok ? __fdividef(T[p], __fsub_rn(1.f, al)) : T[p];
                     const float a1 = ok ? al : 0.f;
+                    // T before this Gaussian, recovered from the T after it (a
+                    // pair that does not count has a1 = 0 and leaves T as is)
+                    T[p] = __fdividef(T[p], __fsub_rn(1.f, a1));
                     const float w = a1 * T[p];
                     m6 = fmaf(w, dL0[p], m6);
                     m7 = fmaf(w, dL1[p], m7);
@@ -285,12 +284,15 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                     const float diff = e - D[p];
                     const float ga = T[p] * diff;
                     D[p] = fmaf(a1, diff, D[p]);
-                    const float gm = (ok && au <= kAlphaMax) ? au * ga : 0.f;
+                    // dalpha/dm needs the unclamped alpha: a1 = au when it counts
+                    const float gm = au <= kAlphaMax ? a1 * ga : 0.f;
                     const float gy = gm * dy;
                     s0m += gm;
                     sy += gy;
                     syy = fmaf(gy, dy, syy);
                 }
+                // a Gaussian no pixel of the warp counted leaves every sum at zero
+                const bool any = s0m != 0.f || m6 != 0.f || m7 != 0.f || m8 != 0.f;
                 if (__any_sync(F, any)) {
                     float m[9];
                     m[0] = s0m;
