@@ -9,6 +9,7 @@ The arithmetic lives in ``swgs_oracle.c`` (plain C, FP64, compiled with
 adds two steps that are plain array bookkeeping:
 
 * ``frame_update`` -- the slice replacement of Alg. 2 (update_thread);
+* ``schedule_expire`` and ``mature`` -- the maturation of Alg. 1 (mature);
 * ``l1_loss_grad`` -- the L1 photometric term of Alg. 1 (loss_func) and its
   gradient.
 """
@@ -459,3 +460,56 @@ def frame_update(buffer, update, target_frame: int, swin_size: int):
               "birth", "frozen"):
         getattr(out, k)[lo:hi] = getattr(update, k)
     return out
+
+
+_FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh", "start", "expire", "birth",
+           "frozen")
+
+
+def _rows(scene, idx):
+    """The rows idx of a scene, as a new object of the same type."""
+    d = {k: getattr(scene, k)[idx].copy() for k in _FIELDS}
+    return type(scene)(sh_degree=scene.sh_degree, **d)
+
+
+def _concat(a, b):
+    d = {k: np.concatenate([getattr(a, k), getattr(b, k)]) for k in _FIELDS}
+    return type(a)(sh_degree=a.sh_degree, **d)
+
+
+def schedule_expire(gs, swin_size: int):
+    """Alg. 1 schedule_expire, which the paper does not define (reading): after
+    the first window [0, swin_size) the gs slots split into swin_size equal
+    slices (Sec. 4.2.1) and slice k gets expire = k for k >= 1, slice 0 expire =
+    swin_size. Expiries then fall on distinct frames modulo swin_size, so one
+    slice matures per frame, and a slice's next version (birth = its expire) is
+    inserted by Alg. 2 at buffer slice birth mod swin_size = k, the slice whose
+    data just expired. Returns a new scene."""
+    out = gs.copy()
+    slice_size = gs.n // swin_size
+    for k in range(swin_size):
+        out.expire[k * slice_size:(k + 1) * slice_size] = k if k >= 1 else swin_size
+    return out
+
+
+def mature(gs, matured, st: int, swin_size: int, num_gs: int):
+    """Alg. 1 mature(st), in the algorithm's order:
+    mature_idx = the gs slots with start < st (ascending);
+    the stream receives gs[mature_idx] as they are (stream.write);
+    matured += those rows (marked frozen: no longer optimised), then only the
+    last num_gs rows are kept;
+    gs[mature_idx]: birth = expire, start = expire, expire = start + swin_size.
+    gs: scene of the optimisable Gaussians; matured: scene of the matured rows,
+    oldest first (may be empty). Returns (gs', matured', snapshot, mature_idx)."""
+    idx = np.nonzero(gs.start < st)[0]
+    snap = _rows(gs, idx)
+    grown = _rows(snap, np.arange(snap.n))
+    grown.frozen[:] = 1
+    m2 = grown if matured is None or matured.n == 0 else _concat(matured, grown)
+    if m2.n > num_gs:
+        m2 = _rows(m2, np.arange(m2.n - num_gs, m2.n))
+    g2 = gs.copy()
+    g2.birth[idx] = gs.expire[idx]
+    g2.start[idx] = gs.expire[idx]
+    g2.expire[idx] = g2.start[idx] + swin_size
+    return g2, m2, snap, idx
