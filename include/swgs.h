@@ -166,6 +166,41 @@ swgs_status swgs_frame_update(swgs_ctx *ctx, const swgs_gaussians *dst, int64_t 
                               void *stream);
 
 /*
+ * Maturation of Alg. 1 (procedure mature, Sec. 4.2) on the device. buf holds
+ * the optimisable Gaussians (gs) in slots [0, num_gs) and the ring of the last
+ * num_gs matured rows in slots [num_gs, 2 num_gs) (frozen = 1; ring slots never
+ * written yet keep an empty lifespan, start = expire). Requires
+ * buf->capacity >= 2 num_gs, num_gs a multiple of swin_size, and the birth and
+ * frozen arrays. In the algorithm's order:
+ *  1. mature_idx = the gs slots with start < st, ascending;
+ *  2. stream.write: those rows as they are (every array, lifespans included)
+ *     go to rows 0..n-1 of `snapshot` (optional, same layout, capacity >=
+ *     num_gs; pinned host memory when snapshot_on_host = 1, else device; host
+ *     rows are complete when the stream reaches this point);
+ *  3. matured += the rows, keeping the last num_gs: row j goes to ring slot
+ *     num_gs + (*head + j) mod num_gs with frozen = 1, and *head advances by n
+ *     (mod num_gs; the ring read from *head is the matured list oldest first);
+ *  4. the gs rows start their next lifespan: birth = expire, start = expire,
+ *     expire = start + swin_size.
+ * *n_out receives n = |mature_idx|. The call synchronises the stream once (to
+ * read n). SWGS_EINVAL: bad buffer, head, sizes or snapshot.
+ */
+swgs_status swgs_mature(swgs_ctx *ctx, const swgs_gaussians *buf, int64_t num_gs, int32_t st,
+                        int32_t swin_size, int64_t *head, const swgs_gaussians *snapshot,
+                        int32_t snapshot_on_host, int64_t *n_out, void *stream);
+
+/*
+ * Alg. 1 schedule_expire, which the paper leaves undefined (reading): after the
+ * first window, slice k of the gs slots (slice_size = num_gs / swin_size)
+ * gets expire = k for k >= 1 and slice 0 expire = swin_size, so that exactly
+ * one slice matures per frame and each streamed slice lands, by Alg. 2's
+ * birth mod swin_size rule, on the slice whose data just expired. Same buffer
+ * requirements as swgs_mature.
+ */
+swgs_status swgs_schedule_expire(swgs_ctx *ctx, const swgs_gaussians *buf, int64_t num_gs,
+                                 int32_t swin_size, void *stream);
+
+/*
  * Forward render (Sec. 2.1 Eq. 3 over the frame-t active set) of n_views views,
  * each at its own frame.
  *   bg: host float[3] background; out_rgb[v]: device float[3*H*W] planar;

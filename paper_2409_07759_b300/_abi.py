@@ -112,6 +112,11 @@ PROTOTYPES = [
                                         C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                         C.c_void_p, C.c_int32, C.POINTER(C.c_void_p),
                                         C.c_void_p]),
+    ("swgs_mature", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_int64, C.c_int32,
+                              C.c_int32, C.POINTER(C.c_int64), C.POINTER(SwgsGaussians),
+                              C.c_int32, C.POINTER(C.c_int64), C.c_void_p]),
+    ("swgs_schedule_expire", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_int64,
+                                       C.c_int32, C.c_void_p]),
     ("swgs_render_bwd", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_void_p,
                                   C.POINTER(C.c_void_p), C.POINTER(SwgsGaussians), C.c_void_p]),
     ("swgs_saved_release", C.c_int, [C.c_void_p, C.c_void_p]),

@@ -95,6 +95,26 @@ class GaussianState:
         return {k: getattr(self, k).cpu().pin_memory() for k in
                 PARAM_NAMES + ("start", "expire", "birth", "frozen")}
 
+    def rows(self, lo: int, hi: int) -> "GaussianState":
+        """Views of the slots [lo, hi) (no copy)."""
+        return GaussianState(*[getattr(self, k)[lo:hi] for k in
+                               PARAM_NAMES + ("start", "expire", "birth", "frozen")],
+                             sh_degree=self.sh_degree)
+
+    @staticmethod
+    def with_matured_ring(gs: "GaussianState") -> "GaussianState":
+        """The training buffer of Alg. 1: gs in slots [0, num_gs) followed by an
+        empty ring of num_gs matured slots (frozen, empty lifespan start =
+        expire = 0) that swgs_mature fills."""
+        def cat(a, fill):
+            return torch.cat([a, torch.full_like(a, fill)]).contiguous()
+        return GaussianState(cat(gs.means, 0), cat(gs.log_scales, 0), cat(gs.quats, 0),
+                             cat(gs.opacity_logits, 0), cat(gs.sh, 0), cat(gs.start, 0),
+                             cat(gs.expire, 0), cat(gs.birth, 0),
+                             torch.cat([torch.zeros_like(gs.frozen),
+                                        torch.ones_like(gs.frozen)]).contiguous(),
+                             sh_degree=gs.sh_degree)
+
 
 @dataclass
 class GaussianGrads:
@@ -390,6 +410,42 @@ class Renderer:
         self._check(_abi.load().swgs_frame_update(self.ctx, C.byref(d), int(first), n,
                                                   C.byref(s), int(bool(src_on_host)),
                                                   self._stream(stream)))
+
+    # -- Alg. 1 mature / schedule_expire ---------------------------------------
+    def schedule_expire(self, buf: GaussianState, num_gs: int, swin_size: int, stream=None):
+        """Stagger the gs expiries after the first window (slice k: expire k,
+        slice 0: swin_size). buf: GaussianState.with_matured_ring layout."""
+        b = buf.c_struct()
+        self._check(_abi.load().swgs_schedule_expire(self.ctx, C.byref(b), int(num_gs),
+                                                     int(swin_size), self._stream(stream)))
+
+    def mature(self, buf: GaussianState, num_gs: int, st: int, swin_size: int, head: int,
+               snapshot=None, stream=None):
+        """Alg. 1 mature(st) on buf (GaussianState.with_matured_ring layout).
+        snapshot: None, a GaussianState of >= num_gs rows (device), or a dict of
+        pinned host tensors of >= num_gs rows (GaussianState.pin_host form); its
+        first n rows receive the matured rows as they were (stream.write).
+        Returns (n, new ring head)."""
+        b = buf.c_struct()
+        h = C.c_int64(int(head))
+        n = C.c_int64(0)
+        snap, on_host = None, 0
+        if isinstance(snapshot, dict):
+            snap = _host_struct(snapshot, int(snapshot["means"].shape[0]), buf.sh_degree)
+            on_host = 1
+        elif snapshot is not None:
+            snap = snapshot.c_struct()
+        self._check(_abi.load().swgs_mature(self.ctx, C.byref(b), int(num_gs), int(st),
+                                            int(swin_size), C.byref(h),
+                                            C.byref(snap) if snap is not None else None,
+                                            on_host, C.byref(n), self._stream(stream)))
+        return n.value, h.value
+
+
+def _host_struct(d: dict, n: int, sh_degree: int) -> _abi.SwgsGaussians:
+    return _abi.SwgsGaussians(*[d[k].data_ptr() for k in
+                                PARAM_NAMES + ("start", "expire", "birth", "frozen")],
+                              n, sh_degree)
 
 
 def slice_range(target_frame: int, swin_size: int, num_gs: int):

@@ -75,7 +75,7 @@ struct swgs_ctx {
     cudaStream_t last_stream = nullptr;
     // transient scratch
     Buf frames, block_cnt, scan_tmp, counts, order_a, order_b, tcount, koff, keys_a, keys_b,
-        vals_tmp, vals_b, sranges, tile_cnt, tile_off, sort_tmp, counter, totals, l1_tab, reloc_w, reloc_cdf, reloc_dead, reloc_tg,
+        vals_tmp, vals_b, sranges, tile_cnt, tile_off, mature_ids, mature_stage, sort_tmp, counter, totals, l1_tab, reloc_w, reloc_cdf, reloc_dead, reloc_tg,
         reloc_cnt, reloc_nd;
     void* pinned = nullptr;
     size_t pinned_cap = 0;
@@ -645,7 +645,8 @@ void swgs_destroy(swgs_ctx* ctx) {
     cudaStreamSynchronize(s);
     Buf* bs[] = {&ctx->frames, &ctx->block_cnt, &ctx->scan_tmp, &ctx->counts, &ctx->order_a,
                  &ctx->order_b, &ctx->tcount, &ctx->koff, &ctx->keys_a, &ctx->keys_b,
-                 &ctx->vals_tmp, &ctx->vals_b, &ctx->sranges, &ctx->tile_cnt, &ctx->tile_off, &ctx->sort_tmp, &ctx->counter, &ctx->totals, &ctx->l1_tab,
+                 &ctx->vals_tmp, &ctx->vals_b, &ctx->sranges, &ctx->tile_cnt, &ctx->tile_off,
+                 &ctx->mature_ids, &ctx->mature_stage, &ctx->sort_tmp, &ctx->counter, &ctx->totals, &ctx->l1_tab,
                  &ctx->reloc_w, &ctx->reloc_cdf, &ctx->reloc_dead, &ctx->reloc_tg,
                  &ctx->reloc_cnt, &ctx->reloc_nd};
     for (Buf* b : bs) ctx_free(ctx, *b, s);
@@ -730,6 +731,98 @@ swgs_status swgs_frame_update(swgs_ctx* ctx, const swgs_gaussians* dst, int64_t 
         return SWGS_OK;
     }
     CK(launch_copy_slice(*dst, first, count, *src, s));
+    return SWGS_OK;
+}
+
+static swgs_status check_mature_buffer(swgs_ctx* ctx, const swgs_gaussians* buf, int64_t num_gs,
+                                       int32_t swin_size) {
+    swgs_status st = check_gaussians(ctx, buf, true);
+    if (st != SWGS_OK) return st;
+    if (!buf->birth || !buf->frozen)
+        return fail(ctx, SWGS_EINVAL, "maturation needs the birth and frozen arrays");
+    if (num_gs <= 0 || buf->capacity < 2 * num_gs)
+        return fail(ctx, SWGS_EINVAL, "capacity %lld cannot hold gs and the matured ring of %lld",
+                    (long long)buf->capacity, (long long)num_gs);
+    if (swin_size <= 0 || num_gs % swin_size != 0)
+        return fail(ctx, SWGS_EINVAL, "num_gs %lld is not a multiple of swin_size %d",
+                    (long long)num_gs, swin_size);
+    return SWGS_OK;
+}
+
+swgs_status swgs_schedule_expire(swgs_ctx* ctx, const swgs_gaussians* buf, int64_t num_gs,
+                                 int32_t swin_size, void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    swgs_status st = check_mature_buffer(ctx, buf, num_gs, swin_size);
+    if (st != SWGS_OK) return st;
+    CK(launch_schedule_expire(buf->expire, num_gs, swin_size, s));
+    return SWGS_OK;
+}
+
+swgs_status swgs_mature(swgs_ctx* ctx, const swgs_gaussians* buf, int64_t num_gs, int32_t st_frame,
+                        int32_t swin_size, int64_t* head, const swgs_gaussians* snapshot,
+                        int32_t snapshot_on_host, int64_t* n_out, void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    swgs_status st = check_mature_buffer(ctx, buf, num_gs, swin_size);
+    if (st != SWGS_OK) return st;
+    if (!head || *head < 0 || *head >= num_gs || !n_out)
+        return fail(ctx, SWGS_EINVAL, "bad ring head or null count");
+    if (snapshot && (snapshot->capacity < num_gs || snapshot->sh_degree != buf->sh_degree))
+        return fail(ctx, SWGS_EINVAL, "snapshot must hold num_gs rows of the same SH degree");
+    const long long n_blocks = (num_gs + 255) / 256;
+    if (!ensure(ctx, ctx->block_cnt, sizeof(uint32_t) * (size_t)(n_blocks + 1), s) ||
+        !ensure(ctx, ctx->scan_tmp, scan_u32_temp_bytes(n_blocks + 1) + 64, s) ||
+        !ensure(ctx, ctx->totals, 64, s) ||
+        !ensure(ctx, ctx->mature_ids, sizeof(int32_t) * (size_t)num_gs, s))
+        return fail(ctx, SWGS_ENOMEM, "allocation failed (maturation)");
+    // 1. mature_idx: the gs slots with start < st, ascending
+    CK(launch_mature_ids(buf->start, num_gs, st_frame, P<uint32_t>(ctx->block_cnt),
+                         ctx->scan_tmp.p, P<unsigned long long>(ctx->totals),
+                         P<int32_t>(ctx->mature_ids), s));
+    CK(cudaMemcpyAsync(ctx->pinned, ctx->totals.p, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    unsigned long long n = 0;
+    memcpy(&n, ctx->pinned, sizeof(n));
+    *n_out = (int64_t)n;
+    if (n == 0) return SWGS_OK;
+    // 2-4. snapshot and ring copies of the rows as they are, then their rebirth
+    const int K = (buf->sh_degree + 1) * (buf->sh_degree + 1);
+    const size_t row_b[9] = {12, 12, 16, 4, (size_t)12 * K, 4, 4, 4, 1};
+    void* snap[9] = {nullptr, nullptr, nullptr, nullptr, nullptr,
+                     nullptr, nullptr, nullptr, nullptr};
+    void* const hs[9] = {snapshot ? snapshot->means : nullptr,
+                         snapshot ? snapshot->log_scales : nullptr,
+                         snapshot ? snapshot->quats : nullptr,
+                         snapshot ? snapshot->opacity_logits : nullptr,
+                         snapshot ? snapshot->sh : nullptr,
+                         snapshot ? snapshot->start : nullptr,
+                         snapshot ? snapshot->expire : nullptr,
+                         snapshot ? snapshot->birth : nullptr,
+                         snapshot ? (void*)snapshot->frozen : nullptr};
+    if (snapshot && snapshot_on_host) {
+        // staged on the device, then one copy per array to the pinned rows
+        size_t off[9], tot = 0;
+        for (int i = 0; i < 9; ++i) {
+            off[i] = tot;
+            tot += (row_b[i] * (size_t)n + 255) & ~(size_t)255;
+        }
+        if (!ensure(ctx, ctx->mature_stage, tot, s))
+            return fail(ctx, SWGS_ENOMEM, "allocation failed (maturation snapshot)");
+        for (int i = 0; i < 9; ++i) snap[i] = hs[i] ? (char*)ctx->mature_stage.p + off[i] : nullptr;
+    } else if (snapshot) {
+        for (int i = 0; i < 9; ++i) snap[i] = hs[i];
+    }
+    CK(launch_mature_move(*buf, P<int32_t>(ctx->mature_ids), (long long)n, num_gs, *head,
+                          swin_size, snap, s));
+    if (snapshot && snapshot_on_host)
+        for (int i = 0; i < 9; ++i)
+            if (hs[i])
+                CK(cudaMemcpyAsync(hs[i], snap[i], row_b[i] * (size_t)n, cudaMemcpyDeviceToHost, s));
+    *head = (int64_t)((*head + (long long)n) % num_gs);
     return SWGS_OK;
 }
 

@@ -425,6 +425,16 @@ cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, cons
                                 const uint32_t* toff, uint32_t* vals, long long cap, int2* ranges,
                                 cudaStream_t s);
 
+// k_mature.cu (Alg. 1 mature, schedule_expire)
+cudaError_t launch_mature_ids(const int32_t* start, long long n, int st, uint32_t* block_counts,
+                              void* scan_tmp, unsigned long long* total, int32_t* ids,
+                              cudaStream_t s);
+cudaError_t launch_mature_move(const swgs_gaussians& buf, const int32_t* ids, long long n,
+                               long long num_gs, long long head, int swin_size,
+                               void* const snap[9], cudaStream_t s);
+cudaError_t launch_schedule_expire(int32_t* expire, long long num_gs, int swin_size,
+                                   cudaStream_t s);
+
 // k_blend.cu
 struct BlendArgs {
     const ViewDev* views;

@@ -1,0 +1,90 @@
+"""Maturation of Alg. 1 on the device (swgs_mature, swgs_schedule_expire)
+against the oracle, step by step over a clip: the matured count, the
+snapshot rows (stream.write), the optimisable half of the buffer and the ring
+of matured rows read oldest first from its head, all bit for bit."""
+import numpy as np
+import pytest
+
+from paper_2409_07759_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+FIELDS = ("means", "log_scales", "quats", "opacity_logits", "sh", "start", "expire", "birth",
+          "frozen")
+
+
+def _gs(num_gs, swin, seed=3):
+    rng = np.random.default_rng(seed)
+    attrs = synth.make_gaussians(rng, num_gs, 1)
+    z = np.zeros(num_gs, np.int32)
+    return synth._scene(attrs, 1, z.copy(), np.full(num_gs, swin, np.int32), birth=z.copy())
+
+
+def _train_host(gs, st):
+    g = gs.copy()
+    g.means[:, 1] += np.float32(1.0)
+    g.means[:, 2] = np.float32(st)
+    return g
+
+
+def _train_dev(buf, num_gs, st):
+    buf.means[:num_gs, 1] += 1.0
+    buf.means[:num_gs, 2] = float(st)
+
+
+def _eq(dev, host, what):
+    np.testing.assert_array_equal(dev.cpu().numpy(), host, err_msg=what)
+
+
+@pytest.mark.parametrize("swin,S", [(5, 300), (4, 7)])
+def test_maturation_matches_oracle(oracle_mod, swin, S):
+    from paper_2409_07759_b300 import api
+    num_gs = swin * S
+    r = api.Renderer()
+    g0 = _gs(num_gs, swin)
+    host = _train_host(g0, 0)
+    buf = api.GaussianState.with_matured_ring(api.GaussianState.from_scene(g0))
+    _train_dev(buf, num_gs, 0)
+    host = oracle_mod.schedule_expire(host, swin)
+    r.schedule_expire(buf, num_gs, swin)
+    _eq(buf.expire[:num_gs], host.expire, "schedule_expire")
+    matured, head = None, 0
+    dev_snap = api.GaussianState.from_scene(g0)             # num_gs rows on the device
+    host_snap = api.GaussianState.from_scene(g0).pin_host()  # num_gs rows, pinned host
+    for st in range(1, 4 * swin + 3):
+        host, matured, snap, idx = oracle_mod.mature(host, matured, st, swin, num_gs)
+        use_host = st % 2 == 0
+        n, head = r.mature(buf, num_gs, st, swin, head,
+                           snapshot=host_snap if use_host else dev_snap)
+        torch.cuda.synchronize()
+        assert n == len(idx), st
+        for k in FIELDS:
+            got = host_snap[k][:n].numpy() if use_host else getattr(dev_snap, k)[:n].cpu().numpy()
+            np.testing.assert_array_equal(got, getattr(snap, k), err_msg=f"snapshot {k} st={st}")
+            _eq(getattr(buf, k)[:num_gs], getattr(host, k), f"gs {k} st={st}")
+        # the ring, oldest first from the head, is the matured list
+        order = (head + np.arange(num_gs)) % num_gs + num_gs
+        assert matured.n == num_gs
+        for k in FIELDS:
+            _eq(getattr(buf, k)[torch.from_numpy(order).cuda()], getattr(matured, k),
+                f"ring {k} st={st}")
+        host = _train_host(host, st)
+        _train_dev(buf, num_gs, st)
+    r.close()
+
+
+def test_maturation_rejects_bad_buffers():
+    from paper_2409_07759_b300 import api
+    from paper_2409_07759_b300._abi import SwgsError
+    r = api.Renderer()
+    g = api.GaussianState.from_scene(_gs(20, 5))
+    with pytest.raises(SwgsError):  # no room for the ring
+        r.mature(g, 20, 1, 5, 0)
+    buf = api.GaussianState.with_matured_ring(g)
+    with pytest.raises(SwgsError):  # num_gs not a multiple of swin_size
+        r.mature(buf, 20, 1, 3, 0)
+    with pytest.raises(SwgsError):  # head outside the ring
+        r.mature(buf, 20, 1, 5, 20)
+    r.close()
