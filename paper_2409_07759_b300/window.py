@@ -72,6 +72,20 @@ class WindowTrainer:
         self.dl = [torch.empty_like(i) for i in self.images]
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
 
+    def set_window(self, views: Sequence, targets: Sequence[torch.Tensor]):
+        """Move the trainer to another window's views and targets (buffers are
+        reallocated only where a view's size changes)."""
+        views = list(views)
+        if len(views) != len(self.views) or any(
+                (a.width, a.height) != (b.width, b.height) for a, b in zip(views, self.views)):
+            self.images = [torch.empty((3, v.height, v.width), dtype=torch.float32,
+                                       device="cuda") for v in views]
+            self.dl = [torch.empty_like(i) for i in self.images]
+            self._bufs = None
+        self.views = views
+        self.targets = list(targets)
+        self.frames = sorted({int(v.frame) for v in views})
+
     def prefetch_targets(self, host_targets: Sequence[torch.Tensor]):
         """Start copying the next step's targets from pinned host memory into a
         back buffer on a side stream, so that the copy overlaps the step in
@@ -121,3 +135,76 @@ class WindowTrainer:
         if self._bufs is not None:
             self._released[self._front].record()
         return self.loss
+
+
+class ClipTrainer:
+    """Alg. 1 main over a clip: the first window [0, swin_size) trained from the
+    initial Gaussians, schedule_expire, then for every window start st: mature
+    (st) -- whose snapshot is the stream that Alg. 2 clients read -- and the
+    window [st, st + swin_size) trained.
+
+    The buffer holds gs in slots [0, num_gs) and the ring of matured rows in
+    [num_gs, 2 num_gs) (GaussianState.with_matured_ring), so every render sees
+    gs and matured together and only gs is optimised (the ring is frozen).
+    Each iteration is one batched step over every view of the window's frames
+    (the paper samples one frame per iteration).
+
+    window(st, ed) -> (views, targets): the training views of frames [st, ed)
+    and their target images (device tensors, float32 or uint8).
+    """
+
+    def __init__(self, renderer: api.Renderer, gs: api.GaussianState, swin_size: int,
+                 window, iterations: int = 1, params: Optional[dict] = None, seed: int = 0,
+                 snapshot_to_host: bool = True):
+        self.r = renderer
+        self.num_gs = gs.n
+        if self.num_gs % swin_size:
+            raise ValueError("num_gs must be a multiple of swin_size")
+        self.swin = swin_size
+        self.buf = api.GaussianState.with_matured_ring(gs)
+        self.window = window
+        self.iterations = iterations
+        self.head = 0
+        self.step_count = 0
+        views, targets = window(0, swin_size)
+        self.trainer = WindowTrainer(renderer, self.buf, views, targets, params=params, seed=seed)
+        self.snapshot_to_host = snapshot_to_host
+        self.stream = []   # [(st, n, snapshot)]
+
+    def _train(self, st: int):
+        views, targets = self.window(st, st + self.swin)
+        self.trainer.set_window(views, targets)
+        loss = None
+        for _ in range(self.iterations):
+            loss = self.trainer.step(self.step_count)
+            self.step_count += 1
+        return loss
+
+    def _snapshot(self):
+        s = api.GaussianState(*[torch.empty_like(getattr(self.buf, k)[:self.num_gs]) for k in
+                                api.PARAM_NAMES + ("start", "expire", "birth", "frozen")],
+                              sh_degree=self.buf.sh_degree)
+        return s.pin_host() if self.snapshot_to_host else s
+
+    def mature(self, st: int):
+        snap = self._snapshot()
+        n, self.head = self.r.mature(self.buf, self.num_gs, st, self.swin, self.head,
+                                     snapshot=snap)
+        self.stream.append((st, n, snap))
+        return n
+
+    def run(self, total_frames: int):
+        """Alg. 1 main (the initial Gaussians are the caller's gs); returns the
+        loss of the last step."""
+        # main: birth = start = 0, expire = swin_size for every gs slot
+        g = self.buf.rows(0, self.num_gs)
+        g.birth.zero_()
+        g.start.zero_()
+        g.expire.fill_(self.swin)
+        loss = self._train(0)
+        self.r.schedule_expire(self.buf, self.num_gs, self.swin)
+        for st in range(1, total_frames):
+            self.mature(st)
+            loss = self._train(st)
+        self.mature(total_frames)
+        return loss

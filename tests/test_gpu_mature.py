@@ -88,3 +88,52 @@ def test_maturation_rejects_bad_buffers():
     with pytest.raises(SwgsError):  # head outside the ring
         r.mature(buf, 20, 1, 5, 20)
     r.close()
+
+
+def test_clip_trainer_streams_a_valid_alg2_sequence(oracle_mod):
+    """Alg. 1 main on a short clip: the first snapshot holds all num_gs
+    Gaussians, every later one one slice born at st - 1, and an Alg. 2 client
+    fed the stream has exactly num_gs Gaussians covering every frame."""
+    from paper_2409_07759_b300 import api
+    from paper_2409_07759_b300.window import ClipTrainer
+    swin, S, T = 5, 40, 9
+    num_gs = swin * S
+    sc, _, _ = synth.config2(width=64, height=48, n=num_gs, n_frames=1, per_frame=1)
+    ring = synth.ring_cameras(20, 4.0, 64, 48)
+    rng = np.random.default_rng(5)
+    tg = {}
+
+    def window(st, ed):
+        views, targets = [], []
+        for f in range(st, ed):
+            for c in (f % 20, (f + 7) % 20):
+                v = ring[c]
+                views.append(synth.View(v.width, v.height, v.fx, v.fy, v.cx, v.cy, v.R, v.t, f))
+                if (f, c) not in tg:
+                    tg[(f, c)] = torch.from_numpy(
+                        rng.integers(0, 256, size=(3, 48, 64), dtype=np.uint8)).cuda()
+                targets.append(tg[(f, c)])
+        return views, targets
+
+    r = api.Renderer()
+    gs = api.GaussianState.from_scene(sc)
+    ct = ClipTrainer(r, gs, swin, window, iterations=2, seed=1)
+    loss = ct.run(T)
+    torch.cuda.synchronize()
+    assert np.isfinite(float(loss.item()))
+    assert [n for _, n, _ in ct.stream] == [num_gs] + [S] * (T - 1)
+    for st, n, snap in ct.stream[1:]:
+        assert set(snap["birth"][:n].tolist()) == {st - 1}
+    assert bool((ct.buf.frozen[num_gs:] == 1).all()) and bool((ct.buf.frozen[:num_gs] == 0).all())
+
+    def scene_of(snap, n):
+        d = {k: snap[k][:n].numpy().copy() for k in FIELDS}
+        return synth.Scene(sh_degree=sc.sh_degree, **d)
+
+    buffer = scene_of(ct.stream[0][2], num_gs)
+    events = {int(snap["birth"][0]): scene_of(snap, n) for _, n, snap in ct.stream[1:]}
+    for f in range(T):
+        if f in events:
+            buffer = oracle_mod.frame_update(buffer, events[f], f, swin)
+        assert int(((buffer.start <= f) & (f < buffer.expire)).sum()) == num_gs, f
+    r.close()
