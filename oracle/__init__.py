@@ -10,6 +10,8 @@ adds two steps that are plain array bookkeeping:
 
 * ``frame_update`` -- the slice replacement of Alg. 2 (update_thread);
 * ``schedule_expire`` and ``mature`` -- the maturation of Alg. 1 (mature);
+* ``reg_loss_grad`` -- the opacity and scale regularisers of Alg. 1 reg() (Sec. 4.4);
+* ``mean_grad_scale`` -- the per-Gaussian gradient scale on the means (Sec. 4.5.1);
 * ``l1_loss_grad`` -- the L1 photometric term of Alg. 1 (loss_func) and its
   gradient.
 """
@@ -513,3 +515,42 @@ def mature(gs, matured, st: int, swin_size: int, num_gs: int):
     g2.start[idx] = gs.expire[idx]
     g2.expire[idx] = g2.start[idx] + swin_size
     return g2, m2, snap, idx
+
+
+def reg_loss_grad(scene, view_frames, opacity_reg: float, scale_reg: float):
+    """Alg. 1 reg(active_gs) with the regularisers of [14] (Sec. 4.4; weights
+    opacity_reg = 2e-2, scale_reg = 1e-2 in Sec. 8.1), for a batch whose loss is
+    the mean over its views (view v renders frame view_frames[v]):
+        reg_v = opacity_reg * mean_{i active at f_v} sigmoid(logit_i)
+              + scale_reg * mean_{i active at f_v, c} exp(log_scale_ic),
+    loss = mean_v reg_v. Active includes frozen (matured) Gaussians, which
+    receive no gradient. Returns (loss, grads) with grads of the logits and
+    log-scales (FP64; the other attributes get none)."""
+    V = len(view_frames)
+    logit = scene.opacity_logits.astype(np.float64)
+    ls = scene.log_scales.astype(np.float64)
+    sig = 1.0 / (1.0 + np.exp(-logit))
+    sc = np.exp(ls)
+    g_logit = np.zeros_like(logit)
+    g_ls = np.zeros_like(ls)
+    loss = 0.0
+    live = scene.frozen == 0
+    for f in view_frames:
+        act = (scene.start <= f) & (f < scene.expire)
+        n = int(act.sum())
+        if n == 0:
+            continue
+        loss += (opacity_reg * sig[act].mean() + scale_reg * sc[act].mean()) / V
+        m = act & live
+        g_logit[m] += opacity_reg * sig[m] * (1.0 - sig[m]) / (n * V)
+        g_ls[m] += scale_reg * sc[m] / (3 * n * V)
+    return loss, {"opacity_logits": g_logit, "log_scales": g_ls}
+
+
+def mean_grad_scale(start, window_start: int, swin_size: int, decay: float):
+    """Sec. 4.5.1, whose formula the paper does not give (reading): the gradient
+    of a Gaussian's means is scaled by decay^(k - 1), k = window_start - start +
+    swin_size the number of windows [st, st + swin_size) that have trained its
+    current lifespan [start, start + swin_size) so far (k >= 1)."""
+    k = np.maximum(1, window_start - np.asarray(start, np.int64) + swin_size)
+    return np.float64(decay) ** (k - 1).astype(np.float64)
