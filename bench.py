@@ -124,6 +124,57 @@ def config3_leg(args):
             "autotuned": dict(best, tile="%dx%d" % tuple(best["tile"]))}
 
 
+def mature_leg(state, swin=50, reps=20):
+    """Alg. 1 mature(st) on the window scene laid out as gs (300k slots, swin
+    50: 6,000-slot slices) + the ring of matured rows, snapshot to pinned host
+    memory (stream.write): the per-frame maturation once the first window's
+    full snapshot has been taken. Times each call (it synchronises once to read
+    the count) with CUDA events and host time."""
+    import torch
+    from paper_2409_07759_b300 import api
+    num_gs = state.n - state.n % swin
+    gs = state.rows(0, num_gs)
+    buf = api.GaussianState.with_matured_ring(
+        api.GaussianState(*[t.clone() for t in (gs.means, gs.log_scales, gs.quats,
+                                                 gs.opacity_logits, gs.sh, gs.start,
+                                                 gs.expire, gs.birth, gs.frozen)],
+                          sh_degree=gs.sh_degree))
+    r = api.Renderer()
+    buf.start.zero_()
+    buf.birth.zero_()
+    buf.expire[:num_gs] = swin
+    snap = api.GaussianState(*[torch.empty_like(getattr(buf, k)[:num_gs]) for k in
+                               api.PARAM_NAMES + ("start", "expire", "birth", "frozen")],
+                             sh_degree=buf.sh_degree).pin_host()
+    r.schedule_expire(buf, num_gs, swin)
+    head = 0
+    n0, head = r.mature(buf, num_gs, 1, swin, head, snapshot=snap)   # the first window
+    times, ns = [], []
+    for st in range(2, 2 + reps):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        a.record()
+        n, head = r.mature(buf, num_gs, st, swin, head, snapshot=snap)
+        b.record()
+        b.synchronize()
+        times.append((a.elapsed_time(b), 1e3 * (time.perf_counter() - t0)))
+        ns.append(n)
+    r.close()
+    row = sum(getattr(buf, k)[:1].numel() * getattr(buf, k).element_size() for k in
+              api.PARAM_NAMES + ("start", "expire", "birth", "frozen"))
+    dev_ms = statistics.median(t[0] for t in times)
+    n = int(statistics.median(ns))
+    # per maturation: lifespans of every gs slot read (4 B) + n rows read, written to
+    # the ring and to the staging snapshot, 12 B of lifespans rewritten; n rows D2H
+    moved = 4 * num_gs + 3 * n * row + 12 * n
+    return {"num_gs": num_gs, "swin_size": swin, "first_window_rows": n0,
+            "rows_per_frame": n, "row_bytes": row, "ms_per_frame": dev_ms,
+            "host_ms_per_frame": statistics.median(t[1] for t in times),
+            "device_bytes": moved, "d2h_bytes": n * row,
+            "achieved_gbs": moved / (dev_ms / 1e3) / 1e9}
+
+
 def serving_leg(args):
     """Config 4: 300k Gaussians in 50 slices of 6,000 (swin_size 50), one
     slice swapped per frame at 30 fps, Poisson viewers on orbits requesting the
@@ -502,6 +553,8 @@ def main():
                 "frac": None, "traffic": None}
 
     if not args.no_serving:
+        torch.cuda.synchronize()
+        extra["mature"] = mature_leg(state)
         torch.cuda.synchronize()
         extra["serving"] = serving_leg(args)
     if not args.no_config3:

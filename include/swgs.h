@@ -27,7 +27,7 @@
 extern "C" {
 #endif
 
-#define SWGS_ABI_VERSION 2
+#define SWGS_ABI_VERSION 3
 
 typedef enum swgs_status {
     SWGS_OK = 0,
@@ -262,6 +262,29 @@ swgs_status swgs_render_bwd(swgs_ctx *ctx, const swgs_gaussians *g, const swgs_s
                             const float *const *dL_drgb, const swgs_gaussians *grads,
                             void *stream);
 
+/*
+ * Regularisers of Alg. 1 reg(active_gs) (Sec. 4.4, weights in Sec. 8.1; the
+ * terms of [14]): for a loss that is the mean over the forward's views, view
+ * v (frame f_v) adds
+ *   opacity_reg * mean_{i active at f_v} sigmoid(logit_i)
+ *   + scale_reg * mean_{i active at f_v, c} exp(log_scale_ic) / V.
+ * Matured (frozen) Gaussians count in the means but get no gradient.
+ * n_views_total: V (0 = the forward's number of views).
+ */
+typedef struct swgs_reg_params {
+    float opacity_reg, scale_reg;
+    int32_t n_views_total;
+} swgs_reg_params;
+
+/*
+ * swgs_render_bwd plus the gradient of the regularisers (reg may be NULL: no
+ * regulariser). If loss (device float) is non-NULL the regulariser value is
+ * ADDED to it.
+ */
+swgs_status swgs_render_bwd_reg(swgs_ctx *ctx, const swgs_gaussians *g, const swgs_saved *saved,
+                                const float *const *dL_drgb, const swgs_gaussians *grads,
+                                const swgs_reg_params *reg, float *loss, void *stream);
+
 /* Returns a saved state to the context's pool (stream-ordered reuse). */
 swgs_status swgs_saved_release(swgs_ctx *ctx, swgs_saved *saved);
 
@@ -322,6 +345,13 @@ typedef struct swgs_sgld_params {
     int32_t adam;              /* 1: Adam step from grads before the noise */
     int32_t relocate;          /* 1: relocate dead Gaussians after the noise */
     int32_t max_n;             /* cap on copies per target in the formulas */
+    /* Sec. 4.5.1 (formula not given; reading): the means gradient of slot i is
+     * scaled by mean_grad_decay^(k-1) before the Adam step, k = max(1,
+     * window_start - start_i + swin_size) the windows that have trained the
+     * slot's current lifespan. Off when mean_grad_decay == 1 or swin_size <= 0. */
+    float mean_grad_decay;
+    int32_t window_start;
+    int32_t swin_size;
 } swgs_sgld_params;
 
 /* Adam moments, device arrays shaped like the five float parameter arrays. */

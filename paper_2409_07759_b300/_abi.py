@@ -62,7 +62,14 @@ class SwgsSgldParams(C.Structure):
                 ("lr_logits", C.c_float), ("lr_sh_dc", C.c_float), ("lr_sh_rest", C.c_float),
                 ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
                 ("noise_lr", C.c_float), ("noise_k", C.c_float), ("noise_t", C.c_float),
-                ("adam", C.c_int32), ("relocate", C.c_int32), ("max_n", C.c_int32)]
+                ("adam", C.c_int32), ("relocate", C.c_int32), ("max_n", C.c_int32),
+                ("mean_grad_decay", C.c_float), ("window_start", C.c_int32),
+                ("swin_size", C.c_int32)]
+
+
+class SwgsRegParams(C.Structure):
+    _fields_ = [("opacity_reg", C.c_float), ("scale_reg", C.c_float),
+                ("n_views_total", C.c_int32)]
 
 
 class SwgsAdamState(C.Structure):
@@ -112,6 +119,9 @@ PROTOTYPES = [
                                         C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                         C.c_void_p, C.c_int32, C.POINTER(C.c_void_p),
                                         C.c_void_p]),
+    ("swgs_render_bwd_reg", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_void_p,
+                                      C.POINTER(C.c_void_p), C.POINTER(SwgsGaussians),
+                                      C.POINTER(SwgsRegParams), C.c_void_p, C.c_void_p]),
     ("swgs_mature", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_int64, C.c_int32,
                               C.c_int32, C.POINTER(C.c_int64), C.POINTER(SwgsGaussians),
                               C.c_int32, C.POINTER(C.c_int64), C.c_void_p]),
@@ -142,7 +152,7 @@ _lib = None
 
 
 # The struct layouts above mirror include/swgs.h at this SWGS_ABI_VERSION.
-ABI_VERSION = 2
+ABI_VERSION = 3
 
 
 def load():

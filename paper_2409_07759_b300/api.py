@@ -350,14 +350,23 @@ class Renderer:
         return out, dL_out, loss_out, saved
 
     def backward(self, state: GaussianState, saved: SavedState, dL_drgb, grads: GaussianGrads,
-                 stream=None):
+                 reg: Optional[dict] = None, loss: Optional[torch.Tensor] = None, stream=None):
+        """Accumulate into grads the gradient of the render (and, with reg =
+        dict(opacity_reg=..., scale_reg=...), of Alg. 1 reg(); its value is
+        added to `loss` when given)."""
         for t in dL_drgb:
             assert t.is_contiguous() and t.dtype == torch.float32
         g = state.c_struct()
         gr = grads.c_struct()
-        self._check(_abi.load().swgs_render_bwd(self.ctx, C.byref(g), saved.handle,
-                                                _ptr_array(dL_drgb), C.byref(gr),
-                                                self._stream(stream)))
+        rp = None
+        if reg is not None:
+            rp = _abi.SwgsRegParams(float(reg.get("opacity_reg", 0.0)),
+                                    float(reg.get("scale_reg", 0.0)),
+                                    int(reg.get("n_views_total", 0)))
+        self._check(_abi.load().swgs_render_bwd_reg(self.ctx, C.byref(g), saved.handle,
+                                                    _ptr_array(dL_drgb), C.byref(gr),
+                                                    C.byref(rp) if rp is not None else None,
+                                                    _ptr(loss), self._stream(stream)))
         return grads
 
     # -- Alg. 1 loss_func (L1) -------------------------------------------------
@@ -376,7 +385,9 @@ class Renderer:
     def sgld_step(self, state: GaussianState, frames, params: dict, seed: int, step: int,
                   grads: Optional[GaussianGrads] = None, adam: Optional[dict] = None,
                   targets: Optional[torch.Tensor] = None, count_relocated=False, stream=None):
-        p = _abi.SwgsSgldParams(**params)
+        known = {f[0] for f in _abi.SwgsSgldParams._fields_}
+        p = _abi.SwgsSgldParams(**{"mean_grad_decay": 1.0,
+                                   **{k: v for k, v in params.items() if k in known}})
         fr = (C.c_int32 * max(1, len(frames)))(*[int(f) for f in frames])
         ad = None
         if adam is not None:

@@ -51,9 +51,16 @@ __global__ void __launch_bounds__(256) sgld_kernel(SgldArgs a) {
     if (!is_eligible(a.g, i, a.frames, a.n_frames)) return;
     const int K = (a.g.sh_degree + 1) * (a.g.sh_degree + 1);
     if (a.p.adam && a.has_grads && a.has_adam) {
+        // Sec. 4.5.1: the means gradient shrinks with the windows that have
+        // trained the slot's current lifespan
+        float gscale = 1.f;
+        if (a.p.mean_grad_decay != 1.f && a.p.swin_size > 0) {
+            const int k = max(1, a.p.window_start - a.g.start[i] + a.p.swin_size);
+            gscale = exp2f((float)(k - 1) * log2f(a.p.mean_grad_decay));
+        }
         for (int k = 0; k < 3; ++k) {
             adam1(&a.g.means[3 * i + k], &a.adam.m_means[3 * i + k], &a.adam.v_means[3 * i + k],
-                  a.grads.means[3 * i + k], a.p.lr_means, a);
+                  a.grads.means[3 * i + k] * gscale, a.p.lr_means, a);
             adam1(&a.g.log_scales[3 * i + k], &a.adam.m_log_scales[3 * i + k],
                   &a.adam.v_log_scales[3 * i + k], a.grads.log_scales[3 * i + k],
                   a.p.lr_log_scales, a);

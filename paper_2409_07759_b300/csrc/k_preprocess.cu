@@ -340,15 +340,40 @@ struct PreBwdArgs {
     const int32_t* ids;
     long long total_active;
     const float* grad2d;
+    bool reg;      // regulariser weights in the groups
+    float* loss;   // regulariser value added here (or null)
 };
+
+// Alg. 1 reg(): with w_o = opacity_reg vc / (V n), w_s = scale_reg vc / (3 V n)
+// for a frame of n active Gaussians seen by vc of the V views, a Gaussian adds
+// w_o sigmoid(logit) + w_s sum_c exp(log_scale_c) to the loss (frozen ones
+// too: they count in the means) and, unless frozen, w_o sigmoid (1 - sigmoid)
+// to its logit gradient and w_s exp(log_scale_c) to its log-scale gradients.
+__device__ __forceinline__ void reg_loss_add(float v, float* loss) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(loss, v);
+}
 
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= a.total_active) return;
-    const int gi = find_group(a.groups, a.n_groups, t);
+    const bool in = t < a.total_active;
+    const int gi = in ? find_group(a.groups, a.n_groups, t) : 0;
+    const long long slot = in ? a.ids[t] : 0;
+    if (a.reg && a.loss) {
+        float v = 0.f;
+        if (in) {
+            const GroupDev& G0 = a.groups[gi];
+            const float op = 1.0f / (1.0f + __expf(-a.g.opacity_logits[slot]));
+            v = G0.reg_o * op;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v += G0.reg_s * __expf(a.g.log_scales[3 * slot + k]);
+        }
+        reg_loss_add(v, a.loss);
+    }
+    if (!in) return;
     const GroupDev G = a.groups[gi];
     const int i = (int)(t - G.act_base);
-    const long long slot = a.ids[t];
     if (a.g.frozen && a.g.frozen[slot]) return;
     const int K = (a.g.sh_degree + 1) * (a.g.sh_degree + 1);
 
@@ -500,7 +525,17 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) gmu[c] += V.R[c] * gp0 + V.R[3 + c] * gp1 + V.R[6 + c] * gz;
     }
-    if (!any) return;
+    if (!any) {
+        if (a.reg) {
+            red_add(&a.grads.opacity_logits[slot], G.reg_o * opacity * (1.f - opacity));
+#pragma unroll
+            for (int k = 0; k < 3; ++k) red_add(&a.grads.log_scales[3 * slot + k], G.reg_s * s[k]);
+        }
+        return;
+    }
+    if (a.reg) {
+        glogit += G.reg_o * opacity * (1.f - opacity);
+    }
     // Sigma = M M^T, M = Rq diag(s)
     float GM[3][3];
 #pragma unroll
@@ -515,7 +550,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {
         float gsc = 0.f;
 #pragma unroll
         for (int r = 0; r < 3; ++r) { gsc += Rq[r][c] * GM[r][c]; GR[r][c] = s[c] * GM[r][c]; }
-        gls[c] = gsc * s[c];
+        gls[c] = gsc * s[c] + (a.reg ? G.reg_s * s[c] : 0.f);
     }
     float gq[4];
     gq[0] = 2.f * (-zq * GR[0][1] + y * GR[0][2] + zq * GR[1][0] - x * GR[1][2] - y * GR[2][0] +
@@ -544,9 +579,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {
 cudaError_t launch_preprocess_bwd(const swgs_gaussians& g, const swgs_gaussians& grads,
                                   const ViewDev* views, const GroupDev* groups, int n_groups,
                                   const int32_t* ids, long long total_active,
-                                  const float* grad2d, cudaStream_t s) {
+                                  const float* grad2d, bool reg, float* loss, cudaStream_t s) {
     if (total_active <= 0) return cudaSuccess;
-    PreBwdArgs a{g, grads, views, groups, n_groups, ids, total_active, grad2d};
+    PreBwdArgs a{g, grads, views, groups, n_groups, ids, total_active, grad2d, reg, loss};
     note_launch();
     preprocess_bwd_kernel<<<div_up(total_active, 128), 128, 0, s>>>(a);
     return cudaGetLastError();

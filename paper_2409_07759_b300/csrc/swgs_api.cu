@@ -490,7 +490,9 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
 }
 
 swgs_status backward_batch(swgs_ctx* ctx, const swgs_gaussians* g, BatchState& B,
-                           const float* const* dL, const swgs_gaussians* grads, cudaStream_t s) {
+                           const float* const* dL, const swgs_gaussians* grads,
+                           const swgs_reg_params* reg, int n_views_total, float* loss,
+                           cudaStream_t s) {
     const int tw = ctx->cfg.tile_w, th = ctx->cfg.tile_h;
     for (size_t i = 0; i < B.h_views.size(); ++i) {
         B.h_views[i].dL = dL[B.call_index[i]];
@@ -532,9 +534,22 @@ swgs_status backward_batch(swgs_ctx* ctx, const swgs_gaussians* g, BatchState& B
     }
     {
         StageScope sc_(ctx, SWGS_STAGE_PREPROCESS_BWD, s);
+        const bool use_reg = reg && (reg->opacity_reg != 0.f || reg->scale_reg != 0.f);
+        if (use_reg) {
+            // per-frame weights of one active Gaussian in the view-mean of reg()
+            const int V = reg->n_views_total > 0 ? reg->n_views_total : n_views_total;
+            for (GroupDev& G : B.h_groups) {
+                const double w = G.n_active > 0 ? (double)G.view_count / ((double)V * G.n_active)
+                                                : 0.0;
+                G.reg_o = (float)(reg->opacity_reg * w);
+                G.reg_s = (float)(reg->scale_reg * w / 3.0);
+            }
+            CK(cudaMemcpyAsync(B.groups.p, B.h_groups.data(), sizeof(GroupDev) * B.h_groups.size(),
+                               cudaMemcpyHostToDevice, s));
+        }
         CK(launch_preprocess_bwd(*g, *grads, P<ViewDev>(B.views), P<GroupDev>(B.groups),
                                  B.n_groups, P<int32_t>(B.ids), B.total_active,
-                                 P<float>(B.grad2d), s));
+                                 P<float>(B.grad2d), use_reg, use_reg ? loss : nullptr, s));
     }
     return SWGS_OK;
 }
@@ -966,6 +981,12 @@ static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32
 swgs_status swgs_render_bwd(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_saved* saved,
                             const float* const* dL_drgb, const swgs_gaussians* grads,
                             void* stream) {
+    return swgs_render_bwd_reg(ctx, g, saved, dL_drgb, grads, nullptr, nullptr, stream);
+}
+
+swgs_status swgs_render_bwd_reg(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_saved* saved,
+                                const float* const* dL_drgb, const swgs_gaussians* grads,
+                                const swgs_reg_params* reg, float* loss, void* stream) {
     if (!ctx) return SWGS_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     ctx->last_stream = s;
@@ -977,8 +998,10 @@ swgs_status swgs_render_bwd(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_s
         !grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh)
         return fail(ctx, SWGS_EINVAL, "gradient buffers do not match the Gaussian state");
     swgs_saved* sv = const_cast<swgs_saved*>(saved);
+    if (reg && (!(reg->opacity_reg >= 0.f) || !(reg->scale_reg >= 0.f) || reg->n_views_total < 0))
+        return fail(ctx, SWGS_EINVAL, "regulariser weights must be >= 0");
     for (int b = 0; b < sv->n_batches; ++b) {
-        st = backward_batch(ctx, g, sv->batches[b], dL_drgb, grads, s);
+        st = backward_batch(ctx, g, sv->batches[b], dL_drgb, grads, reg, sv->n_views, loss, s);
         if (st != SWGS_OK) return st;
     }
     return SWGS_OK;

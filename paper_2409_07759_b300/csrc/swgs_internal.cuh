@@ -48,6 +48,7 @@ struct GroupDev {
     int rec_base;      // first record of this group
     int view_begin;    // first view of this group (views of a group are contiguous)
     int view_count;
+    float reg_o, reg_s;  // regulariser weights of one active Gaussian (backward)
 };
 
 // Records of one (view, Gaussian) pair, structure of float4 arrays.
@@ -386,7 +387,7 @@ cudaError_t launch_preprocess(const swgs_gaussians& g, const ViewDev* views, con
 cudaError_t launch_preprocess_bwd(const swgs_gaussians& g, const swgs_gaussians& grads,
                                   const ViewDev* views, const GroupDev* groups, int n_groups,
                                   const int32_t* ids, long long total_active,
-                                  const float* grad2d, cudaStream_t s);
+                                  const float* grad2d, bool reg, float* loss, cudaStream_t s);
 
 // k_sort.cu
 struct SortPlan {

@@ -16,7 +16,11 @@ from . import api
 
 DEFAULT_SGLD = dict(lr_means=1.6e-4, lr_log_scales=5e-3, lr_quats=1e-3, lr_logits=5e-2,
                     lr_sh_dc=2.5e-3, lr_sh_rest=2.5e-3 / 20.0, beta1=0.9, beta2=0.999, eps=1e-15,
-                    noise_lr=5e4, noise_k=100.0, noise_t=0.005, adam=1, relocate=1, max_n=51)
+                    noise_lr=5e4, noise_k=100.0, noise_t=0.005, adam=1, relocate=1, max_n=51,
+                    # Alg. 1 reg(): the regulariser weights of Sec. 8.1
+                    opacity_reg=2e-2, scale_reg=1e-2,
+                    # Sec. 4.5.1 means-gradient scale (1 = off); ClipTrainer sets the window
+                    mean_grad_decay=1.0, window_start=0, swin_size=0)
 
 
 def _flat_views(n: int, K: int, device="cuda"):
@@ -126,7 +130,11 @@ class WindowTrainer:
                                           batched=self.batched, out=self.images,
                                           dL_out=self.dl, loss_out=self.loss)
         self._gflat.zero_()
-        self.r.backward(self.state, saved, self.dl, self.grads)
+        reg = None
+        if self.params.get("opacity_reg", 0.0) or self.params.get("scale_reg", 0.0):
+            reg = dict(opacity_reg=self.params["opacity_reg"],
+                       scale_reg=self.params["scale_reg"])
+        self.r.backward(self.state, saved, self.dl, self.grads, reg=reg, loss=self.loss)
         saved.release()
         if self.reduce is not None:
             self.reduce(self._gflat, self.loss)
@@ -174,6 +182,7 @@ class ClipTrainer:
     def _train(self, st: int):
         views, targets = self.window(st, st + self.swin)
         self.trainer.set_window(views, targets)
+        self.trainer.params.update(window_start=st, swin_size=self.swin)
         loss = None
         for _ in range(self.iterations):
             loss = self.trainer.step(self.step_count)

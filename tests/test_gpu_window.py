@@ -42,7 +42,9 @@ def test_window_step_matches_explicit_calls():
     frames = sorted({v.frame for v in views})
     imgs, dl, loss, saved = r.render_l1(st_b, views, tg)
     grads = st_b.zero_grads()
-    r.backward(st_b, saved, dl, grads)
+    r.backward(st_b, saved, dl, grads,
+               reg=dict(opacity_reg=params["opacity_reg"], scale_reg=params["scale_reg"]),
+               loss=loss)
     saved.release()
     adam = {}
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
