@@ -12,6 +12,8 @@ adds two steps that are plain array bookkeeping:
 * ``schedule_expire`` and ``mature`` -- the maturation of Alg. 1 (mature);
 * ``reg_loss_grad`` -- the opacity and scale regularisers of Alg. 1 reg() (Sec. 4.4);
 * ``mean_grad_scale`` -- the per-Gaussian gradient scale on the means (Sec. 4.5.1);
+* ``slice_encode`` / ``slice_decode`` -- the Table 6 attribute quantisation of a
+  streamed slice and the Sec. 5.5 tail drop of its lowest-opacity Gaussians;
 * ``l1_loss_grad`` -- the L1 photometric term of Alg. 1 (loss_func) and its
   gradient.
 """
@@ -155,6 +157,7 @@ def lib():
         _lib.or_sgld_step.restype = C.c_int64
         _lib.or_sgld_step.argtypes = [P(OrState), P(OrFGrads), P(OrAdam), C.c_void_p, C.c_int32,
                                       P(OrSgldParams), C.c_uint64, C.c_uint64, C.c_void_p]
+        _lib.or_opacity_u8.argtypes = [C.c_void_p, C.c_int64, C.c_void_p]
         _lib.or_num_threads.restype = C.c_int
         _lib.or_record_tiles.restype = C.c_int32
         _lib.or_record_tiles.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
@@ -554,3 +557,74 @@ def mean_grad_scale(start, window_start: int, swin_size: int, decay: float):
     current lifespan [start, start + swin_size) so far (k >= 1)."""
     k = np.maximum(1, window_start - np.asarray(start, np.int64) + swin_size)
     return np.float64(decay) ** (k - 1).astype(np.float64)
+
+
+def opacity_u8(logits) -> np.ndarray:
+    """Table 6 opacity code k = rint(255 sigmoid(logit)) (FP32, key-mode exp)."""
+    lg = _c(logits, np.float32)
+    out = np.zeros(max(1, lg.size), np.uint8)
+    lib().or_opacity_u8(_p(lg), lg.size, _p(out))
+    return out[: lg.size].copy()
+
+
+def slice_encode(rows, keep: int):
+    """Table 6 quantisation of one slice (Sec. 5.6.2: means fp16, rotation
+    uint8, scale fp16, opacity uint8, only the DC of the SH kept, at full
+    precision) and the ABR tail drop of Sec. 5.5 (keep the `keep` Gaussians of
+    highest opacity, ties by slot; the rest travel as nothing and are marked
+    empty on decode). The slice's rows share one lifespan (Sec. 4.2.1), sent
+    once. Returns the packet as a dict of arrays, kept rows in slot order.
+
+    Codes: means and log-scales: float16 (round to nearest even); quaternion:
+    q / |q| per component as rint((q_c + 1) * 127.5); opacity: opacity_u8; DC:
+    float32."""
+    S = rows.n
+    keep = int(min(max(keep, 0), S))
+    order = np.lexsort((np.arange(S), -rows.opacity_logits.astype(np.float64)))
+    kept = np.sort(order[:keep]).astype(np.uint32)
+    q = rows.quats[kept].astype(np.float32)
+    nn = q[:, 0] * q[:, 0]
+    nn = nn + q[:, 1] * q[:, 1]
+    nn = nn + q[:, 2] * q[:, 2]
+    nn = nn + q[:, 3] * q[:, 3]
+    qn = q / np.sqrt(nn)[:, None]
+    qk = np.clip(np.rint((qn + np.float32(1.0)) * np.float32(127.5)), 0, 255).astype(np.uint8)
+    return dict(count=S, keep=keep, sh_degree=rows.sh_degree,
+                birth=int(rows.birth[0]) if S else 0, start=int(rows.start[0]) if S else 0,
+                expire=int(rows.expire[0]) if S else 0,
+                index=kept, means=rows.means[kept].astype(np.float16),
+                log_scales=rows.log_scales[kept].astype(np.float16), quats=qk,
+                opacity=opacity_u8(rows.opacity_logits[kept]),
+                dc=rows.sh[kept, 0, :].astype(np.float32))
+
+
+def slice_decode(pkt, make):
+    """Inverse of slice_encode into a full slice of pkt['count'] rows built by
+    make(n, sh_degree) -> empty scene: kept rows get means and log-scales back
+    to float32, q_c = k * (2/255) - 1, logit = ln(o / (1 - o)) with o =
+    clamp(k, 0.5, 254.5) / 255, the DC and zero higher SH bands, the slice's
+    lifespan and frozen = 1 (a streamed snapshot); dropped rows are left empty
+    (start = expire: never active)."""
+    S, K = pkt["count"], (pkt["sh_degree"] + 1) ** 2
+    out = make(S, pkt["sh_degree"])
+    out.start[:] = pkt["start"]
+    out.expire[:] = pkt["start"]
+    out.birth[:] = pkt["birth"]
+    out.frozen[:] = 1
+    i = pkt["index"].astype(np.int64)
+    out.means[i] = pkt["means"].astype(np.float32)
+    out.log_scales[i] = pkt["log_scales"].astype(np.float32)
+    out.quats[i] = pkt["quats"].astype(np.float32) * np.float32(2.0 / 255.0) - np.float32(1.0)
+    o = np.clip(pkt["opacity"].astype(np.float32), np.float32(0.5), np.float32(254.5)) \
+        / np.float32(255.0)
+    out.opacity_logits[i] = np.log(o / (np.float32(1.0) - o))
+    out.sh[i] = 0.0
+    out.sh[i, 0, :] = pkt["dc"]
+    out.expire[i] = pkt["expire"]
+    return out
+
+
+def slice_packet_bytes(count: int, keep: int) -> int:
+    """Payload bytes of a packet: 29 per kept Gaussian (6 + 6 + 4 + 1 + 12),
+    plus a 4-byte slot index each when the tail drop removed any."""
+    return keep * 29 + (4 * keep if keep < count else 0)

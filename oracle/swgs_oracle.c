@@ -1416,3 +1416,23 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+
+/*
+ * Table 6 opacity code (uint8): k = rint(255 sigmoid(logit)), the sigmoid
+ * computed in FP32 through the key-mode exp above so that the integer does not
+ * depend on a library's exp. Round half to even (rintf, default mode).
+ */
+void or_opacity_u8(const float *logits, int64_t n, uint8_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        float e = km_exp(-logits[i]);
+        float den = 1.0f + e;
+        float o = 1.0f / den;
+        float t = o * 255.0f;
+        float k = rintf(t);
+        if (k < 0.0f) k = 0.0f;
+        if (k > 255.0f) k = 255.0f;
+        out[i] = (uint8_t)k;
+    }
+}
