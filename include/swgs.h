@@ -190,6 +190,41 @@ swgs_status swgs_mature(swgs_ctx *ctx, const swgs_gaussians *buf, int64_t num_gs
                         int32_t snapshot_on_host, int64_t *n_out, void *stream);
 
 /*
+ * Streamed-slice codec: the attribute quantisation of Table 6 as the paper
+ * practises it (Sec. 5.6.2: means and log-scales fp16, rotation uint8,
+ * opacity uint8, only the DC of the SH kept, at full precision) and the ABR
+ * tail drop of Sec. 5.5 (keep the `keep` highest-opacity Gaussians of the
+ * slice, ties by slot; the others travel as nothing and decode as empty).
+ *
+ * Packet layout (all little-endian): int32 header[8] = {magic 0x43574753,
+ * version 1, count, keep, sh_degree, birth, start, expire}, then sections each
+ * starting on a 16-byte boundary: slot index uint32[keep] (only when keep <
+ * count), means fp16[keep][3], log_scales fp16[keep][3], rotation
+ * uint8[keep][4] = rint((q_c / |q| + 1) * 127.5), opacity uint8[keep] =
+ * rint(255 sigmoid(logit)) (FP32, the key-mode exp), DC float[keep][3]. Rows
+ * are in slot order; the slice's lifespan (shared by its rows, Sec. 4.2.1)
+ * is taken from its row 0. 29 bytes per kept Gaussian (+4 with the index).
+ */
+size_t swgs_slice_packet_bytes(int64_t count, int64_t keep); /* 0 if keep > count */
+
+/* Encode rows [0, count) of src (device) into `out` (device, or pinned host
+ * when out_on_host = 1; complete when the stream reaches this point). */
+swgs_status swgs_slice_encode(swgs_ctx *ctx, const swgs_gaussians *src, int64_t count,
+                              int64_t keep, void *out, size_t out_capacity, int32_t out_on_host,
+                              size_t *out_bytes, void *stream);
+
+/* Decode a packet into slots [first, first + count) of dst (Alg. 2's slice
+ * replacement): kept rows get their attributes (q_c = k * 2/255 - 1, logit =
+ * ln(o / (1 - o)) with o = clamp(k, 0.5, 254.5) / 255, DC and zero higher SH
+ * bands), the slice's lifespan and frozen = 1; dropped rows are emptied (zero
+ * attributes, start = expire: never active). A device packet costs one stream
+ * synchronisation (to read its header). SWGS_EINVAL: bad or truncated packet,
+ * SH degree mismatch, slots outside dst. */
+swgs_status swgs_slice_decode(swgs_ctx *ctx, const void *packet, size_t bytes,
+                              int32_t packet_on_host, const swgs_gaussians *dst, int64_t first,
+                              void *stream);
+
+/*
  * Alg. 1 schedule_expire, which the paper leaves undefined (reading): after the
  * first window, slice k of the gs slots (slice_size = num_gs / swin_size)
  * gets expire = k for k >= 1 and slice 0 expire = swin_size, so that exactly

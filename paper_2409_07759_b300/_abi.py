@@ -122,6 +122,12 @@ PROTOTYPES = [
     ("swgs_render_bwd_reg", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_void_p,
                                       C.POINTER(C.c_void_p), C.POINTER(SwgsGaussians),
                                       C.POINTER(SwgsRegParams), C.c_void_p, C.c_void_p]),
+    ("swgs_slice_packet_bytes", C.c_size_t, [C.c_int64, C.c_int64]),
+    ("swgs_slice_encode", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_int64, C.c_int64,
+                                    C.c_void_p, C.c_size_t, C.c_int32, C.POINTER(C.c_size_t),
+                                    C.c_void_p]),
+    ("swgs_slice_decode", C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_int32,
+                                    C.POINTER(SwgsGaussians), C.c_int64, C.c_void_p]),
     ("swgs_mature", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_int64, C.c_int32,
                               C.c_int32, C.POINTER(C.c_int64), C.POINTER(SwgsGaussians),
                               C.c_int32, C.POINTER(C.c_int64), C.c_void_p]),

@@ -422,6 +422,37 @@ class Renderer:
                                                   C.byref(s), int(bool(src_on_host)),
                                                   self._stream(stream)))
 
+    # -- streamed-slice codec (Table 6, Sec. 5.5) ---------------------------------
+    @staticmethod
+    def slice_packet_bytes(count: int, keep: int) -> int:
+        return int(_abi.load().swgs_slice_packet_bytes(int(count), int(keep)))
+
+    def slice_encode(self, src: GaussianState, count: int, keep: Optional[int] = None,
+                     out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Encode rows [0, count) of src; keep < count drops the lowest-opacity
+        Gaussians. out: a uint8 tensor (device, or pinned host) of at least
+        slice_packet_bytes(count, keep) bytes; allocated on the device if None.
+        Returns the packet (a view of out)."""
+        keep = count if keep is None else int(keep)
+        nbytes = self.slice_packet_bytes(count, keep)
+        if out is None:
+            out = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        used = C.c_size_t(0)
+        g = src.c_struct()
+        self._check(_abi.load().swgs_slice_encode(self.ctx, C.byref(g), int(count), keep,
+                                                  out.data_ptr(), out.numel(),
+                                                  int(not out.is_cuda), C.byref(used),
+                                                  self._stream(stream)))
+        return out[:used.value]
+
+    def slice_decode(self, packet: torch.Tensor, dst: GaussianState, first: int, stream=None):
+        """Decode a packet (device or pinned host uint8 tensor) into the slots
+        [first, first + count) of dst."""
+        d = dst.c_struct()
+        self._check(_abi.load().swgs_slice_decode(self.ctx, packet.data_ptr(), packet.numel(),
+                                                  int(not packet.is_cuda), C.byref(d),
+                                                  int(first), self._stream(stream)))
+
     # -- Alg. 1 mature / schedule_expire ---------------------------------------
     def schedule_expire(self, buf: GaussianState, num_gs: int, swin_size: int, stream=None):
         """Stagger the gs expiries after the first window (slice k: expire k,

@@ -75,7 +75,8 @@ struct swgs_ctx {
     cudaStream_t last_stream = nullptr;
     // transient scratch
     Buf frames, block_cnt, scan_tmp, counts, order_a, order_b, tcount, koff, keys_a, keys_b,
-        vals_tmp, vals_b, sranges, tile_cnt, tile_off, mature_ids, mature_stage, sort_tmp, counter, totals, l1_tab, reloc_w, reloc_cdf, reloc_dead, reloc_tg,
+        vals_tmp, vals_b, sranges, tile_cnt, tile_off, mature_ids, mature_stage, codec_keys_a,
+        codec_keys_b, codec_vals_a, codec_vals_b, codec_flags, codec_idx, codec_stage, sort_tmp, counter, totals, l1_tab, reloc_w, reloc_cdf, reloc_dead, reloc_tg,
         reloc_cnt, reloc_nd;
     void* pinned = nullptr;
     size_t pinned_cap = 0;
@@ -661,7 +662,9 @@ void swgs_destroy(swgs_ctx* ctx) {
     Buf* bs[] = {&ctx->frames, &ctx->block_cnt, &ctx->scan_tmp, &ctx->counts, &ctx->order_a,
                  &ctx->order_b, &ctx->tcount, &ctx->koff, &ctx->keys_a, &ctx->keys_b,
                  &ctx->vals_tmp, &ctx->vals_b, &ctx->sranges, &ctx->tile_cnt, &ctx->tile_off,
-                 &ctx->mature_ids, &ctx->mature_stage, &ctx->sort_tmp, &ctx->counter, &ctx->totals, &ctx->l1_tab,
+                 &ctx->mature_ids, &ctx->mature_stage, &ctx->codec_keys_a, &ctx->codec_keys_b,
+                 &ctx->codec_vals_a, &ctx->codec_vals_b, &ctx->codec_flags, &ctx->codec_idx,
+                 &ctx->codec_stage, &ctx->sort_tmp, &ctx->counter, &ctx->totals, &ctx->l1_tab,
                  &ctx->reloc_w, &ctx->reloc_cdf, &ctx->reloc_dead, &ctx->reloc_tg,
                  &ctx->reloc_cnt, &ctx->reloc_nd};
     for (Buf* b : bs) ctx_free(ctx, *b, s);
@@ -761,6 +764,103 @@ static swgs_status check_mature_buffer(swgs_ctx* ctx, const swgs_gaussians* buf,
     if (swin_size <= 0 || num_gs % swin_size != 0)
         return fail(ctx, SWGS_EINVAL, "num_gs %lld is not a multiple of swin_size %d",
                     (long long)num_gs, swin_size);
+    return SWGS_OK;
+}
+
+size_t swgs_slice_packet_bytes(int64_t count, int64_t keep) {
+    if (count < 0 || keep < 0 || keep > count) return 0;
+    CodecLayout L;
+    codec_layout(count, keep, &L);
+    return L.total;
+}
+
+swgs_status swgs_slice_encode(swgs_ctx* ctx, const swgs_gaussians* src, int64_t count,
+                              int64_t keep, void* out, size_t out_capacity, int32_t out_on_host,
+                              size_t* out_bytes, void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    swgs_status st = check_gaussians(ctx, src, true);
+    if (st != SWGS_OK) return st;
+    if (!src->birth || count < 0 || count > src->capacity || keep < 0 || keep > count ||
+        count > 0x7fffffffLL || !out || !out_bytes)
+        return fail(ctx, SWGS_EINVAL, "bad slice encode arguments (count %lld, keep %lld)",
+                    (long long)count, (long long)keep);
+    CodecLayout L;
+    codec_layout(count, keep, &L);
+    if (out_capacity < L.total)
+        return fail(ctx, SWGS_EINVAL, "packet needs %zu bytes, buffer has %zu", L.total,
+                    out_capacity);
+    *out_bytes = L.total;
+    const uint32_t* idx = nullptr;
+    if (keep > 0 && keep < count) {
+        const long long nb = (count + 255) / 256;
+        const size_t n = (size_t)count;
+        if (!ensure(ctx, ctx->codec_keys_a, 4 * n, s) || !ensure(ctx, ctx->codec_keys_b, 4 * n, s) ||
+            !ensure(ctx, ctx->codec_vals_a, 4 * n, s) || !ensure(ctx, ctx->codec_vals_b, 4 * n, s) ||
+            !ensure(ctx, ctx->codec_flags, n, s) || !ensure(ctx, ctx->codec_idx, 4 * n, s) ||
+            !ensure(ctx, ctx->block_cnt, 4 * (size_t)(nb + 1), s) ||
+            !ensure(ctx, ctx->scan_tmp, scan_u32_temp_bytes(nb + 1) + 64, s) ||
+            !ensure(ctx, ctx->totals, 64, s) ||
+            !ensure(ctx, ctx->sort_tmp, radix_temp_bytes(count, ctx->num_sms), s))
+            return fail(ctx, SWGS_ENOMEM, "allocation failed (slice encode)");
+        CodecScratch w{P<uint32_t>(ctx->codec_keys_a), P<uint32_t>(ctx->codec_keys_b),
+                       P<uint32_t>(ctx->codec_vals_a), P<uint32_t>(ctx->codec_vals_b),
+                       P<uint32_t>(ctx->block_cnt), P<uint32_t>(ctx->codec_idx),
+                       P<uint8_t>(ctx->codec_flags), ctx->sort_tmp.p, ctx->scan_tmp.p,
+                       P<unsigned long long>(ctx->totals)};
+        uint32_t* sel = nullptr;
+        CK(launch_codec_select(src->opacity_logits, count, keep, w, ctx->num_sms, &sel, s));
+        idx = sel;
+    }
+    unsigned char* dst = (unsigned char*)out;
+    if (out_on_host) {
+        if (!ensure(ctx, ctx->codec_stage, L.total, s))
+            return fail(ctx, SWGS_ENOMEM, "allocation failed (slice encode)");
+        dst = P<unsigned char>(ctx->codec_stage);
+    }
+    CK(launch_codec_encode(*src, idx, count, keep, L, dst, s));
+    if (out_on_host) CK(cudaMemcpyAsync(out, dst, L.total, cudaMemcpyDeviceToHost, s));
+    return SWGS_OK;
+}
+
+swgs_status swgs_slice_decode(swgs_ctx* ctx, const void* packet, size_t bytes,
+                              int32_t packet_on_host, const swgs_gaussians* dst, int64_t first,
+                              void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    swgs_status st = check_gaussians(ctx, dst, true);
+    if (st != SWGS_OK) return st;
+    if (!packet || bytes < kCodecHeaderBytes)
+        return fail(ctx, SWGS_EINVAL, "packet shorter than its header");
+    int32_t h[8];
+    if (packet_on_host) {
+        memcpy(h, packet, sizeof(h));
+    } else {
+        CK(cudaMemcpyAsync(ctx->pinned, packet, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        memcpy(h, ctx->pinned, sizeof(h));
+    }
+    const long long count = h[2], keep = h[3];
+    if ((uint32_t)h[0] != kCodecMagic || h[1] != kCodecVersion || count < 0 || keep < 0 ||
+        keep > count || h[4] != dst->sh_degree)
+        return fail(ctx, SWGS_EINVAL, "not a slice packet of this version and SH degree");
+    CodecLayout L;
+    codec_layout(count, keep, &L);
+    if (bytes < L.total) return fail(ctx, SWGS_EINVAL, "packet truncated (%zu < %zu)", bytes, L.total);
+    if (first < 0 || first + count > dst->capacity)
+        return fail(ctx, SWGS_EINVAL, "slice [%lld, %lld) outside capacity %lld", (long long)first,
+                    (long long)(first + count), (long long)dst->capacity);
+    const unsigned char* in = (const unsigned char*)packet;
+    if (packet_on_host) {
+        if (!ensure(ctx, ctx->codec_stage, L.total, s))
+            return fail(ctx, SWGS_ENOMEM, "allocation failed (slice decode)");
+        CK(cudaMemcpyAsync(ctx->codec_stage.p, packet, L.total, cudaMemcpyHostToDevice, s));
+        in = P<unsigned char>(ctx->codec_stage);
+    }
+    StageScope sc_(ctx, SWGS_STAGE_UPDATE, s);
+    CK(launch_codec_decode(*dst, first, count, keep, L, in, h[5], h[6], h[7], s));
     return SWGS_OK;
 }
 

@@ -436,6 +436,29 @@ cudaError_t launch_mature_move(const swgs_gaussians& buf, const int32_t* ids, lo
 cudaError_t launch_schedule_expire(int32_t* expire, long long num_gs, int swin_size,
                                    cudaStream_t s);
 
+// k_codec.cu (Table 6 codec, Sec. 5.5 tail drop)
+constexpr size_t kCodecHeaderBytes = 32;
+constexpr uint32_t kCodecMagic = 0x43574753u;  // "SGWC" little-endian
+constexpr int32_t kCodecVersion = 1;
+struct CodecLayout {
+    size_t index, means, log_scales, quats, opacity, dc, total;  // byte offsets
+};
+void codec_layout(long long count, long long keep, CodecLayout* L);
+struct CodecScratch {
+    uint32_t *keys_a, *keys_b, *vals_a, *vals_b, *block_cnt, *idx;
+    uint8_t* flags;
+    void *sort_tmp, *scan_tmp;
+    unsigned long long* total;
+};
+cudaError_t launch_codec_select(const float* logits, long long count, long long keep,
+                                CodecScratch& w, int num_sms, uint32_t** out_idx, cudaStream_t s);
+cudaError_t launch_codec_encode(const swgs_gaussians& src, const uint32_t* idx, long long count,
+                                long long keep, const CodecLayout& L, unsigned char* out,
+                                cudaStream_t s);
+cudaError_t launch_codec_decode(const swgs_gaussians& dst, long long first, long long count,
+                                long long keep, const CodecLayout& L, const unsigned char* in,
+                                int32_t birth, int32_t start, int32_t expire, cudaStream_t s);
+
 // k_blend.cu
 struct BlendArgs {
     const ViewDev* views;
