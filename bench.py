@@ -175,6 +175,74 @@ def mature_leg(state, swin=50, reps=20):
             "achieved_gbs": moved / (dev_ms / 1e3) / 1e9}
 
 
+def codec_leg(state, views, slice_size=6000, fracs=(1.0, 0.8, 0.6, 0.4, 0.2)):
+    """Table 6 codec + Sec. 5.5 tail drop on the window scene: encode/decode
+    time of one 6,000-row slice (pinned host packets, as a client receives
+    them), and the rate-distortion of keeping a fraction of every slice (the
+    Fig. 10-12 sweep: 100/80/60/40/20%), as packet bytes per update and PSNR of
+    the decoded scene's render against the unquantised render (4 views)."""
+    import torch
+    from paper_2409_07759_b300 import api
+    r = api.Renderer()
+    n = state.n - state.n % slice_size
+    sl = state.rows(0, slice_size)
+    host = torch.empty(api.Renderer.slice_packet_bytes(slice_size, slice_size),
+                       dtype=torch.uint8).pin_memory()
+    dst = api.GaussianState(*[t.clone() for t in (state.means, state.log_scales, state.quats,
+                                                   state.opacity_logits, state.sh, state.start,
+                                                   state.expire, state.birth, state.frozen)],
+                            sh_degree=state.sh_degree)
+    enc, dec = [], []
+    for _ in range(20):
+        torch.cuda.synchronize()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        pkt = r.slice_encode(sl, slice_size, out=host)
+        b.record()
+        r.slice_decode(pkt, dst, 0)
+        c.record()
+        c.synchronize()
+        enc.append(a.elapsed_time(b))
+        dec.append(b.elapsed_time(c))
+    # slices share one lifespan (Sec. 4.2.1): a copy of the scene active over
+    # the rendered frames
+    base = api.GaussianState(*[t.clone() for t in (state.means, state.log_scales, state.quats,
+                                                    state.opacity_logits, state.sh, state.start,
+                                                    state.expire, state.birth, state.frozen)],
+                             sh_degree=state.sh_degree)
+    base.start.zero_()
+    base.birth.zero_()
+    base.expire.fill_(1000)
+    state = base
+    vs = views[:4]
+    ref, _ = r.render(state, vs)
+    curve = []
+    for f in fracs:
+        keep = int(round(f * slice_size))
+        q = api.GaussianState(*[t.clone() for t in (state.means, state.log_scales, state.quats,
+                                                     state.opacity_logits, state.sh,
+                                                     state.start, state.expire, state.birth,
+                                                     state.frozen)], sh_degree=state.sh_degree)
+        nbytes = 0
+        for first in range(0, n, slice_size):
+            p = r.slice_encode(state.rows(first, first + slice_size), slice_size, keep)
+            nbytes = p.numel()
+            r.slice_decode(p, q, first)
+        img, _ = r.render(q, vs)
+        mse = sum(float(((x - y) ** 2).mean()) for x, y in zip(img, ref)) / len(vs)
+        curve.append({"keep_fraction": f, "packet_bytes_per_slice": nbytes,
+                      "psnr_db": 10.0 * math.log10(1.0 / max(mse, 1e-20))})
+    r.close()
+    raw_row = 4 * (3 + 3 + 4 + 1 + state.sh.shape[1] * 3)
+    return {"slice_rows": slice_size, "encode_ms": statistics.median(enc),
+            "decode_ms": statistics.median(dec),
+            "packet_bytes": api.Renderer.slice_packet_bytes(slice_size, slice_size),
+            "raw_bytes": slice_size * raw_row, "bytes_per_gaussian": 29,
+            "rate_distortion": curve,
+            "note": "PSNR of the decoded synthetic scene against its unquantised render "
+                    "(DC-only SH and fp16/uint8 codes); not a dataset PSNR"}
+
+
 def serving_leg(args):
     """Config 4: 300k Gaussians in 50 slices of 6,000 (swin_size 50), one
     slice swapped per frame at 30 fps, Poisson viewers on orbits requesting the
@@ -555,6 +623,8 @@ def main():
     if not args.no_serving:
         torch.cuda.synchronize()
         extra["mature"] = mature_leg(state)
+        torch.cuda.synchronize()
+        extra["codec"] = codec_leg(state, views)
         torch.cuda.synchronize()
         extra["serving"] = serving_leg(args)
     if not args.no_config3:
