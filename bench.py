@@ -243,6 +243,54 @@ def codec_leg(state, views, slice_size=6000, fracs=(1.0, 0.8, 0.6, 0.4, 0.2)):
                     "(DC-only SH and fp16/uint8 codes); not a dataset PSNR"}
 
 
+def memory_leg(lengths=(10, 30, 100), num_gs=300_000, swin=5):
+    """Table 3 in spirit: peak device memory of Alg. 1 main (ClipTrainer) over
+    clips of 10, 30 and 100 frames -- 300k Gaussians (swin 5: 60k-row slices),
+    one 676x507 view per frame, one step per window, the stream to pinned host."""
+    import torch
+    from paper_2409_07759_b300 import api, synth
+    from paper_2409_07759_b300.window import ClipTrainer
+    w, h = 676, 507
+    sc, _, _ = synth.config2(width=w, height=h, n=num_gs, n_frames=1, per_frame=1)
+    ring = synth.ring_cameras(20, 4.0, w, h)
+
+    def window(st, ed):
+        views, targets = [], []
+        g = torch.Generator(device="cuda")
+        for f in range(st, ed):
+            v = ring[f % 20]
+            views.append(synth.View(v.width, v.height, v.fx, v.fy, v.cx, v.cy, v.R, v.t, f))
+            g.manual_seed(f)
+            targets.append(torch.randint(0, 256, (3, h, w), dtype=torch.uint8, device="cuda",
+                                         generator=g))
+        return views, targets
+
+    out = {}
+    for T in lengths:
+        r = api.Renderer()
+        torch.cuda.synchronize()
+        base = torch.cuda.memory_allocated()
+        torch.cuda.reset_peak_memory_stats()
+        # the stream goes out as Table 6 packets (as a server would send it)
+        sent = [0, 0]
+
+        def sink(st, n, pkt):
+            sent[0] += n
+            sent[1] += pkt.numel()
+        ct = ClipTrainer(r, api.GaussianState.from_scene(sc), swin, window, iterations=1,
+                         codec=True, sink=sink)
+        t0 = time.perf_counter()
+        ct.run(T)
+        torch.cuda.synchronize()
+        out[str(T)] = {"peak_bytes_over_base": int(torch.cuda.max_memory_allocated() - base),
+                       "seconds": time.perf_counter() - t0,
+                       "stream_rows": sent[0], "stream_bytes": sent[1]}
+        r.close()
+        del ct
+        torch.cuda.empty_cache()
+    return {"num_gs": num_gs, "swin_size": swin, "view": f"{w}x{h}", "clips": out}
+
+
 def serving_leg(args):
     """Config 4: 300k Gaussians in 50 slices of 6,000 (swin_size 50), one
     slice swapped per frame at 30 fps, Poisson viewers on orbits requesting the
@@ -625,6 +673,8 @@ def main():
         extra["mature"] = mature_leg(state)
         torch.cuda.synchronize()
         extra["codec"] = codec_leg(state, views)
+        torch.cuda.synchronize()
+        extra["memory_invariance"] = memory_leg()
         torch.cuda.synchronize()
         extra["serving"] = serving_leg(args)
     if not args.no_config3:

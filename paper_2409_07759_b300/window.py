@@ -159,11 +159,18 @@ class ClipTrainer:
 
     window(st, ed) -> (views, targets): the training views of frames [st, ed)
     and their target images (device tensors, float32 or uint8).
+    Each maturation's rows go to sink(st, n, data): with codec = False, data is
+    a dict of host tensors of the n rows as they were (stream.write); with
+    codec = True, host uint8 packets of the slice codec (Table 6), one per
+    slice of num_gs / swin_size rows (`keep` gives the Sec. 5.5 tail drop as a
+    fraction of each slice's rows). The default sink
+    appends (st, n, data) to self.stream. The snapshot and packet buffers are
+    allocated once, so memory does not grow with the clip.
     """
 
     def __init__(self, renderer: api.Renderer, gs: api.GaussianState, swin_size: int,
                  window, iterations: int = 1, params: Optional[dict] = None, seed: int = 0,
-                 snapshot_to_host: bool = True):
+                 codec: bool = False, keep: float = 1.0, sink=None):
         self.r = renderer
         self.num_gs = gs.n
         if self.num_gs % swin_size:
@@ -176,8 +183,18 @@ class ClipTrainer:
         self.step_count = 0
         views, targets = window(0, swin_size)
         self.trainer = WindowTrainer(renderer, self.buf, views, targets, params=params, seed=seed)
-        self.snapshot_to_host = snapshot_to_host
-        self.stream = []   # [(st, n, snapshot)]
+        self.codec = codec
+        self.keep = keep
+        self.stream = []   # [(st, n, data)] with the default sink
+        self.sink = sink if sink is not None else (lambda st, n, d: self.stream.append((st, n, d)))
+        self._snap = api.GaussianState(
+            *[torch.empty_like(getattr(self.buf, k)[:self.num_gs]) for k in
+              api.PARAM_NAMES + ("start", "expire", "birth", "frozen")],
+            sh_degree=self.buf.sh_degree)
+        self._packet = None
+        if codec:
+            n = api.Renderer.slice_packet_bytes(self.num_gs, self.num_gs) + 16
+            self._packet = torch.empty(n, dtype=torch.uint8).pin_memory()
 
     def _train(self, st: int):
         views, targets = self.window(st, st + self.swin)
@@ -189,17 +206,26 @@ class ClipTrainer:
             self.step_count += 1
         return loss
 
-    def _snapshot(self):
-        s = api.GaussianState(*[torch.empty_like(getattr(self.buf, k)[:self.num_gs]) for k in
-                                api.PARAM_NAMES + ("start", "expire", "birth", "frozen")],
-                              sh_degree=self.buf.sh_degree)
-        return s.pin_host() if self.snapshot_to_host else s
-
     def mature(self, st: int):
-        snap = self._snapshot()
         n, self.head = self.r.mature(self.buf, self.num_gs, st, self.swin, self.head,
-                                     snapshot=snap)
-        self.stream.append((st, n, snap))
+                                     snapshot=self._snap)
+        if n == 0:
+            self.sink(st, 0, None)
+            return 0
+        if self.codec:
+            # one packet per slice (a slice's rows share their lifespan, Sec.
+            # 4.2.1): the first full snapshot gives swin_size of them
+            S = self.num_gs // self.swin
+            for c0 in range(0, n, S):
+                m = min(S, n - c0)
+                keep = max(0, min(m, int(round(self.keep * m))))
+                pkt = self.r.slice_encode(self._snap.rows(c0, c0 + m), m, keep, out=self._packet)
+                torch.cuda.current_stream().synchronize()
+                self.sink(st, m, pkt.clone())
+        else:
+            rows = {k: getattr(self._snap, k)[:n].cpu() for k in
+                    api.PARAM_NAMES + ("start", "expire", "birth", "frozen")}
+            self.sink(st, n, rows)
         return n
 
     def run(self, total_frames: int):

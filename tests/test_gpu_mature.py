@@ -125,6 +125,24 @@ def test_clip_trainer_streams_a_valid_alg2_sequence(oracle_mod):
     for st, n, snap in ct.stream[1:]:
         assert set(snap["birth"][:n].tolist()) == {st - 1}
     assert bool((ct.buf.frozen[num_gs:] == 1).all()) and bool((ct.buf.frozen[:num_gs] == 0).all())
+    # the codec stream decodes, on the device, into a client buffer that covers
+    # every frame with num_gs Gaussians (Alg. 2 with Table 6 packets)
+    ct2 = ClipTrainer(r, api.GaussianState.from_scene(sc), swin, window, iterations=1, seed=1,
+                      codec=True)
+    ct2.run(T)
+    assert [n for _, n, _ in ct2.stream] == [S] * (swin + T - 1)
+    client = api.GaussianState.from_scene(sc)
+    for k in range(swin):  # Alg. 2 main: the first num_gs Gaussians
+        r.slice_decode(ct2.stream[k][2], client, k * S)
+    ev = {}
+    for st, n, pkt in ct2.stream[swin:]:
+        ev[st - 1] = pkt
+    for f in range(T):
+        if f in ev:
+            first, _ = api.slice_range(f, swin, num_gs)
+            r.slice_decode(ev[f], client, first)
+        act = (client.start <= f) & (client.expire > f)
+        assert int(act.sum()) == num_gs, f
 
     def scene_of(snap, n):
         d = {k: snap[k][:n].numpy().copy() for k in FIELDS}
@@ -137,3 +155,43 @@ def test_clip_trainer_streams_a_valid_alg2_sequence(oracle_mod):
             buffer = oracle_mod.frame_update(buffer, events[f], f, swin)
         assert int(((buffer.start <= f) & (f < buffer.expire)).sum()) == num_gs, f
     r.close()
+
+
+def test_training_memory_does_not_grow_with_clip_length():
+    """Table 3 in spirit: the device memory of training a clip (Alg. 1 main)
+    is the same for 10, 30 and 100 frames -- the buffer holds gs and the
+    matured ring, the window's views are the only per-step inputs and the
+    stream goes to pinned host memory."""
+    from paper_2409_07759_b300 import api
+    from paper_2409_07759_b300.window import ClipTrainer
+    swin, S = 5, 60
+    num_gs = swin * S
+    sc, _, _ = synth.config2(width=64, height=48, n=num_gs, n_frames=1, per_frame=1)
+    ring = synth.ring_cameras(20, 4.0, 64, 48)
+
+    def window(st, ed):
+        views, targets = [], []
+        g = torch.Generator(device="cuda")
+        for f in range(st, ed):
+            v = ring[f % 20]
+            views.append(synth.View(v.width, v.height, v.fx, v.fy, v.cx, v.cy, v.R, v.t, f))
+            g.manual_seed(f)
+            targets.append(torch.randint(0, 256, (3, 48, 64), dtype=torch.uint8, device="cuda",
+                                         generator=g))
+        return views, targets
+
+    peaks = {}
+    for T in (10, 30, 100):
+        r = api.Renderer()
+        ct = ClipTrainer(r, api.GaussianState.from_scene(sc), swin, window, iterations=1)
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats()
+        base = torch.cuda.memory_allocated()
+        ct.run(T)
+        torch.cuda.synchronize()
+        peaks[T] = torch.cuda.max_memory_allocated() - base
+        assert len(ct.stream) == T
+        r.close()
+        del ct
+    assert peaks[10] > 0
+    assert max(peaks.values()) <= 1.02 * min(peaks.values()), peaks
