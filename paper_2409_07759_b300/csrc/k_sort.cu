@@ -14,6 +14,8 @@
 // per-key tile sort (ceil(log2(tiles)) bits, 2 passes up to 18 bits). Sorting
 // records by depth and then keys stably by tile gives the order of a stable
 // sort on (tile << 32 | depth), the per-tile depth ordering of Eq. 3.
+#include <atomic>
+
 #include "swgs_internal.cuh"
 
 namespace swgs {
@@ -233,14 +235,19 @@ cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_
     off += scan_u32_temp_bytes((long long)kMaxBins * G + 1);
     off = (off + 255) & ~(size_t)255;
     unsigned long long* total = (unsigned long long*)((char*)temp + off);
-    static bool attr_set = false;
+    // the shared-memory opt-in is a per-device function attribute
+    constexpr int kMaxDevices = 64;
+    static std::atomic<bool> attr_set[kMaxDevices];
     const size_t smem = sizeof(DownSmem);
-    if (!attr_set) {
+    int dev = 0;
+    cudaError_t e0 = cudaGetDevice(&dev);
+    if (e0 != cudaSuccess) return e0;
+    if (dev < 0 || dev >= kMaxDevices || !attr_set[dev].load()) {
         cudaError_t e = cudaFuncSetAttribute(radix_downsweep,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        if (dev >= 0 && dev < kMaxDevices) attr_set[dev].store(true);
     }
     uint32_t *ki = keys_a, *vi = vals_a, *ko = keys_b, *vo = vals_b;
     int shift = plan.begin_bit;
