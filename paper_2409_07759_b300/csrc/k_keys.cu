@@ -12,11 +12,6 @@ namespace swgs {
 // tile's list is the same depth-ordered list a per-tile key sort gives, from a
 // sort over about a fifth as many keys (4x4 super tiles of 16x16-pixel tiles).
 
-__device__ __forceinline__ int super_count(short4 rc, int tiles, int sx, int sy) {
-    if (tiles == 0) return 0;
-    return (rc.y / sx - rc.x / sx + 1) * (rc.w / sy - rc.z / sy + 1);
-}
-
 // out[k] = super tiles keyed by the k-th record in depth order; *exact += the
 // records' exact tile counts (the number of per-tile list entries).
 __global__ void __launch_bounds__(256)
@@ -27,9 +22,8 @@ gather_supers_kernel(const uint32_t* __restrict__ order, Records rec, int sx, in
     unsigned long long t = 0;
     if (k < n) {
         const uint32_t r = order[k];
-        const int tiles = rec.tiles[r];
-        out[k] = (uint32_t)super_count(rec.rect[r], tiles, sx, sy);
-        t = (unsigned long long)tiles;
+        out[k] = (uint32_t)rec.supers[r];
+        t = (unsigned long long)rec.tiles[r];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
@@ -65,10 +59,13 @@ __device__ __forceinline__ int record_row_run(const Records& rec, uint32_t r, sh
 }
 
 // The k-th record in depth order writes, for every super tile of its super
-// rectangle (row-major, at offsets[k]), the key (global super tile id) |
-// (coverage mask << 16) and the value r. Bit ly*SX + lx of the mask is set when
-// the record covers tile (lx, ly) of the super tile by the row rule. The sort
-// reads only the low 16 bits (the super tile id), so the mask rides along.
+// rectangle that holds one of its tiles (row-major, at offsets[k]), the key
+// (global super tile id) | (coverage mask << 16) and the value r. Bit
+// ly*SX + lx of the mask is set when the record covers tile (lx, ly) of the
+// super tile by the row rule. The sort reads only the low 16 bits (the super
+// tile id), so the mask rides along. Positions of the record's range left over
+// (the projection's count is an upper bound) get the key of its first super
+// tile with an empty mask, which the expansion passes over.
 __global__ void __launch_bounds__(256)
 emit_supers_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
                    long long n_rec, Records rec, const ViewDev* __restrict__ views, int n_views,
@@ -83,6 +80,7 @@ emit_supers_kernel(const uint32_t* __restrict__ order, const uint32_t* __restric
         const ViewDev& V = views[find_view_by_record(views, n_views, (int)r)];
         const int x0 = rc.x / sx, x1 = rc.y / sx, y0 = rc.z / sy, y1 = rc.w / sy;
         uint32_t o = offsets[k];
+        const uint32_t o_end = o + (uint32_t)rec.supers[r];
         for (int y = y0; y <= y1; ++y) {
             int f[8], n[8];
 #pragma unroll
@@ -101,10 +99,16 @@ emit_supers_kernel(const uint32_t* __restrict__ order, const uint32_t* __restric
                     const int lo = max(f[ly], tx0), hi = min(f[ly] + n[ly], tx0 + sx);
                     if (ly < sy && lo < hi) m |= ((1u << (hi - lo)) - 1u) << (lo - tx0 + ly * sx);
                 }
-                keys[o] = (uint32_t)(V.super_base + y * V.nsx + x) | (m << 16);
-                vals[o] = r;
-                ++o;
+                if (m != 0 && o < o_end) {
+                    keys[o] = (uint32_t)(V.super_base + y * V.nsx + x) | (m << 16);
+                    vals[o] = r;
+                    ++o;
+                }
             }
+        }
+        for (; o < o_end; ++o) {
+            keys[o] = (uint32_t)(V.super_base + y0 * V.nsx + x0);
+            vals[o] = r;
         }
     }
 }
@@ -263,18 +267,20 @@ cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, cons
 // sranges[t] = [first, last+1) of super tile t (the low 16 key bits) in the
 // sorted super keys (sranges zeroed before).
 __global__ void super_ranges_kernel(const uint32_t* __restrict__ keys, long long n,
-                                    int2* __restrict__ ranges) {
+                                    long long n_supers, int2* __restrict__ ranges) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t t = keys[i] & 0xffffu;
+    if (t >= n_supers) return;
     if (i == 0 || (keys[i - 1] & 0xffffu) != t) ranges[t].x = (int)i;
     if (i == n - 1 || (keys[i + 1] & 0xffffu) != t) ranges[t].y = (int)(i + 1);
 }
 
-cudaError_t launch_super_ranges(const uint32_t* keys, long long n, int2* ranges, cudaStream_t s) {
+cudaError_t launch_super_ranges(const uint32_t* keys, long long n, long long n_supers,
+                                int2* ranges, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     note_launch();
-    super_ranges_kernel<<<div_up(n, 256), 256, 0, s>>>(keys, n, ranges);
+    super_ranges_kernel<<<div_up(n, 256), 256, 0, s>>>(keys, n, n_supers, ranges);
     return cudaGetLastError();
 }
 

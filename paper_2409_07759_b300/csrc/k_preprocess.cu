@@ -168,6 +168,7 @@ struct PreArgs {
     const int32_t* ids;
     long long total_active;
     int tile_w, tile_h;
+    int sx, sy;  // super tile in tiles
     float near_plane;
     Records rec;
 };
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_
         p[k] = kadd(kadd(kadd(s0, s1), s2), V.t[k]);
     }
     const float z = p[2];
-    int tiles = 0;
+    int tiles = 0, supers = 0;
     short4 rect = make_short4(0, -1, 0, -1);
     float u = 0.f, v = 0.f, A = 0.f, B = 0.f, C = 0.f;
     bool culled = !(z > a.near_plane);
@@ -278,6 +279,10 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_
                 const KmEllipse el = km_ellipse(A, B, C);
                 const bool narrow = x1 - x0 < 255;
                 uint16_t* runs = a.rec.runs + r * kRunRows;
+                // super tiles holding kept tiles: per super row, the span of super
+                // columns its tile rows' runs reach (a convex ellipse's rows leave
+                // no gap in practice; any overcount is padded by the emission)
+                int srow = -1, smin = 0, smax = -1;
                 for (int ty = y0; ty <= y1; ++ty) {
                     int f = 0, l = 0;
                     const int cnt = km_row_run_fast(el, u, v, x0, x1, ty, a.tile_w, a.tile_h,
@@ -285,7 +290,20 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_
                     if (ty - y0 < kRunRows && narrow)
                         runs[ty - y0] = (uint16_t)((cnt ? (f - x0) : 0) | (cnt << 8));
                     tiles += cnt;
+                    if (cnt > 0) {
+                        const int sr = ty / a.sy, c0 = f / a.sx, c1 = (f + cnt - 1) / a.sx;
+                        if (sr != srow) {
+                            if (smax >= smin) supers += smax - smin + 1;
+                            srow = sr;
+                            smin = c0;
+                            smax = c1;
+                        } else {
+                            smin = min(smin, c0);
+                            smax = max(smax, c1);
+                        }
+                    }
                 }
+                if (smax >= smin) supers += smax - smin + 1;
             }
             rect = make_short4((short)x0, (short)x1, (short)y0, (short)y1);
         }
@@ -312,6 +330,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_
     a.rec.c[r] = make_float4(fmaxf(col0 + 0.5f, 0.f), fmaxf(col1 + 0.5f, 0.f),
                              fmaxf(col2 + 0.5f, 0.f), 0.f);
     a.rec.tiles[r] = culled ? 0 : tiles;
+    a.rec.supers[r] = culled ? 0 : supers;
     a.rec.rect[r] = culled ? make_short4(0, -1, 0, -1) : rect;
     a.rec.depth_key[r] = (culled || tiles == 0) ? 0xffffffffu : __float_as_uint(z);
 }
@@ -321,7 +340,8 @@ cudaError_t launch_preprocess(const swgs_gaussians& g, const ViewDev* views, con
                               long long n_rec, int tile_w, int tile_h, float near_plane,
                               Records rec, cudaStream_t s) {
     if (n_rec <= 0) return cudaSuccess;
-    PreArgs a{g, views, groups, n_groups, ids, total_active, tile_w, tile_h, near_plane, rec};
+    PreArgs a{g, views, groups, n_groups, ids, total_active, tile_w, tile_h, super_w(tile_w),
+              super_h(tile_w), near_plane, rec};
     note_launch();
     preprocess_kernel<<<div_up(n_rec, 256), 256, 0, s>>>(a, n_rec);
     return cudaGetLastError();

@@ -49,7 +49,7 @@ struct BatchState {
     std::vector<GroupDev> h_groups;
     std::vector<int> call_index;    // table entry -> index in the call's view list
     Buf views, groups, ids, rec_a, rec_b, rec_c, rec_tiles, rec_rect, rec_depth, rec_runs, vals,
-        ranges, T, last, grad2d;
+        ranges, T, last, grad2d, rec_supers;
     bool has_grad2d = false;
 };
 
@@ -208,7 +208,7 @@ void free_saved_buffers(swgs_ctx* c, swgs_saved* s, cudaStream_t st) {
     for (auto& b : s->batches) {
         Buf* bs[] = {&b.views, &b.groups, &b.ids, &b.rec_a, &b.rec_b, &b.rec_c, &b.rec_tiles,
                      &b.rec_rect, &b.rec_depth, &b.rec_runs, &b.vals, &b.ranges, &b.T, &b.last,
-                     &b.grad2d};
+                     &b.grad2d, &b.rec_supers};
         for (Buf* x : bs) ctx_free(c, *x, st);
     }
     ctx_free(c, s->pairs, st);
@@ -223,6 +223,7 @@ Records records_of(BatchState& b) {
     r.rect = P<short4>(b.rec_rect);
     r.depth_key = P<uint32_t>(b.rec_depth);
     r.runs = P<uint16_t>(b.rec_runs);
+    r.supers = P<int32_t>(b.rec_supers);
     return r;
 }
 
@@ -352,6 +353,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
         !ensure(ctx, B.rec_a, sizeof(float4) * R, s) || !ensure(ctx, B.rec_b, sizeof(float4) * R, s) ||
         !ensure(ctx, B.rec_c, sizeof(float4) * R, s) ||
         !ensure(ctx, B.rec_tiles, sizeof(int32_t) * R, s) ||
+        !ensure(ctx, B.rec_supers, sizeof(int32_t) * R, s) ||
         !ensure(ctx, B.rec_rect, sizeof(short4) * R, s) ||
         !ensure(ctx, B.rec_depth, sizeof(uint32_t) * R, s) ||
         !ensure(ctx, B.rec_runs, sizeof(uint16_t) * kRunRows * R, s) ||
@@ -445,7 +447,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
         {
             StageScope sc_(ctx, SWGS_STAGE_RANGES, s);
             CK(cudaMemsetAsync(ctx->sranges.p, 0, sizeof(int2) * (size_t)supers, s));
-            CK(launch_super_ranges(skeys, (long long)K, P<int2>(ctx->sranges), s));
+            CK(launch_super_ranges(skeys, (long long)K, supers, P<int2>(ctx->sranges), s));
             CK(launch_expand_count(P<int2>(ctx->sranges), skeys, P<ViewDev>(B.views),
                                    (int)B.h_views.size(), (int)supers, tw,
                                    P<uint32_t>(ctx->tile_cnt), s));

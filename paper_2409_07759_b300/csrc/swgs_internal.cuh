@@ -60,6 +60,7 @@ struct Records {
     short4* rect;      // tx0, tx1, ty0, ty1
     uint32_t* depth_key;  // FP32 depth bits, 0xffffffff if no tiles
     uint16_t* runs;    // kRunRows per record: first - tx0 (low byte), length (high byte)
+    int32_t* supers;   // super tiles holding at least one of the record's tiles
 };
 
 // Rows of a record whose tile runs are stored; taller rectangles recompute the rest.
@@ -417,7 +418,8 @@ cudaError_t launch_emit_supers(const uint32_t* order, const uint32_t* offsets, l
                                const Records rec, const ViewDev* views, int n_views, int sx,
                                int sy, int tile_w, int tile_h, int num_sms, uint32_t* keys,
                                uint32_t* vals, cudaStream_t s);
-cudaError_t launch_super_ranges(const uint32_t* keys, long long n, int2* ranges, cudaStream_t s);
+cudaError_t launch_super_ranges(const uint32_t* keys, long long n, long long n_supers,
+                                int2* ranges, cudaStream_t s);
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
                                 int n_views, int total_supers, int tile_w, uint32_t* tcount,
                                 cudaStream_t s);
