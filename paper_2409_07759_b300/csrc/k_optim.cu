@@ -45,38 +45,49 @@ __device__ __forceinline__ void adam1(float* p, float* m, float* v, float g, flo
     *v = vv;
 }
 
+// Adam, one thread per parameter element (coalesced); blockIdx.y picks the
+// array: 0 means, 1 log-scales, 2 quaternions, 3 opacity logits, 4 SH.
+__global__ void __launch_bounds__(256) adam_kernel(SgldArgs a) {
+    const int arr = blockIdx.y;
+    const int K = (a.g.sh_degree + 1) * (a.g.sh_degree + 1);
+    float *P, *M, *V;
+    const float* G;
+    long long w;
+    float lr;
+    switch (arr) {
+        case 0: P = a.g.means; M = a.adam.m_means; V = a.adam.v_means; G = a.grads.means;
+                w = 3; lr = a.p.lr_means; break;
+        case 1: P = a.g.log_scales; M = a.adam.m_log_scales; V = a.adam.v_log_scales;
+                G = a.grads.log_scales; w = 3; lr = a.p.lr_log_scales; break;
+        case 2: P = a.g.quats; M = a.adam.m_quats; V = a.adam.v_quats; G = a.grads.quats;
+                w = 4; lr = a.p.lr_quats; break;
+        case 3: P = a.g.opacity_logits; M = a.adam.m_logits; V = a.adam.v_logits;
+                G = a.grads.opacity_logits; w = 1; lr = a.p.lr_logits; break;
+        default: P = a.g.sh; M = a.adam.m_sh; V = a.adam.v_sh; G = a.grads.sh; w = 3LL * K;
+                 lr = a.p.lr_sh_rest; break;
+    }
+    const long long n = a.g.capacity * w;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / w;
+        if (!is_eligible(a.g, i, a.frames, a.n_frames)) continue;
+        float g = G[e];
+        float l = lr;
+        if (arr == 0 && a.p.mean_grad_decay != 1.f && a.p.swin_size > 0) {
+            // Sec. 4.5.1: the means gradient shrinks with the windows that have
+            // trained the slot's current lifespan
+            const int k = max(1, a.p.window_start - a.g.start[i] + a.p.swin_size);
+            g *= exp2f((float)(k - 1) * log2f(a.p.mean_grad_decay));
+        }
+        if (arr == 4 && (e - i * w) < 3) l = a.p.lr_sh_dc;  // the DC band
+        adam1(&P[e], &M[e], &V[e], g, l, a);
+    }
+}
+
 __global__ void __launch_bounds__(256) sgld_kernel(SgldArgs a) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.g.capacity) return;
     if (!is_eligible(a.g, i, a.frames, a.n_frames)) return;
-    const int K = (a.g.sh_degree + 1) * (a.g.sh_degree + 1);
-    if (a.p.adam && a.has_grads && a.has_adam) {
-        // Sec. 4.5.1: the means gradient shrinks with the windows that have
-        // trained the slot's current lifespan
-        float gscale = 1.f;
-        if (a.p.mean_grad_decay != 1.f && a.p.swin_size > 0) {
-            const int k = max(1, a.p.window_start - a.g.start[i] + a.p.swin_size);
-            gscale = exp2f((float)(k - 1) * log2f(a.p.mean_grad_decay));
-        }
-        for (int k = 0; k < 3; ++k) {
-            adam1(&a.g.means[3 * i + k], &a.adam.m_means[3 * i + k], &a.adam.v_means[3 * i + k],
-                  a.grads.means[3 * i + k] * gscale, a.p.lr_means, a);
-            adam1(&a.g.log_scales[3 * i + k], &a.adam.m_log_scales[3 * i + k],
-                  &a.adam.v_log_scales[3 * i + k], a.grads.log_scales[3 * i + k],
-                  a.p.lr_log_scales, a);
-        }
-        for (int k = 0; k < 4; ++k)
-            adam1(&a.g.quats[4 * i + k], &a.adam.m_quats[4 * i + k], &a.adam.v_quats[4 * i + k],
-                  a.grads.quats[4 * i + k], a.p.lr_quats, a);
-        adam1(&a.g.opacity_logits[i], &a.adam.m_logits[i], &a.adam.v_logits[i],
-              a.grads.opacity_logits[i], a.p.lr_logits, a);
-        for (int k = 0; k < K; ++k)
-            for (int ch = 0; ch < 3; ++ch) {
-                const long long e = (i * K + k) * 3 + ch;
-                adam1(&a.g.sh[e], &a.adam.m_sh[e], &a.adam.v_sh[e], a.grads.sh[e],
-                      k == 0 ? a.p.lr_sh_dc : a.p.lr_sh_rest, a);
-            }
-    }
     // noise from the (possibly updated) opacity and covariance
     const float o = 1.f / (1.f + expf(-a.g.opacity_logits[i]));
     const float gate = 1.f / (1.f + expf(a.p.noise_k * (o - a.p.noise_t)));
@@ -128,6 +139,15 @@ cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
     a.bc2 = (float)(1.0 - pow((double)p.beta2, (double)(step + 1)));
     a.seed = seed;
     a.step = step;
+    if (p.adam && grads && adam) {
+        const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+        long long gx = div_up(g.capacity * 3LL * K, 256);
+        if (gx > 148LL * 16) gx = 148LL * 16;
+        note_launch();
+        adam_kernel<<<dim3((unsigned)gx, 5), 256, 0, s>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     note_launch();
     sgld_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
