@@ -41,6 +41,8 @@ struct TileGeom {
     static_assert(TH % PPT == 0, "pixels per thread must divide the tile height");
 };
 
+constexpr int kFwdUnroll = 8;
+
 template <int TW, int TH, int BATCH, int PPT, bool COUNT>
 __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
     constexpr int NT = TileGeom<TW, TH, PPT>::NT;
@@ -83,8 +85,15 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
             }
             __syncthreads();
             const int cnt = min(BATCH, rg.y - b0);
-            for (int j = 0; j < cnt; ++j) {
+            // kFwdUnroll staged Gaussians per iteration, in list order (one warp
+            // vote and one loop test for all); a pixel done after one of them
+            // ignores the rest
+            for (int j2 = 0; j2 < cnt; j2 += kFwdUnroll) {
                 if (__all_sync(F, tdone)) break;
+#pragma unroll
+                for (int jj = 0; jj < kFwdUnroll; ++jj) {
+                const int j = j2 + jj;
+                if (j >= cnt) break;
                 const float4 g0 = s0[j];
                 const float4 g1 = s1[j];
                 const float4 c = s2[j];
@@ -106,6 +115,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
                     C2[p] = __fmaf_rn(c.z, w, C2[p]);
                     T[p] = __fsub_rn(T[p], w);
                     last[p] = inc ? pos1 : last[p];
+                }
                 }
                 tdone = true;
 #pragma unroll
