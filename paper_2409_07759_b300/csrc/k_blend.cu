@@ -42,6 +42,7 @@ struct TileGeom {
 };
 
 constexpr int kFwdUnroll = 8;
+constexpr int kBwdUnroll = 2;
 
 template <int TW, int TH, int BATCH, int PPT, bool COUNT>
 __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
@@ -265,9 +266,15 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                 stage_gaussian(a.rec, r, &s0[k], &s1[k], &s2[k]);
             }
             __syncthreads();
-            for (int j = cnt - 1; j >= 0; --j) {
+            // kBwdUnroll staged Gaussians per iteration, back to front; the
+            // group is skipped when it lies beyond every pixel's last
+            for (int j2 = cnt - 1; j2 >= 0; j2 -= kBwdUnroll) {
+                if (__all_sync(F, b0 + max(j2 - kBwdUnroll + 1, 0) - rg.x >= mylast)) continue;
+#pragma unroll
+                for (int jj = 0; jj < kBwdUnroll; ++jj) {
+                const int j = j2 - jj;
+                if (j < 0) break;
                 const int pos = b0 + j - rg.x;
-                if (__all_sync(F, pos >= mylast)) continue;
                 const float4 g0 = s0[j];
                 const float4 g1 = s1[j];
                 const float4 c = s2[j];
@@ -315,6 +322,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                     m[7] = m7;
                     m[8] = m8;
                     warp_sum9_to_smem(m, &s_acc[j * 9]);
+                }
                 }
             }
             __syncthreads();
