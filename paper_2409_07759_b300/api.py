@@ -214,7 +214,7 @@ class Renderer:
 
     def __init__(self, tile=(16, 16), batch=128, near_plane=0.2, blocks_per_sm=0,
                  count_pairs=False, pixels_per_thread=2, bwd_pixels_per_thread=None,
-                 bwd_batch=128, use_torch_allocator=True):
+                 bwd_batch=64, use_torch_allocator=True):
         if bwd_pixels_per_thread is None:  # 8x8 tiles hold at most 2 pixels per thread
             bwd_pixels_per_thread = 2 if tuple(tile) == (8, 8) else 8
         L = _abi.load()

@@ -622,7 +622,7 @@ swgs_status swgs_default_config(swgs_config* cfg) {
     cfg->count_pairs = 0;
     cfg->pixels_per_thread = 2;
     cfg->bwd_pixels_per_thread = 8;
-    cfg->bwd_batch = 128;
+    cfg->bwd_batch = 64;
     return SWGS_OK;
 }
 
