@@ -314,3 +314,51 @@ def test_fused_forward_l1(R, oracle_mod):
     ref_img = oracle_mod.render(sc, views[0], mode="tiled")["rgb"]
     ref_loss, _ = oracle_mod.l1_loss_grad([ref_img], targets)
     assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-5)
+
+
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_backward_sh_degrees(oracle_mod, deg):
+    """Gradients of every attribute for SH degrees 0-2 (degree 3 above)."""
+    from paper_2409_07759_b300 import api
+    r = api.Renderer()
+    sc, view = synth.tiny_scene(5 + deg, n=180, sh_degree=deg, width=80, height=64, depth=3.0,
+                                log_scale_mean=-2.2, spread=0.9)
+    view.fx = view.fy = 80.0
+    d = np.random.default_rng(deg).normal(size=(3, 64, 80))
+    print(_grads_vs_oracle(r, oracle_mod, sc, [view], [d], bg=(0.2, 0.1, 0.0)))
+    r.close()
+
+
+def test_batches_split_by_super_tiles():
+    """A batched call whose views hold more than 2^16 super tiles (8x8 tiles:
+    32x32-pixel super tiles; 33 views of 1920x1080 need 67,320) runs in
+    several batches and gives exactly the images of the plain path."""
+    from paper_2409_07759_b300 import api
+    sc, _, _ = synth.config2(width=64, height=48, n=20000, n_frames=1, per_frame=1)
+    ring = synth.ring_cameras(20, 4.0, 1920, 1080)
+    views = []
+    for j in range(33):
+        v = ring[j % 20]
+        views.append(synth.View(v.width, v.height, v.fx, v.fy, v.cx, v.cy, v.R, v.t, 150))
+    r = api.Renderer(tile=(8, 8), pixels_per_thread=2)
+    st = _state(sc)
+    a, saved = r.render(st, views, batched=True, keep_saved=True)
+    assert saved.info().n_batches == 2
+    saved.release()
+    b, _ = r.render(st, views, batched=False)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    r.close()
+
+
+def test_view_beyond_the_super_tile_limit_is_rejected():
+    from paper_2409_07759_b300 import api
+    from paper_2409_07759_b300._abi import SwgsError
+    sc, _ = synth.tiny_scene(1, n=10, sh_degree=0)
+    # 8x8 tiles, 32-pixel super tiles: 8224 x 8224 pixels hold 257^2 > 2^16
+    v = synth.View(8224, 8224, 8000.0, 8000.0, 4112.0, 4112.0, np.eye(3, dtype=np.float32),
+                   np.zeros(3, np.float32), 0)
+    r = api.Renderer(tile=(8, 8), pixels_per_thread=2)
+    with pytest.raises(SwgsError):
+        r.render(_state(sc), [v])
+    r.close()
