@@ -214,7 +214,7 @@ class Renderer:
 
     def __init__(self, tile=(16, 16), batch=128, near_plane=0.2, blocks_per_sm=0,
                  count_pairs=False, pixels_per_thread=2, bwd_pixels_per_thread=None,
-                 bwd_batch=64, use_torch_allocator=True):
+                 bwd_batch=64, use_torch_allocator=True, alloc_guard=None):
         if bwd_pixels_per_thread is None:  # 8x8 tiles hold at most 2 pixels per thread
             bwd_pixels_per_thread = 2 if tuple(tile) == (8, 8) else 8
         L = _abi.load()
@@ -229,11 +229,16 @@ class Renderer:
         cfg.bwd_pixels_per_thread = int(bwd_pixels_per_thread)
         cfg.bwd_batch = int(bwd_batch)
         self.cfg = cfg
+        self.alloc_guard = alloc_guard
         self.device = torch.cuda.current_device()
         if use_torch_allocator:
             dev = self.device
 
             def _alloc(user, nbytes, stream):
+                # alloc_guard(nbytes) -> False refuses the allocation (a memory
+                # budget, or an injected failure): the call returns SWGS_ENOMEM
+                if self.alloc_guard is not None and not self.alloc_guard(int(nbytes)):
+                    return None
                 try:
                     return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
                 except Exception:

@@ -186,7 +186,7 @@ class ClipTrainer:
         self.codec = codec
         self.keep = keep
         self.stream = []   # [(st, n, data)] with the default sink
-        self.sink = sink if sink is not None else (lambda st, n, d: self.stream.append((st, n, d)))
+        self.sink = sink   # None: append to self.stream (no self-reference, no cycle)
         self._snap = api.GaussianState(
             *[torch.empty_like(getattr(self.buf, k)[:self.num_gs]) for k in
               api.PARAM_NAMES + ("start", "expire", "birth", "frozen")],
@@ -210,7 +210,7 @@ class ClipTrainer:
         n, self.head = self.r.mature(self.buf, self.num_gs, st, self.swin, self.head,
                                      snapshot=self._snap)
         if n == 0:
-            self.sink(st, 0, None)
+            self._emit(st, 0, None)
             return 0
         if self.codec:
             # one packet per slice (a slice's rows share their lifespan, Sec.
@@ -221,25 +221,77 @@ class ClipTrainer:
                 keep = max(0, min(m, int(round(self.keep * m))))
                 pkt = self.r.slice_encode(self._snap.rows(c0, c0 + m), m, keep, out=self._packet)
                 torch.cuda.current_stream().synchronize()
-                self.sink(st, m, pkt.clone())
+                self._emit(st, m, pkt.clone())
         else:
             rows = {k: getattr(self._snap, k)[:n].cpu() for k in
                     api.PARAM_NAMES + ("start", "expire", "birth", "frozen")}
-            self.sink(st, n, rows)
+            self._emit(st, n, rows)
         return n
 
-    def run(self, total_frames: int):
-        """Alg. 1 main (the initial Gaussians are the caller's gs); returns the
-        loss of the last step."""
-        # main: birth = start = 0, expire = swin_size for every gs slot
-        g = self.buf.rows(0, self.num_gs)
-        g.birth.zero_()
-        g.start.zero_()
-        g.expire.fill_(self.swin)
-        loss = self._train(0)
-        self.r.schedule_expire(self.buf, self.num_gs, self.swin)
-        for st in range(1, total_frames):
+    def _emit(self, st, n, data):
+        if self.sink is None:
+            self.stream.append((st, n, data))
+        else:
+            self.sink(st, n, data)
+
+    def run(self, total_frames: int, start: int = 0, stop: Optional[int] = None):
+        """Alg. 1 main (the initial Gaussians are the caller's gs) over the
+        window starts [start, stop) of a clip of total_frames frames (start 0:
+        the first window; a later start continues a run restored with
+        load_state_dict; stop defaults to the end, where the last maturation
+        runs). Returns the loss of the last step."""
+        stop = total_frames if stop is None else min(stop, total_frames)
+        loss = None
+        if start == 0 and stop > 0:
+            # main: birth = start = 0, expire = swin_size for every gs slot
+            g = self.buf.rows(0, self.num_gs)
+            g.birth.zero_()
+            g.start.zero_()
+            g.expire.fill_(self.swin)
+            loss = self._train(0)
+            self.r.schedule_expire(self.buf, self.num_gs, self.swin)
+            start = 1
+            self.next_start = 1
+        for st in range(start, stop):
             self.mature(st)
             loss = self._train(st)
-        self.mature(total_frames)
+            self.next_start = st + 1
+        if stop == total_frames and getattr(self, "next_start", 0) == total_frames:
+            self.mature(total_frames)
+            self.next_start = total_frames + 1
         return loss
+
+    def state_dict(self) -> dict:
+        """Everything a resumed run needs: the buffer (gs and matured ring),
+        the Adam moments, the ring head, the step counter, the seed and the
+        next window start (random draws are counter-based, nothing else)."""
+        arrays = {k: getattr(self.buf, k) for k in
+                  api.PARAM_NAMES + ("start", "expire", "birth", "frozen")}
+        arrays.update({"adam_" + k: v for k, v in self.trainer.adam.items()})
+        scalars = dict(num_gs=self.num_gs, swin_size=self.swin, head=self.head,
+                       step_count=self.step_count, seed=self.trainer.seed,
+                       sh_degree=self.buf.sh_degree, next_start=getattr(self, "next_start", 0))
+        return {"arrays": arrays, "scalars": scalars}
+
+    def load_state_dict(self, sd: dict):
+        a, sc = sd["arrays"], sd["scalars"]
+        if sc["num_gs"] != self.num_gs or sc["swin_size"] != self.swin:
+            raise ValueError("checkpoint of another num_gs / swin_size")
+        for k in api.PARAM_NAMES + ("start", "expire", "birth", "frozen"):
+            getattr(self.buf, k).copy_(a[k])
+        for k, v in self.trainer.adam.items():
+            v.copy_(a["adam_" + k])
+        self.head = int(sc["head"])
+        self.step_count = int(sc["step_count"])
+        self.trainer.seed = int(sc["seed"])
+        self.next_start = int(sc["next_start"])
+
+    def save(self, path):
+        from . import checkpoint
+        sd = self.state_dict()
+        checkpoint.save(path, sd["arrays"], sd["scalars"])
+
+    def load(self, path):
+        from . import checkpoint
+        arrays, scalars = checkpoint.load(path)
+        self.load_state_dict({"arrays": arrays, "scalars": scalars})

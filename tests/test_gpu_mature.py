@@ -2,6 +2,8 @@
 against the oracle, step by step over a clip: the matured count, the
 snapshot rows (stream.write), the optimisable half of the buffer and the ring
 of matured rows read oldest first from its head, all bit for bit."""
+import gc
+
 import numpy as np
 import pytest
 
@@ -184,6 +186,7 @@ def test_training_memory_does_not_grow_with_clip_length():
     for T in (10, 30, 100):
         r = api.Renderer()
         ct = ClipTrainer(r, api.GaussianState.from_scene(sc), swin, window, iterations=1)
+        gc.collect()
         torch.cuda.synchronize()
         torch.cuda.reset_peak_memory_stats()
         base = torch.cuda.memory_allocated()
@@ -193,5 +196,6 @@ def test_training_memory_does_not_grow_with_clip_length():
         assert len(ct.stream) == T
         r.close()
         del ct
+        gc.collect()
     assert peaks[10] > 0
     assert max(peaks.values()) <= 1.02 * min(peaks.values()), peaks
