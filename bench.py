@@ -79,8 +79,8 @@ def parse():
     ap.add_argument("--views", type=int, default=4, help="cameras per frame")
     ap.add_argument("--frames", type=int, default=10)
     ap.add_argument("--tile", default="16x16", help="blend tile, WxH")
-    ap.add_argument("--batch", type=int, default=128, help="Gaussians staged per block step")
-    ap.add_argument("--ppt", type=int, default=2, help="forward blend pixels per thread")
+    ap.add_argument("--batch", type=int, default=64, help="Gaussians staged per block step")
+    ap.add_argument("--ppt", type=int, default=4, help="forward blend pixels per thread")
     ap.add_argument("--bwd-ppt", type=int, default=8, help="reverse blend pixels per thread")
     ap.add_argument("--bwd-batch", type=int, default=64, help="reverse blend staging batch")
     ap.add_argument("--targets", default="u8", choices=["u8", "f32"],

@@ -100,8 +100,8 @@ typedef struct swgs_view {
 typedef struct swgs_ctx swgs_ctx;
 typedef struct swgs_saved swgs_saved;
 
-/* Fills cfg with 16x16 tiles; forward batch 256 with 2 pixels per thread;
- * reverse blend batch 128 with 4 pixels per thread; near plane 0.2; auto grid. */
+/* Fills cfg with 16x16 tiles; forward batch 64 with 4 pixels per thread;
+ * reverse blend batch 64 with 8 pixels per thread; near plane 0.2; auto grid. */
 swgs_status swgs_default_config(swgs_config *cfg);
 
 /* Creates a context on the current CUDA device. alloc/free may be NULL. */

@@ -212,10 +212,12 @@ class Renderer:
     """One libswgs context (tile shape, batch size, near plane). Scratch memory
     comes from torch's caching allocator through the library's callbacks."""
 
-    def __init__(self, tile=(16, 16), batch=128, near_plane=0.2, blocks_per_sm=0,
-                 count_pairs=False, pixels_per_thread=2, bwd_pixels_per_thread=None,
+    def __init__(self, tile=(16, 16), batch=64, near_plane=0.2, blocks_per_sm=0,
+                 count_pairs=False, pixels_per_thread=None, bwd_pixels_per_thread=None,
                  bwd_batch=64, use_torch_allocator=True, alloc_guard=None):
-        if bwd_pixels_per_thread is None:  # 8x8 tiles hold at most 2 pixels per thread
+        if pixels_per_thread is None:      # 8x8 tiles hold at most 2 pixels per thread
+            pixels_per_thread = 2 if tuple(tile) == (8, 8) else 4
+        if bwd_pixels_per_thread is None:
             bwd_pixels_per_thread = 2 if tuple(tile) == (8, 8) else 8
         L = _abi.load()
         cfg = _abi.SwgsConfig()

@@ -42,6 +42,9 @@ struct TileGeom {
 };
 
 constexpr int kFwdUnroll = 8;
+// row coordinate of a finished pixel in the packed forward: (kGone - y)^2
+// overflows, so q = -inf for every Gaussian (no NaN: |t1 dx| stays finite)
+constexpr float kGone = 3.0e30f;
 constexpr int kBwdUnroll = 2;
 
 template <int TW, int TH, int BATCH, int PPT, bool COUNT>
@@ -175,6 +178,192 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
     }
 }
 
+// Forward with the pixels of a thread taken two at a time as float2: every
+// per-pixel step is one packed FP32x2 instruction (__fadd2_rn, __fmul2_rn,
+// __ffma2_rn round each half exactly like the scalar _rn forms), so the
+// result is bit-identical to blend_fwd_kernel with half the issue slots on
+// the FMA pipe. The staged terms are duplicated into pairs; the centre and the
+// colour are staged negated so that w is carried as -w:
+// -w = (-alpha) T, C + c w = C + (-c)(-w) and T - w = T + (-w), all exact
+// rewrites of the same roundings.
+__device__ __forceinline__ void stage_gaussian_x2(const Records& rec, uint32_t r, float4* sa,
+                                                  float4* sb, float4* sc, float4* sd,
+                                                  float4* se) {
+    const float4 A = rec.a[r];
+    const float4 B = rec.b[r];
+    const float4 Cc = rec.c[r];
+    const float qa = __fmul_rn(B.x, -0.5f * kLog2e), qb = __fmul_rn(B.y, -kLog2e);
+    const float qc = __fmul_rn(B.z, -0.5f * kLog2e);
+    const float lo = __log2f(A.z);
+    *sa = make_float4(-A.x, -A.x, -A.y, -A.y);
+    *sb = make_float4(qa, qa, qb, qb);
+    *sc = make_float4(qc, qc, lo, lo);
+    *sd = make_float4(-Cc.x, -Cc.x, -Cc.y, -Cc.y);
+    *se = make_float4(-Cc.z, -Cc.z, pair_qmin(lo), 0.f);
+}
+
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// 4 pixels a thread: at least 20 blocks of 64 threads per SM (48 registers),
+// measured faster than the 66-register build at 15 blocks
+template <int TW, int TH, int BATCH, int PPT, bool COUNT>
+__global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 20 : 1)) blend_fwd_x2_kernel(BlendArgs a) {
+    static_assert(PPT % 2 == 0, "pixels are taken in pairs");
+    constexpr int NT = TileGeom<TW, TH, PPT>::NT;
+    constexpr int NP = PPT / 2;
+    __shared__ float4 sa[BATCH], sb[BATCH], sc[BATCH], sd[BATCH], se[BATCH];
+    __shared__ int s_item;
+    const unsigned F = 0xffffffffu;
+    const int tid = threadIdx.x;
+    const int lx = tid % TW, ly = (tid / TW) * PPT;
+    unsigned long long pairs = 0;
+    float l1 = 0.f;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.work_counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.total_tiles) break;
+        const int vi = find_view_by_tile(a.views, a.n_views, item);
+        const ViewDev& V = a.views[vi];
+        const int W = V.W, H = V.H;
+        const int lt = item - V.tile_base;
+        const int x = (lt % V.ntx) * TW + lx, y0 = (lt / V.ntx) * TH + ly;
+        const float px = (float)x + 0.5f;
+        const float2 px2 = make_float2(px, px);
+        const int2 rg = a.ranges[item];
+        float2 T[NP], C0[NP], C1[NP], C2[NP], py[NP];
+        int last[PPT], stop[PPT];
+        // a pixel that has stopped (or lies outside the image) moves its row
+        // coordinate to kGone: q is then -inf, so no later pair passes the
+        // q >= qmin test and no per-pixel flag is carried through the loop
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            T[i] = make_float2(1.f, 1.f);
+            C0[i] = C1[i] = C2[i] = make_float2(0.f, 0.f);
+            const int ya = y0 + 2 * i, yb = ya + 1;
+            py[i] = make_float2(x < W && ya < H ? (float)ya + 0.5f : kGone,
+                                x < W && yb < H ? (float)yb + 0.5f : kGone);
+        }
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            last[p] = 0;
+            stop[p] = rg.y;
+        }
+        for (int b0 = rg.x; b0 < rg.y; b0 += BATCH) {
+            bool tdone = true;
+#pragma unroll
+            for (int i = 0; i < NP; ++i) tdone &= (py[i].x == kGone) & (py[i].y == kGone);
+            if (__syncthreads_count(tdone) == NT) break;
+            for (int k = tid; k < BATCH; k += NT) {
+                const int idx = b0 + k;
+                if (idx < rg.y)
+                    stage_gaussian_x2(a.rec, a.vals[idx], &sa[k], &sb[k], &sc[k], &sd[k], &se[k]);
+            }
+            __syncthreads();
+            const int cnt = min(BATCH, rg.y - b0);
+            for (int j2 = 0; j2 < cnt; j2 += kFwdUnroll) {
+                if (__all_sync(F, tdone)) break;
+#pragma unroll
+                for (int jj = 0; jj < kFwdUnroll; ++jj) {
+                const int j = j2 + jj;
+                if (j >= cnt) break;
+                const float4 ga = sa[j], gb = sb[j], gc = sc[j], gd = sd[j], ge = se[j];
+                const int pos = b0 + j, pos1 = pos - rg.x + 1;
+                const float2 dx = __fadd2_rn(px2, lo2(ga));
+                const float2 adx = __fmul2_rn(lo2(gb), dx);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    const float2 dy = __fadd2_rn(py[i], hi2(ga));
+                    const float2 t1 = __ffma2_rn(hi2(gb), dy, adx);
+                    const float2 t2 = __fmul2_rn(__fmul2_rn(lo2(gc), dy), dy);
+                    const float2 q = __ffma2_rn(t1, dx, t2);
+                    const float2 v = __fadd2_rn(q, hi2(gc));
+                    // -alpha = max(-0.99, -2^v)
+                    float2 nal = make_float2(fmaxf(-kAlphaMax, -ex2_approx(v.x)),
+                                             fmaxf(-kAlphaMax, -ex2_approx(v.y)));
+                    const bool ok0 = q.x >= ge.z, ok1 = q.y >= ge.z;
+                    // T (1 - alpha), rounded once: the stopping test
+                    const float2 tT = __ffma2_rn(nal, T[i], T[i]);
+                    const bool inc0 = ok0 && tT.x >= kTStop, inc1 = ok1 && tT.y >= kTStop;
+                    if (COUNT) {
+                        stop[2 * i] = (ok0 && !inc0) ? pos : stop[2 * i];
+                        stop[2 * i + 1] = (ok1 && !inc1) ? pos : stop[2 * i + 1];
+                    }
+                    py[i].x = (ok0 && !inc0) ? kGone : py[i].x;
+                    py[i].y = (ok1 && !inc1) ? kGone : py[i].y;
+                    nal.x = inc0 ? nal.x : 0.f;
+                    nal.y = inc1 ? nal.y : 0.f;
+                    const float2 nw = __fmul2_rn(nal, T[i]);      // -w
+                    C0[i] = __ffma2_rn(lo2(gd), nw, C0[i]);
+                    C1[i] = __ffma2_rn(hi2(gd), nw, C1[i]);
+                    C2[i] = __ffma2_rn(lo2(ge), nw, C2[i]);
+                    T[i] = __fadd2_rn(T[i], nw);
+                    last[2 * i] = inc0 ? pos1 : last[2 * i];
+                    last[2 * i + 1] = inc1 ? pos1 : last[2 * i + 1];
+                }
+                }
+                tdone = true;
+#pragma unroll
+                for (int i = 0; i < NP; ++i) tdone &= (py[i].x == kGone) & (py[i].y == kGone);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int y = y0 + p;
+            const float Tp = (p & 1) ? T[p / 2].y : T[p / 2].x;
+            const float c0 = (p & 1) ? C0[p / 2].y : C0[p / 2].x;
+            const float c1 = (p & 1) ? C1[p / 2].y : C1[p / 2].x;
+            const float c2 = (p & 1) ? C2[p / 2].y : C2[p / 2].x;
+            if (x < W && y < H) {
+                const long long hw = (long long)W * H, q = (long long)y * W + x;
+                const float r0 = c0 + Tp * V.bg[0];
+                const float r1 = c1 + Tp * V.bg[1];
+                const float r2 = c2 + Tp * V.bg[2];
+                V.out_rgb[q] = r0;
+                V.out_rgb[hw + q] = r1;
+                V.out_rgb[2 * hw + q] = r2;
+                if (V.out_T) V.out_T[q] = Tp;
+                if (a.T) a.T[V.pix_base + q] = Tp;
+                if (a.last) a.last[V.pix_base + q] = last[p];
+                if (COUNT)
+                    pairs += (unsigned long long)((stop[p] < rg.y ? stop[p] + 1 : rg.y) - rg.x);
+                if (V.target || V.target_u8) {
+                    // L1 term of the loss and its gradient, sign(0) = 0
+                    float t0, t1, t2;
+                    if (V.target_u8) {  // k x (1/255) in FP32
+                        constexpr float kInv255 = 1.0f / 255.0f;
+                        t0 = __fmul_rn((float)V.target_u8[q], kInv255);
+                        t1 = __fmul_rn((float)V.target_u8[hw + q], kInv255);
+                        t2 = __fmul_rn((float)V.target_u8[2 * hw + q], kInv255);
+                    } else {
+                        t0 = V.target[q];
+                        t1 = V.target[hw + q];
+                        t2 = V.target[2 * hw + q];
+                    }
+                    const float e0 = r0 - t0, e1 = r1 - t1, e2 = r2 - t2;
+                    const float s = V.l1_scale;
+                    V.dL_out[q] = e0 > 0.f ? s : (e0 < 0.f ? -s : 0.f);
+                    V.dL_out[hw + q] = e1 > 0.f ? s : (e1 < 0.f ? -s : 0.f);
+                    V.dL_out[2 * hw + q] = e2 > 0.f ? s : (e2 < 0.f ? -s : 0.f);
+                    l1 += (fabsf(e0) + fabsf(e1) + fabsf(e2)) * s;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (a.loss) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(F, l1, o);
+        if ((tid & 31) == 0 && l1 != 0.f) atomicAdd(a.loss, l1);
+    }
+    if (COUNT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) pairs += __shfl_xor_sync(F, pairs, o);
+        if ((tid & 31) == 0 && pairs) atomicAdd(a.pairs, pairs);
+    }
+}
+
 // Sum 9 per-lane values over the warp and add the sums to acc[0..9) in
 // shared memory. Steps 1-3 halve the values each lane holds while doubling
 // the lanes summed, so lane 4m ends with value m (m < 8); value 8 takes a
@@ -205,6 +394,195 @@ __device__ __forceinline__ void warp_sum9_to_smem(const float* v, float* acc) {
     for (int o = 16; o > 0; o >>= 1) v8 += __shfl_xor_sync(F, v8, o);
     if ((lane & 3) == 0 && y != 0.f) atomicAdd(&acc[lane >> 2], y);
     if (lane == 0 && v8 != 0.f) atomicAdd(&acc[8], v8);
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Reverse blend with the pixels of a thread taken two at a time as float2 (the
+// packed FP32x2 instructions of the forward). It uses the forward's packed
+// staging (centre and colour negated) and carries -alpha, so every sign
+// folds into an exact rewrite: 1 - a = 1 + (-a), w = -((-a) T),
+// D + a (E - D) = D + (-a)(D + (-E)), and dL/dm's factor a (T (E - D)) =
+// (-a)(T (D + (-E))). Each thread's per-pixel sums are kept as two partial
+// sums (the halves) and added before the warp reduction.
+// 8 pixels a thread (one warp a tile): at least 20 warps per SM (96 registers,
+// no spills) hide the ex2 -> rcp latency better than 15 at 130 registers
+template <int TW, int TH, int BATCH, int PPT>
+__global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 20 : 1)) blend_bwd_x2_kernel(BlendArgs a) {
+    static_assert(PPT % 2 == 0, "pixels are taken in pairs");
+    constexpr int NT = TileGeom<TW, TH, PPT>::NT;
+    constexpr int NP = PPT / 2;
+    __shared__ float4 sa[BATCH], sb[BATCH], sc[BATCH], sd[BATCH], se[BATCH];
+    __shared__ uint32_t s_rec[BATCH];
+    __shared__ float s_acc[BATCH * 9];
+    __shared__ int s_item, s_maxlast;
+    const unsigned F = 0xffffffffu;
+    const int tid = threadIdx.x;
+    const int lx = tid % TW, ly = (tid / TW) * PPT;
+    const float2 one2 = make_float2(1.f, 1.f), mone2 = make_float2(-1.f, -1.f);
+    for (int k = tid; k < BATCH * 9; k += NT) s_acc[k] = 0.f;
+    for (;;) {
+        if (tid == 0) { s_item = atomicAdd(a.work_counter, 1); s_maxlast = 0; }
+        __syncthreads();
+        const int item = s_item;
+        if (item >= a.total_tiles) break;
+        const int vi = find_view_by_tile(a.views, a.n_views, item);
+        const ViewDev& V = a.views[vi];
+        const int W = V.W, H = V.H;
+        const int lt = item - V.tile_base;
+        const int x = (lt % V.ntx) * TW + lx, y0 = (lt / V.ntx) * TH + ly;
+        const float px = (float)x + 0.5f;
+        const float2 px2 = make_float2(px, px);
+        const int2 rg = a.ranges[item];
+        // Per pixel: T (recovered back to front), dL/dC, and D = sum_ch dL_ch B_ch with
+        // B the colour composited behind the current Gaussian (starts at the
+        // background). With E = sum_ch dL_ch c_ch: dL/dalpha = T (E - D) and the
+        // step to the next Gaussian in front is D' = D + alpha (E - D).
+        float Tv[PPT], dLa[PPT], dLb[PPT], dLc[PPT], Dv[PPT];
+        int last[PPT];
+        int mylast = 0;
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int y = y0 + p;
+            Tv[p] = 1.f; dLa[p] = dLb[p] = dLc[p] = 0.f; last[p] = 0;
+            if (x < W && y < H) {
+                const long long hw = (long long)W * H, q = (long long)y * W + x;
+                Tv[p] = a.T[V.pix_base + q];
+                last[p] = a.last[V.pix_base + q];
+                dLa[p] = V.dL[q];
+                dLb[p] = V.dL[hw + q];
+                dLc[p] = V.dL[2 * hw + q];
+            }
+            Dv[p] = fmaf(dLa[p], V.bg[0], fmaf(dLb[p], V.bg[1], dLc[p] * V.bg[2]));
+            mylast = max(mylast, last[p]);
+        }
+        float2 T[NP], dL0[NP], dL1[NP], dL2[NP], D[NP], py[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            T[i] = make_float2(Tv[2 * i], Tv[2 * i + 1]);
+            dL0[i] = make_float2(dLa[2 * i], dLa[2 * i + 1]);
+            dL1[i] = make_float2(dLb[2 * i], dLb[2 * i + 1]);
+            dL2[i] = make_float2(dLc[2 * i], dLc[2 * i + 1]);
+            D[i] = make_float2(Dv[2 * i], Dv[2 * i + 1]);
+            py[i] = make_float2((float)(y0 + 2 * i) + 0.5f, (float)(y0 + 2 * i + 1) + 0.5f);
+        }
+        if (mylast > 0) atomicMax(&s_maxlast, mylast);
+        __syncthreads();
+        const int end = rg.x + s_maxlast;
+        for (int b1 = end; b1 > rg.x; b1 -= BATCH) {
+            const int b0 = max(rg.x, b1 - BATCH);
+            const int cnt = b1 - b0;
+            __syncthreads();
+            for (int k = tid; k < cnt; k += NT) {
+                const uint32_t r = a.vals[b0 + k];
+                s_rec[k] = r;
+                stage_gaussian_x2(a.rec, r, &sa[k], &sb[k], &sc[k], &sd[k], &se[k]);
+            }
+            __syncthreads();
+            // kBwdUnroll staged Gaussians per iteration, back to front; the
+            // group is skipped when it lies beyond every pixel's last
+            for (int j2 = cnt - 1; j2 >= 0; j2 -= kBwdUnroll) {
+                if (__all_sync(F, b0 + max(j2 - kBwdUnroll + 1, 0) - rg.x >= mylast)) continue;
+#pragma unroll
+                for (int jj = 0; jj < kBwdUnroll; ++jj) {
+                const int j = j2 - jj;
+                if (j < 0) break;
+                const int pos = b0 + j - rg.x;
+                const float4 ga = sa[j], gb = sb[j], gc = sc[j], gd = sd[j], ge = se[j];
+                const float2 dx = __fadd2_rn(px2, lo2(ga));
+                const float2 adx = __fmul2_rn(lo2(gb), dx);
+                // The thread's pixels share x, so dx is common to them: only
+                // sum gm, sum gm dy and sum gm dy^2 run per pixel; the dx terms
+                // are applied once below. gm here is alpha dL/dalpha (the
+                // factor -1/2 of dalpha/dm is applied at the flush).
+                float2 S0 = make_float2(0.f, 0.f), SY = S0, SYY = S0, M6 = S0, M7 = S0, M8 = S0;
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    const float2 dy = __fadd2_rn(py[i], hi2(ga));
+                    const float2 t1 = __ffma2_rn(hi2(gb), dy, adx);
+                    const float2 t2 = __fmul2_rn(__fmul2_rn(lo2(gc), dy), dy);
+                    const float2 q = __ffma2_rn(t1, dx, t2);
+                    const float2 v = __fadd2_rn(q, hi2(gc));
+                    const float u0 = ex2_approx(v.x), u1 = ex2_approx(v.y);
+                    const bool ok0 = pos < last[2 * i] && q.x >= ge.z;
+                    const bool ok1 = pos < last[2 * i + 1] && q.y >= ge.z;
+                    // -alpha of a counted pair, 0 otherwise; -alpha where
+                    // dalpha/dm is nonzero (the unclamped alpha), 0 otherwise
+                    float2 na, nag;
+                    na.x = ok0 ? fmaxf(-kAlphaMax, -u0) : 0.f;
+                    na.y = ok1 ? fmaxf(-kAlphaMax, -u1) : 0.f;
+                    nag.x = u0 <= kAlphaMax ? na.x : 0.f;
+                    nag.y = u1 <= kAlphaMax ? na.y : 0.f;
+                    // T before this Gaussian, recovered from the T after it (a
+                    // pair that does not count has alpha = 0 and leaves T as is)
+                    const float2 om = __fadd2_rn(one2, na);
+                    T[i] = __fmul2_rn(T[i], make_float2(rcp_approx(om.x), rcp_approx(om.y)));
+                    const float2 nw = __fmul2_rn(na, T[i]);            // -w
+                    M6 = __ffma2_rn(nw, dL0[i], M6);
+                    M7 = __ffma2_rn(nw, dL1[i], M7);
+                    M8 = __ffma2_rn(nw, dL2[i], M8);
+                    // -E = sum_ch dL_ch (-c_ch); nd = D - E
+                    const float2 ne = __ffma2_rn(dL0[i], lo2(gd),
+                                                 __ffma2_rn(dL1[i], hi2(gd),
+                                                            __fmul2_rn(dL2[i], lo2(ge))));
+                    const float2 nd = __fadd2_rn(D[i], ne);
+                    const float2 ngl = __fmul2_rn(T[i], nd);            // -dL/dalpha
+                    D[i] = __ffma2_rn(na, nd, D[i]);
+                    const float2 gm = __fmul2_rn(nag, ngl);
+                    const float2 gy = __fmul2_rn(gm, dy);
+                    S0 = __fadd2_rn(S0, gm);
+                    SY = __fadd2_rn(SY, gy);
+                    SYY = __ffma2_rn(gy, dy, SYY);
+                }
+                float m[9];
+                m[0] = S0.x + S0.y;
+                m[2] = SY.x + SY.y;
+                m[5] = SYY.x + SYY.y;
+                m[6] = -(M6.x + M6.y);
+                m[7] = -(M7.x + M7.y);
+                m[8] = -(M8.x + M8.y);
+                // a Gaussian no pixel of the warp counted leaves every sum at zero
+                const bool any = m[0] != 0.f || m[6] != 0.f || m[7] != 0.f || m[8] != 0.f;
+                if (__any_sync(F, any)) {
+                    m[1] = m[0] * dx.x;
+                    m[3] = m[1] * dx.x;
+                    m[4] = m[2] * dx.x;
+                    warp_sum9_to_smem(m, &s_acc[j * 9]);
+                }
+                }
+            }
+            __syncthreads();
+            for (int k = tid; k < cnt; k += NT) {
+                float* acc = &s_acc[k * 9];
+                bool nz = false;
+#pragma unroll
+                for (int e = 0; e < 9; ++e) nz |= acc[e] != 0.f;
+                if (!nz) continue;
+                const uint32_t r = s_rec[k];
+                const float4 ra = a.rec.a[r];   // u, v, opacity, depth
+                const float4 rb = a.rec.b[r];   // A, B, C
+                // acc[0..5] hold sums of alpha dL/dalpha times (1, dx, dy, dx^2,
+                // dx dy, dy^2); dL/dm = -1/2 of them (G = exp(-m/2)).
+                // m = A dx^2 + 2B dx dy + C dy^2, dx = px - u: dm/du = -2(A dx + B dy)
+                const float m1 = -0.5f * acc[1], m2 = -0.5f * acc[2];
+                const float du = -2.f * (rb.x * m1 + rb.y * m2);
+                const float dv = -2.f * (rb.y * m1 + rb.z * m2);
+                // alpha = o G, dalpha/do = G = alpha/o
+                const float dop = acc[0] / ra.z;
+                float* dst = a.grad2d + 12ll * r;
+                red_add_v4(dst, du, dv, -0.5f * acc[3], -acc[4]);
+                red_add_v4(dst + 4, -0.5f * acc[5], dop, acc[6], acc[7]);
+                red_add(dst + 8, acc[8]);
+#pragma unroll
+                for (int e = 0; e < 9; ++e) acc[e] = 0.f;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 template <int TW, int TH, int BATCH, int PPT>
@@ -355,27 +733,54 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
     }
 }
 
+// even pixel counts per thread take the packed kernel
+template <int TW, int TH, int BATCH, int PPT, bool COUNT>
+static void* fwd_kernel_ptr() {
+    if constexpr (PPT % 2 == 0)
+        return (void*)blend_fwd_x2_kernel<TW, TH, BATCH, PPT, COUNT>;
+    else
+        return (void*)blend_fwd_kernel<TW, TH, BATCH, PPT, COUNT>;
+}
+
 template <int TW, int TH, int BATCH, int PPT>
 static cudaError_t run_fwd(const BlendArgs& a, int grid, cudaStream_t s) {
     note_launch();
-    if (a.pairs)
-        blend_fwd_kernel<TW, TH, BATCH, PPT, true><<<grid, TW * TH / PPT, 0, s>>>(a);
-    else
-        blend_fwd_kernel<TW, TH, BATCH, PPT, false><<<grid, TW * TH / PPT, 0, s>>>(a);
+    if constexpr (PPT % 2 == 0) {
+        if (a.pairs)
+            blend_fwd_x2_kernel<TW, TH, BATCH, PPT, true><<<grid, TW * TH / PPT, 0, s>>>(a);
+        else
+            blend_fwd_x2_kernel<TW, TH, BATCH, PPT, false><<<grid, TW * TH / PPT, 0, s>>>(a);
+    } else {
+        if (a.pairs)
+            blend_fwd_kernel<TW, TH, BATCH, PPT, true><<<grid, TW * TH / PPT, 0, s>>>(a);
+        else
+            blend_fwd_kernel<TW, TH, BATCH, PPT, false><<<grid, TW * TH / PPT, 0, s>>>(a);
+    }
     return cudaGetLastError();
+}
+
+template <int TW, int TH, int BATCH, int PPT>
+static void* bwd_kernel_ptr() {
+    if constexpr (PPT % 2 == 0)
+        return (void*)blend_bwd_x2_kernel<TW, TH, BATCH, PPT>;
+    else
+        return (void*)blend_bwd_kernel<TW, TH, BATCH, PPT>;
 }
 
 template <int TW, int TH, int BATCH, int PPT>
 static cudaError_t run_bwd(const BlendArgs& a, int grid, cudaStream_t s) {
     note_launch();
-    blend_bwd_kernel<TW, TH, BATCH, PPT><<<grid, TW * TH / PPT, 0, s>>>(a);
+    if constexpr (PPT % 2 == 0)
+        blend_bwd_x2_kernel<TW, TH, BATCH, PPT><<<grid, TW * TH / PPT, 0, s>>>(a);
+    else
+        blend_bwd_kernel<TW, TH, BATCH, PPT><<<grid, TW * TH / PPT, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int TW, int TH, int BATCH, int PPT>
 static int occ_fwd() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_fwd_kernel<TW, TH, BATCH, PPT, false>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fwd_kernel_ptr<TW, TH, BATCH, PPT, false>(),
                                                   TW * TH / PPT, 0);
     return n < 1 ? 1 : n;
 }
@@ -383,7 +788,7 @@ static int occ_fwd() {
 template <int TW, int TH, int BATCH, int PPT>
 static int occ_bwd() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, blend_bwd_kernel<TW, TH, BATCH, PPT>,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bwd_kernel_ptr<TW, TH, BATCH, PPT>(),
                                                   TW * TH / PPT, 0);
     return n < 1 ? 1 : n;
 }

@@ -616,11 +616,11 @@ swgs_status swgs_default_config(swgs_config* cfg) {
     if (!cfg) return SWGS_EINVAL;
     cfg->tile_w = 16;
     cfg->tile_h = 16;
-    cfg->batch = 128;
+    cfg->batch = 64;
     cfg->near_plane = 0.2f;
     cfg->blocks_per_sm = 0;
     cfg->count_pairs = 0;
-    cfg->pixels_per_thread = 2;
+    cfg->pixels_per_thread = 4;
     cfg->bwd_pixels_per_thread = 8;
     cfg->bwd_batch = 64;
     return SWGS_OK;

@@ -107,7 +107,7 @@ class ServingLoop:
 
     def __init__(self, state: api.GaussianState, swin_size: int, fps: float = 30.0,
                  n_streams: int = 2, max_batch: int = 16, hbm_budget_bytes: float = 16e9,
-                 slice_provider=None, tile=(16, 16), batch=256, pixels_per_thread=2,
+                 slice_provider=None, tile=(16, 16), batch=64, pixels_per_thread=4,
                  first_frame: int = 0):
         self.state = state
         self.swin = swin_size
