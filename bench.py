@@ -19,6 +19,7 @@ step (data parallel), so per-GPU work is fixed as N grows (weak scaling).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -47,9 +48,9 @@ FLOP_PER_PAIR_BWD = 64
 # captured again.
 TRAFFIC_CAPTURES = {
     ("blend_bwd", "16x16/b64/ppt8"): {
-        "bytes": 1_232_462_080 + 16_006_656,
+        "bytes": 1_232_347_648 + 15_890_688,
         "sources": ("csrc/k_blend.cu", "csrc/swgs_internal.cuh"),
-        "digest": "2eee4c521fa9a86b",
+        "digest": "bb4c344643e04e89",
     },
 }
 
@@ -243,9 +244,9 @@ def codec_leg(state, views, slice_size=6000, fracs=(1.0, 0.8, 0.6, 0.4, 0.2)):
                     "(DC-only SH and fp16/uint8 codes); not a dataset PSNR"}
 
 
-def memory_leg(lengths=(10, 30, 100), num_gs=300_000, swin=5):
+def memory_leg(lengths=(10, 100, 1000), num_gs=300_000, swin=5):
     """Table 3 in spirit: peak device memory of Alg. 1 main (ClipTrainer) over
-    clips of 10, 30 and 100 frames -- 300k Gaussians (swin 5: 60k-row slices),
+    clips of 10, 100 and 1000 frames -- 300k Gaussians (swin 5: 60k-row slices),
     one 676x507 view per frame, one step per window, the stream to pinned host."""
     import torch
     from paper_2409_07759_b300 import api, synth
@@ -287,6 +288,7 @@ def memory_leg(lengths=(10, 30, 100), num_gs=300_000, swin=5):
                        "stream_rows": sent[0], "stream_bytes": sent[1]}
         r.close()
         del ct
+        gc.collect()
         torch.cuda.empty_cache()
     return {"num_gs": num_gs, "swin_size": swin, "view": f"{w}x{h}", "clips": out}
 

@@ -19,11 +19,15 @@ struct SgldArgs {
     swgs_gaussians grads;
     swgs_adam_state adam;
     int has_grads, has_adam;
-    int frames[kMaxStepFrames];
-    int n_frames;
+    const uint8_t* elig;  // eligible slots (launch_eligible)
     swgs_sgld_params p;
     float bc1, bc2;  // Adam bias corrections 1 - beta^(step+1)
     unsigned long long seed, step;
+};
+
+struct StepFrames {
+    int frames[kMaxStepFrames];
+    int n;
 };
 
 __device__ __forceinline__ bool is_eligible(const swgs_gaussians& g, long long i,
@@ -33,6 +37,27 @@ __device__ __forceinline__ bool is_eligible(const swgs_gaussians& g, long long i
     for (int f = 0; f < nf; ++f)
         if (s <= frames[f] && frames[f] < e) return true;
     return false;
+}
+
+// One byte per slot, computed once per step and read by the Adam, noise and
+// relocation-weight kernels (instead of each re-testing every frame).
+__global__ void __launch_bounds__(256) eligible_kernel(swgs_gaussians g, StepFrames f,
+                                                       uint8_t* __restrict__ elig) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.capacity) return;
+    elig[i] = is_eligible(g, i, f.frames, f.n) ? 1 : 0;
+}
+
+cudaError_t launch_eligible(const swgs_gaussians& g, const int32_t* frames, int n_frames,
+                            uint8_t* elig, cudaStream_t s) {
+    if (n_frames > kMaxStepFrames) return cudaErrorInvalidValue;
+    if (g.capacity <= 0) return cudaSuccess;
+    StepFrames f{};
+    for (int k = 0; k < n_frames; ++k) f.frames[k] = frames[k];
+    f.n = n_frames;
+    note_launch();
+    eligible_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(g, f, elig);
+    return cudaGetLastError();
 }
 
 __device__ __forceinline__ void adam1(float* p, float* m, float* v, float g, float lr,
@@ -45,49 +70,56 @@ __device__ __forceinline__ void adam1(float* p, float* m, float* v, float g, flo
     *v = vv;
 }
 
-// Adam, one thread per parameter element (coalesced); blockIdx.y picks the
-// array: 0 means, 1 log-scales, 2 quaternions, 3 opacity logits, 4 SH.
-__global__ void __launch_bounds__(256) adam_kernel(SgldArgs a) {
-    const int arr = blockIdx.y;
-    const int K = (a.g.sh_degree + 1) * (a.g.sh_degree + 1);
-    float *P, *M, *V;
-    const float* G;
-    long long w;
-    float lr;
-    switch (arr) {
-        case 0: P = a.g.means; M = a.adam.m_means; V = a.adam.v_means; G = a.grads.means;
-                w = 3; lr = a.p.lr_means; break;
-        case 1: P = a.g.log_scales; M = a.adam.m_log_scales; V = a.adam.v_log_scales;
-                G = a.grads.log_scales; w = 3; lr = a.p.lr_log_scales; break;
-        case 2: P = a.g.quats; M = a.adam.m_quats; V = a.adam.v_quats; G = a.grads.quats;
-                w = 4; lr = a.p.lr_quats; break;
-        case 3: P = a.g.opacity_logits; M = a.adam.m_logits; V = a.adam.v_logits;
-                G = a.grads.opacity_logits; w = 1; lr = a.p.lr_logits; break;
-        default: P = a.g.sh; M = a.adam.m_sh; V = a.adam.v_sh; G = a.grads.sh; w = 3LL * K;
-                 lr = a.p.lr_sh_rest; break;
-    }
-    const long long n = a.g.capacity * w;
+// Adam over one parameter array of W floats per slot, one thread per element
+// (coalesced); W is a compile-time width so the slot index is a multiply.
+template <int W, int ARR>
+__device__ __forceinline__ void adam_array(const SgldArgs& a, float* P, float* M, float* V,
+                                           const float* G, float lr) {
+    const long long n = a.g.capacity * W;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
          e += (long long)gridDim.x * blockDim.x) {
-        const long long i = e / w;
-        if (!is_eligible(a.g, i, a.frames, a.n_frames)) continue;
+        const long long i = e / W;
+        if (!a.elig[i]) continue;
         float g = G[e];
         float l = lr;
-        if (arr == 0 && a.p.mean_grad_decay != 1.f && a.p.swin_size > 0) {
+        if (ARR == 0 && a.p.mean_grad_decay != 1.f && a.p.swin_size > 0) {
             // Sec. 4.5.1: the means gradient shrinks with the windows that have
             // trained the slot's current lifespan
             const int k = max(1, a.p.window_start - a.g.start[i] + a.p.swin_size);
             g *= exp2f((float)(k - 1) * log2f(a.p.mean_grad_decay));
         }
-        if (arr == 4 && (e - i * w) < 3) l = a.p.lr_sh_dc;  // the DC band
+        if (ARR == 4 && (e - i * W) < 3) l = a.p.lr_sh_dc;  // the DC band
         adam1(&P[e], &M[e], &V[e], g, l, a);
+    }
+}
+
+// blockIdx.y picks the array: 0 means, 1 log-scales, 2 quaternions, 3 opacity
+// logits, 4 SH.
+__global__ void __launch_bounds__(256) adam_kernel(SgldArgs a) {
+    const swgs_gaussians& g = a.g;
+    const swgs_gaussians& d = a.grads;
+    const swgs_adam_state& m = a.adam;
+    switch (blockIdx.y) {
+        case 0: adam_array<3, 0>(a, g.means, m.m_means, m.v_means, d.means, a.p.lr_means); break;
+        case 1: adam_array<3, 1>(a, g.log_scales, m.m_log_scales, m.v_log_scales, d.log_scales,
+                                 a.p.lr_log_scales); break;
+        case 2: adam_array<4, 2>(a, g.quats, m.m_quats, m.v_quats, d.quats, a.p.lr_quats); break;
+        case 3: adam_array<1, 3>(a, g.opacity_logits, m.m_logits, m.v_logits, d.opacity_logits,
+                                 a.p.lr_logits); break;
+        default:
+            switch (g.sh_degree) {
+                case 0: adam_array<3, 4>(a, g.sh, m.m_sh, m.v_sh, d.sh, a.p.lr_sh_rest); break;
+                case 1: adam_array<12, 4>(a, g.sh, m.m_sh, m.v_sh, d.sh, a.p.lr_sh_rest); break;
+                case 2: adam_array<27, 4>(a, g.sh, m.m_sh, m.v_sh, d.sh, a.p.lr_sh_rest); break;
+                default: adam_array<48, 4>(a, g.sh, m.m_sh, m.v_sh, d.sh, a.p.lr_sh_rest); break;
+            }
     }
 }
 
 __global__ void __launch_bounds__(256) sgld_kernel(SgldArgs a) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.g.capacity) return;
-    if (!is_eligible(a.g, i, a.frames, a.n_frames)) return;
+    if (!a.elig[i]) return;
     // noise from the (possibly updated) opacity and covariance
     const float o = 1.f / (1.f + expf(-a.g.opacity_logits[i]));
     const float gate = 1.f / (1.f + expf(a.p.noise_k * (o - a.p.noise_t)));
@@ -121,19 +153,17 @@ __global__ void __launch_bounds__(256) sgld_kernel(SgldArgs a) {
 }
 
 cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
-                        const swgs_adam_state* adam, const int32_t* frames, int n_frames,
+                        const swgs_adam_state* adam, const uint8_t* elig,
                         const swgs_sgld_params& p, unsigned long long seed,
                         unsigned long long step, cudaStream_t s) {
     if (g.capacity <= 0) return cudaSuccess;
-    if (n_frames > kMaxStepFrames) return cudaErrorInvalidValue;
     SgldArgs a{};
     a.g = g;
     if (grads) a.grads = *grads;
     if (adam) a.adam = *adam;
     a.has_grads = grads != nullptr;
     a.has_adam = adam != nullptr;
-    for (int f = 0; f < n_frames; ++f) a.frames[f] = frames[f];
-    a.n_frames = n_frames;
+    a.elig = elig;
     a.p = p;
     a.bc1 = (float)(1.0 - pow((double)p.beta1, (double)(step + 1)));
     a.bc2 = (float)(1.0 - pow((double)p.beta2, (double)(step + 1)));
@@ -158,8 +188,7 @@ cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
 // ---------------------------------------------------------------------------
 struct RelocArgs {
     swgs_gaussians g;
-    int frames[kMaxStepFrames];
-    int n_frames;
+    const uint8_t* elig;
 };
 
 // weight = floor(sigmoid(logit) 2^32) for alive eligible slots, 0 otherwise;
@@ -172,7 +201,7 @@ reloc_weights_kernel(RelocArgs a, unsigned long long* __restrict__ weights,
     if (i >= a.g.capacity) return;
     unsigned long long w = 0;
     uint8_t d = 0;
-    if (is_eligible(a.g, i, a.frames, a.n_frames)) {
+    if (a.elig[i]) {
         const float lg = a.g.opacity_logits[i];
         if (lg <= kLogitDead) {
             d = 1;
@@ -188,13 +217,11 @@ reloc_weights_kernel(RelocArgs a, unsigned long long* __restrict__ weights,
     dead[i] = d;
 }
 
-cudaError_t launch_reloc_weights(const swgs_gaussians& g, const int32_t* frames, int n_frames,
+cudaError_t launch_reloc_weights(const swgs_gaussians& g, const uint8_t* elig,
                                  unsigned long long* weights, uint8_t* dead, cudaStream_t s) {
-    if (n_frames > kMaxStepFrames) return cudaErrorInvalidValue;
     RelocArgs a{};
     a.g = g;
-    for (int f = 0; f < n_frames; ++f) a.frames[f] = frames[f];
-    a.n_frames = n_frames;
+    a.elig = elig;
     note_launch();
     reloc_weights_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(a, weights, dead);
     return cudaGetLastError();

@@ -76,8 +76,9 @@ struct swgs_ctx {
     // transient scratch
     Buf frames, block_cnt, scan_tmp, counts, order_a, order_b, tcount, koff, keys_a, keys_b,
         vals_tmp, vals_b, sranges, tile_cnt, tile_off, mature_ids, mature_stage, codec_keys_a,
-        codec_keys_b, codec_vals_a, codec_vals_b, codec_flags, codec_idx, codec_stage, sort_tmp, counter, totals, l1_tab, reloc_w, reloc_cdf, reloc_dead, reloc_tg,
-        reloc_cnt, reloc_nd;
+        codec_keys_b, codec_vals_a, codec_vals_b, codec_flags, codec_idx, codec_stage, sort_tmp,
+        counter, totals, l1_tab, elig, reloc_w, reloc_cdf, reloc_dead, reloc_tg, reloc_cnt,
+        reloc_nd;
     void* pinned = nullptr;
     size_t pinned_cap = 0;
     std::vector<swgs_saved*> pool;
@@ -667,7 +668,7 @@ void swgs_destroy(swgs_ctx* ctx) {
                  &ctx->mature_ids, &ctx->mature_stage, &ctx->codec_keys_a, &ctx->codec_keys_b,
                  &ctx->codec_vals_a, &ctx->codec_vals_b, &ctx->codec_flags, &ctx->codec_idx,
                  &ctx->codec_stage, &ctx->sort_tmp, &ctx->counter, &ctx->totals, &ctx->l1_tab,
-                 &ctx->reloc_w, &ctx->reloc_cdf, &ctx->reloc_dead, &ctx->reloc_tg,
+                 &ctx->elig, &ctx->reloc_w, &ctx->reloc_cdf, &ctx->reloc_dead, &ctx->reloc_tg,
                  &ctx->reloc_cnt, &ctx->reloc_nd};
     for (Buf* b : bs) ctx_free(ctx, *b, s);
     for (swgs_saved* sv : ctx->all_saved) {
@@ -1350,7 +1351,10 @@ swgs_status swgs_sgld_step(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_ga
     }
     {
         StageScope sc_(ctx, SWGS_STAGE_SGLD, s);
-        CK(launch_sgld(*g, grads, adam, frames, n_frames, *params, seed, step, s));
+        if (!ensure(ctx, ctx->elig, (size_t)N, s))
+            return fail(ctx, SWGS_ENOMEM, "allocation failed (eligible slots)");
+        CK(launch_eligible(*g, frames, n_frames, P<uint8_t>(ctx->elig), s));
+        CK(launch_sgld(*g, grads, adam, P<uint8_t>(ctx->elig), *params, seed, step, s));
     }
     long long nd = 0;
     if (params->relocate) {
@@ -1364,7 +1368,7 @@ swgs_status swgs_sgld_step(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_ga
             (!targets && !ensure(ctx, ctx->reloc_tg, 4 * (size_t)N, s)))
             return fail(ctx, SWGS_ENOMEM, "allocation failed (relocation)");
         int32_t* tg = targets ? targets : P<int32_t>(ctx->reloc_tg);
-        CK(launch_reloc_weights(*g, frames, n_frames, P<unsigned long long>(ctx->reloc_w),
+        CK(launch_reloc_weights(*g, P<uint8_t>(ctx->elig), P<unsigned long long>(ctx->reloc_w),
                                 P<uint8_t>(ctx->reloc_dead), s));
         CK(inclusive_scan_u64(P<unsigned long long>(ctx->reloc_w), P<unsigned long long>(ctx->reloc_cdf),
                               N, ctx->scan_tmp.p, s));

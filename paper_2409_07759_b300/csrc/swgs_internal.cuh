@@ -492,11 +492,14 @@ cudaError_t launch_copy_slice(const swgs_gaussians& dst, long long first, long l
                               const swgs_gaussians& src, cudaStream_t s);
 
 // k_optim.cu
+// elig: one byte per slot, 1 = active at a frame of the step and not frozen
+cudaError_t launch_eligible(const swgs_gaussians& g, const int32_t* frames, int n_frames,
+                            uint8_t* elig, cudaStream_t s);
 cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
-                        const swgs_adam_state* adam, const int32_t* frames, int n_frames,
+                        const swgs_adam_state* adam, const uint8_t* elig,
                         const swgs_sgld_params& p, unsigned long long seed,
                         unsigned long long step, cudaStream_t s);
-cudaError_t launch_reloc_weights(const swgs_gaussians& g, const int32_t* frames, int n_frames,
+cudaError_t launch_reloc_weights(const swgs_gaussians& g, const uint8_t* elig,
                                  unsigned long long* weights, uint8_t* dead, cudaStream_t s);
 cudaError_t launch_reloc_sample(const swgs_gaussians& g, const uint8_t* dead,
                                 const unsigned long long* cdf, unsigned long long seed,
