@@ -3,9 +3,10 @@
 // Each pass (<= 9 bits, up to 512 buckets): an upsweep histogram per block
 // over a contiguous share of 4096-key tiles, an exclusive scan of the
 // (digit, block) counts in digit-major order, and a downsweep that ranks each
-// tile stably (warp match.any ranking, warps in order), stages it in shared
-// memory in digit order and writes it out, so global writes are contiguous
-// within each digit run. Keys and ranks are the only per-item registers; the
+// tile stably (the lanes sharing a digit found with one warp ballot per digit
+// bit, which measured faster than match.any; warps in order), stages it in
+// shared memory in digit order and writes it out, so global writes are
+// contiguous within each digit run. Keys and ranks are the only per-item registers; the
 // values are loaded after the keys have been placed. The grid is a fixed
 // multiple of the SM count and block b owns the same tile range in both
 // kernels, so no block ever waits for another.
@@ -116,6 +117,7 @@ radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     DownSmem& S = *reinterpret_cast<DownSmem*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t mask = (uint32_t)bins - 1u;
+    const int bits_here = __ffs(bins) - 1;
     const unsigned lt_mask = (1u << lane) - 1u;
     for (int d = threadIdx.x; d < bins; d += kSortThreads)
         S.run[d] = offsets[(long long)d * gridDim.x + blockIdx.x];
@@ -138,8 +140,16 @@ radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
 #pragma unroll
         for (int it = 0; it < kSortItems; ++it) {
             const int local = warp * kWarpSpan + it * 32 + lane;
-            const uint32_t d = local < valid ? (k[it] >> shift) & mask : (uint32_t)bins;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const bool ok = local < valid;
+            const uint32_t d = ok ? (k[it] >> shift) & mask : (uint32_t)bins;
+            // lanes with the same digit (and the same validity): one ballot per digit bit
+            const unsigned vm = __ballot_sync(0xffffffffu, ok);
+            unsigned peers = ok ? vm : ~vm;
+            for (int b = 0; b < bits_here; ++b) {
+                const bool bit = (d >> b) & 1u;
+                const unsigned bb = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bb : ~bb;
+            }
             const int leader = __ffs(peers) - 1;
             uint32_t b = 0;
             if (lane == leader) {
