@@ -75,6 +75,8 @@ class WindowTrainer:
         self._released = None    # per buffer: the last step reading it has ended
         self.dl = [torch.empty_like(i) for i in self.images]
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        # largest number of tile keys of any step so far (sizes the scratch)
+        self.max_keys = 0
 
     def set_window(self, views: Sequence, targets: Sequence[torch.Tensor]):
         """Move the trainer to another window's views and targets (buffers are
@@ -135,6 +137,7 @@ class WindowTrainer:
             reg = dict(opacity_reg=self.params["opacity_reg"],
                        scale_reg=self.params["scale_reg"])
         self.r.backward(self.state, saved, self.dl, self.grads, reg=reg, loss=self.loss)
+        self.max_keys = max(self.max_keys, int(saved.info().n_keys))
         saved.release()
         if self.reduce is not None:
             self.reduce(self._gflat, self.loss)
