@@ -50,7 +50,7 @@ TRAFFIC_CAPTURES = {
     ("blend_bwd", "16x16/b64/ppt8"): {
         "bytes": 1_232_347_648 + 15_890_688,
         "sources": ("csrc/k_blend.cu", "csrc/swgs_internal.cuh"),
-        "digest": "58240d387d5c70b2",
+        "digest": "c27b25c7731e7f46",
     },
 }
 

@@ -14,28 +14,40 @@ namespace swgs {
 
 // out[k] = super tiles keyed by the k-th record in depth order; *exact += the
 // records' exact tile counts (the number of per-tile list entries).
+// A bounded grid strides over the records and sums the tile counts per block,
+// so the single total word takes one atomic per block (same-address atomics
+// serialise in L2).
 __global__ void __launch_bounds__(256)
 gather_supers_kernel(const uint32_t* __restrict__ order, Records rec, int sx, int sy,
                      uint32_t* __restrict__ out, unsigned long long* __restrict__ exact,
                      long long n) {
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ unsigned long long part[8];
     unsigned long long t = 0;
-    if (k < n) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
         const uint32_t r = order[k];
         out[k] = (uint32_t)rec.supers[r];
-        t = (unsigned long long)rec.tiles[r];
+        t += (unsigned long long)rec.tiles[r];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if ((threadIdx.x & 31) == 0 && t) atomicAdd(exact, t);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int w = 0; w < 8; ++w) s += part[w];
+        if (s) atomicAdd(exact, s);
+    }
 }
 
 cudaError_t launch_gather_supers(const uint32_t* order, const Records rec, int sx, int sy,
                                  uint32_t* out, unsigned long long* exact, long long n,
-                                 cudaStream_t s) {
+                                 int num_sms, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
+    long long grid = div_up(n, 256);
+    if (grid > 8LL * num_sms) grid = 8LL * num_sms;
     note_launch();
-    gather_supers_kernel<<<div_up(n, 256), 256, 0, s>>>(order, rec, sx, sy, out, exact, n);
+    gather_supers_kernel<<<(unsigned)grid, 256, 0, s>>>(order, rec, sx, sy, out, exact, n);
     return cudaGetLastError();
 }
 

@@ -369,10 +369,20 @@ struct PreBwdArgs {
 // w_o sigmoid(logit) + w_s sum_c exp(log_scale_c) to the loss (frozen ones
 // too: they count in the means) and, unless frozen, w_o sigmoid (1 - sigmoid)
 // to its logit gradient and w_s exp(log_scale_c) to its log-scale gradients.
+// Summed over the block first: one atomic per block, not per warp, on the
+// single loss word (same-address atomics serialise in L2). Every thread of the
+// block must call it.
 __device__ __forceinline__ void reg_loss_add(float v, float* loss) {
+    __shared__ float part[4];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(loss, v);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+        if (s != 0.f) atomicAdd(loss, s);
+    }
 }
 
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {

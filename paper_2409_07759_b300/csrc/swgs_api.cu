@@ -398,7 +398,8 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             StageScope sc_(ctx, SWGS_STAGE_KEY_SCAN, s);
             CK(cudaMemsetAsync(ctx->totals.p, 0, 16, s));
             CK(launch_gather_supers(order, rc, SX, SY, cnt,
-                                    P<unsigned long long>(ctx->totals) + 1, (long long)R, s));
+                                    P<unsigned long long>(ctx->totals) + 1, (long long)R,
+                                    ctx->num_sms, s));
             CK(exclusive_scan_u32(cnt, P<uint32_t>(ctx->koff), (long long)R, ctx->scan_tmp.p,
                                   P<unsigned long long>(ctx->totals), s));
         }

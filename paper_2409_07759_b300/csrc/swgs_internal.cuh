@@ -413,7 +413,7 @@ inline int super_w(int tile_w) { return tile_w == 32 ? 2 : 4; }
 inline int super_h(int tile_w) { return tile_w == 32 ? 8 : 4; }
 cudaError_t launch_gather_supers(const uint32_t* order, const Records rec, int sx, int sy,
                                  uint32_t* out, unsigned long long* exact, long long n,
-                                 cudaStream_t s);
+                                 int num_sms, cudaStream_t s);
 cudaError_t launch_emit_supers(const uint32_t* order, const uint32_t* offsets, long long n_rec,
                                const Records rec, const ViewDev* views, int n_views, int sx,
                                int sy, int tile_w, int tile_h, int num_sms, uint32_t* keys,
