@@ -199,11 +199,56 @@ __device__ __forceinline__ void stage_gaussian_x2(const Records& rec, uint32_t r
     *sb = make_float4(qa, qa, qb, qb);
     *sc = make_float4(qc, qc, lo, lo);
     *sd = make_float4(-Cc.x, -Cc.x, -Cc.y, -Cc.y);
-    *se = make_float4(-Cc.z, -Cc.z, pair_qmin(lo), 0.f);
+    // alpha = min(0.99, o G) with G <= 1 reaches the clamp only when o > 0.99:
+    // the blends skip the clamp's work for the others (a warp-uniform branch)
+    *se = make_float4(-Cc.z, -Cc.z, pair_qmin(lo), A.z > kAlphaMax ? 1.f : 0.f);
 }
 
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// One staged Gaussian against the thread's pixel pairs (the forward's inner
+// step). CLAMP = false drops the 0.99 clamp (valid for opacity <= 0.99).
+template <bool CLAMP, int NP, bool COUNT>
+__device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float4 gd, float4 ge,
+                                          float2 dx, float2 adx, int pos, int pos1,
+                                          float2 (&T)[NP], float2 (&C0)[NP], float2 (&C1)[NP],
+                                          float2 (&C2)[NP], float2 (&py)[NP], int (&last)[2 * NP],
+                                          int (&stop)[2 * NP]) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const float2 dy = __fadd2_rn(py[i], hi2(ga));
+        const float2 t1 = __ffma2_rn(hi2(gb), dy, adx);
+        const float2 t2 = __fmul2_rn(__fmul2_rn(lo2(gc), dy), dy);
+        const float2 q = __ffma2_rn(t1, dx, t2);
+        const float2 v = __fadd2_rn(q, hi2(gc));
+        // -alpha = -min(0.99, 2^v)
+        float2 nal = make_float2(-ex2_approx(v.x), -ex2_approx(v.y));
+        if (CLAMP) {
+            nal.x = fmaxf(-kAlphaMax, nal.x);
+            nal.y = fmaxf(-kAlphaMax, nal.y);
+        }
+        const bool ok0 = q.x >= ge.z, ok1 = q.y >= ge.z;
+        // T (1 - alpha), rounded once: the stopping test
+        const float2 tT = __ffma2_rn(nal, T[i], T[i]);
+        const bool inc0 = ok0 && tT.x >= kTStop, inc1 = ok1 && tT.y >= kTStop;
+        if (COUNT) {
+            stop[2 * i] = (ok0 && !inc0) ? pos : stop[2 * i];
+            stop[2 * i + 1] = (ok1 && !inc1) ? pos : stop[2 * i + 1];
+        }
+        py[i].x = (ok0 && !inc0) ? kGone : py[i].x;
+        py[i].y = (ok1 && !inc1) ? kGone : py[i].y;
+        nal.x = inc0 ? nal.x : 0.f;
+        nal.y = inc1 ? nal.y : 0.f;
+        const float2 nw = __fmul2_rn(nal, T[i]);      // -w
+        C0[i] = __ffma2_rn(lo2(gd), nw, C0[i]);
+        C1[i] = __ffma2_rn(hi2(gd), nw, C1[i]);
+        C2[i] = __ffma2_rn(lo2(ge), nw, C2[i]);
+        T[i] = __fadd2_rn(T[i], nw);
+        last[2 * i] = inc0 ? pos1 : last[2 * i];
+        last[2 * i + 1] = inc1 ? pos1 : last[2 * i + 1];
+    }
+}
 
 // 4 pixels a thread: at least 20 blocks of 64 threads per SM (48 registers),
 // measured faster than the 66-register build at 15 blocks
@@ -272,36 +317,10 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 20 : 1)) blend_fwd_
                 const int pos = b0 + j, pos1 = pos - rg.x + 1;
                 const float2 dx = __fadd2_rn(px2, lo2(ga));
                 const float2 adx = __fmul2_rn(lo2(gb), dx);
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    const float2 dy = __fadd2_rn(py[i], hi2(ga));
-                    const float2 t1 = __ffma2_rn(hi2(gb), dy, adx);
-                    const float2 t2 = __fmul2_rn(__fmul2_rn(lo2(gc), dy), dy);
-                    const float2 q = __ffma2_rn(t1, dx, t2);
-                    const float2 v = __fadd2_rn(q, hi2(gc));
-                    // -alpha = max(-0.99, -2^v)
-                    float2 nal = make_float2(fmaxf(-kAlphaMax, -ex2_approx(v.x)),
-                                             fmaxf(-kAlphaMax, -ex2_approx(v.y)));
-                    const bool ok0 = q.x >= ge.z, ok1 = q.y >= ge.z;
-                    // T (1 - alpha), rounded once: the stopping test
-                    const float2 tT = __ffma2_rn(nal, T[i], T[i]);
-                    const bool inc0 = ok0 && tT.x >= kTStop, inc1 = ok1 && tT.y >= kTStop;
-                    if (COUNT) {
-                        stop[2 * i] = (ok0 && !inc0) ? pos : stop[2 * i];
-                        stop[2 * i + 1] = (ok1 && !inc1) ? pos : stop[2 * i + 1];
-                    }
-                    py[i].x = (ok0 && !inc0) ? kGone : py[i].x;
-                    py[i].y = (ok1 && !inc1) ? kGone : py[i].y;
-                    nal.x = inc0 ? nal.x : 0.f;
-                    nal.y = inc1 ? nal.y : 0.f;
-                    const float2 nw = __fmul2_rn(nal, T[i]);      // -w
-                    C0[i] = __ffma2_rn(lo2(gd), nw, C0[i]);
-                    C1[i] = __ffma2_rn(hi2(gd), nw, C1[i]);
-                    C2[i] = __ffma2_rn(lo2(ge), nw, C2[i]);
-                    T[i] = __fadd2_rn(T[i], nw);
-                    last[2 * i] = inc0 ? pos1 : last[2 * i];
-                    last[2 * i + 1] = inc1 ? pos1 : last[2 * i + 1];
-                }
+                // the clamp is kept for every Gaussian here: splitting on the
+                // staged flag (as the reverse blend does) measured no faster
+                fwd_pairs<true, NP, COUNT>(ga, gb, gc, gd, ge, dx, adx, pos, pos1, T, C0, C1, C2,
+                                           py, last, stop);
                 }
                 tdone = true;
 #pragma unroll
@@ -409,10 +428,69 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // D + a (E - D) = D + (-a)(D + (-E)), and dL/dm's factor a (T (E - D)) =
 // (-a)(T (D + (-E))). Each thread's per-pixel sums are kept as two partial
 // sums (the halves) and added before the warp reduction.
-// 8 pixels a thread (one warp a tile): at least 20 warps per SM (96 registers,
-// no spills) hide the ex2 -> rcp latency better than 15 at 130 registers
+// One staged Gaussian against the thread's pixel pairs (the reverse blend's
+// inner step): T recovery, the colour-behind update and the per-pixel sums.
+// CLAMP: the Gaussian's opacity exceeds 0.99, so alpha may take the clamp
+// (where dalpha/dm is then zero).
+template <bool CLAMP, int NP>
+__device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float4 gd, float4 ge,
+                                          float2 dx, float2 adx, int pos, const float2 (&py)[NP],
+                                          const int (&last)[2 * NP], float2 (&T)[NP],
+                                          float2 (&D)[NP], const float2 (&dL0)[NP],
+                                          const float2 (&dL1)[NP], const float2 (&dL2)[NP],
+                                          float2& S0, float2& SY, float2& SYY, float2& M6,
+                                          float2& M7, float2& M8) {
+    const float2 one2 = make_float2(1.f, 1.f);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const float2 dy = __fadd2_rn(py[i], hi2(ga));
+        const float2 t1 = __ffma2_rn(hi2(gb), dy, adx);
+        const float2 t2 = __fmul2_rn(__fmul2_rn(lo2(gc), dy), dy);
+        const float2 q = __ffma2_rn(t1, dx, t2);
+        const float2 v = __fadd2_rn(q, hi2(gc));
+        const float u0 = ex2_approx(v.x), u1 = ex2_approx(v.y);
+        const bool ok0 = pos < last[2 * i] && q.x >= ge.z;
+        const bool ok1 = pos < last[2 * i + 1] && q.y >= ge.z;
+        // -alpha of a counted pair, 0 otherwise; -alpha where dalpha/dm is
+        // nonzero (the unclamped alpha), 0 otherwise
+        float2 na, nag;
+        if (CLAMP) {
+            na.x = ok0 ? fmaxf(-kAlphaMax, -u0) : 0.f;
+            na.y = ok1 ? fmaxf(-kAlphaMax, -u1) : 0.f;
+            nag.x = u0 <= kAlphaMax ? na.x : 0.f;
+            nag.y = u1 <= kAlphaMax ? na.y : 0.f;
+        } else {
+            na.x = ok0 ? -u0 : 0.f;
+            na.y = ok1 ? -u1 : 0.f;
+            nag = na;
+        }
+        // T before this Gaussian, recovered from the T after it (a pair that
+        // does not count has alpha = 0 and leaves T as is)
+        const float2 om = __fadd2_rn(one2, na);
+        T[i] = __fmul2_rn(T[i], make_float2(rcp_approx(om.x), rcp_approx(om.y)));
+        const float2 nw = __fmul2_rn(na, T[i]);            // -w
+        M6 = __ffma2_rn(nw, dL0[i], M6);
+        M7 = __ffma2_rn(nw, dL1[i], M7);
+        M8 = __ffma2_rn(nw, dL2[i], M8);
+        // -E = sum_ch dL_ch (-c_ch); nd = D - E
+        const float2 ne = __ffma2_rn(dL0[i], lo2(gd),
+                                     __ffma2_rn(dL1[i], hi2(gd), __fmul2_rn(dL2[i], lo2(ge))));
+        const float2 nd = __fadd2_rn(D[i], ne);
+        const float2 ngl = __fmul2_rn(T[i], nd);            // -dL/dalpha
+        D[i] = __ffma2_rn(na, nd, D[i]);
+        const float2 gm = __fmul2_rn(nag, ngl);
+        const float2 gy = __fmul2_rn(gm, dy);
+        S0 = __fadd2_rn(S0, gm);
+        SY = __fadd2_rn(SY, gy);
+        SYY = __ffma2_rn(gy, dy, SYY);
+    }
+}
+
+// 8 pixels a thread (one warp a tile): at least 16 warps per SM (128
+// registers) hide the ex2 -> rcp latency better than 15 at the unbounded 136,
+// and better than 18-20 with their spills
 template <int TW, int TH, int BATCH, int PPT>
-__global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 20 : 1)) blend_bwd_x2_kernel(BlendArgs a) {
+__global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_x2_kernel(BlendArgs a) {
     static_assert(PPT % 2 == 0, "pixels are taken in pairs");
     constexpr int NT = TileGeom<TW, TH, PPT>::NT;
     constexpr int NP = PPT / 2;
@@ -423,7 +501,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 20 : 1)) blend_bwd_
     const unsigned F = 0xffffffffu;
     const int tid = threadIdx.x;
     const int lx = tid % TW, ly = (tid / TW) * PPT;
-    const float2 one2 = make_float2(1.f, 1.f), mone2 = make_float2(-1.f, -1.f);
+    const float2 one2 = make_float2(1.f, 1.f);
     for (int k = tid; k < BATCH * 9; k += NT) s_acc[k] = 0.f;
     for (;;) {
         if (tid == 0) { s_item = atomicAdd(a.work_counter, 1); s_maxlast = 0; }
@@ -500,44 +578,12 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 20 : 1)) blend_bwd_
                 // are applied once below. gm here is alpha dL/dalpha (the
                 // factor -1/2 of dalpha/dm is applied at the flush).
                 float2 S0 = make_float2(0.f, 0.f), SY = S0, SYY = S0, M6 = S0, M7 = S0, M8 = S0;
-#pragma unroll
-                for (int i = 0; i < NP; ++i) {
-                    const float2 dy = __fadd2_rn(py[i], hi2(ga));
-                    const float2 t1 = __ffma2_rn(hi2(gb), dy, adx);
-                    const float2 t2 = __fmul2_rn(__fmul2_rn(lo2(gc), dy), dy);
-                    const float2 q = __ffma2_rn(t1, dx, t2);
-                    const float2 v = __fadd2_rn(q, hi2(gc));
-                    const float u0 = ex2_approx(v.x), u1 = ex2_approx(v.y);
-                    const bool ok0 = pos < last[2 * i] && q.x >= ge.z;
-                    const bool ok1 = pos < last[2 * i + 1] && q.y >= ge.z;
-                    // -alpha of a counted pair, 0 otherwise; -alpha where
-                    // dalpha/dm is nonzero (the unclamped alpha), 0 otherwise
-                    float2 na, nag;
-                    na.x = ok0 ? fmaxf(-kAlphaMax, -u0) : 0.f;
-                    na.y = ok1 ? fmaxf(-kAlphaMax, -u1) : 0.f;
-                    nag.x = u0 <= kAlphaMax ? na.x : 0.f;
-                    nag.y = u1 <= kAlphaMax ? na.y : 0.f;
-                    // T before this Gaussian, recovered from the T after it (a
-                    // pair that does not count has alpha = 0 and leaves T as is)
-                    const float2 om = __fadd2_rn(one2, na);
-                    T[i] = __fmul2_rn(T[i], make_float2(rcp_approx(om.x), rcp_approx(om.y)));
-                    const float2 nw = __fmul2_rn(na, T[i]);            // -w
-                    M6 = __ffma2_rn(nw, dL0[i], M6);
-                    M7 = __ffma2_rn(nw, dL1[i], M7);
-                    M8 = __ffma2_rn(nw, dL2[i], M8);
-                    // -E = sum_ch dL_ch (-c_ch); nd = D - E
-                    const float2 ne = __ffma2_rn(dL0[i], lo2(gd),
-                                                 __ffma2_rn(dL1[i], hi2(gd),
-                                                            __fmul2_rn(dL2[i], lo2(ge))));
-                    const float2 nd = __fadd2_rn(D[i], ne);
-                    const float2 ngl = __fmul2_rn(T[i], nd);            // -dL/dalpha
-                    D[i] = __ffma2_rn(na, nd, D[i]);
-                    const float2 gm = __fmul2_rn(nag, ngl);
-                    const float2 gy = __fmul2_rn(gm, dy);
-                    S0 = __fadd2_rn(S0, gm);
-                    SY = __fadd2_rn(SY, gy);
-                    SYY = __ffma2_rn(gy, dy, SYY);
-                }
+                if (ge.w != 0.f)
+                    bwd_pairs<true, NP>(ga, gb, gc, gd, ge, dx, adx, pos, py, last, T, D, dL0, dL1,
+                                        dL2, S0, SY, SYY, M6, M7, M8);
+                else
+                    bwd_pairs<false, NP>(ga, gb, gc, gd, ge, dx, adx, pos, py, last, T, D, dL0, dL1,
+                                         dL2, S0, SY, SYY, M6, M7, M8);
                 float m[9];
                 m[0] = S0.x + S0.y;
                 m[2] = SY.x + SY.y;
