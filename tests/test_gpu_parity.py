@@ -362,3 +362,22 @@ def test_view_beyond_the_super_tile_limit_is_rejected():
     with pytest.raises(SwgsError):
         r.render(_state(sc), [v])
     r.close()
+
+
+@pytest.mark.parametrize("ppt", [2, 8])
+def test_backward_high_opacity_clamp(oracle_mod, ppt):
+    """A third of the Gaussians above the 0.99 alpha clamp (opacity 0.9975):
+    the blends' clamp branch gives the oracle's image and gradients (where
+    the clamp holds, dalpha/dm is zero), next to the unclamped Gaussians."""
+    from paper_2409_07759_b300 import api
+    r = api.Renderer(bwd_pixels_per_thread=ppt, pixels_per_thread=min(ppt, 4))
+    sc, view = synth.tiny_scene(5, n=200, sh_degree=1, width=96, height=72, depth=3.0,
+                                log_scale_mean=-2.2, spread=0.9)
+    view.fx = view.fy = 90.0
+    high = np.random.default_rng(6).random(sc.n) < 1 / 3
+    sc.opacity_logits[high] = 6.0
+    assert (1 / (1 + np.exp(-sc.opacity_logits)) > 0.99).sum() >= 40
+    _render_and_compare(r, oracle_mod, sc, [view])
+    d = np.random.default_rng(2).normal(size=(3, 72, 96))
+    print(_grads_vs_oracle(r, oracle_mod, sc, [view], [d], bg=(0.1, 0.2, 0.3)))
+    r.close()
