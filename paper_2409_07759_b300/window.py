@@ -113,16 +113,19 @@ class WindowTrainer:
 
     def step(self, step: int, update: Optional[tuple] = None, render_only: bool = False,
              prefetched: bool = False):
-        """One training step. update = (first_slot, pinned host dict) streams a
-        slice in before rendering; prefetched = True takes the targets from the
-        last prefetch_targets call. Returns the (device) loss tensor."""
+        """One training step. update = (first_slot, src) overwrites a slice
+        before rendering: src a pinned host dict (GaussianState.pin_host, the
+        form a streamed slice arrives in) or a GaussianState on the device;
+        prefetched = True takes the targets from the last prefetch_targets call.
+        Returns the (device) loss tensor."""
         if prefetched:
             torch.cuda.current_stream().wait_event(self._copied)
             self._front = 1 - self._front
             self.targets = self._bufs[self._front]
         if update is not None:
-            first, host = update
-            self.r.frame_update(self.state, first, host, src_on_host=True)
+            first, src = update
+            self.r.frame_update(self.state, first, src,
+                                src_on_host=not isinstance(src, api.GaussianState))
         if render_only:
             self.r.render(self.state, self.views, bg=self.bg, batched=self.batched,
                           out=self.images)
