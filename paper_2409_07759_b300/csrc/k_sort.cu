@@ -11,6 +11,16 @@
 // multiple of the SM count and block b owns the same tile range in both
 // kernels, so no block ever waits for another.
 //
+// Inputs below 2^30 keys take the single-pass form of each digit pass
+// (Onesweep, Adinets & Merrill 2022): one histogram kernel counts the digits
+// of every pass up front; each pass is then one kernel whose blocks claim
+// 4096-key tiles in launch order, rank their tile as above, publish its
+// per-digit counts, and find the counts of all earlier tiles by decoupled
+// look-back over the published words (a block only waits on tiles claimed
+// before its own, whose blocks are already running, so the waits end). Every
+// wait is bounded: a wait that runs out sets the error word at the start of
+// the temp buffer and the pass goes on (its output is then wrong, never hung).
+//
 // Used twice per render: the per-record depth sort (32 bits, 4 passes) and the
 // per-key tile sort (ceil(log2(tiles)) bits, 2 passes up to 18 bits). Sorting
 // records by depth and then keys stably by tile gives the order of a stable
@@ -48,6 +58,12 @@ static int sort_grid(long long n, int num_sms) {
     return (int)(g < 1 ? 1 : g);
 }
 
+// single-pass layout: the histograms of every pass, the tile counters, then
+// the status words of each pass (tiles x bins)
+constexpr size_t kOneHistBytes = 4 * 4 * 512;   // kMaxOnePasses x kMaxBins words
+constexpr size_t kOneCounterBytes = 256;
+static size_t one_status_words(long long n) { return (size_t)((n + kSortTile - 1) / kSortTile) * 512; }
+
 size_t radix_temp_bytes(long long n, int num_sms) {
     int G = sort_grid(n, num_sms);
     long long hist = (long long)kMaxBins * G + 1;
@@ -56,7 +72,8 @@ size_t radix_temp_bytes(long long n, int num_sms) {
     b += scan_u32_temp_bytes(hist);
     b = (b + 255) & ~(size_t)255;
     b += 256;  // total
-    return b;
+    const size_t one = kOneHistBytes + kOneCounterBytes + 4 * 4 * one_status_words(n);
+    return b > one ? b : one;
 }
 
 __global__ void __launch_bounds__(kSortThreads)
@@ -231,11 +248,288 @@ radix_downsweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// Single-pass digit passes (decoupled look-back)
+// ---------------------------------------------------------------------------
+constexpr int kMaxOnePasses = 4;
+constexpr int kHistCopies = 4;                 // warp-pair private histograms
+constexpr uint32_t kStatAgg = 1u << 30;        // the tile's own digit count
+constexpr uint32_t kStatInc = 2u << 30;        // count of the tile and every tile before it
+constexpr uint32_t kStatVal = (1u << 30) - 1u;
+constexpr long long kOneMaxKeys = 1LL << 30;   // counts must fit the 30-bit field
+constexpr int kLookbackSpins = 1 << 22;        // per wait, with a short sleep each
+
+struct OnePlan {
+    int passes;
+    int shift[kMaxOnePasses];
+    int bins[kMaxOnePasses];
+};
+static_assert(kOneHistBytes == (size_t)kMaxOnePasses * kMaxBins * 4, "histogram layout");
+static_assert(kOneCounterBytes >= (kMaxOnePasses + 1) * 4, "counters and the spare error word");
+
+// Digit counts of every pass in one read of the keys.
+__global__ void __launch_bounds__(kSortThreads)
+radix_hist_kernel(const uint32_t* __restrict__ keys, long long n, OnePlan pl,
+                  uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[kHistCopies][kMaxOnePasses][kMaxBins];
+    for (int i = threadIdx.x; i < kHistCopies * kMaxOnePasses * kMaxBins; i += kSortThreads)
+        (&h[0][0][0])[i] = 0;
+    __syncthreads();
+    const int copy = (threadIdx.x >> 5) & (kHistCopies - 1);
+    for (long long i = (long long)blockIdx.x * kSortThreads + threadIdx.x; i < n;
+         i += (long long)gridDim.x * kSortThreads) {
+        const uint32_t k = keys[i];
+#pragma unroll
+        for (int p = 0; p < kMaxOnePasses; ++p)
+            if (p < pl.passes)
+                atomicAdd(&h[copy][p][(k >> pl.shift[p]) & (uint32_t)(pl.bins[p] - 1)], 1u);
+    }
+    __syncthreads();
+    for (int p = 0; p < pl.passes; ++p)
+        for (int d = threadIdx.x; d < pl.bins[p]; d += kSortThreads) {
+            uint32_t c = 0;
+#pragma unroll
+            for (int q = 0; q < kHistCopies; ++q) c += h[q][p][d];
+            if (c) atomicAdd(&hist[p * kMaxBins + d], c);
+        }
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+struct OneSmem {
+    uint32_t keys[kSortTile];
+    uint32_t vals[kSortTile];
+    uint32_t whist[kSortWarps][kMaxBins + 1];
+    uint32_t digoff[kMaxBins + 1];  // tile-local exclusive digit offsets
+    uint32_t gbase[kMaxBins];       // output position of the tile's first key of each digit
+    uint32_t cnt[kMaxBins + 1];
+    uint32_t warp_tot[kSortWarps];
+    int tile;
+};
+
+// Exclusive scan of c[0..bins) (two digits per thread) into out; every thread
+// of the block calls it.
+__device__ __forceinline__ void block_digit_scan(const uint32_t* c_in, uint32_t* out, int bins,
+                                                 uint32_t* warp_tot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d0 = threadIdx.x * kBinsPerThread;
+    uint32_t c[kBinsPerThread], sum = 0;
+#pragma unroll
+    for (int e = 0; e < kBinsPerThread; ++e) {
+        c[e] = d0 + e < bins ? c_in[d0 + e] : 0u;
+        sum += c[e];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) run += (w < warp) ? warp_tot[w] : 0u;
+#pragma unroll
+    for (int e = 0; e < kBinsPerThread; ++e) {
+        if (d0 + e < bins) out[d0 + e] = run;
+        run += c[e];
+    }
+    __syncthreads();
+}
+
+// One digit pass: grid = one block per tile.
+__global__ void __launch_bounds__(kSortThreads, 4)
+radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+               uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, long long n,
+               int shift, int bins, const uint32_t* __restrict__ hist, uint32_t* status,
+               uint32_t* tile_counter, uint32_t* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OneSmem& S = *reinterpret_cast<OneSmem*>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t mask = (uint32_t)bins - 1u;
+    const int bits_here = __ffs(bins) - 1;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    if (threadIdx.x == 0) S.tile = (int)atomicAdd(tile_counter, 1u);
+    for (int i = threadIdx.x; i < kSortWarps * (kMaxBins + 1); i += kSortThreads)
+        (&S.whist[0][0])[i] = 0;
+    __syncthreads();
+    const int tile = S.tile;
+    const long long base = (long long)tile * kSortTile;
+    const int valid = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
+    uint32_t k[kSortItems], rk[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const int local = warp * kWarpSpan + it * 32 + lane;
+        k[it] = local < valid ? keys_in[base + local] : 0xffffffffu;
+    }
+    // rank each item among equal digits of its warp, in (item, lane) order
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const int local = warp * kWarpSpan + it * 32 + lane;
+        const bool ok = local < valid;
+        const uint32_t d = ok ? (k[it] >> shift) & mask : (uint32_t)bins;
+        const unsigned vm = __ballot_sync(0xffffffffu, ok);
+        unsigned peers = ok ? vm : ~vm;
+        for (int b = 0; b < bits_here; ++b) {
+            const bool bit = (d >> b) & 1u;
+            const unsigned bb = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bb : ~bb;
+        }
+        const int leader = __ffs(peers) - 1;
+        uint32_t b = 0;
+        if (lane == leader) {
+            b = S.whist[warp][d];
+            S.whist[warp][d] = b + (uint32_t)__popc(peers);
+        }
+        b = __shfl_sync(0xffffffffu, b, leader);
+        rk[it] = b + (uint32_t)__popc(peers & lt_mask);
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, and the tile's digit count
+    for (int d = threadIdx.x; d < bins; d += kSortThreads) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kSortWarps; ++w) {
+            const uint32_t c = S.whist[w][d];
+            S.whist[w][d] = run;
+            run += c;
+        }
+        S.cnt[d] = run;
+        // publish the tile's count at once, so that later tiles can look past it
+        st_relaxed(&status[(long long)tile * bins + d], (tile == 0 ? kStatInc : kStatAgg) | run);
+    }
+    __syncthreads();
+    // this pass's global digit offsets (exclusive scan of the histogram) into gbase
+    block_digit_scan(hist, S.gbase, bins, S.warp_tot);
+    // decoupled look-back: the count of every earlier tile, digit by digit
+    for (int d = threadIdx.x; d < bins; d += kSortThreads) {
+        uint32_t prefix = 0;
+        for (int t = tile - 1; t >= 0; --t) {
+            const uint32_t* w = &status[(long long)t * bins + d];
+            uint32_t v = ld_relaxed(w);
+            int spins = 0;
+            while ((v & ~kStatVal) == 0u) {
+                if (++spins > kLookbackSpins) {
+                    atomicExch(err, 1u);
+                    break;
+                }
+                __nanosleep(32);
+                v = ld_relaxed(w);
+            }
+            prefix += v & kStatVal;
+            if ((v & kStatInc) || spins > kLookbackSpins) break;
+        }
+        if (tile > 0)
+            st_relaxed(&status[(long long)tile * bins + d], kStatInc | ((prefix + S.cnt[d]) & kStatVal));
+        S.gbase[d] += prefix;
+    }
+    // tile-local digit offsets
+    block_digit_scan(S.cnt, S.digoff, bins, S.warp_tot);
+    if (threadIdx.x == 0) S.digoff[bins] = (uint32_t)valid;
+    __syncthreads();
+    // place the keys; rk becomes the tile-local position
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const int local = warp * kWarpSpan + it * 32 + lane;
+        if (local < valid) {
+            const uint32_t d = (k[it] >> shift) & mask;
+            rk[it] += S.digoff[d] + S.whist[warp][d];
+            S.keys[rk[it]] = k[it];
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; ++it) {
+        const int local = warp * kWarpSpan + it * 32 + lane;
+        if (local < valid)
+            S.vals[rk[it]] = vals_in ? vals_in[base + local] : (uint32_t)(base + local);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < valid; i += kSortThreads) {
+        const uint32_t key = S.keys[i];
+        const uint32_t d = (key >> shift) & mask;
+        const uint32_t g = S.gbase[d] + ((uint32_t)i - S.digoff[d]);
+        keys_out[g] = key;
+        vals_out[g] = S.vals[i];
+    }
+}
+
+static cudaError_t radix_sort_one(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
+                                  uint32_t* vals_b, long long n, const SortPlan& plan, void* temp,
+                                  int num_sms, bool vals_iota, bool* in_b, uint32_t* err,
+                                  cudaStream_t s) {
+    uint32_t* hist = (uint32_t*)temp;
+    uint32_t* counters = (uint32_t*)((char*)temp + kOneHistBytes);
+    uint32_t* status = (uint32_t*)((char*)temp + kOneHistBytes + kOneCounterBytes);
+    if (!err) err = counters + kMaxOnePasses;  // a scratch word when the caller keeps none
+    const long long tiles = (n + kSortTile - 1) / kSortTile;
+    OnePlan pl{};
+    pl.passes = plan.passes;
+    size_t status_words = 0;
+    int shift = plan.begin_bit;
+    for (int p = 0; p < plan.passes; ++p) {
+        pl.shift[p] = shift;
+        pl.bins[p] = 1 << plan.bits_per_pass[p];
+        shift += plan.bits_per_pass[p];
+        status_words += (size_t)tiles * pl.bins[p];
+    }
+    // histograms, counters and status words start at zero
+    cudaError_t e = cudaMemsetAsync(temp, 0, kOneHistBytes + kOneCounterBytes + 4 * status_words, s);
+    if (e != cudaSuccess) return e;
+    // the shared-memory opt-in is a per-device function attribute
+    constexpr int kMaxDevices = 64;
+    static std::atomic<bool> attr_set[kMaxDevices];
+    const size_t smem = sizeof(OneSmem);
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices || !attr_set[dev].load()) {
+        e = cudaFuncSetAttribute(radix_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < kMaxDevices) attr_set[dev].store(true);
+    }
+    long long hg = div_up(n, (long long)kSortThreads * 8);
+    if (hg > 4LL * num_sms) hg = 4LL * num_sms;
+    note_launch();
+    radix_hist_kernel<<<(unsigned)hg, kSortThreads, 0, s>>>(keys_a, n, pl, hist);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    uint32_t *ki = keys_a, *vi = vals_a, *ko = keys_b, *vo = vals_b;
+    uint32_t* st = status;
+    for (int p = 0; p < plan.passes; ++p) {
+        const uint32_t* vread = (p == 0 && vals_iota) ? nullptr : vi;
+        note_launch();
+        radix_onesweep<<<(unsigned)tiles, kSortThreads, smem, s>>>(
+            ki, vread, ko, vo, n, pl.shift[p], pl.bins[p], hist + p * kMaxBins, st,
+            counters + p, err);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        st += (size_t)tiles * pl.bins[p];
+        uint32_t* tk = ki; ki = ko; ko = tk;
+        uint32_t* tv = vi; vi = vo; vo = tv;
+        *in_b = !*in_b;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
                              uint32_t* vals_b, long long n, const SortPlan& plan, void* temp,
-                             int num_sms, bool vals_iota, bool* in_b, cudaStream_t s) {
+                             int num_sms, bool vals_iota, bool* in_b, uint32_t* err,
+                             cudaStream_t s) {
     *in_b = false;
     if (n <= 0 || plan.passes == 0) return cudaSuccess;
+    if (n < kOneMaxKeys && plan.passes <= kMaxOnePasses)
+        return radix_sort_one(keys_a, vals_a, keys_b, vals_b, n, plan, temp, num_sms, vals_iota,
+                              in_b, err, s);
     const int G = sort_grid(n, num_sms);
     const long long n_tiles = (n + kSortTile - 1) / kSortTile;
     const int tpb = (int)((n_tiles + G - 1) / G);

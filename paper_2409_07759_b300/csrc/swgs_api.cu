@@ -78,7 +78,7 @@ struct swgs_ctx {
         vals_tmp, vals_b, sranges, tile_cnt, tile_off, mature_ids, mature_stage, codec_keys_a,
         codec_keys_b, codec_vals_a, codec_vals_b, codec_flags, codec_idx, codec_stage, sort_tmp,
         counter, totals, l1_tab, elig, reloc_w, reloc_cdf, reloc_dead, reloc_tg, reloc_cnt,
-        reloc_nd;
+        reloc_nd, sort_err;
     void* pinned = nullptr;
     size_t pinned_cap = 0;
     std::vector<swgs_saved*> pool;
@@ -171,6 +171,16 @@ bool ensure(swgs_ctx* c, Buf& b, size_t bytes, cudaStream_t s) {
 
 template <typename T>
 T* P(Buf& b) { return reinterpret_cast<T*>(b.p); }
+
+// The sorts' look-back error word, zeroed when first allocated; read back with
+// the key totals (null if it cannot be allocated: the sort then keeps none).
+uint32_t* sort_err_word(swgs_ctx* c, cudaStream_t s) {
+    if (!c->sort_err.p) {
+        if (!ensure(c, c->sort_err, 16, s)) return nullptr;
+        if (cudaMemsetAsync(c->sort_err.p, 0, 16, s) != cudaSuccess) return nullptr;
+    }
+    return P<uint32_t>(c->sort_err);
+}
 
 bool valid_tile(int w, int h) { return (w == 16 && h == 16) || (w == 8 && h == 8) || (w == 32 && h == 8); }
 bool valid_batch(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
@@ -387,7 +397,8 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             StageScope sc_(ctx, SWGS_STAGE_DEPTH_SORT, s);
             CK(radix_sort_pairs(P<uint32_t>(B.rec_depth), P<uint32_t>(ctx->order_a),
                                 P<uint32_t>(ctx->order_b), P<uint32_t>(ctx->tcount), (long long)R,
-                                dp, ctx->sort_tmp.p, ctx->num_sms, true, &in_b, s));
+                                dp, ctx->sort_tmp.p, ctx->num_sms, true, &in_b,
+                                sort_err_word(ctx, s), s));
         }
         // 4 passes: results back in (rec_depth, order_a)
         const uint32_t* order = in_b ? P<uint32_t>(ctx->tcount) : P<uint32_t>(ctx->order_a);
@@ -405,9 +416,20 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
         }
         CK(cudaMemcpyAsync(ctx->pinned, ctx->totals.p, 2 * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s));
+        uint32_t* serr = sort_err_word(ctx, s);
+        if (serr)
+            CK(cudaMemcpyAsync((char*)ctx->pinned + 16, serr, 4, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         unsigned long long tot[2] = {0, 0};
         memcpy(tot, ctx->pinned, sizeof(tot));
+        uint32_t sort_failed = 0;
+        if (serr) memcpy(&sort_failed, (char*)ctx->pinned + 16, 4);
+        if (sort_failed) {
+            CK(cudaMemsetAsync(serr, 0, 4, s));
+            return fail(ctx, SWGS_ETIMEOUT,
+                        "a radix-sort look-back wait ran out (this call's depth order, or the "
+                        "previous call's sorted keys, are wrong)");
+        }
         if (tot[1] > 0x7fffffffULL || tot[0] > 0x7fffffffULL)
             return fail(ctx, SWGS_EINVAL,
                         "%llu tile keys (%llu super-tile keys) exceed the 2^31 limit of one "
@@ -442,7 +464,8 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             StageScope sc_(ctx, SWGS_STAGE_TILE_SORT, s);
             CK(radix_sort_pairs(P<uint32_t>(ctx->keys_a), P<uint32_t>(ctx->vals_tmp),
                                 P<uint32_t>(ctx->keys_b), P<uint32_t>(ctx->vals_b), (long long)K,
-                                sp, ctx->sort_tmp.p, ctx->num_sms, false, &kb, s));
+                                sp, ctx->sort_tmp.p, ctx->num_sms, false, &kb,
+                                sort_err_word(ctx, s), s));
         }
         const uint32_t* skeys = kb ? P<uint32_t>(ctx->keys_b) : P<uint32_t>(ctx->keys_a);
         const uint32_t* svals = kb ? P<uint32_t>(ctx->vals_b) : P<uint32_t>(ctx->vals_tmp);
@@ -670,7 +693,7 @@ void swgs_destroy(swgs_ctx* ctx) {
                  &ctx->codec_vals_a, &ctx->codec_vals_b, &ctx->codec_flags, &ctx->codec_idx,
                  &ctx->codec_stage, &ctx->sort_tmp, &ctx->counter, &ctx->totals, &ctx->l1_tab,
                  &ctx->elig, &ctx->reloc_w, &ctx->reloc_cdf, &ctx->reloc_dead, &ctx->reloc_tg,
-                 &ctx->reloc_cnt, &ctx->reloc_nd};
+                 &ctx->reloc_cnt, &ctx->reloc_nd, &ctx->sort_err};
     for (Buf* b : bs) ctx_free(ctx, *b, s);
     for (swgs_saved* sv : ctx->all_saved) {
         free_saved_buffers(ctx, sv, s);
@@ -812,7 +835,7 @@ swgs_status swgs_slice_encode(swgs_ctx* ctx, const swgs_gaussians* src, int64_t 
                        P<uint32_t>(ctx->codec_vals_a), P<uint32_t>(ctx->codec_vals_b),
                        P<uint32_t>(ctx->block_cnt), P<uint32_t>(ctx->codec_idx),
                        P<uint8_t>(ctx->codec_flags), ctx->sort_tmp.p, ctx->scan_tmp.p,
-                       P<unsigned long long>(ctx->totals)};
+                       P<unsigned long long>(ctx->totals), sort_err_word(ctx, s)};
         uint32_t* sel = nullptr;
         CK(launch_codec_select(src->opacity_logits, count, keep, w, ctx->num_sms, &sel, s));
         idx = sel;

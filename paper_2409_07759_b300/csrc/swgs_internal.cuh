@@ -401,9 +401,12 @@ size_t radix_temp_bytes(long long n, int num_sms);
 // Stable LSD sort of (key, value) pairs. Results end in keys_b/vals_b after an
 // odd number of passes, else in keys_a/vals_a; *in_b receives which.
 // vals_iota: the values start as 0..n-1 (vals_a is not read).
+// err: a device word set to 1 if a look-back wait of the single-pass form ran
+// out (the output is then wrong); null keeps no record.
 cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
                              uint32_t* vals_b, long long n, const SortPlan& plan, void* temp,
-                             int num_sms, bool vals_iota, bool* in_b, cudaStream_t s);
+                             int num_sms, bool vals_iota, bool* in_b, uint32_t* err,
+                             cudaStream_t s);
 
 // k_keys.cu
 // Super tiles: SX x SY tiles (4 x 4, or 2 x 8 for 32x8 tiles); at most 2^16 per
@@ -451,6 +454,7 @@ struct CodecScratch {
     uint8_t* flags;
     void *sort_tmp, *scan_tmp;
     unsigned long long* total;
+    uint32_t* sort_err;  // the sort's look-back error word (may be null)
 };
 cudaError_t launch_codec_select(const float* logits, long long count, long long keep,
                                 CodecScratch& w, int num_sms, uint32_t** out_idx, cudaStream_t s);
