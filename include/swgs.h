@@ -452,6 +452,17 @@ swgs_status swgs_profile_read(swgs_ctx *ctx, swgs_profile *out, int32_t reset);
 /* Kernels launched by this library in this process so far (all contexts). */
 int64_t swgs_kernel_launches(void);
 
+/* Failure-path check of the radix sort's bounded look-back wait (no paper
+ * counterpart). Runs one digit pass over two 4096-key tiles of scratch data
+ * with the tile counter started at 1: the one block takes tile 1, and tile 0,
+ * which no block takes, never publishes its counts, so the block's look-back
+ * wait runs out after its iteration limit (about a second) and
+ * the pass finishes with its output wrong. Every access stays inside the
+ * scratch buffers. Synchronises `stream`; returns SWGS_ETIMEOUT when the
+ * sort's error word was raised (the expected result), SWGS_OK if it was not.
+ * The context stays usable. */
+swgs_status swgs_selftest_sort_timeout(swgs_ctx *ctx, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

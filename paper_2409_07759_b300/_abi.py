@@ -152,6 +152,7 @@ PROTOTYPES = [
     ("swgs_profile_enable", C.c_int, [C.c_void_p, C.c_int32]),
     ("swgs_profile_read", C.c_int, [C.c_void_p, C.POINTER(SwgsProfile), C.c_int32]),
     ("swgs_kernel_launches", C.c_int64, []),
+    ("swgs_selftest_sort_timeout", C.c_int, [C.c_void_p, C.c_void_p]),
 ]
 
 _lib = None

@@ -296,6 +296,11 @@ class Renderer:
     def kernel_launches() -> int:
         return int(_abi.load().swgs_kernel_launches())
 
+    def selftest_sort_timeout(self, stream=None):
+        """Run the radix sort's look-back timeout check (include/swgs.h): raises
+        SwgsError (ETIMEOUT) when the bounded wait ran out, as it should."""
+        self._check(_abi.load().swgs_selftest_sort_timeout(self.ctx, self._stream(stream)))
+
     # -- Sec. 4.2 / Alg. 2 filter ------------------------------------------------
     def active_ids(self, state: GaussianState, frame: int, stream=None) -> torch.Tensor:
         ids = torch.empty(max(1, state.n), dtype=torch.int32, device="cuda")

@@ -257,7 +257,7 @@ constexpr uint32_t kStatAgg = 1u << 30;        // the tile's own digit count
 constexpr uint32_t kStatInc = 2u << 30;        // count of the tile and every tile before it
 constexpr uint32_t kStatVal = (1u << 30) - 1u;
 constexpr long long kOneMaxKeys = 1LL << 30;   // counts must fit the 30-bit field
-constexpr int kLookbackSpins = 1 << 22;        // per wait, with a short sleep each
+constexpr int kLookbackSpins = 1 << 20;        // per wait (~1 us each: about a second)
 
 struct OnePlan {
     int passes;
@@ -519,6 +519,42 @@ static cudaError_t radix_sort_one(uint32_t* keys_a, uint32_t* vals_a, uint32_t* 
         *in_b = !*in_b;
     }
     return cudaSuccess;
+}
+
+// The look-back timeout check: scratch = 2 x kSortTile keys, 2 x kSortTile out
+// keys and values, the status words of two 128-bin tiles, a counter and the
+// error word (sort_timeout_scratch_bytes). The counter starts at 1, so the one
+// block takes tile 1 and waits on tile 0, which nobody publishes.
+size_t sort_timeout_scratch_bytes() {
+    return (size_t)(3 * 2 * kSortTile + 2 * 128 + kMaxBins + 64) * sizeof(uint32_t);
+}
+
+cudaError_t launch_sort_timeout_check(void* scratch, uint32_t* err, cudaStream_t s) {
+    uint32_t* keys = (uint32_t*)scratch;
+    uint32_t* keys_out = keys + 2 * kSortTile;
+    uint32_t* vals_out = keys_out + 2 * kSortTile;
+    uint32_t* status = vals_out + 2 * kSortTile;
+    uint32_t* hist = status + 2 * 128;
+    uint32_t* counter = hist + kMaxBins;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sort_timeout_scratch_bytes(), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(counter, 1, 1, s);  // counter = 1
+    if (e != cudaSuccess) return e;
+    constexpr int kMaxDevices = 64;
+    static std::atomic<bool> attr_set[kMaxDevices];
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices || !attr_set[dev].load()) {
+        e = cudaFuncSetAttribute(radix_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(OneSmem));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < kMaxDevices) attr_set[dev].store(true);
+    }
+    note_launch();
+    radix_onesweep<<<1, kSortThreads, sizeof(OneSmem), s>>>(
+        keys, nullptr, keys_out, vals_out, 2LL * kSortTile, 0, 128, hist, status, counter, err);
+    return cudaGetLastError();
 }
 
 cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,

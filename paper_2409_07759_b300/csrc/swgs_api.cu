@@ -1416,6 +1416,25 @@ swgs_status swgs_sgld_step(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_ga
     return SWGS_OK;
 }
 
+swgs_status swgs_selftest_sort_timeout(swgs_ctx* ctx, void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    ctx->err.clear();
+    if (!ensure(ctx, ctx->sort_tmp, sort_timeout_scratch_bytes(), s))
+        return fail(ctx, SWGS_ENOMEM, "allocation failed (sort check)");
+    uint32_t* serr = sort_err_word(ctx, s);
+    if (!serr) return fail(ctx, SWGS_ENOMEM, "allocation failed (sort error word)");
+    CK(launch_sort_timeout_check(ctx->sort_tmp.p, serr, s));
+    CK(cudaMemcpyAsync(ctx->pinned, serr, 4, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    uint32_t raised = 0;
+    memcpy(&raised, ctx->pinned, 4);
+    CK(cudaMemsetAsync(serr, 0, 4, s));
+    if (raised) return fail(ctx, SWGS_ETIMEOUT, "the sort's look-back wait ran out (expected)");
+    return SWGS_OK;
+}
+
 swgs_status swgs_profile_enable(swgs_ctx* ctx, int32_t on) {
     if (!ctx) return SWGS_EINVAL;
     ctx->prof = on != 0;

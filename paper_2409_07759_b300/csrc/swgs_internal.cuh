@@ -401,6 +401,10 @@ size_t radix_temp_bytes(long long n, int num_sms);
 // Stable LSD sort of (key, value) pairs. Results end in keys_b/vals_b after an
 // odd number of passes, else in keys_a/vals_a; *in_b receives which.
 // vals_iota: the values start as 0..n-1 (vals_a is not read).
+// One digit pass whose look-back wait runs out by construction (the failure
+// path check); scratch of sort_timeout_scratch_bytes().
+size_t sort_timeout_scratch_bytes();
+cudaError_t launch_sort_timeout_check(void* scratch, uint32_t* err, cudaStream_t s);
 // err: a device word set to 1 if a look-back wait of the single-pass form ran
 // out (the output is then wrong); null keeps no record.
 cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
