@@ -50,7 +50,7 @@ TRAFFIC_CAPTURES = {
     ("blend_bwd", "16x16/b64/ppt8"): {
         "bytes": 1_232_157_952 + 20_062_208,
         "sources": ("csrc/k_blend.cu", "csrc/swgs_internal.cuh"),
-        "digest": "95ce481a8e2e7db9",
+        "digest": "404d0e007b4a42d5",
     },
 }
 
