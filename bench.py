@@ -656,8 +656,10 @@ def main():
     stage_cost = {
         "blend_fwd": ("alu", FLOP_PER_PAIR_FWD * pairs_fwd / 1e12, "TFLOP/s"),
         "blend_bwd": ("alu", FLOP_PER_PAIR_BWD * pairs_bwd / 1e12, "TFLOP/s"),
-        "tile_sort": ("hbm", 16.0 * sort_passes * n_sort_keys / 1e9, "GB/s"),
-        "depth_sort": ("hbm", 16.0 * 4 * n_rec / 1e9, "GB/s"),
+        # per digit pass: read + write key and value (16 B); once: the digit
+        # counts' read of the keys (4 B)
+        "tile_sort": ("hbm", (16.0 * sort_passes + 4.0) * n_sort_keys / 1e9, "GB/s"),
+        "depth_sort": ("hbm", (16.0 * 4 + 4.0) * n_rec / 1e9, "GB/s"),
         # super keys written, record rectangles and row runs read
         "emit": ("hbm", (8.0 * n_sort_keys + 80.0 * n_rec) / 1e9, "GB/s"),
         # super ranges (4 B/key), count pass (4 B/key), write pass (8 B/key
