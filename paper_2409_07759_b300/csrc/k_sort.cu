@@ -413,20 +413,30 @@ radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict_
     // decoupled look-back: the count of every earlier tile, digit by digit
     for (int d = threadIdx.x; d < bins; d += kSortThreads) {
         uint32_t prefix = 0;
-        for (int t = tile - 1; t >= 0; --t) {
-            const uint32_t* w = &status[(long long)t * bins + d];
-            uint32_t v = ld_relaxed(w);
-            int spins = 0;
-            while ((v & ~kStatVal) == 0u) {
-                if (++spins > kLookbackSpins) {
-                    atomicExch(err, 1u);
-                    break;
+        bool done = false;
+        for (int t0 = tile - 1; t0 >= 0 && !done; t0 -= 4) {
+            // the next four predecessors' words in flight together
+            uint32_t v4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                v4[q] = t0 - q >= 0 ? ld_relaxed(&status[(long long)(t0 - q) * bins + d]) : kStatInc;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (done || t0 - q < 0) continue;
+                const uint32_t* w = &status[(long long)(t0 - q) * bins + d];
+                uint32_t v = v4[q];
+                int spins = 0;
+                while ((v & ~kStatVal) == 0u) {
+                    if (++spins > kLookbackSpins) {
+                        atomicExch(err, 1u);
+                        break;
+                    }
+                    __nanosleep(32);
+                    v = ld_relaxed(w);
                 }
-                __nanosleep(32);
-                v = ld_relaxed(w);
+                prefix += v & kStatVal;
+                if ((v & kStatInc) || spins > kLookbackSpins) done = true;
             }
-            prefix += v & kStatVal;
-            if ((v & kStatInc) || spins > kLookbackSpins) break;
         }
         if (tile > 0)
             st_relaxed(&status[(long long)tile * bins + d], kStatInc | ((prefix + S.cnt[d]) & kStatVal));
