@@ -193,8 +193,11 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
     const int ltx = tx0 + (lane & 15) % SX, lty = ty0 + (lane & 15) / SX;
     const bool lvalid = lane < 16 && ltx < V.ntx && lty < V.nty;
     const int ltile = V.tile_base + lty * V.ntx + ltx;
-    long long run = (WRITE && lvalid) ? (long long)toff[ltile] : 0;  // tile's next offset
-    long long total = 0;                                            // counting pass
+    // offsets in 32 bits: a batch holds fewer than 2^31 tile keys (checked when
+    // it is sized), so cap and every offset below fit
+    const uint32_t cap32 = (uint32_t)(cap < 0x7fffffffLL ? cap : 0x7fffffffLL);
+    uint32_t run = (WRITE && lvalid) ? toff[ltile] : 0u;  // tile's next offset
+    uint32_t total = 0;                                  // counting pass
     for (int c0 = 0; c0 < L; c0 += NT) {
         const int i = c0 + threadIdx.x;
         unsigned m = 0;
@@ -211,23 +214,23 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
             *reinterpret_cast<uint4*>(s_cnt[warp]) = make_uint4(sp[0], sp[1], sp[2], sp[3]);
         __syncthreads();
         // lane t < 16: tile t's count in the warps before this one, and in the chunk
-        long long before = 0, chunk = 0;
+        uint32_t before = 0, chunk = 0;
         if (lane < 16) {
             const int k = lane >> 2, sh = 8 * (lane & 3);
             for (int w = 0; w < kExpandWarps; ++w) {
-                const long long c = (s_cnt[w][k] >> sh) & 0xffu;
+                const uint32_t c = (s_cnt[w][k] >> sh) & 0xffu;
                 before += w < warp ? c : 0;
                 chunk += c;
             }
         }
         if (WRITE) {
-            const long long base = run + before;
+            const uint32_t base = run + before;
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
                 const bool hit = (m >> t) & 1u;
                 const unsigned bal = __ballot_sync(0xffffffffu, hit);
-                const long long o = __shfl_sync(0xffffffffu, base, t) + __popc(bal & lt);
-                if (hit && o < cap) vals[o] = r;
+                const uint32_t o = __shfl_sync(0xffffffffu, base, t) + (uint32_t)__popc(bal & lt);
+                if (hit && o < cap32) vals[o] = r;
             }
             run += chunk;
         } else {
@@ -237,8 +240,8 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
     }
     if (warp == 0 && lvalid) {
         if (WRITE) {
-            const long long s0 = toff[ltile];
-            ranges[ltile] = make_int2((int)(s0 < cap ? s0 : cap), (int)(run < cap ? run : cap));
+            const uint32_t s0 = toff[ltile];
+            ranges[ltile] = make_int2((int)(s0 < cap32 ? s0 : cap32), (int)(run < cap32 ? run : cap32));
         } else {
             tcount[ltile] = (uint32_t)total;
         }
