@@ -208,7 +208,9 @@ __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); 
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
 // One staged Gaussian against the thread's pixel pairs (the forward's inner
-// step). CLAMP = false drops the 0.99 clamp (valid for opacity <= 0.99).
+// step). CLAMP: the Gaussian's opacity exceeds 0.99, so alpha may take the
+// 0.99 clamp; the reverse blend splits on the same staged flag, so both
+// passes take the same alpha.
 template <bool CLAMP, int NP, bool COUNT>
 __device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float4 gd, float4 ge,
                                           float2 dx, float2 adx, int pos, int pos1,
@@ -250,10 +252,10 @@ __device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float
     }
 }
 
-// 4 pixels a thread: at least 20 blocks of 64 threads per SM (48 registers),
-// measured faster than the 66-register build at 15 blocks
+// 4 pixels a thread: at least 16 blocks of 64 threads per SM (63 registers,
+// no spills with the two clamp bodies); 18-20 blocks spill
 template <int TW, int TH, int BATCH, int PPT, bool COUNT>
-__global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 20 : 1)) blend_fwd_x2_kernel(BlendArgs a) {
+__global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_x2_kernel(BlendArgs a) {
     static_assert(PPT % 2 == 0, "pixels are taken in pairs");
     constexpr int NT = TileGeom<TW, TH, PPT>::NT;
     constexpr int NP = PPT / 2;
@@ -317,10 +319,12 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 20 : 1)) blend_fwd_
                 const int pos = b0 + j, pos1 = pos - rg.x + 1;
                 const float2 dx = __fadd2_rn(px2, lo2(ga));
                 const float2 adx = __fmul2_rn(lo2(gb), dx);
-                // the clamp is kept for every Gaussian here: splitting on the
-                // staged flag (as the reverse blend does) measured no faster
-                fwd_pairs<true, NP, COUNT>(ga, gb, gc, gd, ge, dx, adx, pos, pos1, T, C0, C1, C2,
-                                           py, last, stop);
+                if (ge.w != 0.f)
+                    fwd_pairs<true, NP, COUNT>(ga, gb, gc, gd, ge, dx, adx, pos, pos1, T, C0, C1,
+                                               C2, py, last, stop);
+                else
+                    fwd_pairs<false, NP, COUNT>(ga, gb, gc, gd, ge, dx, adx, pos, pos1, T, C0,
+                                                C1, C2, py, last, stop);
                 }
                 tdone = true;
 #pragma unroll
