@@ -432,6 +432,20 @@ def build_workload(args, rank=0):
     return scene, views, targets
 
 
+def arm_config(args, views, world=1):
+    """The workload both arms report (the reference arm samples it on the host)."""
+    mpix = sum(v.width * v.height for v in views) / 1e6
+    return {"workload": "sliding-window step: 300k Gaussians SH3, frames 145-154 x "
+                        f"{args.views} of 20 ring cameras = {len(views)} views of 1352x1014, "
+                        "fwd+bwd + Adam/SGLD + relocation + 6k-slot slice update (from HBM; "
+                        "from pinned host in e2e)",
+            "mpix_per_step": mpix, "tile": args.tile, "batch": args.batch,
+            "pixels_per_thread": args.ppt,
+            "bwd_pixels_per_thread": args.bwd_ppt, "bwd_batch": args.bwd_batch,
+            "targets": ("8-bit RGB frames (k/255)" if args.targets == "u8" else "float32 RGB"),
+            "parallelism": f"dp{world}", "l2": "flushed (256 MB write) before each step"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -455,9 +469,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "sliding-window step, 300k Gaussians SH3, 40 x 1352x1014 "
-                                   "views (one view per reference step)",
-                       "l2": "inputs larger than L2"},
+            "config": arm_config(args, views),
             "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
                              "sample": "one view per step: " + sample},
             "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0,
@@ -724,16 +736,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded scene shaped like DyNeRF multi-view clips)",
-            "config": {"workload": "sliding-window step: 300k Gaussians SH3, frames 145-154 x "
-                                   f"{args.views} of 20 ring cameras = {len(views)} views of "
-                                   "1352x1014, fwd+bwd + Adam/SGLD + relocation + 6k-slot "
-                                   "slice update (from HBM; from pinned host in e2e)",
-                       "mpix_per_step": mpix, "tile": args.tile, "batch": args.batch,
-                       "pixels_per_thread": args.ppt,
-                       "bwd_pixels_per_thread": args.bwd_ppt, "bwd_batch": args.bwd_batch,
-                       "targets": ("8-bit RGB frames (k/255)" if args.targets == "u8"
-                                   else "float32 RGB"),
-                       "parallelism": f"dp{world}", "l2": "flushed (256 MB write) before each step"},
+            "config": arm_config(args, views, world),
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
