@@ -69,7 +69,7 @@ def captured_traffic(stage: str, shape: str):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="swgs", choices=["swgs", "reference"])
     ap.add_argument("--plain-steps", type=int, default=3)
