@@ -1,25 +1,27 @@
 // k_sort.cu -- stable LSD radix sort of (uint32 key, uint32 value) pairs.
 //
-// Each pass (<= 9 bits, up to 512 buckets): an upsweep histogram per block
-// over a contiguous share of 4096-key tiles, an exclusive scan of the
-// (digit, block) counts in digit-major order, and a downsweep that ranks each
-// tile stably (the lanes sharing a digit found with one warp ballot per digit
-// bit, which measured faster than match.any; warps in order), stages it in
-// shared memory in digit order and writes it out, so global writes are
-// contiguous within each digit run. Keys and ranks are the only per-item registers; the
-// values are loaded after the keys have been placed. The grid is a fixed
-// multiple of the SM count and block b owns the same tile range in both
-// kernels, so no block ever waits for another.
+// Digit passes of up to 9 bits (512 buckets). Every pass ranks 4096-key tiles
+// the same way: the lanes of a warp that share a digit are found with one
+// warp ballot per digit bit (measured faster than match.any), warps in order;
+// the tile is staged in shared memory in digit order and written out, so
+// global writes are contiguous within each digit run. Keys and ranks are the
+// only per-item registers; the values are loaded after the keys are placed.
 //
 // Inputs below 2^30 keys take the single-pass form of each digit pass
 // (Onesweep, Adinets & Merrill 2022): one histogram kernel counts the digits
 // of every pass up front; each pass is then one kernel whose blocks claim
-// 4096-key tiles in launch order, rank their tile as above, publish its
-// per-digit counts, and find the counts of all earlier tiles by decoupled
-// look-back over the published words (a block only waits on tiles claimed
-// before its own, whose blocks are already running, so the waits end). Every
-// wait is bounded: a wait that runs out sets the error word at the start of
-// the temp buffer and the pass goes on (its output is then wrong, never hung).
+// tiles in launch order, rank their tile, publish its per-digit counts, and
+// find the counts of all earlier tiles by decoupled look-back over the
+// published words, four tiles at a time. A block only waits on tiles claimed
+// before its own, whose blocks are already running, so the waits end; every
+// wait is still bounded, and one that runs out sets the caller's error word
+// (or a spare word of the temp buffer) and the pass goes on, its output wrong
+// but never hung.
+//
+// Larger inputs take three kernels per pass: an upsweep histogram per block
+// over a contiguous share of tiles, an exclusive scan of the (digit, block)
+// counts in digit-major order, and a downsweep over the same tiles; no block
+// waits for another.
 //
 // Used twice per render: the per-record depth sort (32 bits, 4 passes) and the
 // per-key tile sort (ceil(log2(tiles)) bits, 2 passes up to 18 bits). Sorting
