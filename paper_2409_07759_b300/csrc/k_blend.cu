@@ -6,10 +6,17 @@
 // thread owns PPT vertically adjacent pixels of the tile; the Gaussians of the
 // tile's depth-sorted list are staged in shared memory BATCH at a time
 // (converted once per block to the log2-domain form the inner loop needs).
-// The inner loops are branch-free: every lane of a warp walks the list in
-// lockstep with predicated updates, so no lane diverges at the per-pair
-// tests, and the warp leaves as soon as a vote says all its pixels saturated;
-// the block stops staging when all its pixels have.
+// The inner loops are branch-free per pair: every lane of a warp walks the
+// list in lockstep with predicated updates, so no lane diverges at the
+// per-pair tests, and the warp leaves as soon as a vote says all its pixels
+// saturated; the block stops staging when all its pixels have. The only
+// branch inside is warp-uniform: it skips the 0.99 alpha clamp's work for
+// Gaussians whose opacity cannot reach it.
+//
+// With an even number of pixels per thread (the defaults: 4 forward, 8
+// reverse) the pixels are taken two at a time as float2 and every per-pixel
+// step is one packed FP32x2 instruction; one pixel per thread keeps the scalar
+// kernels (blend_fwd_kernel, blend_bwd_kernel).
 //
 // The backward walks the list from the block's largest last-contributor index
 // down to the front, recovering each T from the saved final transmittance by
