@@ -27,7 +27,7 @@
 extern "C" {
 #endif
 
-#define SWGS_ABI_VERSION 3
+#define SWGS_ABI_VERSION 4
 
 typedef enum swgs_status {
     SWGS_OK = 0,
@@ -57,6 +57,10 @@ typedef struct swgs_config {
     int32_t bwd_pixels_per_thread; /* reverse blend: 1, 2, 4 or 8 (16x16, 32x8: up to 8;
                                       8x8: up to 2); 0 = pixels_per_thread */
     int32_t bwd_batch;       /* reverse blend staging batch; 0 = batch */
+    int32_t sort_single_pass; /* 1: each radix digit pass is one kernel (decoupled
+                                 look-back; inputs below 2^30 keys); 0: three
+                                 kernels per pass (histogram, scan, scatter).
+                                 Same sorted order either way. */
 } swgs_config;
 
 /*
@@ -101,7 +105,8 @@ typedef struct swgs_ctx swgs_ctx;
 typedef struct swgs_saved swgs_saved;
 
 /* Fills cfg with 16x16 tiles; forward batch 64 with 4 pixels per thread;
- * reverse blend batch 64 with 8 pixels per thread; near plane 0.2; auto grid. */
+ * reverse blend batch 64 with 8 pixels per thread; near plane 0.2; auto grid;
+ * single-pass sort. */
 swgs_status swgs_default_config(swgs_config *cfg);
 
 /* Creates a context on the current CUDA device. alloc/free may be NULL. */

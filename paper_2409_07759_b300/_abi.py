@@ -35,7 +35,8 @@ class SwgsConfig(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("batch", C.c_int32),
                 ("near_plane", C.c_float), ("blocks_per_sm", C.c_int32),
                 ("count_pairs", C.c_int32), ("pixels_per_thread", C.c_int32),
-                ("bwd_pixels_per_thread", C.c_int32), ("bwd_batch", C.c_int32)]
+                ("bwd_pixels_per_thread", C.c_int32), ("bwd_batch", C.c_int32),
+                ("sort_single_pass", C.c_int32)]
 
 
 class SwgsGaussians(C.Structure):
@@ -159,7 +160,7 @@ _lib = None
 
 
 # The struct layouts above mirror include/swgs.h at this SWGS_ABI_VERSION.
-ABI_VERSION = 3
+ABI_VERSION = 4
 
 
 def load():

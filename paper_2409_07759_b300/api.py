@@ -214,7 +214,8 @@ class Renderer:
 
     def __init__(self, tile=(16, 16), batch=64, near_plane=0.2, blocks_per_sm=0,
                  count_pairs=False, pixels_per_thread=None, bwd_pixels_per_thread=None,
-                 bwd_batch=64, use_torch_allocator=True, alloc_guard=None):
+                 bwd_batch=64, use_torch_allocator=True, alloc_guard=None,
+                 sort_single_pass=True):
         if pixels_per_thread is None:      # 8x8 tiles hold at most 2 pixels per thread
             pixels_per_thread = 2 if tuple(tile) == (8, 8) else 4
         if bwd_pixels_per_thread is None:
@@ -230,6 +231,7 @@ class Renderer:
         cfg.pixels_per_thread = int(pixels_per_thread)
         cfg.bwd_pixels_per_thread = int(bwd_pixels_per_thread)
         cfg.bwd_batch = int(bwd_batch)
+        cfg.sort_single_pass = int(bool(sort_single_pass))
         self.cfg = cfg
         self.alloc_guard = alloc_guard
         self.device = torch.cuda.current_device()

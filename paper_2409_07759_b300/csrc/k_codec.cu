@@ -202,7 +202,7 @@ cudaError_t launch_codec_select(const float* logits, long long count, long long 
     const SortPlan plan = make_sort_plan(0, 32);
     bool in_b = false;
     e = radix_sort_pairs(w.keys_a, w.vals_a, w.keys_b, w.vals_b, count, plan, w.sort_tmp, num_sms,
-                         true, &in_b, w.sort_err, s);
+                         true, &in_b, w.sort_single_pass, w.sort_err, s);
     if (e != cudaSuccess) return e;
     const uint32_t* ranked = in_b ? w.vals_b : w.vals_a;
     e = cudaMemsetAsync(w.flags, 0, (size_t)count, s);

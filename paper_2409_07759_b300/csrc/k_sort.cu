@@ -571,11 +571,11 @@ cudaError_t launch_sort_timeout_check(void* scratch, uint32_t* err, cudaStream_t
 
 cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
                              uint32_t* vals_b, long long n, const SortPlan& plan, void* temp,
-                             int num_sms, bool vals_iota, bool* in_b, uint32_t* err,
-                             cudaStream_t s) {
+                             int num_sms, bool vals_iota, bool* in_b, bool single_pass,
+                             uint32_t* err, cudaStream_t s) {
     *in_b = false;
     if (n <= 0 || plan.passes == 0) return cudaSuccess;
-    if (n < kOneMaxKeys && plan.passes <= kMaxOnePasses)
+    if (single_pass && n < kOneMaxKeys && plan.passes <= kMaxOnePasses)
         return radix_sort_one(keys_a, vals_a, keys_b, vals_b, n, plan, temp, num_sms, vals_iota,
                               in_b, err, s);
     const int G = sort_grid(n, num_sms);

@@ -398,7 +398,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             CK(radix_sort_pairs(P<uint32_t>(B.rec_depth), P<uint32_t>(ctx->order_a),
                                 P<uint32_t>(ctx->order_b), P<uint32_t>(ctx->tcount), (long long)R,
                                 dp, ctx->sort_tmp.p, ctx->num_sms, true, &in_b,
-                                sort_err_word(ctx, s), s));
+                                ctx->cfg.sort_single_pass != 0, sort_err_word(ctx, s), s));
         }
         // 4 passes: results back in (rec_depth, order_a)
         const uint32_t* order = in_b ? P<uint32_t>(ctx->tcount) : P<uint32_t>(ctx->order_a);
@@ -465,7 +465,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             CK(radix_sort_pairs(P<uint32_t>(ctx->keys_a), P<uint32_t>(ctx->vals_tmp),
                                 P<uint32_t>(ctx->keys_b), P<uint32_t>(ctx->vals_b), (long long)K,
                                 sp, ctx->sort_tmp.p, ctx->num_sms, false, &kb,
-                                sort_err_word(ctx, s), s));
+                                ctx->cfg.sort_single_pass != 0, sort_err_word(ctx, s), s));
         }
         const uint32_t* skeys = kb ? P<uint32_t>(ctx->keys_b) : P<uint32_t>(ctx->keys_a);
         const uint32_t* svals = kb ? P<uint32_t>(ctx->vals_b) : P<uint32_t>(ctx->vals_tmp);
@@ -648,6 +648,7 @@ swgs_status swgs_default_config(swgs_config* cfg) {
     cfg->pixels_per_thread = 4;
     cfg->bwd_pixels_per_thread = 8;
     cfg->bwd_batch = 64;
+    cfg->sort_single_pass = 1;
     return SWGS_OK;
 }
 
@@ -660,7 +661,7 @@ swgs_status swgs_create(const swgs_config* cfg, swgs_alloc_fn alloc, swgs_free_f
     if (c.bwd_pixels_per_thread == 0) c.bwd_pixels_per_thread = c.pixels_per_thread;
     if (c.bwd_batch == 0) c.bwd_batch = c.batch;
     if (!valid_tile(c.tile_w, c.tile_h) || !valid_batch(c.batch) || !(c.near_plane > 0.f) ||
-        c.blocks_per_sm < 0 ||
+        c.blocks_per_sm < 0 || (c.sort_single_pass != 0 && c.sort_single_pass != 1) ||
         !blend_config_valid(c.tile_w, c.tile_h, c.batch, c.pixels_per_thread, false) ||
         !blend_config_valid(c.tile_w, c.tile_h, c.bwd_batch, c.bwd_pixels_per_thread, true))
         return SWGS_EINVAL;
@@ -835,7 +836,8 @@ swgs_status swgs_slice_encode(swgs_ctx* ctx, const swgs_gaussians* src, int64_t 
                        P<uint32_t>(ctx->codec_vals_a), P<uint32_t>(ctx->codec_vals_b),
                        P<uint32_t>(ctx->block_cnt), P<uint32_t>(ctx->codec_idx),
                        P<uint8_t>(ctx->codec_flags), ctx->sort_tmp.p, ctx->scan_tmp.p,
-                       P<unsigned long long>(ctx->totals), sort_err_word(ctx, s)};
+                       P<unsigned long long>(ctx->totals), sort_err_word(ctx, s),
+                       ctx->cfg.sort_single_pass != 0};
         uint32_t* sel = nullptr;
         CK(launch_codec_select(src->opacity_logits, count, keep, w, ctx->num_sms, &sel, s));
         idx = sel;

@@ -407,10 +407,12 @@ size_t sort_timeout_scratch_bytes();
 cudaError_t launch_sort_timeout_check(void* scratch, uint32_t* err, cudaStream_t s);
 // err: a device word set to 1 if a look-back wait of the single-pass form ran
 // out (the output is then wrong); null keeps no record.
+// single_pass: one kernel per digit pass (inputs below 2^30 keys); false, or
+// larger inputs: three kernels per pass. The sorted order is the same.
 cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
                              uint32_t* vals_b, long long n, const SortPlan& plan, void* temp,
-                             int num_sms, bool vals_iota, bool* in_b, uint32_t* err,
-                             cudaStream_t s);
+                             int num_sms, bool vals_iota, bool* in_b, bool single_pass,
+                             uint32_t* err, cudaStream_t s);
 
 // k_keys.cu
 // Super tiles: SX x SY tiles (4 x 4, or 2 x 8 for 32x8 tiles); at most 2^16 per
@@ -459,6 +461,7 @@ struct CodecScratch {
     void *sort_tmp, *scan_tmp;
     unsigned long long* total;
     uint32_t* sort_err;  // the sort's look-back error word (may be null)
+    bool sort_single_pass;
 };
 cudaError_t launch_codec_select(const float* logits, long long count, long long keep,
                                 CodecScratch& w, int num_sms, uint32_t** out_idx, cudaStream_t s);

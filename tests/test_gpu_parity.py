@@ -381,3 +381,27 @@ def test_backward_high_opacity_clamp(oracle_mod, ppt):
     d = np.random.default_rng(2).normal(size=(3, 72, 96))
     print(_grads_vs_oracle(r, oracle_mod, sc, [view], [d], bg=(0.1, 0.2, 0.3)))
     r.close()
+
+
+def test_sort_forms_agree():
+    """The single-pass digit passes and the three-kernel passes give the same
+    depth order, per-tile lists and images (bit for bit), over several views."""
+    from paper_2409_07759_b300 import api, _abi
+    sc, views, _ = synth.config2(width=320, height=240, n=60000, n_frames=3, per_frame=2)
+    st = _state(sc)
+    out = {}
+    for single in (True, False):
+        r = api.Renderer(sort_single_pass=single)
+        imgs, saved = r.render(st, views, keep_saved=True)
+        torch.cuda.synchronize()
+        out[single] = ([_np(i) for i in imgs],
+                       saved.export(_abi.EXPORT_SORTED_SLOT), saved.export(_abi.EXPORT_TILE_RANGES),
+                       saved.export(_abi.EXPORT_RECORD_DEPTH), saved.export(_abi.EXPORT_LAST))
+        saved.release()
+        r.close()
+    a, b = out[True], out[False]
+    assert a[1].size > 10000
+    for x, y in zip(a[0], b[0]):
+        np.testing.assert_array_equal(x, y)
+    for x, y in zip(a[1:], b[1:]):
+        np.testing.assert_array_equal(x, y)
