@@ -193,6 +193,10 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
 // colour are staged negated so that w is carried as -w:
 // -w = (-alpha) T, C + c w = C + (-c)(-w) and T - w = T + (-w), all exact
 // rewrites of the same roundings.
+// INT_FLAG: the clamp flag in the last word is the integer 1 (tested as a
+// bit; the reverse blend runs faster so) rather than the float 1 (tested by
+// a float compare; the forward runs faster so).
+template <bool INT_FLAG>
 __device__ __forceinline__ void stage_gaussian_x2(const Records& rec, uint32_t r, float4* sa,
                                                   float4* sb, float4* sc, float4* sd,
                                                   float4* se) {
@@ -208,7 +212,9 @@ __device__ __forceinline__ void stage_gaussian_x2(const Records& rec, uint32_t r
     *sd = make_float4(-Cc.x, -Cc.x, -Cc.y, -Cc.y);
     // alpha = min(0.99, o G) with G <= 1 reaches the clamp only when o > 0.99:
     // the blends skip the clamp's work for the others (a warp-uniform branch)
-    *se = make_float4(-Cc.z, -Cc.z, pair_qmin(lo), A.z > kAlphaMax ? 1.f : 0.f);
+    const bool clamp = A.z > kAlphaMax;
+    *se = make_float4(-Cc.z, -Cc.z, pair_qmin(lo),
+                      INT_FLAG ? __uint_as_float(clamp ? 1u : 0u) : (clamp ? 1.f : 0.f));
 }
 
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
@@ -312,7 +318,8 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
             for (int k = tid; k < BATCH; k += NT) {
                 const int idx = b0 + k;
                 if (idx < rg.y)
-                    stage_gaussian_x2(a.rec, a.vals[idx], &sa[k], &sb[k], &sc[k], &sd[k], &se[k]);
+                    stage_gaussian_x2<false>(a.rec, a.vals[idx], &sa[k], &sb[k], &sc[k], &sd[k],
+                                             &se[k]);
             }
             __syncthreads();
             const int cnt = min(BATCH, rg.y - b0);
@@ -569,7 +576,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
             for (int k = tid; k < cnt; k += NT) {
                 const uint32_t r = a.vals[b0 + k];
                 s_rec[k] = r;
-                stage_gaussian_x2(a.rec, r, &sa[k], &sb[k], &sc[k], &sd[k], &se[k]);
+                stage_gaussian_x2<true>(a.rec, r, &sa[k], &sb[k], &sc[k], &sd[k], &se[k]);
             }
             __syncthreads();
             // kBwdUnroll staged Gaussians per iteration, back to front; the
@@ -589,7 +596,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                 // are applied once below. gm here is alpha dL/dalpha (the
                 // factor -1/2 of dalpha/dm is applied at the flush).
                 float2 S0 = make_float2(0.f, 0.f), SY = S0, SYY = S0, M6 = S0, M7 = S0, M8 = S0;
-                if (ge.w != 0.f)
+                if (__float_as_uint(ge.w) & 1u)
                     bwd_pairs<true, NP>(ga, gb, gc, gd, ge, dx, adx, pos, py, last, T, D, dL0, dL1,
                                         dL2, S0, SY, SYY, M6, M7, M8);
                 else

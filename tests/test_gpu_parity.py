@@ -405,3 +405,50 @@ def test_sort_forms_agree():
         np.testing.assert_array_equal(x, y)
     for x, y in zip(a[1:], b[1:]):
         np.testing.assert_array_equal(x, y)
+
+
+def _edge_scene():
+    """Small, thin, rotated Gaussians spread over a 128x96 view (supports a
+    few pixels across), a sixth of them above the 0.99 clamp."""
+    sc, view = synth.tiny_scene(11, n=3000, sh_degree=1, width=128, height=96, depth=3.0,
+                                log_scale_mean=-3.6, spread=1.0)
+    rng = np.random.default_rng(12)
+    sc.log_scales[:, 0] += rng.uniform(-0.2, 1.6, size=sc.n).astype(np.float32)
+    sc.opacity_logits[rng.random(sc.n) < 1 / 6] = 6.0
+    view.fx = view.fy = 110.0
+    return sc, view
+
+
+@pytest.mark.parametrize("tile,ppts", [((16, 16), (1, 2, 4)), ((32, 8), (1, 2, 4))])
+def test_forward_forms_agree(oracle_mod, tile, ppts):
+    """Every pixels-per-thread form of the forward blend gives the same image,
+    final transmittance and last-contributor index, bit for bit: the packed
+    FP32x2 forms (2 and 4 pixels a thread, negated staging, the clamp branch)
+    against the scalar form (1 pixel a thread), on thin rotated Gaussians and
+    a window-step scene."""
+    from paper_2409_07759_b300 import api, _abi
+    scenes = [_edge_scene()]
+    sc2, views2, _ = synth.config2(width=200, height=150, n=30000, n_frames=2, per_frame=2)
+    scenes.append((sc2, views2))
+    for sc, views in scenes:
+        views = views if isinstance(views, list) else [views]
+        st = _state(sc)
+        out = []
+        for ppt in ppts:
+            r = api.Renderer(tile=tile, batch=64, pixels_per_thread=ppt)
+            imgs, saved = r.render(st, views, bg=(0.2, 0.3, 0.4), keep_saved=True)
+            torch.cuda.synchronize()
+            out.append(([_np(i) for i in imgs], saved.export(_abi.EXPORT_FINAL_T),
+                        saved.export(_abi.EXPORT_LAST)))
+            saved.release()
+            r.close()
+        assert out[0][2].max() > 0
+        for o in out[1:]:
+            for x, y in zip(out[0][0], o[0]):
+                np.testing.assert_array_equal(x, y)
+            np.testing.assert_array_equal(out[0][1], o[1])
+            np.testing.assert_array_equal(out[0][2], o[2])
+    sc, view = scenes[0]
+    r = api.Renderer(tile=tile, pixels_per_thread=4)
+    _render_and_compare(r, oracle_mod, sc, [view], tile=tile)
+    r.close()
