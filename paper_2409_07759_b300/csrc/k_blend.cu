@@ -449,8 +449,10 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // One staged Gaussian against the thread's pixel pairs (the reverse blend's
 // inner step): T recovery, the colour-behind update and the per-pixel sums.
 // CLAMP: the Gaussian's opacity exceeds 0.99, so alpha may take the clamp
-// (where dalpha/dm is then zero).
-template <bool CLAMP, int NP>
+// (where dalpha/dm is then zero). ALL: the Gaussian lies in front of every
+// pixel's last contributor (pos below the warp's smallest last), so no pixel
+// needs the pos < last test.
+template <bool CLAMP, bool ALL, int NP>
 __device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float4 gd, float4 ge,
                                           float2 dx, float2 adx, int pos, const float2 (&py)[NP],
                                           const int (&last)[2 * NP], float2 (&T)[NP],
@@ -467,8 +469,8 @@ __device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float
         const float2 q = __ffma2_rn(t1, dx, t2);
         const float2 v = __fadd2_rn(q, hi2(gc));
         const float u0 = ex2_approx(v.x), u1 = ex2_approx(v.y);
-        const bool ok0 = pos < last[2 * i] && q.x >= ge.z;
-        const bool ok1 = pos < last[2 * i + 1] && q.y >= ge.z;
+        const bool ok0 = (ALL || pos < last[2 * i]) && q.x >= ge.z;
+        const bool ok1 = (ALL || pos < last[2 * i + 1]) && q.y >= ge.z;
         // -alpha of a counted pair, 0 otherwise; -alpha where dalpha/dm is
         // nonzero (the unclamped alpha), 0 otherwise
         float2 na, nag;
@@ -567,6 +569,11 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
             py[i] = make_float2((float)(y0 + 2 * i) + 0.5f, (float)(y0 + 2 * i + 1) + 0.5f);
         }
         if (mylast > 0) atomicMax(&s_maxlast, mylast);
+        // below the warp's smallest last every pixel of the warp takes part
+        int myfirst = last[0];
+#pragma unroll
+        for (int p = 1; p < PPT; ++p) myfirst = min(myfirst, last[p]);
+        const int wfirst = __reduce_min_sync(F, myfirst);
         __syncthreads();
         const int end = rg.x + s_maxlast;
         for (int b1 = end; b1 > rg.x; b1 -= BATCH) {
@@ -597,11 +604,14 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                 // factor -1/2 of dalpha/dm is applied at the flush).
                 float2 S0 = make_float2(0.f, 0.f), SY = S0, SYY = S0, M6 = S0, M7 = S0, M8 = S0;
                 if (__float_as_uint(ge.w) & 1u)
-                    bwd_pairs<true, NP>(ga, gb, gc, gd, ge, dx, adx, pos, py, last, T, D, dL0, dL1,
-                                        dL2, S0, SY, SYY, M6, M7, M8);
+                    bwd_pairs<true, false, NP>(ga, gb, gc, gd, ge, dx, adx, pos, py, last, T, D,
+                                               dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
+                else if (pos < wfirst)
+                    bwd_pairs<false, true, NP>(ga, gb, gc, gd, ge, dx, adx, pos, py, last, T, D,
+                                               dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
                 else
-                    bwd_pairs<false, NP>(ga, gb, gc, gd, ge, dx, adx, pos, py, last, T, D, dL0, dL1,
-                                         dL2, S0, SY, SYY, M6, M7, M8);
+                    bwd_pairs<false, false, NP>(ga, gb, gc, gd, ge, dx, adx, pos, py, last, T, D,
+                                                dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
                 float m[9];
                 m[0] = S0.x + S0.y;
                 m[2] = SY.x + SY.y;
