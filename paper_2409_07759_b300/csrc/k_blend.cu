@@ -619,14 +619,13 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                 m[6] = -(M6.x + M6.y);
                 m[7] = -(M7.x + M7.y);
                 m[8] = -(M8.x + M8.y);
-                // a Gaussian no pixel of the warp counted leaves every sum at zero
-                const bool any = m[0] != 0.f || m[6] != 0.f || m[7] != 0.f || m[8] != 0.f;
-                if (__any_sync(F, any)) {
-                    m[1] = m[0] * dx.x;
-                    m[3] = m[1] * dx.x;
-                    m[4] = m[2] * dx.x;
-                    warp_sum9_to_smem(m, &s_acc[j * 9]);
-                }
+                // every staged Gaussian is reduced: nearly all in a tile's list
+                // reach some pixel, so a vote to skip the rest costs more than it
+                // saves (the flush skips the all-zero sums)
+                m[1] = m[0] * dx.x;
+                m[3] = m[1] * dx.x;
+                m[4] = m[2] * dx.x;
+                warp_sum9_to_smem(m, &s_acc[j * 9]);
                 }
             }
             __syncthreads();
