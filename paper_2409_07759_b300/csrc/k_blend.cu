@@ -405,6 +405,9 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
 // shared memory. Steps 1-3 halve the values each lane holds while doubling
 // the lanes summed, so lane 4m ends with value m (m < 8); value 8 takes a
 // plain butterfly.
+// SOLO: the block is this one warp, so nothing else adds to acc and plain
+// read-modify-writes replace the shared-memory atomics.
+template <bool SOLO>
 __device__ __forceinline__ void warp_sum9_to_smem(const float* v, float* acc) {
     const unsigned F = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -429,8 +432,13 @@ __device__ __forceinline__ void warp_sum9_to_smem(const float* v, float* acc) {
     float v8 = v[8];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v8 += __shfl_xor_sync(F, v8, o);
-    if ((lane & 3) == 0 && y != 0.f) atomicAdd(&acc[lane >> 2], y);
-    if (lane == 0 && v8 != 0.f) atomicAdd(&acc[8], v8);
+    if constexpr (SOLO) {
+        if ((lane & 3) == 0) acc[lane >> 2] += y;
+        if (lane == 0) acc[8] += v8;
+    } else {
+        if ((lane & 3) == 0 && y != 0.f) atomicAdd(&acc[lane >> 2], y);
+        if (lane == 0 && v8 != 0.f) atomicAdd(&acc[8], v8);
+    }
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -625,7 +633,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                 m[1] = m[0] * dx.x;
                 m[3] = m[1] * dx.x;
                 m[4] = m[2] * dx.x;
-                warp_sum9_to_smem(m, &s_acc[j * 9]);
+                warp_sum9_to_smem<NT == 32>(m, &s_acc[j * 9]);
                 }
             }
             __syncthreads();
@@ -772,7 +780,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                     m[6] = m6;
                     m[7] = m7;
                     m[8] = m8;
-                    warp_sum9_to_smem(m, &s_acc[j * 9]);
+                    warp_sum9_to_smem<NT == 32>(m, &s_acc[j * 9]);
                 }
                 }
             }
