@@ -405,10 +405,9 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
 // shared memory. Steps 1-3 halve the values each lane holds while doubling
 // the lanes summed, so lane 4m ends with value m (m < 8); value 8 takes a
 // plain butterfly.
-// SOLO: the block is this one warp, so nothing else adds to acc and plain
-// read-modify-writes replace the shared-memory atomics.
-template <bool SOLO>
-__device__ __forceinline__ void warp_sum9_to_smem(const float* v, float* acc) {
+// Steps 1-3 of the transposing butterfly on v[0..8): lane l ends with value
+// l >> 2 summed over the 8 lanes that differ from it in bits 2-4.
+__device__ __forceinline__ float warp_sum8_part(const float* v) {
     const unsigned F = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const bool bA = lane & 16, bB = lane & 8, bC = lane & 4;
@@ -426,7 +425,16 @@ __device__ __forceinline__ void warp_sum9_to_smem(const float* v, float* acc) {
         const float keep = bB ? w[k + 2] : w[k];
         x[k] = keep + __shfl_xor_sync(F, send, 8);
     }
-    float y = (bC ? x[1] : x[0]) + __shfl_xor_sync(F, bC ? x[0] : x[1], 4);
+    return (bC ? x[1] : x[0]) + __shfl_xor_sync(F, bC ? x[0] : x[1], 4);
+}
+
+// SOLO: the block is this one warp, so nothing else adds to acc and plain
+// read-modify-writes replace the shared-memory atomics.
+template <bool SOLO>
+__device__ __forceinline__ void warp_sum9_to_smem(const float* v, float* acc) {
+    const unsigned F = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float y = warp_sum8_part(v);
     y += __shfl_xor_sync(F, y, 2);
     y += __shfl_xor_sync(F, y, 1);
     float v8 = v[8];
@@ -439,6 +447,27 @@ __device__ __forceinline__ void warp_sum9_to_smem(const float* v, float* acc) {
         if ((lane & 3) == 0 && y != 0.f) atomicAdd(&acc[lane >> 2], y);
         if (lane == 0 && v8 != 0.f) atomicAdd(&acc[8], v8);
     }
+}
+
+// The rest of two Gaussians' reductions at once, for a block of one warp:
+// yA, yB from warp_sum8_part, v8A, v8B their ninth values. The last two
+// butterfly steps and the ninth value's sum are transposed across the pair,
+// so one shuffle serves both Gaussians: lanes 4i and 4i + 2 end with value i
+// of A and of B, lanes 0 and 16 with the ninth. accB null: there is no B.
+__device__ __forceinline__ void warp_finish2_solo(float yA, float yB, float v8A, float v8B,
+                                                  float* accA, float* accB) {
+    const unsigned F = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool b1 = lane & 2, b4 = lane & 16;
+    float y = (b1 ? yB : yA) + __shfl_xor_sync(F, b1 ? yA : yB, 2);
+    y += __shfl_xor_sync(F, y, 1);
+    float w = (b4 ? v8B : v8A) + __shfl_xor_sync(F, b4 ? v8A : v8B, 16);
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) w += __shfl_xor_sync(F, w, o);
+    float* acc = b1 ? accB : accA;
+    if ((lane & 1) == 0 && acc) acc[lane >> 2] += y;
+    float* acc8 = b4 ? accB : accA;
+    if ((lane & 15) == 0 && acc8) acc8[8] += w;
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -598,9 +627,15 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
             // group is skipped when it lies beyond every pixel's last
             for (int j2 = cnt - 1; j2 >= 0; j2 -= kBwdUnroll) {
                 if (__all_sync(F, b0 + max(j2 - kBwdUnroll + 1, 0) - rg.x >= mylast)) continue;
+                // one warp a block: the group's two Gaussians finish their warp
+                // reductions together
+                constexpr bool kPair = NT == 32 && kBwdUnroll == 2;
+                float yp[kBwdUnroll], v8p[kBwdUnroll];
 #pragma unroll
                 for (int jj = 0; jj < kBwdUnroll; ++jj) {
                 const int j = j2 - jj;
+                yp[jj] = 0.f;
+                v8p[jj] = 0.f;
                 if (j < 0) break;
                 const int pos = b0 + j - rg.x;
                 const float4 ga = sa[j], gb = sb[j], gc = sc[j], gd = sd[j], ge = se[j];
@@ -633,8 +668,16 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                 m[1] = m[0] * dx.x;
                 m[3] = m[1] * dx.x;
                 m[4] = m[2] * dx.x;
-                warp_sum9_to_smem<NT == 32>(m, &s_acc[j * 9]);
+                if constexpr (kPair) {
+                    yp[jj] = warp_sum8_part(m);
+                    v8p[jj] = m[8];
+                } else {
+                    warp_sum9_to_smem<NT == 32>(m, &s_acc[j * 9]);
                 }
+                }
+                if constexpr (kPair)
+                    warp_finish2_solo(yp[0], yp[1], v8p[0], v8p[1], &s_acc[j2 * 9],
+                                      j2 >= 1 ? &s_acc[(j2 - 1) * 9] : nullptr);
             }
             __syncthreads();
             for (int k = tid; k < cnt; k += NT) {
