@@ -452,3 +452,39 @@ def test_forward_forms_agree(oracle_mod, tile, ppts):
     r = api.Renderer(tile=tile, pixels_per_thread=4)
     _render_and_compare(r, oracle_mod, sc, [view], tile=tile)
     r.close()
+
+
+def test_backward_forms_agree_on_covered_tiles():
+    """Every pixels-per-thread form of the reverse blend gives the same
+    gradients (to 1e-5 of each attribute's largest magnitude: the forms sum
+    in different orders) on a scene where a third of the tiles are fully
+    covered, so that the packed forms run their body for Gaussians in front
+    of every pixel's last contributor. The scalar form (1 pixel a thread) has no such body,
+    no paired warp reductions and reduces with shared-memory atomics."""
+    from paper_2409_07759_b300 import api, _abi
+    sc, views, _ = synth.config2(width=256, height=192, n=60000, n_frames=1, per_frame=2)
+    st = _state(sc)
+    rng = np.random.default_rng(9)
+    dls = [torch.from_numpy(rng.normal(size=(3, v.height, v.width)).astype(np.float32)).cuda()
+           for v in views]
+    grads = {}
+    covered = None
+    for ppt in (1, 2, 4, 8):
+        r = api.Renderer(bwd_pixels_per_thread=ppt, pixels_per_thread=min(ppt, 4))
+        imgs, saved = r.render(st, views, keep_saved=True)
+        if covered is None:
+            last = saved.export(_abi.EXPORT_LAST).reshape(len(views), 192, 256)
+            t = last.reshape(len(views), 12, 16, 16, 16).min(axis=(2, 4))
+            covered = float((t > 0).mean())
+        g = st.zero_grads()
+        r.backward(st, saved, dls, g)
+        torch.cuda.synchronize()
+        grads[ppt] = {k: _np(getattr(g, k)).copy() for k in api.PARAM_NAMES}
+        saved.release()
+        r.close()
+    assert covered > 0.25, covered  # 38% of the tiles: the object fills the middle
+    for ppt in (2, 4, 8):
+        for k in api.PARAM_NAMES:
+            a, b = grads[1][k], grads[ppt][k]
+            scale = max(float(np.abs(a).max()), 1e-30)
+            assert float(np.abs(a - b).max()) <= 1e-5 * scale, (ppt, k)
