@@ -77,12 +77,17 @@ __device__ __forceinline__ int record_row_run(const Records& rec, uint32_t r, sh
 // super tile by the row rule. The sort reads only the low 16 bits (the super
 // tile id), so the mask rides along. Positions of the record's range left over
 // (the projection's count is an upper bound) get the key of its first super
-// tile with an empty mask, which the expansion passes over.
+// tile with an empty mask, which the expansion passes over. The super tile's
+// shape (SX x SY tiles) is a template parameter, so the mask loops run over
+// its SY rows only.
+template <int SX, int SY>
 __global__ void __launch_bounds__(256)
 emit_supers_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
                    long long n_rec, Records rec, const ViewDev* __restrict__ views, int n_views,
-                   int sx, int sy, int tile_w, int tile_h, uint32_t* __restrict__ keys,
+                   int tile_w, int tile_h, uint32_t* __restrict__ keys,
                    uint32_t* __restrict__ vals) {
+    static_assert(SX * SY == 16, "16 tiles per super tile");
+    constexpr int sx = SX, sy = SY;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_rec;
          k += (long long)gridDim.x * blockDim.x) {
         const uint32_t r = order[k];
@@ -94,22 +99,22 @@ emit_supers_kernel(const uint32_t* __restrict__ order, const uint32_t* __restric
         uint32_t o = offsets[k];
         const uint32_t o_end = o + (uint32_t)rec.supers[r];
         for (int y = y0; y <= y1; ++y) {
-            int f[8], n[8];
+            int f[SY], n[SY];
 #pragma unroll
-            for (int ly = 0; ly < 8; ++ly) {
+            for (int ly = 0; ly < SY; ++ly) {
                 f[ly] = 0;
                 n[ly] = 0;
                 const int ty = y * sy + ly;
-                if (ly < sy && ty >= rc.z && ty <= rc.w)
+                if (ty >= rc.z && ty <= rc.w)
                     n[ly] = record_row_run(rec, r, rc, ty, tile_w, tile_h, &f[ly]);
             }
             for (int x = x0; x <= x1; ++x) {
                 const int tx0 = x * sx;
                 unsigned m = 0;
 #pragma unroll
-                for (int ly = 0; ly < 8; ++ly) {
+                for (int ly = 0; ly < SY; ++ly) {
                     const int lo = max(f[ly], tx0), hi = min(f[ly] + n[ly], tx0 + sx);
-                    if (ly < sy && lo < hi) m |= ((1u << (hi - lo)) - 1u) << (lo - tx0 + ly * sx);
+                    if (lo < hi) m |= ((1u << (hi - lo)) - 1u) << (lo - tx0 + ly * sx);
                 }
                 if (m != 0 && o < o_end) {
                     keys[o] = (uint32_t)(V.super_base + y * V.nsx + x) | (m << 16);
@@ -133,8 +138,14 @@ cudaError_t launch_emit_supers(const uint32_t* order, const uint32_t* offsets, l
     long long blocks = div_up(n_rec, 256);
     if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
     note_launch();
-    emit_supers_kernel<<<(int)blocks, 256, 0, s>>>(order, offsets, n_rec, rec, views, n_views,
-                                                   sx, sy, tile_w, tile_h, keys, vals);
+    if (sx == 4 && sy == 4)
+        emit_supers_kernel<4, 4><<<(int)blocks, 256, 0, s>>>(order, offsets, n_rec, rec, views,
+                                                             n_views, tile_w, tile_h, keys, vals);
+    else if (sx == 2 && sy == 8)
+        emit_supers_kernel<2, 8><<<(int)blocks, 256, 0, s>>>(order, offsets, n_rec, rec, views,
+                                                             n_views, tile_w, tile_h, keys, vals);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
