@@ -187,7 +187,11 @@ __device__ __forceinline__ int find_group_by_record(const GroupDev* groups, int 
 // group, active Gaussian i): consecutive threads write consecutive records and
 // read consecutive active ids; a Gaussian's parameters are re-read by each view
 // of its frame from L2.
+// The tile shape (TW x TH pixels; super tiles of SX x SY tiles) is a template
+// parameter, so the tile arithmetic of the row runs folds to constants.
+template <int TW, int TH>
 __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_rec) {
+    constexpr int SX = TW == 32 ? 2 : 4, SY = TW == 32 ? 8 : 4;
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rec) return;
     const int gi = find_group_by_record(a.groups, a.n_groups, r);
@@ -263,10 +267,10 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_
             A = kdiv(cc, det);
             B = -kdiv(cb, det);
             C = kdiv(ca, det);
-            const float fxlo = floorf(kdiv(ksub(u, rad), (float)a.tile_w));
-            const float fxhi = floorf(kdiv(kadd(u, rad), (float)a.tile_w));
-            const float fylo = floorf(kdiv(ksub(v, rad), (float)a.tile_h));
-            const float fyhi = floorf(kdiv(kadd(v, rad), (float)a.tile_h));
+            const float fxlo = floorf(kdiv(ksub(u, rad), (float)TW));
+            const float fxhi = floorf(kdiv(kadd(u, rad), (float)TW));
+            const float fylo = floorf(kdiv(ksub(v, rad), (float)TH));
+            const float fyhi = floorf(kdiv(kadd(v, rad), (float)TH));
             const int ntx = V.ntx, nty = V.nty;
             const int x0 = fxlo < 0.0f ? 0 : (fxlo > (float)ntx ? ntx : (int)fxlo);
             const int x1 = fxhi > (float)(ntx - 1) ? ntx - 1 : (fxhi < -1.0f ? -1 : (int)fxhi);
@@ -285,13 +289,13 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_
                 int srow = -1, smin = 0, smax = -1;
                 for (int ty = y0; ty <= y1; ++ty) {
                     int f = 0, l = 0;
-                    const int cnt = km_row_run_fast(el, u, v, x0, x1, ty, a.tile_w, a.tile_h,
+                    const int cnt = km_row_run_fast(el, u, v, x0, x1, ty, TW, TH,
                                                     &f, &l);
                     if (ty - y0 < kRunRows && narrow)
                         runs[ty - y0] = (uint16_t)((cnt ? (f - x0) : 0) | (cnt << 8));
                     tiles += cnt;
                     if (cnt > 0) {
-                        const int sr = ty / a.sy, c0 = f / a.sx, c1 = (f + cnt - 1) / a.sx;
+                        const int sr = ty / SY, c0 = f / SX, c1 = (f + cnt - 1) / SX;
                         if (sr != srow) {
                             if (smax >= smin) supers += smax - smin + 1;
                             srow = sr;
@@ -343,7 +347,15 @@ cudaError_t launch_preprocess(const swgs_gaussians& g, const ViewDev* views, con
     PreArgs a{g, views, groups, n_groups, ids, total_active, tile_w, tile_h, super_w(tile_w),
               super_h(tile_w), near_plane, rec};
     note_launch();
-    preprocess_kernel<<<div_up(n_rec, 256), 256, 0, s>>>(a, n_rec);
+    const int blocks = div_up(n_rec, 256);
+    if (tile_w == 16 && tile_h == 16)
+        preprocess_kernel<16, 16><<<blocks, 256, 0, s>>>(a, n_rec);
+    else if (tile_w == 8 && tile_h == 8)
+        preprocess_kernel<8, 8><<<blocks, 256, 0, s>>>(a, n_rec);
+    else if (tile_w == 32 && tile_h == 8)
+        preprocess_kernel<32, 8><<<blocks, 256, 0, s>>>(a, n_rec);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
