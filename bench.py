@@ -343,6 +343,7 @@ def serving_leg(args):
     loop = serving.ServingLoop(st, swin, fps=30.0, n_streams=args.serve_streams, max_batch=16,
                                hbm_budget_bytes=args.hbm_budget_gb * 1e9,
                                slice_provider=provider)
+    loop.reserve(1920, 1080)
     warm = serving.make_requests(args.viewers, args.rate, 1.0, seed=40)
     loop.run(warm, 1.0)
     reqs = serving.make_requests(args.viewers, args.rate, args.serve_seconds, seed=41)

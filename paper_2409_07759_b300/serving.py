@@ -16,6 +16,7 @@ Everything here is host-side scheduling; all GPU work is libswgs calls.
 """
 from __future__ import annotations
 
+import gc
 import math
 import threading
 import time
@@ -129,10 +130,36 @@ class ServingLoop:
         # last index, sort keys), refined from the key counts observed
         self.bytes_per_px = 12 + 8 + 16 * 8.0
         self.rec_bytes = 96.0 * state.n
+        self.out_pool: List[List[torch.Tensor]] = []   # filled by reserve()
+        self.pool_px = 0
 
     # -- memory model for admission ---------------------------------------------
     def request_bytes(self, r: Request) -> float:
         return self.bytes_per_px * r.width * r.height + self.rec_bytes
+
+    def reserve(self, width: int, height: int):
+        """Grow every worker's scratch to the largest batch the admission rule
+        lets through at width x height (max_batch requests within the HBM
+        budget), so that no device allocation happens while serving: a batch
+        larger than any seen before would otherwise grow the scratch mid-run
+        and stall every request queued behind it."""
+        R, t = orbit_pose(np.array([0.0, 0.0, 1.0]), 0.0, 0.0, 0.0)
+        probe = Request(rid=-1, viewer=-1, arrival=0.0, width=width, height=height, R=R, t=t)
+        n, used = 0, 0.0
+        while n < self.max_batch and (n == 0 or used + self.request_bytes(probe) <= self.budget):
+            used += self.request_bytes(probe)
+            n += 1
+        fx, fy, cx, cy = synth.intrinsics_for(width, height)
+        views = [synth.View(width, height, fx, fy, cx, cy, probe.R, probe.t, self.frame)] * n
+        self.out_pool = []
+        self.pool_px = width * height
+        for w, s in enumerate(self.streams):
+            with torch.cuda.stream(s):
+                # the worker's output images: max_batch planar buffers of this size
+                self.out_pool.append([torch.empty(3 * self.pool_px, dtype=torch.float32,
+                                                  device="cuda") for _ in range(self.max_batch)])
+                self.renderers[w].render(self.state, views, stream=s)
+            s.synchronize()
 
     # -- Alg. 2 update_thread ---------------------------------------------------
     def apply_update(self, frame: int):
@@ -156,9 +183,16 @@ class ServingLoop:
     def render_batch(self, w: int, reqs: List[Request], t0: float):
         """Render `reqs` together on worker stream w at the current frame."""
         s = self.streams[w]
-        with torch.cuda.stream(s):
-            outs = [torch.empty((3, r.height, r.width), dtype=torch.float32, device="cuda")
-                    for r in reqs]
+        pool = self.out_pool[w] if self.out_pool else None
+        if pool is not None and len(reqs) <= len(pool) and \
+                all(r.width * r.height <= self.pool_px for r in reqs):
+            # views of the worker's reserved buffers: no allocation while serving
+            outs = [pool[i][:3 * r.width * r.height].view(3, r.height, r.width)
+                    for i, r in enumerate(reqs)]
+        else:
+            with torch.cuda.stream(s):
+                outs = [torch.empty((3, r.height, r.width), dtype=torch.float32, device="cuda")
+                        for r in reqs]
         with self.submit_lock:
             frame = self.frame
             views = []
@@ -189,7 +223,20 @@ class ServingLoop:
 
     def run(self, requests: List[Request], duration_s: float, keep_images=False):
         """Serve `requests` (arrival times relative to the start) in real time
-        for duration_s seconds of arrivals, then drain. Returns ServeStats."""
+        for duration_s seconds of arrivals, then drain. Returns ServeStats.
+        Python's cyclic garbage collector is held off while serving (a full
+        collection of a large heap pauses every thread for tens of ms) and
+        restored afterwards."""
+        gc_on = gc.isenabled()
+        gc.collect()
+        gc.disable()
+        try:
+            return self._run(requests, duration_s, keep_images)
+        finally:
+            if gc_on:
+                gc.enable()
+
+    def _run(self, requests: List[Request], duration_s: float, keep_images=False):
         pending = deque()
         todo = deque(requests)
         lock = threading.Lock()
@@ -219,7 +266,7 @@ class ServingLoop:
                 outs = self.render_batch(w, batch, t0)
                 if keep_images:
                     for r, o in zip(batch, outs):
-                        images[r.rid] = o
+                        images[r.rid] = o.clone() if self.out_pool else o
                 with cond:
                     batches.append(len(batch))
                     free[w] = True

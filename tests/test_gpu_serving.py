@@ -90,3 +90,26 @@ def test_budget_limits_batches():
     stats = loop.run(reqs, 0.5)
     assert stats.n == len(reqs) and stats.mean_batch == 1.0
     loop.close()
+
+
+def test_reserved_buffers_give_the_same_images():
+    """After reserve(), a worker renders into its reserved output buffers (no
+    allocation while serving); the images equal the allocating path's, and a
+    run that keeps its images gets copies, not the reused buffers."""
+    from paper_2409_07759_b300 import serving
+    _, st, _, loop = _loop()
+    reqs = serving.make_requests(6, 5.0, 2.0, seed=1, resolutions=RES)[:5]
+    before = [o.clone() for o in loop.render_batch(1, reqs, 0.0)]
+    loop.reserve(640, 360)
+    after = loop.render_batch(1, reqs, 0.0)
+    pool_ptrs = {t.data_ptr() for t in loop.out_pool[1]}
+    assert all(o.data_ptr() in pool_ptrs for o in after)
+    torch.cuda.synchronize()
+    for a, b in zip(before, after):
+        assert torch.equal(a, b)
+    run = serving.make_requests(8, 30.0, 0.5, seed=5, resolutions=RES)
+    stats, images = loop.run(run, 0.5, keep_images=True)
+    assert stats.n == len(run) == len(images)
+    ptrs = {t.data_ptr() for p in loop.out_pool for t in p}
+    assert all(im.data_ptr() not in ptrs for im in images.values())
+    loop.close()
