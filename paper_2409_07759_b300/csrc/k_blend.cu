@@ -25,7 +25,11 @@
 // over the thread's pixels, sums them across the warp (a transposing butterfly,
 // 14 shuffles for 9 values) and across the block in shared memory, and turns
 // them into the nine 2D gradients (centre, conic, opacity, colour) once per
-// Gaussian per tile before one vector atomic.
+// Gaussian per tile before one vector atomic. At 8 pixels per thread a block
+// is one warp: the two Gaussians of an iteration share their butterflies' last
+// steps and the sums go to shared memory by plain adds. Besides the clamp
+// split, a Gaussian in front of every pixel's last contributor (below the
+// warp's smallest last) takes a body without the per-pixel last test.
 #include "swgs_internal.cuh"
 
 namespace swgs {
