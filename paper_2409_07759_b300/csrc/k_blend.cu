@@ -628,9 +628,12 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
             }
             __syncthreads();
             // kBwdUnroll staged Gaussians per iteration, back to front; the
-            // group is skipped when it lies beyond every pixel's last
+            // group is skipped when it lies beyond every pixel of the warp's last
+            // (never, in a block of one warp: the walk starts at its largest last)
             for (int j2 = cnt - 1; j2 >= 0; j2 -= kBwdUnroll) {
-                if (__all_sync(F, b0 + max(j2 - kBwdUnroll + 1, 0) - rg.x >= mylast)) continue;
+                if (NT > 32 &&
+                    __all_sync(F, b0 + max(j2 - kBwdUnroll + 1, 0) - rg.x >= mylast))
+                    continue;
                 // one warp a block: the group's two Gaussians finish their warp
                 // reductions together
                 constexpr bool kPair = NT == 32 && kBwdUnroll == 2;
