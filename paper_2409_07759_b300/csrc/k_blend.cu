@@ -480,6 +480,13 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// A block of one warp synchronises its lanes alone (shared-memory ordering
+// included); larger blocks take the block barrier.
+template <int NT>
+__device__ __forceinline__ void block_sync() {
+    if constexpr (NT == 32) __syncwarp(); else __syncthreads();
+}
+
 // Reverse blend with the pixels of a thread taken two at a time as float2 (the
 // packed FP32x2 instructions of the forward). It uses the forward's packed
 // staging (centre and colour negated) and carries -alpha, so every sign
@@ -566,7 +573,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
     for (int k = tid; k < BATCH * 9; k += NT) s_acc[k] = 0.f;
     for (;;) {
         if (tid == 0) { s_item = atomicAdd(a.work_counter, 1); s_maxlast = 0; }
-        __syncthreads();
+        block_sync<NT>();
         const int item = s_item;
         if (item >= a.total_tiles) break;
         const int vi = find_view_by_tile(a.views, a.n_views, item);
@@ -609,24 +616,24 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
             D[i] = make_float2(Dv[2 * i], Dv[2 * i + 1]);
             py[i] = make_float2((float)(y0 + 2 * i) + 0.5f, (float)(y0 + 2 * i + 1) + 0.5f);
         }
-        if (mylast > 0) atomicMax(&s_maxlast, mylast);
+        if (NT > 32 && mylast > 0) atomicMax(&s_maxlast, mylast);
         // below the warp's smallest last every pixel of the warp takes part
         int myfirst = last[0];
 #pragma unroll
         for (int p = 1; p < PPT; ++p) myfirst = min(myfirst, last[p]);
         const int wfirst = __reduce_min_sync(F, myfirst);
-        __syncthreads();
-        const int end = rg.x + s_maxlast;
+        block_sync<NT>();
+        const int end = rg.x + (NT == 32 ? __reduce_max_sync(F, mylast) : s_maxlast);
         for (int b1 = end; b1 > rg.x; b1 -= BATCH) {
             const int b0 = max(rg.x, b1 - BATCH);
             const int cnt = b1 - b0;
-            __syncthreads();
+            block_sync<NT>();
             for (int k = tid; k < cnt; k += NT) {
                 const uint32_t r = a.vals[b0 + k];
                 s_rec[k] = r;
                 stage_gaussian_x2<true>(a.rec, r, &sa[k], &sb[k], &sc[k], &sd[k], &se[k]);
             }
-            __syncthreads();
+            block_sync<NT>();
             // kBwdUnroll staged Gaussians per iteration, back to front; the
             // group is skipped when it lies beyond every pixel of the warp's last
             // (never, in a block of one warp: the walk starts at its largest last)
@@ -686,7 +693,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                     warp_finish2_solo(yp[0], yp[1], v8p[0], v8p[1], &s_acc[j2 * 9],
                                       j2 >= 1 ? &s_acc[(j2 - 1) * 9] : nullptr);
             }
-            __syncthreads();
+            block_sync<NT>();
             for (int k = tid; k < cnt; k += NT) {
                 float* acc = &s_acc[k * 9];
                 bool nz = false;
@@ -712,7 +719,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                 for (int e = 0; e < 9; ++e) acc[e] = 0.f;
             }
         }
-        __syncthreads();
+        block_sync<NT>();
     }
 }
 
