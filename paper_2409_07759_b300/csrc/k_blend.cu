@@ -41,7 +41,7 @@ __device__ __forceinline__ void stage_gaussian(const Records& rec, uint32_t r, f
     const float4 Cc = rec.c[r];
     *s0 = make_float4(A.x, A.y, __fmul_rn(B.x, -0.5f * kLog2e), __fmul_rn(B.y, -kLog2e));
     const float lo = __log2f(A.z);
-    *s1 = make_float4(__fmul_rn(B.z, -0.5f * kLog2e), lo, pair_qmin(lo), 0.f);
+    *s1 = make_float4(__fmul_rn(B.z, -0.5f * kLog2e), lo, pair_vmin(lo), 0.f);
     *s2 = Cc;
 }
 
@@ -54,7 +54,7 @@ struct TileGeom {
 
 constexpr int kFwdUnroll = 8;
 // row coordinate of a finished pixel in the packed forward: (kGone - y)^2
-// overflows, so q = -inf for every Gaussian (no NaN: |t1 dx| stays finite)
+// overflows, so v = -inf for every Gaussian (no NaN: |t1 dx| stays finite)
 constexpr float kGone = 3.0e30f;
 constexpr int kBwdUnroll = 2;
 
@@ -116,9 +116,9 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     float dx, dy, au;
-                    const float q = pair_q(px, py[p], g0, g1.x, &dx, &dy);
-                    const float al = pair_alpha(q, g1.y, &au);
-                    const bool ok = !done[p] && q >= g1.z;
+                    const float v = pair_v(px, py[p], g0, g1.x, g1.y, &dx, &dy);
+                    const float al = pair_alpha(v, &au);
+                    const bool ok = !done[p] && v >= g1.z;
                     // T (1 - alpha), rounded once: the stopping test
                     const float tT = __fmaf_rn(-al, T[p], T[p]);
                     const bool inc = ok && tT >= kTStop;
@@ -217,7 +217,7 @@ __device__ __forceinline__ void stage_gaussian_x2(const Records& rec, uint32_t r
     // alpha = min(0.99, o G) with G <= 1 reaches the clamp only when o > 0.99:
     // the blends skip the clamp's work for the others (a warp-uniform branch)
     const bool clamp = A.z > kAlphaMax;
-    *se = make_float4(-Cc.z, -Cc.z, pair_qmin(lo),
+    *se = make_float4(-Cc.z, -Cc.z, pair_vmin(lo),
                       INT_FLAG ? __uint_as_float(clamp ? 1u : 0u) : (clamp ? 1.f : 0.f));
 }
 
@@ -238,16 +238,15 @@ __device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float
     for (int i = 0; i < NP; ++i) {
         const float2 dy = __fadd2_rn(py[i], hi2(ga));
         const float2 t1 = __ffma2_rn(hi2(gb), dy, adx);
-        const float2 t2 = __fmul2_rn(__fmul2_rn(lo2(gc), dy), dy);
-        const float2 q = __ffma2_rn(t1, dx, t2);
-        const float2 v = __fadd2_rn(q, hi2(gc));
+        const float2 t2 = __ffma2_rn(__fmul2_rn(lo2(gc), dy), dy, hi2(gc));
+        const float2 v = __ffma2_rn(t1, dx, t2);
         // -alpha = -min(0.99, 2^v)
         float2 nal = make_float2(-ex2_approx(v.x), -ex2_approx(v.y));
         if (CLAMP) {
             nal.x = fmaxf(-kAlphaMax, nal.x);
             nal.y = fmaxf(-kAlphaMax, nal.y);
         }
-        const bool ok0 = q.x >= ge.z, ok1 = q.y >= ge.z;
+        const bool ok0 = v.x >= ge.z, ok1 = v.y >= ge.z;
         // T (1 - alpha), rounded once: the stopping test
         const float2 tT = __ffma2_rn(nal, T[i], T[i]);
         const bool inc0 = ok0 && tT.x >= kTStop, inc1 = ok1 && tT.y >= kTStop;
@@ -299,8 +298,8 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
         float2 T[NP], C0[NP], C1[NP], C2[NP], py[NP];
         int last[PPT], stop[PPT];
         // a pixel that has stopped (or lies outside the image) moves its row
-        // coordinate to kGone: q is then -inf, so no later pair passes the
-        // q >= qmin test and no per-pixel flag is carried through the loop
+        // coordinate to kGone: v is then -inf, so no later pair passes the
+        // v >= vmin test and no per-pixel flag is carried through the loop
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
             T[i] = make_float2(1.f, 1.f);
@@ -513,12 +512,11 @@ __device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float
     for (int i = 0; i < NP; ++i) {
         const float2 dy = __fadd2_rn(py[i], hi2(ga));
         const float2 t1 = __ffma2_rn(hi2(gb), dy, adx);
-        const float2 t2 = __fmul2_rn(__fmul2_rn(lo2(gc), dy), dy);
-        const float2 q = __ffma2_rn(t1, dx, t2);
-        const float2 v = __fadd2_rn(q, hi2(gc));
+        const float2 t2 = __ffma2_rn(__fmul2_rn(lo2(gc), dy), dy, hi2(gc));
+        const float2 v = __ffma2_rn(t1, dx, t2);
         const float u0 = ex2_approx(v.x), u1 = ex2_approx(v.y);
-        const bool ok0 = (ALL || pos < last[2 * i]) && q.x >= ge.z;
-        const bool ok1 = (ALL || pos < last[2 * i + 1]) && q.y >= ge.z;
+        const bool ok0 = (ALL || pos < last[2 * i]) && v.x >= ge.z;
+        const bool ok1 = (ALL || pos < last[2 * i + 1]) && v.y >= ge.z;
         // -alpha of a counted pair, 0 otherwise; -alpha where dalpha/dm is
         // nonzero (the unclamped alpha), 0 otherwise
         float2 na, nag;
@@ -802,9 +800,9 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
 #pragma unroll
                 for (int p = 0; p < PPT; ++p) {
                     float dy, au;
-                    const float q = pair_q(px, py[p], g0, g1.x, &dx, &dy);
-                    const float al = pair_alpha(q, g1.y, &au);
-                    const bool ok = pos < last[p] && q >= g1.z;
+                    const float v = pair_v(px, py[p], g0, g1.x, g1.y, &dx, &dy);
+                    const float al = pair_alpha(v, &au);
+                    const bool ok = pos < last[p] && v >= g1.z;
                     const float a1 = ok ? al : 0.f;
                     // T before this Gaussian, recovered from the T after it (a
                     // pair that does not count has a1 = 0 and leaves T as is)

@@ -286,7 +286,8 @@ constexpr float kLogitDead = -0x1.52c582p+2f;
 // forward's decisions).
 //   staged: (u, v, qa, qb) and (qc, lo): qa = -A/2 log2e, qb = -B log2e,
 //   qc = -C/2 log2e, lo = log2(opacity).
-// Returns q (= -m/2 log2e); *au = unclamped o*G, *a = min(0.99, *au).
+// pair_v returns v = q + lo, q = -m/2 log2e, with lo added inside the last
+// FMA of the quadratic form; *au = unclamped o*G = 2^v, *a = min(0.99, *au).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -294,26 +295,26 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
-__device__ __forceinline__ float pair_q(float px, float py, float4 g0, float qc, float* dx,
-                                        float* dy) {
+__device__ __forceinline__ float pair_v(float px, float py, float4 g0, float qc, float lo,
+                                        float* dx, float* dy) {
     float ddx = __fsub_rn(px, g0.x);
     float ddy = __fsub_rn(py, g0.y);
     float t1 = __fmaf_rn(g0.w, ddy, __fmul_rn(g0.z, ddx));
-    float t2 = __fmul_rn(__fmul_rn(qc, ddy), ddy);
+    float t2 = __fmaf_rn(__fmul_rn(qc, ddy), ddy, lo);
     *dx = ddx;
     *dy = ddy;
     return __fmaf_rn(t1, ddx, t2);
 }
 
-// Per-Gaussian lower bound on q for a pair to count: m <= 9 and alpha >= 1/255
-// (alpha = min(0.99, 2^(q + lo)) with lo = log2(o)). Both blends test q
-// against it, so their decisions agree exactly.
-__device__ __forceinline__ float pair_qmin(float lo) {
-    return fmaxf(kQMin, __fsub_rn(kLog2AlphaMin, lo));
+// Per-Gaussian lower bound on v = q + lo for a pair to count: m <= 9 and
+// alpha >= 1/255 (alpha = min(0.99, 2^v) with lo = log2(o)). Both blends test
+// v against it, so their decisions agree exactly.
+__device__ __forceinline__ float pair_vmin(float lo) {
+    return fmaxf(__fadd_rn(kQMin, lo), kLog2AlphaMin);
 }
 
-__device__ __forceinline__ float pair_alpha(float q, float lo, float* au) {
-    float u = ex2_approx(__fadd_rn(q, lo));
+__device__ __forceinline__ float pair_alpha(float v, float* au) {
+    float u = ex2_approx(v);
     *au = u;
     return fminf(kAlphaMax, u);
 }
