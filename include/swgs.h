@@ -141,10 +141,11 @@ swgs_status swgs_active_ids(swgs_ctx *ctx, const int32_t *start, const int32_t *
  *
  * Same arguments and result as swgs_active_ids, but no context: its scratch
  * (about 66 KB) is a fixed array compiled into the library, which every GPU
- * that loads the library holds until the process exits. The first call on
- * each device looks up that array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture. It calls no cudaMalloc,
- * cudaFree or other allocating routine.
+ * that loads the library holds until the process exits. Every call looks up
+ * that array's device address in the current context (cudaGetSymbolAddress,
+ * which allocates nothing), so the first call on a device may load the
+ * library's module there: make a first call before any stream capture. It
+ * calls no cudaMalloc, cudaFree or other allocating routine.
  *   - n must be at most SWGS_NOALLOC_MAX_SLOTS; larger n returns SWGS_EINVAL
  *     and enqueues nothing.
  *   - All calls on a device share the one array: calls whose work overlaps on

@@ -46,11 +46,16 @@ __global__ void codec_keys_kernel(const float* __restrict__ logits, long long n,
     keys[i] = ~asc;
 }
 
-// flags[sorted_slot[j]] = 1 for the first `keep` entries of the ranking.
+// flags[sorted_slot[j]] = 1 for the first `keep` entries of the ranking. A
+// sort whose look-back wait ran out may leave stale words in the ranking:
+// those past the slice are dropped (the error word reports the failure).
 __global__ void codec_flag_kernel(const uint32_t* __restrict__ ranked, long long keep,
-                                  uint8_t* __restrict__ flags) {
+                                  long long count, uint8_t* __restrict__ flags) {
     const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < keep) flags[ranked[j]] = 1;
+    if (j < keep) {
+        const uint32_t r = ranked[j];
+        if ((long long)r < count) flags[r] = 1;
+    }
 }
 
 __global__ void __launch_bounds__(256)
@@ -208,7 +213,7 @@ cudaError_t launch_codec_select(const float* logits, long long count, long long 
     e = cudaMemsetAsync(w.flags, 0, (size_t)count, s);
     if (e != cudaSuccess) return e;
     note_launch();
-    codec_flag_kernel<<<div_up(keep, 256), 256, 0, s>>>(ranked, keep, w.flags);
+    codec_flag_kernel<<<div_up(keep, 256), 256, 0, s>>>(ranked, keep, count, w.flags);
     const long long nb = div_up(count, 256);
     note_launch();
     codec_flag_count_kernel<<<(unsigned)nb, 256, 0, s>>>(w.flags, count, w.block_cnt);

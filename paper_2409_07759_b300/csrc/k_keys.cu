@@ -26,6 +26,9 @@ gather_supers_kernel(const uint32_t* __restrict__ order, Records rec, int sx, in
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const uint32_t r = order[k];
+        // a depth sort whose look-back wait ran out may leave stale words in
+        // order: never index past the records with one (the call then fails)
+        if (r >= (uint32_t)n) { out[k] = 0; continue; }
         out[k] = (uint32_t)rec.supers[r];
         t += (unsigned long long)rec.tiles[r];
     }
@@ -188,7 +191,8 @@ __global__ void __launch_bounds__(kExpandWarps * 32)
 expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict__ skeys,
                     const uint32_t* __restrict__ svals, const ViewDev* __restrict__ views,
                     int n_views, uint32_t* __restrict__ tcount, const uint32_t* __restrict__ toff,
-                    uint32_t* __restrict__ vals, long long cap, int2* __restrict__ ranges) {
+                    uint32_t* __restrict__ vals, long long cap, int2* __restrict__ ranges,
+                    const uint32_t* __restrict__ sort_err) {
     static_assert(SX * SY == 16, "16 tiles per super tile");
     constexpr int NT = kExpandWarps * 32;
     __shared__ __align__(16) uint32_t s_cnt[kExpandWarps][4];
@@ -197,7 +201,10 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
     const int ls = sup - V.super_base;
     const int tx0 = (ls % V.nsx) * SX, ty0 = (ls / V.nsx) * SY;
     const int2 sr = sranges[sup];
-    const int b = sr.x, L = sr.y - sr.x;
+    // a super-key sort whose look-back wait ran out leaves stale keys and
+    // values: every tile then gets an empty list (the call reports the failure)
+    const bool sort_failed = sort_err && *sort_err != 0u;
+    const int b = sr.x, L = sort_failed ? 0 : sr.y - sr.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     // lane t < 16 of every warp tracks tile t of the super tile
@@ -263,31 +270,32 @@ template <bool WRITE>
 static cudaError_t run_expand(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
                               const ViewDev* views, int n_views, int total_supers, int tile_w,
                               uint32_t* tcount, const uint32_t* toff, uint32_t* vals,
-                              long long cap, int2* ranges, cudaStream_t s) {
+                              long long cap, int2* ranges, const uint32_t* sort_err,
+                              cudaStream_t s) {
     if (total_supers <= 0) return cudaSuccess;
     note_launch();
     if (tile_w == 32)
         expand_tiles_kernel<2, 8, WRITE><<<total_supers, kExpandWarps * 32, 0, s>>>(
-            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges);
+            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges, sort_err);
     else
         expand_tiles_kernel<4, 4, WRITE><<<total_supers, kExpandWarps * 32, 0, s>>>(
-            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges);
+            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges, sort_err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
                                 int n_views, int total_supers, int tile_w, uint32_t* tcount,
-                                cudaStream_t s) {
+                                const uint32_t* sort_err, cudaStream_t s) {
     return run_expand<false>(sranges, skeys, nullptr, views, n_views, total_supers, tile_w,
-                             tcount, nullptr, nullptr, 0, nullptr, s);
+                             tcount, nullptr, nullptr, 0, nullptr, sort_err, s);
 }
 
 cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
                                 const ViewDev* views, int n_views, int total_supers, int tile_w,
                                 const uint32_t* toff, uint32_t* vals, long long cap, int2* ranges,
-                                cudaStream_t s) {
+                                const uint32_t* sort_err, cudaStream_t s) {
     return run_expand<true>(sranges, skeys, svals, views, n_views, total_supers, tile_w,
-                            nullptr, toff, vals, cap, ranges, s);
+                            nullptr, toff, vals, cap, ranges, sort_err, s);
 }
 
 // sranges[t] = [first, last+1) of super tile t (the low 16 key bits) in the

@@ -9,8 +9,6 @@
 // swgs_active_ids, but its scratch (per-block counts, scan partials, the frame
 // word) lives in one fixed array compiled into the library, so it needs no
 // context and allocates nothing.
-#include <mutex>
-
 #include "swgs_internal.cuh"
 
 namespace swgs {
@@ -32,25 +30,16 @@ constexpr size_t kScratchBytes = kOffParts + align_up(kPartsBytes);
 // Shared by every call on a device and kept until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the array on the current device, looked up once per
-// device (host code must not pass the array's own name to a kernel).
+// Device address of the array in the current context, looked up on every
+// call: cudaGetSymbolAddress allocates nothing and costs little, and an
+// address cached across calls would go stale after cudaDeviceReset or under
+// another context on the same device. (Host code must not pass the array's
+// own name to a kernel: in host code that name is only a stand-in.)
 cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 

@@ -432,11 +432,11 @@ cudaError_t launch_super_ranges(const uint32_t* keys, long long n, long long n_s
                                 int2* ranges, cudaStream_t s);
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
                                 int n_views, int total_supers, int tile_w, uint32_t* tcount,
-                                cudaStream_t s);
+                                const uint32_t* sort_err, cudaStream_t s);
 cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
                                 const ViewDev* views, int n_views, int total_supers, int tile_w,
                                 const uint32_t* toff, uint32_t* vals, long long cap, int2* ranges,
-                                cudaStream_t s);
+                                const uint32_t* sort_err, cudaStream_t s);
 
 // k_mature.cu (Alg. 1 mature, schedule_expire)
 cudaError_t launch_mature_ids(const int32_t* start, long long n, int st, uint32_t* block_counts,
