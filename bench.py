@@ -33,14 +33,19 @@ from pathlib import Path
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-FP32_LANES_PER_SM = 128          # FP32 lanes per SM (4 partitions x 32)
-# Algorithmic FP32 operations per evaluated (pixel, Gaussian) pair, FMA = 2.
-# Forward (Eq. 3): offset d 2, Mahalanobis form m 9, G = exp(-m/2) 2, o*G 1,
-# T(1 - alpha) 2, colour accumulation c*alpha*T 7.
-# Backward: the forward's alpha 14, T recovery 2, colour weights 4, dL/dalpha 9,
-# colour-behind update 9, dalpha/dm 2, conic/centre/opacity terms 15, sums 9.
-FLOP_PER_PAIR_FWD = 23
-FLOP_PER_PAIR_BWD = 64
+# Algorithmic FP32 operations per evaluated (pixel, Gaussian) pair, the
+# roofline's numerator: the forward pass of Eq. 3 takes about 12 (offset,
+# Mahalanobis form, G, alpha, the transmittance and colour updates) plus one
+# ex2; its adjoint about 40 plus one ex2.
+FLOP_PER_PAIR_FWD = 12
+FLOP_PER_PAIR_BWD = 40
+# The same counted per issued operation of this implementation (an FMA counts
+# 2), reported beside: forward d 2, m 9, G 2, o*G 1, T(1 - alpha) 2, colour
+# 7; backward alpha 14, T recovery 2, colour weights 4, dL/dalpha 9,
+# colour-behind 9, dalpha/dm 2, sums 9 per pair (the conic/centre/opacity
+# chain rule runs once per Gaussian and tile, not per pair).
+OWN_FLOP_PER_PAIR_FWD = 23
+OWN_FLOP_PER_PAIR_BWD = 49
 
 # DRAM bytes (read + write) per launch from one ncu capture of the full-size
 # window step, keyed by stage and launch shape, with a digest of the sources
@@ -410,14 +415,66 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
 
 
+# -------------------------------------------------------------- FP32 peak --
+
+def fp32_peak_leg(reps=10, warmup=3):
+    """Measured FP32-pipe throughput: the library's probe (8 independent FMA
+    chains per thread, 8 blocks of 256 threads per SM) as scalar FFMA and as
+    packed FFMA2, timed with CUDA events on the launching stream, with the SM
+    clock sampled meanwhile. Returns TFLOP/s of each form (an FMA counts 2)."""
+    import ctypes
+    import torch
+    from paper_2409_07759_b300 import _abi
+    lib = _abi.load()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks = sms * 8
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {"blocks": blocks, "threads_per_block": 256, "chains_per_thread": 8}
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    for packed, name in ((0, "ffma"), (1, "ffma2")):
+        iters = 32768
+        fl = ctypes.c_double(0.0)
+        for _ in range(warmup):
+            st = lib.swgs_fp32_peak_launch(packed, blocks, iters, sink.data_ptr(),
+                                           ctypes.byref(fl), ctypes.c_void_p(stream.cuda_stream))
+            if st != 0:
+                raise RuntimeError(f"swgs_fp32_peak_launch failed ({st})")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            lib.swgs_fp32_peak_launch(packed, blocks, iters, sink.data_ptr(), ctypes.byref(fl),
+                                      ctypes.c_void_p(stream.cuda_stream))
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        out[name] = {"tflops": fl.value / (ms / 1e3) / 1e12, "ms_per_launch": ms,
+                     "flop_per_launch": fl.value}
+    clocks = sampler.stop()
+    out["clocks"] = clocks
+    out["tflops"] = max(out["ffma"]["tflops"], out["ffma2"]["tflops"])
+    out["form"] = "ffma2" if out["ffma2"]["tflops"] >= out["ffma"]["tflops"] else "ffma"
+    if clocks.get("sm_mhz"):
+        # FLOP per SM per clock at the sampled median clock
+        for k in ("ffma", "ffma2"):
+            out[k]["flop_per_sm_clk"] = out[k]["tflops"] * 1e12 / (sms * clocks["sm_mhz"] * 1e6)
+    return out
+
+
 # ------------------------------------------------------------- CPU oracle --
 
-def cpu_oracle_sample(scene, views, targets, budget_s=15.0, max_views=None):
+def cpu_oracle_sample(scene, views, targets, budget_s=15.0, max_views=None, threads=None):
     """Time the FP64 oracle (tiled fwd + bwd of whole views) on the host cores
-    until about budget_s of work; returns (mpix_per_s, cores, sample text)."""
+    (or on `threads` threads) until about budget_s of work; returns
+    (mpix_per_s, cores, sample text)."""
     import numpy as np
     import oracle
     oracle.build()
+    all_cores = oracle.num_threads()
+    if threads:
+        oracle.set_threads(threads)
     cores = oracle.num_threads()
     t0 = time.perf_counter()
     pix = 0
@@ -431,6 +488,8 @@ def cpu_oracle_sample(scene, views, targets, budget_s=15.0, max_views=None):
         if time.perf_counter() - t0 > budget_s or (max_views and n >= max_views):
             break
     dt = time.perf_counter() - t0
+    if threads:
+        oracle.set_threads(all_cores)
     return pix / dt / 1e6, cores, f"{n} of {len(views)} views, fwd+bwd (tiled FP64 oracle), {dt:.1f} s"
 
 
@@ -514,6 +573,8 @@ def main():
         if (ROOT / "MEASURED_PEAKS.json").exists() else {}
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    # the FP32 pipe's measured throughput (the blends' roofline denominator)
+    fp32 = fp32_peak_leg()
 
     # weak scaling: every rank holds a replica of the scene and renders its own
     # 4 cameras per frame of the window (rank 0: the single-GPU workload)
@@ -671,9 +732,7 @@ def main():
 
     # ---- roofline of the dominant kernel ----
     steps = args.steps
-    sm_count = torch.cuda.get_device_properties(0).multi_processor_count
-    clk = (clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0))
-    alu_peak = sm_count * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    alu_peak = fp32["tflops"]
     # the list sort orders (super tile, record) keys: ceil(bits / 9) digit passes
     sort_passes = math.ceil(math.ceil(math.log2(max(2, n_supers))) / 9)
     stage_cost = {
@@ -714,11 +773,20 @@ def main():
         roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"],
                 "peak": alu_peak if d["bound"] == "alu" else hbm_peak, "unit": d["unit"],
                 "frac": d["frac"], "traffic": traffic,
-                "peak_source": ("FP32 lanes x 2 x max SM clock" if d["bound"] == "alu"
-                                else f"{hbm_src} copy bandwidth")}
+                "peak_source": (f"measured: FP32 probe ({fp32['form']}, "
+                                f"{fp32['blocks']} blocks x 256 threads, CUDA events)"
+                                if d["bound"] == "alu" else f"{hbm_src} copy bandwidth")}
+        if d["bound"] == "alu":
+            own = OWN_FLOP_PER_PAIR_BWD if dom == "blend_bwd" else OWN_FLOP_PER_PAIR_FWD
+            roof["flop_per_pair"] = (FLOP_PER_PAIR_BWD if dom == "blend_bwd"
+                                     else FLOP_PER_PAIR_FWD)
+            roof["own_count"] = {"flop_per_pair": own, "achieved": d["achieved"] * own /
+                                 roof["flop_per_pair"],
+                                 "frac": d["frac"] * own / roof["flop_per_pair"]}
     else:
         roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None,
                 "frac": None, "traffic": None}
+    extra["fp32_peak"] = fp32
 
     if not args.no_serving:
         torch.cuda.synchronize()
@@ -739,6 +807,11 @@ def main():
         rate, cores, sample = cpu_oracle_sample(scene, views, oracle_targets, budget_s=15.0)
         cpu = {"value": rate, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
                "sample": sample}
+        # the plain single-threaded oracle on one view of the same workload
+        rate1, cores1, sample1 = cpu_oracle_sample(scene, views, oracle_targets, budget_s=1.0,
+                                                   max_views=1, threads=1)
+        cpu["single_thread"] = {"value": rate1, "unit": "Mpix/s", "cores": cores1,
+                                "sample": sample1}
 
     if rank == 0:
         line = {

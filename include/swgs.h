@@ -469,6 +469,17 @@ int64_t swgs_kernel_launches(void);
  * The context stays usable. */
 swgs_status swgs_selftest_sort_timeout(swgs_ctx *ctx, void *stream);
 
+/* FP32-pipe throughput probe (no paper counterpart): the measured peak that
+ * the blends' roofline is taken against. Launches `blocks` blocks of 256
+ * threads on `stream`; every thread runs 8 independent multiply-add chains
+ * for `iters` iterations, as scalar FP32 FMAs (packed = 0) or packed FP32x2
+ * FMAs (packed = 1, two FMAs per instruction), and writes its chains' sum to
+ * sink[thread] (device float[blocks * 256], caller-owned). *flops receives the
+ * launch's floating-point operations (an FMA counts 2). The caller times the
+ * launch with events on `stream`. SWGS_EINVAL for bad arguments. */
+swgs_status swgs_fp32_peak_launch(int32_t packed, int32_t blocks, int32_t iters, float *sink,
+                                  double *flops, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

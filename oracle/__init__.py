@@ -158,6 +158,8 @@ def lib():
         _lib.or_sgld_step.argtypes = [P(OrState), P(OrFGrads), P(OrAdam), C.c_void_p, C.c_int32,
                                       P(OrSgldParams), C.c_uint64, C.c_uint64, C.c_void_p]
         _lib.or_opacity_u8.argtypes = [C.c_void_p, C.c_int64, C.c_void_p]
+        _lib.or_set_threads.argtypes = [C.c_int]
+        _lib.or_set_threads.restype = None
         _lib.or_num_threads.restype = C.c_int
         _lib.or_record_tiles.restype = C.c_int32
         _lib.or_record_tiles.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
@@ -214,6 +216,11 @@ def _bands(b):
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Number of host threads the oracle's parallel loops use from now on."""
+    lib().or_set_threads(int(n))
 
 
 def active_ids(start, expire, frame: int) -> np.ndarray:

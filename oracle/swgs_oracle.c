@@ -1417,6 +1417,17 @@ int or_num_threads(void)
 #endif
 }
 
+/* Threads of the parallel loops from now on (n >= 1); used to time the
+ * oracle single-threaded beside its all-core run. */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 
 /*
  * Table 6 opacity code (uint8): k = rint(255 sigmoid(logit)), the sigmoid
