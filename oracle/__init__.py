@@ -134,6 +134,11 @@ def lib():
         _lib.or_render_pixels.argtypes = [P(OrScene), P(OrView), C.c_void_p, C.c_float,
                                           C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib.or_render_variants.restype = C.c_int
+        _lib.or_render_variants.argtypes = [P(OrScene), P(OrView), C.c_void_p, C.c_int32,
+                                            C.c_int32, C.c_float, C.c_void_p, C.c_int64,
+                                            C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p,
+                                            C.c_void_p, C.c_void_p]
         _lib.or_view_lists.restype = C.c_int64
         _lib.or_view_lists.argtypes = [P(OrScene), P(OrView), C.c_int32, C.c_int32, C.c_float,
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -297,6 +302,36 @@ def render(scene, view, bg=(0.0, 0.0, 0.0), tile_w=16, tile_h=16, near=0.2, mode
     if rc != 0:
         raise MemoryError("oracle render failed")
     return dict(rgb=rgb, T=T, last_slot=last_slot, last_pos=last_pos, flags=flags)
+
+
+def render_variants(scene, view, px, py, bands, bg=(0.0, 0.0, 0.0), tile_w=16, tile_h=16,
+                    near=0.2, max_per=256):
+    """Every valid (rgb, T, last) of selected pixels (tiled walk) when the
+    per-pair tests of Eq. 3 may be decided either way at pairs whose FP64 test
+    value lies within `bands` of its threshold. Returns a list, per pixel, of
+    (rgb[v,3], T[v], last[v]) arrays, or None for a pixel with more than
+    max_per results."""
+    ref = _SceneRef(scene)
+    vw = make_view(view)
+    px = _c(px, np.int32)
+    py = _c(py, np.int32)
+    n = px.shape[0]
+    bgv = np.asarray(bg, np.float64)
+    out = np.zeros((max(1, n), max_per, 4), np.float64)
+    last = np.zeros((max(1, n), max_per), np.int32)
+    cnt = np.zeros(max(1, n), np.int32)
+    b = _bands(bands)
+    rc = lib().or_render_variants(C.byref(ref.s), C.byref(vw), _p(bgv), tile_w, tile_h, near,
+                                  C.byref(b), n, _p(px), _p(py), max_per, _p(out), _p(last),
+                                  _p(cnt))
+    if rc != 0:
+        raise MemoryError("oracle variants failed")
+    res = []
+    for k in range(n):
+        c = int(cnt[k])
+        res.append(None if c < 0 else (out[k, :c, :3].copy(), out[k, :c, 3].copy(),
+                                       last[k, :c].copy()))
+    return res
 
 
 def render_pixels(scene, view, px, py, bg=(0.0, 0.0, 0.0), near=0.2, bands=None):

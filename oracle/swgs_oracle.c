@@ -149,7 +149,7 @@ static int km_row_extent(const km_ell *e, float ya, float yb, float *left, float
 
 /* The run [*first, *last] of kept tiles of row ty inside [tx0, tx1]
  * (returns its length, 0 if none). A tile is kept when its pixel-centre
- * x-span [xa, xb] meets [left, right]. If det_c <= 0 (degenerate conic) the
+ * x-span [xa, xb] meets [left, right]: xb >= left and xa <= right. If det_c <= 0 (degenerate conic) the
  * whole row of the rectangle is kept. */
 static int km_row_run(const km_ell *e, float u, float v, int tx0, int tx1, int ty, int tile_w,
                       int tile_h, int *first, int *last)
@@ -172,6 +172,12 @@ static int km_row_run(const km_ell *e, float u, float v, int tx0, int tx1, int t
         float xa = ((float)(b * tile_w) + 0.5f) - u;
         if (xa <= right) break;
         --b;
+    }
+    /* [left, right] may fall short of tile a's span (left of its first pixel
+     * centre, or in the gap between two tiles' pixel centres): no tile then */
+    {
+        float xa = ((float)(a * tile_w) + 0.5f) - u;
+        if (!(xa <= right)) return 0;
     }
     *first = a;
     *last = b;
@@ -828,6 +834,115 @@ int or_render(const or_scene *sc, const or_view *vw, const double bg[3], int32_t
                     if (flags) flags[pix] = fl;
                 }
         }
+    }
+    vset_free(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Every valid result of one pixel when the per-pair tests of Eq. 3 are      */
+/* decided in a lower precision.                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Near a threshold, an FP32 renderer can take the other side of a test that
+ * FP64 decides one way: m <= 9 (the 3-sigma support), alpha >= 1/255, and the
+ * stop rule T (1 - alpha) < 1e-4. Both outcomes are then valid renders of the
+ * same rule. The walk below is the one of blend_pixel, but at every pair whose
+ * FP64 test value lies within the band of its threshold it follows both
+ * outcomes (depth first), each with its own running T, so later tests are
+ * judged on that branch's own values. Every leaf is one valid (rgb, T, last).
+ * The 0.99 clamp is continuous in value and is not branched. */
+typedef struct {
+    const or_vset *S;
+    const int32_t *list;
+    int64_t len;
+    double px, py;
+    const double *bg;
+    const or_bands *bd;
+    int32_t max_out, n_out, overflow;
+    double *out;      /* [max_out, 4]: rgb, T */
+    int32_t *last;    /* [max_out] */
+} var_walk;
+
+static void var_leaf(var_walk *w, const double C[3], double T, int32_t last)
+{
+    if (w->n_out >= w->max_out) { w->overflow = 1; return; }
+    double *o = w->out + 4 * (int64_t)w->n_out;
+    for (int ch = 0; ch < 3; ++ch) o[ch] = C[ch] + T * w->bg[ch];
+    o[3] = T;
+    w->last[w->n_out] = last;
+    w->n_out += 1;
+}
+
+static void var_step(var_walk *w, int64_t j, double T, const double Cin[3], int32_t last)
+{
+    double C[3] = {Cin[0], Cin[1], Cin[2]};
+    for (; j < w->len; ++j) {
+        if (w->overflow) return;
+        const or_proj *P = &w->S->pj[w->list[j]];
+        double dx = w->px - P->u, dy = w->py - P->v;
+        double m = P->A * dx * dx + 2.0 * P->B * dx * dy + P->C * dy * dy;
+        int pass = m <= OR_MAHAL_MAX;
+        if (fabs(m - OR_MAHAL_MAX) <= w->bd->m * OR_MAHAL_MAX) {
+            /* both outcomes of the support test: skipped (recursion), inside (below) */
+            var_step(w, j + 1, T, C, last);
+            pass = 1;
+        }
+        if (!pass) continue;
+        double aU = P->o * exp(-0.5 * m);
+        double alpha = aU > OR_ALPHA_MAX ? OR_ALPHA_MAX : aU;
+        int big = alpha >= OR_ALPHA_MIN;
+        if (fabs(alpha - OR_ALPHA_MIN) <= w->bd->alpha * OR_ALPHA_MIN) {
+            /* both outcomes of the alpha test */
+            var_step(w, j + 1, T, C, last);
+            big = 1;
+        }
+        if (!big) continue;
+        double tT = T * (1.0 - alpha);
+        int stop = tT < OR_T_STOP;
+        if (fabs(tT - OR_T_STOP) <= w->bd->t_stop * OR_T_STOP) {
+            /* both: stop here, and include it and go on */
+            var_leaf(w, C, T, last);
+            stop = 0;
+        }
+        if (stop) { var_leaf(w, C, T, last); return; }
+        for (int ch = 0; ch < 3; ++ch) C[ch] += P->rgb[ch] * alpha * T;
+        T = tT;
+        last = (int32_t)(j + 1);
+    }
+    var_leaf(w, C, T, last);
+}
+
+/* For n pixels (px, py) of one view in tiled mode: up to max_per valid
+ * results each (out[k, i] = rgb[3], T; last[k, i] = 1 + tile-list position of
+ * the last included Gaussian), count[k] = the number written, or -1 when the
+ * pixel has more than max_per. Returns 0 on success. */
+int or_render_variants(const or_scene *sc, const or_view *vw, const double bg[3],
+                       int32_t tile_w, int32_t tile_h, float near_plane, const or_bands *bd,
+                       int64_t n, const int32_t *px, const int32_t *py, int32_t max_per,
+                       double *out, int32_t *last, int32_t *count)
+{
+    or_vset S;
+    if (vset_build(sc, vw, tile_w, tile_h, near_plane, 1, &S)) { vset_free(&S); return -1; }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t tI = (int64_t)(py[k] / tile_h) * S.ntx + px[k] / tile_w;
+        var_walk w;
+        w.S = &S;
+        w.list = S.tile_rec + S.tile_off[tI];
+        w.len = S.tile_off[tI + 1] - S.tile_off[tI];
+        w.px = px[k] + 0.5;
+        w.py = py[k] + 0.5;
+        w.bg = bg;
+        w.bd = bd;
+        w.max_out = max_per;
+        w.n_out = 0;
+        w.overflow = 0;
+        w.out = out + 4 * k * (int64_t)max_per;
+        w.last = last + k * (int64_t)max_per;
+        const double C0[3] = {0.0, 0.0, 0.0};
+        var_step(&w, 0, 1.0, C0, 0);
+        count[k] = w.overflow ? -1 : w.n_out;
     }
     vset_free(&S);
     return 0;

@@ -216,6 +216,9 @@ __device__ __forceinline__ int km_row_run_fast(const KmEllipse& e, float u, floa
     int b = (int)gb;
     while (b < tx1 && xa_of(b + 1) <= right) ++b;
     while (b > a && !(xa_of(b) <= right)) --b;
+    // [left, right] may fall short of tile a's span (left of its first pixel
+    // centre, or in the gap between two tiles' pixel centres): no tile then
+    if (!(xa_of(b) <= right)) return 0;
     *first = a;
     *last = b;
     return b - a + 1;
@@ -243,6 +246,7 @@ __device__ __forceinline__ int km_row_run(const KmEllipse& e, float u, float v, 
         if (xa <= right) break;
         --b;
     }
+    if (!(ksub(kadd((float)(a * tile_w), 0.5f), u) <= right)) return 0;
     *first = a;
     *last = b;
     return b - a + 1;

@@ -47,8 +47,14 @@ def gpu_pixels(saved, view_index, what):
     return arr[pb:pb + v.width * v.height].reshape(v.height, v.width)
 
 
-def compare_image(gpu_rgb, gpu_T, gpu_last, ref, max_flag_frac=0.02):
-    """Assert pixel parity on unflagged pixels; return the error report."""
+def compare_image(gpu_rgb, gpu_T, gpu_last, ref, max_flag_frac=0.02, replay=None):
+    """Pixel parity. Unflagged pixels: rgb and T within 1e-4 of the FP64
+    oracle and last equal. Flagged pixels (an FP64 pair within BANDS of a
+    threshold, where FP32 may decide the test the other way): with `replay` =
+    (scene, view, tile_w, tile_h, bg), the oracle replays each such pixel's
+    walk with both outcomes at every near-threshold pair, and the GPU's rgb, T
+    (within 1e-4) and last (exactly) must equal one of those valid results.
+    Returns the error report."""
     flag = (ref["flags"] & 1) != 0
     ok = ~flag
     err_rgb = np.abs(gpu_rgb.astype(np.float64) - ref["rgb"])
@@ -62,7 +68,43 @@ def compare_image(gpu_rgb, gpu_T, gpu_last, ref, max_flag_frac=0.02):
     assert rep["max_abs_rgb"] <= PIX_TOL, rep
     assert rep["max_abs_T"] <= PIX_TOL, rep
     assert rep["last_mismatch"] == 0, rep
+    if replay is not None and rep["flagged"]:
+        rep.update(check_flagged(gpu_rgb, gpu_T, gpu_last, flag, ref, *replay))
     return rep
+
+
+def check_flagged(gpu_rgb, gpu_T, gpu_last, flag, ref, scene, view, tile_w, tile_h, bg):
+    """Every flagged pixel's GPU result equals one of the oracle's valid
+    results (decision replay) within 1e-4 (rgb, T) and exactly (last).
+    Also counts the flagged pixels where the GPU took the other side of a
+    near-threshold test than FP64 (its result is not the FP64 walk's)."""
+    import oracle
+    py, px = np.nonzero(flag)
+    res = oracle.render_variants(scene, view, px, py, BANDS, bg=bg, tile_w=tile_w,
+                                 tile_h=tile_h, max_per=4096)
+    unverifiable, mismatched, other_side, worst = 0, [], 0, 0.0
+    for k, r in enumerate(res):
+        if r is None:
+            unverifiable += 1
+            continue
+        rgb, T, last = r
+        y, x = int(py[k]), int(px[k])
+        g_rgb = gpu_rgb[:, y, x].astype(np.float64)
+        g_T = float(gpu_T[y, x])
+        g_last = int(gpu_last[y, x])
+        d = np.maximum(np.abs(rgb - g_rgb[None, :]).max(1), np.abs(T - g_T))
+        d = np.where(last == g_last, d, np.inf)
+        i = int(np.argmin(d))
+        if not d[i] <= PIX_TOL:
+            mismatched.append((x, y, float(d[i])))
+            continue
+        worst = max(worst, float(d[i]))
+        d64 = max(float(np.abs(ref["rgb"][:, y, x] - g_rgb).max()), abs(ref["T"][y, x] - g_T))
+        other_side += int(g_last != ref["last_pos"][y, x] or d64 > PIX_TOL)
+    out = dict(flagged_unverifiable=unverifiable, flagged_mismatched=len(mismatched),
+               flagged_max_abs=worst, flagged_other_side=other_side)
+    assert unverifiable == 0 and not mismatched, (out, mismatched[:10])
+    return out
 
 
 def compare_grads(gpu: dict, ref: dict, tol=GRAD_REL_TOL):

@@ -1,0 +1,95 @@
+"""Parity of the exact call the benchmark times: the sliding-window step of
+300k Gaussians (SH3, 300-frame lifespans, 1% of logits forced to -8), frames
+145-154 x 4 of 20 ring cameras = 40 views of 1352x1014 in one batched call,
+16x16 tiles, staging batch 64, 4 pixels a thread forward and 8 in reverse,
+8-bit targets with the L1 term fused into the forward.
+
+Three sampled views (first, middle, last of the batch) are checked against
+the FP64 oracle: records, tile counts, depth keys and per-tile order bit for
+bit; every pixel (flagged pixels by the oracle's decision replay); and the
+gradients of all attributes when the reverse pass runs over the whole
+40-view batch with a seeded dL on the sampled views and zero on the others
+(so the result is exactly those views' share)."""
+import numpy as np
+import pytest
+
+from paper_2409_07759_b300 import synth
+
+from gpu_helpers import BANDS, compare_grads, compare_image, gpu_lists, gpu_pixels
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SAMPLE = (0, 17, 39)
+
+
+@pytest.fixture(scope="module")
+def bench_call():
+    assert torch.cuda.is_available()
+    from paper_2409_07759_b300 import api
+    sc, views, targets = synth.config2(n_frames=10, per_frame=4, forced_dead_fraction=0.01)
+    assert len(views) == 40 and sc.n == 300_000
+    t8 = [torch.from_numpy(np.rint(t * 255.0).astype(np.uint8)).cuda() for t in targets]
+    st = api.GaussianState.from_scene(sc)
+    r = api.Renderer(tile=(16, 16), batch=64, pixels_per_thread=4, bwd_pixels_per_thread=8,
+                     bwd_batch=64)
+    imgs, dls, loss, saved = r.render_l1(st, views, t8)
+    yield sc, views, st, r, imgs, saved
+    saved.release()
+    r.close()
+
+
+def test_bench_call_records_keys_order(bench_call, oracle_mod):
+    from paper_2409_07759_b300 import _abi
+    sc, views, st, r, imgs, saved = bench_call
+    info = saved.info()
+    assert info.n_batches == 1  # all 40 views in one batched call
+    rslot = saved.export(_abi.EXPORT_RECORD_SLOT)
+    rview = saved.export(_abi.EXPORT_RECORD_VIEW)
+    rtiles = saved.export(_abi.EXPORT_RECORD_TILES)
+    rdepth = saved.export(_abi.EXPORT_RECORD_DEPTH)
+    for vi in SAMPLE:
+        ids, km, nk, off, slots = oracle_mod.view_lists(sc, views[vi], 16, 16)
+        m = rview == vi
+        np.testing.assert_array_equal(rslot[m], ids)
+        np.testing.assert_array_equal(rtiles[m], np.where(km["culled"] == 1, 0, km["tiles"]))
+        live = km["culled"] == 0
+        np.testing.assert_array_equal(rdepth[m][live].view(np.uint32),
+                                      km["z"][live].view(np.uint32))
+        goff, gslots = gpu_lists(saved, vi)
+        np.testing.assert_array_equal(goff, off)
+        np.testing.assert_array_equal(gslots, slots)
+
+
+def test_bench_call_pixels(bench_call, oracle_mod):
+    from paper_2409_07759_b300 import _abi
+    sc, views, st, r, imgs, saved = bench_call
+    for vi in SAMPLE:
+        v = views[vi]
+        ref = oracle_mod.render(sc, v, tile_w=16, tile_h=16, mode="tiled", bands=BANDS)
+        rep = compare_image(imgs[vi].cpu().numpy(), gpu_pixels(saved, vi, _abi.EXPORT_FINAL_T),
+                            gpu_pixels(saved, vi, _abi.EXPORT_LAST), ref,
+                            replay=(sc, v, 16, 16, (0.0, 0.0, 0.0)))
+        print(vi, rep)
+
+
+def test_bench_call_gradients_of_sampled_views(bench_call, oracle_mod):
+    from paper_2409_07759_b300 import api
+    sc, views, st, r, imgs, saved = bench_call
+    rng = np.random.default_rng(20)
+    dls, host = [], {}
+    for vi, v in enumerate(views):
+        if vi in SAMPLE:
+            d = rng.normal(size=(3, v.height, v.width)).astype(np.float32)
+            host[vi] = d
+            dls.append(torch.from_numpy(d).cuda())
+        else:
+            dls.append(torch.zeros((3, v.height, v.width), dtype=torch.float32, device="cuda"))
+    grads = st.zero_grads()
+    r.backward(st, saved, dls, grads)
+    ref = oracle_mod.zero_grads(sc)
+    for vi in SAMPLE:
+        oracle_mod.render_bwd(sc, views[vi], host[vi].astype(np.float64), grads=ref, bands=BANDS)
+    gpu = {k: getattr(grads, k).cpu().numpy() for k in api.PARAM_NAMES}
+    print(compare_grads(gpu, ref))

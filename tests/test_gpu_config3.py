@@ -55,8 +55,10 @@ def test_config3_sampled_views_match_oracle(c3, oracle_mod, tile):
         np.testing.assert_array_equal(goff, off)
         np.testing.assert_array_equal(gslots, slots)
         ref = oracle_mod.render(sc, v, tile_w=tile[0], tile_h=tile[1], mode="tiled", bands=BANDS)
-        compare_image(imgs[vi].cpu().numpy(), gpu_pixels(saved, vi, _abi.EXPORT_FINAL_T),
-                      gpu_pixels(saved, vi, _abi.EXPORT_LAST), ref)
+        rep = compare_image(imgs[vi].cpu().numpy(), gpu_pixels(saved, vi, _abi.EXPORT_FINAL_T),
+                            gpu_pixels(saved, vi, _abi.EXPORT_LAST), ref,
+                            replay=(sc, v, tile[0], tile[1], (0.0, 0.0, 0.0)))
+        print(vi, rep)
     saved.release()
     r.close()
 

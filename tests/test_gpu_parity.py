@@ -123,7 +123,8 @@ def _render_and_compare(R, oracle_mod, sc, views, bg=(0.0, 0.0, 0.0), tile=(16, 
                                 bands=BANDS)
         T = gpu_pixels(saved, vi, _abi.EXPORT_FINAL_T)
         last = gpu_pixels(saved, vi, _abi.EXPORT_LAST)
-        reps.append(compare_image(_np(imgs[vi]), T, last, ref))
+        reps.append(compare_image(_np(imgs[vi]), T, last, ref,
+                                  replay=(sc, v, tile[0], tile[1], bg)))
     saved.release()
     return reps
 

@@ -295,3 +295,78 @@ def test_sorted_lists_are_depth_then_slot(oracle_mod):
         z = km["z"][np.searchsorted(ids, lst)]
         keys = list(zip(z.view(np.uint32).tolist(), lst.tolist()))
         assert keys == sorted(keys)
+
+
+def _rect_min_m(A, B, Cc, lo, hi):
+    """Exact minimum of m(d) = A dx^2 + 2 B dx dy + C dy^2 (positive definite)
+    over the box lo <= d <= hi, in FP64: 0 when the box holds the centre,
+    else the smallest of the four edges' 1D minima (each a clamped vertex)."""
+    if lo[0] <= 0.0 <= hi[0] and lo[1] <= 0.0 <= hi[1]:
+        return 0.0
+    best = math.inf
+    for dy in (lo[1], hi[1]):       # horizontal edges: minimise over dx
+        dx = min(max(-B * dy / A, lo[0]), hi[0])
+        best = min(best, A * dx * dx + 2 * B * dx * dy + Cc * dy * dy)
+    for dx in (lo[0], hi[0]):       # vertical edges: minimise over dy
+        dy = min(max(-B * dx / Cc, lo[1]), hi[1])
+        best = min(best, A * dx * dx + 2 * B * dx * dy + Cc * dy * dy)
+    return best
+
+
+def _thin_scene(seed, n=60, width=112, height=96):
+    """Needle-like Gaussians (one scale ~20-50x the others) at random
+    orientations, plus round ones."""
+    sc, view = synth.tiny_scene(seed, n=n, sh_degree=0, width=width, height=height, depth=3.0,
+                                log_scale_mean=-2.0, spread=1.0)
+    rng = np.random.default_rng(100 + seed)
+    thin = rng.random(n) < 0.6
+    ls = sc.log_scales.copy()
+    ls[thin, 0] = rng.normal(-0.9, 0.3, thin.sum())
+    ls[thin, 1] = rng.normal(-4.2, 0.3, thin.sum())
+    ls[thin, 2] = rng.normal(-4.0, 0.3, thin.sum())
+    sc.log_scales = ls.astype(np.float32)
+    q = rng.normal(size=(n, 4))
+    sc.quats = (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+    view.fx = view.fy = 90.0
+    return sc, view
+
+
+@pytest.mark.parametrize("seed,tile", [(0, (16, 16)), (1, (16, 16)), (2, (8, 8)),
+                                       (3, (32, 8)), (4, (16, 16))])
+def test_tile_coverage_exact_minimum_thin_gaussians(oracle_mod, seed, tile):
+    """Tile coverage, pinned a second way: for every record, a tile of its
+    bounding rectangle is kept iff the exact FP64 minimum of m over the
+    rectangle of the tile's pixel centres (closed form: centre or edge
+    minimisers) is <= 9.009, up to 1e-5 relative (the FP32 row rule's
+    rounding); and every pixel whose centre has m <= 9 lies in a kept tile
+    (brute force over all pixels). Scenes of thin, rotated Gaussians."""
+    tw, th = tile
+    sc, view = _thin_scene(seed)
+    km = oracle_mod.keymode(sc, view, np.arange(sc.n), tile_w=tw, tile_h=th)
+    ntx = (view.width + tw - 1) // tw
+    yy, xx = np.mgrid[0:view.height, 0:view.width]
+    checked = dropped = near = 0
+    for i in range(sc.n):
+        k = km[i]
+        if k["culled"]:
+            continue
+        kept = set(oracle_mod.record_tiles(k, view, tw, th).tolist())
+        u, v, A, B, Cc = (float(k[f]) for f in ("u", "v", "A", "B", "C"))
+        for ty in range(k["ty0"], k["ty1"] + 1):
+            for tx in range(k["tx0"], k["tx1"] + 1):
+                lo = (tx * tw + 0.5 - u, ty * th + 0.5 - v)
+                hi = (lo[0] + tw - 1, lo[1] + th - 1)
+                mmin = _rect_min_m(A, B, Cc, lo, hi)
+                if abs(mmin - 9.009) <= 9.009e-5:
+                    near += 1
+                    continue
+                assert ((ty * ntx + tx) in kept) == (mmin <= 9.009), (i, tx, ty, mmin)
+                checked += 1
+                dropped += (ty * ntx + tx) not in kept
+        # brute force over pixel centres: m <= 9 => the pixel's tile is kept
+        dx, dy = xx + 0.5 - u, yy + 0.5 - v
+        m = A * dx * dx + 2 * B * dx * dy + Cc * dy * dy
+        for y, x in zip(*np.nonzero(m <= 9.0)):
+            assert (y // th) * ntx + (x // tw) in kept, (i, x, y)
+    assert checked > 200 and dropped > 20, (checked, dropped)
+    assert near <= 0.01 * checked, near
