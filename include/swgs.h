@@ -469,6 +469,33 @@ int64_t swgs_kernel_launches(void);
  * The context stays usable. */
 swgs_status swgs_selftest_sort_timeout(swgs_ctx *ctx, void *stream);
 
+/*
+ * Data-parallel gradient exchange (no paper counterpart: the paper trains on
+ * one GPU; this serves a window step sharded by views over several GPUs, each
+ * holding a replica of the state). Only the eligible slots -- active at one of
+ * `frames` (host int32[n_frames], at most 64) and not frozen, the slots the
+ * Adam/noise step of swgs_sgld_step reads gradients of -- can carry a nonzero
+ * gradient, and every replica finds the same ones, so the ranks sum those rows
+ * only.
+ *
+ * swgs_grad_pack writes the eligible slots, ascending, to ids (device int32,
+ * capacity g->capacity), their number to *count (device int64) and their
+ * gradient rows to packed (device float, capacity g->capacity x R), row k =
+ * the gradients of slot ids[k]: means 3, log_scales 3, quats 4, opacity logit
+ * 1, sh 3K, so R = 11 + 3K with K = (sh_degree + 1)^2, each value multiplied
+ * by `scale` (a rank's share of the window's views). grads has the state's
+ * capacity and SH degree. The caller reads the count, sums packed[0, count x R)
+ * over the ranks, and calls
+ * swgs_grad_unpack, which writes row k back to slot ids[k] of grads for
+ * k < *count (other slots are left as they are). Both are asynchronous on
+ * `stream`; buffers are caller-owned. SWGS_EINVAL for bad arguments.
+ */
+swgs_status swgs_grad_pack(swgs_ctx *ctx, const swgs_gaussians *g, const swgs_gaussians *grads,
+                           const int32_t *frames, int32_t n_frames, float scale, int32_t *ids,
+                           int64_t *count, float *packed, void *stream);
+swgs_status swgs_grad_unpack(swgs_ctx *ctx, const swgs_gaussians *grads, const int32_t *ids,
+                             const int64_t *count, const float *packed, void *stream);
+
 /* FP32-pipe throughput probe (no paper counterpart): the measured peak that
  * the blends' roofline is taken against. Launches `blocks` blocks of 256
  * threads on `stream`; every thread runs 8 independent multiply-add chains

@@ -154,6 +154,11 @@ PROTOTYPES = [
     ("swgs_profile_read", C.c_int, [C.c_void_p, C.POINTER(SwgsProfile), C.c_int32]),
     ("swgs_kernel_launches", C.c_int64, []),
     ("swgs_selftest_sort_timeout", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("swgs_grad_pack", C.c_int,
+     [C.c_void_p, C.POINTER(SwgsGaussians), C.POINTER(SwgsGaussians), C.POINTER(C.c_int32),
+      C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("swgs_grad_unpack", C.c_int,
+     [C.c_void_p, C.POINTER(SwgsGaussians), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("swgs_fp32_peak_launch", C.c_int,
      [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
 ]

@@ -418,6 +418,27 @@ class Renderer:
             self._stream(stream)))
         return int(nrel.value) if count_relocated else None
 
+    # -- data-parallel gradient exchange -----------------------------------------
+    def grad_pack(self, state: GaussianState, grads: GaussianGrads, frames, ids: torch.Tensor,
+                  count: torch.Tensor, packed: torch.Tensor, scale: float = 1.0, stream=None):
+        """Pack the gradient rows (times `scale`) of the slots eligible at
+        `frames` (active at one of them, not frozen) into packed[:count] (rows
+        of 11 + 3K floats), their slots into ids[:count] and their number into
+        count (device int64)."""
+        fr = (C.c_int32 * max(1, len(frames)))(*[int(f) for f in frames])
+        g = state.c_struct()
+        gr = grads.c_struct()
+        self._check(_abi.load().swgs_grad_pack(self.ctx, C.byref(g), C.byref(gr), fr, len(frames),
+                                               float(scale), _ptr(ids), _ptr(count), _ptr(packed),
+                                               self._stream(stream)))
+
+    def grad_unpack(self, grads: GaussianGrads, ids: torch.Tensor, count: torch.Tensor,
+                    packed: torch.Tensor, stream=None):
+        """Write packed row k back to slot ids[k] of grads, for k < count."""
+        gr = grads.c_struct()
+        self._check(_abi.load().swgs_grad_unpack(self.ctx, C.byref(gr), _ptr(ids), _ptr(count),
+                                                 _ptr(packed), self._stream(stream)))
+
     # -- Alg. 2 update_thread ----------------------------------------------------
     def frame_update(self, dst: GaussianState, first: int, src, src_on_host: bool, stream=None):
         """Overwrite slots [first, first + n) of dst with src (a GaussianState on

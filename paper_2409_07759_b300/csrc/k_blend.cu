@@ -224,16 +224,40 @@ __device__ __forceinline__ void stage_gaussian_x2(const Records& rec, uint32_t r
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
 
+// Forward staging: the terms of stage_gaussian_x2, with the Gaussian's 1-based
+// position in its tile's list in the last word (the value `last` takes when
+// the Gaussian is included). Returns whether its opacity exceeds 0.99, the
+// only case in which alpha can take the 0.99 clamp.
+__device__ __forceinline__ bool stage_gaussian_fwd(const Records& rec, uint32_t r, int pos1,
+                                                   float4* sa, float4* sb, float4* sc, float4* sd,
+                                                   float4* se) {
+    const float4 A = rec.a[r];
+    const float4 B = rec.b[r];
+    const float4 Cc = rec.c[r];
+    const float qa = __fmul_rn(B.x, -0.5f * kLog2e), qb = __fmul_rn(B.y, -kLog2e);
+    const float qc = __fmul_rn(B.z, -0.5f * kLog2e);
+    const float lo = __log2f(A.z);
+    *sa = make_float4(-A.x, -A.x, -A.y, -A.y);
+    *sb = make_float4(qa, qa, qb, qb);
+    *sc = make_float4(qc, qc, lo, lo);
+    *sd = make_float4(-Cc.x, -Cc.x, -Cc.y, -Cc.y);
+    *se = make_float4(-Cc.z, -Cc.z, pair_vmin(lo), __int_as_float(pos1));
+    return A.z > kAlphaMax;
+}
+
 // One staged Gaussian against the thread's pixel pairs (the forward's inner
-// step). CLAMP: the Gaussian's opacity exceeds 0.99, so alpha may take the
-// 0.99 clamp; the reverse blend splits on the same staged flag, so both
-// passes take the same alpha.
+// step). CLAMP: alpha takes min(0.99, .) -- exact for every Gaussian, needed
+// only for those whose opacity exceeds 0.99, so chunks without one skip it;
+// the reverse blend splits on the same per-Gaussian flag, and both passes take
+// the same alpha. COUNT: also records each pixel's stopping position (the
+// pair-counting form, not timed).
 template <bool CLAMP, int NP, bool COUNT>
 __device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float4 gd, float4 ge,
-                                          float2 dx, float2 adx, int pos, int pos1,
+                                          float2 dx, float2 adx, int pos,
                                           float2 (&T)[NP], float2 (&C0)[NP], float2 (&C1)[NP],
                                           float2 (&C2)[NP], float2 (&py)[NP], int (&last)[2 * NP],
                                           int (&stop)[2 * NP]) {
+    const int pos1 = __float_as_int(ge.w);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         const float2 dy = __fadd2_rn(py[i], hi2(ga));
@@ -246,9 +270,9 @@ __device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float
             nal.x = fmaxf(-kAlphaMax, nal.x);
             nal.y = fmaxf(-kAlphaMax, nal.y);
         }
-        const bool ok0 = v.x >= ge.z, ok1 = v.y >= ge.z;
         // T (1 - alpha), rounded once: the stopping test
         const float2 tT = __ffma2_rn(nal, T[i], T[i]);
+        const bool ok0 = v.x >= ge.z, ok1 = v.y >= ge.z;
         const bool inc0 = ok0 && tT.x >= kTStop, inc1 = ok1 && tT.y >= kTStop;
         if (COUNT) {
             stop[2 * i] = (ok0 && !inc0) ? pos : stop[2 * i];
@@ -258,24 +282,54 @@ __device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float
         py[i].y = (ok1 && !inc1) ? kGone : py[i].y;
         nal.x = inc0 ? nal.x : 0.f;
         nal.y = inc1 ? nal.y : 0.f;
+        last[2 * i] = inc0 ? pos1 : last[2 * i];
+        last[2 * i + 1] = inc1 ? pos1 : last[2 * i + 1];
         const float2 nw = __fmul2_rn(nal, T[i]);      // -w
         C0[i] = __ffma2_rn(lo2(gd), nw, C0[i]);
         C1[i] = __ffma2_rn(hi2(gd), nw, C1[i]);
         C2[i] = __ffma2_rn(lo2(ge), nw, C2[i]);
         T[i] = __fadd2_rn(T[i], nw);
-        last[2 * i] = inc0 ? pos1 : last[2 * i];
-        last[2 * i + 1] = inc1 ? pos1 : last[2 * i + 1];
     }
 }
 
-// 4 pixels a thread: at least 16 blocks of 64 threads per SM (63 registers,
-// no spills with the two clamp bodies); 18-20 blocks spill
+// One staged Gaussian j: its terms from shared memory, then fwd_pairs.
+template <bool CLAMP, int NP, bool COUNT>
+__device__ __forceinline__ void fwd_step(const float4* sa, const float4* sb, const float4* sc,
+                                         const float4* sd, const float4* se, int j, int pos,
+                                         float2 px2, float2 (&T)[NP], float2 (&C0)[NP],
+                                         float2 (&C1)[NP], float2 (&C2)[NP], float2 (&py)[NP],
+                                         int (&last)[2 * NP], int (&stop)[2 * NP]) {
+    const float4 ga = sa[j], gb = sb[j], gc = sc[j], gd = sd[j], ge = se[j];
+    const float2 dx = __fadd2_rn(px2, lo2(ga));
+    const float2 adx = __fmul2_rn(lo2(gb), dx);
+    fwd_pairs<CLAMP, NP, COUNT>(ga, gb, gc, gd, ge, dx, adx, pos, T, C0, C1, C2, py, last, stop);
+}
+
+// Whether every pixel of the thread has stopped (or lies outside the image).
+template <int NP>
+__device__ __forceinline__ bool all_gone(const float2 (&py)[NP]) {
+    bool d = true;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) d &= (py[i].x == kGone) & (py[i].y == kGone);
+    return d;
+}
+
+// 4 pixels a thread: at least 16 blocks of 64 threads per SM (64 registers;
+// 14 blocks at 72 registers and 12 at 80 measured slower).
+// The staged Gaussians are taken kFwdUnroll at a time (one warp vote for
+// all). A full chunk holding no Gaussian of opacity > 0.99 (one bit per staged
+// Gaussian, set at staging) runs the body without the clamp, unrolled with no
+// per-Gaussian test; any other chunk -- one with such a Gaussian, or the
+// batch's partial last chunk -- runs the clamp body, exact for every
+// Gaussian, with a bound test per Gaussian.
 template <int TW, int TH, int BATCH, int PPT, bool COUNT>
 __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_x2_kernel(BlendArgs a) {
     static_assert(PPT % 2 == 0, "pixels are taken in pairs");
+    static_assert(BATCH % kFwdUnroll == 0 && 32 % kFwdUnroll == 0, "chunks within a mask word");
     constexpr int NT = TileGeom<TW, TH, PPT>::NT;
     constexpr int NP = PPT / 2;
     __shared__ float4 sa[BATCH], sb[BATCH], sc[BATCH], sd[BATCH], se[BATCH];
+    __shared__ unsigned s_cm[BATCH / 32];  // clamp bits of the staged Gaussians
     __shared__ int s_item;
     const unsigned F = 0xffffffffu;
     const int tid = threadIdx.x;
@@ -314,40 +368,49 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
             stop[p] = rg.y;
         }
         for (int b0 = rg.x; b0 < rg.y; b0 += BATCH) {
-            bool tdone = true;
-#pragma unroll
-            for (int i = 0; i < NP; ++i) tdone &= (py[i].x == kGone) & (py[i].y == kGone);
+            bool tdone = all_gone<NP>(py);
             if (__syncthreads_count(tdone) == NT) break;
             for (int k = tid; k < BATCH; k += NT) {
                 const int idx = b0 + k;
+                bool cl = false;
                 if (idx < rg.y)
-                    stage_gaussian_x2<false>(a.rec, a.vals[idx], &sa[k], &sb[k], &sc[k], &sd[k],
-                                             &se[k]);
+                    cl = stage_gaussian_fwd(a.rec, a.vals[idx], idx - rg.x + 1, &sa[k], &sb[k],
+                                            &sc[k], &sd[k], &se[k]);
+                const unsigned m = __ballot_sync(F, cl);
+                if ((tid & 31) == 0) s_cm[k >> 5] = m;
             }
             __syncthreads();
             const int cnt = min(BATCH, rg.y - b0);
-            for (int j2 = 0; j2 < cnt; j2 += kFwdUnroll) {
+            int j2 = 0;
+            for (; j2 < cnt; j2 += kFwdUnroll) {
                 if (__all_sync(F, tdone)) break;
+                const unsigned cm = (s_cm[j2 >> 5] >> (j2 & 31)) & ((1u << kFwdUnroll) - 1u);
+                if (cm == 0u && j2 + kFwdUnroll <= cnt) {
 #pragma unroll
-                for (int jj = 0; jj < kFwdUnroll; ++jj) {
-                const int j = j2 + jj;
-                if (j >= cnt) break;
-                const float4 ga = sa[j], gb = sb[j], gc = sc[j], gd = sd[j], ge = se[j];
-                const int pos = b0 + j, pos1 = pos - rg.x + 1;
-                const float2 dx = __fadd2_rn(px2, lo2(ga));
-                const float2 adx = __fmul2_rn(lo2(gb), dx);
-                if (ge.w != 0.f)
-                    fwd_pairs<true, NP, COUNT>(ga, gb, gc, gd, ge, dx, adx, pos, pos1, T, C0, C1,
-                                               C2, py, last, stop);
-                else
-                    fwd_pairs<false, NP, COUNT>(ga, gb, gc, gd, ge, dx, adx, pos, pos1, T, C0,
-                                                C1, C2, py, last, stop);
+                    for (int jj = 0; jj < kFwdUnroll; ++jj)
+                        fwd_step<false, NP, COUNT>(sa, sb, sc, sd, se, j2 + jj, b0 + j2 + jj,
+                                                   px2, T, C0, C1, C2, py, last, stop);
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < kFwdUnroll; ++jj) {
+                        if (j2 + jj >= cnt) break;
+                        fwd_step<true, NP, COUNT>(sa, sb, sc, sd, se, j2 + jj, b0 + j2 + jj,
+                                                  px2, T, C0, C1, C2, py, last, stop);
+                    }
                 }
-                tdone = true;
-#pragma unroll
-                for (int i = 0; i < NP; ++i) tdone &= (py[i].x == kGone) & (py[i].y == kGone);
+                tdone = all_gone<NP>(py);
             }
         }
+        // the view's fields, read before the stores below (which may alias them)
+        const float bg0 = V.bg[0], bg1 = V.bg[1], bg2 = V.bg[2];
+        float* const out_rgb = V.out_rgb;
+        float* const out_T = V.out_T;
+        const long long pix_base = V.pix_base;
+        const float* const tgt = V.target;
+        const uint8_t* const tgt8 = V.target_u8;
+        float* const dL_out = V.dL_out;
+        const float l1s = V.l1_scale;
+        const long long hw = (long long)W * H;
 #pragma unroll
         for (int p = 0; p < PPT; ++p) {
             const int y = y0 + p;
@@ -356,37 +419,36 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
             const float c1 = (p & 1) ? C1[p / 2].y : C1[p / 2].x;
             const float c2 = (p & 1) ? C2[p / 2].y : C2[p / 2].x;
             if (x < W && y < H) {
-                const long long hw = (long long)W * H, q = (long long)y * W + x;
-                const float r0 = c0 + Tp * V.bg[0];
-                const float r1 = c1 + Tp * V.bg[1];
-                const float r2 = c2 + Tp * V.bg[2];
-                V.out_rgb[q] = r0;
-                V.out_rgb[hw + q] = r1;
-                V.out_rgb[2 * hw + q] = r2;
-                if (V.out_T) V.out_T[q] = Tp;
-                if (a.T) a.T[V.pix_base + q] = Tp;
-                if (a.last) a.last[V.pix_base + q] = last[p];
+                const long long q = (long long)y * W + x;
+                const float r0 = c0 + Tp * bg0;
+                const float r1 = c1 + Tp * bg1;
+                const float r2 = c2 + Tp * bg2;
+                out_rgb[q] = r0;
+                out_rgb[hw + q] = r1;
+                out_rgb[2 * hw + q] = r2;
+                if (out_T) out_T[q] = Tp;
+                if (a.T) a.T[pix_base + q] = Tp;
+                if (a.last) a.last[pix_base + q] = last[p];
                 if (COUNT)
                     pairs += (unsigned long long)((stop[p] < rg.y ? stop[p] + 1 : rg.y) - rg.x);
-                if (V.target || V.target_u8) {
+                if (tgt || tgt8) {
                     // L1 term of the loss and its gradient, sign(0) = 0
                     float t0, t1, t2;
-                    if (V.target_u8) {  // k x (1/255) in FP32
+                    if (tgt8) {  // k x (1/255) in FP32
                         constexpr float kInv255 = 1.0f / 255.0f;
-                        t0 = __fmul_rn((float)V.target_u8[q], kInv255);
-                        t1 = __fmul_rn((float)V.target_u8[hw + q], kInv255);
-                        t2 = __fmul_rn((float)V.target_u8[2 * hw + q], kInv255);
+                        t0 = __fmul_rn((float)tgt8[q], kInv255);
+                        t1 = __fmul_rn((float)tgt8[hw + q], kInv255);
+                        t2 = __fmul_rn((float)tgt8[2 * hw + q], kInv255);
                     } else {
-                        t0 = V.target[q];
-                        t1 = V.target[hw + q];
-                        t2 = V.target[2 * hw + q];
+                        t0 = tgt[q];
+                        t1 = tgt[hw + q];
+                        t2 = tgt[2 * hw + q];
                     }
                     const float e0 = r0 - t0, e1 = r1 - t1, e2 = r2 - t2;
-                    const float s = V.l1_scale;
-                    V.dL_out[q] = e0 > 0.f ? s : (e0 < 0.f ? -s : 0.f);
-                    V.dL_out[hw + q] = e1 > 0.f ? s : (e1 < 0.f ? -s : 0.f);
-                    V.dL_out[2 * hw + q] = e2 > 0.f ? s : (e2 < 0.f ? -s : 0.f);
-                    l1 += (fabsf(e0) + fabsf(e1) + fabsf(e2)) * s;
+                    dL_out[q] = e0 > 0.f ? l1s : (e0 < 0.f ? -l1s : 0.f);
+                    dL_out[hw + q] = e1 > 0.f ? l1s : (e1 < 0.f ? -l1s : 0.f);
+                    dL_out[2 * hw + q] = e2 > 0.f ? l1s : (e2 < 0.f ? -l1s : 0.f);
+                    l1 += (fabsf(e0) + fabsf(e1) + fabsf(e2)) * l1s;
                 }
             }
         }

@@ -60,6 +60,105 @@ cudaError_t launch_eligible(const swgs_gaussians& g, const int32_t* frames, int 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Gradient rows of the eligible slots, packed for a data-parallel sum: only
+// those rows can hold a nonzero gradient, and every replica finds the same
+// set (same state, same frames), so the ranks exchange count x R floats
+// instead of the whole buffer. Row layout: means 3, log_scales 3, quats 4,
+// opacity logit 1, sh 3K (R = 11 + 3K); rows in ascending slot order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int grad_row_floats(int K) { return 11 + 3 * K; }
+
+__global__ void __launch_bounds__(256)
+elig_count_kernel(const uint8_t* __restrict__ elig, long long n, uint32_t* __restrict__ counts) {
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    const int c = __syncthreads_count(i < n && elig[i]);
+    if (threadIdx.x == 0) counts[blockIdx.x] = (uint32_t)c;
+}
+
+template <bool PACK>
+__device__ __forceinline__ void grad_row_copy(const swgs_gaussians& gr, long long slot, int K,
+                                              float* row, float scale) {
+    const int nsh = 3 * K;
+    float* dst[5] = {gr.means + 3 * slot, gr.log_scales + 3 * slot, gr.quats + 4 * slot,
+                     gr.opacity_logits + slot, gr.sh + (long long)nsh * slot};
+    const int len[5] = {3, 3, 4, 1, nsh};
+    int o = 0;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+        for (int e = 0; e < len[a]; ++e) {
+            if (PACK) row[o + e] = dst[a][e] * scale;
+            else dst[a][e] = row[o + e];
+        }
+        o += len[a];
+    }
+}
+
+__global__ void __launch_bounds__(256)
+grad_pack_kernel(swgs_gaussians gr, const uint8_t* __restrict__ elig, long long n,
+                 const uint32_t* __restrict__ block_off, int K, float scale,
+                 int32_t* __restrict__ ids, float* __restrict__ packed) {
+    __shared__ uint32_t warp_off[8];
+    const long long i = (long long)blockIdx.x * 256 + threadIdx.x;
+    const bool m = i < n && elig[i];
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, m);
+    if (lane == 0) warp_off[warp] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t c = warp_off[w];
+            warp_off[w] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (!m) return;
+    const long long pos = (long long)block_off[blockIdx.x] + warp_off[warp] +
+                          __popc(bal & ((1u << lane) - 1u));
+    ids[pos] = (int32_t)i;
+    grad_row_copy<true>(gr, i, K, packed + pos * grad_row_floats(K), scale);
+}
+
+__global__ void __launch_bounds__(256)
+grad_unpack_kernel(swgs_gaussians gr, const int32_t* __restrict__ ids,
+                   const long long* __restrict__ count, int K, const float* __restrict__ packed) {
+    const long long k = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (k >= *count) return;
+    grad_row_copy<false>(gr, ids[k], K, const_cast<float*>(packed) + k * grad_row_floats(K), 1.f);
+}
+
+cudaError_t launch_grad_pack(const swgs_gaussians& g, const swgs_gaussians& grads,
+                             const int32_t* frames, int n_frames, float scale, uint8_t* elig,
+                             uint32_t* block_cnt, void* scan_tmp, int32_t* ids, long long* count,
+                             float* packed, cudaStream_t s) {
+    const long long n = g.capacity;
+    cudaError_t e = launch_eligible(g, frames, n_frames, elig, s);
+    if (e != cudaSuccess) return e;
+    const long long nb = div_up(n, 256);
+    note_launch();
+    elig_count_kernel<<<(unsigned)nb, 256, 0, s>>>(elig, n, block_cnt);
+    e = exclusive_scan_u32(block_cnt, block_cnt, nb, scan_tmp, (unsigned long long*)count, s);
+    if (e != cudaSuccess) return e;
+    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    note_launch();
+    grad_pack_kernel<<<(unsigned)nb, 256, 0, s>>>(grads, elig, n, block_cnt, K, scale, ids,
+                                                  packed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_unpack(const swgs_gaussians& grads, const int32_t* ids,
+                               const long long* count, long long capacity, const float* packed,
+                               cudaStream_t s) {
+    if (capacity <= 0) return cudaSuccess;
+    const int K = (grads.sh_degree + 1) * (grads.sh_degree + 1);
+    note_launch();
+    grad_unpack_kernel<<<(unsigned)div_up(capacity, 256), 256, 0, s>>>(grads, ids, count, K,
+                                                                       packed);
+    return cudaGetLastError();
+}
+
 __device__ __forceinline__ void adam1(float* p, float* m, float* v, float g, float lr,
                                       const SgldArgs& a) {
     const float mm = a.p.beta1 * *m + (1.f - a.p.beta1) * g;

@@ -1355,6 +1355,52 @@ swgs_status swgs_loss_l1(swgs_ctx* ctx, int32_t n_views, const swgs_view* views,
     return SWGS_OK;
 }
 
+swgs_status swgs_grad_pack(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_gaussians* grads,
+                           const int32_t* frames, int32_t n_frames, float scale, int32_t* ids,
+                           int64_t* count, float* packed, void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    ctx->err.clear();
+    swgs_status st = check_gaussians(ctx, g, true);
+    if (st != SWGS_OK) return st;
+    st = check_gaussians(ctx, grads, false);
+    if (st != SWGS_OK) return st;
+    if (grads->capacity != g->capacity || grads->sh_degree != g->sh_degree)
+        return fail(ctx, SWGS_EINVAL, "gradients must match the state's capacity and SH degree");
+    if (n_frames < 0 || n_frames > 64 || (n_frames > 0 && !frames) || !count ||
+        (g->capacity > 0 && (!ids || !packed)))
+        return fail(ctx, SWGS_EINVAL, "bad frames or output buffers (at most 64 frames)");
+    const long long N = g->capacity;
+    if (N == 0) {
+        CK(cudaMemsetAsync(count, 0, sizeof(int64_t), s));
+        return SWGS_OK;
+    }
+    const long long nb = (N + 255) / 256;
+    if (!ensure(ctx, ctx->elig, (size_t)N, s) ||
+        !ensure(ctx, ctx->block_cnt, sizeof(uint32_t) * (size_t)(nb + 1), s) ||
+        !ensure(ctx, ctx->scan_tmp, scan_u32_temp_bytes(nb + 1) + 64, s))
+        return fail(ctx, SWGS_ENOMEM, "allocation failed (gradient packing)");
+    CK(launch_grad_pack(*g, *grads, frames, n_frames, scale, P<uint8_t>(ctx->elig),
+                        P<uint32_t>(ctx->block_cnt), ctx->scan_tmp.p, ids, (long long*)count,
+                        packed, s));
+    return SWGS_OK;
+}
+
+swgs_status swgs_grad_unpack(swgs_ctx* ctx, const swgs_gaussians* grads, const int32_t* ids,
+                             const int64_t* count, const float* packed, void* stream) {
+    if (!ctx) return SWGS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    ctx->last_stream = s;
+    ctx->err.clear();
+    swgs_status st = check_gaussians(ctx, grads, false);
+    if (st != SWGS_OK) return st;
+    if (!count || (grads->capacity > 0 && (!ids || !packed)))
+        return fail(ctx, SWGS_EINVAL, "null ids, count or packed rows");
+    CK(launch_grad_unpack(*grads, ids, (const long long*)count, grads->capacity, packed, s));
+    return SWGS_OK;
+}
+
 swgs_status swgs_sgld_step(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_gaussians* grads,
                            const swgs_adam_state* adam, const int32_t* frames, int32_t n_frames,
                            const swgs_sgld_params* params, uint64_t seed, uint64_t step,

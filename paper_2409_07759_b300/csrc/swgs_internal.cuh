@@ -511,6 +511,14 @@ cudaError_t launch_copy_slice(const swgs_gaussians& dst, long long first, long l
 // elig: one byte per slot, 1 = active at a frame of the step and not frozen
 cudaError_t launch_eligible(const swgs_gaussians& g, const int32_t* frames, int n_frames,
                             uint8_t* elig, cudaStream_t s);
+// data-parallel exchange: eligible slots' gradient rows packed [count, 11 + 3K]
+cudaError_t launch_grad_pack(const swgs_gaussians& g, const swgs_gaussians& grads,
+                             const int32_t* frames, int n_frames, float scale, uint8_t* elig,
+                             uint32_t* block_cnt, void* scan_tmp, int32_t* ids, long long* count,
+                             float* packed, cudaStream_t s);
+cudaError_t launch_grad_unpack(const swgs_gaussians& grads, const int32_t* ids,
+                               const long long* count, long long capacity, const float* packed,
+                               cudaStream_t s);
 cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
                         const swgs_adam_state* adam, const uint8_t* elig,
                         const swgs_sgld_params& p, unsigned long long seed,

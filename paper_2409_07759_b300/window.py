@@ -77,6 +77,7 @@ class WindowTrainer:
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
         # largest number of tile keys of any step so far (sizes the scratch)
         self.max_keys = 0
+        self._rows = None  # data parallel: the eligible rows' exchange buffers
 
     def set_window(self, views: Sequence, targets: Sequence[torch.Tensor]):
         """Move the trainer to another window's views and targets (buffers are
@@ -143,7 +144,11 @@ class WindowTrainer:
         self.max_keys = max(self.max_keys, int(saved.info().n_keys))
         saved.release()
         if self.reduce is not None:
-            self.reduce(self._gflat, self.loss)
+            if self._rows is None:
+                from . import dp
+                self._rows = dp.RowExchange(self.r, self.state, self.grads, self.frames)
+            self._rows.frames = self.frames
+            self.reduce(self._gflat, self.loss, rows=self._rows)
         self.r.sgld_step(self.state, self.frames, self.params, self.seed, step,
                          grads=self.grads, adam=self.adam)
         if self._bufs is not None:

@@ -60,6 +60,30 @@ def _unflat(flat, like):
     return out
 
 
+class _HostRows:
+    """Host stand-in of dp.RowExchange for the CPU ranks: the gradient rows of
+    the eligible slots (active at a frame of the window, not frozen) in the
+    library's row layout (means 3, log_scales 3, quats 4, logit 1, sh 3K)."""
+
+    def __init__(self, sc, g, frames):
+        f = np.asarray(frames)
+        act = ((sc.start[:, None] <= f[None, :]) & (f[None, :] < sc.expire[:, None])).any(1)
+        self.ids = np.nonzero(act & (sc.frozen == 0))[0]
+        self.g = g
+
+    def pack(self, scale=1.0):
+        rows = np.concatenate([self.g[k][self.ids].reshape(len(self.ids), -1) for k in GRAD_KEYS],
+                              axis=1)
+        return torch.from_numpy(rows * scale), len(self.ids)
+
+    def unpack(self, packed, n):
+        o = 0
+        for k in GRAD_KEYS:
+            w = int(np.prod(self.g[k].shape[1:]))
+            self.g[k][self.ids] = packed[:n, o:o + w].numpy().reshape((n,) + self.g[k].shape[1:])
+            o += w
+
+
 def _worker(rank, world, port, result_dir):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -74,8 +98,21 @@ def _worker(rank, world, port, result_dir):
     flat = _flat(g)
     lt_loss = torch.tensor([loss], dtype=torch.float64)
     red = dp.GradientReducer(len(lv), dp.total_views(len(lv)))
+    # the eligible rows' exchange: the same sums from far fewer floats
+    frames = sorted({v.frame for v in views})
+    g_rows = {k: v.copy() for k, v in g.items()}
+    rows = _HostRows(sc, g_rows, frames)
+    outside = np.setdiff1d(np.arange(sc.n), rows.ids)
+    for k in GRAD_KEYS:  # nothing outside the eligible rows carries a gradient
+        assert not np.any(g[k][outside]), k
+    red(None, None, rows=rows)
+    exchanged = red.last_exchanged
     red(flat, lt_loss)
     reduced = _unflat(flat, g)
+    for k in GRAD_KEYS:
+        np.testing.assert_allclose(g_rows[k], reduced[k], rtol=1e-13,
+                                   atol=1e-15 * max(1e-30, np.abs(reduced[k]).max()))
+    assert exchanged < flat.numel() / 2, (exchanged, flat.numel())
     # the replicas' optimiser step from the reduced gradients
     grads32 = {k: v.astype(np.float32) for k, v in reduced.items()}
     new, _, n_dead, tg = oracle.sgld_step(sc, grads32, None, [v.frame for v in views],

@@ -189,3 +189,87 @@ def test_frame_update_matches_alg2(R, oracle_mod, on_host):
             np.testing.assert_array_equal(_np(getattr(st, k)), getattr(ref, k))
         ids = _np(R.active_ids(st, f))
         np.testing.assert_array_equal(ids, np.arange(buf.n, dtype=np.int32))
+
+
+# ------------------------------------------------- data-parallel exchange --
+
+def test_grad_pack_unpack_eligible_rows(R):
+    """swgs_grad_pack: the eligible slots (active at one of the frames, not
+    frozen), ascending, and their gradient rows (means 3, log_scales 3, quats 4,
+    logit 1, sh 3K) times the scale, bit for bit; swgs_grad_unpack writes the
+    rows back to those slots only."""
+    from paper_2409_07759_b300 import api
+    sc, _, _ = _scene(n=20011)
+    st = _state(sc)
+    rng = np.random.default_rng(3)
+    g = st.zero_grads()
+    for k in NAMES:
+        getattr(g, k).copy_(torch.from_numpy(
+            rng.normal(size=tuple(getattr(g, k).shape)).astype(np.float32)))
+    frames = [145, 147]
+    f = np.asarray(frames)
+    act = ((sc.start[:, None] <= f[None, :]) & (f[None, :] < sc.expire[:, None])).any(1)
+    want_ids = np.nonzero(act & (sc.frozen == 0))[0]
+    K = 16
+    ids = torch.full((sc.n,), -1, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    packed = torch.full((sc.n, 11 + 3 * K), float("nan"), dtype=torch.float32, device="cuda")
+    R.grad_pack(st, g, frames, ids, cnt, packed, scale=0.25)
+    n = int(cnt.item())
+    assert n == len(want_ids) and 0 < n < sc.n
+    np.testing.assert_array_equal(_np(ids[:n]), want_ids)
+    host = {k: _np(getattr(g, k)) for k in NAMES}
+    rows = np.concatenate([host[k][want_ids].reshape(n, -1) for k in NAMES], 1) * np.float32(0.25)
+    np.testing.assert_array_equal(_np(packed[:n]), rows)
+    g2 = st.zero_grads()
+    R.grad_unpack(g2, ids, cnt, packed)
+    for k in NAMES:
+        a = _np(getattr(g2, k))
+        np.testing.assert_array_equal(a[want_ids], host[k][want_ids] * np.float32(0.25))
+        mask = np.ones(sc.n, bool)
+        mask[want_ids] = False
+        assert not np.any(a[mask])
+
+
+def test_row_exchange_through_nccl():
+    """One rank (NCCL): the eligible-row exchange of dp.GradientReducer leaves
+    the backward's gradients scaled by the rank's view share, bit for bit
+    (x 0.5 is exact), exchanging fewer than half the buffer's floats; and a
+    window step with the reducer runs through it."""
+    import datetime
+    import os
+    import socket
+    import torch.distributed as dist
+    from paper_2409_07759_b300 import api, dp
+    from paper_2409_07759_b300.window import WindowTrainer
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(s.getsockname()[1])
+    s.close()
+    dist.init_process_group("nccl", rank=0, world_size=1,
+                            timeout=datetime.timedelta(seconds=60))
+    try:
+        sc, views, targets = synth.config2(width=128, height=96, n=20000, n_frames=3,
+                                           per_frame=2, forced_dead_fraction=0.01)
+        tg = [torch.from_numpy(t).cuda() for t in targets]
+        r = api.Renderer()
+        st = api.GaussianState.from_scene(sc)
+        grads = st.zero_grads()
+        imgs, dls, loss, saved = r.render_l1(st, views, tg)
+        r.backward(st, saved, dls, grads)
+        saved.release()
+        before = {k: _np(getattr(grads, k)).copy() for k in NAMES}
+        frames = sorted({v.frame for v in views})
+        red = dp.GradientReducer(1, 2)
+        red(None, loss, rows=dp.RowExchange(r, st, grads, frames))
+        for k in NAMES:
+            np.testing.assert_array_equal(_np(getattr(grads, k)), before[k] * np.float32(0.5))
+        assert 0 < red.last_exchanged < st.n * (11 + 48) // 2
+        tr = WindowTrainer(r, st, views, tg, seed=5,
+                           reduce=dp.GradientReducer(len(views), len(views)))
+        assert torch.isfinite(tr.step(0)).all()
+        torch.cuda.synchronize()
+        r.close()
+    finally:
+        dist.destroy_process_group()
