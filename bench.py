@@ -105,7 +105,11 @@ def parse():
     ap.add_argument("--viewers", type=int, default=64)
     ap.add_argument("--rate", type=float, default=30.0, help="requests/s per viewer")
     ap.add_argument("--serve-streams", type=int, default=3)
+    ap.add_argument("--serve-slots", type=int, default=1,
+                    help="batches each serving worker may have in flight")
     ap.add_argument("--hbm-budget-gb", type=float, default=24.0)
+    ap.add_argument("--sweep-seconds", type=float, default=2.5,
+                    help="seconds per rate of the serving sweep (0: no sweep)")
     return ap.parse_args()
 
 
@@ -347,7 +351,7 @@ def serving_leg(args):
 
     loop = serving.ServingLoop(st, swin, fps=30.0, n_streams=args.serve_streams, max_batch=16,
                                hbm_budget_bytes=args.hbm_budget_gb * 1e9,
-                               slice_provider=provider)
+                               slice_provider=provider, n_slots=args.serve_slots)
     loop.reserve(1920, 1080)
     warm = serving.make_requests(args.viewers, args.rate, 1.0, seed=40)
     loop.run(warm, 1.0)
@@ -359,9 +363,57 @@ def serving_leg(args):
     out.update(viewers=args.viewers, rate_hz_per_viewer=args.rate,
                resolutions="640x480:1280x720:1920x1080 = 1:2:1", gaussians=scene.n,
                swin_size=swin, slice_size=S, streams=args.serve_streams,
-               hbm_budget_gb=args.hbm_budget_gb, serial=ser,
-               offered_mpix_s=sum(r.width * r.height for r in reqs) / 1e6 / args.serve_seconds)
+               hbm_budget_gb=args.hbm_budget_gb, serial=ser, slots=args.serve_slots,
+               delivered="8-bit RGB [H,W,3] to pinned host memory",
+               offered_mpix_s=sum(r.width * r.height for r in reqs) / 1e6 / args.serve_seconds,
+               latency="arrival to image in pinned host memory (p50/p99_ms); to the end of "
+                       "the render on the device (p50/p99_render_ms)")
+    if args.sweep_seconds > 0:
+        out["sweep"] = {
+            "mix_1_2_1": serving_sweep(args, st, swin, provider, None, "1920x1080"),
+            "all_1280x720": serving_sweep(args, st, swin, provider, [(1280, 720)], "1280x720"),
+        }
     return out
+
+
+def serving_sweep(args, st, swin, provider, resolutions, reserve_res):
+    """Per-viewer request rate raised step by step (64 viewers, Poisson
+    arrivals) until p99 passes 16 ms or the served rate falls behind the
+    offered one; reports each rate and the highest one whose p99 (arrival to
+    image in host memory) stays under 16 ms."""
+    from paper_2409_07759_b300 import serving
+    loop = serving.ServingLoop(st, swin, fps=30.0, n_streams=args.serve_streams, max_batch=16,
+                               hbm_budget_bytes=args.hbm_budget_gb * 1e9,
+                               slice_provider=provider, n_slots=args.serve_slots)
+    w, h = (int(x) for x in reserve_res.split("x"))
+    loop.reserve(w, h)
+    rows, best, misses = [], None, 0
+    for rate in (30, 60, 90, 120, 160, 200, 250, 300, 400, 500):
+        warm = serving.make_requests(args.viewers, rate, 0.5, seed=50 + rate,
+                                     resolutions=resolutions)
+        loop.run(warm, 0.5)
+        reqs = serving.make_requests(args.viewers, rate, args.sweep_seconds, seed=60 + rate,
+                                     resolutions=resolutions)
+        stats = loop.run(reqs, args.sweep_seconds)
+        offered = sum(r.width * r.height for r in reqs) / 1e6 / args.sweep_seconds
+        rows.append({"rate_hz_per_viewer": rate, "requests_per_s": len(reqs) / args.sweep_seconds,
+                     "p50_ms": stats.p50_ms, "p99_ms": stats.p99_ms,
+                     "p99_render_ms": stats.p99_render_ms, "served_mpix_s": stats.mpix_per_s,
+                     "offered_mpix_s": offered, "mean_batch": stats.mean_batch})
+        ok = stats.p99_ms < 16.0 and stats.mpix_per_s >= 0.9 * offered
+        if ok:
+            best = rate
+            misses = 0
+        else:
+            misses += 1
+            if misses >= 2:
+                break
+    loop.close()
+    return {"viewers": args.viewers, "seconds_per_rate": args.sweep_seconds, "rates": rows,
+            "max_rate_p99_under_16ms": best,
+            "max_served_mpix_s_p99_under_16ms": max(
+                (r["served_mpix_s"] for r in rows if r["rate_hz_per_viewer"] == best),
+                default=None)}
 
 
 # ----------------------------------------------------------------- clocks --

@@ -27,7 +27,7 @@
 extern "C" {
 #endif
 
-#define SWGS_ABI_VERSION 4
+#define SWGS_ABI_VERSION 5
 
 typedef enum swgs_status {
     SWGS_OK = 0,
@@ -266,6 +266,18 @@ swgs_status swgs_render_fwd(swgs_ctx *ctx, const swgs_gaussians *g, int32_t n_vi
                             void *stream);
 
 /*
+ * swgs_render_fwd writing 8-bit images instead of float ones, for delivery to
+ * a viewer: out_rgb8[v] is device uint8 [H,W,3] (interleaved RGB), each value
+ * round(255 clamp(c, 0, 1)) of the channel c that swgs_render_fwd writes (ties
+ * to even). out_T, saved, batched and errors as in swgs_render_fwd; a saved
+ * state serves swgs_render_bwd as well.
+ */
+swgs_status swgs_render_fwd_rgb8(swgs_ctx *ctx, const swgs_gaussians *g, int32_t n_views,
+                                 const swgs_view *views, const float *bg,
+                                 uint8_t *const *out_rgb8, float *const *out_T, int32_t batched,
+                                 swgs_saved **saved, void *stream);
+
+/*
  * swgs_render_fwd fused with the L1 term of Alg. 1 loss_func (same as
  * swgs_loss_l1 on the rendered images, without a separate pass over them):
  * besides out_rgb it reads target[v] (device float[3*H*W]), writes
@@ -339,6 +351,12 @@ typedef struct swgs_saved_info {
     int64_t pairs;         /* evaluated (pixel, Gaussian) pairs (count_pairs = 1) */
     int64_t n_sort_keys;   /* (super tile, Gaussian) keys sorted to build the tile lists */
     int64_t n_supers;      /* super tiles over all views */
+    /* Device bytes the forward's data takes at the sizes it needed (the saved
+     * state and the context scratch it used; the caller's images excluded), and
+     * the part of it that grows with the records (the active-set ids and the
+     * per-record arrays). A server can size its admission from these. */
+    int64_t device_bytes;
+    int64_t record_bytes;
 } swgs_saved_info;
 
 swgs_status swgs_saved_query(swgs_ctx *ctx, const swgs_saved *saved, swgs_saved_info *info);
@@ -393,6 +411,12 @@ typedef struct swgs_sgld_params {
     float mean_grad_decay;
     int32_t window_start;
     int32_t swin_size;
+    /* 1 (grads given): after the Adam step has read them, the gradients of the
+     * eligible slots are set to zero, so the next backward starts its sums from
+     * zero without a clearing pass. Gradients of other slots are left as they
+     * are (a backward over frames outside `frames` writes some there).
+     * 0: grads is only read. */
+    int32_t clear_grads;
 } swgs_sgld_params;
 
 /* Adam moments, device arrays shaped like the five float parameter arrays. */

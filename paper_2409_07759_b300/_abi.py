@@ -55,7 +55,8 @@ class SwgsView(C.Structure):
 class SwgsSavedInfo(C.Structure):
     _fields_ = [("n_views", C.c_int32), ("n_batches", C.c_int32), ("n_records", C.c_int64),
                 ("n_keys", C.c_int64), ("n_tiles", C.c_int64), ("n_pixels", C.c_int64),
-                ("pairs", C.c_int64), ("n_sort_keys", C.c_int64), ("n_supers", C.c_int64)]
+                ("pairs", C.c_int64), ("n_sort_keys", C.c_int64), ("n_supers", C.c_int64),
+                ("device_bytes", C.c_int64), ("record_bytes", C.c_int64)]
 
 
 class SwgsSgldParams(C.Structure):
@@ -65,7 +66,7 @@ class SwgsSgldParams(C.Structure):
                 ("noise_lr", C.c_float), ("noise_k", C.c_float), ("noise_t", C.c_float),
                 ("adam", C.c_int32), ("relocate", C.c_int32), ("max_n", C.c_int32),
                 ("mean_grad_decay", C.c_float), ("window_start", C.c_int32),
-                ("swin_size", C.c_int32)]
+                ("swin_size", C.c_int32), ("clear_grads", C.c_int32)]
 
 
 class SwgsRegParams(C.Structure):
@@ -109,6 +110,10 @@ PROTOTYPES = [
                                   C.POINTER(SwgsView), C.POINTER(C.c_float),
                                   C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32,
                                   C.POINTER(C.c_void_p), C.c_void_p]),
+    ("swgs_render_fwd_rgb8", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_int32,
+                                       C.POINTER(SwgsView), C.POINTER(C.c_float),
+                                       C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int32,
+                                       C.POINTER(C.c_void_p), C.c_void_p]),
     ("swgs_render_fwd_l1", C.c_int, [C.c_void_p, C.POINTER(SwgsGaussians), C.c_int32,
                                      C.POINTER(SwgsView), C.POINTER(C.c_float),
                                      C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
@@ -167,7 +172,7 @@ _lib = None
 
 
 # The struct layouts above mirror include/swgs.h at this SWGS_ABI_VERSION.
-ABI_VERSION = 4
+ABI_VERSION = 5
 
 
 def load():

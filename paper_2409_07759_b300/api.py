@@ -331,6 +331,24 @@ class Renderer:
         saved = SavedState(self, handle, cviews) if keep_saved else None
         return out, saved
 
+    def render_rgb8(self, state: GaussianState, views: Sequence, bg=(0.0, 0.0, 0.0),
+                    batched=True, keep_saved=False, out=None, out_T=None, stream=None):
+        """Render views to 8-bit images: images[v] is a uint8 [H,W,3] tensor
+        (round(255 clamp(c, 0, 1))). Returns (images, saved)."""
+        cviews = _views_array(views)
+        if out is None:
+            out = [torch.empty((v.height, v.width, 3), dtype=torch.uint8, device="cuda")
+                   for v in cviews]
+        bgv = (C.c_float * 3)(*[float(x) for x in bg])
+        handle = C.c_void_p()
+        g = state.c_struct()
+        self._check(_abi.load().swgs_render_fwd_rgb8(
+            self.ctx, C.byref(g), len(cviews), cviews, bgv, _ptr_array(out),
+            _ptr_array(out_T) if out_T is not None else None, int(bool(batched)),
+            C.byref(handle) if keep_saved else None, self._stream(stream)))
+        saved = SavedState(self, handle, cviews) if keep_saved else None
+        return out, saved
+
     def render_l1(self, state: GaussianState, views: Sequence, targets, bg=(0.0, 0.0, 0.0),
                   batched=True, keep_saved=True, out=None, dL_out=None, loss_out=None,
                   stream=None):

@@ -145,9 +145,17 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
                 const float r0 = C0[p] + T[p] * V.bg[0];
                 const float r1 = C1[p] + T[p] * V.bg[1];
                 const float r2 = C2[p] + T[p] * V.bg[2];
-                V.out_rgb[q] = r0;
-                V.out_rgb[hw + q] = r1;
-                V.out_rgb[2 * hw + q] = r2;
+                if (V.out_rgb) {
+                    V.out_rgb[q] = r0;
+                    V.out_rgb[hw + q] = r1;
+                    V.out_rgb[2 * hw + q] = r2;
+                }
+                if (V.out_rgb8) {
+                    uint8_t* o8 = V.out_rgb8 + 3 * q;
+                    o8[0] = rgb8_of(r0);
+                    o8[1] = rgb8_of(r1);
+                    o8[2] = rgb8_of(r2);
+                }
                 if (V.out_T) V.out_T[q] = T[p];
                 if (a.T) a.T[V.pix_base + q] = T[p];
                 if (a.last) a.last[V.pix_base + q] = last[p];
@@ -404,6 +412,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
         // the view's fields, read before the stores below (which may alias them)
         const float bg0 = V.bg[0], bg1 = V.bg[1], bg2 = V.bg[2];
         float* const out_rgb = V.out_rgb;
+        uint8_t* const out_rgb8 = V.out_rgb8;
         float* const out_T = V.out_T;
         const long long pix_base = V.pix_base;
         const float* const tgt = V.target;
@@ -423,9 +432,17 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
                 const float r0 = c0 + Tp * bg0;
                 const float r1 = c1 + Tp * bg1;
                 const float r2 = c2 + Tp * bg2;
-                out_rgb[q] = r0;
-                out_rgb[hw + q] = r1;
-                out_rgb[2 * hw + q] = r2;
+                if (out_rgb) {
+                    out_rgb[q] = r0;
+                    out_rgb[hw + q] = r1;
+                    out_rgb[2 * hw + q] = r2;
+                }
+                if (out_rgb8) {
+                    uint8_t* o8 = out_rgb8 + 3 * q;
+                    o8[0] = rgb8_of(r0);
+                    o8[1] = rgb8_of(r1);
+                    o8[2] = rgb8_of(r2);
+                }
                 if (out_T) out_T[q] = Tp;
                 if (a.T) a.T[pix_base + q] = Tp;
                 if (a.last) a.last[pix_base + q] = last[p];

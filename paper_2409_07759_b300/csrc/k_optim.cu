@@ -219,6 +219,17 @@ __global__ void __launch_bounds__(256) sgld_kernel(SgldArgs a) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.g.capacity) return;
     if (!a.elig[i]) return;
+    if (a.p.clear_grads && a.has_grads) {
+        // the Adam step (an earlier launch) has read this slot's gradients:
+        // leave them zero for the next backward's sums
+        const swgs_gaussians& d = a.grads;
+        const int nsh = 3 * (d.sh_degree + 1) * (d.sh_degree + 1);
+        for (int k = 0; k < 3; ++k) d.means[3 * i + k] = 0.f;
+        for (int k = 0; k < 3; ++k) d.log_scales[3 * i + k] = 0.f;
+        for (int k = 0; k < 4; ++k) d.quats[4 * i + k] = 0.f;
+        d.opacity_logits[i] = 0.f;
+        for (int k = 0; k < nsh; ++k) d.sh[(long long)nsh * i + k] = 0.f;
+    }
     // noise from the (possibly updated) opacity and covariance
     const float o = 1.f / (1.f + expf(-a.g.opacity_logits[i]));
     const float gate = 1.f / (1.f + expf(a.p.noise_k * (o - a.p.noise_t)));

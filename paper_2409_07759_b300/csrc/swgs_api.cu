@@ -247,6 +247,7 @@ int ceil_log2(long long x) {
 // Render one batch of views (indices idx[] into the call's view list).
 swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view* views,
                          const std::vector<int>& idx, const float* bg, float* const* out_rgb,
+                         uint8_t* const* out_rgb8,
                          float* const* out_T, const void* const* targets, int target_u8,
                          float* const* dls,
                          float* loss, int n_views_total, BatchState& B,
@@ -331,7 +332,8 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
                 V.campos[e] = (float)c;
             }
             for (int e = 0; e < 3; ++e) V.bg[e] = bg ? bg[e] : 0.f;
-            V.out_rgb = out_rgb[v];
+            V.out_rgb = out_rgb ? out_rgb[v] : nullptr;
+            V.out_rgb8 = out_rgb8 ? out_rgb8[v] : nullptr;
             V.out_T = out_T ? out_T[v] : nullptr;
             V.dL = nullptr;
             V.target = (targets && !target_u8) ? (const float*)targets[v] : nullptr;
@@ -580,6 +582,23 @@ swgs_status backward_batch(swgs_ctx* ctx, const swgs_gaussians* g, BatchState& B
                                  P<float>(B.grad2d), use_reg, use_reg ? loss : nullptr, s));
     }
     return SWGS_OK;
+}
+
+// Device bytes of one batch's data at the sizes it needed, with the element
+// sizes render_batch allocates: *rec = the record-proportional part (active
+// ids of each frame group's slots, the per-record arrays of the saved state
+// and the record-order scratch), *all = that plus the keys, tile lists, tile
+// ranges and per-pixel arrays.
+void batch_device_bytes(const BatchState& B, long long* rec, long long* all) {
+    const long long per_record = 3 * 16 + 4 + 4 + 8 + 4 + 2 * kRunRows  // saved records
+                                 + 4 * 4;                               // order, counts, offsets
+    const long long ids = 4LL * B.total_active;
+    *rec = ids + per_record * B.n_rec;
+    *all = *rec + 16LL * B.n_sort_keys     // super keys and values, ping-pong
+           + 4LL * B.n_keys                // per-tile lists
+           + 16LL * B.n_tiles              // tile ranges, counts, offsets
+           + 8LL * B.n_supers              // super-tile ranges
+           + 8LL * B.n_pix;                // final T and last
 }
 
 // ---- export helpers -------------------------------------------------------
@@ -972,7 +991,8 @@ swgs_status swgs_mature(swgs_ctx* ctx, const swgs_gaussians* buf, int64_t num_gs
 
 static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
                                    const swgs_view* views, const float* bg,
-                                   float* const* out_rgb, float* const* out_T,
+                                   float* const* out_rgb, uint8_t* const* out_rgb8,
+                                   float* const* out_T,
                                    const void* const* targets, int target_u8,
                                    float* const* dls, float* loss,
                                    int32_t batched, swgs_saved** saved, void* stream);
@@ -981,8 +1001,16 @@ swgs_status swgs_render_fwd(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_vi
                             const swgs_view* views, const float* bg, float* const* out_rgb,
                             float* const* out_T, int32_t batched, swgs_saved** saved,
                             void* stream) {
-    return render_fwd_impl(ctx, g, n_views, views, bg, out_rgb, out_T, nullptr, 0, nullptr,
-                           nullptr, batched, saved, stream);
+    return render_fwd_impl(ctx, g, n_views, views, bg, out_rgb, nullptr, out_T, nullptr, 0,
+                           nullptr, nullptr, batched, saved, stream);
+}
+
+swgs_status swgs_render_fwd_rgb8(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
+                                 const swgs_view* views, const float* bg,
+                                 uint8_t* const* out_rgb8, float* const* out_T, int32_t batched,
+                                 swgs_saved** saved, void* stream) {
+    return render_fwd_impl(ctx, g, n_views, views, bg, nullptr, out_rgb8, out_T, nullptr, 0,
+                           nullptr, nullptr, batched, saved, stream);
 }
 
 static swgs_status render_fwd_l1_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
@@ -998,7 +1026,7 @@ static swgs_status render_fwd_l1_impl(swgs_ctx* ctx, const swgs_gaussians* g, in
         if (!target[v] || !dL_drgb[v]) return fail(ctx, SWGS_EINVAL, "view %d: null target or dL", v);
     if (cudaMemsetAsync(loss, 0, sizeof(float), (cudaStream_t)stream) != cudaSuccess)
         return fail(ctx, SWGS_ECUDA, "clearing the loss failed");
-    return render_fwd_impl(ctx, g, n_views, views, bg, out_rgb, out_T, target, target_u8,
+    return render_fwd_impl(ctx, g, n_views, views, bg, out_rgb, nullptr, out_T, target, target_u8,
                            dL_drgb, loss, batched, saved, stream);
 }
 
@@ -1024,7 +1052,8 @@ swgs_status swgs_render_fwd_l1_u8(swgs_ctx* ctx, const swgs_gaussians* g, int32_
 
 static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32_t n_views,
                                    const swgs_view* views, const float* bg,
-                                   float* const* out_rgb, float* const* out_T,
+                                   float* const* out_rgb, uint8_t* const* out_rgb8,
+                                   float* const* out_T,
                                    const void* const* targets, int target_u8,
                                    float* const* dls, float* loss,
                                    int32_t batched, swgs_saved** saved, void* stream) {
@@ -1034,14 +1063,14 @@ static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32
     ctx->err.clear();
     swgs_status st = check_gaussians(ctx, g, true);
     if (st != SWGS_OK) return st;
-    if (n_views <= 0 || !views || !out_rgb)
+    if (n_views <= 0 || !views || (!out_rgb && !out_rgb8))
         return fail(ctx, SWGS_EINVAL, "need at least one view and its output buffer");
     if (n_views > kMaxViewsPerBatch)
         return fail(ctx, SWGS_EINVAL, "at most %d views per call", kMaxViewsPerBatch);
     for (int v = 0; v < n_views; ++v) {
         const swgs_view& w = views[v];
         if (w.width <= 0 || w.height <= 0 || w.width > 16384 || w.height > 16384 ||
-            !(w.fx > 0.f) || !(w.fy > 0.f) || !out_rgb[v])
+            !(w.fx > 0.f) || !(w.fy > 0.f) || (out_rgb ? !out_rgb[v] : !out_rgb8[v]))
             return fail(ctx, SWGS_EINVAL, "view %d: bad size, focal length or output", v);
     }
     if (saved) *saved = nullptr;
@@ -1089,7 +1118,8 @@ static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32
         }
     }
     for (int b = 0; b < nb; ++b) {
-        st = render_batch(ctx, g, views, parts[b], bg, out_rgb, out_T, targets, target_u8, dls,
+        st = render_batch(ctx, g, views, parts[b], bg, out_rgb, out_rgb8, out_T, targets,
+                          target_u8, dls,
                           loss, n_views,
                           sv->batches[b], pairs, s);
         if (st != SWGS_OK) {
@@ -1155,6 +1185,10 @@ swgs_status swgs_saved_query(swgs_ctx* ctx, const swgs_saved* saved, swgs_saved_
         o.n_pixels += B.n_pix;
         o.n_sort_keys += B.n_sort_keys;
         o.n_supers += B.n_supers;
+        long long rb = 0, db = 0;
+        batch_device_bytes(B, &rb, &db);
+        o.record_bytes += rb;
+        o.device_bytes += db;
     }
     if (saved->count_pairs && saved->pairs.p) {
         cudaStream_t s = ctx->last_stream;

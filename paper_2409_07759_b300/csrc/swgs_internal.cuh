@@ -32,7 +32,8 @@ struct ViewDev {
     float t[3];
     float campos[3];
     float bg[3];
-    float* out_rgb;    // [3,H,W]
+    float* out_rgb;    // [3,H,W] or null
+    uint8_t* out_rgb8; // [H,W,3] 8-bit RGB (round(255 clamp(c, 0, 1))) or null
     float* out_T;      // [H,W] or null
     const float* dL;   // [3,H,W] (backward only)
     const float* target;  // [3,H,W] (forward fused with the L1 term) or null
@@ -293,6 +294,11 @@ constexpr float kLogitDead = -0x1.52c582p+2f;
 // pair_v returns v = q + lo, q = -m/2 log2e, with lo added inside the last
 // FMA of the quadratic form; *au = unclamped o*G = 2^v, *a = min(0.99, *au).
 // ---------------------------------------------------------------------------
+// 8-bit display value of a colour channel: round(255 clamp(c, 0, 1)), ties to even.
+__device__ __forceinline__ uint8_t rgb8_of(float c) {
+    return (uint8_t)__float2int_rn(__fmul_rn(fminf(fmaxf(c, 0.f), 1.f), 255.f));
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -4,9 +4,12 @@ update_thread swaps in one slice per frame at the video frame rate).
 
 Many viewers send render requests (pose, resolution) for the current frame.
 Requests that arrive while others are on the GPU are admitted as soon as a
-worker stream frees up and the HBM budget allows, and are rendered together in
-one batched call; several worker streams keep batches overlapping on the
-device. The slot buffer stays on the GPU; each video frame, the slice
+worker stream frees up and the device memory they need fits in the HBM budget
+next to the batches already in flight (one byte counter over all workers),
+and are rendered together in one batched call; several worker streams keep
+batches overlapping on the device. Each image is delivered to pinned host
+memory, and a request's latency runs from its arrival to the end of that
+copy. The slot buffer stays on the GPU; each video frame, the slice
 (frame mod swin_size) is overwritten from pinned host memory on its own stream
 (Alg. 2 update_thread). CUDA events order every slice update after the
 renders already submitted (they read the old slice) and before the renders
@@ -18,6 +21,7 @@ from __future__ import annotations
 
 import gc
 import math
+import queue
 import sys
 import threading
 import time
@@ -44,7 +48,8 @@ class Request:
     t: np.ndarray
     frame: int = -1           # assigned when the request is submitted
     submit: float = -1.0
-    done: float = -1.0
+    rendered: float = -1.0    # the batch's render finished on the device
+    done: float = -1.0        # the image is in host memory
 
     @property
     def latency(self) -> float:
@@ -95,6 +100,10 @@ class ServeStats:
     mean_batch: float
     updates: int
     wall_s: float
+    p50_render_ms: float = 0.0     # arrival -> render finished (before delivery)
+    p99_render_ms: float = 0.0
+    inflight_hwm_bytes: float = 0.0  # largest admitted in-flight bytes
+    budget_bytes: float = 0.0
     latencies_ms: np.ndarray = field(repr=False, default=None)
 
     def as_dict(self):
@@ -103,15 +112,36 @@ class ServeStats:
         return d
 
 
+@dataclass
+class _Submitted:
+    """A batch on the device: its host images (filled by the delivery copies),
+    the events after its render and after its delivery, and its sizes."""
+    reqs: List[Request]
+    hosts: List[torch.Tensor]
+    ev_render: torch.cuda.Event
+    ev_copy: torch.cuda.Event
+    info: object
+    px: int
+
+
 class ServingLoop:
     """Continuous batching over `n_streams` worker streams (one libswgs context
-    each) plus one update stream."""
+    each, with its own delivery stream) plus one update stream.
+
+    A worker admits a batch, submits its render and the copies of its images
+    to pinned host memory, and goes on to admit the next batch; a completion
+    thread per worker waits for each batch's events, stamps its requests and
+    releases its bytes. Each worker has n_slots output slots: with two, one
+    batch can render while the previous one is being delivered. Images are
+    delivered as 8-bit RGB (the display format), a quarter of the float
+    image's bytes."""
 
     def __init__(self, state: api.GaussianState, swin_size: int, fps: float = 30.0,
                  n_streams: int = 2, max_batch: int = 16, hbm_budget_bytes: float = 16e9,
                  slice_provider=None, tile=(16, 16), batch=64, pixels_per_thread=4,
-                 first_frame: int = 0):
+                 first_frame: int = 0, n_slots: int = 1):
         self.state = state
+        self.n_slots = n_slots   # batches a worker may have in flight
         self.swin = swin_size
         self.fps = fps
         self.max_batch = max_batch
@@ -122,44 +152,77 @@ class ServingLoop:
                                        pixels_per_thread=pixels_per_thread)
                           for _ in range(n_streams)]
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.copy_streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.upd_renderer = api.Renderer()
         self.upd_stream = torch.cuda.Stream()
         self.submit_lock = threading.Lock()
         self.last_render_ev = [None] * n_streams
         self.update_ev: Optional[torch.cuda.Event] = None
-        # bytes per pixel of one request's device footprint (image, final T,
-        # last index, sort keys), refined from the key counts observed
-        self.bytes_per_px = 12 + 8 + 16 * 8.0
-        self.rec_bytes = 96.0 * state.n
-        self.out_pool: List[List[torch.Tensor]] = []   # filled by reserve()
+        # Device bytes of one request: view_bytes (its records: one per active
+        # Gaussian) + px_bytes per pixel (tile keys, tile lists and ranges, T,
+        # last). Both are re-measured from every batch's reported sizes
+        # (swgs_saved_info.device_bytes / record_bytes); these first values are
+        # replaced by reserve()'s probe.
+        self.view_bytes = 152.0 * state.n
+        self.px_bytes = 8.0 + 20.0 * 4.0
+        self.inflight = 0.0      # admitted bytes of the batches on the device
+        self.inflight_hwm = 0.0
+        # filled by reserve(): per worker and slot, max_batch 8-bit output
+        # images on the device and their pinned host delivery buffers
+        self.out_pool: List[List[List[torch.Tensor]]] = []
+        self.host_pool: List[List[torch.Tensor]] = []
         self.pool_px = 0
 
     # -- memory model for admission ---------------------------------------------
     def request_bytes(self, r: Request) -> float:
-        return self.bytes_per_px * r.width * r.height + self.rec_bytes
+        return self.view_bytes + self.px_bytes * r.width * r.height
+
+    def _measure(self, info, px: int):
+        """Re-estimate the per-view and per-pixel bytes from a batch's sizes."""
+        if info.n_views <= 0 or px <= 0:
+            return
+        vb = info.record_bytes / info.n_views
+        pb = (info.device_bytes - info.record_bytes) / px
+        self.view_bytes = 0.7 * self.view_bytes + 0.3 * vb
+        self.px_bytes = 0.7 * self.px_bytes + 0.3 * pb
 
     def reserve(self, width: int, height: int):
         """Grow every worker's scratch to the largest batch the admission rule
         lets through at width x height (max_batch requests within the HBM
-        budget), so that no device allocation happens while serving: a batch
-        larger than any seen before would otherwise grow the scratch mid-run
-        and stall every request queued behind it."""
+        budget), give each worker its output images and pinned host delivery
+        buffers, and measure the per-request bytes from a probe, so that no
+        allocation happens while serving: a batch larger than any seen before
+        would otherwise grow the scratch mid-run and stall every request queued
+        behind it."""
         R, t = orbit_pose(np.array([0.0, 0.0, 1.0]), 0.0, 0.0, 0.0)
         probe = Request(rid=-1, viewer=-1, arrival=0.0, width=width, height=height, R=R, t=t)
+        fx, fy, cx, cy = synth.intrinsics_for(width, height)
+        view = synth.View(width, height, fx, fy, cx, cy, probe.R, probe.t, self.frame)
+        # measure one request first, then size the batch the budget admits
+        _, saved = self.renderers[0].render(self.state, [view], keep_saved=True,
+                                            stream=self.streams[0])
+        info = saved.info()
+        self.view_bytes = float(info.record_bytes)
+        self.px_bytes = (info.device_bytes - info.record_bytes) / (width * height)
+        saved.release()
+        self.streams[0].synchronize()
         n, used = 0, 0.0
         while n < self.max_batch and (n == 0 or used + self.request_bytes(probe) <= self.budget):
             used += self.request_bytes(probe)
             n += 1
-        fx, fy, cx, cy = synth.intrinsics_for(width, height)
-        views = [synth.View(width, height, fx, fy, cx, cy, probe.R, probe.t, self.frame)] * n
-        self.out_pool = []
+        views = [view] * n
+        self.out_pool, self.host_pool = [], []
         self.pool_px = width * height
         for w, s in enumerate(self.streams):
             with torch.cuda.stream(s):
-                # the worker's output images: max_batch planar buffers of this size
-                self.out_pool.append([torch.empty(3 * self.pool_px, dtype=torch.float32,
-                                                  device="cuda") for _ in range(self.max_batch)])
-                self.renderers[w].render(self.state, views, stream=s)
+                self.out_pool.append([[torch.empty(3 * self.pool_px, dtype=torch.uint8,
+                                                   device="cuda")
+                                       for _ in range(self.max_batch)]
+                                      for _ in range(self.n_slots)])
+                self.renderers[w].render_rgb8(self.state, views, stream=s)
+            self.host_pool.append([torch.empty((self.max_batch, 3 * self.pool_px),
+                                               dtype=torch.uint8).pin_memory()
+                                   for _ in range(self.n_slots)])
             s.synchronize()
 
     # -- Alg. 2 update_thread ---------------------------------------------------
@@ -181,19 +244,27 @@ class ServingLoop:
             self.frame = frame
 
     # -- one batch on one worker stream -----------------------------------------
-    def render_batch(self, w: int, reqs: List[Request], t0: float):
-        """Render `reqs` together on worker stream w at the current frame."""
+    def submit_batch(self, w: int, reqs: List[Request], t0: float, slot: int = 0) -> _Submitted:
+        """Submit the render of `reqs` together on worker stream w at the
+        current frame into output slot `slot`, and the copies of the images to
+        pinned host memory on the worker's delivery stream; returns without
+        waiting for either."""
         s = self.streams[w]
-        pool = self.out_pool[w] if self.out_pool else None
-        if pool is not None and len(reqs) <= len(pool) and \
-                all(r.width * r.height <= self.pool_px for r in reqs):
+        pool = self.out_pool[w][slot] if self.out_pool else None
+        pooled = pool is not None and len(reqs) <= len(pool) and \
+            all(r.width * r.height <= self.pool_px for r in reqs)
+        if pooled:
             # views of the worker's reserved buffers: no allocation while serving
-            outs = [pool[i][:3 * r.width * r.height].view(3, r.height, r.width)
+            outs = [pool[i][:3 * r.width * r.height].view(r.height, r.width, 3)
                     for i, r in enumerate(reqs)]
+            hosts = [self.host_pool[w][slot][i][:3 * r.width * r.height]
+                     .view(r.height, r.width, 3) for i, r in enumerate(reqs)]
         else:
             with torch.cuda.stream(s):
-                outs = [torch.empty((3, r.height, r.width), dtype=torch.float32, device="cuda")
+                outs = [torch.empty((r.height, r.width, 3), dtype=torch.uint8, device="cuda")
                         for r in reqs]
+            hosts = [torch.empty((r.height, r.width, 3), dtype=torch.uint8).pin_memory()
+                     for r in reqs]
         with self.submit_lock:
             frame = self.frame
             views = []
@@ -205,22 +276,45 @@ class ServingLoop:
             now = time.perf_counter() - t0
             for r in reqs:
                 r.frame, r.submit = frame, now
-            _, saved = self.renderers[w].render(self.state, views, out=outs, keep_saved=True,
-                                                stream=s)
+            _, saved = self.renderers[w].render_rgb8(self.state, views, out=outs,
+                                                     keep_saved=True, stream=s)
             ev = torch.cuda.Event()
             ev.record(s)
             self.last_render_ev[w] = ev
+        # delivery on the worker's copy stream, after the render
+        cs = self.copy_streams[w]
+        cs.wait_event(ev)
+        with torch.cuda.stream(cs):
+            for h, o in zip(hosts, outs):
+                h.copy_(o, non_blocking=True)
+            dev = torch.cuda.Event()
+            dev.record(cs)
+        if not pooled:
+            # the unpooled images must outlive the copies
+            for o in outs:
+                o.record_stream(cs)
         info = saved.info()
         saved.release()
-        px = sum(r.width * r.height for r in reqs)
-        if px:
-            kpp = info.n_keys / px
-            self.bytes_per_px = 0.8 * self.bytes_per_px + 0.2 * (20 + 16 * kpp)
-        ev.synchronize()
+        return _Submitted(reqs, hosts, ev, dev, info, sum(r.width * r.height for r in reqs))
+
+    @staticmethod
+    def finish(b: _Submitted, t0: float):
+        """Wait for a submitted batch: stamp its requests when the render ends
+        and when its images are in host memory."""
+        b.ev_render.synchronize()
+        rendered = time.perf_counter() - t0
+        b.ev_copy.synchronize()
         done = time.perf_counter() - t0
-        for r in reqs:
+        for r in b.reqs:
+            r.rendered = rendered
             r.done = done
-        return outs
+
+    def render_batch(self, w: int, reqs: List[Request], t0: float, slot: int = 0):
+        """Render and deliver `reqs` on worker w and wait for them; returns
+        (host images: uint8 [H,W,3], batch sizes, pixels)."""
+        b = self.submit_batch(w, reqs, t0, slot)
+        self.finish(b, t0)
+        return b.hosts, b.info, b.px
 
     def run(self, requests: List[Request], duration_s: float, keep_images=False):
         """Serve `requests` (arrival times relative to the start) in real time
@@ -244,40 +338,74 @@ class ServingLoop:
                 gc.enable()
 
     def _run(self, requests: List[Request], duration_s: float, keep_images=False):
+        self.inflight, self.inflight_hwm = 0.0, 0.0
         pending = deque()
         todo = deque(requests)
         lock = threading.Lock()
         stop = threading.Event()
-        free = [True] * len(self.streams)
         cond = threading.Condition(lock)
+        on_device = [0]   # batches submitted and not yet delivered
         batches = []
         images = {}
         t0 = time.perf_counter()
         n_updates = [0]
 
-        def worker(w):
+        def admit():
+            """Take the longest run of pending requests (at most max_batch) whose
+            bytes fit in the budget next to the batches in flight; a request
+            that alone exceeds the budget is admitted only onto an idle device.
+            Called with the lock held; returns (batch, bytes)."""
+            batch, used = [], 0.0
+            while pending and len(batch) < self.max_batch:
+                need = self.request_bytes(pending[0])
+                if self.inflight + used + need > self.budget and \
+                        (batch or self.inflight > 0.0):
+                    break
+                used += need
+                batch.append(pending.popleft())
+            return batch, used
+
+        def completer(q, slots):
             while True:
-                with cond:
-                    while not stop.is_set() and not pending:
-                        cond.wait(0.0005)
-                    if stop.is_set() and not pending:
-                        return
-                    batch, used = [], 0.0
-                    while pending and len(batch) < self.max_batch:
-                        need = self.request_bytes(pending[0])
-                        if batch and used + need > self.budget:
-                            break
-                        used += need
-                        batch.append(pending.popleft())
-                    free[w] = False
-                outs = self.render_batch(w, batch, t0)
+                item = q.get()
+                if item is None:
+                    return
+                b, used = item
+                self.finish(b, t0)
                 if keep_images:
-                    for r, o in zip(batch, outs):
-                        images[r.rid] = o.clone() if self.out_pool else o
+                    for r, o in zip(b.reqs, b.hosts):
+                        images[r.rid] = o.clone()
                 with cond:
-                    batches.append(len(batch))
-                    free[w] = True
+                    self.inflight -= used
+                    self._measure(b.info, b.px)
+                    batches.append(len(b.reqs))
+                    on_device[0] -= 1
                     cond.notify_all()
+                slots.release()
+
+        def worker(w):
+            q = queue.Queue()
+            slots = threading.Semaphore(self.n_slots)
+            done_th = threading.Thread(target=completer, args=(q, slots), daemon=True)
+            done_th.start()
+            slot = 0
+            while True:
+                slots.acquire()
+                with cond:
+                    while True:
+                        if stop.is_set() and not pending:
+                            q.put(None)
+                            done_th.join()
+                            return
+                        batch, used = admit() if pending else ([], 0.0)
+                        if batch:
+                            break
+                        cond.wait(0.0005)
+                    self.inflight += used
+                    self.inflight_hwm = max(self.inflight_hwm, self.inflight)
+                    on_device[0] += 1
+                q.put((self.submit_batch(w, batch, t0, slot), used))
+                slot = (slot + 1) % self.n_slots
 
         threads = [threading.Thread(target=worker, args=(w,), daemon=True)
                    for w in range(len(self.streams))]
@@ -297,7 +425,7 @@ class ServingLoop:
                     moved = True
                 if moved:
                     cond.notify_all()
-                finished = not todo and not pending and all(free)
+                finished = not todo and not pending and on_device[0] == 0
             if finished and now >= duration_s:
                 break
             time.sleep(0.0002)
@@ -309,12 +437,17 @@ class ServingLoop:
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         lat = np.array([r.latency * 1e3 for r in requests if r.done >= 0])
+        rlat = np.array([(r.rendered - r.arrival) * 1e3 for r in requests if r.done >= 0])
         px = sum(r.width * r.height for r in requests if r.done >= 0)
         stats = ServeStats(n=len(lat), p50_ms=float(np.percentile(lat, 50)),
                            p99_ms=float(np.percentile(lat, 99)), mean_ms=float(lat.mean()),
                            mpix_per_s=px / 1e6 / wall, batches=len(batches),
                            mean_batch=float(np.mean(batches)) if batches else 0.0,
-                           updates=n_updates[0], wall_s=wall, latencies_ms=lat)
+                           updates=n_updates[0], wall_s=wall,
+                           p50_render_ms=float(np.percentile(rlat, 50)),
+                           p99_render_ms=float(np.percentile(rlat, 99)),
+                           inflight_hwm_bytes=float(self.inflight_hwm),
+                           budget_bytes=float(self.budget), latencies_ms=lat)
         return (stats, images) if keep_images else stats
 
     def close(self):
@@ -334,7 +467,7 @@ def serial_rates(state: api.GaussianState, requests: List[Request], frame: int,
         v = synth.View(q.width, q.height, fx, fy, cx, cy, q.R, q.t, frame)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        r.render(state, [v], batched=False)
+        r.render_rgb8(state, [v], batched=False)
         b.record()
         b.synchronize()
         times.append(a.elapsed_time(b))

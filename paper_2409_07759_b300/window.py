@@ -20,7 +20,10 @@ DEFAULT_SGLD = dict(lr_means=1.6e-4, lr_log_scales=5e-3, lr_quats=1e-3, lr_logit
                     # Alg. 1 reg(): the regulariser weights of Sec. 8.1
                     opacity_reg=2e-2, scale_reg=1e-2,
                     # Sec. 4.5.1 means-gradient scale (1 = off); ClipTrainer sets the window
-                    mean_grad_decay=1.0, window_start=0, swin_size=0)
+                    mean_grad_decay=1.0, window_start=0, swin_size=0,
+                    # the optimiser step leaves the gradients zero for the next
+                    # backward (no separate clearing pass)
+                    clear_grads=1)
 
 
 def _flat_views(n: int, K: int, device="cuda"):
@@ -135,7 +138,9 @@ class WindowTrainer:
         _, _, _, saved = self.r.render_l1(self.state, self.views, self.targets, bg=self.bg,
                                           batched=self.batched, out=self.images,
                                           dL_out=self.dl, loss_out=self.loss)
-        self._gflat.zero_()
+        if not self.params.get("clear_grads", 0):
+            # the last step kept its gradients: clear them for this backward
+            self._gflat.zero_()
         reg = None
         if self.params.get("opacity_reg", 0.0) or self.params.get("scale_reg", 0.0):
             reg = dict(opacity_reg=self.params["opacity_reg"],

@@ -273,3 +273,34 @@ def test_row_exchange_through_nccl():
         r.close()
     finally:
         dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("adam_on", [1, 0])
+def test_sgld_step_clears_gradients_it_reads(R, adam_on):
+    """clear_grads = 1: with or without the Adam step, every gradient element of
+    an eligible slot is zero after the step and the others are untouched. The
+    parameters move exactly as with clear_grads = 0."""
+    from paper_2409_07759_b300 import api
+    sc, grads, adam = _scene(n=9001)
+    frames = [145, 146]
+    out = []
+    for clear in (0, 1):
+        st = _state(sc)
+        g = api.GaussianGrads(*[torch.from_numpy(grads[k]).cuda() for k in NAMES], sc.sh_degree)
+        ad = {k: torch.from_numpy(v.copy()).cuda() for k, v in adam.items()}
+        R.sgld_step(st, frames, dict(adam=adam_on, relocate=1, lr_means=1e-3, noise_lr=5e4,
+                                     noise_k=100.0, noise_t=0.005, beta1=0.9, beta2=0.999,
+                                     eps=1e-15, lr_log_scales=5e-3, lr_quats=1e-3,
+                                     lr_logits=5e-2, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4,
+                                     max_n=51, clear_grads=clear), 9, 4, grads=g, adam=ad)
+        torch.cuda.synchronize()
+        out.append((st, g))
+    f = np.asarray(frames)
+    elig = ((sc.start[:, None] <= f[None, :]) & (f[None, :] < sc.expire[:, None])).any(1) \
+        & (sc.frozen == 0)
+    for k in NAMES:
+        assert torch.equal(getattr(out[0][0], k), getattr(out[1][0], k)), k
+        kept, cleared = _np(getattr(out[0][1], k)), _np(getattr(out[1][1], k))
+        np.testing.assert_array_equal(kept, grads[k])
+        assert not np.any(cleared[elig])
+        np.testing.assert_array_equal(cleared[~elig], grads[k][~elig])

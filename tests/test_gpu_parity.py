@@ -489,3 +489,19 @@ def test_backward_forms_agree_on_covered_tiles():
             a, b = grads[1][k], grads[ppt][k]
             scale = max(float(np.abs(a).max()), 1e-30)
             assert float(np.abs(a - b).max()) <= 1e-5 * scale, (ppt, k)
+
+
+def test_rgb8_images_are_the_quantised_float_images(R):
+    """swgs_render_fwd_rgb8 writes round(255 clamp(c, 0, 1)) of the float
+    render's channels, interleaved [H,W,3], bit for bit (ragged sizes, a
+    background, several views and frames in one batch)."""
+    sc, views, _ = synth.config2(width=203, height=117, n=20000, n_frames=2, per_frame=2)
+    st = _state(sc)
+    bg = (0.1, 0.7, 1.3)  # a channel above 1 exercises the clamp
+    f32, _ = R.render(st, views, bg=bg)
+    u8, saved = R.render_rgb8(st, views, bg=bg, keep_saved=True)
+    for a, b in zip(f32, u8):
+        want = np.rint(np.clip(_np(a), 0.0, 1.0).astype(np.float32) * np.float32(255.0))
+        np.testing.assert_array_equal(_np(b), want.transpose(1, 2, 0).astype(np.uint8))
+    assert saved.info().n_views == len(views)
+    saved.release()

@@ -48,8 +48,8 @@ def test_alone_equals_mixed_batch():
     from paper_2409_07759_b300 import serving
     _, st, _, loop = _loop()
     reqs = serving.make_requests(6, 5.0, 2.0, seed=1, resolutions=RES)[:5]
-    alone = [loop.render_batch(0, [r], 0.0)[0] for r in reqs]
-    mixed = loop.render_batch(1, reqs, 0.0)
+    alone = [loop.render_batch(0, [r], 0.0)[0][0] for r in reqs]
+    mixed = loop.render_batch(1, reqs, 0.0)[0]
     torch.cuda.synchronize()
     for a, b in zip(alone, mixed):
         assert torch.equal(a, b)
@@ -83,12 +83,32 @@ def test_run_serves_everything_and_swaps_slices(oracle_mod):
 
 
 def test_budget_limits_batches():
-    """With a budget smaller than two requests, every batch holds one request."""
+    """With a budget smaller than two requests, every batch holds one request
+    (and only one batch is in flight at a time)."""
     from paper_2409_07759_b300 import serving
     _, st, _, loop = _loop(budget=1.0)
     reqs = serving.make_requests(8, 30.0, 0.5, seed=3, resolutions=RES)
     stats = loop.run(reqs, 0.5)
     assert stats.n == len(reqs) and stats.mean_batch == 1.0
+    loop.close()
+
+
+def test_budget_bounds_bytes_in_flight_across_workers():
+    """A budget of about three requests and three worker streams under heavy
+    load: the admitted bytes of the batches in flight together (one counter
+    over all workers) never exceed the budget, and the budget binds."""
+    from paper_2409_07759_b300 import serving
+    _, st, _, loop = _loop(n_streams=3)
+    loop.reserve(640, 360)
+    one = loop.request_bytes(serving.make_requests(1, 5.0, 1.0, seed=9,
+                                                   resolutions=[(640, 360)])[0])
+    assert one > 152 * st.n * 0.9  # the measured size: about one record per Gaussian
+    loop.budget = 3.2 * one
+    reqs = serving.make_requests(16, 60.0, 0.6, seed=6, resolutions=RES)
+    stats = loop.run(reqs, 0.6)
+    assert stats.n == len(reqs)
+    assert 2.0 * one < stats.inflight_hwm_bytes <= loop.budget, (stats, one)
+    assert stats.mean_batch <= 3.0
     loop.close()
 
 
@@ -99,17 +119,18 @@ def test_reserved_buffers_give_the_same_images():
     from paper_2409_07759_b300 import serving
     _, st, _, loop = _loop()
     reqs = serving.make_requests(6, 5.0, 2.0, seed=1, resolutions=RES)[:5]
-    before = [o.clone() for o in loop.render_batch(1, reqs, 0.0)]
+    before = [o.clone() for o in loop.render_batch(1, reqs, 0.0)[0]]
     loop.reserve(640, 360)
-    after = loop.render_batch(1, reqs, 0.0)
-    pool_ptrs = {t.data_ptr() for t in loop.out_pool[1]}
-    assert all(o.data_ptr() in pool_ptrs for o in after)
-    torch.cuda.synchronize()
+    after = loop.render_batch(1, reqs, 0.0)[0]
+    # delivered into the worker's pinned host rows
+    base = loop.host_pool[1][0].data_ptr()
+    end = base + loop.host_pool[1][0].numel() * 4
+    assert all(base <= o.data_ptr() < end and o.is_pinned() for o in after)
     for a, b in zip(before, after):
         assert torch.equal(a, b)
     run = serving.make_requests(8, 30.0, 0.5, seed=5, resolutions=RES)
     stats, images = loop.run(run, 0.5, keep_images=True)
     assert stats.n == len(run) == len(images)
-    ptrs = {t.data_ptr() for p in loop.out_pool for t in p}
-    assert all(im.data_ptr() not in ptrs for im in images.values())
+    assert all(not (base <= im.data_ptr() < end) for im in images.values())
+    assert stats.p99_ms >= stats.p99_render_ms
     loop.close()

@@ -35,7 +35,7 @@ def test_window_step_matches_explicit_calls():
     # noise and relocation only, the step's result does not depend on the
     # gradient's rounding and must match bit for bit; the gradients are
     # compared on their own.
-    params = dict(DEFAULT_SGLD, adam=0)
+    params = dict(DEFAULT_SGLD, adam=0, clear_grads=0)  # keep the gradients to compare
     tr = WindowTrainer(r, st_a, views, tg, seed=5, params=params)
     loss_a = float(tr.step(7).item())
     # the same step by hand
