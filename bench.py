@@ -108,6 +108,8 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=1,
                     help="batches each serving worker may have in flight")
     ap.add_argument("--hbm-budget-gb", type=float, default=24.0)
+    ap.add_argument("--sync-sizing", action="store_true",
+                    help="size every forward exactly (two host round trips per batch)")
     ap.add_argument("--sweep-seconds", type=float, default=2.5,
                     help="seconds per rate of the serving sweep (0: no sweep)")
     return ap.parse_args()
@@ -565,7 +567,8 @@ def arm_config(args, views, world=1):
             "pixels_per_thread": args.ppt,
             "bwd_pixels_per_thread": args.bwd_ppt, "bwd_batch": args.bwd_batch,
             "targets": ("8-bit RGB frames (k/255)" if args.targets == "u8" else "float32 RGB"),
-            "parallelism": f"dp{world}", "l2": "flushed (256 MB write) before each step"}
+            "parallelism": f"dp{world}", "l2": "flushed (256 MB write) before each step",
+            "sizing": "deferred (no host round trip in a step)"}
 
 
 def run_reference(args):
@@ -641,8 +644,10 @@ def main():
     tgt_host = [torch.from_numpy(t).pin_memory() for t in targets]
     tgt_dev = [t.cuda() for t in tgt_host]
     tw, th = (int(x) for x in args.tile.split("x"))
+    # deferred sizing: after the first step no forward waits for the device
     r = api.Renderer(tile=(tw, th), batch=args.batch, pixels_per_thread=args.ppt,
-                     bwd_pixels_per_thread=args.bwd_ppt, bwd_batch=args.bwd_batch)
+                     bwd_pixels_per_thread=args.bwd_ppt, bwd_batch=args.bwd_batch,
+                     deferred_sizing=not args.sync_sizing)
     reducer = None
     if world > 1:
         # one all-reduce of the flat gradient buffer (weighted by view share)
@@ -699,6 +704,7 @@ def main():
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
+    tr.settle()
     launches = api.Renderer.kernel_launches() - launches0
     prof = r.profile_read(reset=True)
     r.profile(False)

@@ -35,8 +35,10 @@ typedef enum swgs_status {
     SWGS_ENOMEM = 2,   /* the allocator failed */
     SWGS_ECUDA = 3,    /* a CUDA runtime call failed */
     SWGS_ETIMEOUT = 4, /* a bounded device wait expired */
-    SWGS_EDEVICE = 5,  /* a kernel raised the device error word */
-    SWGS_ESTATE = 6    /* stale or mismatched saved state / slice */
+    SWGS_EDEVICE = 5,  /* a kernel raised the device error word, or a batch
+                          outgrew the capacities of deferred sizing */
+    SWGS_ESTATE = 6,   /* stale or mismatched saved state / slice */
+    SWGS_EPENDING = 7  /* deferred sizing: the call's result has not arrived yet */
 } swgs_status;
 
 /* Scratch allocator: returns device memory usable on `stream` (NULL on
@@ -61,6 +63,17 @@ typedef struct swgs_config {
                                  look-back; inputs below 2^30 keys); 0: three
                                  kernels per pass (histogram, scan, scatter).
                                  Same sorted order either way. */
+    int32_t deferred_sizing;  /* 0: a forward reads its active and key counts back
+                                 (two stream synchronisations per batch) and sizes
+                                 its buffers exactly. 1: after a context's first
+                                 forward, buffers are sized from capacities learned
+                                 on earlier calls (1/8 headroom) and the counts
+                                 stay on the device: no synchronisation. A batch
+                                 that outgrows them renders background, makes this
+                                 context's next swgs_sgld_step do nothing, and is
+                                 reported by swgs_saved_status (SWGS_EDEVICE: render
+                                 again; the capacities have grown). Needs
+                                 sort_single_pass = 1. */
 } swgs_config;
 
 /*
@@ -360,6 +373,17 @@ typedef struct swgs_saved_info {
 } swgs_saved_info;
 
 swgs_status swgs_saved_query(swgs_ctx *ctx, const swgs_saved *saved, swgs_saved_info *info);
+
+/* Outcome of the forward that made `saved`. With deferred sizing the forward
+ * returned before its counts were known: wait = 1 blocks until its batches'
+ * totals have arrived, wait = 0 returns SWGS_EPENDING if they have not.
+ * SWGS_OK; SWGS_EDEVICE: a batch outgrew the capacities (its images are
+ * background, its backward does nothing): render the views again -- the
+ * context's capacities have grown to what it needed; SWGS_ETIMEOUT: a sort's
+ * look-back wait ran out. Without deferred sizing the forward already
+ * returned its status and this returns SWGS_OK. swgs_saved_query,
+ * swgs_saved_count and swgs_saved_export wait the same way. */
+swgs_status swgs_saved_status(swgs_ctx *ctx, const swgs_saved *saved, int32_t wait);
 
 /* Intermediate arrays of a saved forward, copied to `dst` (device or host,
  * `bytes` must match). Records, keys and tiles are concatenated over batches

@@ -11,9 +11,10 @@ from pathlib import Path
 
 LIB_PATH = Path(__file__).resolve().parent / "libswgs.so"
 
-SWGS_OK, SWGS_EINVAL, SWGS_ENOMEM, SWGS_ECUDA, SWGS_ETIMEOUT, SWGS_EDEVICE, SWGS_ESTATE = range(7)
+(SWGS_OK, SWGS_EINVAL, SWGS_ENOMEM, SWGS_ECUDA, SWGS_ETIMEOUT, SWGS_EDEVICE, SWGS_ESTATE,
+ SWGS_EPENDING) = range(8)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EDEVICE",
-                6: "ESTATE"}
+                6: "ESTATE", 7: "EPENDING"}
 
 EXPORT_RECORD_SLOT = 0
 EXPORT_RECORD_VIEW = 1
@@ -36,7 +37,7 @@ class SwgsConfig(C.Structure):
                 ("near_plane", C.c_float), ("blocks_per_sm", C.c_int32),
                 ("count_pairs", C.c_int32), ("pixels_per_thread", C.c_int32),
                 ("bwd_pixels_per_thread", C.c_int32), ("bwd_batch", C.c_int32),
-                ("sort_single_pass", C.c_int32)]
+                ("sort_single_pass", C.c_int32), ("deferred_sizing", C.c_int32)]
 
 
 class SwgsGaussians(C.Structure):
@@ -143,6 +144,7 @@ PROTOTYPES = [
                                   C.POINTER(C.c_void_p), C.POINTER(SwgsGaussians), C.c_void_p]),
     ("swgs_saved_release", C.c_int, [C.c_void_p, C.c_void_p]),
     ("swgs_saved_query", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(SwgsSavedInfo)]),
+    ("swgs_saved_status", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
     ("swgs_saved_export", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t,
                                     C.c_void_p]),
     ("swgs_saved_count", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),

@@ -183,6 +183,12 @@ class SavedState:
         except Exception:
             pass
 
+    def status(self, wait: bool = True) -> int:
+        """The forward's outcome (see swgs_saved_status): _abi.SWGS_OK, SWGS_EDEVICE
+        (a batch outgrew the deferred capacities: render again), SWGS_ETIMEOUT,
+        or with wait=False SWGS_EPENDING if it has not arrived yet."""
+        return int(_abi.load().swgs_saved_status(self.renderer.ctx, self.handle, int(bool(wait))))
+
     def info(self) -> _abi.SwgsSavedInfo:
         inf = _abi.SwgsSavedInfo()
         self.renderer._check(_abi.load().swgs_saved_query(self.renderer.ctx, self.handle,
@@ -215,7 +221,7 @@ class Renderer:
     def __init__(self, tile=(16, 16), batch=64, near_plane=0.2, blocks_per_sm=0,
                  count_pairs=False, pixels_per_thread=None, bwd_pixels_per_thread=None,
                  bwd_batch=64, use_torch_allocator=True, alloc_guard=None,
-                 sort_single_pass=True):
+                 sort_single_pass=True, deferred_sizing=False):
         if pixels_per_thread is None:      # 8x8 tiles hold at most 2 pixels per thread
             pixels_per_thread = 2 if tuple(tile) == (8, 8) else 4
         if bwd_pixels_per_thread is None:
@@ -232,6 +238,9 @@ class Renderer:
         cfg.bwd_pixels_per_thread = int(bwd_pixels_per_thread)
         cfg.bwd_batch = int(bwd_batch)
         cfg.sort_single_pass = int(bool(sort_single_pass))
+        # True: after the first forward, no stream synchronisation; the caller
+        # checks SavedState.status() (the trainer and the server do)
+        cfg.deferred_sizing = int(bool(deferred_sizing))
         self.cfg = cfg
         self.alloc_guard = alloc_guard
         self.device = torch.cuda.current_device()

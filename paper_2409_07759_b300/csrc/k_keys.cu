@@ -20,8 +20,9 @@ namespace swgs {
 __global__ void __launch_bounds__(256)
 gather_supers_kernel(const uint32_t* __restrict__ order, Records rec, int sx, int sy,
                      uint32_t* __restrict__ out, unsigned long long* __restrict__ exact,
-                     long long n) {
+                     long long cap, const unsigned long long* __restrict__ n_dev) {
     __shared__ unsigned long long part[8];
+    const long long n = dev_count(cap, n_dev);
     unsigned long long t = 0;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
@@ -45,12 +46,12 @@ gather_supers_kernel(const uint32_t* __restrict__ order, Records rec, int sx, in
 
 cudaError_t launch_gather_supers(const uint32_t* order, const Records rec, int sx, int sy,
                                  uint32_t* out, unsigned long long* exact, long long n,
-                                 int num_sms, cudaStream_t s) {
+                                 int num_sms, cudaStream_t s, const unsigned long long* n_dev) {
     if (n <= 0) return cudaSuccess;
     long long grid = div_up(n, 256);
     if (grid > 8LL * num_sms) grid = 8LL * num_sms;
     note_launch();
-    gather_supers_kernel<<<(unsigned)grid, 256, 0, s>>>(order, rec, sx, sy, out, exact, n);
+    gather_supers_kernel<<<(unsigned)grid, 256, 0, s>>>(order, rec, sx, sy, out, exact, n, n_dev);
     return cudaGetLastError();
 }
 
@@ -88,9 +89,10 @@ __global__ void __launch_bounds__(256)
 emit_supers_kernel(const uint32_t* __restrict__ order, const uint32_t* __restrict__ offsets,
                    long long n_rec, Records rec, const ViewDev* __restrict__ views, int n_views,
                    int tile_w, int tile_h, uint32_t* __restrict__ keys,
-                   uint32_t* __restrict__ vals) {
+                   uint32_t* __restrict__ vals, const unsigned long long* __restrict__ n_dev) {
     static_assert(SX * SY == 16, "16 tiles per super tile");
     constexpr int sx = SX, sy = SY;
+    n_rec = dev_count(n_rec, n_dev);
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_rec;
          k += (long long)gridDim.x * blockDim.x) {
         const uint32_t r = order[k];
@@ -136,17 +138,19 @@ emit_supers_kernel(const uint32_t* __restrict__ order, const uint32_t* __restric
 cudaError_t launch_emit_supers(const uint32_t* order, const uint32_t* offsets, long long n_rec,
                                const Records rec, const ViewDev* views, int n_views, int sx,
                                int sy, int tile_w, int tile_h, int num_sms, uint32_t* keys,
-                               uint32_t* vals, cudaStream_t s) {
+                               uint32_t* vals, cudaStream_t s, const unsigned long long* n_dev) {
     if (n_rec <= 0) return cudaSuccess;
     long long blocks = div_up(n_rec, 256);
     if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
     note_launch();
     if (sx == 4 && sy == 4)
         emit_supers_kernel<4, 4><<<(int)blocks, 256, 0, s>>>(order, offsets, n_rec, rec, views,
-                                                             n_views, tile_w, tile_h, keys, vals);
+                                                             n_views, tile_w, tile_h, keys, vals,
+                                                             n_dev);
     else if (sx == 2 && sy == 8)
         emit_supers_kernel<2, 8><<<(int)blocks, 256, 0, s>>>(order, offsets, n_rec, rec, views,
-                                                             n_views, tile_w, tile_h, keys, vals);
+                                                             n_views, tile_w, tile_h, keys, vals,
+                                                             n_dev);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -300,8 +304,10 @@ cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, cons
 
 // sranges[t] = [first, last+1) of super tile t (the low 16 key bits) in the
 // sorted super keys (sranges zeroed before).
-__global__ void super_ranges_kernel(const uint32_t* __restrict__ keys, long long n,
-                                    long long n_supers, int2* __restrict__ ranges) {
+__global__ void super_ranges_kernel(const uint32_t* __restrict__ keys, long long cap,
+                                    long long n_supers, int2* __restrict__ ranges,
+                                    const unsigned long long* __restrict__ n_dev) {
+    const long long n = dev_count(cap, n_dev);
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t t = keys[i] & 0xffffu;
@@ -311,10 +317,10 @@ __global__ void super_ranges_kernel(const uint32_t* __restrict__ keys, long long
 }
 
 cudaError_t launch_super_ranges(const uint32_t* keys, long long n, long long n_supers,
-                                int2* ranges, cudaStream_t s) {
+                                int2* ranges, cudaStream_t s, const unsigned long long* n_dev) {
     if (n <= 0) return cudaSuccess;
     note_launch();
-    super_ranges_kernel<<<div_up(n, 256), 256, 0, s>>>(keys, n, n_supers, ranges);
+    super_ranges_kernel<<<div_up(n, 256), 256, 0, s>>>(keys, n, n_supers, ranges, n_dev);
     return cudaGetLastError();
 }
 

@@ -113,4 +113,83 @@ cudaError_t launch_copy_slice(const swgs_gaussians& dst, long long first, long l
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Deferred sizing: the tables and totals of a batch from device counts.
+// ---------------------------------------------------------------------------
+__global__ void plan_kernel(GroupDev* groups, int n_groups, ViewDev* views,
+                            const int32_t* __restrict__ counts, unsigned long long* totals,
+                            long long rec_cap) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    long long act = 0, rec = 0;
+    for (int k = 0; k < n_groups; ++k) {
+        GroupDev& G = groups[k];
+        const int n = counts[k];
+        G.n_active = n;
+        G.act_base = (int)act;
+        G.rec_base = (int)rec;
+        G.reg_o = n > 0 ? (float)(G.reg_o_num / (double)n) : 0.f;
+        G.reg_s = n > 0 ? (float)(G.reg_s_num / (double)n) : 0.f;
+        for (int j = 0; j < G.view_count; ++j) {
+            ViewDev& V = views[G.view_begin + j];
+            V.rec_base = (int)(rec + (long long)j * n);
+            V.n_rec = n;
+        }
+        act += n;
+        rec += (long long)n * G.view_count;
+    }
+    if (totals) {
+        totals[kTotNeedRecords] = (unsigned long long)rec;
+        if (rec > rec_cap) {
+            totals[kTotStatus] |= 1ull;
+            rec = 0;
+            act = 0;
+        }
+        totals[kTotRecords] = (unsigned long long)rec;
+        totals[kTotActive] = (unsigned long long)act;
+    }
+}
+
+cudaError_t launch_plan(GroupDev* groups, int n_groups, ViewDev* views, const int32_t* counts,
+                        unsigned long long* totals, long long rec_cap, cudaStream_t s) {
+    note_launch();
+    plan_kernel<<<1, 32, 0, s>>>(groups, n_groups, views, counts, totals, rec_cap);
+    return cudaGetLastError();
+}
+
+__global__ void check_keys_kernel(const unsigned long long* __restrict__ key_totals,
+                                  unsigned long long* totals, long long super_cap,
+                                  long long key_cap, uint32_t* sort_err, uint32_t* gate) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long st = totals[kTotStatus];
+    if (sort_err && *sort_err) {
+        st |= 4ull;
+        *sort_err = 0u;
+    }
+    if (key_totals) {
+        // before the key emission: a wait that ran out left the depth order
+        // unusable, so it stops the batch like an overflow does
+        const unsigned long long sk = key_totals[0], tk = key_totals[1];
+        totals[kTotNeedSuperKeys] = sk;
+        totals[kTotNeedTileKeys] = tk;
+        if ((long long)sk > super_cap || (long long)tk > key_cap) st |= 2ull;
+        const bool stop = (st & 7ull) != 0ull;
+        totals[kTotSuperKeys] = stop ? 0ull : sk;
+        totals[kTotTileKeys] = stop ? 0ull : tk;
+        if (stop) {
+            totals[kTotRecords] = 0ull;
+            totals[kTotActive] = 0ull;
+        }
+    }
+    totals[kTotStatus] = st;
+    if (gate && st) atomicOr(gate, (uint32_t)st);
+}
+
+cudaError_t launch_check_keys(const unsigned long long* key_totals, unsigned long long* totals,
+                              long long super_cap, long long key_cap, uint32_t* sort_err,
+                              uint32_t* gate, cudaStream_t s) {
+    note_launch();
+    check_keys_kernel<<<1, 32, 0, s>>>(key_totals, totals, super_cap, key_cap, sort_err, gate);
+    return cudaGetLastError();
+}
+
 }  // namespace swgs

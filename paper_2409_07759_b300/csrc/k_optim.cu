@@ -20,6 +20,7 @@ struct SgldArgs {
     swgs_adam_state adam;
     int has_grads, has_adam;
     const uint8_t* elig;  // eligible slots (launch_eligible)
+    const uint32_t* gate;  // nonzero: the forward before this step failed, do nothing
     swgs_sgld_params p;
     float bc1, bc2;  // Adam bias corrections 1 - beta^(step+1)
     unsigned long long seed, step;
@@ -195,6 +196,7 @@ __device__ __forceinline__ void adam_array(const SgldArgs& a, float* P, float* M
 // blockIdx.y picks the array: 0 means, 1 log-scales, 2 quaternions, 3 opacity
 // logits, 4 SH.
 __global__ void __launch_bounds__(256) adam_kernel(SgldArgs a) {
+    if (a.gate && *a.gate) return;
     const swgs_gaussians& g = a.g;
     const swgs_gaussians& d = a.grads;
     const swgs_adam_state& m = a.adam;
@@ -216,6 +218,7 @@ __global__ void __launch_bounds__(256) adam_kernel(SgldArgs a) {
 }
 
 __global__ void __launch_bounds__(256) sgld_kernel(SgldArgs a) {
+    if (a.gate && *a.gate) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.g.capacity) return;
     if (!a.elig[i]) return;
@@ -265,10 +268,11 @@ __global__ void __launch_bounds__(256) sgld_kernel(SgldArgs a) {
 cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
                         const swgs_adam_state* adam, const uint8_t* elig,
                         const swgs_sgld_params& p, unsigned long long seed,
-                        unsigned long long step, cudaStream_t s) {
+                        unsigned long long step, cudaStream_t s, const uint32_t* gate) {
     if (g.capacity <= 0) return cudaSuccess;
     SgldArgs a{};
     a.g = g;
+    a.gate = gate;
     if (grads) a.grads = *grads;
     if (adam) a.adam = *adam;
     a.has_grads = grads != nullptr;
@@ -299,6 +303,7 @@ cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
 struct RelocArgs {
     swgs_gaussians g;
     const uint8_t* elig;
+    const uint32_t* gate;  // nonzero: no slot is dead (nothing is relocated)
 };
 
 // weight = floor(sigmoid(logit) 2^32) for alive eligible slots, 0 otherwise;
@@ -311,7 +316,7 @@ reloc_weights_kernel(RelocArgs a, unsigned long long* __restrict__ weights,
     if (i >= a.g.capacity) return;
     unsigned long long w = 0;
     uint8_t d = 0;
-    if (a.elig[i]) {
+    if (a.elig[i] && !(a.gate && *a.gate)) {
         const float lg = a.g.opacity_logits[i];
         if (lg <= kLogitDead) {
             d = 1;
@@ -328,10 +333,12 @@ reloc_weights_kernel(RelocArgs a, unsigned long long* __restrict__ weights,
 }
 
 cudaError_t launch_reloc_weights(const swgs_gaussians& g, const uint8_t* elig,
-                                 unsigned long long* weights, uint8_t* dead, cudaStream_t s) {
+                                 unsigned long long* weights, uint8_t* dead, cudaStream_t s,
+                                 const uint32_t* gate) {
     RelocArgs a{};
     a.g = g;
     a.elig = elig;
+    a.gate = gate;
     note_launch();
     reloc_weights_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(a, weights, dead);
     return cudaGetLastError();

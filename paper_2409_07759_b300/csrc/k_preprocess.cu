@@ -190,10 +190,11 @@ __device__ __forceinline__ int find_group_by_record(const GroupDev* groups, int 
 // The tile shape (TW x TH pixels; super tiles of SX x SY tiles) is a template
 // parameter, so the tile arithmetic of the row runs folds to constants.
 template <int TW, int TH>
-__global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_rec) {
+__global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_rec,
+                                                         const unsigned long long* n_dev) {
     constexpr int SX = TW == 32 ? 2 : 4, SY = TW == 32 ? 8 : 4;
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rec) return;
+    if (r >= dev_count(n_rec, n_dev)) return;
     const int gi = find_group_by_record(a.groups, a.n_groups, r);
     const GroupDev G = a.groups[gi];
     const long long off = r - G.rec_base;
@@ -342,18 +343,18 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_
 cudaError_t launch_preprocess(const swgs_gaussians& g, const ViewDev* views, const GroupDev* groups,
                               int n_groups, const int32_t* ids, long long total_active,
                               long long n_rec, int tile_w, int tile_h, float near_plane,
-                              Records rec, cudaStream_t s) {
+                              Records rec, cudaStream_t s, const unsigned long long* n_dev) {
     if (n_rec <= 0) return cudaSuccess;
     PreArgs a{g, views, groups, n_groups, ids, total_active, tile_w, tile_h, super_w(tile_w),
               super_h(tile_w), near_plane, rec};
     note_launch();
     const int blocks = div_up(n_rec, 256);
     if (tile_w == 16 && tile_h == 16)
-        preprocess_kernel<16, 16><<<blocks, 256, 0, s>>>(a, n_rec);
+        preprocess_kernel<16, 16><<<blocks, 256, 0, s>>>(a, n_rec, n_dev);
     else if (tile_w == 8 && tile_h == 8)
-        preprocess_kernel<8, 8><<<blocks, 256, 0, s>>>(a, n_rec);
+        preprocess_kernel<8, 8><<<blocks, 256, 0, s>>>(a, n_rec, n_dev);
     else if (tile_w == 32 && tile_h == 8)
-        preprocess_kernel<32, 8><<<blocks, 256, 0, s>>>(a, n_rec);
+        preprocess_kernel<32, 8><<<blocks, 256, 0, s>>>(a, n_rec, n_dev);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -374,6 +375,7 @@ struct PreBwdArgs {
     const float* grad2d;
     bool reg;      // regulariser weights in the groups
     float* loss;   // regulariser value added here (or null)
+    const unsigned long long* n_dev;  // deferred sizing: the true total_active
 };
 
 // Alg. 1 reg(): with w_o = opacity_reg vc / (V n), w_s = scale_reg vc / (3 V n)
@@ -399,7 +401,7 @@ __device__ __forceinline__ void reg_loss_add(float v, float* loss) {
 
 __global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in = t < a.total_active;
+    const bool in = t < dev_count(a.total_active, a.n_dev);
     const int gi = in ? find_group(a.groups, a.n_groups, t) : 0;
     const long long slot = in ? a.ids[t] : 0;
     if (a.reg && a.loss) {
@@ -621,9 +623,10 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {
 cudaError_t launch_preprocess_bwd(const swgs_gaussians& g, const swgs_gaussians& grads,
                                   const ViewDev* views, const GroupDev* groups, int n_groups,
                                   const int32_t* ids, long long total_active,
-                                  const float* grad2d, bool reg, float* loss, cudaStream_t s) {
+                                  const float* grad2d, bool reg, float* loss, cudaStream_t s,
+                                  const unsigned long long* n_dev) {
     if (total_active <= 0) return cudaSuccess;
-    PreBwdArgs a{g, grads, views, groups, n_groups, ids, total_active, grad2d, reg, loss};
+    PreBwdArgs a{g, grads, views, groups, n_groups, ids, total_active, grad2d, reg, loss, n_dev};
     note_launch();
     preprocess_bwd_kernel<<<div_up(total_active, 128), 128, 0, s>>>(a);
     return cudaGetLastError();

@@ -43,7 +43,9 @@ __device__ __forceinline__ T block_excl_scan(T v, T* total) {
 
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads)
-scan_reduce_kernel(const T* __restrict__ in, long long n, unsigned long long* __restrict__ part) {
+scan_reduce_kernel(const T* __restrict__ in, long long cap, unsigned long long* __restrict__ part,
+                   const unsigned long long* __restrict__ n_dev) {
+    const long long n = dev_count(cap, n_dev);
     const long long base = (long long)blockIdx.x * kScanTile;
     unsigned long long s = 0;
 #pragma unroll
@@ -80,8 +82,10 @@ scan_partials_kernel(unsigned long long* __restrict__ part, long long nb,
 // INCL = false: exclusive, out[n] = total. INCL = true: inclusive.
 template <typename T, bool INCL>
 __global__ void __launch_bounds__(kScanThreads)
-scan_final_kernel(const T* __restrict__ in, T* __restrict__ out, long long n,
-                  const unsigned long long* __restrict__ part) {
+scan_final_kernel(const T* __restrict__ in, T* __restrict__ out, long long cap,
+                  const unsigned long long* __restrict__ part,
+                  const unsigned long long* __restrict__ n_dev) {
+    const long long n = dev_count(cap, n_dev);
     const long long base = (long long)blockIdx.x * kScanTile;
     const long long first = base + (long long)threadIdx.x * kScanItems;
     T v[kScanItems];
@@ -101,8 +105,9 @@ scan_final_kernel(const T* __restrict__ in, T* __restrict__ out, long long n,
         if (INCL) run += v[k];
         if (i < n) out[i] = run;
         if (!INCL) run += v[k];
+        if (!INCL && i == n - 1) out[n] = run;
     }
-    if (!INCL && blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) out[n] = run;
+    if (!INCL && n == 0 && blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
 }
 
 size_t scan_u32_temp_bytes(long long n) {
@@ -111,7 +116,8 @@ size_t scan_u32_temp_bytes(long long n) {
 }
 
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, long long n, void* temp,
-                               unsigned long long* total, cudaStream_t s) {
+                               unsigned long long* total, cudaStream_t s,
+                               const unsigned long long* n_dev) {
     if (n <= 0) {
         cudaError_t e = cudaMemsetAsync(out, 0, sizeof(uint32_t), s);
         if (e != cudaSuccess) return e;
@@ -121,11 +127,12 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, long long n, v
     long long nb = (n + kScanTile - 1) / kScanTile;
     unsigned long long* part = (unsigned long long*)temp;
     note_launch();
-    scan_reduce_kernel<uint32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part);
+    scan_reduce_kernel<uint32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part, n_dev);
     note_launch();
     scan_partials_kernel<<<1, kScanThreads, 0, s>>>(part, nb, total);
     note_launch();
-    scan_final_kernel<uint32_t, false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, part);
+    scan_final_kernel<uint32_t, false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, part,
+                                                                             n_dev);
     return cudaGetLastError();
 }
 
@@ -137,12 +144,14 @@ cudaError_t inclusive_scan_u64(const unsigned long long* in, unsigned long long*
     long long nb = (n + kScanTile - 1) / kScanTile;
     unsigned long long* part = (unsigned long long*)temp;
     note_launch();
-    scan_reduce_kernel<unsigned long long><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part);
+    scan_reduce_kernel<unsigned long long><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part,
+                                                                                 nullptr);
     note_launch();
     scan_partials_kernel<<<1, kScanThreads, 0, s>>>(part, nb, nullptr);
     note_launch();
     scan_final_kernel<unsigned long long, true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n,
-                                                                                       part);
+                                                                                       part,
+                                                                                       nullptr);
     return cudaGetLastError();
 }
 

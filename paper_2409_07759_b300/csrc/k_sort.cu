@@ -271,8 +271,9 @@ static_assert(kOneCounterBytes >= (kMaxOnePasses + 1) * 4, "counters and the spa
 
 // Digit counts of every pass in one read of the keys.
 __global__ void __launch_bounds__(kSortThreads)
-radix_hist_kernel(const uint32_t* __restrict__ keys, long long n, OnePlan pl,
-                  uint32_t* __restrict__ hist) {
+radix_hist_kernel(const uint32_t* __restrict__ keys, long long cap, OnePlan pl,
+                  uint32_t* __restrict__ hist, const unsigned long long* __restrict__ n_dev) {
+    const long long n = dev_count(cap, n_dev);
     __shared__ uint32_t h[kHistCopies][kMaxOnePasses][kMaxBins];
     for (int i = threadIdx.x; i < kHistCopies * kMaxOnePasses * kMaxBins; i += kSortThreads)
         (&h[0][0][0])[i] = 0;
@@ -353,7 +354,8 @@ __global__ void __launch_bounds__(kSortThreads, 4)
 radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, long long n,
                int shift, int bins, const uint32_t* __restrict__ hist, uint32_t* status,
-               uint32_t* tile_counter, uint32_t* err) {
+               uint32_t* tile_counter, uint32_t* err,
+               const unsigned long long* __restrict__ n_dev) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OneSmem& S = *reinterpret_cast<OneSmem*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -366,6 +368,13 @@ radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict_
     __syncthreads();
     const int tile = S.tile;
     const long long base = (long long)tile * kSortTile;
+    // deferred sizing: the grid covers the capacity; tiles past the true count
+    // hold no key (tiles are claimed in order, so no real tile waits on them)
+    if (n_dev) {
+        const long long nn = dev_count(n, n_dev);
+        if (base >= nn && tile > 0) return;
+        n = nn;
+    }
     const int valid = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
     uint32_t k[kSortItems], rk[kSortItems];
 #pragma unroll
@@ -477,7 +486,7 @@ radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict_
 static cudaError_t radix_sort_one(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
                                   uint32_t* vals_b, long long n, const SortPlan& plan, void* temp,
                                   int num_sms, bool vals_iota, bool* in_b, uint32_t* err,
-                                  cudaStream_t s) {
+                                  const unsigned long long* n_dev, cudaStream_t s) {
     uint32_t* hist = (uint32_t*)temp;
     uint32_t* counters = (uint32_t*)((char*)temp + kOneHistBytes);
     uint32_t* status = (uint32_t*)((char*)temp + kOneHistBytes + kOneCounterBytes);
@@ -512,7 +521,7 @@ static cudaError_t radix_sort_one(uint32_t* keys_a, uint32_t* vals_a, uint32_t* 
     long long hg = div_up(n, (long long)kSortThreads * 8);
     if (hg > 4LL * num_sms) hg = 4LL * num_sms;
     note_launch();
-    radix_hist_kernel<<<(unsigned)hg, kSortThreads, 0, s>>>(keys_a, n, pl, hist);
+    radix_hist_kernel<<<(unsigned)hg, kSortThreads, 0, s>>>(keys_a, n, pl, hist, n_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     uint32_t *ki = keys_a, *vi = vals_a, *ko = keys_b, *vo = vals_b;
@@ -522,7 +531,7 @@ static cudaError_t radix_sort_one(uint32_t* keys_a, uint32_t* vals_a, uint32_t* 
         note_launch();
         radix_onesweep<<<(unsigned)tiles, kSortThreads, smem, s>>>(
             ki, vread, ko, vo, n, pl.shift[p], pl.bins[p], hist + p * kMaxBins, st,
-            counters + p, err);
+            counters + p, err, n_dev);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         st += (size_t)tiles * pl.bins[p];
@@ -565,19 +574,22 @@ cudaError_t launch_sort_timeout_check(void* scratch, uint32_t* err, cudaStream_t
     }
     note_launch();
     radix_onesweep<<<1, kSortThreads, sizeof(OneSmem), s>>>(
-        keys, nullptr, keys_out, vals_out, 2LL * kSortTile, 0, 128, hist, status, counter, err);
+        keys, nullptr, keys_out, vals_out, 2LL * kSortTile, 0, 128, hist, status, counter, err,
+        nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
                              uint32_t* vals_b, long long n, const SortPlan& plan, void* temp,
                              int num_sms, bool vals_iota, bool* in_b, bool single_pass,
-                             uint32_t* err, cudaStream_t s) {
+                             uint32_t* err, cudaStream_t s, const unsigned long long* n_dev) {
     *in_b = false;
     if (n <= 0 || plan.passes == 0) return cudaSuccess;
+    if (n_dev && !(single_pass && n < kOneMaxKeys && plan.passes <= kMaxOnePasses))
+        return cudaErrorInvalidValue;  // a device count needs the single-pass form
     if (single_pass && n < kOneMaxKeys && plan.passes <= kMaxOnePasses)
         return radix_sort_one(keys_a, vals_a, keys_b, vals_b, n, plan, temp, num_sms, vals_iota,
-                              in_b, err, s);
+                              in_b, err, n_dev, s);
     const int G = sort_grid(n, num_sms);
     const long long n_tiles = (n + kSortTile - 1) / kSortTile;
     const int tpb = (int)((n_tiles + G - 1) / G);

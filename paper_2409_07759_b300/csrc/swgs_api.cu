@@ -51,7 +51,18 @@ struct BatchState {
     Buf views, groups, ids, rec_a, rec_b, rec_c, rec_tiles, rec_rect, rec_depth, rec_runs, vals,
         ranges, T, last, grad2d, rec_supers;
     bool has_grad2d = false;
+    // deferred sizing: the counts live on the device (counts_b: active per
+    // frame group; dtot: BatchTotal words); a pinned slot receives them with
+    // the batch, and `ev` marks its arrival
+    Buf counts_b, dtot;
+    void* h_slot = nullptr;       // pinned: kTotWords u64, then the group counts
+    cudaEvent_t ev = nullptr;
+    bool deferred = false, resolved = true;
+    long long rec_cap = 0, act_cap = 0;
+    swgs_status status = SWGS_OK;
 };
+
+constexpr size_t kSlotBytes = sizeof(unsigned long long) * kTotWords + 4 * kMaxViewsPerBatch;
 
 }  // namespace
 
@@ -81,6 +92,10 @@ struct swgs_ctx {
         reloc_nd, sort_err;
     void* pinned = nullptr;
     size_t pinned_cap = 0;
+    // deferred sizing: capacities learned from earlier calls, and the word the
+    // forward raises when a batch outgrew them (the optimiser step tests it)
+    long long cap_rec = 0, cap_sk = 0, cap_keys = 0;
+    Buf gate;
     std::vector<swgs_saved*> pool;
     std::vector<swgs_saved*> all_saved;
     // stage profiling
@@ -182,6 +197,17 @@ uint32_t* sort_err_word(swgs_ctx* c, cudaStream_t s) {
     return P<uint32_t>(c->sort_err);
 }
 
+// The context's gate word: raised by a forward whose batch outgrew the deferred
+// capacities, so that the optimiser steps after it do nothing (zeroed at the
+// start of each deferred forward call).
+uint32_t* gate_word(swgs_ctx* c, cudaStream_t s) {
+    if (!c->gate.p) {
+        if (!ensure(c, c->gate, 16, s)) return nullptr;
+        if (cudaMemsetAsync(c->gate.p, 0, 16, s) != cudaSuccess) return nullptr;
+    }
+    return P<uint32_t>(c->gate);
+}
+
 bool valid_tile(int w, int h) { return (w == 16 && h == 16) || (w == 8 && h == 8) || (w == 32 && h == 8); }
 bool valid_batch(int b) { return b == 32 || b == 64 || b == 128 || b == 256; }
 
@@ -200,6 +226,8 @@ swgs_status check_gaussians(swgs_ctx* ctx, const swgs_gaussians* g, bool need_li
     return SWGS_OK;
 }
 
+swgs_status resolve_batch(swgs_ctx* c, BatchState& B, bool wait);
+
 swgs_saved* acquire_saved(swgs_ctx* c) {
     swgs_saved* s;
     if (!c->pool.empty()) {
@@ -210,6 +238,7 @@ swgs_saved* acquire_saved(swgs_ctx* c) {
         s->ctx = c;
         c->all_saved.push_back(s);
     }
+    for (auto& b : s->batches) resolve_batch(c, b, true);  // long finished by now
     s->n_batches = 0;
     s->n_views = 0;
     return s;
@@ -219,10 +248,70 @@ void free_saved_buffers(swgs_ctx* c, swgs_saved* s, cudaStream_t st) {
     for (auto& b : s->batches) {
         Buf* bs[] = {&b.views, &b.groups, &b.ids, &b.rec_a, &b.rec_b, &b.rec_c, &b.rec_tiles,
                      &b.rec_rect, &b.rec_depth, &b.rec_runs, &b.vals, &b.ranges, &b.T, &b.last,
-                     &b.grad2d, &b.rec_supers};
+                     &b.grad2d, &b.rec_supers, &b.counts_b, &b.dtot};
         for (Buf* x : bs) ctx_free(c, *x, st);
+        if (b.h_slot) cudaFreeHost(b.h_slot);
+        if (b.ev) cudaEventDestroy(b.ev);
+        b.h_slot = nullptr;
+        b.ev = nullptr;
     }
     ctx_free(c, s->pairs, st);
+}
+
+long long grow_cap(long long x) { return x + x / 8 + 4096; }
+
+// The host tables' count-dependent fields from the active counts, as the
+// plan kernel computes them on the device.
+void tables_from_counts(BatchState& B, const int32_t* counts) {
+    long long act = 0, rec = 0;
+    for (size_t k = 0; k < B.h_groups.size(); ++k) {
+        GroupDev& G = B.h_groups[k];
+        const int n = counts[k];
+        G.n_active = n;
+        G.act_base = (int)act;
+        G.rec_base = (int)rec;
+        for (int j = 0; j < G.view_count; ++j) {
+            ViewDev& V = B.h_views[(size_t)G.view_begin + j];
+            V.rec_base = (int)(rec + (long long)j * n);
+            V.n_rec = n;
+        }
+        act += n;
+        rec += (long long)n * G.view_count;
+    }
+}
+
+// Deferred sizing: take a finished batch's totals from its pinned slot (wait:
+// block until they have arrived; else SWGS_EPENDING if they have not), fill
+// its host counts and tables, grow the context's capacities to what it needed,
+// and return its status: SWGS_EDEVICE when it outgrew the capacities (its
+// outputs are background and every later launch of it did nothing: render it
+// again), SWGS_ETIMEOUT when a sort's look-back wait ran out.
+swgs_status resolve_batch(swgs_ctx* c, BatchState& B, bool wait) {
+    if (!B.deferred || B.resolved) return B.status;
+    const cudaError_t e = wait ? cudaEventSynchronize(B.ev) : cudaEventQuery(B.ev);
+    if (e == cudaErrorNotReady) return SWGS_EPENDING;
+    if (e != cudaSuccess) return fail(c, SWGS_ECUDA, "deferred totals: %s", cudaGetErrorString(e));
+    unsigned long long tot[kTotWords];
+    memcpy(tot, B.h_slot, sizeof(tot));
+    tables_from_counts(B, (const int32_t*)((const char*)B.h_slot + sizeof(tot)));
+    B.n_rec = (long long)tot[kTotRecords];
+    B.total_active = (long long)tot[kTotActive];
+    B.n_sort_keys = (long long)tot[kTotSuperKeys];
+    B.n_keys = (long long)tot[kTotTileKeys];
+    const unsigned long long st = tot[kTotStatus];
+    c->cap_rec = std::max(c->cap_rec, grow_cap((long long)tot[kTotNeedRecords]));
+    c->cap_sk = std::max(c->cap_sk, grow_cap((long long)tot[kTotNeedSuperKeys]));
+    c->cap_keys = std::max(c->cap_keys, grow_cap((long long)tot[kTotNeedTileKeys]));
+    if ((st & 1ull) && B.rec_cap > 0) {
+        // the records did not fit, so the keys were never counted: grow their
+        // capacities in proportion, so that the call issued again likely fits
+        const double f = (double)tot[kTotNeedRecords] / (double)B.rec_cap;
+        c->cap_sk = std::max(c->cap_sk, grow_cap((long long)(f * (double)c->cap_sk)));
+        c->cap_keys = std::max(c->cap_keys, grow_cap((long long)(f * (double)c->cap_keys)));
+    }
+    B.status = (st & 3ull) ? SWGS_EDEVICE : ((st & 4ull) ? SWGS_ETIMEOUT : SWGS_OK);
+    B.resolved = true;
+    return B.status;
 }
 
 Records records_of(BatchState& b) {
@@ -268,14 +357,30 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
     B.n_views = (int)idx.size();
     B.n_groups = F;
     B.has_grad2d = false;
+    // deferred sizing: once capacities are known, nothing is read back here;
+    // the counts stay on the device and size every launch from there
+    const bool deferred = ctx->cfg.deferred_sizing != 0 && ctx->cap_rec > 0 &&
+                          ctx->cfg.sort_single_pass != 0 && ctx->cap_rec < (1LL << 30) &&
+                          ctx->cap_sk < (1LL << 30);
+    B.deferred = deferred;
+    B.resolved = !deferred;
+    B.status = SWGS_OK;
     // 1. compaction
     const int nb = N > 0 ? (int)((N + kCompactBlock - 1) / kCompactBlock) : 0;
     if (!ensure(ctx, ctx->frames, sizeof(int32_t) * F, s) ||
         !ensure(ctx, ctx->block_cnt, sizeof(uint32_t) * ((size_t)F * nb + 1), s) ||
         !ensure(ctx, ctx->scan_tmp, scan_u32_temp_bytes((long long)F * nb + 1) + 64, s) ||
-        !ensure(ctx, ctx->counts, sizeof(int32_t) * F, s) || !ensure(ctx, ctx->totals, 64, s) ||
+        !ensure(ctx, B.counts_b, sizeof(int32_t) * F, s) || !ensure(ctx, ctx->totals, 64, s) ||
+        !ensure(ctx, B.dtot, sizeof(unsigned long long) * kTotWords, s) ||
         !ensure(ctx, B.ids, sizeof(int32_t) * ((size_t)F * (N > 0 ? N : 1)), s))
         return fail(ctx, SWGS_ENOMEM, "allocation failed (compaction)");
+    if (deferred && !B.h_slot) {
+        if (cudaMallocHost(&B.h_slot, kSlotBytes) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming) != cudaSuccess)
+            return fail(ctx, SWGS_ENOMEM, "allocation failed (deferred totals)");
+    }
+    CK(cudaMemsetAsync(B.dtot.p, 0, sizeof(unsigned long long) * kTotWords, s));
+    B.act_cap = (long long)F * (N > 0 ? N : 1);
     CK(cudaMemcpyAsync(ctx->frames.p, frames.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, s));
     std::vector<int> n_act(F, 0);
     if (N > 0) {
@@ -286,10 +391,13 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
                               (long long)F * nb, ctx->scan_tmp.p, P<unsigned long long>(ctx->totals), s));
         CK(launch_active_write(g->start, g->expire, N, P<int32_t>(ctx->frames), F,
                                P<uint32_t>(ctx->block_cnt), nb, P<int32_t>(B.ids), 0,
-                               P<int32_t>(ctx->counts), s));
+                               P<int32_t>(B.counts_b), s));
+    } else {
+        CK(cudaMemsetAsync(B.counts_b.p, 0, sizeof(int32_t) * F, s));
     }
-    if (N > 0) {
-        CK(cudaMemcpyAsync(ctx->pinned, ctx->counts.p, sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s));
+    if (N > 0 && !deferred) {
+        CK(cudaMemcpyAsync(ctx->pinned, B.counts_b.p, sizeof(int32_t) * F, cudaMemcpyDeviceToHost,
+                           s));
         CK(cudaStreamSynchronize(s));
         memcpy(n_act.data(), ctx->pinned, sizeof(int32_t) * F);
     }
@@ -360,7 +468,11 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
     B.n_supers = supers;
     B.n_sort_keys = 0;
     B.n_pix = pix;
+    if (deferred) rec = ctx->cap_rec;  // every record launch is sized by it
+    B.rec_cap = rec;
     const size_t R = (size_t)rec;
+    unsigned long long* dtot = P<unsigned long long>(B.dtot);
+    const unsigned long long* n_rec_dev = deferred ? dtot + kTotRecords : nullptr;
     if (!ensure(ctx, B.views, sizeof(ViewDev) * B.h_views.size(), s) ||
         !ensure(ctx, B.groups, sizeof(GroupDev) * F, s) ||
         !ensure(ctx, B.rec_a, sizeof(float4) * R, s) || !ensure(ctx, B.rec_b, sizeof(float4) * R, s) ||
@@ -382,11 +494,14 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
     CK(cudaMemcpyAsync(B.views.p, B.h_views.data(), sizeof(ViewDev) * B.h_views.size(),
                        cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(B.groups.p, B.h_groups.data(), sizeof(GroupDev) * F, cudaMemcpyHostToDevice, s));
+    if (deferred)
+        CK(launch_plan(P<GroupDev>(B.groups), F, P<ViewDev>(B.views), P<int32_t>(B.counts_b), dtot,
+                       ctx->cap_rec, s));
     Records rc = records_of(B);
     {
         StageScope sc_(ctx, SWGS_STAGE_PREPROCESS, s);
         CK(launch_preprocess(*g, P<ViewDev>(B.views), P<GroupDev>(B.groups), F, P<int32_t>(B.ids),
-                             act, rec, tw, th, ctx->cfg.near_plane, rc, s));
+                             act, rec, tw, th, ctx->cfg.near_plane, rc, s, n_rec_dev));
     }
     // 3. depth order of the records and their key offsets
     long long n_keys = 0;
@@ -400,7 +515,8 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             CK(radix_sort_pairs(P<uint32_t>(B.rec_depth), P<uint32_t>(ctx->order_a),
                                 P<uint32_t>(ctx->order_b), P<uint32_t>(ctx->tcount), (long long)R,
                                 dp, ctx->sort_tmp.p, ctx->num_sms, true, &in_b,
-                                ctx->cfg.sort_single_pass != 0, sort_err_word(ctx, s), s));
+                                ctx->cfg.sort_single_pass != 0, sort_err_word(ctx, s), s,
+                                n_rec_dev));
         }
         // 4 passes: results back in (rec_depth, order_a)
         const uint32_t* order = in_b ? P<uint32_t>(ctx->tcount) : P<uint32_t>(ctx->order_a);
@@ -412,34 +528,48 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             CK(cudaMemsetAsync(ctx->totals.p, 0, 16, s));
             CK(launch_gather_supers(order, rc, SX, SY, cnt,
                                     P<unsigned long long>(ctx->totals) + 1, (long long)R,
-                                    ctx->num_sms, s));
+                                    ctx->num_sms, s, n_rec_dev));
             CK(exclusive_scan_u32(cnt, P<uint32_t>(ctx->koff), (long long)R, ctx->scan_tmp.p,
-                                  P<unsigned long long>(ctx->totals), s));
+                                  P<unsigned long long>(ctx->totals), s, n_rec_dev));
         }
-        CK(cudaMemcpyAsync(ctx->pinned, ctx->totals.p, 2 * sizeof(unsigned long long),
-                           cudaMemcpyDeviceToHost, s));
-        uint32_t* serr = sort_err_word(ctx, s);
-        if (serr)
-            CK(cudaMemcpyAsync((char*)ctx->pinned + 16, serr, 4, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        unsigned long long tot[2] = {0, 0};
-        memcpy(tot, ctx->pinned, sizeof(tot));
-        uint32_t sort_failed = 0;
-        if (serr) memcpy(&sort_failed, (char*)ctx->pinned + 16, 4);
-        if (sort_failed) {
-            CK(cudaMemsetAsync(serr, 0, 4, s));
-            return fail(ctx, SWGS_ETIMEOUT,
-                        "a radix-sort look-back wait ran out (this call's depth order, or the "
-                        "previous call's sorted keys, are wrong)");
+        long long n_sk = 0;
+        if (deferred) {
+            // sized by the capacities; a batch over them stops here on the device
+            n_sk = ctx->cap_sk;
+            n_keys = ctx->cap_keys;
+            CK(launch_check_keys(P<unsigned long long>(ctx->totals), dtot, n_sk, n_keys,
+                                 sort_err_word(ctx, s), gate_word(ctx, s), s));
+        } else {
+            CK(cudaMemcpyAsync(ctx->pinned, ctx->totals.p, 2 * sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, s));
+            uint32_t* serr = sort_err_word(ctx, s);
+            if (serr)
+                CK(cudaMemcpyAsync((char*)ctx->pinned + 16, serr, 4, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            unsigned long long tot[2] = {0, 0};
+            memcpy(tot, ctx->pinned, sizeof(tot));
+            uint32_t sort_failed = 0;
+            if (serr) memcpy(&sort_failed, (char*)ctx->pinned + 16, 4);
+            if (sort_failed) {
+                CK(cudaMemsetAsync(serr, 0, 4, s));
+                return fail(ctx, SWGS_ETIMEOUT,
+                            "a radix-sort look-back wait ran out (this call's depth order, or "
+                            "the previous call's sorted keys, are wrong)");
+            }
+            if (tot[1] > 0x7fffffffULL || tot[0] > 0x7fffffffULL)
+                return fail(ctx, SWGS_EINVAL,
+                            "%llu tile keys (%llu super-tile keys) exceed the 2^31 limit of one "
+                            "batch; render fewer views per call", tot[1], tot[0]);
+            n_keys = (long long)tot[1];
+            n_sk = (long long)tot[0];
+            // the capacities a later deferred call starts from
+            ctx->cap_rec = std::max(ctx->cap_rec, grow_cap(rec));
+            ctx->cap_sk = std::max(ctx->cap_sk, grow_cap(n_sk));
+            ctx->cap_keys = std::max(ctx->cap_keys, grow_cap(n_keys));
         }
-        if (tot[1] > 0x7fffffffULL || tot[0] > 0x7fffffffULL)
-            return fail(ctx, SWGS_EINVAL,
-                        "%llu tile keys (%llu super-tile keys) exceed the 2^31 limit of one "
-                        "batch; render fewer views per call", tot[1], tot[0]);
-        n_keys = (long long)tot[1];
         B.n_keys = n_keys;
-        const long long n_sk = (long long)tot[0];
         B.n_sort_keys = n_sk;
+        const unsigned long long* n_sk_dev = deferred ? dtot + kTotSuperKeys : nullptr;
         // 4. super-tile keys, their stable sort by super tile, per-tile lists
         const SortPlan sp = make_sort_plan(0, ceil_log2(supers));
         const size_t K = (size_t)n_sk;
@@ -459,7 +589,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             CK(launch_emit_supers(order, P<uint32_t>(ctx->koff), (long long)R, rc,
                                   P<ViewDev>(B.views), (int)B.h_views.size(), SX, SY, tw, th,
                                   ctx->num_sms, P<uint32_t>(ctx->keys_a),
-                                  P<uint32_t>(ctx->vals_tmp), s));
+                                  P<uint32_t>(ctx->vals_tmp), s, n_rec_dev));
         }
         bool kb = false;
         {
@@ -467,14 +597,16 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             CK(radix_sort_pairs(P<uint32_t>(ctx->keys_a), P<uint32_t>(ctx->vals_tmp),
                                 P<uint32_t>(ctx->keys_b), P<uint32_t>(ctx->vals_b), (long long)K,
                                 sp, ctx->sort_tmp.p, ctx->num_sms, false, &kb,
-                                ctx->cfg.sort_single_pass != 0, sort_err_word(ctx, s), s));
+                                ctx->cfg.sort_single_pass != 0, sort_err_word(ctx, s), s,
+                                n_sk_dev));
         }
         const uint32_t* skeys = kb ? P<uint32_t>(ctx->keys_b) : P<uint32_t>(ctx->keys_a);
         const uint32_t* svals = kb ? P<uint32_t>(ctx->vals_b) : P<uint32_t>(ctx->vals_tmp);
         {
             StageScope sc_(ctx, SWGS_STAGE_RANGES, s);
             CK(cudaMemsetAsync(ctx->sranges.p, 0, sizeof(int2) * (size_t)supers, s));
-            CK(launch_super_ranges(skeys, (long long)K, supers, P<int2>(ctx->sranges), s));
+            CK(launch_super_ranges(skeys, (long long)K, supers, P<int2>(ctx->sranges), s,
+                                   n_sk_dev));
             CK(launch_expand_count(P<int2>(ctx->sranges), skeys, P<ViewDev>(B.views),
                                    (int)B.h_views.size(), (int)supers, tw,
                                    P<uint32_t>(ctx->tile_cnt), sort_err_word(ctx, s), s));
@@ -516,6 +648,16 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
         StageScope sc_(ctx, SWGS_STAGE_BLEND_FWD, s);
         CK(launch_blend_fwd(ba, tw, th, ctx->cfg.batch, ppt, (int)grid, s));
     }
+    if (deferred) {
+        // the tile sort's wait into the status, then the totals and the group
+        // counts to this batch's pinned slot
+        CK(launch_check_keys(nullptr, dtot, 0, 0, sort_err_word(ctx, s), gate_word(ctx, s), s));
+        CK(cudaMemcpyAsync(B.h_slot, dtot, sizeof(unsigned long long) * kTotWords,
+                           cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync((char*)B.h_slot + sizeof(unsigned long long) * kTotWords, B.counts_b.p,
+                           sizeof(int32_t) * F, cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(B.ev, s));
+    }
     return SWGS_OK;
 }
 
@@ -528,14 +670,38 @@ swgs_status backward_batch(swgs_ctx* ctx, const swgs_gaussians* g, BatchState& B
         B.h_views[i].dL = dL[B.call_index[i]];
         if (!B.h_views[i].dL) return fail(ctx, SWGS_EINVAL, "null dL_drgb for view %d", B.call_index[i]);
     }
+    // deferred sizing, forward not yet resolved: the counts are on the device
+    // only, so sizes come from the batch's capacities and launches read the
+    // device totals (a batch that outgrew them has zero counts there)
+    const bool dev = B.deferred && !B.resolved;
+    unsigned long long* dtot = P<unsigned long long>(B.dtot);
+    const bool use_reg = reg && (reg->opacity_reg != 0.f || reg->scale_reg != 0.f);
+    if (use_reg) {
+        // per-frame weights of one active Gaussian in the view-mean of reg():
+        // view_count / (V n_active) times each weight (the division by n_active
+        // on the device when the count is only there)
+        const int V = reg->n_views_total > 0 ? reg->n_views_total : n_views_total;
+        for (GroupDev& G : B.h_groups) {
+            G.reg_o_num = (double)reg->opacity_reg * G.view_count / (double)V;
+            G.reg_s_num = (double)reg->scale_reg * G.view_count / (3.0 * V);
+            G.reg_o = G.n_active > 0 ? (float)(G.reg_o_num / (double)G.n_active) : 0.f;
+            G.reg_s = G.n_active > 0 ? (float)(G.reg_s_num / (double)G.n_active) : 0.f;
+        }
+        CK(cudaMemcpyAsync(B.groups.p, B.h_groups.data(), sizeof(GroupDev) * B.h_groups.size(),
+                           cudaMemcpyHostToDevice, s));
+    }
     CK(cudaMemcpyAsync(B.views.p, B.h_views.data(), sizeof(ViewDev) * B.h_views.size(),
                        cudaMemcpyHostToDevice, s));
-    if (!ensure(ctx, B.grad2d, sizeof(float) * 12 * (size_t)(B.n_rec > 0 ? B.n_rec : 1), s) ||
+    if (dev)  // the uploads carried no counts: restore them (and the weights) on the device
+        CK(launch_plan(P<GroupDev>(B.groups), B.n_groups, P<ViewDev>(B.views),
+                       P<int32_t>(B.counts_b), nullptr, 0, s));
+    const long long n_rec = dev ? B.rec_cap : B.n_rec;
+    if (!ensure(ctx, B.grad2d, sizeof(float) * 12 * (size_t)(n_rec > 0 ? n_rec : 1), s) ||
         !ensure(ctx, ctx->counter, 64, s))
         return fail(ctx, SWGS_ENOMEM, "allocation failed (grad2d)");
-    CK(cudaMemsetAsync(B.grad2d.p, 0, sizeof(float) * 12 * (size_t)(B.n_rec > 0 ? B.n_rec : 1), s));
+    CK(cudaMemsetAsync(B.grad2d.p, 0, sizeof(float) * 12 * (size_t)(n_rec > 0 ? n_rec : 1), s));
     B.has_grad2d = true;
-    if (B.n_rec == 0) return SWGS_OK;
+    if (n_rec == 0) return SWGS_OK;
     BlendArgs ba{};
     ba.views = P<ViewDev>(B.views);
     ba.n_views = (int)B.h_views.size();
@@ -564,22 +730,10 @@ swgs_status backward_batch(swgs_ctx* ctx, const swgs_gaussians* g, BatchState& B
     }
     {
         StageScope sc_(ctx, SWGS_STAGE_PREPROCESS_BWD, s);
-        const bool use_reg = reg && (reg->opacity_reg != 0.f || reg->scale_reg != 0.f);
-        if (use_reg) {
-            // per-frame weights of one active Gaussian in the view-mean of reg()
-            const int V = reg->n_views_total > 0 ? reg->n_views_total : n_views_total;
-            for (GroupDev& G : B.h_groups) {
-                const double w = G.n_active > 0 ? (double)G.view_count / ((double)V * G.n_active)
-                                                : 0.0;
-                G.reg_o = (float)(reg->opacity_reg * w);
-                G.reg_s = (float)(reg->scale_reg * w / 3.0);
-            }
-            CK(cudaMemcpyAsync(B.groups.p, B.h_groups.data(), sizeof(GroupDev) * B.h_groups.size(),
-                               cudaMemcpyHostToDevice, s));
-        }
         CK(launch_preprocess_bwd(*g, *grads, P<ViewDev>(B.views), P<GroupDev>(B.groups),
-                                 B.n_groups, P<int32_t>(B.ids), B.total_active,
-                                 P<float>(B.grad2d), use_reg, use_reg ? loss : nullptr, s));
+                                 B.n_groups, P<int32_t>(B.ids),
+                                 dev ? B.act_cap : B.total_active, P<float>(B.grad2d), use_reg,
+                                 use_reg ? loss : nullptr, s, dev ? dtot + kTotActive : nullptr));
     }
     return SWGS_OK;
 }
@@ -668,6 +822,7 @@ swgs_status swgs_default_config(swgs_config* cfg) {
     cfg->bwd_pixels_per_thread = 8;
     cfg->bwd_batch = 64;
     cfg->sort_single_pass = 1;
+    cfg->deferred_sizing = 0;
     return SWGS_OK;
 }
 
@@ -681,6 +836,7 @@ swgs_status swgs_create(const swgs_config* cfg, swgs_alloc_fn alloc, swgs_free_f
     if (c.bwd_batch == 0) c.bwd_batch = c.batch;
     if (!valid_tile(c.tile_w, c.tile_h) || !valid_batch(c.batch) || !(c.near_plane > 0.f) ||
         c.blocks_per_sm < 0 || (c.sort_single_pass != 0 && c.sort_single_pass != 1) ||
+        (c.deferred_sizing != 0 && c.deferred_sizing != 1) ||
         !blend_config_valid(c.tile_w, c.tile_h, c.batch, c.pixels_per_thread, false) ||
         !blend_config_valid(c.tile_w, c.tile_h, c.bwd_batch, c.bwd_pixels_per_thread, true))
         return SWGS_EINVAL;
@@ -713,7 +869,7 @@ void swgs_destroy(swgs_ctx* ctx) {
                  &ctx->codec_vals_a, &ctx->codec_vals_b, &ctx->codec_flags, &ctx->codec_idx,
                  &ctx->codec_stage, &ctx->sort_tmp, &ctx->counter, &ctx->totals, &ctx->l1_tab,
                  &ctx->elig, &ctx->reloc_w, &ctx->reloc_cdf, &ctx->reloc_dead, &ctx->reloc_tg,
-                 &ctx->reloc_cnt, &ctx->reloc_nd, &ctx->sort_err};
+                 &ctx->reloc_cnt, &ctx->reloc_nd, &ctx->sort_err, &ctx->gate};
     for (Buf* b : bs) ctx_free(ctx, *b, s);
     for (swgs_saved* sv : ctx->all_saved) {
         free_saved_buffers(ctx, sv, s);
@@ -1074,6 +1230,15 @@ static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32
             return fail(ctx, SWGS_EINVAL, "view %d: bad size, focal length or output", v);
     }
     if (saved) *saved = nullptr;
+    if (ctx->cfg.deferred_sizing) {
+        // learn the capacities from every earlier call that has finished, and
+        // lower the gate for this call's optimiser steps
+        for (swgs_saved* o : ctx->all_saved)
+            for (auto& b : o->batches) resolve_batch(ctx, b, false);
+        uint32_t* gw = gate_word(ctx, s);
+        if (!gw) return fail(ctx, SWGS_ENOMEM, "allocation failed (gate word)");
+        CK(cudaMemsetAsync(gw, 0, 4, s));
+    }
     swgs_saved* sv = acquire_saved(ctx);
     sv->n_views = n_views;
     sv->count_pairs = ctx->cfg.count_pairs != 0;
@@ -1123,6 +1288,11 @@ static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32
                           loss, n_views,
                           sv->batches[b], pairs, s);
         if (st != SWGS_OK) {
+            // a failed call leaves no deferred totals to wait for
+            for (int k = 0; k <= b; ++k) {
+                sv->batches[k].resolved = true;
+                sv->batches[k].status = st;
+            }
             ctx->pool.push_back(sv);
             return st;
         }
@@ -1172,8 +1342,38 @@ swgs_status swgs_saved_release(swgs_ctx* ctx, swgs_saved* saved) {
     return SWGS_OK;
 }
 
+swgs_status swgs_saved_status(swgs_ctx* ctx, const swgs_saved* saved, int32_t wait) {
+    if (!ctx || !saved || saved->ctx != ctx) return SWGS_EINVAL;
+    swgs_status out = SWGS_OK;
+    for (int b = 0; b < saved->n_batches; ++b) {
+        BatchState& B = const_cast<swgs_saved*>(saved)->batches[b];
+        const swgs_status st = resolve_batch(ctx, B, wait != 0);
+        if (st == SWGS_EPENDING) return SWGS_EPENDING;
+        if (st != SWGS_OK && out == SWGS_OK) out = st;
+    }
+    if (out == SWGS_EDEVICE)
+        return fail(ctx, SWGS_EDEVICE,
+                    "a batch outgrew the deferred capacities (its outputs are background); the "
+                    "context has grown them to %lld records, %lld super keys, %lld tile keys: "
+                    "render it again", ctx->cap_rec, ctx->cap_sk, ctx->cap_keys);
+    if (out == SWGS_ETIMEOUT)
+        return fail(ctx, SWGS_ETIMEOUT, "a radix-sort look-back wait ran out in this call");
+    return out;
+}
+
+// Every batch's host counts, waiting for deferred ones.
+static swgs_status resolve_all(swgs_ctx* ctx, const swgs_saved* saved) {
+    for (int b = 0; b < saved->n_batches; ++b) {
+        const swgs_status st =
+            resolve_batch(ctx, const_cast<swgs_saved*>(saved)->batches[b], true);
+        if (st == SWGS_ECUDA) return st;
+    }
+    return SWGS_OK;
+}
+
 swgs_status swgs_saved_query(swgs_ctx* ctx, const swgs_saved* saved, swgs_saved_info* info) {
     if (!ctx || !saved || !info) return SWGS_EINVAL;
+    if (resolve_all(ctx, saved) != SWGS_OK) return SWGS_ECUDA;
     swgs_saved_info o{};
     o.n_views = saved->n_views;
     o.n_batches = saved->n_batches;
@@ -1207,6 +1407,7 @@ swgs_status swgs_saved_query(swgs_ctx* ctx, const swgs_saved* saved, swgs_saved_
 
 swgs_status swgs_saved_count(swgs_ctx* ctx, const swgs_saved* saved, int32_t what, int64_t* count) {
     if (!ctx || !saved || !count) return SWGS_EINVAL;
+    if (resolve_all(ctx, saved) != SWGS_OK) return SWGS_ECUDA;
     long long n = 0;
     for (int b = 0; b < saved->n_batches; ++b) {
         const BatchState& B = saved->batches[b];
@@ -1460,7 +1661,8 @@ swgs_status swgs_sgld_step(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_ga
         if (!ensure(ctx, ctx->elig, (size_t)N, s))
             return fail(ctx, SWGS_ENOMEM, "allocation failed (eligible slots)");
         CK(launch_eligible(*g, frames, n_frames, P<uint8_t>(ctx->elig), s));
-        CK(launch_sgld(*g, grads, adam, P<uint8_t>(ctx->elig), *params, seed, step, s));
+        CK(launch_sgld(*g, grads, adam, P<uint8_t>(ctx->elig), *params, seed, step, s,
+                       ctx->cfg.deferred_sizing ? gate_word(ctx, s) : nullptr));
     }
     long long nd = 0;
     if (params->relocate) {
@@ -1475,7 +1677,8 @@ swgs_status swgs_sgld_step(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_ga
             return fail(ctx, SWGS_ENOMEM, "allocation failed (relocation)");
         int32_t* tg = targets ? targets : P<int32_t>(ctx->reloc_tg);
         CK(launch_reloc_weights(*g, P<uint8_t>(ctx->elig), P<unsigned long long>(ctx->reloc_w),
-                                P<uint8_t>(ctx->reloc_dead), s));
+                                P<uint8_t>(ctx->reloc_dead), s,
+                                ctx->cfg.deferred_sizing ? gate_word(ctx, s) : nullptr));
         CK(inclusive_scan_u64(P<unsigned long long>(ctx->reloc_w), P<unsigned long long>(ctx->reloc_cdf),
                               N, ctx->scan_tmp.p, s));
         CK(cudaMemsetAsync(ctx->reloc_cnt.p, 0, 4 * (size_t)N, s));

@@ -50,6 +50,22 @@ struct GroupDev {
     int view_begin;    // first view of this group (views of a group are contiguous)
     int view_count;
     float reg_o, reg_s;  // regulariser weights of one active Gaussian (backward)
+    // the weights before the division by n_active (set by the host; the plan
+    // kernel divides once the count is known on the device)
+    double reg_o_num, reg_s_num;
+};
+
+// Device totals of one batch (deferred sizing keeps them on the device; the
+// plan and check kernels write them, later launches read their counts).
+enum BatchTotal {
+    kTotRecords = 0,    // records (view, active Gaussian)
+    kTotActive = 1,     // active ids over the frame groups
+    kTotSuperKeys = 2,  // (super tile, record) keys
+    kTotTileKeys = 3,   // per-tile list entries
+    kTotStatus = 4,     // bit 0: records over capacity, bit 1: keys over capacity,
+                        // bit 2: a sort's look-back wait ran out
+    kTotNeedRecords = 5, kTotNeedSuperKeys = 6, kTotNeedTileKeys = 7,
+    kTotWords = 8
 };
 
 // Records of one (view, Gaussian) pair, structure of float4 arrays.
@@ -294,6 +310,15 @@ constexpr float kLogitDead = -0x1.52c582p+2f;
 // pair_v returns v = q + lo, q = -m/2 log2e, with lo added inside the last
 // FMA of the quadratic form; *au = unclamped o*G = 2^v, *a = min(0.99, *au).
 // ---------------------------------------------------------------------------
+// Element count of a launch sized by a host capacity `cap`: with deferred
+// sizing the true count lives on the device (n, written by an earlier launch)
+// and is capped by the capacity; without it (n null) the capacity is exact.
+__device__ __forceinline__ long long dev_count(long long cap, const unsigned long long* n) {
+    if (!n) return cap;
+    const long long v = (long long)*n;
+    return v < cap ? v : cap;
+}
+
 // 8-bit display value of a colour channel: round(255 clamp(c, 0, 1)), ties to even.
 __device__ __forceinline__ uint8_t rgb8_of(float c) {
     return (uint8_t)__float2int_rn(__fmul_rn(fminf(fmaxf(c, 0.f), 1.f), 255.f));
@@ -385,8 +410,10 @@ constexpr int kCompactBlock = 1024;
 
 // k_scan.cu
 size_t scan_u32_temp_bytes(long long n);
+// n_dev (optional): the true count on the device, at most n (deferred sizing)
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, long long n, void* temp,
-                               unsigned long long* total, cudaStream_t s);
+                               unsigned long long* total, cudaStream_t s,
+                               const unsigned long long* n_dev = nullptr);
 size_t scan_u64_temp_bytes(long long n);
 cudaError_t inclusive_scan_u64(const unsigned long long* in, unsigned long long* out, long long n,
                                void* temp, cudaStream_t s);
@@ -395,11 +422,13 @@ cudaError_t inclusive_scan_u64(const unsigned long long* in, unsigned long long*
 cudaError_t launch_preprocess(const swgs_gaussians& g, const ViewDev* views, const GroupDev* groups,
                               int n_groups, const int32_t* ids, long long total_active,
                               long long n_rec, int tile_w, int tile_h, float near_plane,
-                              Records rec, cudaStream_t s);
+                              Records rec, cudaStream_t s,
+                              const unsigned long long* n_dev = nullptr);
 cudaError_t launch_preprocess_bwd(const swgs_gaussians& g, const swgs_gaussians& grads,
                                   const ViewDev* views, const GroupDev* groups, int n_groups,
                                   const int32_t* ids, long long total_active,
-                                  const float* grad2d, bool reg, float* loss, cudaStream_t s);
+                                  const float* grad2d, bool reg, float* loss, cudaStream_t s,
+                                  const unsigned long long* n_dev = nullptr);
 
 // k_sort.cu
 struct SortPlan {
@@ -423,7 +452,8 @@ cudaError_t launch_sort_timeout_check(void* scratch, uint32_t* err, cudaStream_t
 cudaError_t radix_sort_pairs(uint32_t* keys_a, uint32_t* vals_a, uint32_t* keys_b,
                              uint32_t* vals_b, long long n, const SortPlan& plan, void* temp,
                              int num_sms, bool vals_iota, bool* in_b, bool single_pass,
-                             uint32_t* err, cudaStream_t s);
+                             uint32_t* err, cudaStream_t s,
+                             const unsigned long long* n_dev = nullptr);
 
 // k_keys.cu
 // Super tiles: SX x SY tiles (4 x 4, or 2 x 8 for 32x8 tiles); at most 2^16 per
@@ -433,13 +463,16 @@ inline int super_w(int tile_w) { return tile_w == 32 ? 2 : 4; }
 inline int super_h(int tile_w) { return tile_w == 32 ? 8 : 4; }
 cudaError_t launch_gather_supers(const uint32_t* order, const Records rec, int sx, int sy,
                                  uint32_t* out, unsigned long long* exact, long long n,
-                                 int num_sms, cudaStream_t s);
+                                 int num_sms, cudaStream_t s,
+                                 const unsigned long long* n_dev = nullptr);
 cudaError_t launch_emit_supers(const uint32_t* order, const uint32_t* offsets, long long n_rec,
                                const Records rec, const ViewDev* views, int n_views, int sx,
                                int sy, int tile_w, int tile_h, int num_sms, uint32_t* keys,
-                               uint32_t* vals, cudaStream_t s);
+                               uint32_t* vals, cudaStream_t s,
+                               const unsigned long long* n_dev = nullptr);
 cudaError_t launch_super_ranges(const uint32_t* keys, long long n, long long n_supers,
-                                int2* ranges, cudaStream_t s);
+                                int2* ranges, cudaStream_t s,
+                                const unsigned long long* n_dev = nullptr);
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
                                 int n_views, int total_supers, int tile_w, uint32_t* tcount,
                                 const uint32_t* sort_err, cudaStream_t s);
@@ -512,6 +545,21 @@ cudaError_t launch_loss_l1(const ViewDev* views, int n_views, long long total_pi
                            cudaStream_t s);
 cudaError_t launch_copy_slice(const swgs_gaussians& dst, long long first, long long count,
                               const swgs_gaussians& src, cudaStream_t s);
+// The count-dependent fields of a batch's tables from the active counts on the
+// device (n_active, act_base, rec_base per frame group, rec_base / n_rec per
+// view, the regulariser weights); with `totals`, also the record and active
+// totals, checked against rec_cap (over it: status bit 0 and the counts zeroed,
+// so every later launch of the batch does nothing).
+cudaError_t launch_plan(GroupDev* groups, int n_groups, ViewDev* views, const int32_t* counts,
+                        unsigned long long* totals, long long rec_cap, cudaStream_t s);
+// Copies the key totals (super keys, tile-list entries; none when key_totals
+// is null) into the batch totals and checks them against the capacities (over:
+// status bit 1, counts zeroed); takes the sort's look-back error word into
+// status bit 2 and clears it; ORs the status into *gate (the context's word
+// that its later optimiser steps test).
+cudaError_t launch_check_keys(const unsigned long long* key_totals, unsigned long long* totals,
+                              long long super_cap, long long key_cap, uint32_t* sort_err,
+                              uint32_t* gate, cudaStream_t s);
 
 // k_optim.cu
 // elig: one byte per slot, 1 = active at a frame of the step and not frozen
@@ -528,9 +576,11 @@ cudaError_t launch_grad_unpack(const swgs_gaussians& grads, const int32_t* ids,
 cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
                         const swgs_adam_state* adam, const uint8_t* elig,
                         const swgs_sgld_params& p, unsigned long long seed,
-                        unsigned long long step, cudaStream_t s);
+                        unsigned long long step, cudaStream_t s,
+                        const uint32_t* gate = nullptr);
 cudaError_t launch_reloc_weights(const swgs_gaussians& g, const uint8_t* elig,
-                                 unsigned long long* weights, uint8_t* dead, cudaStream_t s);
+                                 unsigned long long* weights, uint8_t* dead, cudaStream_t s,
+                                 const uint32_t* gate = nullptr);
 cudaError_t launch_reloc_sample(const swgs_gaussians& g, const uint8_t* dead,
                                 const unsigned long long* cdf, unsigned long long seed,
                                 unsigned long long step, int32_t* targets, int32_t* counts,

@@ -32,7 +32,7 @@ from typing import List, Optional
 import numpy as np
 import torch
 
-from . import api, synth
+from . import _abi, api, synth
 
 RESOLUTIONS = [(640, 480), (1280, 720), (1280, 720), (1920, 1080)]  # 1:2:1
 
@@ -120,8 +120,11 @@ class _Submitted:
     hosts: List[torch.Tensor]
     ev_render: torch.cuda.Event
     ev_copy: torch.cuda.Event
-    info: object
+    saved: object             # the forward's saved state, released by finish()
     px: int
+    w: int = 0
+    slot: int = 0
+    info: object = None       # its sizes, read by finish()
 
 
 class ServingLoop:
@@ -148,9 +151,13 @@ class ServingLoop:
         self.budget = hbm_budget_bytes
         self.slice_provider = slice_provider
         self.frame = first_frame
+        # deferred sizing: after a worker's first batch its renders never
+        # wait for the device; each batch's status is read once it is delivered
         self.renderers = [api.Renderer(tile=tile, batch=batch,
-                                       pixels_per_thread=pixels_per_thread)
+                                       pixels_per_thread=pixels_per_thread,
+                                       deferred_sizing=True)
                           for _ in range(n_streams)]
+        self.rerenders = 0
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.copy_streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.upd_renderer = api.Renderer()
@@ -293,17 +300,30 @@ class ServingLoop:
             # the unpooled images must outlive the copies
             for o in outs:
                 o.record_stream(cs)
-        info = saved.info()
-        saved.release()
-        return _Submitted(reqs, hosts, ev, dev, info, sum(r.width * r.height for r in reqs))
+        return _Submitted(reqs, hosts, ev, dev, saved, sum(r.width * r.height for r in reqs),
+                          w, slot)
 
-    @staticmethod
-    def finish(b: _Submitted, t0: float):
+    def finish(self, b: _Submitted, t0: float):
         """Wait for a submitted batch: stamp its requests when the render ends
-        and when its images are in host memory."""
+        and when its images are in host memory. A batch that outgrew the
+        deferred capacities (rare: the first batches of new sizes) rendered
+        background; it is rendered and delivered again, and its requests are
+        stamped when that copy is done."""
         b.ev_render.synchronize()
         rendered = time.perf_counter() - t0
         b.ev_copy.synchronize()
+        st = b.saved.status(wait=True)
+        if st == _abi.SWGS_EDEVICE:
+            b.saved.release()
+            self.rerenders += 1
+            again = self.submit_batch(b.w, b.reqs, t0, b.slot)
+            self.finish(again, t0)
+            b.info, b.hosts = again.info, again.hosts
+            return
+        if st != _abi.SWGS_OK:
+            raise _abi.SwgsError(st, "serving batch failed on the device")
+        b.info = b.saved.info()
+        b.saved.release()
         done = time.perf_counter() - t0
         for r in b.reqs:
             r.rendered = rendered

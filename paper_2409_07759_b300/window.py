@@ -12,7 +12,7 @@ from typing import Optional, Sequence
 
 import torch
 
-from . import api
+from . import _abi, api
 
 DEFAULT_SGLD = dict(lr_means=1.6e-4, lr_log_scales=5e-3, lr_quats=1e-3, lr_logits=5e-2,
                     lr_sh_dc=2.5e-3, lr_sh_rest=2.5e-3 / 20.0, beta1=0.9, beta2=0.999, eps=1e-15,
@@ -81,6 +81,9 @@ class WindowTrainer:
         # largest number of tile keys of any step so far (sizes the scratch)
         self.max_keys = 0
         self._rows = None  # data parallel: the eligible rows' exchange buffers
+        # deferred sizing: the last step's forward, checked at the next step
+        self._pending = None
+        self.reruns = 0
 
     def set_window(self, views: Sequence, targets: Sequence[torch.Tensor]):
         """Move the trainer to another window's views and targets (buffers are
@@ -115,6 +118,26 @@ class WindowTrainer:
                 d.copy_(h, non_blocking=True)
             self._copied.record(self._copy_stream)
 
+    def settle(self):
+        """With a deferred-sizing renderer: check the last step's forward (this
+        waits until it has finished on the device, which the next step's
+        launches do not need). A step whose batch outgrew the capacities
+        changed nothing (its optimiser step was gated); it runs again now that
+        the capacities have grown."""
+        p, self._pending = self._pending, None
+        if p is None:
+            return
+        saved, args = p
+        st = saved.status(wait=True)
+        self.max_keys = max(self.max_keys, int(saved.info().n_keys))
+        saved.release()
+        if st == _abi.SWGS_EDEVICE:
+            self.reruns += 1
+            self.step(*args)
+            self.settle()
+        elif st != _abi.SWGS_OK:
+            raise _abi.SwgsError(st, "window step failed on the device")
+
     def step(self, step: int, update: Optional[tuple] = None, render_only: bool = False,
              prefetched: bool = False):
         """One training step. update = (first_slot, src) overwrites a slice
@@ -122,6 +145,7 @@ class WindowTrainer:
         form a streamed slice arrives in) or a GaussianState on the device;
         prefetched = True takes the targets from the last prefetch_targets call.
         Returns the (device) loss tensor."""
+        self.settle()
         if prefetched:
             torch.cuda.current_stream().wait_event(self._copied)
             self._front = 1 - self._front
@@ -146,8 +170,12 @@ class WindowTrainer:
             reg = dict(opacity_reg=self.params["opacity_reg"],
                        scale_reg=self.params["scale_reg"])
         self.r.backward(self.state, saved, self.dl, self.grads, reg=reg, loss=self.loss)
-        self.max_keys = max(self.max_keys, int(saved.info().n_keys))
-        saved.release()
+        if self.r.cfg.deferred_sizing:
+            # its counts are still on the device: check it at the next step
+            self._pending = (saved, (step, update, False, False))
+        else:
+            self.max_keys = max(self.max_keys, int(saved.info().n_keys))
+            saved.release()
         if self.reduce is not None:
             if self._rows is None:
                 from . import dp
