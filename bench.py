@@ -108,8 +108,10 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=1,
                     help="batches each serving worker may have in flight")
     ap.add_argument("--hbm-budget-gb", type=float, default=24.0)
-    ap.add_argument("--sync-sizing", action="store_true",
-                    help="size every forward exactly (two host round trips per batch)")
+    ap.add_argument("--deferred-sizing", action="store_true",
+                    help="training renders without host round trips (capacities learned)")
+    ap.add_argument("--serve-deferred", action="store_true",
+                    help="serving workers render without host round trips")
     ap.add_argument("--sweep-seconds", type=float, default=2.5,
                     help="seconds per rate of the serving sweep (0: no sweep)")
     return ap.parse_args()
@@ -353,7 +355,8 @@ def serving_leg(args):
 
     loop = serving.ServingLoop(st, swin, fps=30.0, n_streams=args.serve_streams, max_batch=16,
                                hbm_budget_bytes=args.hbm_budget_gb * 1e9,
-                               slice_provider=provider, n_slots=args.serve_slots)
+                               slice_provider=provider, n_slots=args.serve_slots,
+                               deferred_sizing=args.serve_deferred)
     loop.reserve(1920, 1080)
     warm = serving.make_requests(args.viewers, args.rate, 1.0, seed=40)
     loop.run(warm, 1.0)
@@ -386,7 +389,8 @@ def serving_sweep(args, st, swin, provider, resolutions, reserve_res):
     from paper_2409_07759_b300 import serving
     loop = serving.ServingLoop(st, swin, fps=30.0, n_streams=args.serve_streams, max_batch=16,
                                hbm_budget_bytes=args.hbm_budget_gb * 1e9,
-                               slice_provider=provider, n_slots=args.serve_slots)
+                               slice_provider=provider, n_slots=args.serve_slots,
+                               deferred_sizing=args.serve_deferred)
     w, h = (int(x) for x in reserve_res.split("x"))
     loop.reserve(w, h)
     rows, best, misses = [], None, 0
@@ -568,7 +572,8 @@ def arm_config(args, views, world=1):
             "bwd_pixels_per_thread": args.bwd_ppt, "bwd_batch": args.bwd_batch,
             "targets": ("8-bit RGB frames (k/255)" if args.targets == "u8" else "float32 RGB"),
             "parallelism": f"dp{world}", "l2": "flushed (256 MB write) before each step",
-            "sizing": "deferred (no host round trip in a step)"}
+            "sizing": ("deferred (no host round trip in a step)" if args.deferred_sizing
+                       else "exact (two host round trips per batch)")}
 
 
 def run_reference(args):
@@ -644,10 +649,9 @@ def main():
     tgt_host = [torch.from_numpy(t).pin_memory() for t in targets]
     tgt_dev = [t.cuda() for t in tgt_host]
     tw, th = (int(x) for x in args.tile.split("x"))
-    # deferred sizing: after the first step no forward waits for the device
     r = api.Renderer(tile=(tw, th), batch=args.batch, pixels_per_thread=args.ppt,
                      bwd_pixels_per_thread=args.bwd_ppt, bwd_batch=args.bwd_batch,
-                     deferred_sizing=not args.sync_sizing)
+                     deferred_sizing=args.deferred_sizing)
     reducer = None
     if world > 1:
         # one all-reduce of the flat gradient buffer (weighted by view share)

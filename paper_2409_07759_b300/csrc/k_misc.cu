@@ -118,7 +118,7 @@ cudaError_t launch_copy_slice(const swgs_gaussians& dst, long long first, long l
 // ---------------------------------------------------------------------------
 __global__ void plan_kernel(GroupDev* groups, int n_groups, ViewDev* views,
                             const int32_t* __restrict__ counts, unsigned long long* totals,
-                            long long rec_cap) {
+                            long long rec_cap, long long act_cap) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     long long act = 0, rec = 0;
     for (int k = 0; k < n_groups; ++k) {
@@ -139,7 +139,8 @@ __global__ void plan_kernel(GroupDev* groups, int n_groups, ViewDev* views,
     }
     if (totals) {
         totals[kTotNeedRecords] = (unsigned long long)rec;
-        if (rec > rec_cap) {
+        totals[kTotNeedActive] = (unsigned long long)act;
+        if (rec > rec_cap || act > act_cap) {
             totals[kTotStatus] |= 1ull;
             rec = 0;
             act = 0;
@@ -150,9 +151,10 @@ __global__ void plan_kernel(GroupDev* groups, int n_groups, ViewDev* views,
 }
 
 cudaError_t launch_plan(GroupDev* groups, int n_groups, ViewDev* views, const int32_t* counts,
-                        unsigned long long* totals, long long rec_cap, cudaStream_t s) {
+                        unsigned long long* totals, long long rec_cap, long long act_cap,
+                        cudaStream_t s) {
     note_launch();
-    plan_kernel<<<1, 32, 0, s>>>(groups, n_groups, views, counts, totals, rec_cap);
+    plan_kernel<<<1, 32, 0, s>>>(groups, n_groups, views, counts, totals, rec_cap, act_cap);
     return cudaGetLastError();
 }
 

@@ -94,7 +94,7 @@ struct swgs_ctx {
     size_t pinned_cap = 0;
     // deferred sizing: capacities learned from earlier calls, and the word the
     // forward raises when a batch outgrew them (the optimiser step tests it)
-    long long cap_rec = 0, cap_sk = 0, cap_keys = 0;
+    long long cap_rec = 0, cap_sk = 0, cap_keys = 0, cap_act = 0;
     Buf gate;
     std::vector<swgs_saved*> pool;
     std::vector<swgs_saved*> all_saved;
@@ -300,6 +300,7 @@ swgs_status resolve_batch(swgs_ctx* c, BatchState& B, bool wait) {
     B.n_keys = (long long)tot[kTotTileKeys];
     const unsigned long long st = tot[kTotStatus];
     c->cap_rec = std::max(c->cap_rec, grow_cap((long long)tot[kTotNeedRecords]));
+    c->cap_act = std::max(c->cap_act, grow_cap((long long)tot[kTotNeedActive]));
     c->cap_sk = std::max(c->cap_sk, grow_cap((long long)tot[kTotNeedSuperKeys]));
     c->cap_keys = std::max(c->cap_keys, grow_cap((long long)tot[kTotNeedTileKeys]));
     if ((st & 1ull) && B.rec_cap > 0) {
@@ -380,7 +381,10 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             return fail(ctx, SWGS_ENOMEM, "allocation failed (deferred totals)");
     }
     CK(cudaMemsetAsync(B.dtot.p, 0, sizeof(unsigned long long) * kTotWords, s));
+    // the active ids over the groups: at most F N (their buffer's size); the
+    // launches over them are sized by the learned capacity when deferred
     B.act_cap = (long long)F * (N > 0 ? N : 1);
+    if (deferred) B.act_cap = std::min(B.act_cap, ctx->cap_act);
     CK(cudaMemcpyAsync(ctx->frames.p, frames.data(), sizeof(int32_t) * F, cudaMemcpyHostToDevice, s));
     std::vector<int> n_act(F, 0);
     if (N > 0) {
@@ -496,7 +500,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
     CK(cudaMemcpyAsync(B.groups.p, B.h_groups.data(), sizeof(GroupDev) * F, cudaMemcpyHostToDevice, s));
     if (deferred)
         CK(launch_plan(P<GroupDev>(B.groups), F, P<ViewDev>(B.views), P<int32_t>(B.counts_b), dtot,
-                       ctx->cap_rec, s));
+                       ctx->cap_rec, B.act_cap, s));
     Records rc = records_of(B);
     {
         StageScope sc_(ctx, SWGS_STAGE_PREPROCESS, s);
@@ -564,6 +568,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             n_sk = (long long)tot[0];
             // the capacities a later deferred call starts from
             ctx->cap_rec = std::max(ctx->cap_rec, grow_cap(rec));
+            ctx->cap_act = std::max(ctx->cap_act, grow_cap(act));
             ctx->cap_sk = std::max(ctx->cap_sk, grow_cap(n_sk));
             ctx->cap_keys = std::max(ctx->cap_keys, grow_cap(n_keys));
         }
@@ -694,7 +699,7 @@ swgs_status backward_batch(swgs_ctx* ctx, const swgs_gaussians* g, BatchState& B
                        cudaMemcpyHostToDevice, s));
     if (dev)  // the uploads carried no counts: restore them (and the weights) on the device
         CK(launch_plan(P<GroupDev>(B.groups), B.n_groups, P<ViewDev>(B.views),
-                       P<int32_t>(B.counts_b), nullptr, 0, s));
+                       P<int32_t>(B.counts_b), nullptr, 0, 0, s));
     const long long n_rec = dev ? B.rec_cap : B.n_rec;
     if (!ensure(ctx, B.grad2d, sizeof(float) * 12 * (size_t)(n_rec > 0 ? n_rec : 1), s) ||
         !ensure(ctx, ctx->counter, 64, s))

@@ -64,8 +64,8 @@ enum BatchTotal {
     kTotTileKeys = 3,   // per-tile list entries
     kTotStatus = 4,     // bit 0: records over capacity, bit 1: keys over capacity,
                         // bit 2: a sort's look-back wait ran out
-    kTotNeedRecords = 5, kTotNeedSuperKeys = 6, kTotNeedTileKeys = 7,
-    kTotWords = 8
+    kTotNeedRecords = 5, kTotNeedSuperKeys = 6, kTotNeedTileKeys = 7, kTotNeedActive = 8,
+    kTotWords = 9
 };
 
 // Records of one (view, Gaussian) pair, structure of float4 arrays.
@@ -548,10 +548,11 @@ cudaError_t launch_copy_slice(const swgs_gaussians& dst, long long first, long l
 // The count-dependent fields of a batch's tables from the active counts on the
 // device (n_active, act_base, rec_base per frame group, rec_base / n_rec per
 // view, the regulariser weights); with `totals`, also the record and active
-// totals, checked against rec_cap (over it: status bit 0 and the counts zeroed,
-// so every later launch of the batch does nothing).
+// totals, checked against rec_cap and act_cap (over: status bit 0 and the
+// counts zeroed, so every later launch of the batch does nothing).
 cudaError_t launch_plan(GroupDev* groups, int n_groups, ViewDev* views, const int32_t* counts,
-                        unsigned long long* totals, long long rec_cap, cudaStream_t s);
+                        unsigned long long* totals, long long rec_cap, long long act_cap,
+                        cudaStream_t s);
 // Copies the key totals (super keys, tile-list entries; none when key_totals
 // is null) into the batch totals and checks them against the capacities (over:
 // status bit 1, counts zeroed); takes the sort's look-back error word into

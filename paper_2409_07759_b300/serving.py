@@ -104,6 +104,7 @@ class ServeStats:
     p99_render_ms: float = 0.0
     inflight_hwm_bytes: float = 0.0  # largest admitted in-flight bytes
     budget_bytes: float = 0.0
+    rerenders: int = 0             # batches rendered again (deferred sizing overflow)
     latencies_ms: np.ndarray = field(repr=False, default=None)
 
     def as_dict(self):
@@ -142,7 +143,7 @@ class ServingLoop:
     def __init__(self, state: api.GaussianState, swin_size: int, fps: float = 30.0,
                  n_streams: int = 2, max_batch: int = 16, hbm_budget_bytes: float = 16e9,
                  slice_provider=None, tile=(16, 16), batch=64, pixels_per_thread=4,
-                 first_frame: int = 0, n_slots: int = 1):
+                 first_frame: int = 0, n_slots: int = 1, deferred_sizing: bool = False):
         self.state = state
         self.n_slots = n_slots   # batches a worker may have in flight
         self.swin = swin_size
@@ -155,7 +156,7 @@ class ServingLoop:
         # wait for the device; each batch's status is read once it is delivered
         self.renderers = [api.Renderer(tile=tile, batch=batch,
                                        pixels_per_thread=pixels_per_thread,
-                                       deferred_sizing=True)
+                                       deferred_sizing=deferred_sizing)
                           for _ in range(n_streams)]
         self.rerenders = 0
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
@@ -359,6 +360,7 @@ class ServingLoop:
 
     def _run(self, requests: List[Request], duration_s: float, keep_images=False):
         self.inflight, self.inflight_hwm = 0.0, 0.0
+        rerenders0 = self.rerenders
         pending = deque()
         todo = deque(requests)
         lock = threading.Lock()
@@ -467,7 +469,8 @@ class ServingLoop:
                            p50_render_ms=float(np.percentile(rlat, 50)),
                            p99_render_ms=float(np.percentile(rlat, 99)),
                            inflight_hwm_bytes=float(self.inflight_hwm),
-                           budget_bytes=float(self.budget), latencies_ms=lat)
+                           budget_bytes=float(self.budget),
+                           rerenders=self.rerenders - rerenders0, latencies_ms=lat)
         return (stats, images) if keep_images else stats
 
     def close(self):

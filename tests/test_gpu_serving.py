@@ -32,13 +32,14 @@ def _provider(pool):
     return get
 
 
-def _loop(budget=16e9, n_streams=2):
+def _loop(budget=16e9, n_streams=2, deferred=False):
     from paper_2409_07759_b300 import api, serving
     scene = synth.config4_initial(SLICE, SWIN, 3)
     st = api.GaussianState.from_scene(scene)
     pool = _pool()
     loop = serving.ServingLoop(st, SWIN, fps=30.0, n_streams=n_streams, max_batch=8,
-                               hbm_budget_bytes=budget, slice_provider=_provider(pool))
+                               hbm_budget_bytes=budget, slice_provider=_provider(pool),
+                               deferred_sizing=deferred)
     return scene, st, pool, loop
 
 
@@ -56,11 +57,13 @@ def test_alone_equals_mixed_batch():
     loop.close()
 
 
-def test_run_serves_everything_and_swaps_slices(oracle_mod):
+@pytest.mark.parametrize("deferred", [False, True])
+def test_run_serves_everything_and_swaps_slices(oracle_mod, deferred):
     """A short real-time run: every request completes, one slice is swapped in
-    per video frame, and the slot buffer equals the Alg. 2 replay."""
+    per video frame, and the slot buffer equals the Alg. 2 replay (with the
+    workers' forwards sized exactly, and with deferred sizing)."""
     from paper_2409_07759_b300 import serving
-    scene, st, pool, loop = _loop()
+    scene, st, pool, loop = _loop(deferred=deferred)
     reqs = serving.make_requests(8, 30.0, 1.5, seed=2, resolutions=RES)
     stats = loop.run(reqs, 1.5)
     assert stats.n == len(reqs) > 100
