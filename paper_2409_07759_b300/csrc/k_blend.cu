@@ -261,7 +261,7 @@ __device__ __forceinline__ bool stage_gaussian_fwd(const Records& rec, uint32_t 
 // pair-counting form, not timed).
 template <bool CLAMP, int NP, bool COUNT>
 __device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float4 gd, float4 ge,
-                                          float2 dx, float2 adx, int pos,
+                                          float2 bdx, float2 k, int pos,
                                           float2 (&T)[NP], float2 (&C0)[NP], float2 (&C1)[NP],
                                           float2 (&C2)[NP], float2 (&py)[NP], int (&last)[2 * NP],
                                           int (&stop)[2 * NP]) {
@@ -269,9 +269,7 @@ __device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         const float2 dy = __fadd2_rn(py[i], hi2(ga));
-        const float2 t1 = __ffma2_rn(hi2(gb), dy, adx);
-        const float2 t2 = __ffma2_rn(__fmul2_rn(lo2(gc), dy), dy, hi2(gc));
-        const float2 v = __ffma2_rn(t1, dx, t2);
+        const float2 v = __ffma2_rn(__ffma2_rn(lo2(gc), dy, bdx), dy, k);
         // -alpha = -min(0.99, 2^v)
         float2 nal = make_float2(-ex2_approx(v.x), -ex2_approx(v.y));
         if (CLAMP) {
@@ -309,8 +307,9 @@ __device__ __forceinline__ void fwd_step(const float4* sa, const float4* sb, con
                                          int (&last)[2 * NP], int (&stop)[2 * NP]) {
     const float4 ga = sa[j], gb = sb[j], gc = sc[j], gd = sd[j], ge = se[j];
     const float2 dx = __fadd2_rn(px2, lo2(ga));
-    const float2 adx = __fmul2_rn(lo2(gb), dx);
-    fwd_pairs<CLAMP, NP, COUNT>(ga, gb, gc, gd, ge, dx, adx, pos, T, C0, C1, C2, py, last, stop);
+    const float2 bdx = __fmul2_rn(hi2(gb), dx);
+    const float2 k = __ffma2_rn(__fmul2_rn(lo2(gb), dx), dx, hi2(gc));
+    fwd_pairs<CLAMP, NP, COUNT>(ga, gb, gc, gd, ge, bdx, k, pos, T, C0, C1, C2, py, last, stop);
 }
 
 // Whether every pixel of the thread has stopped (or lies outside the image).
@@ -580,7 +579,7 @@ __device__ __forceinline__ void block_sync() {
 // needs the pos < last test.
 template <bool CLAMP, bool ALL, int NP>
 __device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float4 gd, float4 ge,
-                                          float2 dx, float2 adx, int pos, const float2 (&py)[NP],
+                                          float2 bdx, float2 k, int pos, const float2 (&py)[NP],
                                           const int (&last)[2 * NP], float2 (&T)[NP],
                                           float2 (&D)[NP], const float2 (&dL0)[NP],
                                           const float2 (&dL1)[NP], const float2 (&dL2)[NP],
@@ -590,9 +589,7 @@ __device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         const float2 dy = __fadd2_rn(py[i], hi2(ga));
-        const float2 t1 = __ffma2_rn(hi2(gb), dy, adx);
-        const float2 t2 = __ffma2_rn(__fmul2_rn(lo2(gc), dy), dy, hi2(gc));
-        const float2 v = __ffma2_rn(t1, dx, t2);
+        const float2 v = __ffma2_rn(__ffma2_rn(lo2(gc), dy, bdx), dy, k);
         const float u0 = ex2_approx(v.x), u1 = ex2_approx(v.y);
         const bool ok0 = (ALL || pos < last[2 * i]) && v.x >= ge.z;
         const bool ok1 = (ALL || pos < last[2 * i + 1]) && v.y >= ge.z;
@@ -621,9 +618,10 @@ __device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float
         const float2 ne = __ffma2_rn(dL0[i], lo2(gd),
                                      __ffma2_rn(dL1[i], hi2(gd), __fmul2_rn(dL2[i], lo2(ge))));
         const float2 nd = __fadd2_rn(D[i], ne);
-        const float2 ngl = __fmul2_rn(T[i], nd);            // -dL/dalpha
         D[i] = __ffma2_rn(na, nd, D[i]);
-        const float2 gm = __fmul2_rn(nag, ngl);
+        // gm = alpha T (E - D): (-w)(D - E), or with the clamp (-alpha where
+        // dalpha/dm is nonzero) T (D - E)
+        const float2 gm = CLAMP ? __fmul2_rn(nag, __fmul2_rn(T[i], nd)) : __fmul2_rn(nw, nd);
         const float2 gy = __fmul2_rn(gm, dy);
         S0 = __fadd2_rn(S0, gm);
         SY = __fadd2_rn(SY, gy);
@@ -731,20 +729,21 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                 const int pos = b0 + j - rg.x;
                 const float4 ga = sa[j], gb = sb[j], gc = sc[j], gd = sd[j], ge = se[j];
                 const float2 dx = __fadd2_rn(px2, lo2(ga));
-                const float2 adx = __fmul2_rn(lo2(gb), dx);
+                const float2 bdx = __fmul2_rn(hi2(gb), dx);
+                const float2 k = __ffma2_rn(__fmul2_rn(lo2(gb), dx), dx, hi2(gc));
                 // The thread's pixels share x, so dx is common to them: only
                 // sum gm, sum gm dy and sum gm dy^2 run per pixel; the dx terms
                 // are applied once below. gm here is alpha dL/dalpha (the
                 // factor -1/2 of dalpha/dm is applied at the flush).
                 float2 S0 = make_float2(0.f, 0.f), SY = S0, SYY = S0, M6 = S0, M7 = S0, M8 = S0;
                 if (__float_as_uint(ge.w) & 1u)
-                    bwd_pairs<true, false, NP>(ga, gb, gc, gd, ge, dx, adx, pos, py, last, T, D,
+                    bwd_pairs<true, false, NP>(ga, gb, gc, gd, ge, bdx, k, pos, py, last, T, D,
                                                dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
                 else if (pos < wfirst)
-                    bwd_pairs<false, true, NP>(ga, gb, gc, gd, ge, dx, adx, pos, py, last, T, D,
+                    bwd_pairs<false, true, NP>(ga, gb, gc, gd, ge, bdx, k, pos, py, last, T, D,
                                                dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
                 else
-                    bwd_pairs<false, false, NP>(ga, gb, gc, gd, ge, dx, adx, pos, py, last, T, D,
+                    bwd_pairs<false, false, NP>(ga, gb, gc, gd, ge, bdx, k, pos, py, last, T, D,
                                                 dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
                 float m[9];
                 m[0] = S0.x + S0.y;
@@ -892,10 +891,9 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                     m8 = fmaf(w, dL2[p], m8);
                     const float e = fmaf(dL0[p], c.x, fmaf(dL1[p], c.y, dL2[p] * c.z));
                     const float diff = e - D[p];
-                    const float ga = T[p] * diff;
                     D[p] = fmaf(a1, diff, D[p]);
                     // dalpha/dm needs the unclamped alpha: a1 = au when it counts
-                    const float gm = au <= kAlphaMax ? a1 * ga : 0.f;
+                    const float gm = au <= kAlphaMax ? w * diff : 0.f;
                     const float gy = gm * dy;
                     s0m += gm;
                     sy += gy;

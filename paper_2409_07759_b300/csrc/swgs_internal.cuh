@@ -300,16 +300,6 @@ constexpr unsigned long long kTagReloc = 0x52454c4fULL;  // "RELO"
 // float not above ln(0.005 / 0.995).
 constexpr float kLogitDead = -0x1.52c582p+2f;
 
-// ---------------------------------------------------------------------------
-// Compositing of one (pixel, Gaussian) pair. The forward and the backward
-// blend call this same function; every operation is an explicit intrinsic so
-// both recompute identical alphas (the backward relies on it to retrace the
-// forward's decisions).
-//   staged: (u, v, qa, qb) and (qc, lo): qa = -A/2 log2e, qb = -B log2e,
-//   qc = -C/2 log2e, lo = log2(opacity).
-// pair_v returns v = q + lo, q = -m/2 log2e, with lo added inside the last
-// FMA of the quadratic form; *au = unclamped o*G = 2^v, *a = min(0.99, *au).
-// ---------------------------------------------------------------------------
 // Element count of a launch sized by a host capacity `cap`: with deferred
 // sizing the true count lives on the device (n, written by an earlier launch)
 // and is capped by the capacity; without it (n null) the capacity is exact.
@@ -324,6 +314,17 @@ __device__ __forceinline__ uint8_t rgb8_of(float c) {
     return (uint8_t)__float2int_rn(__fmul_rn(fminf(fmaxf(c, 0.f), 1.f), 255.f));
 }
 
+// ---------------------------------------------------------------------------
+// Compositing of one (pixel, Gaussian) pair. The forward and the backward
+// blend call this same function; every operation is an explicit intrinsic so
+// both recompute identical alphas (the backward relies on it to retrace the
+// forward's decisions).
+//   staged: (u, v, qa, qb) and (qc, lo): qa = -A/2 log2e, qb = -B log2e,
+//   qc = -C/2 log2e, lo = log2(opacity).
+// pair_v returns v = q + lo, q = -m/2 log2e, as (qc dy + qb dx) dy + k with
+// k = qa dx dx + lo (lo added inside the FMA of the dx term); pair_alpha
+// gives min(0.99, 2^v) and the unclamped *au = o G = 2^v.
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -334,11 +335,13 @@ __device__ __forceinline__ float pair_v(float px, float py, float4 g0, float qc,
                                         float* dx, float* dy) {
     float ddx = __fsub_rn(px, g0.x);
     float ddy = __fsub_rn(py, g0.y);
-    float t1 = __fmaf_rn(g0.w, ddy, __fmul_rn(g0.z, ddx));
-    float t2 = __fmaf_rn(__fmul_rn(qc, ddy), ddy, lo);
+    // q + lo = (qc dy + qb dx) dy + (qa dx dx + lo): the dx terms are common
+    // to every pixel of a column
+    const float k = __fmaf_rn(__fmul_rn(g0.z, ddx), ddx, lo);
+    const float bdx = __fmul_rn(g0.w, ddx);
     *dx = ddx;
     *dy = ddy;
-    return __fmaf_rn(t1, ddx, t2);
+    return __fmaf_rn(__fmaf_rn(qc, ddy, bdx), ddy, k);
 }
 
 // Per-Gaussian lower bound on v = q + lo for a pair to count: m <= 9 and
