@@ -3,9 +3,10 @@
 // colour of Sec. 8.1), and its backward (Alg. 1 loss.backward through the
 // projection).
 //
-// One thread per (frame group, active Gaussian). The thread reads the
-// Gaussian's parameters once and writes one record per view of its frame
-// group, so the parameter bytes are read once per frame, not once per view.
+// One thread per record (view of a frame group x active Gaussian of that
+// frame). Consecutive threads take consecutive active Gaussians of one view, so
+// a Gaussian's parameters are read from HBM once per frame and from L2 by the
+// frame's other views.
 //
 // The discrete quantities (culling, tile rectangle, tile count, depth key)
 // follow a written-down FP32 operation sequence ("key mode": correctly
@@ -171,6 +172,7 @@ struct PreArgs {
     int sx, sy;  // super tile in tiles
     float near_plane;
     Records rec;
+    bool sh_vec;  // SH rows read as float4: K * 3 a multiple of 4, sh 16-byte aligned
 };
 
 __device__ __forceinline__ int find_group_by_record(const GroupDev* groups, int n_groups,
@@ -321,15 +323,33 @@ __global__ void __launch_bounds__(256) preprocess_kernel(PreArgs a, long long n_
     float Y[kMaxShCoeffs];
     sh_basis(K, dx, dy, dz, Y);
     const float* shp = a.g.sh + slot * (long long)(K * 3);
-    float col0 = 0.f, col1 = 0.f, col2 = 0.f;
+    float col[3] = {0.f, 0.f, 0.f};
+    if (a.sh_vec) {
+        // 16-byte loads (K * 3 a multiple of 4, the array 16-byte aligned);
+        // element e = 3 k + ch, taken in order, so each channel sums over k in
+        // the same order as the scalar loop
+        const float4* sh4 = reinterpret_cast<const float4*>(shp);
 #pragma unroll
-    for (int k = 0; k < kMaxShCoeffs; ++k) {
-        if (k < K) {
-            col0 = fmaf(Y[k], shp[3 * k + 0], col0);
-            col1 = fmaf(Y[k], shp[3 * k + 1], col1);
-            col2 = fmaf(Y[k], shp[3 * k + 2], col2);
+        for (int q = 0; q < kMaxShCoeffs * 3 / 4; ++q) {
+            if (4 * q < K * 3) {
+                const float4 c4 = sh4[q];
+                const float c[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    col[(4 * q + e) % 3] = fmaf(Y[(4 * q + e) / 3], c[e], col[(4 * q + e) % 3]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kMaxShCoeffs; ++k) {
+            if (k < K) {
+                col[0] = fmaf(Y[k], shp[3 * k + 0], col[0]);
+                col[1] = fmaf(Y[k], shp[3 * k + 1], col[1]);
+                col[2] = fmaf(Y[k], shp[3 * k + 2], col[2]);
+            }
         }
     }
+    const float col0 = col[0], col1 = col[1], col2 = col[2];
     a.rec.a[r] = make_float4(u, v, opacity, z);
     a.rec.b[r] = make_float4(A, B, C, 0.f);
     a.rec.c[r] = make_float4(fmaxf(col0 + 0.5f, 0.f), fmaxf(col1 + 0.5f, 0.f),
@@ -345,8 +365,10 @@ cudaError_t launch_preprocess(const swgs_gaussians& g, const ViewDev* views, con
                               long long n_rec, int tile_w, int tile_h, float near_plane,
                               Records rec, cudaStream_t s, const unsigned long long* n_dev) {
     if (n_rec <= 0) return cudaSuccess;
+    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    const bool sh_vec = (K * 3) % 4 == 0 && (reinterpret_cast<uintptr_t>(g.sh) & 15u) == 0;
     PreArgs a{g, views, groups, n_groups, ids, total_active, tile_w, tile_h, super_w(tile_w),
-              super_h(tile_w), near_plane, rec};
+              super_h(tile_w), near_plane, rec, sh_vec};
     note_launch();
     const int blocks = div_up(n_rec, 256);
     if (tile_w == 16 && tile_h == 16)
@@ -376,6 +398,7 @@ struct PreBwdArgs {
     bool reg;      // regulariser weights in the groups
     float* loss;   // regulariser value added here (or null)
     const unsigned long long* n_dev;  // deferred sizing: the true total_active
+    bool sh_vec;  // SH rows of values and gradients as float4 (both 16-byte aligned)
 };
 
 // Alg. 1 reg(): with w_o = opacity_reg vc / (V n), w_s = scale_reg vc / (3 V n)
@@ -445,8 +468,20 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {
     const float opacity = 1.0f / (1.0f + __expf(-a.g.opacity_logits[slot]));
     float sh[kMaxShCoeffs * 3];
     const float* shp = a.g.sh + slot * (long long)(K * 3);
+    if (a.sh_vec) {  // 16-byte loads (see PreArgs::sh_vec)
 #pragma unroll
-    for (int k = 0; k < kMaxShCoeffs * 3; ++k) sh[k] = k < K * 3 ? shp[k] : 0.f;
+        for (int q = 0; q < kMaxShCoeffs * 3 / 4; ++q) {
+            const float4 c4 = 4 * q < K * 3 ? reinterpret_cast<const float4*>(shp)[q]
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            sh[4 * q] = c4.x;
+            sh[4 * q + 1] = c4.y;
+            sh[4 * q + 2] = c4.z;
+            sh[4 * q + 3] = c4.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kMaxShCoeffs * 3; ++k) sh[k] = k < K * 3 ? shp[k] : 0.f;
+    }
 
     float gmu[3] = {0.f, 0.f, 0.f};
     float GS[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
@@ -615,9 +650,17 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {
     for (int k = 0; k < 4; ++k) red_add(&a.grads.quats[4 * slot + k], (gq[k] - qn[k] * dq) * qinv);
     red_add(&a.grads.opacity_logits[slot], glogit);
     float* gshp = a.grads.sh + slot * (long long)(K * 3);
+    if (a.sh_vec) {  // one 16-byte reduction per four coefficients
 #pragma unroll
-    for (int k = 0; k < kMaxShCoeffs * 3; ++k)
-        if (k < K * 3) red_add(&gshp[k], gsh[k]);
+        for (int q = 0; q < kMaxShCoeffs * 3 / 4; ++q)
+            if (4 * q < K * 3)
+                red_add_v4(&gshp[4 * q], gsh[4 * q], gsh[4 * q + 1], gsh[4 * q + 2],
+                           gsh[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kMaxShCoeffs * 3; ++k)
+            if (k < K * 3) red_add(&gshp[k], gsh[k]);
+    }
 }
 
 cudaError_t launch_preprocess_bwd(const swgs_gaussians& g, const swgs_gaussians& grads,
@@ -626,7 +669,11 @@ cudaError_t launch_preprocess_bwd(const swgs_gaussians& g, const swgs_gaussians&
                                   const float* grad2d, bool reg, float* loss, cudaStream_t s,
                                   const unsigned long long* n_dev) {
     if (total_active <= 0) return cudaSuccess;
-    PreBwdArgs a{g, grads, views, groups, n_groups, ids, total_active, grad2d, reg, loss, n_dev};
+    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    const bool sh_vec = (K * 3) % 4 == 0 && (reinterpret_cast<uintptr_t>(g.sh) & 15u) == 0 &&
+                        (reinterpret_cast<uintptr_t>(grads.sh) & 15u) == 0;
+    PreBwdArgs a{g, grads, views, groups, n_groups, ids, total_active, grad2d, reg, loss, n_dev,
+                 sh_vec};
     note_launch();
     preprocess_bwd_kernel<<<div_up(total_active, 128), 128, 0, s>>>(a);
     return cudaGetLastError();
