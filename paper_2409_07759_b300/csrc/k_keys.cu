@@ -188,7 +188,7 @@ __device__ __forceinline__ void spread_mask(unsigned m, unsigned out[4]) {
 //    with the bit set at offset + (rank among the warp's set lanes): every
 //    tile's list keeps the depth order. It then writes the tiles' ranges at
 //    their offsets from the scan of the lengths (never past cap).
-constexpr int kExpandWarps = 8;
+constexpr int kExpandWarps = 4;
 
 template <int SX, int SY, bool WRITE>
 __global__ void __launch_bounds__(kExpandWarps * 32)
