@@ -1,7 +1,8 @@
-// k_scan.cu -- device prefix sums (reduce, scan the block totals, scan again
-// with the block offsets). Used for the compaction block counts, the key
-// offsets of the tiles touched in depth order, and the integer CDF of the
-// relocation weights.
+// k_scan.cu -- device prefix sums in two launches: the block totals, then the
+// scan of each block's elements from the sum of the earlier blocks' totals
+// (each block adds those up itself). Used for the compaction block counts, the
+// key offsets of the tiles touched in depth order, the radix histograms and the
+// integer CDF of the relocation weights.
 #include "swgs_internal.cuh"
 
 namespace swgs {
@@ -58,34 +59,20 @@ scan_reduce_kernel(const T* __restrict__ in, long long cap, unsigned long long* 
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// One block scans all the block totals (exclusive) and writes the grand total.
-__global__ void __launch_bounds__(kScanThreads)
-scan_partials_kernel(unsigned long long* __restrict__ part, long long nb,
-                     unsigned long long* __restrict__ total) {
-    __shared__ unsigned long long carry_s;
-    __shared__ unsigned long long chunk_tot;
-    if (threadIdx.x == 0) carry_s = 0;
-    __syncthreads();
-    for (long long b0 = 0; b0 < nb; b0 += kScanThreads) {
-        long long i = b0 + threadIdx.x;
-        unsigned long long v = i < nb ? part[i] : 0ULL;
-        unsigned long long e = block_excl_scan<unsigned long long>(v, &chunk_tot);
-        unsigned long long carry = carry_s;
-        if (i < nb) part[i] = carry + e;
-        __syncthreads();
-        if (threadIdx.x == 0) carry_s = carry + chunk_tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && total) *total = carry_s;
-}
-
-// INCL = false: exclusive, out[n] = total. INCL = true: inclusive.
+// INCL = false: exclusive, out[n] = total. INCL = true: inclusive. The last
+// block writes the grand total to *total (if given).
 template <typename T, bool INCL>
 __global__ void __launch_bounds__(kScanThreads)
 scan_final_kernel(const T* __restrict__ in, T* __restrict__ out, long long cap,
                   const unsigned long long* __restrict__ part,
-                  const unsigned long long* __restrict__ n_dev) {
+                  const unsigned long long* __restrict__ n_dev,
+                  unsigned long long* __restrict__ total) {
     const long long n = dev_count(cap, n_dev);
+    // this block's offset: the earlier blocks' totals
+    unsigned long long p = 0;
+    for (long long b = threadIdx.x; b < (long long)blockIdx.x; b += kScanThreads) p += part[b];
+    __shared__ unsigned long long off;
+    block_excl_scan<unsigned long long>(p, &off);
     const long long base = (long long)blockIdx.x * kScanTile;
     const long long first = base + (long long)threadIdx.x * kScanItems;
     T v[kScanItems];
@@ -98,7 +85,9 @@ scan_final_kernel(const T* __restrict__ in, T* __restrict__ out, long long cap,
     }
     __shared__ T tot;
     T e = block_excl_scan<T>(s, &tot);
-    T run = (T)part[blockIdx.x] + e;
+    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+        *total = off + (unsigned long long)tot;
+    T run = (T)off + e;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         long long i = first + k;
@@ -129,10 +118,8 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, long long n, v
     note_launch();
     scan_reduce_kernel<uint32_t><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part, n_dev);
     note_launch();
-    scan_partials_kernel<<<1, kScanThreads, 0, s>>>(part, nb, total);
-    note_launch();
     scan_final_kernel<uint32_t, false><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, part,
-                                                                             n_dev);
+                                                                             n_dev, total);
     return cudaGetLastError();
 }
 
@@ -147,11 +134,8 @@ cudaError_t inclusive_scan_u64(const unsigned long long* in, unsigned long long*
     scan_reduce_kernel<unsigned long long><<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, part,
                                                                                  nullptr);
     note_launch();
-    scan_partials_kernel<<<1, kScanThreads, 0, s>>>(part, nb, nullptr);
-    note_launch();
-    scan_final_kernel<unsigned long long, true><<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n,
-                                                                                       part,
-                                                                                       nullptr);
+    scan_final_kernel<unsigned long long, true><<<(unsigned)nb, kScanThreads, 0, s>>>(
+        in, out, n, part, nullptr, nullptr);
     return cudaGetLastError();
 }
 
