@@ -170,16 +170,40 @@ __device__ __forceinline__ void adam1(float* p, float* m, float* v, float g, flo
     *v = vv;
 }
 
-// Adam over one parameter array of W floats per slot, one thread per element
-// (coalesced); W is a compile-time width so the slot index is a multiply.
+// The eligible slots among a block's 256 consecutive slots, gathered into
+// s_ids (ascending) by one ballot a warp; returns their count. Eligible slots
+// are a small, scattered fraction of the buffer, so the per-slot work below
+// runs on packed lanes instead of leaving most lanes of most warps idle. Every
+// thread of the block must call it.
+__device__ __forceinline__ int gather_block_slots(bool take, long long i, int32_t* s_ids) {
+    __shared__ int s_wcnt[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, take);
+    if (lane == 0) s_wcnt[warp] = __popc(bal);
+    __syncthreads();
+    int off = 0, c = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const int n = s_wcnt[w];
+        off += w < warp ? n : 0;
+        c += n;
+    }
+    if (take) s_ids[off + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+    __syncthreads();
+    return c;
+}
+
+// Adam over one parameter array of W floats per slot for the c gathered
+// slots, element-wise (a slot's W floats are contiguous); W is a compile-time
+// width so the slot index is a multiply. With clear_grads each gradient
+// element is zeroed once read.
 template <int W, int ARR>
-__device__ __forceinline__ void adam_array(const SgldArgs& a, float* P, float* M, float* V,
-                                           const float* G, float lr) {
-    const long long n = a.g.capacity * W;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-        const long long i = e / W;
-        if (!a.elig[i]) continue;
+__device__ __forceinline__ void adam_slots(const SgldArgs& a, const int32_t* ids, int c,
+                                           float* P, float* M, float* V, float* G, float lr) {
+    for (int f = threadIdx.x; f < c * W; f += blockDim.x) {
+        const int cs = f / W;
+        const long long i = ids[cs];
+        const long long e = i * W + (f - cs * W);
         float g = G[e];
         float l = lr;
         if (ARR == 0 && a.p.mean_grad_decay != 1.f && a.p.swin_size > 0) {
@@ -188,52 +212,23 @@ __device__ __forceinline__ void adam_array(const SgldArgs& a, float* P, float* M
             const int k = max(1, a.p.window_start - a.g.start[i] + a.p.swin_size);
             g *= exp2f((float)(k - 1) * log2f(a.p.mean_grad_decay));
         }
-        if (ARR == 4 && (e - i * W) < 3) l = a.p.lr_sh_dc;  // the DC band
+        if (ARR == 4 && (f - cs * W) < 3) l = a.p.lr_sh_dc;  // the DC band
         adam1(&P[e], &M[e], &V[e], g, l, a);
+        if (a.p.clear_grads) G[e] = 0.f;
     }
 }
 
-// blockIdx.y picks the array: 0 means, 1 log-scales, 2 quaternions, 3 opacity
-// logits, 4 SH.
-__global__ void __launch_bounds__(256) adam_kernel(SgldArgs a) {
-    if (a.gate && *a.gate) return;
-    const swgs_gaussians& g = a.g;
-    const swgs_gaussians& d = a.grads;
-    const swgs_adam_state& m = a.adam;
-    switch (blockIdx.y) {
-        case 0: adam_array<3, 0>(a, g.means, m.m_means, m.v_means, d.means, a.p.lr_means); break;
-        case 1: adam_array<3, 1>(a, g.log_scales, m.m_log_scales, m.v_log_scales, d.log_scales,
-                                 a.p.lr_log_scales); break;
-        case 2: adam_array<4, 2>(a, g.quats, m.m_quats, m.v_quats, d.quats, a.p.lr_quats); break;
-        case 3: adam_array<1, 3>(a, g.opacity_logits, m.m_logits, m.v_logits, d.opacity_logits,
-                                 a.p.lr_logits); break;
-        default:
-            switch (g.sh_degree) {
-                case 0: adam_array<3, 4>(a, g.sh, m.m_sh, m.v_sh, d.sh, a.p.lr_sh_rest); break;
-                case 1: adam_array<12, 4>(a, g.sh, m.m_sh, m.v_sh, d.sh, a.p.lr_sh_rest); break;
-                case 2: adam_array<27, 4>(a, g.sh, m.m_sh, m.v_sh, d.sh, a.p.lr_sh_rest); break;
-                default: adam_array<48, 4>(a, g.sh, m.m_sh, m.v_sh, d.sh, a.p.lr_sh_rest); break;
-            }
+template <int W>
+__device__ __forceinline__ void clear_slots(const int32_t* ids, int c, float* G) {
+    for (int f = threadIdx.x; f < c * W; f += blockDim.x) {
+        const int cs = f / W;
+        G[(long long)ids[cs] * W + (f - cs * W)] = 0.f;
     }
 }
 
-__global__ void __launch_bounds__(256) sgld_kernel(SgldArgs a) {
-    if (a.gate && *a.gate) return;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.g.capacity) return;
-    if (!a.elig[i]) return;
-    if (a.p.clear_grads && a.has_grads) {
-        // the Adam step (an earlier launch) has read this slot's gradients:
-        // leave them zero for the next backward's sums
-        const swgs_gaussians& d = a.grads;
-        const int nsh = 3 * (d.sh_degree + 1) * (d.sh_degree + 1);
-        for (int k = 0; k < 3; ++k) d.means[3 * i + k] = 0.f;
-        for (int k = 0; k < 3; ++k) d.log_scales[3 * i + k] = 0.f;
-        for (int k = 0; k < 4; ++k) d.quats[4 * i + k] = 0.f;
-        d.opacity_logits[i] = 0.f;
-        for (int k = 0; k < nsh; ++k) d.sh[(long long)nsh * i + k] = 0.f;
-    }
-    // noise from the (possibly updated) opacity and covariance
+// SGLD noise of one eligible slot, from its (possibly updated) opacity and
+// covariance: mu += lr_means noise_lr sigmoid(-k (o - t)) Sigma eta.
+__device__ __forceinline__ void noise_slot(const SgldArgs& a, long long i) {
     const float o = 1.f / (1.f + expf(-a.g.opacity_logits[i]));
     const float gate = 1.f / (1.f + expf(a.p.noise_k * (o - a.p.noise_t)));
     const float scale = a.p.lr_means * a.p.noise_lr * gate;
@@ -265,6 +260,47 @@ __global__ void __launch_bounds__(256) sgld_kernel(SgldArgs a) {
         a.g.means[3 * i + k] += scale * (R[k][0] * tq[0] + R[k][1] * tq[1] + R[k][2] * tq[2]);
 }
 
+// One block per 256 slots: the eligible ones are gathered, take the Adam step
+// (if on) array by array, then, once the block's updates are done, the noise.
+template <int WSH>
+__device__ __forceinline__ void adam_sgld_block(const SgldArgs& a) {
+    __shared__ int32_t s_ids[256];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = gather_block_slots(i < a.g.capacity && a.elig[i], i, s_ids);
+    if (c == 0) return;
+    const swgs_gaussians& g = a.g;
+    const swgs_gaussians& d = a.grads;
+    const swgs_adam_state& m = a.adam;
+    if (a.p.adam && a.has_grads && a.has_adam) {
+        adam_slots<3, 0>(a, s_ids, c, g.means, m.m_means, m.v_means, d.means, a.p.lr_means);
+        adam_slots<3, 1>(a, s_ids, c, g.log_scales, m.m_log_scales, m.v_log_scales,
+                         d.log_scales, a.p.lr_log_scales);
+        adam_slots<4, 2>(a, s_ids, c, g.quats, m.m_quats, m.v_quats, d.quats, a.p.lr_quats);
+        adam_slots<1, 3>(a, s_ids, c, g.opacity_logits, m.m_logits, m.v_logits,
+                         d.opacity_logits, a.p.lr_logits);
+        adam_slots<WSH, 4>(a, s_ids, c, g.sh, m.m_sh, m.v_sh, d.sh, a.p.lr_sh_rest);
+        __syncthreads();  // the noise reads the updated opacity and covariance
+    } else if (a.p.clear_grads && a.has_grads) {
+        // no Adam: the gradients are still left zero for the next backward
+        clear_slots<3>(s_ids, c, d.means);
+        clear_slots<3>(s_ids, c, d.log_scales);
+        clear_slots<4>(s_ids, c, d.quats);
+        clear_slots<1>(s_ids, c, d.opacity_logits);
+        clear_slots<WSH>(s_ids, c, d.sh);
+    }
+    for (int t = threadIdx.x; t < c; t += blockDim.x) noise_slot(a, s_ids[t]);
+}
+
+__global__ void __launch_bounds__(256) adam_sgld_kernel(SgldArgs a) {
+    if (a.gate && *a.gate) return;
+    switch (a.g.sh_degree) {
+        case 0: adam_sgld_block<3>(a); break;
+        case 1: adam_sgld_block<12>(a); break;
+        case 2: adam_sgld_block<27>(a); break;
+        default: adam_sgld_block<48>(a); break;
+    }
+}
+
 cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
                         const swgs_adam_state* adam, const uint8_t* elig,
                         const swgs_sgld_params& p, unsigned long long seed,
@@ -283,17 +319,8 @@ cudaError_t launch_sgld(const swgs_gaussians& g, const swgs_gaussians* grads,
     a.bc2 = (float)(1.0 - pow((double)p.beta2, (double)(step + 1)));
     a.seed = seed;
     a.step = step;
-    if (p.adam && grads && adam) {
-        const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
-        long long gx = div_up(g.capacity * 3LL * K, 256);
-        if (gx > 148LL * 16) gx = 148LL * 16;
-        note_launch();
-        adam_kernel<<<dim3((unsigned)gx, 5), 256, 0, s>>>(a);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
     note_launch();
-    sgld_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(a);
+    adam_sgld_kernel<<<div_up(g.capacity, 256), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -309,27 +336,31 @@ struct RelocArgs {
 // weight = floor(sigmoid(logit) 2^32) for alive eligible slots, 0 otherwise;
 // the sigmoid uses the polynomial exp so the integer matches any IEEE-754
 // implementation of the same operation sequence.
+// The FP64 arithmetic runs on the block's alive eligible slots gathered onto
+// packed lanes (FP64 issue is the cost; those slots are a small fraction).
 __global__ void __launch_bounds__(256)
 reloc_weights_kernel(RelocArgs a, unsigned long long* __restrict__ weights,
                      uint8_t* __restrict__ dead) {
+    __shared__ int32_t s_ids[256];
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.g.capacity) return;
-    unsigned long long w = 0;
-    uint8_t d = 0;
-    if (a.elig[i] && !(a.gate && *a.gate)) {
-        const float lg = a.g.opacity_logits[i];
-        if (lg <= kLogitDead) {
-            d = 1;
-        } else {
-            const double e = kd_exp(-(double)lg);
-            const double o = __ddiv_rn(1.0, __dadd_rn(1.0, e));
-            double f = floor(__dmul_rn(o, 4294967296.0));
-            if (f > 4294967295.0) f = 4294967295.0;
-            w = (unsigned long long)f;
-        }
+    const bool live = i < a.g.capacity;
+    const bool el = live && a.elig[i] && !(a.gate && *a.gate);
+    const float lg = el ? a.g.opacity_logits[i] : 0.f;
+    const bool d = el && lg <= kLogitDead;
+    const bool need = el && !d;
+    if (live) {
+        dead[i] = d ? 1 : 0;
+        if (!need) weights[i] = 0;
     }
-    weights[i] = w;
-    dead[i] = d;
+    const int c = gather_block_slots(need, i, s_ids);
+    for (int t = threadIdx.x; t < c; t += blockDim.x) {
+        const long long j = s_ids[t];
+        const double e = kd_exp(-(double)a.g.opacity_logits[j]);
+        const double o = __ddiv_rn(1.0, __dadd_rn(1.0, e));
+        double f = floor(__dmul_rn(o, 4294967296.0));
+        if (f > 4294967295.0) f = 4294967295.0;
+        weights[j] = (unsigned long long)f;
+    }
 }
 
 cudaError_t launch_reloc_weights(const swgs_gaussians& g, const uint8_t* elig,
@@ -406,13 +437,17 @@ __device__ __forceinline__ void zero_moments(const swgs_adam_state& m, long long
 
 // Phase 1 (before the targets change): each dead slot copies its target with
 // the target's relocated opacity and scale.
+// Both phases gather the block's slots that have work onto packed lanes (FP64
+// issue is the cost; those slots are a small fraction).
 __global__ void __launch_bounds__(256)
 reloc_copy_kernel(swgs_gaussians g, swgs_adam_state m, const int32_t* __restrict__ targets,
                   const int32_t* __restrict__ counts, int max_n) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.capacity) return;
+    __shared__ int32_t s_ids[256];
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = gather_block_slots(i0 < g.capacity && targets[i0] >= 0, i0, s_ids);
+    if ((int)threadIdx.x >= c) return;
+    const long long i = s_ids[threadIdx.x];
     const int32_t j = targets[i];
-    if (j < 0) return;
     const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
     int nn = counts[j] + 1;
     if (nn > max_n) nn = max_n;
@@ -433,9 +468,11 @@ reloc_copy_kernel(swgs_gaussians g, swgs_adam_state m, const int32_t* __restrict
 __global__ void __launch_bounds__(256)
 reloc_target_kernel(swgs_gaussians g, swgs_adam_state m, const int32_t* __restrict__ counts,
                     int max_n) {
-    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= g.capacity) return;
-    if (counts[j] == 0) return;
+    __shared__ int32_t s_ids[256];
+    const long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = gather_block_slots(j0 < g.capacity && counts[j0] != 0, j0, s_ids);
+    if ((int)threadIdx.x >= c) return;
+    const long long j = s_ids[threadIdx.x];
     const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
     int nn = counts[j] + 1;
     if (nn > max_n) nn = max_n;
