@@ -108,6 +108,9 @@ def parse():
     ap.add_argument("--serve-slots", type=int, default=1,
                     help="batches each serving worker may have in flight")
     ap.add_argument("--hbm-budget-gb", type=float, default=24.0)
+    ap.add_argument("--no-images", action="store_true",
+                    help="write no rendered image (the step needs only the loss and its "
+                         "gradient, which the forward computes in its epilogue)")
     ap.add_argument("--deferred-sizing", action="store_true",
                     help="training renders without host round trips (capacities learned)")
     ap.add_argument("--serve-deferred", action="store_true",
@@ -573,7 +576,9 @@ def arm_config(args, views, world=1):
             "targets": ("8-bit RGB frames (k/255)" if args.targets == "u8" else "float32 RGB"),
             "parallelism": f"dp{world}", "l2": "flushed (256 MB write) before each step",
             "sizing": ("deferred (no host round trip in a step)" if args.deferred_sizing
-                       else "exact (two host round trips per batch)")}
+                       else "exact (two host round trips per batch)"),
+            "images": ("not written (the L1 term and its gradient are computed in the "
+                       "forward's epilogue)" if args.no_images else "written every step")}
 
 
 def run_reference(args):
@@ -658,7 +663,8 @@ def main():
         # before the optimiser/SGLD step; same seed on every replica
         from paper_2409_07759_b300 import dp
         reducer = dp.GradientReducer(len(views), dp.total_views(len(views), device="cuda"))
-    tr = WindowTrainer(r, state, views, tgt_dev, seed=1234, reduce=reducer)
+    tr = WindowTrainer(r, state, views, tgt_dev, seed=1234, reduce=reducer,
+                       keep_images=not args.no_images)
     # the streamed slices: 6,000-slot slices of the initial state. The timed
     # step takes them resident in HBM (its inputs are on the device); the end
     # to end step streams them from pinned host memory.

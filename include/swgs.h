@@ -295,7 +295,8 @@ swgs_status swgs_render_fwd_rgb8(swgs_ctx *ctx, const swgs_gaussians *g, int32_t
  * swgs_loss_l1 on the rendered images, without a separate pass over them):
  * besides out_rgb it reads target[v] (device float[3*H*W]), writes
  * dL_drgb[v] = sign(rgb - target)/(3*H*W*V) and overwrites *loss (device
- * float) with the mean over views of mean |rgb - target|.
+ * float) with the mean over views of mean |rgb - target|. out_rgb may be NULL:
+ * no image is written (a training step needs only the loss and dL_drgb).
  */
 swgs_status swgs_render_fwd_l1(swgs_ctx *ctx, const swgs_gaussians *g, int32_t n_views,
                                const swgs_view *views, const float *bg, float *const *out_rgb,

@@ -363,7 +363,8 @@ class Renderer:
                   stream=None):
         """Forward render fused with the L1 term: returns (images, dL/drgb, loss,
         saved). targets: float32 [3,H,W] per view, or uint8 [3,H,W] (8-bit
-        frames, read as k * (1/255) in FP32)."""
+        frames, read as k * (1/255) in FP32). out=False writes no image (the
+        loss and its gradient need none; images is then None)."""
         cviews = _views_array(views)
         dts = {t.dtype for t in targets}
         if len(dts) != 1 or dts.pop() not in (torch.float32, torch.uint8):
@@ -376,7 +377,8 @@ class Renderer:
             out = [torch.empty((3, v.height, v.width), dtype=torch.float32, device="cuda")
                    for v in cviews]
         if dL_out is None:
-            dL_out = [torch.empty_like(o) for o in out]
+            dL_out = [torch.empty((3, v.height, v.width), dtype=torch.float32, device="cuda")
+                      for v in cviews]
         if loss_out is None:
             loss_out = torch.zeros(1, dtype=torch.float32, device="cuda")
         bgv = (C.c_float * 3)(*[float(x) for x in bg])
@@ -384,11 +386,12 @@ class Renderer:
         g = state.c_struct()
         fn = _abi.load().swgs_render_fwd_l1_u8 if u8 else _abi.load().swgs_render_fwd_l1
         self._check(fn(
-            self.ctx, C.byref(g), len(cviews), cviews, bgv, _ptr_array(out), None,
+            self.ctx, C.byref(g), len(cviews), cviews, bgv,
+            None if out is False else _ptr_array(out), None,
             _ptr_array(targets), _ptr_array(dL_out), _ptr(loss_out), int(bool(batched)),
             C.byref(handle) if keep_saved else None, self._stream(stream)))
         saved = SavedState(self, handle, cviews) if keep_saved else None
-        return out, dL_out, loss_out, saved
+        return (None if out is False else out), dL_out, loss_out, saved
 
     def backward(self, state: GaussianState, saved: SavedState, dL_drgb, grads: GaussianGrads,
                  reg: Optional[dict] = None, loss: Optional[torch.Tensor] = None, stream=None):

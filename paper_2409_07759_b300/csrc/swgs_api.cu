@@ -1224,14 +1224,16 @@ static swgs_status render_fwd_impl(swgs_ctx* ctx, const swgs_gaussians* g, int32
     ctx->err.clear();
     swgs_status st = check_gaussians(ctx, g, true);
     if (st != SWGS_OK) return st;
-    if (n_views <= 0 || !views || (!out_rgb && !out_rgb8))
+    // the L1 forms need no image: their outputs are the loss and its gradient
+    if (n_views <= 0 || !views || (!out_rgb && !out_rgb8 && !targets))
         return fail(ctx, SWGS_EINVAL, "need at least one view and its output buffer");
     if (n_views > kMaxViewsPerBatch)
         return fail(ctx, SWGS_EINVAL, "at most %d views per call", kMaxViewsPerBatch);
     for (int v = 0; v < n_views; ++v) {
         const swgs_view& w = views[v];
         if (w.width <= 0 || w.height <= 0 || w.width > 16384 || w.height > 16384 ||
-            !(w.fx > 0.f) || !(w.fy > 0.f) || (out_rgb ? !out_rgb[v] : !out_rgb8[v]))
+            !(w.fx > 0.f) || !(w.fy > 0.f) ||
+            (out_rgb ? !out_rgb[v] : (out_rgb8 && !out_rgb8[v])))
             return fail(ctx, SWGS_EINVAL, "view %d: bad size, focal length or output", v);
     }
     if (saved) *saved = nullptr;

@@ -42,7 +42,8 @@ class WindowTrainer:
 
     def __init__(self, renderer: api.Renderer, state: api.GaussianState, views: Sequence,
                  targets: Sequence[torch.Tensor], params: Optional[dict] = None, seed: int = 0,
-                 batched: bool = True, bg=(0.0, 0.0, 0.0), reduce=None):
+                 batched: bool = True, bg=(0.0, 0.0, 0.0), reduce=None,
+                 keep_images: bool = True):
         self.r = renderer
         self.state = state
         self.views = list(views)
@@ -67,8 +68,12 @@ class WindowTrainer:
         for k, a, b in zip(names, m, v):
             self.adam["m_" + k] = a
             self.adam["v_" + k] = b
-        self.images = [torch.empty((3, vw.height, vw.width), dtype=torch.float32, device="cuda")
-                       for vw in self.views]
+        # the rendered images of the last step (keep_images = False: the L1 term
+        # is fused into the forward, so a step needs no image written)
+        self.keep_images = keep_images
+        self.images = None
+        if keep_images:
+            self._alloc_images()
         # host-input pipeline: two target buffers, the back one filled on a side
         # stream while a step reads the front one
         self._bufs = None
@@ -76,7 +81,8 @@ class WindowTrainer:
         self._copy_stream = None
         self._copied = None      # event: the back buffer is filled
         self._released = None    # per buffer: the last step reading it has ended
-        self.dl = [torch.empty_like(i) for i in self.images]
+        self.dl = [torch.empty((3, vw.height, vw.width), dtype=torch.float32, device="cuda")
+                   for vw in self.views]
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
         # largest number of tile keys of any step so far (sizes the scratch)
         self.max_keys = 0
@@ -91,11 +97,13 @@ class WindowTrainer:
         views = list(views)
         if len(views) != len(self.views) or any(
                 (a.width, a.height) != (b.width, b.height) for a, b in zip(views, self.views)):
-            self.images = [torch.empty((3, v.height, v.width), dtype=torch.float32,
-                                       device="cuda") for v in views]
-            self.dl = [torch.empty_like(i) for i in self.images]
+            self.dl = [torch.empty((3, v.height, v.width), dtype=torch.float32, device="cuda")
+                       for v in views]
+            self.images = None
             self._bufs = None
         self.views = views
+        if self.keep_images and self.images is None:
+            self._alloc_images()
         self.targets = list(targets)
         self.frames = sorted({int(v.frame) for v in views})
 
@@ -138,6 +146,10 @@ class WindowTrainer:
         elif st != _abi.SWGS_OK:
             raise _abi.SwgsError(st, "window step failed on the device")
 
+    def _alloc_images(self):
+        self.images = [torch.empty((3, vw.height, vw.width), dtype=torch.float32, device="cuda")
+                       for vw in self.views]
+
     def step(self, step: int, update: Optional[tuple] = None, render_only: bool = False,
              prefetched: bool = False):
         """One training step. update = (first_slot, src) overwrites a slice
@@ -155,12 +167,15 @@ class WindowTrainer:
             self.r.frame_update(self.state, first, src,
                                 src_on_host=not isinstance(src, api.GaussianState))
         if render_only:
+            if self.images is None:
+                self._alloc_images()
             self.r.render(self.state, self.views, bg=self.bg, batched=self.batched,
                           out=self.images)
             return None
         # forward with the L1 term fused into the blend's epilogue
         _, _, _, saved = self.r.render_l1(self.state, self.views, self.targets, bg=self.bg,
-                                          batched=self.batched, out=self.images,
+                                          batched=self.batched,
+                                          out=self.images if self.keep_images else False,
                                           dL_out=self.dl, loss_out=self.loss)
         if not self.params.get("clear_grads", 0):
             # the last step kept its gradients: clear them for this backward

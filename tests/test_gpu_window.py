@@ -92,3 +92,39 @@ def test_prefetched_host_targets_match_device_targets():
     for k in ("means", "log_scales", "quats", "opacity_logits", "sh"):
         assert torch.equal(getattr(st_a, k), getattr(st_b, k)), k
     r.close()
+
+
+def test_step_without_images_matches():
+    """A trainer that writes no image (the L1 term and its gradient come from
+    the forward's epilogue, out=False) takes the same steps, bit for bit (Adam
+    off, as above), as one that keeps the rendered images; render_l1 without an
+    image gives the same dL/drgb and loss (to the atomics' rounding order)."""
+    from paper_2409_07759_b300 import api
+    from paper_2409_07759_b300.window import WindowTrainer, DEFAULT_SGLD
+    sc, views, targets = _window()
+    r = api.Renderer()
+    tg = [torch.from_numpy(t).cuda() for t in targets]
+    st = api.GaussianState.from_scene(sc)
+    _, dl_a, loss_a, sa = r.render_l1(st, views, tg)
+    img, dl_b, loss_b, sb = r.render_l1(st, views, tg, out=False)
+    assert img is None
+    # the loss is summed by atomics (order-dependent rounding)
+    assert float(loss_b.item()) == pytest.approx(float(loss_a.item()), rel=1e-6)
+    for a, b in zip(dl_a, dl_b):
+        assert torch.equal(a, b)
+    sa.release()
+    sb.release()
+    out = []
+    for keep in (True, False):
+        s = api.GaussianState.from_scene(sc)
+        tr = WindowTrainer(r, s, views, tg, seed=5, params=dict(DEFAULT_SGLD, adam=0),
+                           keep_images=keep)
+        assert (tr.images is None) != keep
+        for k in range(2):
+            tr.step(k)
+        tr.settle()
+        torch.cuda.synchronize()
+        out.append({k: getattr(s, k).clone() for k in ("means", "log_scales", "quats",
+                                                       "opacity_logits", "sh")})
+    for k in out[0]:
+        assert torch.equal(out[0][k], out[1][k]), k
