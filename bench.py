@@ -39,13 +39,16 @@ sys.path.insert(0, str(ROOT))
 # ex2; its adjoint about 40 plus one ex2.
 FLOP_PER_PAIR_FWD = 12
 FLOP_PER_PAIR_BWD = 40
-# The same counted per issued operation of this implementation (an FMA counts
-# 2), reported beside: forward d 2, m 9, G 2, o*G 1, T(1 - alpha) 2, colour
-# 7; backward alpha 14, T recovery 2, colour weights 4, dL/dalpha 9,
-# colour-behind 9, dalpha/dm 2, sums 9 per pair (the conic/centre/opacity
-# chain rule runs once per Gaussian and tile, not per pair).
-OWN_FLOP_PER_PAIR_FWD = 23
-OWN_FLOP_PER_PAIR_BWD = 49
+# The same counted per issued FP32 operation of this implementation (an FMA
+# counts 2), reported beside. Per pair, with the terms common to a thread's
+# column of pixels (dx, qb dx, qa dx dx + lo) shared by its 4 (forward) or 8
+# (reverse) pixels: forward offset 1.25, Mahalanobis form 5, T(1 - alpha) and
+# the T update 3, colour 7 = 16; reverse alpha recompute 5.6, T recovery 2,
+# colour weights 7, E and D - E 6, colour-behind 2, alpha dL/dalpha 1,
+# moments 5, the per-Gaussian sums before the warp reduction 2.6 = 31 (the
+# conic/centre/opacity chain rule runs once per Gaussian and tile).
+OWN_FLOP_PER_PAIR_FWD = 16
+OWN_FLOP_PER_PAIR_BWD = 31
 
 # DRAM bytes (read + write) per launch from one ncu capture of the full-size
 # window step, keyed by stage and launch shape, with a digest of the sources
@@ -53,9 +56,9 @@ OWN_FLOP_PER_PAIR_BWD = 49
 # captured again.
 TRAFFIC_CAPTURES = {
     ("blend_bwd", "16x16/b64/ppt8"): {
-        "bytes": 1_232_475_392 + 17_421_056,
+        "bytes": 1_232_771_328 + 17_458_944,
         "sources": ("csrc/k_blend.cu", "csrc/swgs_internal.cuh"),
-        "digest": "adc18d0a3ffb57f5",
+        "digest": "9756b693e0047f23",
     },
 }
 
