@@ -400,7 +400,7 @@ def serving_sweep(args, st, swin, provider, resolutions, reserve_res):
     w, h = (int(x) for x in reserve_res.split("x"))
     loop.reserve(w, h)
     rows, best, misses = [], None, 0
-    for rate in (30, 60, 90, 120, 160, 200, 250, 300, 400, 500):
+    for rate in (10, 20, 30, 45, 60, 90, 120, 160, 200, 250, 300, 400, 500):
         warm = serving.make_requests(args.viewers, rate, 0.5, seed=50 + rate,
                                      resolutions=resolutions)
         loop.run(warm, 0.5)
