@@ -435,68 +435,83 @@ __device__ __forceinline__ void zero_moments(const swgs_adam_state& m, long long
     for (int k = 0; k < 3 * K; ++k) { m.m_sh[i * 3 * K + k] = 0.f; m.v_sh[i * 3 * K + k] = 0.f; }
 }
 
-// Phase 1 (before the targets change): each dead slot copies its target with
-// the target's relocated opacity and scale.
-// Both phases gather the block's slots that have work onto packed lanes (FP64
-// issue is the cost; those slots are a small fraction).
+// Phase 0: each target's relocated values, once (FP64, on the block's target
+// slots gathered onto packed lanes): log(ratio), the log-scale shift, and the
+// new opacity logit log(o') - log(1 - o').
 __global__ void __launch_bounds__(256)
-reloc_copy_kernel(swgs_gaussians g, swgs_adam_state m, const int32_t* __restrict__ targets,
-                  const int32_t* __restrict__ counts, int max_n) {
+reloc_values_kernel(swgs_gaussians g, const int32_t* __restrict__ counts, int max_n,
+                    double* __restrict__ lr, float* __restrict__ nl) {
     __shared__ int32_t s_ids[256];
-    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = gather_block_slots(i0 < g.capacity && targets[i0] >= 0, i0, s_ids);
+    const long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = gather_block_slots(j0 < g.capacity && counts[j0] != 0, j0, s_ids);
     if ((int)threadIdx.x >= c) return;
-    const long long i = s_ids[threadIdx.x];
-    const int32_t j = targets[i];
-    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    const long long j = s_ids[threadIdx.x];
     int nn = counts[j] + 1;
     if (nn > max_n) nn = max_n;
     const double o = 1.0 / (1.0 + exp(-(double)g.opacity_logits[j]));
     double on, ratio;
     reloc_values(o, nn, &on, &ratio);
+    lr[j] = log(ratio);
+    nl[j] = (float)(log(on) - log1p(-on));
+}
+
+// Phase 1 (before the targets change): each dead slot copies its target with
+// the target's relocated opacity and scale. Both phases gather the block's
+// slots that have work onto packed lanes.
+__global__ void __launch_bounds__(256)
+reloc_copy_kernel(swgs_gaussians g, swgs_adam_state m, const int32_t* __restrict__ targets,
+                  const double* __restrict__ lr, const float* __restrict__ nl) {
+    __shared__ int32_t s_ids[256];
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = gather_block_slots(i0 < g.capacity && targets[i0] >= 0, i0, s_ids);
+    if ((int)threadIdx.x >= c) return;
+    const long long i = s_ids[threadIdx.x];
+    const long long j = targets[i];
+    const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
+    const double l = lr[j];
     for (int k = 0; k < 3; ++k) {
-        g.means[3 * i + k] = g.means[3 * (long long)j + k];
-        g.log_scales[3 * i + k] = (float)((double)g.log_scales[3 * (long long)j + k] + log(ratio));
+        g.means[3 * i + k] = g.means[3 * j + k];
+        g.log_scales[3 * i + k] = (float)((double)g.log_scales[3 * j + k] + l);
     }
-    for (int k = 0; k < 4; ++k) g.quats[4 * i + k] = g.quats[4 * (long long)j + k];
-    g.opacity_logits[i] = (float)(log(on) - log1p(-on));
-    for (int k = 0; k < 3 * K; ++k) g.sh[i * 3 * K + k] = g.sh[(long long)j * 3 * K + k];
+    for (int k = 0; k < 4; ++k) g.quats[4 * i + k] = g.quats[4 * j + k];
+    g.opacity_logits[i] = nl[j];
+    for (int k = 0; k < 3 * K; ++k) g.sh[i * 3 * K + k] = g.sh[j * 3 * K + k];
     zero_moments(m, i, K);
 }
 
 // Phase 2: every target takes its own relocated opacity and scale.
 __global__ void __launch_bounds__(256)
 reloc_target_kernel(swgs_gaussians g, swgs_adam_state m, const int32_t* __restrict__ counts,
-                    int max_n) {
+                    const double* __restrict__ lr, const float* __restrict__ nl) {
     __shared__ int32_t s_ids[256];
     const long long j0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = gather_block_slots(j0 < g.capacity && counts[j0] != 0, j0, s_ids);
     if ((int)threadIdx.x >= c) return;
     const long long j = s_ids[threadIdx.x];
     const int K = (g.sh_degree + 1) * (g.sh_degree + 1);
-    int nn = counts[j] + 1;
-    if (nn > max_n) nn = max_n;
-    const double o = 1.0 / (1.0 + exp(-(double)g.opacity_logits[j]));
-    double on, ratio;
-    reloc_values(o, nn, &on, &ratio);
+    const double l = lr[j];
     for (int k = 0; k < 3; ++k)
-        g.log_scales[3 * j + k] = (float)((double)g.log_scales[3 * j + k] + log(ratio));
-    g.opacity_logits[j] = (float)(log(on) - log1p(-on));
+        g.log_scales[3 * j + k] = (float)((double)g.log_scales[3 * j + k] + l);
+    g.opacity_logits[j] = nl[j];
     zero_moments(m, j, K);
 }
 
 cudaError_t launch_reloc_apply(const swgs_gaussians& g, const swgs_adam_state* adam,
                                const int32_t* targets, const int32_t* counts, int max_n,
-                               cudaStream_t s) {
+                               double* lr, float* nl, cudaStream_t s) {
     swgs_adam_state m{};
     if (adam) m = *adam;
     const int grid = div_up(g.capacity, 256);
     note_launch();
-    reloc_copy_kernel<<<grid, 256, 0, s>>>(g, m, targets, counts, max_n);
+    reloc_values_kernel<<<grid, 256, 0, s>>>(g, counts, max_n, lr, nl);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     note_launch();
-    reloc_target_kernel<<<grid, 256, 0, s>>>(g, m, counts, max_n);
+    reloc_copy_kernel<<<grid, 256, 0, s>>>(g, m, targets, lr, nl);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    note_launch();
+    reloc_target_kernel<<<grid, 256, 0, s>>>(g, m, counts, lr, nl);
     return cudaGetLastError();
 }
 

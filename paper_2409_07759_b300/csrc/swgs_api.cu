@@ -89,7 +89,7 @@ struct swgs_ctx {
         vals_tmp, vals_b, sranges, tile_cnt, tile_off, mature_ids, mature_stage, codec_keys_a,
         codec_keys_b, codec_vals_a, codec_vals_b, codec_flags, codec_idx, codec_stage, sort_tmp,
         counter, totals, l1_tab, elig, reloc_w, reloc_cdf, reloc_dead, reloc_tg, reloc_cnt,
-        reloc_nd, sort_err;
+        reloc_nd, reloc_lr, reloc_nl, sort_err;
     void* pinned = nullptr;
     size_t pinned_cap = 0;
     // deferred sizing: capacities learned from earlier calls, and the word the
@@ -874,7 +874,8 @@ void swgs_destroy(swgs_ctx* ctx) {
                  &ctx->codec_vals_a, &ctx->codec_vals_b, &ctx->codec_flags, &ctx->codec_idx,
                  &ctx->codec_stage, &ctx->sort_tmp, &ctx->counter, &ctx->totals, &ctx->l1_tab,
                  &ctx->elig, &ctx->reloc_w, &ctx->reloc_cdf, &ctx->reloc_dead, &ctx->reloc_tg,
-                 &ctx->reloc_cnt, &ctx->reloc_nd, &ctx->sort_err, &ctx->gate};
+                 &ctx->reloc_cnt, &ctx->reloc_nd, &ctx->reloc_lr, &ctx->reloc_nl, &ctx->sort_err,
+                 &ctx->gate};
     for (Buf* b : bs) ctx_free(ctx, *b, s);
     for (swgs_saved* sv : ctx->all_saved) {
         free_saved_buffers(ctx, sv, s);
@@ -1679,6 +1680,8 @@ swgs_status swgs_sgld_step(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_ga
             !ensure(ctx, ctx->reloc_dead, (size_t)N, s) ||
             !ensure(ctx, ctx->reloc_cnt, 4 * (size_t)N, s) ||
             !ensure(ctx, ctx->reloc_nd, 64, s) ||
+            !ensure(ctx, ctx->reloc_lr, 8 * (size_t)N, s) ||
+            !ensure(ctx, ctx->reloc_nl, 4 * (size_t)N, s) ||
             !ensure(ctx, ctx->scan_tmp, scan_u64_temp_bytes(N) + 64, s) ||
             (!targets && !ensure(ctx, ctx->reloc_tg, 4 * (size_t)N, s)))
             return fail(ctx, SWGS_ENOMEM, "allocation failed (relocation)");
@@ -1693,7 +1696,8 @@ swgs_status swgs_sgld_step(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_ga
         CK(launch_reloc_sample(*g, P<uint8_t>(ctx->reloc_dead), P<unsigned long long>(ctx->reloc_cdf),
                                seed, step, tg, P<int32_t>(ctx->reloc_cnt),
                                P<unsigned long long>(ctx->reloc_nd), s));
-        CK(launch_reloc_apply(*g, adam, tg, P<int32_t>(ctx->reloc_cnt), params->max_n, s));
+        CK(launch_reloc_apply(*g, adam, tg, P<int32_t>(ctx->reloc_cnt), params->max_n,
+                              P<double>(ctx->reloc_lr), P<float>(ctx->reloc_nl), s));
         if (n_relocated) {
             CK(cudaMemcpyAsync(ctx->pinned, ctx->reloc_nd.p, 8, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));

@@ -589,8 +589,9 @@ cudaError_t launch_reloc_sample(const swgs_gaussians& g, const uint8_t* dead,
                                 const unsigned long long* cdf, unsigned long long seed,
                                 unsigned long long step, int32_t* targets, int32_t* counts,
                                 unsigned long long* n_dead, cudaStream_t s);
+// lr, nl: capacity-sized scratch (per target: log of the scale ratio, new logit)
 cudaError_t launch_reloc_apply(const swgs_gaussians& g, const swgs_adam_state* adam,
                                const int32_t* targets, const int32_t* counts, int max_n,
-                               cudaStream_t s);
+                               double* lr, float* nl, cudaStream_t s);
 
 }  // namespace swgs
