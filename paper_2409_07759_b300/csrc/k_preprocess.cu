@@ -422,7 +422,10 @@ __device__ __forceinline__ void reg_loss_add(float v, float* loss) {
     }
 }
 
-__global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {
+// At least 4 blocks of 128 per SM (128 registers, a small spill): 201 registers
+// unbounded (2 blocks), 168 with the SH coefficients read where used (3 blocks);
+// 5 and 6 blocks spill more than they gain (measured).
+__global__ void __launch_bounds__(128, 4) preprocess_bwd_kernel(PreBwdArgs a) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const bool in = t < dev_count(a.total_active, a.n_dev);
     const int gi = in ? find_group(a.groups, a.n_groups, t) : 0;
@@ -466,22 +469,18 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) Sg[r][c] = M[r][0] * M[c][0] + M[r][1] * M[c][1] + M[r][2] * M[c][2];
     const float opacity = 1.0f / (1.0f + __expf(-a.g.opacity_logits[slot]));
-    float sh[kMaxShCoeffs * 3];
+    // the SH coefficients are read where used, once for a view's colour and once
+    // for its gradients (L1 hits after the first view), not held in registers:
+    // the gradient sums already take 3K of them
     const float* shp = a.g.sh + slot * (long long)(K * 3);
-    if (a.sh_vec) {  // 16-byte loads (see PreArgs::sh_vec)
+    const bool sh_vec = a.sh_vec;
+    auto sh4 = [&](int q) {  // coefficients 4q .. 4q + 3 (zero past 3K)
+        if (sh_vec) return reinterpret_cast<const float4*>(shp)[q];
+        float c[4];
 #pragma unroll
-        for (int q = 0; q < kMaxShCoeffs * 3 / 4; ++q) {
-            const float4 c4 = 4 * q < K * 3 ? reinterpret_cast<const float4*>(shp)[q]
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
-            sh[4 * q] = c4.x;
-            sh[4 * q + 1] = c4.y;
-            sh[4 * q + 2] = c4.z;
-            sh[4 * q + 3] = c4.w;
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < kMaxShCoeffs * 3; ++k) sh[k] = k < K * 3 ? shp[k] : 0.f;
-    }
+        for (int t = 0; t < 4; ++t) c[t] = 4 * q + t < K * 3 ? shp[4 * q + t] : 0.f;
+        return make_float4(c[0], c[1], c[2], c[3]);
+    };
 
     float gmu[3] = {0.f, 0.f, 0.f};
     float GS[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
@@ -512,21 +511,36 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(PreBwdArgs a) {
             dx *= inv; dy *= inv; dz *= inv;
             float Y[kMaxShCoeffs];
             sh_basis(K, dx, dy, dz, Y);
+            // the view's colour, summed over k in the forward's order per channel
+            float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < kMaxShCoeffs * 3 / 4; ++q) {
+                if (4 * q >= K * 3) break;
+                const float4 c4 = sh4(q);
+                const float c[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int e = 4 * q + t;
+                    if (e < K * 3) acc[e % 3] = fmaf(Y[e / 3], c[t], acc[e % 3]);
+                }
+            }
+            float gc[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) gc[ch] = (acc[ch] + 0.5f > 0.f) ? gcol[ch] : 0.f;
             float wgt[kMaxShCoeffs];
 #pragma unroll
             for (int k = 0; k < kMaxShCoeffs; ++k) wgt[k] = 0.f;
 #pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                float acc = 0.f;
+            for (int q = 0; q < kMaxShCoeffs * 3 / 4; ++q) {
+                if (4 * q >= K * 3) break;
+                const float4 c4 = sh4(q);
+                const float c[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-                for (int k = 0; k < kMaxShCoeffs; ++k)
-                    if (k < K) acc = fmaf(Y[k], sh[3 * k + ch], acc);
-                const float gc = (acc + 0.5f > 0.f) ? gcol[ch] : 0.f;
-#pragma unroll
-                for (int k = 0; k < kMaxShCoeffs; ++k) {
-                    if (k < K) {
-                        gsh[3 * k + ch] += Y[k] * gc;
-                        wgt[k] += gc * sh[3 * k + ch];
+                for (int t = 0; t < 4; ++t) {
+                    const int e = 4 * q + t;
+                    if (e < K * 3) {
+                        gsh[e] += Y[e / 3] * gc[e % 3];
+                        wgt[e / 3] += gc[e % 3] * c[t];
                     }
                 }
             }
