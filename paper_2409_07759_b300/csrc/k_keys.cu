@@ -79,7 +79,8 @@ __device__ __forceinline__ int record_row_run(const Records& rec, uint32_t r, sh
 // (global super tile id) | (coverage mask << 16) and the value r. Bit
 // ly*SX + lx of the mask is set when the record covers tile (lx, ly) of the
 // super tile by the row rule. The sort reads only the low 16 bits (the super
-// tile id), so the mask rides along. Positions of the record's range left over
+// tile id), so the mask rides along. Per super row only the super columns its
+// tile rows' runs reach are visited. Positions of the record's range left over
 // (the projection's count is an upper bound) get the key of its first super
 // tile with an empty mask, which the expansion passes over. The super tile's
 // shape (SX x SY tiles) is a template parameter, so the mask loops run over
@@ -100,7 +101,7 @@ emit_supers_kernel(const uint32_t* __restrict__ order, const uint32_t* __restric
         if (tiles == 0) continue;
         const short4 rc = rec.rect[r];
         const ViewDev& V = views[find_view_by_record(views, n_views, (int)r)];
-        const int x0 = rc.x / sx, x1 = rc.y / sx, y0 = rc.z / sy, y1 = rc.w / sy;
+        const int x0 = rc.x / sx, y0 = rc.z / sy, y1 = rc.w / sy;
         uint32_t o = offsets[k];
         const uint32_t o_end = o + (uint32_t)rec.supers[r];
         for (int y = y0; y <= y1; ++y) {
@@ -113,7 +114,17 @@ emit_supers_kernel(const uint32_t* __restrict__ order, const uint32_t* __restric
                 if (ty >= rc.z && ty <= rc.w)
                     n[ly] = record_row_run(rec, r, rc, ty, tile_w, tile_h, &f[ly]);
             }
-            for (int x = x0; x <= x1; ++x) {
+            // only the super columns the rows' runs reach (the rest have empty masks)
+            int cmin = 0x7fffffff, cmax = -1;
+#pragma unroll
+            for (int ly = 0; ly < SY; ++ly) {
+                if (n[ly] > 0) {
+                    cmin = min(cmin, f[ly]);
+                    cmax = max(cmax, f[ly] + n[ly] - 1);
+                }
+            }
+            if (cmax < 0) continue;
+            for (int x = cmin / sx; x <= cmax / sx; ++x) {
                 const int tx0 = x * sx;
                 unsigned m = 0;
 #pragma unroll
