@@ -42,7 +42,9 @@ typedef enum swgs_status {
 } swgs_status;
 
 /* Scratch allocator: returns device memory usable on `stream` (NULL on
- * failure). free receives the same pointer and size. */
+ * failure), aligned to 256 bytes as cudaMalloc's is (the kernels read their
+ * scratch with 16-byte vector loads; a pointer aligned less is freed and the
+ * call fails with SWGS_ENOMEM). free receives the same pointer and size. */
 typedef void *(*swgs_alloc_fn)(void *user, size_t bytes, void *stream);
 typedef void (*swgs_free_fn)(void *user, void *ptr, size_t bytes, void *stream);
 

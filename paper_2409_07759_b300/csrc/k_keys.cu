@@ -314,24 +314,44 @@ cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, cons
 }
 
 // sranges[t] = [first, last+1) of super tile t (the low 16 key bits) in the
-// sorted super keys (sranges zeroed before).
+// sorted super keys (sranges zeroed before). Four consecutive keys a thread
+// (one 16-byte load; the key buffers are 16-byte aligned) and the keys on
+// either side.
 __global__ void super_ranges_kernel(const uint32_t* __restrict__ keys, long long cap,
                                     long long n_supers, int2* __restrict__ ranges,
                                     const unsigned long long* __restrict__ n_dev) {
     const long long n = dev_count(cap, n_dev);
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t t = keys[i] & 0xffffu;
-    if (t >= n_supers) return;
-    if (i == 0 || (keys[i - 1] & 0xffffu) != t) ranges[t].x = (int)i;
-    if (i == n - 1 || (keys[i + 1] & 0xffffu) != t) ranges[t].y = (int)(i + 1);
+    const long long i0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (i0 >= n) return;
+    constexpr uint32_t kNone = 0xffffffffu;  // no key: differs from every 16-bit id
+    uint32_t t[6];
+    t[0] = i0 > 0 ? (keys[i0 - 1] & 0xffffu) : kNone;
+    if (i0 + 4 <= n) {
+        const uint4 v = *reinterpret_cast<const uint4*>(keys + i0);
+        t[1] = v.x & 0xffffu;
+        t[2] = v.y & 0xffffu;
+        t[3] = v.z & 0xffffu;
+        t[4] = v.w & 0xffffu;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t[j + 1] = i0 + j < n ? (keys[i0 + j] & 0xffffu) : kNone;
+    }
+    t[5] = i0 + 4 < n ? (keys[i0 + 4] & 0xffffu) : kNone;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t c = t[j + 1];
+        if (c >= (uint32_t)n_supers) continue;  // also past n (kNone)
+        if (t[j] != c) ranges[c].x = (int)(i0 + j);
+        if (t[j + 2] != c) ranges[c].y = (int)(i0 + j + 1);
+    }
 }
 
 cudaError_t launch_super_ranges(const uint32_t* keys, long long n, long long n_supers,
                                 int2* ranges, cudaStream_t s, const unsigned long long* n_dev) {
     if (n <= 0) return cudaSuccess;
     note_launch();
-    super_ranges_kernel<<<div_up(n, 256), 256, 0, s>>>(keys, n, n_supers, ranges, n_dev);
+    super_ranges_kernel<<<div_up(div_up(n, 4), 256), 256, 0, s>>>(keys, n, n_supers, ranges,
+                                                                   n_dev);
     return cudaGetLastError();
 }
 

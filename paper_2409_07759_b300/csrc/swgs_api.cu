@@ -158,7 +158,15 @@ struct StageScope {
 };
 
 void* ctx_alloc(swgs_ctx* c, size_t bytes, cudaStream_t s) {
-    if (c->alloc) return c->alloc(c->user, bytes, (void*)s);
+    if (c->alloc) {
+        void* p = c->alloc(c->user, bytes, (void*)s);
+        // the kernels read scratch with 16-byte vector loads
+        if (p && (reinterpret_cast<uintptr_t>(p) & 255u) != 0) {
+            if (c->free_fn) c->free_fn(c->user, p, bytes, (void*)s);
+            return nullptr;
+        }
+        return p;
+    }
     void* p = nullptr;
     if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) return nullptr;
     return p;
