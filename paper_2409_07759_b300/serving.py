@@ -89,6 +89,43 @@ def make_requests(n_viewers: int, rate_hz: float, duration_s: float, seed: int =
     return reqs
 
 
+class _SharedLock:
+    """Shared holders (batch submissions, which may wait for their own stream
+    while the library sizes a batch) or one exclusive holder (a slice update);
+    a waiting exclusive request lets no new shared holder in."""
+
+    def __init__(self):
+        self._c = threading.Condition()
+        self._shared = 0
+        self._excl = False
+        self._excl_waiting = 0
+
+    def acquire_shared(self):
+        with self._c:
+            while self._excl or self._excl_waiting:
+                self._c.wait()
+            self._shared += 1
+
+    def release_shared(self):
+        with self._c:
+            self._shared -= 1
+            if self._shared == 0:
+                self._c.notify_all()
+
+    def acquire_exclusive(self):
+        with self._c:
+            self._excl_waiting += 1
+            while self._excl or self._shared:
+                self._c.wait()
+            self._excl_waiting -= 1
+            self._excl = True
+
+    def release_exclusive(self):
+        with self._c:
+            self._excl = False
+            self._c.notify_all()
+
+
 @dataclass
 class ServeStats:
     n: int
@@ -163,7 +200,10 @@ class ServingLoop:
         self.copy_streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.upd_renderer = api.Renderer()
         self.upd_stream = torch.cuda.Stream()
-        self.submit_lock = threading.Lock()
+        # submissions hold it shared (they run concurrently, each on its own
+        # context and stream), a slice update exclusively: a render reads
+        # either the old slice or the new one, never a mix
+        self.submit_lock = _SharedLock()
         self.last_render_ev = [None] * n_streams
         self.update_ev: Optional[torch.cuda.Event] = None
         # Device bytes of one request: view_bytes (its records: one per active
@@ -240,7 +280,8 @@ class ServingLoop:
         the copy."""
         host = self.slice_provider(frame)
         first, count = api.slice_range(frame, self.swin, self.state.n)
-        with self.submit_lock:
+        self.submit_lock.acquire_exclusive()
+        try:
             for ev in self.last_render_ev:
                 if ev is not None:
                     self.upd_stream.wait_event(ev)
@@ -250,6 +291,8 @@ class ServingLoop:
             ev.record(self.upd_stream)
             self.update_ev = ev
             self.frame = frame
+        finally:
+            self.submit_lock.release_exclusive()
 
     # -- one batch on one worker stream -----------------------------------------
     def submit_batch(self, w: int, reqs: List[Request], t0: float, slot: int = 0) -> _Submitted:
@@ -273,7 +316,8 @@ class ServingLoop:
                         for r in reqs]
             hosts = [torch.empty((r.height, r.width, 3), dtype=torch.uint8).pin_memory()
                      for r in reqs]
-        with self.submit_lock:
+        self.submit_lock.acquire_shared()
+        try:
             frame = self.frame
             views = []
             for r in reqs:
@@ -289,6 +333,8 @@ class ServingLoop:
             ev = torch.cuda.Event()
             ev.record(s)
             self.last_render_ev[w] = ev
+        finally:
+            self.submit_lock.release_shared()
         # delivery on the worker's copy stream, after the render
         cs = self.copy_streams[w]
         cs.wait_event(ev)
