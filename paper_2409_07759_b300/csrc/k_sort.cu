@@ -267,12 +267,16 @@ struct OnePlan {
     int bins[kMaxOnePasses];
 };
 static_assert(kOneHistBytes == (size_t)kMaxOnePasses * kMaxBins * 4, "histogram layout");
-static_assert(kOneCounterBytes >= (kMaxOnePasses + 1) * 4, "counters and the spare error word");
+static_assert(kOneCounterBytes >= (2 * kMaxOnePasses + 2) * 4,
+              "tile counters, the spare error word, the finished-block count, the trivial flags");
 
-// Digit counts of every pass in one read of the keys.
+// Digit counts of every pass in one read of the keys. The block that finishes
+// last also marks each pass whose keys all share one digit (trivial[p] = 1):
+// that pass leaves the order as it is.
 __global__ void __launch_bounds__(kSortThreads)
 radix_hist_kernel(const uint32_t* __restrict__ keys, long long cap, OnePlan pl,
-                  uint32_t* __restrict__ hist, const unsigned long long* __restrict__ n_dev) {
+                  uint32_t* __restrict__ hist, uint32_t* __restrict__ done,
+                  uint32_t* __restrict__ trivial, const unsigned long long* __restrict__ n_dev) {
     const long long n = dev_count(cap, n_dev);
     __shared__ uint32_t h[kHistCopies][kMaxOnePasses][kMaxBins];
     for (int i = threadIdx.x; i < kHistCopies * kMaxOnePasses * kMaxBins; i += kSortThreads)
@@ -295,6 +299,16 @@ radix_hist_kernel(const uint32_t* __restrict__ keys, long long cap, OnePlan pl,
             for (int q = 0; q < kHistCopies; ++q) c += h[q][p][d];
             if (c) atomicAdd(&hist[p * kMaxBins + d], c);
         }
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int p = 0; p < pl.passes; ++p)
+        for (int d = threadIdx.x; d < pl.bins[p]; d += kSortThreads)
+            if (*(volatile const uint32_t*)&hist[p * kMaxBins + d] == (uint32_t)n) trivial[p] = 1u;
 }
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
@@ -316,6 +330,7 @@ struct OneSmem {
     uint32_t cnt[kMaxBins + 1];
     uint32_t warp_tot[kSortWarps];
     int tile;
+    int trivial;
 };
 
 // Exclusive scan of c[0..bins) (two digits per thread) into out; every thread
@@ -353,7 +368,8 @@ __device__ __forceinline__ void block_digit_scan(const uint32_t* c_in, uint32_t*
 __global__ void __launch_bounds__(kSortThreads, 4)
 radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, long long n,
-               int shift, int bins, const uint32_t* __restrict__ hist, uint32_t* status,
+               int shift, int bins, const uint32_t* __restrict__ hist,
+               const uint32_t* __restrict__ trivial, uint32_t* status,
                uint32_t* tile_counter, uint32_t* err,
                const unsigned long long* __restrict__ n_dev) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -362,7 +378,10 @@ radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict_
     const uint32_t mask = (uint32_t)bins - 1u;
     const int bits_here = __ffs(bins) - 1;
     const unsigned lt_mask = (1u << lane) - 1u;
-    if (threadIdx.x == 0) S.tile = (int)atomicAdd(tile_counter, 1u);
+    if (threadIdx.x == 0) {
+        S.tile = (int)atomicAdd(tile_counter, 1u);
+        S.trivial = *trivial;
+    }
     for (int i = threadIdx.x; i < kSortWarps * (kMaxBins + 1); i += kSortThreads)
         (&S.whist[0][0])[i] = 0;
     __syncthreads();
@@ -376,6 +395,16 @@ radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict_
         n = nn;
     }
     const int valid = (int)((n - base) < kSortTile ? (n - base) : kSortTile);
+    // a pass whose digit is the same for every key keeps their order: each tile
+    // is copied through (the flag comes from the digit-count kernel, so every
+    // tile decides alike and none waits on another)
+    if (S.trivial) {
+        for (int i = threadIdx.x; i < valid; i += kSortThreads) {
+            keys_out[base + i] = keys_in[base + i];
+            vals_out[base + i] = vals_in ? vals_in[base + i] : (uint32_t)(base + i);
+        }
+        return;
+    }
     uint32_t k[kSortItems], rk[kSortItems];
 #pragma unroll
     for (int it = 0; it < kSortItems; ++it) {
@@ -491,6 +520,8 @@ static cudaError_t radix_sort_one(uint32_t* keys_a, uint32_t* vals_a, uint32_t* 
     uint32_t* counters = (uint32_t*)((char*)temp + kOneHistBytes);
     uint32_t* status = (uint32_t*)((char*)temp + kOneHistBytes + kOneCounterBytes);
     if (!err) err = counters + kMaxOnePasses;  // a scratch word when the caller keeps none
+    uint32_t* done = counters + kMaxOnePasses + 1;     // digit-count blocks finished
+    uint32_t* trivial = counters + kMaxOnePasses + 2;  // per pass: one digit for every key
     const long long tiles = (n + kSortTile - 1) / kSortTile;
     OnePlan pl{};
     pl.passes = plan.passes;
@@ -521,7 +552,8 @@ static cudaError_t radix_sort_one(uint32_t* keys_a, uint32_t* vals_a, uint32_t* 
     long long hg = div_up(n, (long long)kSortThreads * 8);
     if (hg > 4LL * num_sms) hg = 4LL * num_sms;
     note_launch();
-    radix_hist_kernel<<<(unsigned)hg, kSortThreads, 0, s>>>(keys_a, n, pl, hist, n_dev);
+    radix_hist_kernel<<<(unsigned)hg, kSortThreads, 0, s>>>(keys_a, n, pl, hist, done, trivial,
+                                                              n_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     uint32_t *ki = keys_a, *vi = vals_a, *ko = keys_b, *vo = vals_b;
@@ -530,7 +562,7 @@ static cudaError_t radix_sort_one(uint32_t* keys_a, uint32_t* vals_a, uint32_t* 
         const uint32_t* vread = (p == 0 && vals_iota) ? nullptr : vi;
         note_launch();
         radix_onesweep<<<(unsigned)tiles, kSortThreads, smem, s>>>(
-            ki, vread, ko, vo, n, pl.shift[p], pl.bins[p], hist + p * kMaxBins, st,
+            ki, vread, ko, vo, n, pl.shift[p], pl.bins[p], hist + p * kMaxBins, trivial + p, st,
             counters + p, err, n_dev);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -574,8 +606,8 @@ cudaError_t launch_sort_timeout_check(void* scratch, uint32_t* err, cudaStream_t
     }
     note_launch();
     radix_onesweep<<<1, kSortThreads, sizeof(OneSmem), s>>>(
-        keys, nullptr, keys_out, vals_out, 2LL * kSortTile, 0, 128, hist, status, counter, err,
-        nullptr);
+        keys, nullptr, keys_out, vals_out, 2LL * kSortTile, 0, 128, hist, hist, status, counter,
+        err, nullptr);
     return cudaGetLastError();
 }
 
