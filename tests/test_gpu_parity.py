@@ -236,6 +236,23 @@ def test_backward_small_scene(oracle_mod, ppt, tile):
     r.close()
 
 
+@pytest.mark.parametrize("deg", [0, 1, 2])
+def test_sh_degrees_pixels_and_gradients(oracle_mod, deg):
+    """SH degrees 0-2: 3K coefficients per Gaussian of 3, 12 and 27 floats, so the
+    projection and its backward read them as float4 rows (12) and as scalars
+    (3, 27, not multiples of 4). Pixels and the gradients of every attribute
+    against the FP64 oracle."""
+    from paper_2409_07759_b300 import api
+    r = api.Renderer()
+    sc, view = synth.tiny_scene(3 + deg, n=200, sh_degree=deg, width=96, height=72, depth=3.0,
+                                log_scale_mean=-2.2, spread=0.9)
+    view.fx = view.fy = 90.0
+    _render_and_compare(r, oracle_mod, sc, [view], bg=(0.1, 0.2, 0.3))
+    d = np.random.default_rng(40 + deg).normal(size=(3, 72, 96))
+    print(_grads_vs_oracle(r, oracle_mod, sc, [view], [d], bg=(0.1, 0.2, 0.3)))
+    r.close()
+
+
 def test_backward_config1_l1(R, oracle_mod):
     """Config 1 full size: L1 loss against the seeded target, gradients of all
     attributes of the 100k Gaussians."""
