@@ -482,12 +482,9 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
     }
 }
 
-// Sum 9 per-lane values over the warp and add the sums to acc[0..9) in
-// shared memory. Steps 1-3 halve the values each lane holds while doubling
-// the lanes summed, so lane 4m ends with value m (m < 8); value 8 takes a
-// plain butterfly.
-// Steps 1-3 of the transposing butterfly on v[0..8): lane l ends with value
-// l >> 2 summed over the 8 lanes that differ from it in bits 2-4.
+// Steps 1-3 of a transposing butterfly on v[0..8): each step halves the
+// values a lane holds while doubling the lanes summed, so lane l ends with
+// value l >> 2 summed over the 8 lanes that differ from it in bits 2-4.
 __device__ __forceinline__ float warp_sum8_part(const float* v) {
     const unsigned F = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -509,9 +506,9 @@ __device__ __forceinline__ float warp_sum8_part(const float* v) {
     return (bC ? x[1] : x[0]) + __shfl_xor_sync(F, bC ? x[0] : x[1], 4);
 }
 
-// SOLO: the block is this one warp, so nothing else adds to acc and plain
-// read-modify-writes replace the shared-memory atomics.
-template <bool SOLO>
+// Sum 9 per-lane values over the warp (value 8 by a plain butterfly) and add
+// the sums to acc[0..9) in shared memory, which the block's other warps also
+// add to.
 __device__ __forceinline__ void warp_sum9_to_smem(const float* v, float* acc) {
     const unsigned F = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -521,34 +518,93 @@ __device__ __forceinline__ void warp_sum9_to_smem(const float* v, float* acc) {
     float v8 = v[8];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v8 += __shfl_xor_sync(F, v8, o);
-    if constexpr (SOLO) {
-        if ((lane & 3) == 0) acc[lane >> 2] += y;
-        if (lane == 0) acc[8] += v8;
-    } else {
-        if ((lane & 3) == 0 && y != 0.f) atomicAdd(&acc[lane >> 2], y);
-        if (lane == 0 && v8 != 0.f) atomicAdd(&acc[8], v8);
-    }
+    if ((lane & 3) == 0 && y != 0.f) atomicAdd(&acc[lane >> 2], y);
+    if (lane == 0 && v8 != 0.f) atomicAdd(&acc[8], v8);
 }
 
-// The rest of two Gaussians' reductions at once, for a block of one warp:
-// yA, yB from warp_sum8_part, v8A, v8B their ninth values. The last two
-// butterfly steps and the ninth value's sum are transposed across the pair,
-// so one shuffle serves both Gaussians: lanes 4i and 4i + 2 end with value i
-// of A and of B, lanes 0 and 16 with the ninth. accB null: there is no B.
-__device__ __forceinline__ void warp_finish2_solo(float yA, float yB, float v8A, float v8B,
-                                                  float* accA, float* accB) {
+// Staged Gaussians whose per-lane sums one shared-memory round reduces in a
+// block of one warp.
+constexpr int kRoundG = 4;
+
+// The reduction of kRoundG staged Gaussians in a block of one warp. Lane l
+// has written, for slot g, its column sums ma[g][l] = (S0, SY, SYY, M6) and
+// mb[g][l] = (M7, M8): S0 = sum gm, SY = sum gm dy, SYY = sum gm dy^2 over its
+// pixels and M_c = sum (-w) dL_c. Lane L sums slot L / 8 over source lanes
+// L % 8 + 8i (i < 4); a source's column in the tile is its lane mod TW, so
+// the sources fall in min(4, TW / 8) columns. Against the tile's centre column
+// (x offset xl = column + 1/2 - TW/2) it forms
+//   P0 = sum S0, P1 = sum S0 xl, P2 = sum S0 xl^2, Q0 = sum SY,
+//   Q1 = sum SY xl, R = sum SYY and the three colour sums,
+// then sums them over its group of 8 lanes (a transposing butterfly: lane L
+// ends with value L % 8, every lane with the ninth) and stores them to
+// acc[9 j ..] for the slot's Gaussian j = j_top - g (slots with j < 0 are
+// not staged and are dropped). With dx = xl + c, c = tile centre - u, the
+// x moments follow at the flush: sum gm dx = P1 + c P0,
+// sum gm dx^2 = P2 + 2c P1 + c^2 P0, sum gm dx dy = Q1 + c Q0.
+template <int TW>
+__device__ __forceinline__ void round_reduce(const float4 (*ma)[32], const float2 (*mb)[32],
+                                             float* acc, int j_top) {
+    constexpr int NCOL = TW / 8 < 4 ? TW / 8 : 4;
+    static_assert(NCOL >= 1 && 4 % NCOL == 0, "8, 16 or 32 columns");
     const unsigned F = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const bool b1 = lane & 2, b4 = lane & 16;
-    float y = (b1 ? yB : yA) + __shfl_xor_sync(F, b1 ? yA : yB, 2);
-    y += __shfl_xor_sync(F, y, 1);
-    float w = (b4 ? v8B : v8A) + __shfl_xor_sync(F, b4 ? v8A : v8B, 16);
+    const int g = lane >> 3, part = lane & 7;
+    float4 ca[NCOL];
+    float2 cb[NCOL];
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) w += __shfl_xor_sync(F, w, o);
-    float* acc = b1 ? accB : accA;
-    if ((lane & 1) == 0 && acc) acc[lane >> 2] += y;
-    float* acc8 = b4 ? accB : accA;
-    if ((lane & 15) == 0 && acc8) acc8[8] += w;
+    for (int i = 0; i < 4; ++i) {
+        const float4 sa = ma[g][part + 8 * i];
+        const float2 sb = mb[g][part + 8 * i];
+        const int c = i % NCOL;
+        if (i < NCOL) {
+            ca[c] = sa;
+            cb[c] = sb;
+        } else {
+            const float2 lo = __fadd2_rn(lo2(ca[c]), lo2(sa));
+            const float2 hi = __fadd2_rn(hi2(ca[c]), hi2(sa));
+            ca[c] = make_float4(lo.x, lo.y, hi.x, hi.y);
+            cb[c] = __fadd2_rn(cb[c], sb);
+        }
+    }
+    float2 p0q0 = make_float2(0.f, 0.f), p1q1 = p0q0, rm6 = p0q0, m78 = p0q0;
+    float p2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) {
+        const float xl = (float)(part + 8 * c) + (0.5f - 0.5f * TW);
+        const float2 sq = lo2(ca[c]);                       // (S0, SY)
+        const float2 t = __fmul2_rn(sq, make_float2(xl, xl));
+        p0q0 = __fadd2_rn(p0q0, sq);
+        p1q1 = __fadd2_rn(p1q1, t);
+        p2 = fmaf(t.x, xl, p2);
+        rm6 = __fadd2_rn(rm6, hi2(ca[c]));                  // (SYY, M6)
+        m78 = __fadd2_rn(m78, cb[c]);
+    }
+    const float v[8] = {p0q0.x, p1q1.x, p2, p0q0.y, p1q1.y, rm6.x, rm6.y, m78.x};
+    const bool b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
+    float w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float send = b2 ? v[k] : v[k + 4];
+        const float keep = b2 ? v[k + 4] : v[k];
+        w[k] = keep + __shfl_xor_sync(F, send, 4);
+    }
+    float x[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const float send = b1 ? w[k] : w[k + 2];
+        const float keep = b1 ? w[k + 2] : w[k];
+        x[k] = keep + __shfl_xor_sync(F, send, 2);
+    }
+    const float y = (b0 ? x[1] : x[0]) + __shfl_xor_sync(F, b0 ? x[0] : x[1], 1);
+    float v8 = m78.y;
+    v8 += __shfl_xor_sync(F, v8, 4);
+    v8 += __shfl_xor_sync(F, v8, 2);
+    v8 += __shfl_xor_sync(F, v8, 1);
+    const int j = j_top - g;
+    if (j >= 0) {
+        acc[9 * j + part] = y;
+        if (part == 0) acc[9 * j + 8] = v8;
+    }
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -641,6 +697,12 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
     __shared__ uint32_t s_rec[BATCH];
     __shared__ float s_acc[BATCH * 9];
     __shared__ int s_item, s_maxlast;
+    // a block of one warp reduces its per-lane sums through shared memory,
+    // kRoundG Gaussians a round (round_reduce); larger blocks by shuffles
+    constexpr bool kRound = NT == 32;
+    static_assert(BATCH % kRoundG == 0, "rounds within a batch");
+    __shared__ float4 s_ma[kRound ? kRoundG : 1][32];
+    __shared__ float2 s_mb[kRound ? kRoundG : 1][32];
     const unsigned F = 0xffffffffu;
     const int tid = threadIdx.x;
     const int lx = tid % TW, ly = (tid / TW) * PPT;
@@ -709,22 +771,47 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                 stage_gaussian_x2<true>(a.rec, r, &sa[k], &sb[k], &sc[k], &sd[k], &se[k]);
             }
             block_sync<NT>();
+            if constexpr (kRound) {
+            // kRoundG staged Gaussians per round, back to front: each lane
+            // leaves its column sums in s_ma/s_mb (the thread's pixels share
+            // x, so only sum gm, sum gm dy and sum gm dy^2 run per pixel; gm
+            // is alpha dL/dalpha, its factor -1/2 applied at the flush), then
+            // the warp reduces the round
+            for (int j4 = cnt - 1; j4 >= 0; j4 -= kRoundG) {
+#pragma unroll
+                for (int jj = 0; jj < kRoundG; ++jj) {
+                const int j = j4 - jj;
+                if (j < 0) break;
+                const int pos = b0 + j - rg.x;
+                const float4 ga = sa[j], gb = sb[j], gc = sc[j], gd = sd[j], ge = se[j];
+                const float2 dx = __fadd2_rn(px2, lo2(ga));
+                const float2 bdx = __fmul2_rn(hi2(gb), dx);
+                const float2 k = __ffma2_rn(__fmul2_rn(lo2(gb), dx), dx, hi2(gc));
+                float2 S0 = make_float2(0.f, 0.f), SY = S0, SYY = S0, M6 = S0, M7 = S0, M8 = S0;
+                if (__float_as_uint(ge.w) & 1u)
+                    bwd_pairs<true, false, NP>(ga, gb, gc, gd, ge, bdx, k, pos, py, last, T, D,
+                                               dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
+                else if (pos < wfirst)
+                    bwd_pairs<false, true, NP>(ga, gb, gc, gd, ge, bdx, k, pos, py, last, T, D,
+                                               dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
+                else
+                    bwd_pairs<false, false, NP>(ga, gb, gc, gd, ge, bdx, k, pos, py, last, T, D,
+                                                dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
+                s_ma[jj][tid] = make_float4(S0.x + S0.y, SY.x + SY.y, SYY.x + SYY.y, M6.x + M6.y);
+                s_mb[jj][tid] = make_float2(M7.x + M7.y, M8.x + M8.y);
+                }
+                __syncwarp();
+                round_reduce<TW>(s_ma, s_mb, s_acc, j4);
+                __syncwarp();
+            }
+            } else {
             // kBwdUnroll staged Gaussians per iteration, back to front; the
             // group is skipped when it lies beyond every pixel of the warp's last
-            // (never, in a block of one warp: the walk starts at its largest last)
             for (int j2 = cnt - 1; j2 >= 0; j2 -= kBwdUnroll) {
-                if (NT > 32 &&
-                    __all_sync(F, b0 + max(j2 - kBwdUnroll + 1, 0) - rg.x >= mylast))
-                    continue;
-                // one warp a block: the group's two Gaussians finish their warp
-                // reductions together
-                constexpr bool kPair = NT == 32 && kBwdUnroll == 2;
-                float yp[kBwdUnroll], v8p[kBwdUnroll];
+                if (__all_sync(F, b0 + max(j2 - kBwdUnroll + 1, 0) - rg.x >= mylast)) continue;
 #pragma unroll
                 for (int jj = 0; jj < kBwdUnroll; ++jj) {
                 const int j = j2 - jj;
-                yp[jj] = 0.f;
-                v8p[jj] = 0.f;
                 if (j < 0) break;
                 const int pos = b0 + j - rg.x;
                 const float4 ga = sa[j], gb = sb[j], gc = sc[j], gd = sd[j], ge = se[j];
@@ -758,16 +845,9 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                 m[1] = m[0] * dx.x;
                 m[3] = m[1] * dx.x;
                 m[4] = m[2] * dx.x;
-                if constexpr (kPair) {
-                    yp[jj] = warp_sum8_part(m);
-                    v8p[jj] = m[8];
-                } else {
-                    warp_sum9_to_smem<NT == 32>(m, &s_acc[j * 9]);
+                warp_sum9_to_smem(m, &s_acc[j * 9]);
                 }
-                }
-                if constexpr (kPair)
-                    warp_finish2_solo(yp[0], yp[1], v8p[0], v8p[1], &s_acc[j2 * 9],
-                                      j2 >= 1 ? &s_acc[(j2 - 1) * 9] : nullptr);
+            }
             }
             block_sync<NT>();
             for (int k = tid; k < cnt; k += NT) {
@@ -779,6 +859,23 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                 const uint32_t r = s_rec[k];
                 const float4 ra = a.rec.a[r];   // u, v, opacity, depth
                 const float4 rb = a.rec.b[r];   // A, B, C
+                float* dst = a.grad2d + 12ll * r;
+                if constexpr (kRound) {
+                    // round_reduce's sums about the tile's centre column:
+                    // (P0, P1, P2, Q0, Q1, R, M6, M7, M8), dx = xl + c
+                    const float c = (float)(x - lx + TW / 2) - ra.x;
+                    const float sx = fmaf(c, acc[0], acc[1]);
+                    const float sxx = fmaf(c, fmaf(c, acc[0], 2.f * acc[1]), acc[2]);
+                    const float sxy = fmaf(c, acc[3], acc[4]);
+                    const float m1 = -0.5f * sx, m2 = -0.5f * acc[3];
+                    const float du = -2.f * (rb.x * m1 + rb.y * m2);
+                    const float dv = -2.f * (rb.y * m1 + rb.z * m2);
+                    const float dop = acc[0] / ra.z;
+                    red_add_v4(dst, du, dv, -0.5f * sxx, -sxy);
+                    red_add_v4(dst + 4, -0.5f * acc[5], dop, -acc[6], -acc[7]);
+                    red_add(dst + 8, -acc[8]);
+                    continue;
+                }
                 // acc[0..5] hold sums of alpha dL/dalpha times (1, dx, dy, dx^2,
                 // dx dy, dy^2); dL/dm = -1/2 of them (G = exp(-m/2)).
                 // m = A dx^2 + 2B dx dy + C dy^2, dx = px - u: dm/du = -2(A dx + B dy)
@@ -787,7 +884,6 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
                 const float dv = -2.f * (rb.y * m1 + rb.z * m2);
                 // alpha = o G, dalpha/do = G = alpha/o
                 const float dop = acc[0] / ra.z;
-                float* dst = a.grad2d + 12ll * r;
                 red_add_v4(dst, du, dv, -0.5f * acc[3], -acc[4]);
                 red_add_v4(dst + 4, -0.5f * acc[5], dop, acc[6], acc[7]);
                 red_add(dst + 8, acc[8]);
@@ -912,7 +1008,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_bwd_kernel(BlendArgs a) {
                     m[6] = m6;
                     m[7] = m7;
                     m[8] = m8;
-                    warp_sum9_to_smem<NT == 32>(m, &s_acc[j * 9]);
+                    warp_sum9_to_smem(m, &s_acc[j * 9]);
                 }
                 }
             }
