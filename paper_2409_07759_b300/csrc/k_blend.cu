@@ -529,32 +529,36 @@ constexpr int kRoundG = 4;
 // The reduction of kRoundG staged Gaussians in a block of one warp. Lane l
 // has written, for slot g, its column sums ma[g][l] = (S0, SY, SYY, M6) and
 // mb[g][l] = (M7, M8): S0 = sum gm, SY = sum gm dy, SYY = sum gm dy^2 over its
-// pixels and M_c = sum (-w) dL_c. Lane L sums slot L / 8 over source lanes
-// L % 8 + 8i (i < 4); a source's column in the tile is its lane mod TW, so
-// the sources fall in min(4, TW / 8) columns. Against the tile's centre column
-// (x offset xl = column + 1/2 - TW/2) it forms
+// pixels and M_c = sum (-w) dL_c. The slot's LPG = 32 / kRoundG lanes sum it:
+// lane L takes slot L / LPG over source lanes L % LPG + LPG i (i < kRoundG).
+// A source's column in the tile is its lane mod TW, so a lane's sources fall
+// in min(kRoundG, TW / LPG) columns. Against the tile's centre column (x
+// offset xl = column + 1/2 - TW/2) it forms
 //   P0 = sum S0, P1 = sum S0 xl, P2 = sum S0 xl^2, Q0 = sum SY,
 //   Q1 = sum SY xl, R = sum SYY and the three colour sums,
-// then sums them over its group of 8 lanes (a transposing butterfly: lane L
-// ends with value L % 8, every lane with the ninth) and stores them to
-// acc[9 j ..] for the slot's Gaussian j = j_top - g (slots with j < 0 are
-// not staged and are dropped). With dx = xl + c, c = tile centre - u, the
-// x moments follow at the flush: sum gm dx = P1 + c P0,
-// sum gm dx^2 = P2 + 2c P1 + c^2 P0, sum gm dx dy = Q1 + c Q0.
+// then sums them over the slot's lanes (a transposing butterfly on the first
+// eight: lane L ends with values n (L % LPG) + k, k < n = 8 / LPG; every lane
+// with the ninth) and stores them to acc[9 j ..] for the slot's Gaussian
+// j = j_top - g (slots with j < 0 were not staged and are dropped). With
+// dx = xl + c, c = tile centre - u, the x moments follow at the flush:
+// sum gm dx = P1 + c P0, sum gm dx^2 = P2 + 2c P1 + c^2 P0,
+// sum gm dx dy = Q1 + c Q0.
 template <int TW>
 __device__ __forceinline__ void round_reduce(const float4 (*ma)[32], const float2 (*mb)[32],
                                              float* acc, int j_top) {
-    constexpr int NCOL = TW / 8 < 4 ? TW / 8 : 4;
-    static_assert(NCOL >= 1 && 4 % NCOL == 0, "8, 16 or 32 columns");
+    constexpr int LPG = 32 / kRoundG;
+    constexpr int NCOL = kRoundG < TW / LPG ? kRoundG : TW / LPG;
+    static_assert(LPG >= 2 && LPG <= 8 && NCOL >= 1 && kRoundG % NCOL == 0,
+                  "2 to 16 Gaussians a round, whole columns");
     const unsigned F = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int g = lane >> 3, part = lane & 7;
+    const int g = lane / LPG, part = lane % LPG;
     float4 ca[NCOL];
     float2 cb[NCOL];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 sa = ma[g][part + 8 * i];
-        const float2 sb = mb[g][part + 8 * i];
+    for (int i = 0; i < kRoundG; ++i) {
+        const float4 sa = ma[g][part + LPG * i];
+        const float2 sb = mb[g][part + LPG * i];
         const int c = i % NCOL;
         if (i < NCOL) {
             ca[c] = sa;
@@ -570,7 +574,7 @@ __device__ __forceinline__ void round_reduce(const float4 (*ma)[32], const float
     float p2 = 0.f;
 #pragma unroll
     for (int c = 0; c < NCOL; ++c) {
-        const float xl = (float)(part + 8 * c) + (0.5f - 0.5f * TW);
+        const float xl = (float)(part + LPG * c) + (0.5f - 0.5f * TW);
         const float2 sq = lo2(ca[c]);                       // (S0, SY)
         const float2 t = __fmul2_rn(sq, make_float2(xl, xl));
         p0q0 = __fadd2_rn(p0q0, sq);
@@ -579,30 +583,25 @@ __device__ __forceinline__ void round_reduce(const float4 (*ma)[32], const float
         rm6 = __fadd2_rn(rm6, hi2(ca[c]));                  // (SYY, M6)
         m78 = __fadd2_rn(m78, cb[c]);
     }
-    const float v[8] = {p0q0.x, p1q1.x, p2, p0q0.y, p1q1.y, rm6.x, rm6.y, m78.x};
-    const bool b2 = lane & 4, b1 = lane & 2, b0 = lane & 1;
-    float w[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const float send = b2 ? v[k] : v[k + 4];
-        const float keep = b2 ? v[k + 4] : v[k];
-        w[k] = keep + __shfl_xor_sync(F, send, 4);
-    }
-    float x[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const float send = b1 ? w[k] : w[k + 2];
-        const float keep = b1 ? w[k + 2] : w[k];
-        x[k] = keep + __shfl_xor_sync(F, send, 2);
-    }
-    const float y = (b0 ? x[1] : x[0]) + __shfl_xor_sync(F, b0 ? x[0] : x[1], 1);
+    float v[8] = {p0q0.x, p1q1.x, p2, p0q0.y, p1q1.y, rm6.x, rm6.y, m78.x};
     float v8 = m78.y;
-    v8 += __shfl_xor_sync(F, v8, 4);
-    v8 += __shfl_xor_sync(F, v8, 2);
-    v8 += __shfl_xor_sync(F, v8, 1);
+    int n = 8;
+#pragma unroll
+    for (int o = LPG / 2; o >= 1; o >>= 1) {
+        const bool b = lane & o;
+        n >>= 1;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            const float send = b ? v[k] : v[k + n];
+            const float keep = b ? v[k + n] : v[k];
+            v[k] = keep + __shfl_xor_sync(F, send, o);
+        }
+        v8 += __shfl_xor_sync(F, v8, o);
+    }
     const int j = j_top - g;
     if (j >= 0) {
-        acc[9 * j + part] = y;
+#pragma unroll
+        for (int k = 0; k < 8 / LPG; ++k) acc[9 * j + (8 / LPG) * part + k] = v[k];
         if (part == 0) acc[9 * j + 8] = v8;
     }
 }
