@@ -101,7 +101,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=64, help="Gaussians staged per block step")
     ap.add_argument("--ppt", type=int, default=4, help="forward blend pixels per thread")
     ap.add_argument("--bwd-ppt", type=int, default=8, help="reverse blend pixels per thread")
-    ap.add_argument("--bwd-batch", type=int, default=64, help="reverse blend staging batch")
+    ap.add_argument("--bwd-batch", type=int, default=32, help="reverse blend staging batch")
     ap.add_argument("--targets", default="u8", choices=["u8", "f32"],
                     help="target frames: 8-bit (k/255) or float32")
     ap.add_argument("--serve-seconds", type=float, default=4.0)

@@ -220,7 +220,7 @@ class Renderer:
 
     def __init__(self, tile=(16, 16), batch=64, near_plane=0.2, blocks_per_sm=0,
                  count_pairs=False, pixels_per_thread=None, bwd_pixels_per_thread=None,
-                 bwd_batch=64, use_torch_allocator=True, alloc_guard=None,
+                 bwd_batch=32, use_torch_allocator=True, alloc_guard=None,
                  sort_single_pass=True, deferred_sizing=False):
         if pixels_per_thread is None:      # 8x8 tiles hold at most 2 pixels per thread
             pixels_per_thread = 2 if tuple(tile) == (8, 8) else 4

@@ -57,10 +57,10 @@ def candidates(mode: str):
                 if mode == "fwd":
                     yield dict(tile=tile, batch=batch, pixels_per_thread=ppt,
                                bwd_pixels_per_thread=min(ppt, 2) if tile == (8, 8) else 8,
-                               bwd_batch=64)
+                               bwd_batch=32)
                 else:
                     for bppt in BWD_PPT[tile]:
-                        for bbatch in (64, 128, 256):
+                        for bbatch in (32, 64, 128):
                             yield dict(tile=tile, batch=batch, pixels_per_thread=ppt,
                                        bwd_pixels_per_thread=bppt, bwd_batch=bbatch)
 

@@ -26,11 +26,14 @@
 // 14 shuffles for 9 values) and across the block in shared memory, and turns
 // them into the nine 2D gradients (centre, conic, opacity, colour) once per
 // Gaussian per tile before one vector atomic. At 8 pixels per thread a block
-// is one warp: the two Gaussians of an iteration share their butterflies' last
-// steps and the sums go to shared memory by plain adds. Besides the clamp
-// split, a Gaussian in front of every pixel's last contributor (below the
-// warp's smallest last) takes a body without the per-pixel last test.
+// is one warp: each lane leaves six column sums per Gaussian in shared memory
+// and the warp reduces four Gaussians at a time, 8 lanes per Gaussian, with
+// the x moments taken about the tile's centre column (round_reduce). Besides
+// the clamp split, Gaussians in front of every pixel's last contributor (below
+// the warp's smallest last) take a body without the per-pixel last test; in a
+// one-warp block both choices are made once per round of four.
 #include "swgs_internal.cuh"
+#include <type_traits>
 
 namespace swgs {
 
@@ -209,7 +212,7 @@ __global__ void __launch_bounds__(TW * TH / PPT) blend_fwd_kernel(BlendArgs a) {
 // bit; the reverse blend runs faster so) rather than the float 1 (tested by
 // a float compare; the forward runs faster so).
 template <bool INT_FLAG>
-__device__ __forceinline__ void stage_gaussian_x2(const Records& rec, uint32_t r, float4* sa,
+__device__ __forceinline__ bool stage_gaussian_x2(const Records& rec, uint32_t r, float4* sa,
                                                   float4* sb, float4* sc, float4* sd,
                                                   float4* se) {
     const float4 A = rec.a[r];
@@ -227,6 +230,7 @@ __device__ __forceinline__ void stage_gaussian_x2(const Records& rec, uint32_t r
     const bool clamp = A.z > kAlphaMax;
     *se = make_float4(-Cc.z, -Cc.z, pair_vmin(lo),
                       INT_FLAG ? __uint_as_float(clamp ? 1u : 0u) : (clamp ? 1.f : 0.f));
+    return clamp;
 }
 
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
@@ -628,10 +632,11 @@ __device__ __forceinline__ void block_sync() {
 // sums (the halves) and added before the warp reduction.
 // One staged Gaussian against the thread's pixel pairs (the reverse blend's
 // inner step): T recovery, the colour-behind update and the per-pixel sums.
-// CLAMP: the Gaussian's opacity exceeds 0.99, so alpha may take the clamp
-// (where dalpha/dm is then zero). ALL: the Gaussian lies in front of every
-// pixel's last contributor (pos below the warp's smallest last), so no pixel
-// needs the pos < last test.
+// CLAMP: alpha takes min(0.99, .) (where dalpha/dm is then zero) -- needed
+// only when the Gaussian's opacity exceeds 0.99, and bit-identical to the
+// body without it for every other Gaussian. ALL: the Gaussian lies in front of
+// every pixel's last contributor (pos below the warp's smallest last), so no
+// pixel needs the pos < last test.
 template <bool CLAMP, bool ALL, int NP>
 __device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float4 gd, float4 ge,
                                           float2 bdx, float2 k, int pos, const float2 (&py)[NP],
@@ -650,16 +655,13 @@ __device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float
         const bool ok1 = (ALL || pos < last[2 * i + 1]) && v.y >= ge.z;
         // -alpha of a counted pair, 0 otherwise; -alpha where dalpha/dm is
         // nonzero (the unclamped alpha), 0 otherwise
-        float2 na, nag;
+        float2 na;
         if (CLAMP) {
             na.x = ok0 ? fmaxf(-kAlphaMax, -u0) : 0.f;
             na.y = ok1 ? fmaxf(-kAlphaMax, -u1) : 0.f;
-            nag.x = u0 <= kAlphaMax ? na.x : 0.f;
-            nag.y = u1 <= kAlphaMax ? na.y : 0.f;
         } else {
             na.x = ok0 ? -u0 : 0.f;
             na.y = ok1 ? -u1 : 0.f;
-            nag = na;
         }
         // T before this Gaussian, recovered from the T after it (a pair that
         // does not count has alpha = 0 and leaves T as is)
@@ -674,9 +676,13 @@ __device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float
                                      __ffma2_rn(dL1[i], hi2(gd), __fmul2_rn(dL2[i], lo2(ge))));
         const float2 nd = __fadd2_rn(D[i], ne);
         D[i] = __ffma2_rn(na, nd, D[i]);
-        // gm = alpha T (E - D): (-w)(D - E), or with the clamp (-alpha where
-        // dalpha/dm is nonzero) T (D - E)
-        const float2 gm = CLAMP ? __fmul2_rn(nag, __fmul2_rn(T[i], nd)) : __fmul2_rn(nw, nd);
+        // gm = alpha T (E - D) = (-w)(D - E); zero where alpha takes the clamp
+        // (dalpha/dm = 0 there). Unclamped, both bodies round it alike.
+        float2 gm = __fmul2_rn(nw, nd);
+        if (CLAMP) {
+            gm.x = u0 <= kAlphaMax ? gm.x : 0.f;
+            gm.y = u1 <= kAlphaMax ? gm.y : 0.f;
+        }
         const float2 gy = __fmul2_rn(gm, dy);
         S0 = __fadd2_rn(S0, gm);
         SY = __fadd2_rn(SY, gy);
@@ -702,6 +708,8 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
     static_assert(BATCH % kRoundG == 0, "rounds within a batch");
     __shared__ float4 s_ma[kRound ? kRoundG : 1][32];
     __shared__ float2 s_mb[kRound ? kRoundG : 1][32];
+    // clamp bits of the staged Gaussians, read 64 at a time
+    __shared__ __align__(8) unsigned s_bcm[kRound ? (BATCH + 63) / 64 * 2 : 1];
     const unsigned F = 0xffffffffu;
     const int tid = threadIdx.x;
     const int lx = tid % TW, ly = (tid / TW) * PPT;
@@ -764,10 +772,25 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
             const int b0 = max(rg.x, b1 - BATCH);
             const int cnt = b1 - b0;
             block_sync<NT>();
-            for (int k = tid; k < cnt; k += NT) {
-                const uint32_t r = a.vals[b0 + k];
-                s_rec[k] = r;
-                stage_gaussian_x2<true>(a.rec, r, &sa[k], &sb[k], &sc[k], &sd[k], &se[k]);
+            if constexpr (kRound) {
+                for (int k0 = 0; k0 < cnt; k0 += 32) {
+                    const int k = k0 + tid;
+                    bool cl = false;
+                    if (k < cnt) {
+                        const uint32_t r = a.vals[b0 + k];
+                        s_rec[k] = r;
+                        cl = stage_gaussian_x2<true>(a.rec, r, &sa[k], &sb[k], &sc[k], &sd[k],
+                                                     &se[k]);
+                    }
+                    const unsigned m = __ballot_sync(F, cl);
+                    if (tid == 0) s_bcm[k0 >> 5] = m;
+                }
+            } else {
+                for (int k = tid; k < cnt; k += NT) {
+                    const uint32_t r = a.vals[b0 + k];
+                    s_rec[k] = r;
+                    stage_gaussian_x2<true>(a.rec, r, &sa[k], &sb[k], &sc[k], &sd[k], &se[k]);
+                }
             }
             block_sync<NT>();
             if constexpr (kRound) {
@@ -775,30 +798,44 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
             // leaves its column sums in s_ma/s_mb (the thread's pixels share
             // x, so only sum gm, sum gm dy and sum gm dy^2 run per pixel; gm
             // is alpha dL/dalpha, its factor -1/2 applied at the flush), then
-            // the warp reduces the round
-            for (int j4 = cnt - 1; j4 >= 0; j4 -= kRoundG) {
+            // the warp reduces the round. The body is chosen once a round: the
+            // clamp body if a Gaussian of the round has opacity > 0.99 (exact,
+            // and bit-identical for the others), else the one without the
+            // pos < last test if the round lies below the warp's smallest last.
+            const unsigned long long* cm64 = reinterpret_cast<const unsigned long long*>(s_bcm);
+            auto round = [&](int j4, auto clamp_tag, auto all_tag) {
+                constexpr bool kClamp = decltype(clamp_tag)::value;
+                constexpr bool kAll = decltype(all_tag)::value;
 #pragma unroll
                 for (int jj = 0; jj < kRoundG; ++jj) {
-                const int j = j4 - jj;
-                if (j < 0) break;
-                const int pos = b0 + j - rg.x;
-                const float4 ga = sa[j], gb = sb[j], gc = sc[j], gd = sd[j], ge = se[j];
-                const float2 dx = __fadd2_rn(px2, lo2(ga));
-                const float2 bdx = __fmul2_rn(hi2(gb), dx);
-                const float2 k = __ffma2_rn(__fmul2_rn(lo2(gb), dx), dx, hi2(gc));
-                float2 S0 = make_float2(0.f, 0.f), SY = S0, SYY = S0, M6 = S0, M7 = S0, M8 = S0;
-                if (__float_as_uint(ge.w) & 1u)
-                    bwd_pairs<true, false, NP>(ga, gb, gc, gd, ge, bdx, k, pos, py, last, T, D,
-                                               dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
-                else if (pos < wfirst)
-                    bwd_pairs<false, true, NP>(ga, gb, gc, gd, ge, bdx, k, pos, py, last, T, D,
-                                               dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
-                else
-                    bwd_pairs<false, false, NP>(ga, gb, gc, gd, ge, bdx, k, pos, py, last, T, D,
+                    const int j = j4 - jj;
+                    if (j < 0) break;
+                    const int pos = b0 + j - rg.x;
+                    const float4 ga = sa[j], gb = sb[j], gc = sc[j], gd = sd[j], ge = se[j];
+                    const float2 dx = __fadd2_rn(px2, lo2(ga));
+                    const float2 bdx = __fmul2_rn(hi2(gb), dx);
+                    const float2 k = __ffma2_rn(__fmul2_rn(lo2(gb), dx), dx, hi2(gc));
+                    float2 S0 = make_float2(0.f, 0.f), SY = S0, SYY = S0, M6 = S0, M7 = S0,
+                           M8 = S0;
+                    bwd_pairs<kClamp, kAll, NP>(ga, gb, gc, gd, ge, bdx, k, pos, py, last, T, D,
                                                 dL0, dL1, dL2, S0, SY, SYY, M6, M7, M8);
-                s_ma[jj][tid] = make_float4(S0.x + S0.y, SY.x + SY.y, SYY.x + SYY.y, M6.x + M6.y);
-                s_mb[jj][tid] = make_float2(M7.x + M7.y, M8.x + M8.y);
+                    s_ma[jj][tid] =
+                        make_float4(S0.x + S0.y, SY.x + SY.y, SYY.x + SYY.y, M6.x + M6.y);
+                    s_mb[jj][tid] = make_float2(M7.x + M7.y, M8.x + M8.y);
                 }
+            };
+            for (int j4 = cnt - 1; j4 >= 0; j4 -= kRoundG) {
+                const int jlo = max(j4 - (kRoundG - 1), 0);
+                unsigned long long cm = cm64[jlo >> 6] >> (jlo & 63);
+                if ((j4 >> 6) != (jlo >> 6)) cm |= cm64[j4 >> 6] << (64 - (jlo & 63));
+                using T1 = std::integral_constant<bool, true>;
+                using T0 = std::integral_constant<bool, false>;
+                if (cm & ((2ull << (j4 - jlo)) - 1ull))
+                    round(j4, T1{}, T0{});
+                else if (b0 + j4 - rg.x < wfirst)
+                    round(j4, T0{}, T1{});
+                else
+                    round(j4, T0{}, T0{});
                 __syncwarp();
                 round_reduce<TW>(s_ma, s_mb, s_acc, j4);
                 __syncwarp();

@@ -833,7 +833,7 @@ swgs_status swgs_default_config(swgs_config* cfg) {
     cfg->count_pairs = 0;
     cfg->pixels_per_thread = 4;
     cfg->bwd_pixels_per_thread = 8;
-    cfg->bwd_batch = 64;
+    cfg->bwd_batch = 32;
     cfg->sort_single_pass = 1;
     cfg->deferred_sizing = 0;
     return SWGS_OK;

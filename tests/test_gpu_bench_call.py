@@ -33,7 +33,7 @@ def bench_call():
     t8 = [torch.from_numpy(np.rint(t * 255.0).astype(np.uint8)).cuda() for t in targets]
     st = api.GaussianState.from_scene(sc)
     r = api.Renderer(tile=(16, 16), batch=64, pixels_per_thread=4, bwd_pixels_per_thread=8,
-                     bwd_batch=64)
+                     bwd_batch=32)
     imgs, dls, loss, saved = r.render_l1(st, views, t8)
     yield sc, views, st, r, imgs, saved
     saved.release()
