@@ -45,20 +45,20 @@ FLOP_PER_PAIR_BWD = 40
 # (reverse) pixels: forward offset 1.25, Mahalanobis form 5, T(1 - alpha) and
 # the T update 3, colour 7 = 16; reverse alpha recompute 5.6, T recovery 2,
 # colour weights 7, E and D - E 6, colour-behind 2, alpha dL/dalpha 1,
-# moments 5, the per-Gaussian sums before the warp reduction 2.6 = 31 (the
-# conic/centre/opacity chain rule runs once per Gaussian and tile).
+# moments 5, the per-Gaussian sums and their reduction over the tile 1.5 = 30
+# (the conic/centre/opacity chain rule runs once per Gaussian and tile).
 OWN_FLOP_PER_PAIR_FWD = 16
-OWN_FLOP_PER_PAIR_BWD = 31
+OWN_FLOP_PER_PAIR_BWD = 30
 
 # DRAM bytes (read + write) per launch from one ncu capture of the full-size
 # window step, keyed by stage and launch shape, with a digest of the sources
 # that define the kernel: a changed kernel reports no traffic until it is
 # captured again.
 TRAFFIC_CAPTURES = {
-    ("blend_bwd", "16x16/b64/ppt8"): {
-        "bytes": 1_232_564_736 + 17_480_192,
+    ("blend_bwd", "16x16/b32/ppt8"): {
+        "bytes": 1_232_882_176 + 16_189_696,
         "sources": ("csrc/k_blend.cu", "csrc/swgs_internal.cuh"),
-        "digest": "c39d6ccc9e49960f",
+        "digest": "cc5a5e178ffdeeb0",
     },
 }
 
