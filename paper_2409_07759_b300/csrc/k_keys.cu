@@ -187,9 +187,9 @@ __device__ __forceinline__ void spread_mask(unsigned m, unsigned out[4]) {
     }
 }
 
-// Per-tile lists of one super tile (one block per super tile, kExpandWarps
-// warps). The super tile's depth-ordered keys are taken in chunks of one key
-// per thread; warp w holds keys [32w, 32w + 32) of a chunk. For each chunk:
+// Per-tile lists of one super tile (one block per super tile, NW warps). The
+// super tile's depth-ordered keys are taken in chunks of one key per thread;
+// warp w holds keys [32w, 32w + 32) of a chunk. For each chunk:
 //  - every warp counts, per tile bit, its keys with the bit set (the spread
 //    mask summed over the warp: four warp reductions for 16 tiles);
 //  - the counting pass adds the counts up per tile and writes the tiles' list
@@ -199,18 +199,16 @@ __device__ __forceinline__ void spread_mask(unsigned m, unsigned out[4]) {
 //    with the bit set at offset + (rank among the warp's set lanes): every
 //    tile's list keeps the depth order. It then writes the tiles' ranges at
 //    their offsets from the scan of the lengths (never past cap).
-constexpr int kExpandWarps = 4;
-
-template <int SX, int SY, bool WRITE>
-__global__ void __launch_bounds__(kExpandWarps * 32)
+template <int SX, int SY, int NW, bool WRITE>
+__global__ void __launch_bounds__(NW * 32)
 expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict__ skeys,
                     const uint32_t* __restrict__ svals, const ViewDev* __restrict__ views,
                     int n_views, uint32_t* __restrict__ tcount, const uint32_t* __restrict__ toff,
                     uint32_t* __restrict__ vals, long long cap, int2* __restrict__ ranges,
                     const uint32_t* __restrict__ sort_err) {
     static_assert(SX * SY == 16, "16 tiles per super tile");
-    constexpr int NT = kExpandWarps * 32;
-    __shared__ __align__(16) uint32_t s_cnt[kExpandWarps][4];
+    constexpr int NT = NW * 32;
+    __shared__ __align__(16) uint32_t s_cnt[NW][4];
     const int sup = blockIdx.x;
     const ViewDev& V = views[find_view_by_super(views, n_views, sup)];
     const int ls = sup - V.super_base;
@@ -250,7 +248,7 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
         uint32_t before = 0, chunk = 0;
         if (lane < 16) {
             const int k = lane >> 2, sh = 8 * (lane & 3);
-            for (int w = 0; w < kExpandWarps; ++w) {
+            for (int w = 0; w < NW; ++w) {
                 const uint32_t c = (s_cnt[w][k] >> sh) & 0xffu;
                 before += w < warp ? c : 0;
                 chunk += c;
@@ -281,36 +279,66 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
     }
 }
 
+template <int NW, bool WRITE>
+static void expand_shape(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
+                         const ViewDev* views, int n_views, int total_supers, int tile_w,
+                         uint32_t* tcount, const uint32_t* toff, uint32_t* vals, long long cap,
+                         int2* ranges, const uint32_t* sort_err, cudaStream_t s) {
+    if (tile_w == 32)
+        expand_tiles_kernel<2, 8, NW, WRITE><<<total_supers, NW * 32, 0, s>>>(
+            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges, sort_err);
+    else
+        expand_tiles_kernel<4, 4, NW, WRITE><<<total_supers, NW * 32, 0, s>>>(
+            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges, sort_err);
+}
+
+// Warps per super tile: a block's time is its super tile's list, so a grid of
+// few super tiles (a batch of one or a few views) takes more warps per list,
+// and a grid of many (a training window) fewer, leaving no warp idle on the
+// short lists. Measured (ranges stage, ms): one 1280x720 view (240 super
+// tiles) 0.282 / 0.180 / 0.155 at 4 / 8 / 16 warps; three (720) 0.365 / 0.237
+// / 0.311; eight (1,920) 0.480 / 0.460 / 0.454; 40 views of 1352x1014
+// (14,080) 0.191 / 0.226 / 0.323.
+int expand_warps(int total_supers, int num_sms) {
+    if (total_supers < 2 * num_sms) return 16;
+    if (total_supers < 16 * num_sms) return 8;
+    return 4;
+}
+
 template <bool WRITE>
 static cudaError_t run_expand(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
                               const ViewDev* views, int n_views, int total_supers, int tile_w,
-                              uint32_t* tcount, const uint32_t* toff, uint32_t* vals,
+                              int num_sms, uint32_t* tcount, const uint32_t* toff, uint32_t* vals,
                               long long cap, int2* ranges, const uint32_t* sort_err,
                               cudaStream_t s) {
     if (total_supers <= 0) return cudaSuccess;
     note_launch();
-    if (tile_w == 32)
-        expand_tiles_kernel<2, 8, WRITE><<<total_supers, kExpandWarps * 32, 0, s>>>(
-            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges, sort_err);
+    const int nw = expand_warps(total_supers, num_sms);
+    if (nw == 16)
+        expand_shape<16, WRITE>(sranges, skeys, svals, views, n_views, total_supers, tile_w,
+                                tcount, toff, vals, cap, ranges, sort_err, s);
+    else if (nw == 8)
+        expand_shape<8, WRITE>(sranges, skeys, svals, views, n_views, total_supers, tile_w,
+                               tcount, toff, vals, cap, ranges, sort_err, s);
     else
-        expand_tiles_kernel<4, 4, WRITE><<<total_supers, kExpandWarps * 32, 0, s>>>(
-            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges, sort_err);
+        expand_shape<4, WRITE>(sranges, skeys, svals, views, n_views, total_supers, tile_w,
+                               tcount, toff, vals, cap, ranges, sort_err, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
-                                int n_views, int total_supers, int tile_w, uint32_t* tcount,
-                                const uint32_t* sort_err, cudaStream_t s) {
+                                int n_views, int total_supers, int tile_w, int num_sms,
+                                uint32_t* tcount, const uint32_t* sort_err, cudaStream_t s) {
     return run_expand<false>(sranges, skeys, nullptr, views, n_views, total_supers, tile_w,
-                             tcount, nullptr, nullptr, 0, nullptr, sort_err, s);
+                             num_sms, tcount, nullptr, nullptr, 0, nullptr, sort_err, s);
 }
 
 cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
                                 const ViewDev* views, int n_views, int total_supers, int tile_w,
-                                const uint32_t* toff, uint32_t* vals, long long cap, int2* ranges,
-                                const uint32_t* sort_err, cudaStream_t s) {
+                                int num_sms, const uint32_t* toff, uint32_t* vals, long long cap,
+                                int2* ranges, const uint32_t* sort_err, cudaStream_t s) {
     return run_expand<true>(sranges, skeys, svals, views, n_views, total_supers, tile_w,
-                            nullptr, toff, vals, cap, ranges, sort_err, s);
+                            num_sms, nullptr, toff, vals, cap, ranges, sort_err, s);
 }
 
 // sranges[t] = [first, last+1) of super tile t (the low 16 key bits) in the

@@ -621,12 +621,12 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             CK(launch_super_ranges(skeys, (long long)K, supers, P<int2>(ctx->sranges), s,
                                    n_sk_dev));
             CK(launch_expand_count(P<int2>(ctx->sranges), skeys, P<ViewDev>(B.views),
-                                   (int)B.h_views.size(), (int)supers, tw,
+                                   (int)B.h_views.size(), (int)supers, tw, ctx->num_sms,
                                    P<uint32_t>(ctx->tile_cnt), sort_err_word(ctx, s), s));
             CK(exclusive_scan_u32(P<uint32_t>(ctx->tile_cnt), P<uint32_t>(ctx->tile_off), tiles,
                                   ctx->scan_tmp.p, P<unsigned long long>(ctx->totals) + 2, s));
             CK(launch_expand_write(P<int2>(ctx->sranges), skeys, svals, P<ViewDev>(B.views),
-                                   (int)B.h_views.size(), (int)supers, tw,
+                                   (int)B.h_views.size(), (int)supers, tw, ctx->num_sms,
                                    P<uint32_t>(ctx->tile_off), P<uint32_t>(B.vals), n_keys,
                                    P<int2>(B.ranges), sort_err_word(ctx, s), s));
         }
