@@ -784,24 +784,25 @@ def main():
         extra["batched_over_plain"] = (ms / args.steps) and (pms / (ms / args.steps))
 
     # ---- end to end through the public API with host buffers ----
-    # Every step's targets are copied from pinned host memory (on a side stream,
-    # overlapping the previous step's compute), its slice is streamed in from
-    # pinned host memory, and its loss is copied back to pinned host memory and
-    # read by the host once the next step has been issued (so the device does
-    # not wait for the host between steps).
+    # Every step's targets and slice are copied from pinned host memory (on a
+    # side stream, issued once the step before has been issued, so the copies
+    # overlap its blends; the slice lands in a device staging buffer that the
+    # step writes into the slot buffer), and its loss is copied back to pinned
+    # host memory and read by the host once the next step has been issued (so
+    # the device does not wait for the host between steps).
     h2d = sum(t.numel() * t.element_size() for t in tgt_host) + slice_bytes
     loss_host = [torch.zeros(1, dtype=torch.float32).pin_memory() for _ in range(2)]
     loss_ev = [torch.cuda.Event(), torch.cuda.Event()]
     losses = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tr.prefetch_targets(tgt_host)
+    tr.prefetch_targets(tgt_host, upd_host(0))
     for k in range(args.steps):
-        loss = tr.step(20_000 + k, update=upd_host(k), prefetched=True)
+        loss = tr.step(20_000 + k, prefetched=True)
         loss_host[k % 2].copy_(loss, non_blocking=True)
         loss_ev[k % 2].record()
         if k + 1 < args.steps:
-            tr.prefetch_targets(tgt_host)
+            tr.prefetch_targets(tgt_host, upd_host(k + 1))
         if k > 0:  # the previous step's loss, on the host
             loss_ev[(k - 1) % 2].synchronize()
             losses.append(float(loss_host[(k - 1) % 2].item()))

@@ -36,6 +36,11 @@ def _flat_views(n: int, K: int, device="cuda"):
     return flat, [p.view(s) for p, s in zip(parts, shapes)]
 
 
+# the arrays of a streamed slice (GaussianState.pin_host's keys), in the
+# GaussianState constructor's order
+_SLICE_FIELDS = api.PARAM_NAMES + ("start", "expire", "birth", "frozen")
+
+
 class WindowTrainer:
     """Holds the state, gradients, Adam moments and per-view buffers of one
     window and runs training steps on it."""
@@ -81,6 +86,8 @@ class WindowTrainer:
         self._copy_stream = None
         self._copied = None      # event: the back buffer is filled
         self._released = None    # per buffer: the last step reading it has ended
+        self._stage_bufs = [None, None]  # per buffer: device staging slice
+        self._staged = [None, None]      # per buffer: (first slot, staged slice)
         self.dl = [torch.empty((3, vw.height, vw.width), dtype=torch.float32, device="cuda")
                    for vw in self.views]
         self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
@@ -107,10 +114,13 @@ class WindowTrainer:
         self.targets = list(targets)
         self.frames = sorted({int(v.frame) for v in views})
 
-    def prefetch_targets(self, host_targets: Sequence[torch.Tensor]):
+    def prefetch_targets(self, host_targets: Sequence[torch.Tensor], host_update=None):
         """Start copying the next step's targets from pinned host memory into a
         back buffer on a side stream, so that the copy overlaps the step in
-        flight; the next step(..., prefetched=True) waits for it and uses it."""
+        flight; the next step(..., prefetched=True) waits for it and uses it.
+        host_update = (first_slot, pinned host dict): that step's slice is
+        copied alongside into a device staging slice, which the step then
+        writes into the slot buffer on the device."""
         if self._bufs is None:
             self._bufs = [self.targets, [torch.empty_like(t) for t in self.targets]]
             self._front = 0
@@ -124,6 +134,19 @@ class WindowTrainer:
             self._copy_stream.wait_event(self._released[back])
             for d, h in zip(self._bufs[back], host_targets):
                 d.copy_(h, non_blocking=True)
+            self._staged[back] = None
+            if host_update is not None:
+                first, host = host_update
+                n = int(host["means"].shape[0])
+                st = self._stage_bufs[back]
+                if st is None or st.n != n:
+                    st = api.GaussianState(*[torch.empty_like(host[k], device="cuda")
+                                             for k in _SLICE_FIELDS],
+                                           sh_degree=self.state.sh_degree)
+                    self._stage_bufs[back] = st
+                for k in _SLICE_FIELDS:
+                    getattr(st, k).copy_(host[k], non_blocking=True)
+                self._staged[back] = (int(first), st)
             self._copied.record(self._copy_stream)
 
     def settle(self):
@@ -155,13 +178,15 @@ class WindowTrainer:
         """One training step. update = (first_slot, src) overwrites a slice
         before rendering: src a pinned host dict (GaussianState.pin_host, the
         form a streamed slice arrives in) or a GaussianState on the device;
-        prefetched = True takes the targets from the last prefetch_targets call.
-        Returns the (device) loss tensor."""
+        prefetched = True takes the targets (and the slice, if one was staged)
+        from the last prefetch_targets call. Returns the (device) loss tensor."""
         self.settle()
         if prefetched:
             torch.cuda.current_stream().wait_event(self._copied)
             self._front = 1 - self._front
             self.targets = self._bufs[self._front]
+            if self._staged[self._front] is not None:
+                update = self._staged[self._front]
         if update is not None:
             first, src = update
             self.r.frame_update(self.state, first, src,

@@ -94,6 +94,38 @@ def test_prefetched_host_targets_match_device_targets():
     r.close()
 
 
+def test_prefetched_staged_slices_match_host_updates():
+    """Each step's targets and slice prefetched from pinned host memory (the
+    slice staged on the device and written into the slot buffer by the step)
+    give the same steps, bit for bit (Adam off), as explicit per-step updates
+    from pinned host memory with the targets on the device."""
+    from paper_2409_07759_b300 import api
+    from paper_2409_07759_b300.window import WindowTrainer
+    sc, views, targets = _window()
+    r = api.Renderer()
+    host = [torch.from_numpy(t).pin_memory() for t in targets]
+    dev = [h.cuda() for h in host]
+    donor = api.GaussianState.from_scene(sc)
+    n = 500
+    slices = [(k * n, donor.rows((k + 3) * n, (k + 4) * n).pin_host()) for k in range(4)]
+    st_a = api.GaussianState.from_scene(sc)
+    st_b = api.GaussianState.from_scene(sc)
+    params = dict(adam=0)
+    tr_a = WindowTrainer(r, st_a, views, [torch.empty_like(d) for d in dev], seed=5,
+                         params=params)
+    tr_b = WindowTrainer(r, st_b, views, dev, seed=5, params=params)
+    tr_a.prefetch_targets(host, slices[0])
+    for k in range(len(slices)):
+        la = tr_a.step(k, prefetched=True)
+        if k + 1 < len(slices):
+            tr_a.prefetch_targets(host, slices[k + 1])
+        lb = tr_b.step(k, update=slices[k])
+        assert float(la.item()) == pytest.approx(float(lb.item()), rel=1e-4)
+    for k in ("means", "log_scales", "quats", "opacity_logits", "sh", "start", "expire"):
+        assert torch.equal(getattr(st_a, k), getattr(st_b, k)), k
+    r.close()
+
+
 def test_step_without_images_matches():
     """A trainer that writes no image (the L1 term and its gradient come from
     the forward's epilogue, out=False) takes the same steps, bit for bit (Adam
