@@ -58,7 +58,7 @@ TRAFFIC_CAPTURES = {
     ("blend_bwd", "16x16/b32/ppt8"): {
         "bytes": 1_232_882_176 + 16_189_696,
         "sources": ("csrc/k_blend.cu", "csrc/swgs_internal.cuh"),
-        "digest": "cc5a5e178ffdeeb0",
+        "digest": "6b517d14f249e466",
     },
 }
 
