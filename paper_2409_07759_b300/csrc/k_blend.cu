@@ -645,7 +645,6 @@ __device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float
                                           const float2 (&dL1)[NP], const float2 (&dL2)[NP],
                                           float2& S0, float2& SY, float2& SYY, float2& M6,
                                           float2& M7, float2& M8) {
-    const float2 one2 = make_float2(1.f, 1.f);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         const float2 dy = __fadd2_rn(py[i], hi2(ga));
@@ -665,8 +664,9 @@ __device__ __forceinline__ void bwd_pairs(float4 ga, float4 gb, float4 gc, float
         }
         // T before this Gaussian, recovered from the T after it (a pair that
         // does not count has alpha = 0 and leaves T as is)
-        const float2 om = __fadd2_rn(one2, na);
-        T[i] = __fmul2_rn(T[i], make_float2(rcp_approx(om.x), rcp_approx(om.y)));
+        // (scalar: the reciprocals need not be made a register pair)
+        T[i].x = __fmul_rn(T[i].x, rcp_approx(__fadd_rn(1.f, na.x)));
+        T[i].y = __fmul_rn(T[i].y, rcp_approx(__fadd_rn(1.f, na.y)));
         const float2 nw = __fmul2_rn(na, T[i]);            // -w
         M6 = __ffma2_rn(nw, dL0[i], M6);
         M7 = __ffma2_rn(nw, dL1[i], M7);
@@ -713,7 +713,6 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 8 ? 16 : 1)) blend_bwd_
     const unsigned F = 0xffffffffu;
     const int tid = threadIdx.x;
     const int lx = tid % TW, ly = (tid / TW) * PPT;
-    const float2 one2 = make_float2(1.f, 1.f);
     for (int k = tid; k < BATCH * 9; k += NT) s_acc[k] = 0.f;
     for (;;) {
         if (tid == 0) { s_item = atomicAdd(a.work_counter, 1); s_maxlast = 0; }
