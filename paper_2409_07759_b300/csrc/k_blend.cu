@@ -242,7 +242,7 @@ __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); 
 // only case in which alpha can take the 0.99 clamp.
 __device__ __forceinline__ bool stage_gaussian_fwd(const Records& rec, uint32_t r, int pos1,
                                                    float4* sa, float4* sb, float4* sc, float4* sd,
-                                                   float4* se) {
+                                                   float4* se, float* opacity) {
     const float4 A = rec.a[r];
     const float4 B = rec.b[r];
     const float4 Cc = rec.c[r];
@@ -254,6 +254,7 @@ __device__ __forceinline__ bool stage_gaussian_fwd(const Records& rec, uint32_t 
     *sc = make_float4(qc, qc, lo, lo);
     *sd = make_float4(-Cc.x, -Cc.x, -Cc.y, -Cc.y);
     *se = make_float4(-Cc.z, -Cc.z, pair_vmin(lo), __int_as_float(pos1));
+    *opacity = A.z;
     return A.z > kAlphaMax;
 }
 
@@ -263,7 +264,7 @@ __device__ __forceinline__ bool stage_gaussian_fwd(const Records& rec, uint32_t 
 // the reverse blend splits on the same per-Gaussian flag, and both passes take
 // the same alpha. COUNT: also records each pixel's stopping position (the
 // pair-counting form, not timed).
-template <bool CLAMP, int NP, bool COUNT>
+template <bool CLAMP, int NP, bool COUNT, bool NOSTOP = false>
 __device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float4 gd, float4 ge,
                                           float2 bdx, float2 k, int pos,
                                           float2 (&T)[NP], float2 (&C0)[NP], float2 (&C1)[NP],
@@ -279,6 +280,21 @@ __device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float
         if (CLAMP) {
             nal.x = fmaxf(-kAlphaMax, nal.x);
             nal.y = fmaxf(-kAlphaMax, nal.y);
+        }
+        if (NOSTOP) {
+            // no pixel can stop in this chunk (the caller's bound): every
+            // pair that passes the threshold is included
+            const bool ok0 = v.x >= ge.z, ok1 = v.y >= ge.z;
+            nal.x = ok0 ? nal.x : 0.f;
+            nal.y = ok1 ? nal.y : 0.f;
+            last[2 * i] = ok0 ? pos1 : last[2 * i];
+            last[2 * i + 1] = ok1 ? pos1 : last[2 * i + 1];
+            const float2 nw = __fmul2_rn(nal, T[i]);      // -w
+            C0[i] = __ffma2_rn(lo2(gd), nw, C0[i]);
+            C1[i] = __ffma2_rn(hi2(gd), nw, C1[i]);
+            C2[i] = __ffma2_rn(lo2(ge), nw, C2[i]);
+            T[i] = __fadd2_rn(T[i], nw);
+            continue;
         }
         // T (1 - alpha), rounded once: the stopping test
         const float2 tT = __ffma2_rn(nal, T[i], T[i]);
@@ -303,7 +319,7 @@ __device__ __forceinline__ void fwd_pairs(float4 ga, float4 gb, float4 gc, float
 }
 
 // One staged Gaussian j: its terms from shared memory, then fwd_pairs.
-template <bool CLAMP, int NP, bool COUNT>
+template <bool CLAMP, int NP, bool COUNT, bool NOSTOP = false>
 __device__ __forceinline__ void fwd_step(const float4* sa, const float4* sb, const float4* sc,
                                          const float4* sd, const float4* se, int j, int pos,
                                          float2 px2, float2 (&T)[NP], float2 (&C0)[NP],
@@ -313,7 +329,8 @@ __device__ __forceinline__ void fwd_step(const float4* sa, const float4* sb, con
     const float2 dx = __fadd2_rn(px2, lo2(ga));
     const float2 bdx = __fmul2_rn(hi2(gb), dx);
     const float2 k = __ffma2_rn(__fmul2_rn(lo2(gb), dx), dx, hi2(gc));
-    fwd_pairs<CLAMP, NP, COUNT>(ga, gb, gc, gd, ge, bdx, k, pos, T, C0, C1, C2, py, last, stop);
+    fwd_pairs<CLAMP, NP, COUNT, NOSTOP>(ga, gb, gc, gd, ge, bdx, k, pos, T, C0, C1, C2, py, last,
+                                        stop);
 }
 
 // Whether every pixel of the thread has stopped (or lies outside the image).
@@ -341,6 +358,9 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
     constexpr int NP = PPT / 2;
     __shared__ float4 sa[BATCH], sb[BATCH], sc[BATCH], sd[BATCH], se[BATCH];
     __shared__ unsigned s_cm[BATCH / 32];  // clamp bits of the staged Gaussians
+    // per chunk of kFwdUnroll staged Gaussians: a lower bound on the product
+    // of their (1 - alpha) (each alpha is at most the Gaussian's opacity)
+    __shared__ float s_cp[BATCH / kFwdUnroll];
     __shared__ int s_item;
     const unsigned F = 0xffffffffu;
     const int tid = threadIdx.x;
@@ -384,11 +404,18 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
             for (int k = tid; k < BATCH; k += NT) {
                 const int idx = b0 + k;
                 bool cl = false;
+                float op = 0.f;
                 if (idx < rg.y)
                     cl = stage_gaussian_fwd(a.rec, a.vals[idx], idx - rg.x + 1, &sa[k], &sb[k],
-                                            &sc[k], &sd[k], &se[k]);
+                                            &sc[k], &sd[k], &se[k], &op);
                 const unsigned m = __ballot_sync(F, cl);
                 if ((tid & 31) == 0) s_cm[k >> 5] = m;
+                // 1% below (1 - opacity) a Gaussian: covers the FP32 rounding
+                // of alpha and of T over a chunk
+                float f = (1.f - fminf(op, kAlphaMax)) * 0.99f;
+#pragma unroll
+                for (int o = 1; o < kFwdUnroll; o <<= 1) f *= __shfl_xor_sync(F, f, o);
+                if ((k & (kFwdUnroll - 1)) == 0) s_cp[k / kFwdUnroll] = f;
             }
             __syncthreads();
             const int cnt = min(BATCH, rg.y - b0);
@@ -396,7 +423,23 @@ __global__ void __launch_bounds__(TW * TH / PPT, (PPT == 4 ? 16 : 1)) blend_fwd_
             for (; j2 < cnt; j2 += kFwdUnroll) {
                 if (__all_sync(F, tdone)) break;
                 const unsigned cm = (s_cm[j2 >> 5] >> (j2 & 31)) & ((1u << kFwdUnroll) - 1u);
-                if (cm == 0u && j2 + kFwdUnroll <= cnt) {
+                // the warp's smallest transmittance over its pixels still going
+                float tmin = INFINITY;
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    tmin = fminf(tmin, py[i].x == kGone ? INFINITY : T[i].x);
+                    tmin = fminf(tmin, py[i].y == kGone ? INFINITY : T[i].y);
+                }
+                tmin = __uint_as_float(__reduce_min_sync(F, __float_as_uint(tmin)));
+                if (cm == 0u && j2 + kFwdUnroll <= cnt && tmin * s_cp[j2 / kFwdUnroll] >= kTStop) {
+                    // T (1 - alpha) stays at or above the stop threshold for every
+                    // pixel and Gaussian of the chunk: no stop test is needed
+#pragma unroll
+                    for (int jj = 0; jj < kFwdUnroll; ++jj)
+                        fwd_step<false, NP, COUNT, true>(sa, sb, sc, sd, se, j2 + jj,
+                                                         b0 + j2 + jj, px2, T, C0, C1, C2, py,
+                                                         last, stop);
+                } else if (cm == 0u && j2 + kFwdUnroll <= cnt) {
 #pragma unroll
                     for (int jj = 0; jj < kFwdUnroll; ++jj)
                         fwd_step<false, NP, COUNT>(sa, sb, sc, sd, se, j2 + jj, b0 + j2 + jj,
