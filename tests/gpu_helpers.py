@@ -2,14 +2,17 @@
 through the C ABI, with the FP64 oracle on the same seeded inputs)."""
 import numpy as np
 
-# Tolerances (BASELINE): pixels 1e-4 max abs, gradients 1e-3 relative.
+# Parity tolerances of the FP32 path against the FP64 oracle: pixels 1e-4 max
+# abs, gradients 1e-3 relative.
 PIX_TOL = 1e-4
 GRAD_REL_TOL = 1e-3
 # Near-discontinuity bands (relative) within which FP32 and FP64 may decide a
-# threshold differently; pixels touched by such a pair are reported and left
-# out of the 1e-4 check (they are never silently dropped: the count is asserted
-# to stay small). From FP32 error: m is off by at most ~1e-5 relative (conic
-# conditioning), alpha by ~m/2 of that (<= 4.5e-5), the running T by ~1e-4.
+# threshold differently. A pixel touched by such a pair is flagged: it leaves
+# the plain 1e-4 comparison and is instead checked against every valid result
+# the oracle's decision replay gives for it (check_flagged), and the flagged
+# count is asserted to stay small. From FP32 error: m is off by at most ~1e-5
+# relative (conic conditioning), alpha by ~m/2 of that (<= 4.5e-5), the
+# running T by ~1e-4.
 BANDS = dict(m=3e-5, alpha=6e-5, t_stop=5e-4, clamp=6e-5, guard=1e-4, colour=1e-5)
 
 
