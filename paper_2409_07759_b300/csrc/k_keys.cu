@@ -187,29 +187,33 @@ __device__ __forceinline__ void spread_mask(unsigned m, unsigned out[4]) {
     }
 }
 
-// Per-tile lists of one super tile (one block per super tile, NW warps). The
-// super tile's depth-ordered keys are taken in chunks of one key per thread;
-// warp w holds keys [32w, 32w + 32) of a chunk. For each chunk:
+// Per-tile lists of one part of one super tile (`parts` blocks per super
+// tile, NW warps each). The super tile's depth-ordered keys are cut into
+// `parts` consecutive runs, one per block; a block takes its run in chunks of
+// one key per thread, warp w holding keys [32w, 32w + 32) of a chunk. For
+// each chunk:
 //  - every warp counts, per tile bit, its keys with the bit set (the spread
 //    mask summed over the warp: four warp reductions for 16 tiles);
-//  - the counting pass adds the counts up per tile and writes the tiles' list
-//    lengths;
+//  - the counting pass adds the counts up per tile and writes the part's
+//    count of each tile to tcount[tile * parts + part];
 //  - the writing pass takes, per tile, the count of earlier warps of the chunk
-//    plus the tile's running total as the warp's offset and appends its keys
-//    with the bit set at offset + (rank among the warp's set lanes): every
-//    tile's list keeps the depth order. It then writes the tiles' ranges at
-//    their offsets from the scan of the lengths (never past cap).
+//    plus the part's running total as the warp's offset and appends its keys
+//    with the bit set at offset + (rank among the warp's set lanes). The
+//    offsets come from the exclusive scan of tcount, which runs tile by tile
+//    and, within a tile, part by part in key order, so every tile's list is
+//    contiguous and keeps the depth order whatever the number of parts. The
+//    last part writes the tiles' ranges (never past cap).
 template <int SX, int SY, int NW, bool WRITE>
 __global__ void __launch_bounds__(NW * 32)
 expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict__ skeys,
                     const uint32_t* __restrict__ svals, const ViewDev* __restrict__ views,
-                    int n_views, uint32_t* __restrict__ tcount, const uint32_t* __restrict__ toff,
-                    uint32_t* __restrict__ vals, long long cap, int2* __restrict__ ranges,
-                    const uint32_t* __restrict__ sort_err) {
+                    int n_views, int parts, uint32_t* __restrict__ tcount,
+                    const uint32_t* __restrict__ toff, uint32_t* __restrict__ vals, long long cap,
+                    int2* __restrict__ ranges, const uint32_t* __restrict__ sort_err) {
     static_assert(SX * SY == 16, "16 tiles per super tile");
     constexpr int NT = NW * 32;
     __shared__ __align__(16) uint32_t s_cnt[NW][4];
-    const int sup = blockIdx.x;
+    const int sup = blockIdx.x / parts, part = blockIdx.x - sup * parts;
     const ViewDev& V = views[find_view_by_super(views, n_views, sup)];
     const int ls = sup - V.super_base;
     const int tx0 = (ls % V.nsx) * SX, ty0 = (ls / V.nsx) * SY;
@@ -217,7 +221,11 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
     // a super-key sort whose look-back wait ran out leaves stale keys and
     // values: every tile then gets an empty list (the call reports the failure)
     const bool sort_failed = sort_err && *sort_err != 0u;
-    const int b = sr.x, L = sort_failed ? 0 : sr.y - sr.x;
+    const int Ls = sort_failed ? 0 : sr.y - sr.x;
+    // this part's run of the super tile's keys: [p seg, (p + 1) seg) within Ls
+    const int seg = (Ls + parts - 1) / parts;
+    const int p0 = min(part * seg, Ls), p1 = min(p0 + seg, Ls);
+    const int b = sr.x + p0, L = p1 - p0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     // lane t < 16 of every warp tracks tile t of the super tile
@@ -227,7 +235,8 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
     // offsets in 32 bits: a batch holds fewer than 2^31 tile keys (checked when
     // it is sized), so cap and every offset below fit
     const uint32_t cap32 = (uint32_t)(cap < 0x7fffffffLL ? cap : 0x7fffffffLL);
-    uint32_t run = (WRITE && lvalid) ? toff[ltile] : 0u;  // tile's next offset
+    const long long lslot = (long long)ltile * parts + part;  // tcount / toff slot
+    uint32_t run = (WRITE && lvalid) ? toff[lslot] : 0u;  // tile's next offset
     uint32_t total = 0;                                  // counting pass
     for (int c0 = 0; c0 < L; c0 += NT) {
         const int i = c0 + threadIdx.x;
@@ -271,25 +280,44 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
     }
     if (warp == 0 && lvalid) {
         if (WRITE) {
-            const uint32_t s0 = toff[ltile];
-            ranges[ltile] = make_int2((int)(s0 < cap32 ? s0 : cap32), (int)(run < cap32 ? run : cap32));
+            if (part == parts - 1) {
+                const uint32_t s0 = toff[(long long)ltile * parts];
+                ranges[ltile] = make_int2((int)(s0 < cap32 ? s0 : cap32),
+                                          (int)(run < cap32 ? run : cap32));
+            }
         } else {
-            tcount[ltile] = (uint32_t)total;
+            tcount[lslot] = (uint32_t)total;
         }
     }
 }
 
 template <int NW, bool WRITE>
 static void expand_shape(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
-                         const ViewDev* views, int n_views, int total_supers, int tile_w,
-                         uint32_t* tcount, const uint32_t* toff, uint32_t* vals, long long cap,
-                         int2* ranges, const uint32_t* sort_err, cudaStream_t s) {
+                         const ViewDev* views, int n_views, int total_supers, int parts,
+                         int tile_w, uint32_t* tcount, const uint32_t* toff, uint32_t* vals,
+                         long long cap, int2* ranges, const uint32_t* sort_err, cudaStream_t s) {
+    const int grid = total_supers * parts;
     if (tile_w == 32)
-        expand_tiles_kernel<2, 8, NW, WRITE><<<total_supers, NW * 32, 0, s>>>(
-            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges, sort_err);
+        expand_tiles_kernel<2, 8, NW, WRITE><<<grid, NW * 32, 0, s>>>(
+            sranges, skeys, svals, views, n_views, parts, tcount, toff, vals, cap, ranges,
+            sort_err);
     else
-        expand_tiles_kernel<4, 4, NW, WRITE><<<total_supers, NW * 32, 0, s>>>(
-            sranges, skeys, svals, views, n_views, tcount, toff, vals, cap, ranges, sort_err);
+        expand_tiles_kernel<4, 4, NW, WRITE><<<grid, NW * 32, 0, s>>>(
+            sranges, skeys, svals, views, n_views, parts, tcount, toff, vals, cap, ranges,
+            sort_err);
+}
+
+// Parts per super tile. A block's time is its run of keys, and a grid of few
+// super tiles (a batch of one or a few views, whose lists are long) leaves
+// most SMs idle with one block per super tile; such a grid cuts each super
+// tile's keys into enough parts for about four blocks per SM (at most 16
+// parts). A grid of at least that many super tiles (a training window) keeps
+// one block per super tile.
+int expand_parts(int total_supers, int num_sms) {
+    const long long target = 4LL * num_sms;
+    if (total_supers <= 0 || total_supers >= target) return 1;
+    const long long p = (target + total_supers - 1) / total_supers;
+    return (int)(p < 16 ? p : 16);
 }
 
 // Warps per super tile: a block's time is its super tile's list, so a grid of
@@ -307,37 +335,41 @@ int expand_warps(int total_supers, int num_sms) {
 
 template <bool WRITE>
 static cudaError_t run_expand(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
-                              const ViewDev* views, int n_views, int total_supers, int tile_w,
-                              int num_sms, uint32_t* tcount, const uint32_t* toff, uint32_t* vals,
-                              long long cap, int2* ranges, const uint32_t* sort_err,
-                              cudaStream_t s) {
+                              const ViewDev* views, int n_views, int total_supers, int parts,
+                              int tile_w, int num_sms, uint32_t* tcount, const uint32_t* toff,
+                              uint32_t* vals, long long cap, int2* ranges,
+                              const uint32_t* sort_err, cudaStream_t s) {
     if (total_supers <= 0) return cudaSuccess;
+    if (parts < 1 || parts > 16 || (long long)total_supers * parts > 0x7fffffffLL)
+        return cudaErrorInvalidValue;
     note_launch();
-    const int nw = expand_warps(total_supers, num_sms);
+    const int nw = expand_warps(total_supers * parts, num_sms);
     if (nw == 16)
-        expand_shape<16, WRITE>(sranges, skeys, svals, views, n_views, total_supers, tile_w,
-                                tcount, toff, vals, cap, ranges, sort_err, s);
+        expand_shape<16, WRITE>(sranges, skeys, svals, views, n_views, total_supers, parts,
+                                tile_w, tcount, toff, vals, cap, ranges, sort_err, s);
     else if (nw == 8)
-        expand_shape<8, WRITE>(sranges, skeys, svals, views, n_views, total_supers, tile_w,
-                               tcount, toff, vals, cap, ranges, sort_err, s);
+        expand_shape<8, WRITE>(sranges, skeys, svals, views, n_views, total_supers, parts,
+                               tile_w, tcount, toff, vals, cap, ranges, sort_err, s);
     else
-        expand_shape<4, WRITE>(sranges, skeys, svals, views, n_views, total_supers, tile_w,
-                               tcount, toff, vals, cap, ranges, sort_err, s);
+        expand_shape<4, WRITE>(sranges, skeys, svals, views, n_views, total_supers, parts,
+                               tile_w, tcount, toff, vals, cap, ranges, sort_err, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
-                                int n_views, int total_supers, int tile_w, int num_sms,
-                                uint32_t* tcount, const uint32_t* sort_err, cudaStream_t s) {
-    return run_expand<false>(sranges, skeys, nullptr, views, n_views, total_supers, tile_w,
-                             num_sms, tcount, nullptr, nullptr, 0, nullptr, sort_err, s);
+                                int n_views, int total_supers, int parts, int tile_w,
+                                int num_sms, uint32_t* tcount, const uint32_t* sort_err,
+                                cudaStream_t s) {
+    return run_expand<false>(sranges, skeys, nullptr, views, n_views, total_supers, parts,
+                             tile_w, num_sms, tcount, nullptr, nullptr, 0, nullptr, sort_err, s);
 }
 
 cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
-                                const ViewDev* views, int n_views, int total_supers, int tile_w,
-                                int num_sms, const uint32_t* toff, uint32_t* vals, long long cap,
-                                int2* ranges, const uint32_t* sort_err, cudaStream_t s) {
-    return run_expand<true>(sranges, skeys, svals, views, n_views, total_supers, tile_w,
+                                const ViewDev* views, int n_views, int total_supers, int parts,
+                                int tile_w, int num_sms, const uint32_t* toff, uint32_t* vals,
+                                long long cap, int2* ranges, const uint32_t* sort_err,
+                                cudaStream_t s) {
+    return run_expand<true>(sranges, skeys, svals, views, n_views, total_supers, parts, tile_w,
                             num_sms, nullptr, toff, vals, cap, ranges, sort_err, s);
 }
 

@@ -476,15 +476,20 @@ cudaError_t launch_emit_supers(const uint32_t* order, const uint32_t* offsets, l
 cudaError_t launch_super_ranges(const uint32_t* keys, long long n, long long n_supers,
                                 int2* ranges, cudaStream_t s,
                                 const unsigned long long* n_dev = nullptr);
-// warps per super tile of the expansion for a grid of total_supers blocks
-int expand_warps(int total_supers, int num_sms);
+// warps per block of the expansion for a grid of `blocks` blocks
+int expand_warps(int blocks, int num_sms);
+// blocks per super tile of the expansion (1..16): tcount and toff then hold
+// tiles x parts entries, tile-major, and the scan runs over all of them
+int expand_parts(int total_supers, int num_sms);
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
-                                int n_views, int total_supers, int tile_w, int num_sms,
-                                uint32_t* tcount, const uint32_t* sort_err, cudaStream_t s);
+                                int n_views, int total_supers, int parts, int tile_w,
+                                int num_sms, uint32_t* tcount, const uint32_t* sort_err,
+                                cudaStream_t s);
 cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
-                                const ViewDev* views, int n_views, int total_supers, int tile_w,
-                                int num_sms, const uint32_t* toff, uint32_t* vals, long long cap,
-                                int2* ranges, const uint32_t* sort_err, cudaStream_t s);
+                                const ViewDev* views, int n_views, int total_supers, int parts,
+                                int tile_w, int num_sms, const uint32_t* toff, uint32_t* vals,
+                                long long cap, int2* ranges, const uint32_t* sort_err,
+                                cudaStream_t s);
 
 // k_mature.cu (Alg. 1 mature, schedule_expire)
 cudaError_t launch_mature_ids(const int32_t* start, long long n, int st, uint32_t* block_counts,

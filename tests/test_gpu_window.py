@@ -140,8 +140,11 @@ def test_step_without_images_matches():
     _, dl_a, loss_a, sa = r.render_l1(st, views, tg)
     img, dl_b, loss_b, sb = r.render_l1(st, views, tg, out=False)
     assert img is None
-    # the loss is summed by atomics (order-dependent rounding)
-    assert float(loss_b.item()) == pytest.approx(float(loss_a.item()), rel=1e-6)
+    # the loss is an FP32 sum of per-warp partials added by atomics in the
+    # order the blend's blocks claim tiles, which changes from launch to
+    # launch: a few thousand partials round to about u sqrt(n) ~ 4e-6 of the
+    # sum (u = 2^-24), so two launches agree to 1e-5, not bit for bit
+    assert float(loss_b.item()) == pytest.approx(float(loss_a.item()), rel=1e-5)
     for a, b in zip(dl_a, dl_b):
         assert torch.equal(a, b)
     sa.release()
