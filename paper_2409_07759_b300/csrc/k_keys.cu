@@ -187,34 +187,60 @@ __device__ __forceinline__ void spread_mask(unsigned m, unsigned out[4]) {
     }
 }
 
-// Per-tile lists of one part of one super tile (`parts` blocks per super
-// tile, NW warps each). The super tile's depth-ordered keys are cut into
-// `parts` consecutive runs, one per block; a block takes its run in chunks of
-// one key per thread, warp w holding keys [32w, 32w + 32) of a chunk. For
-// each chunk:
+// Per-tile lists of one part of one super tile (NW warps a block). Without
+// SPLIT every super tile is one block (block = super tile). With SPLIT the
+// super tiles of view v are cut into expand_view_parts(its super
+// tiles) parts each: the view's blocks follow those of the views before it,
+// its super tiles in order and each one's parts in order, and its slots of
+// the per-(tile, part) counts follow theirs likewise (tile by tile, parts
+// inner). A part is a consecutive run of the super tile's depth-ordered keys,
+// which the block takes in chunks of one key per thread, warp w holding keys
+// [32w, 32w + 32) of a chunk. For each chunk:
 //  - every warp counts, per tile bit, its keys with the bit set (the spread
 //    mask summed over the warp: four warp reductions for 16 tiles);
 //  - the counting pass adds the counts up per tile and writes the part's
-//    count of each tile to tcount[tile * parts + part];
+//    count of each tile to its slot of tcount;
 //  - the writing pass takes, per tile, the count of earlier warps of the chunk
 //    plus the part's running total as the warp's offset and appends its keys
 //    with the bit set at offset + (rank among the warp's set lanes). The
-//    offsets come from the exclusive scan of tcount, which runs tile by tile
-//    and, within a tile, part by part in key order, so every tile's list is
-//    contiguous and keeps the depth order whatever the number of parts. The
-//    last part writes the tiles' ranges (never past cap).
-template <int SX, int SY, int NW, bool WRITE>
+//    offsets come from the exclusive scan of tcount, whose slots run view by
+//    view, tile by tile and part by part in key order, so every tile's list is
+//    contiguous, in tile order, and keeps the depth order whatever the number
+//    of parts. The last part writes the tiles' ranges (never past cap).
+template <int SX, int SY, int NW, bool WRITE, bool SPLIT>
 __global__ void __launch_bounds__(NW * 32)
 expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict__ skeys,
                     const uint32_t* __restrict__ svals, const ViewDev* __restrict__ views,
-                    int n_views, int parts, uint32_t* __restrict__ tcount,
+                    int n_views, int num_sms, uint32_t* __restrict__ tcount,
                     const uint32_t* __restrict__ toff, uint32_t* __restrict__ vals, long long cap,
                     int2* __restrict__ ranges, const uint32_t* __restrict__ sort_err) {
     static_assert(SX * SY == 16, "16 tiles per super tile");
     constexpr int NT = NW * 32;
     __shared__ __align__(16) uint32_t s_cnt[NW][4];
-    const int sup = blockIdx.x / parts, part = blockIdx.x - sup * parts;
-    const ViewDev& V = views[find_view_by_super(views, n_views, sup)];
+    int vi, sup, part = 0, parts = 1;
+    long long slot_base;  // the view's first slot of tcount / toff
+    if (SPLIT) {
+        // the view holding this block, from the views' block counts
+        int bb = 0;
+        slot_base = 0;
+        for (vi = 0;; ++vi) {
+            const ViewDev& U = views[vi];
+            parts = expand_view_parts(U.nsx * U.nsy, num_sms);
+            const int nb = U.nsx * U.nsy * parts;
+            if ((int)blockIdx.x < bb + nb || vi == n_views - 1) break;
+            bb += nb;
+            slot_base += (long long)U.ntx * U.nty * parts;
+        }
+        const int local = (int)blockIdx.x - bb;
+        const int sl = local / parts;
+        part = local - sl * parts;
+        sup = views[vi].super_base + sl;
+    } else {
+        sup = blockIdx.x;
+        vi = find_view_by_super(views, n_views, sup);
+        slot_base = views[vi].tile_base;
+    }
+    const ViewDev& V = views[vi];
     const int ls = sup - V.super_base;
     const int tx0 = (ls % V.nsx) * SX, ty0 = (ls / V.nsx) * SY;
     const int2 sr = sranges[sup];
@@ -235,7 +261,9 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
     // offsets in 32 bits: a batch holds fewer than 2^31 tile keys (checked when
     // it is sized), so cap and every offset below fit
     const uint32_t cap32 = (uint32_t)(cap < 0x7fffffffLL ? cap : 0x7fffffffLL);
-    const long long lslot = (long long)ltile * parts + part;  // tcount / toff slot
+    // this tile's first slot of tcount / toff, and this part's
+    const long long tslot0 = slot_base + (long long)(ltile - V.tile_base) * parts;
+    const long long lslot = tslot0 + part;
     uint32_t run = (WRITE && lvalid) ? toff[lslot] : 0u;  // tile's next offset
     uint32_t total = 0;                                  // counting pass
     for (int c0 = 0; c0 < L; c0 += NT) {
@@ -281,7 +309,7 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
     if (warp == 0 && lvalid) {
         if (WRITE) {
             if (part == parts - 1) {
-                const uint32_t s0 = toff[(long long)ltile * parts];
+                const uint32_t s0 = toff[tslot0];
                 ranges[ltile] = make_int2((int)(s0 < cap32 ? s0 : cap32),
                                           (int)(run < cap32 ? run : cap32));
             }
@@ -293,31 +321,47 @@ expand_tiles_kernel(const int2* __restrict__ sranges, const uint32_t* __restrict
 
 template <int NW, bool WRITE>
 static void expand_shape(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
-                         const ViewDev* views, int n_views, int total_supers, int parts,
-                         int tile_w, uint32_t* tcount, const uint32_t* toff, uint32_t* vals,
+                         const ViewDev* views, int n_views, const ExpandPlan& xp, int tile_w,
+                         int num_sms, uint32_t* tcount, const uint32_t* toff, uint32_t* vals,
                          long long cap, int2* ranges, const uint32_t* sort_err, cudaStream_t s) {
-    const int grid = total_supers * parts;
-    if (tile_w == 32)
-        expand_tiles_kernel<2, 8, NW, WRITE><<<grid, NW * 32, 0, s>>>(
-            sranges, skeys, svals, views, n_views, parts, tcount, toff, vals, cap, ranges,
+    if (tile_w == 32 && xp.split)
+        expand_tiles_kernel<2, 8, NW, WRITE, true><<<xp.blocks, NW * 32, 0, s>>>(
+            sranges, skeys, svals, views, n_views, num_sms, tcount, toff, vals, cap, ranges,
+            sort_err);
+    else if (tile_w == 32)
+        expand_tiles_kernel<2, 8, NW, WRITE, false><<<xp.blocks, NW * 32, 0, s>>>(
+            sranges, skeys, svals, views, n_views, num_sms, tcount, toff, vals, cap, ranges,
+            sort_err);
+    else if (xp.split)
+        expand_tiles_kernel<4, 4, NW, WRITE, true><<<xp.blocks, NW * 32, 0, s>>>(
+            sranges, skeys, svals, views, n_views, num_sms, tcount, toff, vals, cap, ranges,
             sort_err);
     else
-        expand_tiles_kernel<4, 4, NW, WRITE><<<grid, NW * 32, 0, s>>>(
-            sranges, skeys, svals, views, n_views, parts, tcount, toff, vals, cap, ranges,
+        expand_tiles_kernel<4, 4, NW, WRITE, false><<<xp.blocks, NW * 32, 0, s>>>(
+            sranges, skeys, svals, views, n_views, num_sms, tcount, toff, vals, cap, ranges,
             sort_err);
 }
 
-// Parts per super tile. A block's time is its run of keys, and a grid of few
-// super tiles (a batch of one or a few views, whose lists are long) leaves
-// most SMs idle with one block per super tile; such a grid cuts each super
-// tile's keys into enough parts for about four blocks per SM (at most 16
-// parts). A grid of at least that many super tiles (a training window) keeps
-// one block per super tile.
-int expand_parts(int total_supers, int num_sms) {
-    const long long target = 4LL * num_sms;
-    if (total_supers <= 0 || total_supers >= target) return 1;
-    const long long p = (target + total_supers - 1) / total_supers;
-    return (int)(p < 16 ? p : 16);
+// A block's time is its run of keys. One block per super tile suits a grid of
+// many super tiles (a training window); a batch of one or a few views has few
+// super tiles with long lists -- longest in its smallest views -- and would
+// leave most SMs idle, so below 16 blocks per SM each view's super tiles are
+// cut into expand_view_parts parts.
+ExpandPlan expand_plan(const ViewDev* views, int n_views, long long total_supers,
+                       long long total_tiles, int num_sms) {
+    ExpandPlan xp{};
+    xp.split = total_supers < 16LL * num_sms;
+    if (!xp.split) {
+        xp.blocks = total_supers;
+        xp.slots = total_tiles;
+        return xp;
+    }
+    for (int v = 0; v < n_views; ++v) {
+        const int p = expand_view_parts(views[v].nsx * views[v].nsy, num_sms);
+        xp.blocks += (long long)views[v].nsx * views[v].nsy * p;
+        xp.slots += (long long)views[v].ntx * views[v].nty * p;
+    }
+    return xp;
 }
 
 // Warps per super tile: a block's time is its super tile's list, so a grid of
@@ -335,42 +379,40 @@ int expand_warps(int total_supers, int num_sms) {
 
 template <bool WRITE>
 static cudaError_t run_expand(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
-                              const ViewDev* views, int n_views, int total_supers, int parts,
+                              const ViewDev* views, int n_views, const ExpandPlan& xp,
                               int tile_w, int num_sms, uint32_t* tcount, const uint32_t* toff,
                               uint32_t* vals, long long cap, int2* ranges,
                               const uint32_t* sort_err, cudaStream_t s) {
-    if (total_supers <= 0) return cudaSuccess;
-    if (parts < 1 || parts > 16 || (long long)total_supers * parts > 0x7fffffffLL)
-        return cudaErrorInvalidValue;
+    if (xp.blocks <= 0) return cudaSuccess;
+    if (xp.blocks > 0x7fffffffLL || n_views <= 0) return cudaErrorInvalidValue;
     note_launch();
-    const int nw = expand_warps(total_supers * parts, num_sms);
+    const int nw = expand_warps((int)xp.blocks, num_sms);
     if (nw == 16)
-        expand_shape<16, WRITE>(sranges, skeys, svals, views, n_views, total_supers, parts,
-                                tile_w, tcount, toff, vals, cap, ranges, sort_err, s);
+        expand_shape<16, WRITE>(sranges, skeys, svals, views, n_views, xp, tile_w, num_sms,
+                                tcount, toff, vals, cap, ranges, sort_err, s);
     else if (nw == 8)
-        expand_shape<8, WRITE>(sranges, skeys, svals, views, n_views, total_supers, parts,
-                               tile_w, tcount, toff, vals, cap, ranges, sort_err, s);
+        expand_shape<8, WRITE>(sranges, skeys, svals, views, n_views, xp, tile_w, num_sms,
+                               tcount, toff, vals, cap, ranges, sort_err, s);
     else
-        expand_shape<4, WRITE>(sranges, skeys, svals, views, n_views, total_supers, parts,
-                               tile_w, tcount, toff, vals, cap, ranges, sort_err, s);
+        expand_shape<4, WRITE>(sranges, skeys, svals, views, n_views, xp, tile_w, num_sms,
+                               tcount, toff, vals, cap, ranges, sort_err, s);
     return cudaGetLastError();
 }
 
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
-                                int n_views, int total_supers, int parts, int tile_w,
-                                int num_sms, uint32_t* tcount, const uint32_t* sort_err,
-                                cudaStream_t s) {
-    return run_expand<false>(sranges, skeys, nullptr, views, n_views, total_supers, parts,
-                             tile_w, num_sms, tcount, nullptr, nullptr, 0, nullptr, sort_err, s);
+                                int n_views, const ExpandPlan& xp, int tile_w, int num_sms,
+                                uint32_t* tcount, const uint32_t* sort_err, cudaStream_t s) {
+    return run_expand<false>(sranges, skeys, nullptr, views, n_views, xp, tile_w, num_sms,
+                             tcount, nullptr, nullptr, 0, nullptr, sort_err, s);
 }
 
 cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
-                                const ViewDev* views, int n_views, int total_supers, int parts,
+                                const ViewDev* views, int n_views, const ExpandPlan& xp,
                                 int tile_w, int num_sms, const uint32_t* toff, uint32_t* vals,
                                 long long cap, int2* ranges, const uint32_t* sort_err,
                                 cudaStream_t s) {
-    return run_expand<true>(sranges, skeys, svals, views, n_views, total_supers, parts, tile_w,
-                            num_sms, nullptr, toff, vals, cap, ranges, sort_err, s);
+    return run_expand<true>(sranges, skeys, svals, views, n_views, xp, tile_w, num_sms, nullptr,
+                            toff, vals, cap, ranges, sort_err, s);
 }
 
 // sranges[t] = [first, last+1) of super tile t (the low 16 key bits) in the

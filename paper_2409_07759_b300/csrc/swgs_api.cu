@@ -586,19 +586,22 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
         // 4. super-tile keys, their stable sort by super tile, per-tile lists
         const SortPlan sp = make_sort_plan(0, ceil_log2(supers));
         const size_t K = (size_t)n_sk;
-        // the expansion's blocks per super tile; its counts and offsets hold
-        // one entry per tile and part
-        const int xparts = expand_parts((int)supers, ctx->num_sms);
-        const long long tslots = (long long)tiles * xparts;
+        // the expansion's launch; its counts and offsets hold one entry per
+        // tile and part
+        const ExpandPlan xp = expand_plan(B.h_views.data(), (int)B.h_views.size(), supers,
+                                          tiles, ctx->num_sms);
+        const long long tslots = xp.slots;
+        const long long tslots_cap =
+            tslots > expand_slots_bound(ctx->num_sms) ? tslots : expand_slots_bound(ctx->num_sms);
         if (!ensure(ctx, ctx->keys_a, sizeof(uint32_t) * K, s) ||
             !ensure(ctx, ctx->keys_b, sizeof(uint32_t) * K, s) ||
             !ensure(ctx, ctx->vals_tmp, sizeof(uint32_t) * K, s) ||
             !ensure(ctx, ctx->vals_b, sizeof(uint32_t) * K, s) ||
             !ensure(ctx, ctx->sranges, sizeof(int2) * (size_t)supers, s) ||
             !ensure(ctx, B.vals, sizeof(uint32_t) * (size_t)n_keys, s) ||
-            !ensure(ctx, ctx->tile_cnt, sizeof(uint32_t) * (size_t)tslots, s) ||
-            !ensure(ctx, ctx->tile_off, sizeof(uint32_t) * (size_t)tslots, s) ||
-            !ensure(ctx, ctx->scan_tmp, scan_u32_temp_bytes(tslots) + 64, s) ||
+            !ensure(ctx, ctx->tile_cnt, sizeof(uint32_t) * (size_t)tslots_cap, s) ||
+            !ensure(ctx, ctx->tile_off, sizeof(uint32_t) * (size_t)tslots_cap, s) ||
+            !ensure(ctx, ctx->scan_tmp, scan_u32_temp_bytes(tslots_cap) + 64, s) ||
             !ensure(ctx, ctx->sort_tmp, radix_temp_bytes((long long)K, ctx->num_sms), s))
             return fail(ctx, SWGS_ENOMEM, "allocation failed (keys)");
         {
@@ -625,13 +628,13 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
             CK(launch_super_ranges(skeys, (long long)K, supers, P<int2>(ctx->sranges), s,
                                    n_sk_dev));
             CK(launch_expand_count(P<int2>(ctx->sranges), skeys, P<ViewDev>(B.views),
-                                   (int)B.h_views.size(), (int)supers, xparts, tw, ctx->num_sms,
+                                   (int)B.h_views.size(), xp, tw, ctx->num_sms,
                                    P<uint32_t>(ctx->tile_cnt), sort_err_word(ctx, s), s));
             CK(exclusive_scan_u32(P<uint32_t>(ctx->tile_cnt), P<uint32_t>(ctx->tile_off),
                                   tslots, ctx->scan_tmp.p,
                                   P<unsigned long long>(ctx->totals) + 2, s));
             CK(launch_expand_write(P<int2>(ctx->sranges), skeys, svals, P<ViewDev>(B.views),
-                                   (int)B.h_views.size(), (int)supers, xparts, tw, ctx->num_sms,
+                                   (int)B.h_views.size(), xp, tw, ctx->num_sms,
                                    P<uint32_t>(ctx->tile_off), P<uint32_t>(B.vals), n_keys,
                                    P<int2>(B.ranges), sort_err_word(ctx, s), s));
         }

@@ -478,15 +478,35 @@ cudaError_t launch_super_ranges(const uint32_t* keys, long long n, long long n_s
                                 const unsigned long long* n_dev = nullptr);
 // warps per block of the expansion for a grid of `blocks` blocks
 int expand_warps(int blocks, int num_sms);
-// blocks per super tile of the expansion (1..16): tcount and toff then hold
-// tiles x parts entries, tile-major, and the scan runs over all of them
-int expand_parts(int total_supers, int num_sms);
+// Blocks per super tile of a view with view_supers super tiles when the
+// expansion splits (see expand_plan): about four blocks per SM for that view
+// alone, at most 16.
+__host__ __device__ __forceinline__ int expand_view_parts(int view_supers, int num_sms) {
+    const long long target = 4LL * num_sms;
+    if (view_supers <= 0 || view_supers >= target) return 1;
+    const long long p = (target + view_supers - 1) / view_supers;
+    return (int)(p < 16 ? p : 16);
+}
+// The expansion's launch: split (a batch of fewer than 16 super tiles per SM
+// cuts each view's super tiles into expand_view_parts parts), its blocks, and
+// the entries of its per-(tile, part) counts and offsets (the tiles when not
+// split), over which the exclusive scan runs.
+struct ExpandPlan {
+    bool split;
+    long long blocks, slots;
+};
+// A split batch has fewer than 16 x SMs super tiles of at most 16 tiles, each
+// in at most 16 parts: fewer slots than this bound, to which the counts and
+// offsets are always sized, so that no split batch grows them (a serving loop
+// sized by its largest batch then allocates nothing more).
+inline long long expand_slots_bound(int num_sms) { return 4096LL * num_sms; }
+ExpandPlan expand_plan(const ViewDev* views, int n_views, long long total_supers,
+                       long long total_tiles, int num_sms);
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
-                                int n_views, int total_supers, int parts, int tile_w,
-                                int num_sms, uint32_t* tcount, const uint32_t* sort_err,
-                                cudaStream_t s);
+                                int n_views, const ExpandPlan& xp, int tile_w, int num_sms,
+                                uint32_t* tcount, const uint32_t* sort_err, cudaStream_t s);
 cudaError_t launch_expand_write(const int2* sranges, const uint32_t* skeys, const uint32_t* svals,
-                                const ViewDev* views, int n_views, int total_supers, int parts,
+                                const ViewDev* views, int n_views, const ExpandPlan& xp,
                                 int tile_w, int num_sms, const uint32_t* toff, uint32_t* vals,
                                 long long cap, int2* ranges, const uint32_t* sort_err,
                                 cudaStream_t s);
