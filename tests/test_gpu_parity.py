@@ -103,6 +103,21 @@ def test_config1_records_keys_order_bit_exact(R, oracle_mod):
     assert _check_records_and_lists(R, oracle_mod, sc, views) > 100_000
 
 
+def test_mixed_resolution_batch_lists_bit_exact(R, oracle_mod):
+    """One batch of four resolutions (96x72, 320x240, 640x480, 1280x720) of
+    one scene: a batch of few super tiles, whose tile-list expansion cuts each
+    view's super tiles into its own number of parts (more for the smaller
+    views, whose super tiles hold longer lists). Every view's records, per-tile
+    lists and their depth order equal the oracle's bit for bit."""
+    sc, v0 = synth.tiny_scene(21, n=30_000, sh_degree=1, width=96, height=72, depth=4.0,
+                              log_scale_mean=-3.2, spread=1.2)
+    views = []
+    for w, h in ((96, 72), (320, 240), (640, 480), (1280, 720)):
+        fx, fy, cx, cy = synth.intrinsics_for(w, h)
+        views.append(synth.View(w, h, fx, fy, cx, cy, v0.R, v0.t, 0))
+    assert _check_records_and_lists(R, oracle_mod, sc, views) > 30_000
+
+
 def test_depth_ties_follow_slot_order(R, oracle_mod):
     sc, view = synth.tiny_scene(9, n=300, sh_degree=0, width=64, height=48, depth=3.0,
                                 log_scale_mean=-2.0, spread=1.0)
