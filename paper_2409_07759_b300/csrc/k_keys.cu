@@ -343,14 +343,18 @@ static void expand_shape(const int2* sranges, const uint32_t* skeys, const uint3
 }
 
 // A block's time is its run of keys. One block per super tile suits a grid of
-// many super tiles (a training window); a batch of one or a few views has few
-// super tiles with long lists -- longest in its smallest views -- and would
-// leave most SMs idle, so below 16 blocks per SM each view's super tiles are
-// cut into expand_view_parts parts.
+// many super tiles with short lists (a training window: 40 views, 95 super
+// tiles per SM); a serving batch (one to 16 views) has fewer super tiles with
+// longer lists -- longest in its smallest views -- and leaves SMs waiting on
+// them, so below 48 super tiles per SM each view's super tiles are cut into
+// expand_view_parts parts. (Each split block walks the views' part counts to
+// find its own, which is cheap for a serving batch; for the training window
+// the walk and the doubled per-block work cost more than the halved lists
+// save.)
 ExpandPlan expand_plan(const ViewDev* views, int n_views, long long total_supers,
                        long long total_tiles, int num_sms) {
     ExpandPlan xp{};
-    xp.split = total_supers < 16LL * num_sms;
+    xp.split = total_supers < 48LL * num_sms && n_views <= 64;
     if (!xp.split) {
         xp.blocks = total_supers;
         xp.slots = total_tiles;

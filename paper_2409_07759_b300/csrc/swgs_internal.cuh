@@ -482,12 +482,12 @@ int expand_warps(int blocks, int num_sms);
 // expansion splits (see expand_plan): about four blocks per SM for that view
 // alone, at most 16.
 __host__ __device__ __forceinline__ int expand_view_parts(int view_supers, int num_sms) {
-    const long long target = 4LL * num_sms;
+    const int target = 4 * num_sms;
     if (view_supers <= 0 || view_supers >= target) return 1;
-    const long long p = (target + view_supers - 1) / view_supers;
-    return (int)(p < 16 ? p : 16);
+    const int p = (target + view_supers - 1) / view_supers;
+    return p < 16 ? p : 16;
 }
-// The expansion's launch: split (a batch of fewer than 16 super tiles per SM
+// The expansion's launch: split (a batch of fewer than 48 super tiles per SM
 // cuts each view's super tiles into expand_view_parts parts), its blocks, and
 // the entries of its per-(tile, part) counts and offsets (the tiles when not
 // split), over which the exclusive scan runs.
@@ -495,11 +495,13 @@ struct ExpandPlan {
     bool split;
     long long blocks, slots;
 };
-// A split batch has fewer than 16 x SMs super tiles of at most 16 tiles, each
-// in at most 16 parts: fewer slots than this bound, to which the counts and
-// offsets are always sized, so that no split batch grows them (a serving loop
-// sized by its largest batch then allocates nothing more).
-inline long long expand_slots_bound(int num_sms) { return 4096LL * num_sms; }
+// A split view with S super tiles has at most S x 16 tiles in at most
+// ceil(4 SMs / S) <= 4 SMs / S + 1 parts: at most 64 SMs + 16 S slots, and a
+// split batch (fewer than 48 x SMs super tiles over at most 64 views) fewer
+// than 64 x 64 SMs + 16 x 48 SMs. The counts and offsets are always sized to
+// this bound, so that no split batch grows them (a serving loop sized by its
+// largest batch then allocates nothing more).
+inline long long expand_slots_bound(int num_sms) { return (64LL * 64 + 16 * 48) * num_sms; }
 ExpandPlan expand_plan(const ViewDev* views, int n_views, long long total_supers,
                        long long total_tiles, int num_sms);
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
