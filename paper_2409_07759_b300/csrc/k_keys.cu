@@ -403,6 +403,36 @@ static cudaError_t run_expand(const int2* sranges, const uint32_t* skeys, const 
     return cudaGetLastError();
 }
 
+// CUDA loads a kernel's module at its first launch unless told otherwise.
+// The expansion picks one of 24 instantiations by batch shape, so a serving
+// loop would meet some of them for the first time mid-run and stall on the
+// load; querying each one's attributes loads them all up front.
+template <int SX, int SY, int NW>
+static cudaError_t load_expand_shape() {
+    cudaFuncAttributes fa;
+    cudaError_t e;
+    if ((e = cudaFuncGetAttributes(&fa, expand_tiles_kernel<SX, SY, NW, false, false>)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncGetAttributes(&fa, expand_tiles_kernel<SX, SY, NW, false, true>)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncGetAttributes(&fa, expand_tiles_kernel<SX, SY, NW, true, false>)) !=
+        cudaSuccess)
+        return e;
+    return cudaFuncGetAttributes(&fa, expand_tiles_kernel<SX, SY, NW, true, true>);
+}
+
+cudaError_t load_expand_kernels() {
+    cudaError_t e;
+    if ((e = load_expand_shape<4, 4, 4>()) != cudaSuccess) return e;
+    if ((e = load_expand_shape<4, 4, 8>()) != cudaSuccess) return e;
+    if ((e = load_expand_shape<4, 4, 16>()) != cudaSuccess) return e;
+    if ((e = load_expand_shape<2, 8, 4>()) != cudaSuccess) return e;
+    if ((e = load_expand_shape<2, 8, 8>()) != cudaSuccess) return e;
+    return load_expand_shape<2, 8, 16>();
+}
+
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
                                 int n_views, const ExpandPlan& xp, int tile_w, int num_sms,
                                 uint32_t* tcount, const uint32_t* sort_err, cudaStream_t s) {

@@ -875,6 +875,12 @@ swgs_status swgs_create(const swgs_config* cfg, swgs_alloc_fn alloc, swgs_free_f
         return SWGS_ECUDA;
     }
     ctx->pinned_cap = 4096;
+    // every expansion instantiation loaded now, not at its first launch
+    if (load_expand_kernels() != cudaSuccess) {
+        cudaFreeHost(ctx->pinned);
+        delete ctx;
+        return SWGS_ECUDA;
+    }
     *out = ctx;
     return SWGS_OK;
 }

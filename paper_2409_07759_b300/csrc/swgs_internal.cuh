@@ -504,6 +504,8 @@ struct ExpandPlan {
 inline long long expand_slots_bound(int num_sms) { return (64LL * 64 + 16 * 48) * num_sms; }
 ExpandPlan expand_plan(const ViewDev* views, int n_views, long long total_supers,
                        long long total_tiles, int num_sms);
+// loads every instantiation of the expansion on the current device
+cudaError_t load_expand_kernels();
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
                                 int n_views, const ExpandPlan& xp, int tile_w, int num_sms,
                                 uint32_t* tcount, const uint32_t* sort_err, cudaStream_t s);
