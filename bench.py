@@ -58,7 +58,7 @@ TRAFFIC_CAPTURES = {
     ("blend_bwd", "16x16/b32/ppt8"): {
         "bytes": 1_233_212_928 + 16_238_080,
         "sources": ("csrc/k_blend.cu", "csrc/swgs_internal.cuh"),
-        "digest": "7c3b877a32d962a1",
+        "digest": "7e9f810f1153d704",
     },
 }
 

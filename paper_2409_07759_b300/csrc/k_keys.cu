@@ -344,17 +344,20 @@ static void expand_shape(const int2* sranges, const uint32_t* skeys, const uint3
 
 // A block's time is its run of keys. One block per super tile suits a grid of
 // many super tiles with short lists (a training window: 40 views, 95 super
-// tiles per SM); a serving batch (one to 16 views) has fewer super tiles with
-// longer lists -- longest in its smallest views -- and leaves SMs waiting on
-// them, so below 48 super tiles per SM each view's super tiles are cut into
-// expand_view_parts parts. (Each split block walks the views' part counts to
-// find its own, which is cheap for a serving batch; for the training window
-// the walk and the doubled per-block work cost more than the halved lists
-// save.)
+// tiles per SM, about 570 super keys per super tile); a grid of few super
+// tiles, or a serving batch of up to 16 views whose super tiles hold thousands
+// of keys, leaves SMs waiting on its longest lists -- longest in its smallest
+// views -- so each view's super tiles are cut into expand_view_parts parts:
+// always below 16 super tiles per SM, and below 48 when the lists average at
+// least 2048 keys. (Each split block walks the views' part counts to find its
+// own, and the per-block fixed work grows with the parts; on the training
+// window that costs more than the shorter lists save.)
 ExpandPlan expand_plan(const ViewDev* views, int n_views, long long total_supers,
-                       long long total_tiles, int num_sms) {
+                       long long total_tiles, long long super_keys, int num_sms) {
     ExpandPlan xp{};
-    xp.split = total_supers < 48LL * num_sms && n_views <= 64;
+    xp.split = n_views <= 64 &&
+               (total_supers < 16LL * num_sms ||
+                (total_supers < 48LL * num_sms && super_keys >= 2048LL * total_supers));
     if (!xp.split) {
         xp.blocks = total_supers;
         xp.slots = total_tiles;

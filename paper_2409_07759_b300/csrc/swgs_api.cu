@@ -589,7 +589,7 @@ swgs_status render_batch(swgs_ctx* ctx, const swgs_gaussians* g, const swgs_view
         // the expansion's launch; its counts and offsets hold one entry per
         // tile and part
         const ExpandPlan xp = expand_plan(B.h_views.data(), (int)B.h_views.size(), supers,
-                                          tiles, ctx->num_sms);
+                                          tiles, (long long)K, ctx->num_sms);
         const long long tslots = xp.slots;
         const long long tslots_cap =
             tslots > expand_slots_bound(ctx->num_sms) ? tslots : expand_slots_bound(ctx->num_sms);

@@ -487,8 +487,9 @@ __host__ __device__ __forceinline__ int expand_view_parts(int view_supers, int n
     const int p = (target + view_supers - 1) / view_supers;
     return p < 16 ? p : 16;
 }
-// The expansion's launch: split (a batch of fewer than 48 super tiles per SM
-// cuts each view's super tiles into expand_view_parts parts), its blocks, and
+// The expansion's launch: split (a batch of fewer than 16 super tiles per SM,
+// or of fewer than 48 whose super tiles average at least 2048 keys, cuts each
+// view's super tiles into expand_view_parts parts), its blocks, and
 // the entries of its per-(tile, part) counts and offsets (the tiles when not
 // split), over which the exclusive scan runs.
 struct ExpandPlan {
@@ -503,7 +504,7 @@ struct ExpandPlan {
 // largest batch then allocates nothing more).
 inline long long expand_slots_bound(int num_sms) { return (64LL * 64 + 16 * 48) * num_sms; }
 ExpandPlan expand_plan(const ViewDev* views, int n_views, long long total_supers,
-                       long long total_tiles, int num_sms);
+                       long long total_tiles, long long super_keys, int num_sms);
 // loads every instantiation of the expansion on the current device
 cudaError_t load_expand_kernels();
 cudaError_t launch_expand_count(const int2* sranges, const uint32_t* skeys, const ViewDev* views,
